@@ -1,0 +1,409 @@
+"""Pins that tie the CPU oracle to the paper and to mathematics (no GPU).
+
+Each test checks the oracle against something other than itself: exact
+solutions the discretisation must reproduce, the monolithic HDG solve (a
+different formulation), convergence orders, the paper's printed iteration
+counts (Table 1), the contraction bounds of Theorems 1 and 2, and
+conservation.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import direct
+from oracle.ehdg import Problem, l2_volume
+from oracle.geometry import face_point_coords, node_coords
+from paper_1601_06681_gb300 import workloads as W
+
+PI = math.pi
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def beta_from(X, comps):
+    return np.ascontiguousarray(np.transpose(np.stack(comps, -1), (0, 2, 1)))
+
+
+# ---------------------------------------------------------------------------
+# exact reproduction of polynomial solutions
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_steady_reproduces_polynomial_2d(p):
+    mesh = W.structured_mesh((3, 4))
+    beta = np.array([1.0, 0.5])
+    prob = Problem(mesh, p, scheme="steady", beta_const=beta)
+    # x*y lies in Q^1 already (tensor-product space)
+    ue = lambda x: 1 + x[..., 0] - 2 * x[..., 1] + x[..., 0] * x[..., 1]
+    grad = lambda x: np.stack([1 + x[..., 1], -2 + x[..., 0]], -1)
+    X, XF = node_coords(mesh, p), face_point_coords(mesh, p, prob.ref.q)
+    f = (grad(X) @ beta)[:, None, :]
+    u, uh, hist = prob.solve_step(np.zeros((prob.nel, 1, prob.Np)), g_new=ue(XF), f_new=f,
+                                  tol=1e-14, max_iter=1000)
+    assert hist[-1] < 1e-14
+    assert np.abs(u[:, 0, :] - ue(X)).max() < 1e-12
+    assert np.abs(uh - ue(XF)).max() < 1e-12
+
+
+def test_steady_reproduces_linear_variable_beta():
+    p = 2
+    mesh = W.structured_mesh((4, 3))
+    X = node_coords(mesh, p)
+    prob = Problem(mesh, p, scheme="steady", beta_nodes=beta_from(X, [X[..., 1] + 0.5, X[..., 0] + 0.2]))
+    ue = lambda x: 1 + x[..., 0] - 2 * x[..., 1]
+    f = ((X[..., 1] + 0.5) * 1 + (X[..., 0] + 0.2) * (-2))[:, None, :]
+    XF = face_point_coords(mesh, p, prob.ref.q)
+    u, uh, _ = prob.solve_step(np.zeros((prob.nel, 1, prob.Np)), g_new=ue(XF), f_new=f,
+                               tol=1e-14, max_iter=2000)
+    assert np.abs(u[:, 0, :] - ue(X)).max() < 1e-12
+
+
+def test_steady_reproduces_polynomial_3d():
+    p = 2
+    mesh = W.structured_mesh((2, 3, 2))
+    beta = np.array([0.8, -0.5, 0.3])
+    prob = Problem(mesh, p, scheme="steady", beta_const=beta)
+    ue = lambda x: 1 + x[..., 0] - x[..., 1] + 2 * x[..., 2] + x[..., 0] * x[..., 2]
+    grad = lambda x: np.stack([1 + x[..., 2], -np.ones(x.shape[:-1]), 2 + x[..., 0]], -1)
+    X, XF = node_coords(mesh, p), face_point_coords(mesh, p, prob.ref.q)
+    u, _, _ = prob.solve_step(np.zeros((prob.nel, 1, prob.Np)), g_new=ue(XF),
+                              f_new=(grad(X) @ beta)[:, None, :], tol=1e-14, max_iter=1000)
+    assert np.abs(u[:, 0, :] - ue(X)).max() < 1e-12
+
+
+def _time_exact(scheme, tfun, dtfun, n_steps=4, dt=0.05):
+    p = 2
+    mesh = W.structured_mesh((3, 3))
+    beta = np.array([0.7, 1.1])
+    prob = Problem(mesh, p, scheme=scheme, dt=dt, beta_const=beta)
+    a = lambda x: 1 + x[..., 0] - 2 * x[..., 1] + x[..., 0] * x[..., 1]
+    ga = lambda x: np.stack([1 + x[..., 1], -2 + x[..., 0]], -1)
+    X, XF = node_coords(mesh, p), face_point_coords(mesh, p, prob.ref.q)
+    ue = lambda x, t: a(x) * tfun(t)
+    f_of_t = lambda t: (a(X) * dtfun(t) + tfun(t) * (ga(X) @ beta))[:, None, :]
+    u, uh, iters, _ = prob.run(ue(X, 0.0)[:, None, :], n_steps, g_of_t=lambda t: ue(XF, t),
+                               f_of_t=f_of_t, tol=1e-14, max_iter=1000)
+    T = n_steps * dt
+    return np.abs(u[:, 0, :] - ue(X, T)).max(), np.abs(uh - ue(XF, T)).max()
+
+
+def test_backward_euler_exact_for_linear_in_time():
+    eu, euh = _time_exact("be", lambda t: 1 + 2 * t, lambda t: 2.0 + 0 * t)
+    assert eu < 1e-12 and euh < 1e-12
+
+
+def test_crank_nicolson_exact_for_quadratic_in_time():
+    eu, euh = _time_exact("cn", lambda t: 1 + t + 3 * t * t, lambda t: 1 + 6 * t)
+    assert eu < 1e-12 and euh < 1e-12
+    # backward Euler is not exact here: the test distinguishes the schemes
+    eu_be, _ = _time_exact("be", lambda t: 1 + t + 3 * t * t, lambda t: 1 + 6 * t)
+    assert eu_be > 1e-4
+
+
+# ---------------------------------------------------------------------------
+# the eHDG fixed point is the HDG solution (monolithic solve, weak traces)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", ["be_const", "be_zero_component", "cn_variable", "3d", "sw"])
+def test_fixed_point_equals_direct_solve(case):
+    rng = np.random.default_rng(11)
+    if case == "be_const":
+        mesh, p = W.structured_mesh((5, 4)), 2
+        prob = Problem(mesh, p, scheme="be", dt=0.05, beta_const=np.array([1.0, 0.5]))
+    elif case == "be_zero_component":
+        mesh, p = W.structured_mesh((4, 3)), 3
+        prob = Problem(mesh, p, scheme="be", dt=0.05, beta_const=np.array([-1.0, 0.0]))
+    elif case == "cn_variable":
+        wl = W.transport_2d_variable(n=(5, 4), p=3)
+        mesh, p = wl.mesh(), 3
+        prob = Problem(mesh, p, scheme="cn", dt=0.05, beta_nodes=wl.beta_nodes(node_coords(mesh, p)))
+    elif case == "3d":
+        mesh, p = W.structured_mesh((3, 2, 2)), 2
+        prob = Problem(mesh, p, scheme="be", dt=0.1, beta_const=np.array([1.0, 0.7, -0.4]))
+    else:
+        mesh, p = W.structured_mesh((4, 3), boundary_tag=W.TAG_WALL), 2
+        prob = Problem(mesh, p, pde="sw", scheme="be", dt=0.01, Phi=1.5)
+    u0 = rng.standard_normal((prob.nel, prob.nf, prob.Np))
+    g = None if prob.pde == "sw" else rng.standard_normal((prob.nface, prob.Nqf))
+    if case == "cn_variable":   # boundary data must lie in the trace space
+        XF = face_point_coords(mesh, p, prob.ref.q)
+        g = np.cos(3 * XF[..., 0]) * np.sin(2 * XF[..., 1] + 0.3)
+    uhn = prob.trace(u0, g) if prob.scheme == "cn" else None
+    u, uh, hist = prob.solve_step(u0, uhn, g_new=g, tol=1e-14, max_iter=2000)
+    ud, uhd = direct.solve(prob, u0, uhn, g=g)
+    assert rel(u, ud) < 1e-12
+    if case != "cn_variable":
+        assert rel(uh, uhd) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# discretisation order p+1 (Sec. 4.1, eq. exact2dsteady; Sec. 4.4)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_steady_2d_smooth_order(p):
+    ue = lambda x: np.sin(PI * x[..., 0]) * np.cos(PI * x[..., 1]) / PI
+    fe = lambda x: (x[..., 1] * np.cos(PI * x[..., 0]) * np.cos(PI * x[..., 1])
+                    - x[..., 0] * np.sin(PI * x[..., 0]) * np.sin(PI * x[..., 1]))
+    errs = []
+    for N in (4, 8, 16):
+        mesh = W.structured_mesh((N, N))
+        X = node_coords(mesh, p)
+        prob = Problem(mesh, p, scheme="steady", beta_nodes=beta_from(X, [X[..., 1], X[..., 0]]))
+        XF = face_point_coords(mesh, p, prob.ref.q)
+        u, _ = direct.solve(prob, np.zeros((prob.nel, 1, prob.Np)), g=ue(XF), f_new=fe(X)[:, None, :])
+        errs.append(l2_volume(prob, u, ue))
+    rate = math.log2(errs[-2] / errs[-1])
+    assert rate > p + 1 - 0.2, errs
+
+
+def test_shallow_water_standing_wave_order():
+    # Sec. 4.4, eq. shallowexact: walls, Phi = 1; short run with a small step
+    p, dt, n_steps = 1, 2e-4, 25
+    s2 = math.sqrt(2.0)
+    phi_e = lambda x, t: np.cos(PI * x[..., 0]) * np.cos(PI * x[..., 1]) * math.cos(s2 * PI * t)
+    errs = []
+    for N in (4, 8, 16):
+        mesh = W.structured_mesh((N, N), boundary_tag=W.TAG_WALL)
+        prob = Problem(mesh, p, pde="sw", scheme="be", dt=dt, Phi=1.0)
+        X = node_coords(mesh, p)
+        u0 = np.zeros((prob.nel, 3, prob.Np))
+        u0[:, 0, :] = phi_e(X, 0.0)
+        u, _, iters, _ = prob.run(u0, n_steps, tol=1e-13)
+        errs.append(l2_volume(prob, u, lambda x: phi_e(x, n_steps * dt)))
+    assert math.log2(errs[-2] / errs[-1]) > p + 1 - 0.2, errs
+
+
+# ---------------------------------------------------------------------------
+# Table 1: iteration counts with the paper's stopping rules
+# ---------------------------------------------------------------------------
+
+def _table1():
+    rows = []
+    with open(os.path.join(GOLDEN, "table1_iterations.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(v) for v in line.split()])
+    return rows
+
+
+def _paper_stop_error_change(prob, ue):
+    """Stopping test of Sec. 4.1 (eq. tolerancecriteria):
+    | ||u^k - u_e|| - ||u^{k-1} - u_e|| | < 1e-10."""
+    state = {"prev": None}
+
+    def stop(unew, uold):
+        e = l2_volume(prob, unew, ue)
+        pe = state["prev"] if state["prev"] is not None else l2_volume(prob, uold, ue)
+        state["prev"] = e
+        return abs(e - pe) < 1e-10
+    return stop
+
+
+def _close(ours, paper):
+    return abs(ours - paper) <= max(4, round(0.06 * paper))
+
+
+@pytest.mark.parametrize("nel2d", [16, 64])
+def test_table1_2d_smooth_iterations(nel2d):
+    ue = lambda x: np.sin(PI * x[..., 0]) * np.cos(PI * x[..., 1]) / PI
+    fe = lambda x: (x[..., 1] * np.cos(PI * x[..., 0]) * np.cos(PI * x[..., 1])
+                    - x[..., 0] * np.sin(PI * x[..., 0]) * np.sin(PI * x[..., 1]))
+    N = int(round(math.sqrt(nel2d)))
+    for row in _table1():
+        if row[0] != nel2d:
+            continue
+        p = row[2]
+        mesh = W.structured_mesh((N, N))
+        X = node_coords(mesh, p)
+        prob = Problem(mesh, p, scheme="steady", beta_nodes=beta_from(X, [X[..., 1], X[..., 0]]))
+        XF = face_point_coords(mesh, p, prob.ref.q)
+        _, _, hist = prob.solve_step(np.zeros((prob.nel, 1, prob.Np)), g_new=ue(XF),
+                                     f_new=fe(X)[:, None, :], max_iter=1000,
+                                     stop=_paper_stop_error_change(prob, ue))
+        assert _close(len(hist), row[3]), (nel2d, p, len(hist), row[3])
+
+
+@pytest.mark.parametrize("nel2d", [16, 64])
+def test_table1_2d_discontinuous_iterations(nel2d):
+    # Sec. 4.2: beta = (1 + sin(pi y / 2), 2) on [0, 2]^2, f = 0, piecewise inflow,
+    # stop on ||u^k - u^{k-1}|| < 1e-10
+    def g(x):
+        X, Y = x[..., 0], x[..., 1]
+        out = np.where(X <= 1e-14, 1.0, 0.0)
+        return np.where((Y <= 1e-14) & (X > 1e-14) & (X <= 1.0), np.sin(PI * X) ** 6, out)
+    N = int(round(math.sqrt(nel2d)))
+    for row in _table1():
+        if row[0] != nel2d:
+            continue
+        p = row[2]
+        mesh = W.structured_mesh((N, N), lo=[0, 0], hi=[2, 2])
+        X = node_coords(mesh, p)
+        prob = Problem(mesh, p, scheme="steady",
+                       beta_nodes=beta_from(X, [1 + np.sin(PI * X[..., 1] / 2), 2 + 0 * X[..., 0]]))
+        XF = face_point_coords(mesh, p, prob.ref.q)
+        _, _, hist = prob.solve_step(np.zeros((prob.nel, 1, prob.Np)), g_new=g(XF), max_iter=1000,
+                                     stop=lambda a, b: l2_volume(prob, a - b) < 1e-10)
+        assert _close(len(hist), row[4]), (nel2d, p, len(hist), row[4])
+
+
+def test_table1_3d_steady_iterations_smallest_mesh():
+    # Sec. 4.3: beta = (z, x, y), u_e = sin(pi x) cos(pi y) sin(pi z) / pi, 2x2x2 hexes
+    ue = lambda x: np.sin(PI * x[..., 0]) * np.cos(PI * x[..., 1]) * np.sin(PI * x[..., 2]) / PI
+
+    def fe(x):
+        X, Y, Z = x[..., 0], x[..., 1], x[..., 2]
+        ux = np.cos(PI * X) * np.cos(PI * Y) * np.sin(PI * Z)
+        uy = -np.sin(PI * X) * np.sin(PI * Y) * np.sin(PI * Z)
+        uz = np.sin(PI * X) * np.cos(PI * Y) * np.cos(PI * Z)
+        return Z * ux + X * uy + Y * uz
+    for row in _table1():
+        if row[1] != 8:
+            continue
+        p = row[2]
+        mesh = W.structured_mesh((2, 2, 2))
+        X = node_coords(mesh, p)
+        prob = Problem(mesh, p, scheme="steady",
+                       beta_nodes=beta_from(X, [X[..., 2], X[..., 0], X[..., 1]]))
+        XF = face_point_coords(mesh, p, prob.ref.q)
+        _, _, hist = prob.solve_step(np.zeros((prob.nel, 1, prob.Np)), g_new=ue(XF),
+                                     f_new=fe(X)[:, None, :], max_iter=1000,
+                                     stop=_paper_stop_error_change(prob, ue))
+        assert _close(len(hist), row[5]), (p, len(hist), row[5])
+
+
+# ---------------------------------------------------------------------------
+# Theorems 1 and 2
+# ---------------------------------------------------------------------------
+
+def _weighted_error_sq(prob, u):
+    """||u||^2_{-div(beta)/2, Omega} + sum_K ||u||^2_{|beta.n|, dK} (Thm 1's left side)."""
+    ref = prob.ref
+    tot = 0.0
+    for K in range(prob.nel):
+        h = prob.mesh["elem_h"][K]
+        J = np.prod(h / 2.0)
+        bn = prob.beta_nodes[K]
+        div = sum((2.0 / h[a]) * (ref.dphi[a] @ bn[a]) for a in range(prob.dim))
+        uq = ref.phi @ u[K, 0]
+        tot += np.sum(ref.W * J * (-div / 2.0) * uq * uq)
+        for f in range(2 * prob.dim):
+            ax, side = divmod(f, 2)
+            bnf = (1.0 if side else -1.0) * (ref.fphi[f] @ bn[ax])
+            uf = ref.fphi[f] @ u[K, 0]
+            tot += np.sum(ref.fW[f] * J * 2.0 / h[ax] * np.abs(bnf) * uf * uf)
+    return tot
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_theorem1_rate_half_per_iteration(p):
+    """Homogeneous steady transport with -div(beta) = 2 > 0: the weighted
+    squared error decays like C(k)/2^k with C polynomial, so the late
+    per-iteration factor is at most 1/2, whatever p."""
+    rng = np.random.default_rng(5)
+    mesh = W.structured_mesh((3, 3))
+    X = node_coords(mesh, p)
+    prob = Problem(mesh, p, scheme="steady", beta_nodes=beta_from(X, [2 - X[..., 0], 2 - X[..., 1]]))
+    A, _, cB = prob.step_system(np.zeros((prob.nel, prob.n)), None)
+    g0 = np.zeros((prob.nface, prob.Nqf))
+    u = rng.standard_normal((prob.nel, 1, prob.Np))
+    E = [_weighted_error_sq(prob, u)]
+    for _ in range(70):
+        uh = prob.trace(u, g0)
+        rhs = cB * np.einsum("eij,ej->ei", prob.B, prob.gather(uh))
+        u = np.linalg.solve(A, rhs[..., None])[..., 0].reshape(u.shape)
+        E.append(_weighted_error_sq(prob, u))
+    late = (E[70] / E[50]) ** (1.0 / 20)
+    assert late <= 0.5, late
+    assert E[70] / E[0] < 1e-12
+
+
+@pytest.mark.parametrize("N,p,Phi", [(8, 1, 1.0), (8, 2, 1.0), (4, 3, 2.0)])
+def test_theorem2_contraction_bound(N, p, Phi):
+    """||(phi^k, vel^k)||^2_{E_h} <= C^k ||(phi^0, vel^0)||^2_{E_h} for the
+    homogeneous problem, C = A/B of eq. ContractionConstant (gamma = 0, h = side)."""
+    rng = np.random.default_rng(3)
+    dt = 1e-3
+    mesh = W.structured_mesh((N, N), boundary_tag=W.TAG_WALL)
+    prob = Problem(mesh, p, pde="sw", scheme="be", dt=dt, Phi=Phi)
+    h = 1.0 / N
+    sq = math.sqrt(Phi)
+    Bc = min(h / (dt * (p + 1) * (p + 2)) + (sq - Phi) / 2,
+             h / (dt * (p + 1) * (p + 2)) + (0.0 - 1 - sq) / 2)
+    C = max((Phi + sq) / 2, (1 + sq) / 2) / Bc
+    assert Bc > 0 and C < 1
+    ref = prob.ref
+
+    def norm2(u):
+        tot = 0.0
+        for K in range(prob.nel):
+            hh = prob.mesh["elem_h"][K]
+            for f in range(4):
+                v = u[K] @ ref.fphi[f].T
+                w = ref.fW[f] * np.prod(hh / 2) * 2 / hh[f // 2]
+                tot += np.sum(w * (v[0] ** 2 + Phi * (v[1] ** 2 + v[2] ** 2)))
+        return tot
+    A, _, cB = prob.step_system(np.zeros((prob.nel, prob.n)), None)
+    u = rng.standard_normal((prob.nel, 3, prob.Np))
+    n0 = norm2(u)
+    for k in range(1, 6):
+        uh = prob.trace(u)
+        rhs = cB * np.einsum("eij,ej->ei", prob.B, prob.gather(uh))
+        u = np.linalg.solve(A, rhs[..., None])[..., 0].reshape(u.shape)
+        assert norm2(u) <= C ** k * n0
+
+
+# ---------------------------------------------------------------------------
+# conservation
+# ---------------------------------------------------------------------------
+
+def test_shallow_water_mass_conserved_and_energy_decays():
+    rng = np.random.default_rng(8)
+    p = 2
+    mesh = W.structured_mesh((5, 4), boundary_tag=W.TAG_WALL)
+    prob = Problem(mesh, p, pde="sw", scheme="be", dt=5e-3, Phi=1.0)
+    u = rng.standard_normal((prob.nel, 3, prob.Np))
+    Mb = prob.M[0]
+    ones = np.zeros(prob.n)
+    ones[:prob.Np] = 1.0
+    mass = lambda v: float(np.sum(v.reshape(prob.nel, -1) @ (Mb @ ones)))
+    energy = lambda v: float(np.einsum("ei,ij,ej->", v.reshape(prob.nel, -1), Mb, v.reshape(prob.nel, -1)))
+    m0, e0 = mass(u), energy(u)
+    for _ in range(3):
+        u, _, _ = prob.solve_step(u, tol=1e-14, max_iter=500)
+        assert abs(mass(u) - m0) <= 1e-12 * max(1.0, abs(m0)) * 10
+        e1 = energy(u)
+        assert e1 <= e0 * (1 + 1e-13)
+        e0 = e1
+
+
+def test_transport_element_conservation():
+    """Testing the local equation with v = 1 gives the element balance
+    (u - u^n)/dt |K| + outflow flux - inflow flux = int f exactly at convergence."""
+    rng = np.random.default_rng(9)
+    p = 3
+    mesh = W.structured_mesh((4, 4))
+    X = node_coords(mesh, p)
+    beta = np.array([0.9, -0.4])
+    prob = Problem(mesh, p, scheme="be", dt=0.02, beta_const=beta)
+    u0 = rng.standard_normal((prob.nel, 1, prob.Np))
+    g = rng.standard_normal((prob.nface, prob.Nqf))
+    u, uh, _ = prob.solve_step(u0, g_new=g, tol=1e-14, max_iter=500)
+    ref = prob.ref
+    for K in range(prob.nel):
+        h = mesh["elem_h"][K]
+        J = np.prod(h / 2)
+        dudt = np.sum(ref.W * J * (ref.phi @ (u[K, 0] - u0[K, 0]))) / prob.dt
+        flux = 0.0
+        for f in range(4):
+            ax, side = divmod(f, 2)
+            bn = (1.0 if side else -1.0) * beta[ax]
+            w = ref.fW[f] * J * 2 / h[ax]
+            uhat = uh[mesh["elem_face"][K, f]]
+            flux += np.sum(w * bn * uhat)        # upwind flux beta.n uhat at convergence
+        assert abs(dudt + flux) < 1e-11
