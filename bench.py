@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the eHDG hot path: trace DOF-iterations per second.
+
+Workload (default): 2D transport on 256 x 256 quads, p = 4, per-element
+velocity 0.5 (cos 2 pi y, sin 2 pi x) plus 8 seeded Fourier modes (amplitude
+0.05), Crank-Nicolson dt = 2e-3 for 50 steps, eHDG to a trace residual of
+1e-10 in every step, float64. One benchmark step = one full 50-step run from
+the initial condition (set state + 50 implicit steps), i.e. one pass of the
+whole hot path (per-step right-hand side, element sweeps, trace updates,
+residual reductions, end-of-step reconstruction).
+
+value: trace DOF x eHDG iterations / device time, inputs resident in HBM.
+e2e:   the same through the C ABI with host buffers (state, boundary data in;
+       state and trace out) inside the timed region.
+--impl reference: the CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "trace DOF-iterations/s"
+UNIT = "DOF*iter/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="mesh side (256 is the benchmark size)")
+    ap.add_argument("--time-steps", type=int, default=50)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n, n_steps):
+    from paper_1601_06681_gb300 import workloads as W
+    return W.transport_2d_variable(n=(n, n), p=4, dt=2e-3, n_steps=n_steps, tol=1e-10)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (getattr(self, "out", "") or "").splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def kernel_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source is unchanged since it was captured (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    ent = d.get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_1601_06681_gb300", "csrc", "kernels.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return ent["bytes_per_launch"] if ent.get("kernels_cu_sha") == sha else None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+def oracle_sample(n_side=32, n_time=2, repeats=1):
+    """Oracle throughput on a n_side x n_side corner of the benchmark mesh
+    (same element size 1/256, velocity field, p, dt, scheme), n_time steps."""
+    from oracle.ehdg import Problem
+    from oracle.geometry import face_point_coords, node_coords
+    from paper_1601_06681_gb300 import workloads as W
+    wl = workload(256, n_time)
+    h = 1.0 / 256
+    mesh = W.structured_mesh((n_side, n_side), lo=[0.0, 0.0], hi=[n_side * h, n_side * h])
+    X = node_coords(mesh, wl.p)
+    prob = Problem(mesh, wl.p, scheme="cn", dt=wl.dt, beta_nodes=wl.beta_nodes(X))
+    XF = face_point_coords(mesh, wl.p, prob.ref.q)
+    u0 = wl.initial(X)
+    g = wl.boundary(XF, 0.0)
+    trace_dof = mesh["n_face"] * (wl.p + 1)
+    times, units = [], []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        _, _, iters, _ = prob.run(u0, n_time, g_of_t=lambda t: g, tol=wl.tol)
+        times.append(time.perf_counter() - t0)
+        units.append(trace_dof * sum(iters))
+    return times, units, f"{n_side}x{n_side} corner of the 256x256 mesh, {n_time} CN steps"
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if ws > 1 and rank != 0:
+        return
+    wt, wu, sample = oracle_sample(repeats=max(args.warmup, 0)) if args.warmup else ([], [], "")
+    times, units, sample = oracle_sample(repeats=args.steps)
+    value = sum(units) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "transport2d_varbeta_256x256_p4_cn (oracle sample)",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    from paper_1601_06681_gb300 import build, ehdg
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    build.build()
+    ehdg.load()
+
+    wl = workload(args.n, args.time_steps)
+    mesh = ehdg.ehdg_mesh_structured((args.n, args.n))
+    stream = torch.cuda.current_stream()
+    # node coordinates come from the library (inputs are evaluated there)
+    probe = None
+    t_setup0 = time.perf_counter()
+    solver = ehdg.Solver(mesh, wl.p, scheme=wl.scheme, dt=wl.dt, tol=wl.tol, max_iter=200,
+                         beta_nodes=_beta_nodes(ehdg, mesh, wl), stream=stream)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup0
+    X = solver.node_coords()
+    XF = solver.face_point_coords()
+    u0_h = np.ascontiguousarray(wl.initial(X))
+    g_h = np.ascontiguousarray(wl.boundary(XF, 0.0))
+    u0_d = torch.from_numpy(u0_h).to(dev)
+    g_d = torch.from_numpy(g_h).to(dev)
+    solver.set_boundary(g_d)
+    trace_dof = solver.info["n_face"] * (wl.p + 1)
+
+    def one_run():
+        solver.set_state(u0_d)
+        return solver.run(wl.n_steps)
+
+    for _ in range(args.warmup):
+        one_run()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    solver.set_profiling(True)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    iters_total = 0
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            iters_total += sum(one_run())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    stats = solver.kernel_stats()
+    solver.set_profiling(False)
+    t_max = ms
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    units = trace_dof * iters_total
+    value = ws * units / (t_max * 1e-3)
+
+    # end to end through host buffers
+    u_out = np.empty(solver.state_shape)
+    uh_out = np.empty(solver.trace_shape)
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    it_e2e = 0
+    for _ in range(args.steps):
+        solver.set_boundary(g_h)
+        solver.set_state(u0_h)
+        it_e2e += sum(solver.run(wl.n_steps))
+        u_out, uh_out = solver.get_state()
+    torch.cuda.synchronize()
+    e_s = time.perf_counter() - e0
+    e2e_value = ws * trace_dof * it_e2e / e_s
+
+    # roofline of the dominant kernel (element sweep)
+    n_elem_launch, elem_ms = stats["elem"]
+    info = solver.info
+    nq = 4 * info["Nqf"]
+    bytes_per_elem = 8 * (nq * nq + 3 * nq) + 4 * 4
+    alg_bytes = bytes_per_elem * info["n_elem"]
+    avg_ms = elem_ms / max(n_elem_launch, 1)
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    flops_per_launch = 2.0 * nq * nq * info["n_elem"]
+    launches = sum(v[0] for v in stats.values())
+    share = {k: round(v[1] / max(sum(x[1] for x in stats.values()), 1e-12), 4) for k, v in stats.items()}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"transport2d_varbeta_{args.n}x{args.n}_p4_cn",
+                       "n_elem": info["n_elem"], "p": wl.p, "time_steps_per_run": wl.n_steps,
+                       "dt": wl.dt, "tol": wl.tol, "trace_dof": trace_dof,
+                       "iterations_per_run": iters_total / args.steps,
+                       "l2": "inputs larger than L2 (per-element operators "
+                             f"{info['device_bytes'] / 1e9:.2f} GB resident)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                       "setup_s": round(setup_s, 3)},
+            "e2e": {"value": e2e_value, "unit": UNIT,
+                    "h2d_bytes_per_step": int(u0_h.nbytes + g_h.nbytes),
+                    "d2h_bytes_per_step": int(u_out.nbytes + uh_out.nbytes)},
+            "gpu_launches": int(launches),
+            "roofline": {"kernel": "k_elem", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                         "traffic": kernel_traffic("k_elem"),
+                         "alg_bytes_per_launch": alg_bytes,
+                         "flops_per_launch": flops_per_launch,
+                         "achieved_fp64_tflops": flops_per_launch / (avg_ms * 1e-3) / 1e12,
+                         "avg_launch_us": avg_ms * 1e3},
+            "kernel_time_share": share,
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            times, cu, sample = oracle_sample(repeats=1)
+            line["cpu_baseline"] = {"value": sum(cu) / sum(times), "unit": UNIT, "cores": 1,
+                                    "kind": "oracle", "sample": sample}
+        print(json.dumps(line), flush=True)
+    solver.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def _beta_nodes(ehdg, mesh, wl):
+    """Nodal velocity [n_elem][2][Np] at the library's own node coordinates."""
+    # a throwaway constant-velocity context gives the node coordinates
+    tmp = ehdg.Solver(mesh, wl.p, scheme="be", dt=1.0, beta_const=[1.0, 0.0], max_iter=1)
+    X = tmp.node_coords()
+    tmp.close()
+    return wl.beta_nodes(X)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,183 @@
+/*
+ * ehdg.h -- C ABI of the GB300 eHDG library (libehdg.so).
+ *
+ * The library runs the eHDG iteration of Muralikrishnan, Tran and Bui-Thanh,
+ * "An iterative solver for HDG discretizations of hyperbolic PDEs"
+ * (arXiv 1601.06681), Algorithm 1, on one GPU: every iteration solves every
+ * element's upwind-HDG local equation for its volume unknowns given the
+ * current traces (Sec. 3, eq. transportLocalk1 for transport, eq.
+ * localSolverDD for linearised shallow water), then recomputes every face's
+ * trace from its two neighbours with the trace formula (Sec. 3, eq.
+ * transportLocale, and the shallow-water trace phihat = {{phi}} +
+ * sqrt(Phi) {{vel.n}}), and stops on a residual tolerance; one such solve
+ * runs inside every implicit time step.
+ *
+ * Conventions shared by every call:
+ *  - Every function returns an ehdg_status; none aborts, traps or exits.
+ *    On failure ehdg_last_error() (thread-local) describes the cause.
+ *  - The caller owns every pointer it passes. The library copies what it
+ *    needs during the call and owns all device memory it allocates until
+ *    ehdg_destroy.
+ *  - Pointers are HOST pointers unless the argument `on_device` is non-zero,
+ *    in which case they are device pointers valid on the context's device.
+ *    Device-pointer transfers are ordered on the context's stream.
+ *  - Meshes are conforming, axis-aligned quads (dim 2) or hexes (dim 3).
+ *    Local faces are numbered f = 2*axis + side (order -x,+x,-y,+y,-z,+z).
+ *    On every face the minus element sees n^- = +e_axis when it lies on the
+ *    low side (interior faces) and the outward normal on boundary faces.
+ *  - Volume unknowns of an element are tensor-product Lagrange values at the
+ *    (p+1)^dim Gauss-Lobatto-Legendre nodes, node i = a0 + (p+1) a1 +
+ *    (p+1)^2 a2; a state array is [n_elem][nf][Np] with nf = 1 (transport)
+ *    or 3 (shallow water: phi, u, v).
+ *  - Traces are stored by their values at the q^(dim-1) Gauss points of each
+ *    face (tangential axes in increasing order, first one fastest), the
+ *    points where the local equations use them: a trace array is
+ *    [n_face][Nqf]. q = p+1 for a constant velocity and ceil(3p/2)+1 for a
+ *    per-node velocity, which integrates every face and volume term exactly.
+ */
+#ifndef EHDG_H
+#define EHDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ehdg_ctx_s* ehdg_ctx;
+
+typedef enum {
+  EHDG_OK = 0,
+  EHDG_ERR_INVALID = 1,        /* bad argument or inconsistent mesh */
+  EHDG_ERR_OOM = 2,            /* device allocation failed */
+  EHDG_ERR_CUDA = 3,           /* a CUDA call failed */
+  EHDG_ERR_NOT_CONVERGED = 4,  /* max_iter reached; state and history stay readable */
+  EHDG_ERR_DIVERGED = 5,       /* non-finite residual */
+  EHDG_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  EHDG_ERR_UNSUPPORTED = 7     /* size or option outside what this build supports */
+} ehdg_status;
+
+typedef enum { EHDG_TRANSPORT = 0, EHDG_SW_LINEAR = 1 } ehdg_pde;
+
+/* Time discretisation of one implicit step. BE: backward Euler (Sec. 3).
+ * CN: Crank-Nicolson, (M/dt)(u^{n+1}-u^n) + 1/2[a(u^{n+1},uhat^{n+1}) +
+ * a(u^n,uhat^n)] = 1/2(F^{n+1}+F^n). STEADY: the steady problem of Sec. 3
+ * (eq. transport). */
+typedef enum { EHDG_BE = 0, EHDG_CN = 1, EHDG_STEADY = 2 } ehdg_scheme;
+
+typedef enum { EHDG_FP64 = 0, EHDG_MIXED_TF32 = 1, EHDG_MIXED_BF16 = 2 } ehdg_precision;
+
+/* Face tags. */
+enum { EHDG_FACE_INTERIOR = 0, EHDG_FACE_DIRICHLET = 1, EHDG_FACE_WALL = 2 };
+
+/* Mesh: partition of the domain into elements K_j and the skeleton of
+ * unique faces (Sec. 2). All arrays are caller-owned and copied at create. */
+typedef struct {
+  int dim;                     /* 2 or 3 */
+  int64_t n_elem, n_face;
+  const double*  elem_lo;      /* [n_elem][dim] lower corner */
+  const double*  elem_h;       /* [n_elem][dim] edge lengths (> 0) */
+  const int64_t* elem_face;    /* [n_elem][2*dim] face id of local face f */
+  const int64_t* face_elem;    /* [n_face][2] minus, plus element; plus = -1 on the boundary */
+  const int8_t*  face_local;   /* [n_face][2] local face on each side; -1 for a missing plus */
+  const int32_t* face_tag;     /* [n_face] EHDG_FACE_*: transport boundaries must be DIRICHLET,
+                                  shallow-water boundaries WALL */
+} ehdg_mesh_desc;
+
+/* Problem (Sec. 3): PDE, degree, velocity or mean depth, time step, tolerance. */
+typedef struct {
+  ehdg_pde pde;
+  int p;                       /* polynomial degree, 1..6 (dim 2), 1..3 (dim 3) */
+  ehdg_scheme scheme;
+  double dt;                   /* time step (ignored for STEADY) */
+  double tol;                  /* stop when ||uhat^{k+1}-uhat^k||_{L2(E_h)} < tol */
+  int max_iter;                /* iteration cap per step, >= 1 */
+  ehdg_precision precision;    /* EHDG_FP64 in this build */
+  const double* beta_const;    /* [dim] constant velocity, or NULL */
+  const double* beta_nodes;    /* [n_elem][dim][Np] nodal velocity, or NULL (transport) */
+  double Phi;                  /* shallow water: mean geopotential Phi > 0 */
+} ehdg_problem_desc;
+
+/* Sizes of a created context. */
+typedef struct {
+  int dim, p, nf, Np, q, Nqf;  /* Np nodes per field, q Gauss points per axis, Nqf per face */
+  int64_t n_elem, n_face;
+  int64_t state_len;           /* n_elem * nf * Np */
+  int64_t trace_len;           /* n_face * Nqf */
+  int shared_operator;         /* 1 if one local operator serves every element */
+  int64_t device_bytes;        /* device memory held by the context */
+} ehdg_info;
+
+/* Structured N0 x N1 (x N2) mesh of the box [lo, hi] with the numbering
+ * above (faces axis by axis, axis 0 fastest within an axis); boundary faces
+ * get `boundary_tag`. Arrays are library-owned: release with ehdg_mesh_free. */
+ehdg_status ehdg_mesh_structured(int dim, const int64_t n[3], const double lo[3],
+                                 const double hi[3], int32_t boundary_tag, ehdg_mesh_desc* out);
+void ehdg_mesh_free(ehdg_mesh_desc* mesh);
+
+/* Validate the mesh, upload it, assemble every local operator of Sec. 3
+ * (eq. transportLocal or localSolverDD plus the time term) on the GPU and
+ * factor it. `cuda_stream` is a cudaStream_t (NULL: the legacy default
+ * stream) on which all later work of the context is ordered. */
+ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* prob,
+                        void* cuda_stream, ehdg_ctx* out);
+ehdg_status ehdg_get_info(ehdg_ctx ctx, ehdg_info* out);
+void ehdg_destroy(ehdg_ctx ctx);
+
+/* Physical coordinates of the volume nodes [n_elem][Np][dim] and of the face
+ * Gauss points [n_face][Nqf][dim] (from the minus element), host arrays. */
+ehdg_status ehdg_node_coords(ehdg_ctx ctx, double* x);
+ehdg_status ehdg_face_point_coords(ehdg_ctx ctx, double* x);
+
+/* Set the state u^n [n_elem][nf][Np]. The trace of the state is the trace
+ * formula applied to u with the current boundary data (Algorithm 1's initial
+ * trace), unless `uhat` [n_face][Nqf] is given. */
+ehdg_status ehdg_set_state(ehdg_ctx ctx, const double* u, const double* uhat, int on_device);
+/* Forcing at the new time level, nodal values [n_elem][nf][Np] of the right-hand
+ * side of u_t + beta.grad u = f (transport) or phi_t + Phi div vel = f_phi,
+ * vel_t + grad phi = f_vel (shallow water); NULL sets zero. */
+ehdg_status ehdg_set_forcing(ehdg_ctx ctx, const double* f, int on_device);
+/* Boundary data g at the face points [n_face][Nqf] for the new time level
+ * (entries of interior faces are ignored). Transport: the exterior value in
+ * the trace formula, so uhat = g where beta.n^- < 0. Kept until replaced;
+ * Crank-Nicolson also keeps the previous level's data. */
+ehdg_status ehdg_set_boundary(ehdg_ctx ctx, const double* g, int on_device);
+
+/* One implicit step (Algorithm 1 from the warm start u^n). Writes the number of
+ * iterations and the last residual; EHDG_ERR_NOT_CONVERGED if max_iter was
+ * reached (the iterate is still the new state). */
+ehdg_status ehdg_step(ehdg_ctx ctx, int* iters, double* final_residual);
+/* n_steps implicit steps; iters_per_step [n_steps] may be NULL. Boundary data
+ * and forcing stay as last set. */
+ehdg_status ehdg_run(ehdg_ctx ctx, int n_steps, int* iters_per_step);
+/* Exactly n_iter eHDG iterations of the current step from the warm start,
+ * without the convergence test (the step is then completed as by ehdg_step). */
+ehdg_status ehdg_step_fixed(ehdg_ctx ctx, int n_iter);
+
+ehdg_status ehdg_get_state(ehdg_ctx ctx, double* u, double* uhat, int on_device);
+/* Residual history r_0, r_1, ... of the last step (host buffer of cap entries). */
+ehdg_status ehdg_get_residual_history(ehdg_ctx ctx, double* buf, int64_t cap, int64_t* n_out);
+
+/* Kernel accounting. Every launch is counted per kind; with profiling on,
+ * each launch is also bracketed by CUDA events on the context's stream and
+ * ehdg_kernel_stats returns the summed device time of the kind (it
+ * synchronises the stream). Turning profiling on resets the counters. */
+typedef enum {
+  EHDG_KERNEL_ASSEMBLE = 0,    /* local operator assembly + factorisation (setup) */
+  EHDG_KERNEL_SIGNS = 1,       /* sgn(beta.n) at face points (setup) */
+  EHDG_KERNEL_STEP = 2,        /* per-step right-hand side G = P w */
+  EHDG_KERNEL_ELEM = 3,        /* element sweep Y = Gy + Hy uhat */
+  EHDG_KERNEL_FACE = 4,        /* trace formula + residual */
+  EHDG_KERNEL_FINAL = 5,       /* end-of-step reconstruction */
+  EHDG_KERNEL_AUX = 6,         /* transposes, extraction, resets */
+  EHDG_KERNEL_KINDS = 7
+} ehdg_kernel_kind;
+ehdg_status ehdg_set_profiling(ehdg_ctx ctx, int on);
+ehdg_status ehdg_kernel_stats(ehdg_ctx ctx, int kind, int64_t* launches, double* total_ms);
+
+const char* ehdg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EHDG_H */

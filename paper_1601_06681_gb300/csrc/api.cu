@@ -1,0 +1,771 @@
+// C ABI of libehdg: validation, device memory, per-step orchestration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ehdg_internal.h"
+
+using namespace ehdg;
+
+struct ehdg_ctx_s {
+  Ctx c;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+ehdg_status fail(ehdg_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+ehdg_status cuda_fail(cudaError_t e, const char* where) {
+  g_err = std::string(where) + ": " + cudaGetErrorString(e);
+  return EHDG_ERR_CUDA;
+}
+
+#define CK(expr)                                          \
+  do {                                                    \
+    cudaError_t _e = (expr);                              \
+    if (_e != cudaSuccess) return cuda_fail(_e, #expr);   \
+  } while (0)
+
+template <class T>
+ehdg_status dalloc(Ctx& c, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EHDG_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+  }
+  c.allocs.push_back(q);
+  c.bytes += (int64_t)(count * sizeof(T));
+  *p = static_cast<T*>(q);
+  return EHDG_OK;
+}
+
+#define TRY(expr)                         \
+  do {                                    \
+    ehdg_status _s = (expr);              \
+    if (_s != EHDG_OK) return _s;         \
+  } while (0)
+
+int ipow(int b, int e) {
+  int r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+ehdg_status validate_mesh(const ehdg_mesh_desc* m, ehdg_pde pde) {
+  if (!m) return fail(EHDG_ERR_INVALID, "mesh is NULL");
+  if (m->dim != 2 && m->dim != 3) return fail(EHDG_ERR_INVALID, "dim must be 2 or 3");
+  if (m->n_elem < 1 || m->n_face < 1) return fail(EHDG_ERR_INVALID, "empty mesh");
+  if (m->n_elem >= (1LL << 31) || m->n_face >= (1LL << 31))
+    return fail(EHDG_ERR_UNSUPPORTED, "more than 2^31-1 elements or faces");
+  if (!m->elem_lo || !m->elem_h || !m->elem_face || !m->face_elem || !m->face_local || !m->face_tag)
+    return fail(EHDG_ERR_INVALID, "mesh array is NULL");
+  const int dim = m->dim, F = 2 * dim;
+  for (int64_t e = 0; e < m->n_elem * dim; ++e)
+    if (!(m->elem_h[e] > 0.0) || !std::isfinite(m->elem_h[e]) || !std::isfinite(m->elem_lo[e]))
+      return fail(EHDG_ERR_INVALID, "element sizes must be positive and finite");
+  std::vector<int> seen((size_t)m->n_elem * F, 0);
+  for (int64_t f = 0; f < m->n_face; ++f) {
+    const int64_t em = m->face_elem[2 * f], ep = m->face_elem[2 * f + 1];
+    const int lm = m->face_local[2 * f], lp = m->face_local[2 * f + 1];
+    if (em < 0 || em >= m->n_elem || ep < -1 || ep >= m->n_elem || lm < 0 || lm >= F)
+      return fail(EHDG_ERR_INVALID, "face " + std::to_string(f) + ": bad element or local face");
+    if (m->elem_face[em * F + lm] != f)
+      return fail(EHDG_ERR_INVALID, "face " + std::to_string(f) + ": elem_face/face_elem mismatch");
+    seen[em * F + lm]++;
+    const int tag = m->face_tag[f];
+    if (ep >= 0) {
+      if (lp < 0 || lp >= F || m->elem_face[ep * F + lp] != f)
+        return fail(EHDG_ERR_INVALID, "face " + std::to_string(f) + ": bad plus side");
+      if ((lm & 1) != 1 || lp != lm - 1)
+        return fail(EHDG_ERR_INVALID, "face " + std::to_string(f) +
+                                          ": interior faces need the minus element on the low side");
+      if (tag != EHDG_FACE_INTERIOR)
+        return fail(EHDG_ERR_INVALID, "interior face with a boundary tag");
+      seen[ep * F + lp]++;
+    } else {
+      if (lp != -1) return fail(EHDG_ERR_INVALID, "boundary face with a plus local face");
+      const int want = (pde == EHDG_TRANSPORT) ? EHDG_FACE_DIRICHLET : EHDG_FACE_WALL;
+      if (tag != want)
+        return fail(EHDG_ERR_INVALID, pde == EHDG_TRANSPORT
+                                          ? "transport boundary faces must be tagged DIRICHLET"
+                                          : "shallow-water boundary faces must be tagged WALL");
+    }
+  }
+  for (size_t i = 0; i < seen.size(); ++i)
+    if (seen[i] != 1) return fail(EHDG_ERR_INVALID, "every local face must belong to exactly one face");
+  return EHDG_OK;
+}
+
+cudaEvent_t pool_event(Ctx& c) {
+  if (!c.ev_pool.empty()) {
+    cudaEvent_t e = c.ev_pool.back();
+    c.ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Launch through `fn`, counting `n` kernels of `kind`; with profiling on the
+// launch is bracketed by events on the context's stream.
+template <class Fn>
+cudaError_t counted(Ctx& c, int kind, int n, Fn fn) {
+  c.launches[kind] += n;
+  if (!c.profiling) return fn();
+  cudaEvent_t a = pool_event(c), b = pool_event(c);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaEventRecord(a, c.stream);
+  if (e != cudaSuccess) return e;
+  e = fn();
+  if (e != cudaSuccess) return e;
+  e = cudaEventRecord(b, c.stream);
+  if (e != cudaSuccess) return e;
+  c.ev_used.push_back({kind, a, b});
+  return cudaSuccess;
+}
+
+ehdg_status upload(Ctx& c, double* dst_soa, const double* src, int64_t outer, int inner,
+                   int on_device) {
+  const double* s = src;
+  if (!on_device) {
+    CK(cudaMemcpyAsync(c.staging, src, sizeof(double) * outer * inner, cudaMemcpyHostToDevice,
+                       c.stream));
+    s = c.staging;
+  }
+  CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_aos_to_soa(s, dst_soa, outer, inner, c.stream); }));
+  if (!on_device) CK(cudaStreamSynchronize(c.stream));
+  return EHDG_OK;
+}
+
+ehdg_status download(Ctx& c, double* dst, const double* src_soa, int64_t outer, int inner,
+                     int on_device) {
+  double* d = on_device ? dst : c.staging;
+  CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_soa_to_aos(src_soa, d, outer, inner, c.stream); }));
+  if (!on_device) {
+    CK(cudaMemcpyAsync(dst, c.staging, sizeof(double) * outer * inner, cudaMemcpyDeviceToHost,
+                       c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+  }
+  return EHDG_OK;
+}
+
+ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
+  CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_reset_iter(c); }));
+  CK(counted(c, EHDG_KERNEL_STEP, 1, [&] { return launch_step(c); }));
+  CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceInitial); }));
+  const int n_it = fixed_iters > 0 ? fixed_iters : c.max_iter;
+  int done = 0;
+  for (int k = 0; k < n_it; ++k) {
+    CK(counted(c, EHDG_KERNEL_ELEM, 1, [&] { return launch_elem(c); }));
+    CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceIterate); }));
+    ++done;
+    if (fixed_iters <= 0) {
+      CK(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
+      CK(cudaStreamSynchronize(c.stream));
+      if (!c.it_host->cont) break;
+    }
+  }
+  CK(counted(c, EHDG_KERNEL_FINAL, 2, [&] { return launch_final(c); }));
+  if (c.have_force)
+    CK(cudaMemcpyAsync(c.force_old, c.force, sizeof(double) * c.n * c.nel,
+                       cudaMemcpyDeviceToDevice, c.stream));
+  CK(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  c.last_iters = std::min(c.it_host->k, c.max_iter);
+  if (iters) *iters = c.it_host->k;
+  if (res) *res = c.it_host->r_last;
+  (void)done;
+  if (fixed_iters > 0) return EHDG_OK;
+  const ehdg_status st = (ehdg_status)c.it_host->status;
+  if (st == EHDG_ERR_NOT_CONVERGED) return fail(st, "eHDG did not reach the tolerance in max_iter iterations");
+  if (st == EHDG_ERR_DIVERGED) return fail(st, "non-finite eHDG residual");
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ehdg_last_error(void) { return g_err.c_str(); }
+
+ehdg_status ehdg_set_profiling(ehdg_ctx h, int on) {
+  if (!h) return fail(EHDG_ERR_INVALID, "NULL context");
+  Ctx& c = h->c;
+  CK(cudaStreamSynchronize(c.stream));
+  for (auto& r : c.ev_used) {
+    c.ev_pool.push_back(r.a);
+    c.ev_pool.push_back(r.b);
+  }
+  c.ev_used.clear();
+  for (int k = 0; k < EHDG_KERNEL_KINDS; ++k) c.launches[k] = 0;
+  c.profiling = on != 0;
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_kernel_stats(ehdg_ctx h, int kind, int64_t* launches, double* total_ms) {
+  if (!h || kind < 0 || kind >= EHDG_KERNEL_KINDS) return fail(EHDG_ERR_INVALID, "bad argument");
+  Ctx& c = h->c;
+  CK(cudaStreamSynchronize(c.stream));
+  double ms = 0.0;
+  for (auto& r : c.ev_used) {
+    if (r.kind != kind) continue;
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, r.a, r.b));
+    ms += t;
+  }
+  if (launches) *launches = c.launches[kind];
+  if (total_ms) *total_ms = ms;
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_mesh_structured(int dim, const int64_t n[3], const double lo[3], const double hi[3],
+                                 int32_t boundary_tag, ehdg_mesh_desc* out) {
+  if (!out || !n || !lo || !hi) return fail(EHDG_ERR_INVALID, "NULL argument");
+  if (dim != 2 && dim != 3) return fail(EHDG_ERR_INVALID, "dim must be 2 or 3");
+  int64_t N[3] = {1, 1, 1};
+  int64_t nel = 1;
+  for (int a = 0; a < dim; ++a) {
+    if (n[a] < 1) return fail(EHDG_ERR_INVALID, "mesh size must be >= 1");
+    if (!(hi[a] > lo[a])) return fail(EHDG_ERR_INVALID, "hi must exceed lo");
+    N[a] = n[a];
+    nel *= n[a];
+  }
+  int64_t nface = 0;
+  for (int ax = 0; ax < dim; ++ax) {
+    int64_t c = 1;
+    for (int a = 0; a < dim; ++a) c *= (a == ax) ? N[a] + 1 : N[a];
+    nface += c;
+  }
+  const int F = 2 * dim;
+  double* elo = (double*)std::malloc(sizeof(double) * nel * dim);
+  double* eh = (double*)std::malloc(sizeof(double) * nel * dim);
+  int64_t* ef = (int64_t*)std::malloc(sizeof(int64_t) * nel * F);
+  int64_t* fe = (int64_t*)std::malloc(sizeof(int64_t) * nface * 2);
+  int8_t* fl = (int8_t*)std::malloc(sizeof(int8_t) * nface * 2);
+  int32_t* ft = (int32_t*)std::malloc(sizeof(int32_t) * nface);
+  if (!elo || !eh || !ef || !fe || !fl || !ft) {
+    std::free(elo); std::free(eh); std::free(ef); std::free(fe); std::free(fl); std::free(ft);
+    return fail(EHDG_ERR_OOM, "host allocation failed");
+  }
+  const int64_t stride[3] = {1, N[0], N[0] * N[1]};
+  for (int64_t e = 0; e < nel; ++e) {
+    int64_t rem = e;
+    for (int a = 0; a < dim; ++a) {
+      const int64_t i = rem % N[a];
+      rem /= N[a];
+      const double h = (hi[a] - lo[a]) / (double)N[a];
+      elo[e * dim + a] = lo[a] + (double)i * h;
+      eh[e * dim + a] = h;
+    }
+  }
+  int64_t fid = 0;
+  for (int ax = 0; ax < dim; ++ax) {
+    int64_t shape[3];
+    int64_t cnt = 1;
+    for (int a = 0; a < dim; ++a) {
+      shape[a] = (a == ax) ? N[a] + 1 : N[a];
+      cnt *= shape[a];
+    }
+    for (int64_t col = 0; col < cnt; ++col, ++fid) {
+      int64_t ii[3] = {0, 0, 0}, rem = col;
+      for (int a = 0; a < dim; ++a) {
+        ii[a] = rem % shape[a];
+        rem /= shape[a];
+      }
+      const int64_t k = ii[ax];
+      int64_t base = 0;
+      for (int a = 0; a < dim; ++a) base += (a == ax ? 0 : ii[a]) * stride[a];
+      if (k > 0 && k < N[ax]) {
+        const int64_t em = base + (k - 1) * stride[ax], ep = base + k * stride[ax];
+        fe[2 * fid] = em; fe[2 * fid + 1] = ep;
+        fl[2 * fid] = (int8_t)(2 * ax + 1); fl[2 * fid + 1] = (int8_t)(2 * ax);
+        ft[fid] = EHDG_FACE_INTERIOR;
+        ef[em * F + 2 * ax + 1] = fid;
+        ef[ep * F + 2 * ax] = fid;
+      } else if (k == 0) {
+        const int64_t em = base;
+        fe[2 * fid] = em; fe[2 * fid + 1] = -1;
+        fl[2 * fid] = (int8_t)(2 * ax); fl[2 * fid + 1] = -1;
+        ft[fid] = boundary_tag;
+        ef[em * F + 2 * ax] = fid;
+      } else {
+        const int64_t em = base + (k - 1) * stride[ax];
+        fe[2 * fid] = em; fe[2 * fid + 1] = -1;
+        fl[2 * fid] = (int8_t)(2 * ax + 1); fl[2 * fid + 1] = -1;
+        ft[fid] = boundary_tag;
+        ef[em * F + 2 * ax + 1] = fid;
+      }
+    }
+  }
+  out->dim = dim;
+  out->n_elem = nel;
+  out->n_face = nface;
+  out->elem_lo = elo;
+  out->elem_h = eh;
+  out->elem_face = ef;
+  out->face_elem = fe;
+  out->face_local = fl;
+  out->face_tag = ft;
+  return EHDG_OK;
+}
+
+void ehdg_mesh_free(ehdg_mesh_desc* m) {
+  if (!m) return;
+  std::free((void*)m->elem_lo);
+  std::free((void*)m->elem_h);
+  std::free((void*)m->elem_face);
+  std::free((void*)m->face_elem);
+  std::free((void*)m->face_local);
+  std::free((void*)m->face_tag);
+  std::memset(m, 0, sizeof(*m));
+}
+
+static void release(Ctx& c) {
+  for (auto& r : c.ev_used) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c.ev_pool) cudaEventDestroy(e);
+  c.ev_used.clear();
+  c.ev_pool.clear();
+  for (void* p : c.allocs) cudaFree(p);
+  c.allocs.clear();
+  if (c.it_host) cudaFreeHost(c.it_host);
+  c.it_host = nullptr;
+}
+
+ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* prob, void* stream,
+                        ehdg_ctx* out) {
+  if (!out) return fail(EHDG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!prob) return fail(EHDG_ERR_INVALID, "problem is NULL");
+  if (prob->pde != EHDG_TRANSPORT && prob->pde != EHDG_SW_LINEAR)
+    return fail(EHDG_ERR_INVALID, "unknown pde");
+  TRY(validate_mesh(mesh, prob->pde));
+  const int dim = mesh->dim, p = prob->p;
+  if (prob->precision != EHDG_FP64)
+    return fail(EHDG_ERR_UNSUPPORTED, "only EHDG_FP64 is available in this build");
+  if (prob->scheme != EHDG_BE && prob->scheme != EHDG_CN && prob->scheme != EHDG_STEADY)
+    return fail(EHDG_ERR_INVALID, "unknown scheme");
+  if (prob->scheme != EHDG_STEADY && !(prob->dt > 0.0 && std::isfinite(prob->dt)))
+    return fail(EHDG_ERR_INVALID, "dt must be positive");
+  if (!(prob->tol >= 0.0) || prob->max_iter < 1) return fail(EHDG_ERR_INVALID, "bad tol or max_iter");
+  if (p < 1 || (dim == 2 && p > 6) || (dim == 3 && p > 3))
+    return fail(EHDG_ERR_UNSUPPORTED, "p must be 1..6 in 2D and 1..3 in 3D");
+  bool variable = false;
+  if (prob->pde == EHDG_TRANSPORT) {
+    if ((prob->beta_const == nullptr) == (prob->beta_nodes == nullptr))
+      return fail(EHDG_ERR_INVALID, "give exactly one of beta_const and beta_nodes");
+    variable = prob->beta_nodes != nullptr;
+  } else {
+    if (dim != 2) return fail(EHDG_ERR_UNSUPPORTED, "shallow water is 2D");
+    if (!(prob->Phi > 0.0)) return fail(EHDG_ERR_INVALID, "Phi must be positive");
+    if (p > 5) return fail(EHDG_ERR_UNSUPPORTED, "shallow water supports p <= 5");
+  }
+  const int q = variable ? (3 * p + 1) / 2 + 1 : p + 1;
+  if (q > kMaxQ || p + 1 > kMaxP1) return fail(EHDG_ERR_UNSUPPORTED, "degree too high");
+
+  ehdg_ctx h = new (std::nothrow) ehdg_ctx_s();
+  if (!h) return fail(EHDG_ERR_OOM, "host allocation failed");
+  Ctx& c = h->c;
+  c.dim = dim;
+  c.p = p;
+  c.pde = prob->pde;
+  c.scheme = prob->scheme;
+  c.nf = prob->pde == EHDG_TRANSPORT ? 1 : 3;
+  c.Np = ipow(p + 1, dim);
+  c.n = c.nf * c.Np;
+  c.q = q;
+  c.Nqf = ipow(q, dim - 1);
+  c.F = 2 * dim;
+  c.NQFS = c.F * c.Nqf;
+  c.nel = mesh->n_elem;
+  c.nface = mesh->n_face;
+  c.dt = prob->dt;
+  // Crank-Nicolson runs as its midpoint form: a backward-Euler stage of dt/2
+  // for v = (u^n + u^{n+1})/2, then u^{n+1} = 2 v - u^n (same iterates).
+  c.dt_eff = prob->scheme == EHDG_CN ? 0.5 * prob->dt : prob->dt;
+  c.res_scale = prob->scheme == EHDG_CN ? 2.0 : 1.0;
+  c.tol = prob->tol;
+  c.max_iter = prob->max_iter;
+  c.Phi = prob->Phi;
+  c.variable_beta = variable;
+  c.stream = (cudaStream_t)stream;
+  if (prob->pde == EHDG_TRANSPORT && !variable)
+    for (int a = 0; a < dim; ++a) c.beta_const[a] = prob->beta_const[a];
+
+  bool uniform = true;
+  for (int64_t e = 1; e < c.nel && uniform; ++e)
+    for (int a = 0; a < dim; ++a)
+      if (mesh->elem_h[e * dim + a] != mesh->elem_h[a]) uniform = false;
+  c.shared_op = uniform && !variable;
+
+  build_ref1d(p, q, &c.r1d);
+  c.ref.dim = dim;
+  c.ref.p = p;
+  c.ref.q = q;
+  c.ref.Np = c.Np;
+  c.ref.Nqf = c.Nqf;
+  c.ref.nf = c.nf;
+  for (int g = 0; g < q; ++g) {
+    c.ref.om[g] = c.r1d.om[g];
+    for (int a = 0; a <= p; ++a) {
+      c.ref.L[g * kMaxP1 + a] = c.r1d.L[g * (p + 1) + a];
+      c.ref.D[g * kMaxP1 + a] = c.r1d.D[g * (p + 1) + a];
+    }
+  }
+  for (int s = 0; s < 2; ++s)
+    for (int a = 0; a <= p; ++a) c.ref.Lend[s * kMaxP1 + a] = c.r1d.Lend[s * (p + 1) + a];
+
+  // face-point extraction Ey: element values at the face points
+  // (transport: u; shallow water: c = (phi + sqrt(Phi) vel.n_f) / 2)
+  std::vector<std::vector<std::pair<int, double>>> ey(c.NQFS);
+  const int n1 = p + 1;
+  for (int f = 0; f < c.F; ++f) {
+    const int ax = f >> 1, side = f & 1;
+    for (int gf = 0; gf < c.Nqf; ++gf) {
+      for (int i = 0; i < c.Np; ++i) {
+        int rem = i, t = 0, gr = gf;
+        double v = 1.0;
+        for (int a = 0; a < dim; ++a) {
+          const int ia = rem % n1;
+          rem /= n1;
+          if (a == ax) {
+            v *= c.r1d.Lend[side * n1 + ia];
+          } else {
+            const int ga = gr % q;
+            gr /= q;
+            v *= c.r1d.L[ga * n1 + ia];
+            ++t;
+          }
+        }
+        if (v == 0.0) continue;
+        const int s = f * c.Nqf + gf;
+        if (c.pde == EHDG_TRANSPORT) {
+          ey[s].push_back({i, v});
+        } else {
+          ey[s].push_back({i, 0.5 * v});
+          ey[s].push_back({(1 + ax) * c.Np + i, 0.5 * std::sqrt(c.Phi) * (side ? 1.0 : -1.0) * v});
+        }
+      }
+    }
+  }
+  c.KE = 0;
+  for (auto& r : ey) c.KE = std::max<int>(c.KE, (int)r.size());
+  std::vector<int> eyi((size_t)c.NQFS * c.KE, 0);
+  std::vector<double> eyv((size_t)c.NQFS * c.KE, 0.0);
+  for (int s = 0; s < c.NQFS; ++s)
+    for (size_t k = 0; k < ey[s].size(); ++k) {
+      eyi[s * c.KE + k] = ey[s][k].first;
+      eyv[s * c.KE + k] = ey[s][k].second;
+    }
+  // rows each element must produce: for a constant velocity only the faces
+  // where it is upwind or tangential (eq. transportLocale selects those)
+  std::vector<int> rows;
+  for (int s = 0; s < c.NQFS; ++s) {
+    const int f = s / c.Nqf, ax = f >> 1;
+    if (c.pde == EHDG_TRANSPORT && !variable) {
+      const double bn = ((f & 1) ? 1.0 : -1.0) * c.beta_const[ax];
+      if (bn < 0.0) continue;
+    }
+    rows.push_back(s);
+  }
+  c.n_rows = (int)rows.size();
+
+  // shared memory needed by the assembly kernel
+  {
+    int Q = ipow(q, dim);
+    size_t smem = sizeof(double) * ((size_t)c.n * (2 * c.n + c.NQFS) + dim * c.Np + 2 * dim * Q +
+                                    c.F * c.Nqf + c.n);
+    if (smem > 220 * 1024) {
+      delete h;
+      return fail(EHDG_ERR_UNSUPPORTED, "local system too large for on-chip assembly");
+    }
+  }
+
+  // host copies
+  c.elem_lo.assign(mesh->elem_lo, mesh->elem_lo + c.nel * dim);
+  c.elem_h.assign(mesh->elem_h, mesh->elem_h + c.nel * dim);
+  c.face_elem_h.assign(mesh->face_elem, mesh->face_elem + 2 * c.nface);
+  c.face_local_h.assign(mesh->face_local, mesh->face_local + 2 * c.nface);
+  c.elem_face_h.assign(mesh->elem_face, mesh->elem_face + c.F * c.nel);
+
+  auto cleanup = [&](ehdg_status s) {
+    std::string msg = g_err;
+    release(c);
+    delete h;
+    g_err = msg;
+    return s;
+  };
+#define TRYC(expr)                               \
+  do {                                           \
+    ehdg_status _s = (expr);                     \
+    if (_s != EHDG_OK) return cleanup(_s);       \
+  } while (0)
+#define CKC(expr)                                                      \
+  do {                                                                 \
+    cudaError_t _e = (expr);                                           \
+    if (_e != cudaSuccess) return cleanup(cuda_fail(_e, #expr));       \
+  } while (0)
+
+  // geometry in SoA / int32
+  std::vector<int32_t> ef32((size_t)c.F * c.nel), fe32((size_t)2 * c.nface);
+  std::vector<int8_t> fl8((size_t)2 * c.nface), tag8(c.nface);
+  std::vector<double> jf(c.nface);
+  for (int64_t e = 0; e < c.nel; ++e)
+    for (int f = 0; f < c.F; ++f) ef32[f * c.nel + e] = (int32_t)mesh->elem_face[e * c.F + f];
+  for (int64_t f = 0; f < c.nface; ++f) {
+    fe32[f] = (int32_t)mesh->face_elem[2 * f];
+    fe32[c.nface + f] = (int32_t)mesh->face_elem[2 * f + 1];
+    fl8[f] = mesh->face_local[2 * f];
+    fl8[c.nface + f] = mesh->face_local[2 * f + 1];
+    tag8[f] = (int8_t)mesh->face_tag[f];
+    const int64_t em = mesh->face_elem[2 * f];
+    const int ax = mesh->face_local[2 * f] >> 1;
+    double v = 1.0;
+    for (int a = 0; a < dim; ++a)
+      if (a != ax) v *= 0.5 * mesh->elem_h[em * dim + a];
+    jf[f] = v;
+  }
+  double* d_h = nullptr;
+  int32_t *d_ef = nullptr, *d_fe = nullptr;
+  int8_t *d_fl = nullptr, *d_tag = nullptr;
+  double* d_jf = nullptr;
+  TRYC(dalloc(c, &d_h, (size_t)c.nel * dim));
+  TRYC(dalloc(c, &d_ef, ef32.size()));
+  TRYC(dalloc(c, &d_fe, fe32.size()));
+  TRYC(dalloc(c, &d_fl, fl8.size()));
+  TRYC(dalloc(c, &d_tag, tag8.size()));
+  TRYC(dalloc(c, &d_jf, jf.size()));
+  CKC(cudaMemcpy(d_h, mesh->elem_h, sizeof(double) * c.nel * dim, cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(d_ef, ef32.data(), sizeof(int32_t) * ef32.size(), cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(d_fe, fe32.data(), sizeof(int32_t) * fe32.size(), cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(d_fl, fl8.data(), fl8.size(), cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(d_tag, tag8.data(), tag8.size(), cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(d_jf, jf.data(), sizeof(double) * jf.size(), cudaMemcpyHostToDevice));
+  c.geo.nel = c.nel;
+  c.geo.nface = c.nface;
+  c.geo.elem_h = d_h;
+  c.geo.elem_face = d_ef;
+  c.geo.face_elem = d_fe;
+  c.geo.face_local = d_fl;
+  c.geo.face_tag = d_tag;
+  c.geo.face_jf = d_jf;
+
+  const int64_t ne = c.shared_op ? 1 : c.nel;
+  TRYC(dalloc(c, &c.P, (size_t)c.n * c.n * ne));
+  TRYC(dalloc(c, &c.H, (size_t)c.n * c.NQFS * ne));
+  TRYC(dalloc(c, &c.Hy, (size_t)c.NQFS * c.NQFS * ne));
+  TRYC(dalloc(c, &c.ey_idx, eyi.size()));
+  TRYC(dalloc(c, &c.ey_val, eyv.size()));
+  TRYC(dalloc(c, &c.rows, rows.size()));
+  CKC(cudaMemcpy(c.ey_idx, eyi.data(), sizeof(int) * eyi.size(), cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(c.ey_val, eyv.data(), sizeof(double) * eyv.size(), cudaMemcpyHostToDevice));
+  CKC(cudaMemcpy(c.rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice));
+  if (variable) {
+    TRYC(dalloc(c, &c.beta_nodes, (size_t)c.nel * dim * c.Np));
+    CKC(cudaMemcpy(c.beta_nodes, prob->beta_nodes, sizeof(double) * c.nel * dim * c.Np,
+                   cudaMemcpyHostToDevice));
+  }
+  const size_t state = (size_t)c.n * c.nel, trace = (size_t)c.Nqf * c.nface;
+  TRYC(dalloc(c, &c.sgn, trace));
+  TRYC(dalloc(c, &c.u, state));
+  TRYC(dalloc(c, &c.G, state));
+  TRYC(dalloc(c, &c.Gy, (size_t)c.NQFS * c.nel));
+  TRYC(dalloc(c, &c.Y, (size_t)c.NQFS * c.nel));
+  TRYC(dalloc(c, &c.uhat, trace));
+  TRYC(dalloc(c, &c.uhat_n, trace));
+  TRYC(dalloc(c, &c.gb, trace));
+  TRYC(dalloc(c, &c.gb_old, trace));
+  TRYC(dalloc(c, &c.force, state));
+  TRYC(dalloc(c, &c.force_old, state));
+  TRYC(dalloc(c, &c.staging, std::max(state, trace)));
+  c.n_partials = (int)std::min<int64_t>((trace + 255) / 256, 152 * 8);
+  if (c.n_partials < 1) c.n_partials = 1;
+  TRYC(dalloc(c, &c.partials, (size_t)c.n_partials));
+  TRYC(dalloc(c, &c.it, 1));
+  TRYC(dalloc(c, &c.hist, (size_t)c.max_iter));
+  CKC(cudaMallocHost(&c.it_host, sizeof(IterState)));
+  CKC(cudaMemsetAsync(c.u, 0, sizeof(double) * state, c.stream));
+  CKC(cudaMemsetAsync(c.Y, 0, sizeof(double) * c.NQFS * c.nel, c.stream));
+  CKC(cudaMemsetAsync(c.uhat, 0, sizeof(double) * trace, c.stream));
+  CKC(cudaMemsetAsync(c.uhat_n, 0, sizeof(double) * trace, c.stream));
+  CKC(cudaMemsetAsync(c.gb, 0, sizeof(double) * trace, c.stream));
+  CKC(cudaMemsetAsync(c.gb_old, 0, sizeof(double) * trace, c.stream));
+  CKC(cudaMemsetAsync(c.hist, 0, sizeof(double) * c.max_iter, c.stream));
+
+  CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_reset_iter(c); }));
+  CKC(counted(c, EHDG_KERNEL_ASSEMBLE, 1, [&] { return launch_assemble(c, c.shared_op ? 1 : (int)c.nel); }));
+  if (c.pde == EHDG_TRANSPORT)
+    CKC(counted(c, EHDG_KERNEL_SIGNS, 1, [&] { return launch_face_signs(c); }));
+  CKC(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
+  CKC(cudaStreamSynchronize(c.stream));
+  if (c.it_host->status != 0) return cleanup(fail(EHDG_ERR_INVALID, "singular local operator"));
+  *out = h;
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_get_info(ehdg_ctx h, ehdg_info* out) {
+  if (!h || !out) return fail(EHDG_ERR_INVALID, "NULL argument");
+  const Ctx& c = h->c;
+  out->dim = c.dim;
+  out->p = c.p;
+  out->nf = c.nf;
+  out->Np = c.Np;
+  out->q = c.q;
+  out->Nqf = c.Nqf;
+  out->n_elem = c.nel;
+  out->n_face = c.nface;
+  out->state_len = (int64_t)c.n * c.nel;
+  out->trace_len = (int64_t)c.Nqf * c.nface;
+  out->shared_operator = c.shared_op ? 1 : 0;
+  out->device_bytes = c.bytes;
+  return EHDG_OK;
+}
+
+void ehdg_destroy(ehdg_ctx h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->c.stream);
+  release(h->c);
+  delete h;
+}
+
+ehdg_status ehdg_node_coords(ehdg_ctx h, double* x) {
+  if (!h || !x) return fail(EHDG_ERR_INVALID, "NULL argument");
+  const Ctx& c = h->c;
+  const int n1 = c.p + 1;
+  for (int64_t e = 0; e < c.nel; ++e)
+    for (int i = 0; i < c.Np; ++i) {
+      int rem = i;
+      for (int a = 0; a < c.dim; ++a) {
+        const int ia = rem % n1;
+        rem /= n1;
+        x[(e * c.Np + i) * c.dim + a] =
+            c.elem_lo[e * c.dim + a] + c.elem_h[e * c.dim + a] * (c.r1d.r[ia] + 1.0) / 2.0;
+      }
+    }
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_face_point_coords(ehdg_ctx h, double* x) {
+  if (!h || !x) return fail(EHDG_ERR_INVALID, "NULL argument");
+  const Ctx& c = h->c;
+  for (int64_t f = 0; f < c.nface; ++f) {
+    const int64_t em = c.face_elem_h[2 * f];
+    const int lf = c.face_local_h[2 * f], ax = lf >> 1, side = lf & 1;
+    for (int g = 0; g < c.Nqf; ++g) {
+      int rem = g;
+      for (int a = 0; a < c.dim; ++a) {
+        double r;
+        if (a == ax) {
+          r = side ? 1.0 : -1.0;
+        } else {
+          r = c.r1d.xi[rem % c.q];
+          rem /= c.q;
+        }
+        x[(f * c.Nqf + g) * c.dim + a] =
+            c.elem_lo[em * c.dim + a] + c.elem_h[em * c.dim + a] * (r + 1.0) / 2.0;
+      }
+    }
+  }
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_set_state(ehdg_ctx h, const double* u, const double* uhat, int on_device) {
+  if (!h || !u) return fail(EHDG_ERR_INVALID, "NULL argument");
+  Ctx& c = h->c;
+  const size_t trace = (size_t)c.Nqf * c.nface;
+  TRY(upload(c, c.u, u, c.nel, c.n, on_device));
+  // the state's own level: boundary data of this level on both sides of CN's average
+  CK(cudaMemcpyAsync(c.gb_old, c.gb, sizeof(double) * trace, cudaMemcpyDeviceToDevice, c.stream));
+  if (uhat) {
+    TRY(upload(c, c.uhat, uhat, c.nface, c.Nqf, on_device));
+  } else {
+    CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_extract(c); }));
+    CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceInitial); }));
+  }
+  CK(cudaMemcpyAsync(c.uhat_n, c.uhat, sizeof(double) * trace, cudaMemcpyDeviceToDevice, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_set_forcing(ehdg_ctx h, const double* f, int on_device) {
+  if (!h) return fail(EHDG_ERR_INVALID, "NULL context");
+  Ctx& c = h->c;
+  if (!f) {
+    c.have_force = false;
+    return EHDG_OK;
+  }
+  TRY(upload(c, c.force, f, c.nel, c.n, on_device));
+  if (!c.have_force)
+    CK(cudaMemcpyAsync(c.force_old, c.force, sizeof(double) * c.n * c.nel,
+                       cudaMemcpyDeviceToDevice, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  c.have_force = true;
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_set_boundary(ehdg_ctx h, const double* g, int on_device) {
+  if (!h || !g) return fail(EHDG_ERR_INVALID, "NULL argument");
+  Ctx& c = h->c;
+  return upload(c, c.gb, g, c.nface, c.Nqf, on_device);
+}
+
+ehdg_status ehdg_step(ehdg_ctx h, int* iters, double* final_residual) {
+  if (!h) return fail(EHDG_ERR_INVALID, "NULL context");
+  return run_step(h->c, 0, iters, final_residual);
+}
+
+ehdg_status ehdg_run(ehdg_ctx h, int n_steps, int* iters_per_step) {
+  if (!h || n_steps < 0) return fail(EHDG_ERR_INVALID, "bad argument");
+  for (int s = 0; s < n_steps; ++s) {
+    int it = 0;
+    const ehdg_status st = run_step(h->c, 0, &it, nullptr);
+    if (iters_per_step) iters_per_step[s] = it;
+    if (st != EHDG_OK) return st;
+  }
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_step_fixed(ehdg_ctx h, int n_iter) {
+  if (!h || n_iter < 1) return fail(EHDG_ERR_INVALID, "bad argument");
+  return run_step(h->c, n_iter, nullptr, nullptr);
+}
+
+ehdg_status ehdg_get_state(ehdg_ctx h, double* u, double* uhat, int on_device) {
+  if (!h) return fail(EHDG_ERR_INVALID, "NULL context");
+  Ctx& c = h->c;
+  if (u) TRY(download(c, u, c.u, c.nel, c.n, on_device));
+  if (uhat) TRY(download(c, uhat, c.uhat, c.nface, c.Nqf, on_device));
+  CK(cudaStreamSynchronize(c.stream));
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_get_residual_history(ehdg_ctx h, double* buf, int64_t cap, int64_t* n_out) {
+  if (!h || (!buf && cap > 0)) return fail(EHDG_ERR_INVALID, "bad argument");
+  Ctx& c = h->c;
+  const int64_t n = std::min<int64_t>(c.last_iters, cap);
+  if (n > 0) {
+    CK(cudaMemcpyAsync(buf, c.hist, sizeof(double) * n, cudaMemcpyDeviceToHost, c.stream));
+    CK(cudaStreamSynchronize(c.stream));
+  }
+  if (n_out) *n_out = c.last_iters;
+  return EHDG_OK;
+}
+
+}  // extern "C"

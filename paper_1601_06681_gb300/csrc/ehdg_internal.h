@@ -1,0 +1,141 @@
+// Internal declarations of libehdg: context, reference tables, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ehdg.h"
+
+namespace ehdg {
+
+// ---------------------------------------------------------------------------
+// 1D reference tables (host side, built independently of any other code)
+// ---------------------------------------------------------------------------
+struct Ref1D {
+  int p = 0, q = 0;
+  std::vector<double> r, wr;      // GLL nodes and weights (p+1)
+  std::vector<double> xi, om;     // Gauss points and weights (q)
+  std::vector<double> L, D;       // [q][p+1] l_a(xi_g), l_a'(xi_g)
+  std::vector<double> Lend;       // [2][p+1] l_a(-1), l_a(+1)
+};
+void build_ref1d(int p, int q, Ref1D* out);
+void gll_rule(int p, std::vector<double>* x, std::vector<double>* w);
+void gauss_rule(int q, std::vector<double>* x, std::vector<double>* w);
+
+// ---------------------------------------------------------------------------
+// Device-side problem description handed to kernels (by value)
+// ---------------------------------------------------------------------------
+constexpr int kMaxP1 = 10;        // max points per axis in the 1D tables
+constexpr int kMaxQ = 10;
+
+struct RefTables {               // lives in kernel parameter space (small)
+  int dim, p, q, Np, Nqf, nf;
+  double L[kMaxQ * kMaxP1];
+  double D[kMaxQ * kMaxP1];
+  double Lend[2 * kMaxP1];
+  double om[kMaxQ];
+};
+
+struct Geometry {
+  int64_t nel, nface;
+  const double* elem_h;          // [nel][dim]
+  const int32_t* elem_face;      // SoA [2*dim][nel]
+  const int32_t* face_elem;      // SoA [2][nface]
+  const int8_t* face_local;      // SoA [2][nface]
+  const int8_t* face_tag;        // [nface]
+  const double* face_jf;         // [nface] face Jacobian J_f
+};
+
+// Iteration state word kept on the device (one per context).
+struct IterState {
+  int k;                         // iterations done in the current step
+  int cont;                      // 1 while the loop must go on
+  int status;                    // ehdg_status of the current step
+  unsigned int counter;          // last-block ticket of the residual reduction
+  double r_last;
+};
+
+struct Ctx {
+  // problem
+  int dim = 0, p = 0, nf = 1, Np = 0, n = 0, q = 0, Nqf = 0, F = 0, NQFS = 0;
+  int64_t nel = 0, nface = 0;
+  ehdg_pde pde = EHDG_TRANSPORT;
+  ehdg_scheme scheme = EHDG_BE;
+  double dt = 0, dt_eff = 0, tol = 0, Phi = 1, res_scale = 1;
+  int max_iter = 0;
+  bool shared_op = false;        // one operator for all elements
+  bool variable_beta = false;
+  double beta_const[3] = {0, 0, 0};
+  cudaStream_t stream = nullptr;
+  RefTables ref{};
+  Ref1D r1d;
+  int KE = 0;                    // nonzeros per row of the face-point extraction
+
+  // host copies for coordinates
+  std::vector<double> elem_lo, elem_h;
+  std::vector<int64_t> face_elem_h, elem_face_h;
+  std::vector<int8_t> face_local_h;
+
+  // device memory
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  Geometry geo{};
+  double* beta_nodes = nullptr;  // [nel][dim][Np] (variable velocity)
+  double* P = nullptr;           // [n][n][ne]   A^{-1} Mblk
+  double* H = nullptr;           // [n][NQFS][ne] A^{-1} B
+  double* Hy = nullptr;          // [NQFS][NQFS][ne] face-point rows of H
+  int* ey_idx = nullptr;         // [NQFS][KE]
+  double* ey_val = nullptr;      // [NQFS][KE]
+  int8_t* sgn = nullptr;         // [Nqf][nface] sgn(beta.n^-) (transport)
+  int* rows = nullptr;           // element output rows (face points) to compute
+  int n_rows = 0;
+  double* u = nullptr;           // [n][nel] state u^n (SoA)
+  double* G = nullptr;           // [n][nel]
+  double* Gy = nullptr;          // [NQFS][nel]
+  double* Y = nullptr;           // [NQFS][nel] element values at face points
+  double* uhat = nullptr;        // [Nqf][nface] current trace (in place)
+  double* uhat_n = nullptr;      // [Nqf][nface] trace of the previous step (CN)
+  double* gb = nullptr;          // [Nqf][nface] boundary data, new level
+  double* gb_old = nullptr;      // [Nqf][nface] boundary data, previous level
+  double* force = nullptr;       // [n][nel] forcing (or null)
+  double* force_old = nullptr;
+  bool have_force = false;
+  double* partials = nullptr;    // residual block partials
+  int n_partials = 0;
+  IterState* it = nullptr;
+  double* hist = nullptr;        // [max_iter]
+  double* staging = nullptr;     // [max(state,trace)] transposition buffer
+  IterState* it_host = nullptr;  // pinned
+  int last_iters = 0;
+
+  // kernel accounting (ehdg_set_profiling / ehdg_kernel_stats)
+  bool profiling = false;
+  int64_t launches[EHDG_KERNEL_KINDS] = {0};
+  struct EvRec {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<EvRec> ev_used;
+  std::vector<cudaEvent_t> ev_pool;
+};
+
+// launchers (kernels.cu)
+cudaError_t launch_assemble(Ctx& c, int n_assemble);
+cudaError_t launch_face_signs(Ctx& c);
+cudaError_t launch_step(Ctx& c);
+cudaError_t launch_elem(Ctx& c);
+cudaError_t launch_face(Ctx& c, int mode);   // 0 initial trace, 1 iteration
+cudaError_t launch_final(Ctx& c);
+cudaError_t launch_aos_to_soa(const double* src, double* dst, int64_t outer, int inner,
+                              cudaStream_t s);   // src [outer][inner] -> dst [inner][outer]
+cudaError_t launch_soa_to_aos(const double* src, double* dst, int64_t outer, int inner,
+                              cudaStream_t s);
+cudaError_t launch_reset_iter(Ctx& c);
+cudaError_t launch_extract(Ctx& c);
+
+enum FaceMode { kFaceInitial = 0, kFaceIterate = 1 };
+
+}  // namespace ehdg

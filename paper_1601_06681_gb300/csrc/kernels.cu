@@ -1,0 +1,820 @@
+// CUDA kernels of libehdg (sm_103a): local-operator assembly and factorisation,
+// the per-step right-hand side, the element sweep, the face trace update with
+// its FP64 residual reduction, and the end-of-step reconstruction.
+//
+// Layout in HBM: per-element quantities are structure-of-arrays with the
+// element index innermost ([row][elem] or [row][col][elem]) so that a warp of
+// consecutive elements reads consecutive addresses; traces are [point][face].
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "ehdg_internal.h"
+
+namespace ehdg {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// tensor-product basis evaluation from the 1D tables
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int digit(int v, int base, int k) {
+  for (int i = 0; i < k; ++i) v /= base;
+  return v % base;
+}
+
+// phi_i at volume quadrature point g
+__device__ double vphi(const RefTables& R, int i, int g) {
+  const int n1 = R.p + 1;
+  double v = 1.0;
+  for (int a = 0; a < R.dim; ++a) v *= R.L[digit(g, R.q, a) * kMaxP1 + digit(i, n1, a)];
+  return v;
+}
+
+// d phi_i / d r_ax at volume point g
+__device__ double vdphi(const RefTables& R, int ax, int i, int g) {
+  const int n1 = R.p + 1;
+  double v = 1.0;
+  for (int a = 0; a < R.dim; ++a) {
+    const int ga = digit(g, R.q, a), ia = digit(i, n1, a);
+    v *= (a == ax) ? R.D[ga * kMaxP1 + ia] : R.L[ga * kMaxP1 + ia];
+  }
+  return v;
+}
+
+// phi_i at point gf of local face f (tangential axes increasing, first fastest)
+__device__ double fphi(const RefTables& R, int f, int i, int gf) {
+  const int n1 = R.p + 1;
+  const int ax = f >> 1, side = f & 1;
+  double v = R.Lend[side * kMaxP1 + digit(i, n1, ax)];
+  int t = 0;
+  for (int a = 0; a < R.dim; ++a) {
+    if (a == ax) continue;
+    v *= R.L[digit(gf, R.q, t) * kMaxP1 + digit(i, n1, a)];
+    ++t;
+  }
+  return v;
+}
+
+__device__ double vweight(const RefTables& R, int g) {
+  double w = 1.0;
+  for (int a = 0; a < R.dim; ++a) w *= R.om[digit(g, R.q, a)];
+  return w;
+}
+
+__device__ double fweight(const RefTables& R, int gf) {
+  double w = 1.0;
+  for (int t = 0; t < R.dim - 1; ++t) w *= R.om[digit(gf, R.q, t)];
+  return w;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace
+
+// ===========================================================================
+// Assembly + Gauss-Jordan: one CTA per element
+// ===========================================================================
+struct AsmParams {
+  RefTables R;
+  int pde, n, NQFS, KE;
+  double tcoef;                 // coefficient of the mass term in A (1/dt_eff, 0 for steady)
+  double Phi;
+  double beta_c[3];
+  int variable;
+  const double* elem_h;         // [nel][dim]
+  const double* beta_nodes;     // [nel][dim][Np]
+  const int* ey_idx;
+  const double* ey_val;
+  double* P;
+  double* H;
+  double* Hy;
+  int64_t ne_out;               // element stride of the outputs (1 for a shared operator)
+  int* err;
+};
+
+__global__ void k_assemble(const AsmParams a) {
+  extern __shared__ double sm[];
+  const RefTables& R = a.R;
+  const int e = blockIdx.x;
+  const int n = a.n, NQFS = a.NQFS, Np = R.Np, dim = R.dim, Nqf = R.Nqf;
+  const int ncol = 2 * n + NQFS;
+  int Q = 1;
+  for (int d = 0; d < dim; ++d) Q *= R.q;
+  const int F = 2 * dim;
+
+  double* aug = sm;                         // [n][ncol]
+  double* bn = aug + n * ncol;              // [dim][Np]
+  double* bq = bn + dim * Np;               // [dim][Q]
+  double* dbq = bq + dim * Q;               // [dim][Q]
+  double* bf = dbq + dim * Q;               // [F][Nqf] beta.n at face points
+  double* fac = bf + F * Nqf;               // [n] elimination column
+  __shared__ int piv;
+  __shared__ double hsh[3];
+
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (tid < dim) hsh[tid] = a.elem_h[(int64_t)e * dim + tid];
+  for (int t = tid; t < dim * Np; t += nt) {
+    const int ax = t / Np;
+    bn[t] = a.variable ? a.beta_nodes[(int64_t)e * dim * Np + t] : a.beta_c[ax];
+  }
+  __syncthreads();
+  double J = 1.0;
+  for (int d = 0; d < dim; ++d) J *= 0.5 * hsh[d];
+
+  if (a.pde == EHDG_TRANSPORT) {
+    for (int t = tid; t < dim * Q; t += nt) {
+      const int ax = t / Q, g = t % Q;
+      double s = 0.0, ds = 0.0;
+      for (int c = 0; c < Np; ++c) {
+        s += vphi(R, c, g) * bn[ax * Np + c];
+        ds += vdphi(R, ax, c, g) * bn[ax * Np + c];
+      }
+      bq[t] = s;
+      dbq[t] = ds;
+    }
+    for (int t = tid; t < F * Nqf; t += nt) {
+      const int f = t / Nqf, gf = t % Nqf, ax = f >> 1;
+      double s = 0.0;
+      for (int c = 0; c < Np; ++c) s += fphi(R, f, c, gf) * bn[ax * Np + c];
+      bf[t] = (f & 1) ? s : -s;
+    }
+  }
+  __syncthreads();
+
+  // ---- fill [A | Mblk | B]
+  if (a.pde == EHDG_TRANSPORT) {
+    for (int t = tid; t < n * n; t += nt) {
+      const int i = t / n, j = t % n;
+      double m = 0.0, adv = 0.0;
+      for (int g = 0; g < Q; ++g) {
+        const double w = vweight(R, g) * J;
+        const double pi = vphi(R, i, g), pj = vphi(R, j, g);
+        double div = 0.0;
+        for (int ax = 0; ax < dim; ++ax)
+          div += (2.0 / hsh[ax]) * (dbq[ax * Q + g] * pi + bq[ax * Q + g] * vdphi(R, ax, i, g));
+        m += w * pi * pj;
+        adv -= w * pj * div;
+      }
+      double fc = 0.0;
+      for (int f = 0; f < F; ++f) {
+        const int ax = f >> 1;
+        const double jf = J * 2.0 / hsh[ax];
+        for (int gf = 0; gf < Nqf; ++gf) {
+          const double b = bf[f * Nqf + gf];
+          const double fi = fphi(R, f, i, gf);
+          if (fi == 0.0) continue;
+          fc += jf * fweight(R, gf) * (b + fabs(b)) * fi * fphi(R, f, j, gf);
+        }
+      }
+      aug[i * ncol + j] = a.tcoef * m + adv + fc;
+      aug[i * ncol + n + j] = m;
+    }
+    for (int t = tid; t < n * NQFS; t += nt) {
+      const int i = t / NQFS, s = t % NQFS;
+      const int f = s / Nqf, gf = s % Nqf, ax = f >> 1;
+      const double jf = J * 2.0 / hsh[ax];
+      aug[i * ncol + 2 * n + s] = jf * fweight(R, gf) * fabs(bf[s]) * fphi(R, f, i, gf);
+    }
+  } else {
+    // linearised shallow water, unknowns (phi, u, v), Sec. 3 eq. localSolverDD
+    const double Phi = a.Phi, sq = sqrt(Phi);
+    for (int t = tid; t < n * n; t += nt) {
+      const int I = t / n, Jc = t % n;
+      const int fi = I / Np, i = I % Np, fj = Jc / Np, j = Jc % Np;
+      double m = 0.0, gx[3] = {0.0, 0.0, 0.0};
+      for (int g = 0; g < Q; ++g) {
+        const double w = vweight(R, g) * J;
+        const double pj = vphi(R, j, g);
+        m += w * vphi(R, i, g) * pj;
+        for (int ax = 0; ax < dim; ++ax) gx[ax] += w * (2.0 / hsh[ax]) * vdphi(R, ax, i, g) * pj;
+      }
+      double ef[6];
+      for (int f = 0; f < F; ++f) {
+        const int ax = f >> 1;
+        const double jf = J * 2.0 / hsh[ax];
+        double s = 0.0;
+        for (int gf = 0; gf < Nqf; ++gf) s += jf * fweight(R, gf) * fphi(R, f, i, gf) * fphi(R, f, j, gf);
+        ef[f] = s;
+      }
+      double A = 0.0, Mb = 0.0;
+      if (fi == 0 && fj == 0) {
+        A = a.tcoef * m;
+        for (int f = 0; f < F; ++f) A += sq * ef[f];
+        Mb = m;
+      } else if (fi == 0) {
+        const int ax = fj - 1;
+        A = -Phi * gx[ax];
+        for (int f = 0; f < F; ++f)
+          if ((f >> 1) == ax) A += Phi * ((f & 1) ? 1.0 : -1.0) * ef[f];
+      } else if (fj == 0) {
+        A = -Phi * gx[fi - 1];
+      } else if (fi == fj) {
+        A = a.tcoef * Phi * m;
+        Mb = Phi * m;
+      }
+      aug[I * ncol + Jc] = A;
+      aug[I * ncol + n + Jc] = Mb;
+    }
+    for (int t = tid; t < n * NQFS; t += nt) {
+      const int I = t / NQFS, s = t % NQFS;
+      const int fi = I / Np, i = I % Np;
+      const int f = s / Nqf, gf = s % Nqf, ax = f >> 1;
+      const double jf = J * 2.0 / hsh[ax];
+      const double base = jf * fweight(R, gf) * fphi(R, f, i, gf);
+      double v = 0.0;
+      if (fi == 0) v = sq * base;
+      else if (fi - 1 == ax) v = -Phi * ((f & 1) ? 1.0 : -1.0) * base;
+      aug[I * ncol + 2 * n + s] = v;
+    }
+  }
+  __syncthreads();
+
+  // ---- Gauss-Jordan elimination with partial pivoting: [A|Mblk|B] -> [I|P|H]
+  for (int k = 0; k < n; ++k) {
+    if (tid < 32) {
+      double best = -1.0;
+      int bi = k;
+      for (int r = k + tid; r < n; r += 32) {
+        const double v = fabs(aug[r * ncol + k]);
+        if (v > best) { best = v; bi = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (tid == 0) piv = bi;
+    }
+    __syncthreads();
+    if (piv != k) {
+      for (int j = tid; j < ncol; j += nt) {
+        const double tmp = aug[k * ncol + j];
+        aug[k * ncol + j] = aug[piv * ncol + j];
+        aug[piv * ncol + j] = tmp;
+      }
+      __syncthreads();
+    }
+    const double pv = aug[k * ncol + k];
+    if (pv == 0.0 || !isfinite(pv)) {
+      if (tid == 0) atomicExch(a.err, 1);
+      return;   // uniform across the block: pv is read from shared memory
+    }
+    for (int r = tid; r < n; r += nt) fac[r] = aug[r * ncol + k];
+    __syncthreads();
+    const double inv = 1.0 / pv;
+    for (int j = tid; j < ncol; j += nt) aug[k * ncol + j] *= inv;
+    __syncthreads();
+    for (int t = tid; t < n * ncol; t += nt) {
+      const int r = t / ncol, j = t % ncol;
+      if (r != k) aug[t] -= fac[r] * aug[k * ncol + j];
+    }
+    __syncthreads();
+  }
+
+  // ---- outputs: P = A^{-1} Mblk, H = A^{-1} B, Hy = Ey H
+  const int64_t ne = a.ne_out;
+  for (int t = tid; t < n * n; t += nt) {
+    const int i = t / n, j = t % n;
+    a.P[(int64_t)t * ne + e] = aug[i * ncol + n + j];
+  }
+  for (int t = tid; t < n * NQFS; t += nt) {
+    const int i = t / NQFS, s = t % NQFS;
+    a.H[(int64_t)t * ne + e] = aug[i * ncol + 2 * n + s];
+  }
+  for (int t = tid; t < NQFS * NQFS; t += nt) {
+    const int s = t / NQFS, c = t % NQFS;
+    double v = 0.0;
+    for (int k = 0; k < a.KE; ++k) {
+      const double ev = a.ey_val[s * a.KE + k];
+      if (ev != 0.0) v += ev * aug[a.ey_idx[s * a.KE + k] * ncol + 2 * n + c];
+    }
+    a.Hy[(int64_t)t * ne + e] = v;
+  }
+}
+
+static size_t asm_smem(const Ctx& c) {
+  int Q = 1;
+  for (int d = 0; d < c.dim; ++d) Q *= c.q;
+  const int ncol = 2 * c.n + c.NQFS;
+  return sizeof(double) * ((size_t)c.n * ncol + c.dim * c.Np + 2 * c.dim * Q + c.F * c.Nqf + c.n);
+}
+
+cudaError_t launch_assemble(Ctx& c, int n_assemble) {
+  AsmParams a;
+  a.R = c.ref;
+  a.pde = c.pde;
+  a.n = c.n;
+  a.NQFS = c.NQFS;
+  a.KE = c.KE;
+  a.tcoef = (c.scheme == EHDG_STEADY) ? 0.0 : 1.0 / c.dt_eff;
+  a.Phi = c.Phi;
+  for (int d = 0; d < 3; ++d) a.beta_c[d] = c.beta_const[d];
+  a.variable = c.variable_beta ? 1 : 0;
+  a.elem_h = c.geo.elem_h;
+  a.beta_nodes = c.beta_nodes;
+  a.ey_idx = c.ey_idx;
+  a.ey_val = c.ey_val;
+  a.P = c.P;
+  a.H = c.H;
+  a.Hy = c.Hy;
+  a.ne_out = c.shared_op ? 1 : c.nel;
+  a.err = reinterpret_cast<int*>(&c.it->status);
+  const size_t smem = asm_smem(c);
+  cudaError_t err = cudaFuncSetAttribute(k_assemble, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  k_assemble<<<n_assemble, 256, smem, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// sgn(beta.n^-) at every face point (transport), from the minus element
+// ===========================================================================
+__global__ void k_face_signs(const RefTables R, Geometry geo, const double* beta_nodes,
+                             int variable, double b0, double b1, double b2, int8_t* sgn) {
+  const int64_t total = (int64_t)R.Nqf * geo.nface;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int gf = (int)(t / geo.nface);
+    const int64_t face = t % geo.nface;
+    const int em = geo.face_elem[face];
+    const int f = geo.face_local[face];
+    const int ax = f >> 1;
+    double s = 0.0;
+    if (variable) {
+      const double* bn = beta_nodes + ((int64_t)em * R.dim + ax) * R.Np;
+      for (int c = 0; c < R.Np; ++c) s += fphi(R, f, c, gf) * bn[c];
+    } else {
+      const double bc = ax == 0 ? b0 : (ax == 1 ? b1 : b2);
+      for (int c = 0; c < R.Np; ++c) s += fphi(R, f, c, gf) * bc;
+    }
+    const double b = (f & 1) ? s : -s;
+    sgn[t] = (int8_t)((b > 0.0) - (b < 0.0));
+  }
+}
+
+cudaError_t launch_face_signs(Ctx& c) {
+  const int64_t total = (int64_t)c.Nqf * c.nface;
+  const int bs = 256;
+  const int grid = (int)((total + bs - 1) / bs);
+  k_face_signs<<<grid, bs, 0, c.stream>>>(c.ref, c.geo, c.beta_nodes, c.variable_beta ? 1 : 0,
+                                           c.beta_const[0], c.beta_const[1], c.beta_const[2],
+                                           c.sgn);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Per-step right-hand side: G = P w, Gy = Ey G, Y0 = Ey u^n
+//   w = u^n / dt_eff + f (time-dependent) or w = f (steady)
+// ===========================================================================
+struct StepParams {
+  int64_t nel;
+  int n, NQFS, KE, shared;
+  double ucoef;                 // 1/dt_eff, or 0 for steady
+  int have_force, force_avg;    // force_avg: use 0.5 (f_old + f) (Crank-Nicolson)
+  const double* P;
+  const double* u;
+  const double* force;
+  const double* force_old;
+  const int* ey_idx;
+  const double* ey_val;
+  double* G;
+  double* Gy;
+  double* Y;
+};
+
+__global__ void k_step(const StepParams s) {
+  extern __shared__ double sm[];
+  const int bd = blockDim.x, tid = threadIdx.x;
+  double* Psh = sm;                                   // shared operator (n*n) if shared
+  double* w = sm + (s.shared ? s.n * s.n : 0);        // [n][bd]
+  double* g = w + s.n * bd;                           // [n][bd]
+  if (s.shared)
+    for (int t = tid; t < s.n * s.n; t += bd) Psh[t] = s.P[t];
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)bd + tid;
+  if (e >= s.nel) return;
+  const int64_t ne = s.nel;
+  for (int c = 0; c < s.n; ++c) {
+    double v = s.u[c * ne + e] * s.ucoef;
+    if (s.have_force)
+      v += s.force_avg ? 0.5 * (s.force[c * ne + e] + s.force_old[c * ne + e]) : s.force[c * ne + e];
+    w[c * bd + tid] = v;
+  }
+  for (int r = 0; r < s.n; ++r) {
+    double acc = 0.0;
+    if (s.shared) {
+      for (int c = 0; c < s.n; ++c) acc += Psh[r * s.n + c] * w[c * bd + tid];
+    } else {
+      const double* Pr = s.P + (int64_t)r * s.n * ne + e;
+      for (int c = 0; c < s.n; ++c) acc += Pr[c * ne] * w[c * bd + tid];
+    }
+    g[r * bd + tid] = acc;
+    s.G[r * ne + e] = acc;
+  }
+  for (int r = 0; r < s.NQFS; ++r) {
+    double gy = 0.0, y0 = 0.0;
+    for (int k = 0; k < s.KE; ++k) {
+      const double ev = s.ey_val[r * s.KE + k];
+      const int ix = s.ey_idx[r * s.KE + k];
+      gy += ev * g[ix * bd + tid];
+      y0 += ev * s.u[ix * ne + e];
+    }
+    s.Gy[r * ne + e] = gy;
+    s.Y[r * ne + e] = y0;
+  }
+}
+
+cudaError_t launch_step(Ctx& c) {
+  StepParams s;
+  s.nel = c.nel;
+  s.n = c.n;
+  s.NQFS = c.NQFS;
+  s.KE = c.KE;
+  s.shared = c.shared_op ? 1 : 0;
+  s.ucoef = (c.scheme == EHDG_STEADY) ? 0.0 : 1.0 / c.dt_eff;
+  s.have_force = c.have_force ? 1 : 0;
+  s.force_avg = (c.scheme == EHDG_CN) ? 1 : 0;
+  s.P = c.P;
+  s.u = c.u;
+  s.force = c.force;
+  s.force_old = c.force_old;
+  s.ey_idx = c.ey_idx;
+  s.ey_val = c.ey_val;
+  s.G = c.G;
+  s.Gy = c.Gy;
+  s.Y = c.Y;
+  int bd = 128;
+  size_t smem = sizeof(double) * ((s.shared ? (size_t)c.n * c.n : 0) + 2 * (size_t)c.n * bd);
+  while (smem > 200 * 1024 && bd > 32) {
+    bd /= 2;
+    smem = sizeof(double) * ((s.shared ? (size_t)c.n * c.n : 0) + 2 * (size_t)c.n * bd);
+  }
+  cudaError_t err = cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int grid = (int)((c.nel + bd - 1) / bd);
+  k_step<<<grid, bd, smem, c.stream>>>(s);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Element sweep (eq. transportLocalk1 / localSolverDD): Y = Gy + Hy uhat
+// ===========================================================================
+struct ElemParams {
+  int64_t nel, nface;
+  int NQFS, Nqf, F, shared, n_rows;
+  const int* rows;              // output rows (face points) to compute
+  const int32_t* elem_face;     // [F][nel]
+  const double* uhat;           // [Nqf][nface]
+  const double* Gy;             // [NQFS][nel]
+  const double* Hy;             // [NQFS][NQFS][ne]
+  double* Y;                    // [NQFS][nel]
+};
+
+__global__ void k_elem(const ElemParams p) {
+  extern __shared__ double sm[];
+  const int bd = blockDim.x, tid = threadIdx.x;
+  double* Hsh = sm;
+  double* uh = sm + (p.shared ? p.NQFS * p.NQFS : 0);   // [NQFS][bd]
+  if (p.shared)
+    for (int t = tid; t < p.NQFS * p.NQFS; t += bd) Hsh[t] = p.Hy[t];
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)bd + tid;
+  if (e >= p.nel) return;
+  const int64_t ne = p.nel;
+  for (int f = 0; f < p.F; ++f) {
+    const int64_t face = p.elem_face[f * ne + e];
+    for (int g = 0; g < p.Nqf; ++g) uh[(f * p.Nqf + g) * bd + tid] = p.uhat[g * p.nface + face];
+  }
+  for (int rr = 0; rr < p.n_rows; ++rr) {
+    const int r = p.rows[rr];
+    double acc = p.Gy[r * ne + e];
+    if (p.shared) {
+      const double* Hr = Hsh + r * p.NQFS;
+      for (int t = 0; t < p.NQFS; ++t) acc += Hr[t] * uh[t * bd + tid];
+    } else {
+      const double* Hr = p.Hy + (int64_t)r * p.NQFS * ne + e;
+      for (int t = 0; t < p.NQFS; ++t) acc += Hr[t * ne] * uh[t * bd + tid];
+    }
+    p.Y[r * ne + e] = acc;
+  }
+}
+
+cudaError_t launch_elem(Ctx& c) {
+  ElemParams p;
+  p.nel = c.nel;
+  p.nface = c.nface;
+  p.NQFS = c.NQFS;
+  p.Nqf = c.Nqf;
+  p.F = c.F;
+  p.shared = c.shared_op ? 1 : 0;
+  p.n_rows = c.n_rows;
+  p.rows = c.rows;
+  p.elem_face = c.geo.elem_face;
+  p.uhat = c.uhat;
+  p.Gy = c.Gy;
+  p.Hy = c.Hy;
+  p.Y = c.Y;
+  int bd = 128;
+  size_t smem = sizeof(double) * ((p.shared ? (size_t)c.NQFS * c.NQFS : 0) + (size_t)c.NQFS * bd);
+  while (smem > 200 * 1024 && bd > 32) {
+    bd /= 2;
+    smem = sizeof(double) * ((p.shared ? (size_t)c.NQFS * c.NQFS : 0) + (size_t)c.NQFS * bd);
+  }
+  cudaError_t err = cudaFuncSetAttribute(k_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int grid = (int)((c.nel + bd - 1) / bd);
+  k_elem<<<grid, bd, smem, c.stream>>>(p);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// Face trace update (eq. transportLocale; shallow-water trace) + residual
+// ===========================================================================
+struct FaceParams {
+  RefTables R;
+  Geometry geo;
+  int pde, mode, cn, Nqf;
+  double tol, res_scale;
+  int max_iter;
+  const int8_t* sgn;
+  const double* Y;              // [NQFS][nel]
+  const double* gb;             // [Nqf][nface]
+  const double* gb_old;
+  double* uhat;                 // [Nqf][nface], updated in place
+  double* partials;
+  IterState* it;
+  double* hist;
+};
+
+constexpr int kFaceBlock = 256;
+
+__global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
+  __shared__ double red[kFaceBlock / 32];
+  __shared__ bool last;
+  const int64_t nface = p.geo.nface, nel = p.geo.nel;
+  const int64_t total = (int64_t)p.Nqf * nface;
+  double acc = 0.0;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int gf = (int)(t / nface);
+    const int64_t face = t - (int64_t)gf * nface;
+    const int em = p.geo.face_elem[face];
+    const int ep = p.geo.face_elem[nface + face];
+    const int fm = p.geo.face_local[face];
+    const int fpl = p.geo.face_local[nface + face];
+    double uh;
+    if (p.pde == EHDG_TRANSPORT) {
+      const int s = p.sgn[t];
+      double ext = 0.0;
+      if (ep < 0) ext = p.cn ? 0.5 * (p.gb[t] + p.gb_old[t]) : p.gb[t];
+      if (s > 0) {
+        uh = p.Y[(int64_t)(fm * p.Nqf + gf) * nel + em];
+      } else if (s < 0) {
+        uh = (ep >= 0) ? p.Y[(int64_t)(fpl * p.Nqf + gf) * nel + ep] : ext;
+      } else {
+        const double ym = p.Y[(int64_t)(fm * p.Nqf + gf) * nel + em];
+        const double yp = (ep >= 0) ? p.Y[(int64_t)(fpl * p.Nqf + gf) * nel + ep] : ext;
+        uh = 0.5 * (ym + yp);
+      }
+    } else {
+      const double ym = p.Y[(int64_t)(fm * p.Nqf + gf) * nel + em];
+      uh = (ep >= 0) ? ym + p.Y[(int64_t)(fpl * p.Nqf + gf) * nel + ep] : 2.0 * ym;
+    }
+    if (p.mode == kFaceIterate) {
+      const double d = uh - p.uhat[t];
+      acc += p.geo.face_jf[face] * fweight(p.R, gf) * d * d;
+    }
+    p.uhat[t] = uh;
+  }
+  if (p.mode != kFaceIterate) return;
+
+  // deterministic reduction: warp -> block -> partials[block] -> last block
+  acc = warp_sum(acc);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (wid == 0) {
+    double v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) {
+      p.partials[blockIdx.x] = v;
+      __threadfence();
+      const unsigned int ticket = atomicAdd(&p.it->counter, 1u);
+      last = (ticket == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+    v += reinterpret_cast<volatile double*>(p.partials)[i];
+  v = warp_sum(v);
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += red[w];
+    const double r = p.res_scale * sqrt(sum);
+    IterState* it = p.it;
+    const int k = it->k;
+    if (k < p.max_iter) p.hist[k] = r;
+    it->k = k + 1;
+    it->r_last = r;
+    it->counter = 0u;
+    int cont = 1, status = EHDG_OK;
+    if (!isfinite(r)) { cont = 0; status = EHDG_ERR_DIVERGED; }
+    else if (r < p.tol) { cont = 0; status = EHDG_OK; }
+    else if (k + 1 >= p.max_iter) { cont = 0; status = EHDG_ERR_NOT_CONVERGED; }
+    it->cont = cont;
+    it->status = status;
+    __threadfence();
+  }
+}
+
+cudaError_t launch_face(Ctx& c, int mode) {
+  FaceParams p;
+  p.R = c.ref;
+  p.geo = c.geo;
+  p.pde = c.pde;
+  p.mode = mode;
+  p.cn = (c.scheme == EHDG_CN) ? 1 : 0;
+  p.Nqf = c.Nqf;
+  p.tol = c.tol;
+  p.res_scale = c.res_scale;
+  p.max_iter = c.max_iter;
+  p.sgn = c.sgn;
+  p.Y = c.Y;
+  p.gb = c.gb;
+  p.gb_old = c.gb_old;
+  p.uhat = c.uhat;
+  p.partials = c.partials;
+  p.it = c.it;
+  p.hist = c.hist;
+  k_face<<<c.n_partials, kFaceBlock, 0, c.stream>>>(p);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// End of step: u^{n+1} = G + H uhat (Crank-Nicolson: 2 v - u^n), trace update
+// ===========================================================================
+struct FinalParams {
+  int64_t nel, nface;
+  int n, NQFS, Nqf, F, shared, cn;
+  const int32_t* elem_face;
+  const double* uhat;
+  const double* G;
+  const double* H;
+  double* u;
+};
+
+__global__ void k_final(const FinalParams p) {
+  extern __shared__ double sm[];
+  const int bd = blockDim.x, tid = threadIdx.x;
+  double* Hsh = sm;
+  double* uh = sm + (p.shared ? p.n * p.NQFS : 0);
+  if (p.shared)
+    for (int t = tid; t < p.n * p.NQFS; t += bd) Hsh[t] = p.H[t];
+  __syncthreads();
+  const int64_t e = blockIdx.x * (int64_t)bd + tid;
+  if (e >= p.nel) return;
+  const int64_t ne = p.nel;
+  for (int f = 0; f < p.F; ++f) {
+    const int64_t face = p.elem_face[f * ne + e];
+    for (int g = 0; g < p.Nqf; ++g) uh[(f * p.Nqf + g) * bd + tid] = p.uhat[g * p.nface + face];
+  }
+  for (int r = 0; r < p.n; ++r) {
+    double acc = p.G[r * ne + e];
+    if (p.shared) {
+      for (int t = 0; t < p.NQFS; ++t) acc += Hsh[r * p.NQFS + t] * uh[t * bd + tid];
+    } else {
+      const double* Hr = p.H + (int64_t)r * p.NQFS * ne + e;
+      for (int t = 0; t < p.NQFS; ++t) acc += Hr[t * ne] * uh[t * bd + tid];
+    }
+    if (p.cn) acc = 2.0 * acc - p.u[r * ne + e];
+    p.u[r * ne + e] = acc;
+  }
+}
+
+__global__ void k_trace_end(int64_t total, int cn, double* uhat, double* uhat_n,
+                            const double* gb, double* gb_old) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    double v = uhat[t];
+    if (cn) {
+      v = 2.0 * v - uhat_n[t];
+      uhat[t] = v;
+    }
+    uhat_n[t] = v;
+    gb_old[t] = gb[t];
+  }
+}
+
+cudaError_t launch_final(Ctx& c) {
+  FinalParams p;
+  p.nel = c.nel;
+  p.nface = c.nface;
+  p.n = c.n;
+  p.NQFS = c.NQFS;
+  p.Nqf = c.Nqf;
+  p.F = c.F;
+  p.shared = c.shared_op ? 1 : 0;
+  p.cn = (c.scheme == EHDG_CN) ? 1 : 0;
+  p.elem_face = c.geo.elem_face;
+  p.uhat = c.uhat;
+  p.G = c.G;
+  p.H = c.H;
+  p.u = c.u;
+  int bd = 128;
+  size_t smem = sizeof(double) * ((p.shared ? (size_t)c.n * c.NQFS : 0) + (size_t)c.NQFS * bd);
+  while (smem > 200 * 1024 && bd > 32) {
+    bd /= 2;
+    smem = sizeof(double) * ((p.shared ? (size_t)c.n * c.NQFS : 0) + (size_t)c.NQFS * bd);
+  }
+  cudaError_t err = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  const int grid = (int)((c.nel + bd - 1) / bd);
+  k_final<<<grid, bd, smem, c.stream>>>(p);
+  err = cudaGetLastError();
+  if (err != cudaSuccess) return err;
+  const int64_t total = (int64_t)c.Nqf * c.nface;
+  k_trace_end<<<(int)((total + 255) / 256), 256, 0, c.stream>>>(total, p.cn, c.uhat, c.uhat_n,
+                                                                  c.gb, c.gb_old);
+  return cudaGetLastError();
+}
+
+// ===========================================================================
+// misc: Y = Ey u (initial trace input), transposes, iteration reset
+// ===========================================================================
+__global__ void k_extract(int64_t nel, int NQFS, int KE, const int* ey_idx, const double* ey_val,
+                          const double* u, double* Y) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nel) return;
+  for (int r = 0; r < NQFS; ++r) {
+    double y = 0.0;
+    for (int k = 0; k < KE; ++k) y += ey_val[r * KE + k] * u[(int64_t)ey_idx[r * KE + k] * nel + e];
+    Y[(int64_t)r * nel + e] = y;
+  }
+}
+
+cudaError_t launch_extract(Ctx& c) {
+  k_extract<<<(int)((c.nel + 127) / 128), 128, 0, c.stream>>>(c.nel, c.NQFS, c.KE, c.ey_idx,
+                                                                c.ey_val, c.u, c.Y);
+  return cudaGetLastError();
+}
+
+// src [rows][cols] -> dst [cols][rows], 32x32 tiles on a 1D grid of tiles
+__global__ void k_transpose(const double* __restrict__ src, double* __restrict__ dst,
+                            int64_t rows, int64_t cols, int64_t ntc) {
+  __shared__ double tile[32][33];
+  const int64_t tr = blockIdx.x / ntc, tc = blockIdx.x % ntc;
+  const int64_t c0 = tc * 32, r0 = tr * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t r = r0 + k, c = c0 + threadIdx.x;
+    if (r < rows && c < cols) tile[k][threadIdx.x] = src[r * cols + c];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t c = c0 + k, r = r0 + threadIdx.x;
+    if (r < rows && c < cols) dst[c * rows + r] = tile[threadIdx.x][k];
+  }
+}
+
+static cudaError_t transpose(const double* src, double* dst, int64_t rows, int64_t cols,
+                             cudaStream_t s) {
+  if (rows == 0 || cols == 0) return cudaSuccess;
+  const int64_t ntr = (rows + 31) / 32, ntc = (cols + 31) / 32;
+  if (ntr * ntc > 0x7fffffffLL) return cudaErrorInvalidValue;
+  k_transpose<<<(unsigned)(ntr * ntc), dim3(32, 8), 0, s>>>(src, dst, rows, cols, ntc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aos_to_soa(const double* src, double* dst, int64_t outer, int inner,
+                              cudaStream_t s) {
+  return transpose(src, dst, outer, inner, s);
+}
+
+cudaError_t launch_soa_to_aos(const double* src, double* dst, int64_t outer, int inner,
+                              cudaStream_t s) {
+  return transpose(src, dst, inner, outer, s);
+}
+
+__global__ void k_reset(IterState* it) {
+  it->k = 0;
+  it->cont = 1;
+  it->status = EHDG_OK;
+  it->counter = 0u;
+  it->r_last = 0.0;
+}
+
+cudaError_t launch_reset_iter(Ctx& c) {
+  k_reset<<<1, 1, 0, c.stream>>>(c.it);
+  return cudaGetLastError();
+}
+
+}  // namespace ehdg

@@ -1,0 +1,303 @@
+"""Thin ctypes binding of libehdg (include/ehdg.h): argument marshalling only.
+
+Every numerical step runs in the CUDA library; this module converts numpy
+arrays and torch CUDA tensors into the pointers and sizes the C ABI takes.
+Loading fails loudly when libehdg.so has not been built (there is no CPU
+fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libehdg.so")
+
+EHDG_OK = 0
+STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "DIVERGED",
+          6: "TIMEOUT", 7: "UNSUPPORTED"}
+PDE = {"transport": 0, "sw": 1}
+SCHEME = {"be": 0, "cn": 1, "steady": 2}
+PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2}
+FACE_INTERIOR, FACE_DIRICHLET, FACE_WALL = 0, 1, 2
+
+
+class EhdgError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"ehdg status {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_elem", C.c_int64), ("n_face", C.c_int64),
+                ("elem_lo", C.POINTER(C.c_double)), ("elem_h", C.POINTER(C.c_double)),
+                ("elem_face", C.POINTER(C.c_int64)), ("face_elem", C.POINTER(C.c_int64)),
+                ("face_local", C.POINTER(C.c_int8)), ("face_tag", C.POINTER(C.c_int32))]
+
+
+class ProblemDesc(C.Structure):
+    _fields_ = [("pde", C.c_int), ("p", C.c_int), ("scheme", C.c_int), ("dt", C.c_double),
+                ("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int),
+                ("beta_const", C.POINTER(C.c_double)), ("beta_nodes", C.POINTER(C.c_double)),
+                ("Phi", C.c_double)]
+
+
+class Info(C.Structure):
+    _fields_ = [("dim", C.c_int), ("p", C.c_int), ("nf", C.c_int), ("Np", C.c_int),
+                ("q", C.c_int), ("Nqf", C.c_int), ("n_elem", C.c_int64), ("n_face", C.c_int64),
+                ("state_len", C.c_int64), ("trace_len", C.c_int64),
+                ("shared_operator", C.c_int), ("device_bytes", C.c_int64)]
+
+
+_lib = None
+
+# (name, restype, argtypes) of every exported entry point
+_SIGS = [
+    ("ehdg_mesh_structured", C.c_int, [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                       C.POINTER(C.c_double), C.c_int32, C.POINTER(MeshDesc)]),
+    ("ehdg_mesh_free", None, [C.POINTER(MeshDesc)]),
+    ("ehdg_create", C.c_int, [C.POINTER(MeshDesc), C.POINTER(ProblemDesc), C.c_void_p,
+                              C.POINTER(C.c_void_p)]),
+    ("ehdg_get_info", C.c_int, [C.c_void_p, C.POINTER(Info)]),
+    ("ehdg_destroy", None, [C.c_void_p]),
+    ("ehdg_node_coords", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("ehdg_face_point_coords", C.c_int, [C.c_void_p, C.c_void_p]),
+    ("ehdg_set_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    ("ehdg_set_forcing", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    ("ehdg_set_boundary", C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    ("ehdg_step", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    ("ehdg_run", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
+    ("ehdg_step_fixed", C.c_int, [C.c_void_p, C.c_int]),
+    ("ehdg_get_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    ("ehdg_get_residual_history", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64,
+                                            C.POINTER(C.c_int64)]),
+    ("ehdg_set_profiling", C.c_int, [C.c_void_p, C.c_int]),
+    ("ehdg_kernel_stats", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_double)]),
+    ("ehdg_last_error", C.c_char_p, []),
+]
+
+KERNEL_KINDS = ["assemble", "signs", "step", "elem", "face", "final", "aux"]
+
+
+def load(path=LIB_PATH):
+    """Load libehdg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1601_06681_gb300.build.build()")
+    lib = C.CDLL(path)
+    for name, res, args in _SIGS:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_names():
+    return [s[0] for s in _SIGS]
+
+
+def _check(status):
+    if status != EHDG_OK:
+        raise EhdgError(status, load().ehdg_last_error().decode())
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _buf(x, shape):
+    """(pointer, on_device, keepalive) for a numpy array or a CUDA tensor."""
+    if x is None:
+        return None, 0, None
+    if hasattr(x, "is_cuda") and x.is_cuda:
+        import torch
+        assert x.dtype == torch.float64 and x.is_contiguous() and x.numel() == int(np.prod(shape))
+        return C.c_void_p(x.data_ptr()), 1, x
+    a = np.ascontiguousarray(x, dtype=np.float64)
+    assert a.size == int(np.prod(shape)), (a.shape, shape)
+    return a.ctypes.data_as(C.c_void_p), 0, a
+
+
+class Mesh:
+    """A mesh descriptor that keeps its arrays alive (from a dict of arrays or
+    from the library's structured-mesh builder)."""
+
+    def __init__(self, d):
+        self.dim = int(d["dim"])
+        self.arrays = dict(
+            elem_lo=np.ascontiguousarray(d["elem_lo"], dtype=np.float64),
+            elem_h=np.ascontiguousarray(d["elem_h"], dtype=np.float64),
+            elem_face=np.ascontiguousarray(d["elem_face"], dtype=np.int64),
+            face_elem=np.ascontiguousarray(d["face_elem"], dtype=np.int64),
+            face_local=np.ascontiguousarray(d["face_local"], dtype=np.int8),
+            face_tag=np.ascontiguousarray(d["face_tag"], dtype=np.int32))
+        a = self.arrays
+        self.n_elem, self.n_face = int(d["n_elem"]), int(d["n_face"])
+        self.desc = MeshDesc(self.dim, self.n_elem, self.n_face, _ptr(a["elem_lo"], C.c_double),
+                             _ptr(a["elem_h"], C.c_double), _ptr(a["elem_face"], C.c_int64),
+                             _ptr(a["face_elem"], C.c_int64), _ptr(a["face_local"], C.c_int8),
+                             _ptr(a["face_tag"], C.c_int32))
+
+    def as_dict(self):
+        return dict(dim=self.dim, n_elem=self.n_elem, n_face=self.n_face, **self.arrays)
+
+
+def ehdg_mesh_structured(n, lo=None, hi=None, boundary_tag=FACE_DIRICHLET):
+    """The library's structured mesh, returned as a dict of numpy arrays."""
+    lib = load()
+    dim = len(n)
+    nn = (C.c_int64 * 3)(*(list(n) + [1] * (3 - dim)))
+    lo = [0.0] * dim if lo is None else list(lo)
+    hi = [1.0] * dim if hi is None else list(hi)
+    clo = (C.c_double * 3)(*(lo + [0.0] * (3 - dim)))
+    chi = (C.c_double * 3)(*(hi + [1.0] * (3 - dim)))
+    desc = MeshDesc()
+    _check(lib.ehdg_mesh_structured(dim, nn, clo, chi, boundary_tag, C.byref(desc)))
+    try:
+        ne, nf = desc.n_elem, desc.n_face
+        out = dict(dim=dim, n_elem=ne, n_face=nf,
+                   elem_lo=np.ctypeslib.as_array(desc.elem_lo, (ne, dim)).copy(),
+                   elem_h=np.ctypeslib.as_array(desc.elem_h, (ne, dim)).copy(),
+                   elem_face=np.ctypeslib.as_array(desc.elem_face, (ne, 2 * dim)).copy(),
+                   face_elem=np.ctypeslib.as_array(desc.face_elem, (nf, 2)).copy(),
+                   face_local=np.ctypeslib.as_array(desc.face_local, (nf, 2)).copy(),
+                   face_tag=np.ctypeslib.as_array(desc.face_tag, (nf,)).copy())
+    finally:
+        lib.ehdg_mesh_free(C.byref(desc))
+    return out
+
+
+class Solver:
+    """One eHDG problem on the GPU (wraps an ehdg_ctx)."""
+
+    def __init__(self, mesh, p, pde="transport", scheme="be", dt=1.0, tol=1e-10, max_iter=1000,
+                 beta_const=None, beta_nodes=None, Phi=1.0, precision="fp64", stream=None):
+        lib = load()
+        self.mesh = mesh if isinstance(mesh, Mesh) else Mesh(mesh)
+        self._beta_const = None if beta_const is None else np.ascontiguousarray(beta_const, np.float64)
+        self._beta_nodes = None if beta_nodes is None else np.ascontiguousarray(beta_nodes, np.float64)
+        prob = ProblemDesc(
+            PDE[pde], int(p), SCHEME[scheme], float(dt), float(tol), int(max_iter),
+            PRECISION[precision],
+            None if self._beta_const is None else _ptr(self._beta_const, C.c_double),
+            None if self._beta_nodes is None else _ptr(self._beta_nodes, C.c_double), float(Phi))
+        if stream is None:
+            s = None
+        elif isinstance(stream, int):
+            s = C.c_void_p(stream)
+        else:
+            s = C.c_void_p(stream.cuda_stream)
+        h = C.c_void_p()
+        _check(lib.ehdg_create(C.byref(self.mesh.desc), C.byref(prob), s, C.byref(h)))
+        self._h = h
+        info = Info()
+        _check(lib.ehdg_get_info(h, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in Info._fields_}
+        self.max_iter = int(max_iter)
+
+    # sizes
+    @property
+    def state_shape(self):
+        i = self.info
+        return (i["n_elem"], i["nf"], i["Np"])
+
+    @property
+    def trace_shape(self):
+        return (self.info["n_face"], self.info["Nqf"])
+
+    def node_coords(self):
+        i = self.info
+        x = np.empty((i["n_elem"], i["Np"], i["dim"]))
+        _check(load().ehdg_node_coords(self._h, x.ctypes.data_as(C.c_void_p)))
+        return x
+
+    def face_point_coords(self):
+        i = self.info
+        x = np.empty((i["n_face"], i["Nqf"], i["dim"]))
+        _check(load().ehdg_face_point_coords(self._h, x.ctypes.data_as(C.c_void_p)))
+        return x
+
+    def set_state(self, u, uhat=None):
+        pu, dev, ku = _buf(u, self.state_shape)
+        ph, dev2, kh = _buf(uhat, self.trace_shape)
+        if uhat is not None:
+            assert dev == dev2
+        _check(load().ehdg_set_state(self._h, pu, ph, dev))
+
+    def set_forcing(self, f):
+        pf, dev, kf = _buf(f, self.state_shape)
+        _check(load().ehdg_set_forcing(self._h, pf, dev))
+
+    def set_boundary(self, g):
+        pg, dev, kg = _buf(g, self.trace_shape)
+        _check(load().ehdg_set_boundary(self._h, pg, dev))
+
+    def step(self, check=True):
+        it, res = C.c_int(), C.c_double()
+        st = load().ehdg_step(self._h, C.byref(it), C.byref(res))
+        if check:
+            _check(st)
+        return it.value, res.value, st
+
+    def step_fixed(self, n_iter):
+        _check(load().ehdg_step_fixed(self._h, int(n_iter)))
+
+    def run(self, n_steps):
+        iters = (C.c_int * max(n_steps, 1))()
+        _check(load().ehdg_run(self._h, int(n_steps), iters))
+        return list(iters)[:n_steps]
+
+    def get_state(self, u_out=None, uhat_out=None):
+        """Host copies (numpy) unless CUDA tensors are given to fill."""
+        if u_out is None and uhat_out is None:
+            u = np.empty(self.state_shape)
+            uh = np.empty(self.trace_shape)
+            _check(load().ehdg_get_state(self._h, u.ctypes.data_as(C.c_void_p),
+                                         uh.ctypes.data_as(C.c_void_p), 0))
+            return u, uh
+        pu, dev, _ = _buf(u_out, self.state_shape)
+        ph, dev2, _ = _buf(uhat_out, self.trace_shape)
+        _check(load().ehdg_get_state(self._h, pu, ph, max(dev, dev2)))
+        return u_out, uhat_out
+
+    def residual_history(self):
+        buf = np.empty(self.max_iter)
+        n = C.c_int64()
+        _check(load().ehdg_get_residual_history(self._h, buf.ctypes.data_as(C.c_void_p),
+                                                buf.size, C.byref(n)))
+        return buf[:min(n.value, buf.size)].copy()
+
+    def set_profiling(self, on=True):
+        _check(load().ehdg_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_stats(self):
+        """{kind: (launches, total device ms)} since profiling was last switched."""
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            n, ms = C.c_int64(), C.c_double()
+            _check(load().ehdg_kernel_stats(self._h, k, C.byref(n), C.byref(ms)))
+            out[name] = (n.value, ms.value)
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().ehdg_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,218 @@
+"""GPU path (through the C ABI) against the CPU oracle, element by element.
+
+Sizes span several thread blocks with a ragged tail; tolerances: relative L2
+1e-12 in float64 (the float64 target of the method's GPU path).
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+from oracle import direct
+from oracle.ehdg import Problem
+from oracle.geometry import face_point_coords, node_coords
+from paper_1601_06681_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def ehdg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_06681_gb300 import build, ehdg as E
+    build.build()
+    E.load()
+    return E
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def make_case(name):
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    if name == "2d_be_const":
+        mesh, p = W.structured_mesh((17, 11)), 2
+        kw = dict(scheme="be", dt=0.02, beta_const=np.array([1.0, 0.5]))
+    elif name == "2d_be_zero_component":
+        mesh, p = W.structured_mesh((13, 10)), 3
+        kw = dict(scheme="be", dt=0.05, beta_const=np.array([-0.8, 0.0]))
+    elif name == "2d_cn_variable":
+        wl = W.transport_2d_variable(n=(14, 11), p=3)
+        mesh, p = wl.mesh(), 3
+        kw = dict(scheme="cn", dt=0.01, beta_nodes=wl.beta_nodes(node_coords(mesh, p)))
+    elif name == "2d_cn_variable_p4":
+        wl = W.transport_2d_variable(n=(12, 12), p=4)
+        mesh, p = wl.mesh(), 4
+        kw = dict(scheme="cn", dt=2e-3, beta_nodes=wl.beta_nodes(node_coords(mesh, p)))
+    elif name == "2d_steady_variable":
+        mesh, p = W.structured_mesh((9, 8)), 2
+        X = node_coords(mesh, p)
+        bn = np.ascontiguousarray(np.transpose(np.stack([X[..., 1] + 0.1, X[..., 0] + 0.2], -1), (0, 2, 1)))
+        kw = dict(scheme="steady", beta_nodes=bn)
+    elif name == "2d_graded_mesh":
+        # conforming mesh with graded spacing: per-element operators, constant beta
+        nx, ny = 10, 13
+        mesh, p = W.structured_mesh((nx, ny)), 2
+        xs = (np.arange(nx + 1) / nx) ** 1.4
+        ys = np.sin(0.5 * np.pi * np.arange(ny + 1) / ny)
+        i0 = np.arange(mesh["n_elem"]) % nx
+        i1 = np.arange(mesh["n_elem"]) // nx
+        mesh["elem_lo"] = np.stack([xs[i0], ys[i1]], -1)
+        mesh["elem_h"] = np.stack([xs[i0 + 1] - xs[i0], ys[i1 + 1] - ys[i1]], -1)
+        kw = dict(scheme="be", dt=0.03, beta_const=np.array([0.6, -0.9]))
+    elif name == "2d_per_element_const_beta":
+        # a constant velocity given per node takes the per-element path
+        mesh, p = W.structured_mesh((10, 13)), 2
+        kw = dict(scheme="be", dt=0.03, beta_nodes=np.ascontiguousarray(
+            np.broadcast_to(np.array([0.6, -0.9])[None, :, None], (mesh["n_elem"], 2, (p + 1) ** 2))))
+    elif name == "3d_be_const":
+        mesh, p = W.structured_mesh((6, 5, 4)), 2
+        kw = dict(scheme="be", dt=0.05, beta_const=np.array([1.0, 1.0, 1.0]) / np.sqrt(3.0))
+    elif name == "3d_be_const_p3":
+        mesh, p = W.structured_mesh((5, 3, 4)), 3
+        kw = dict(scheme="be", dt=5e-3, beta_const=np.array([0.3, -1.0, 0.6]))
+    elif name == "sw_be":
+        mesh, p = W.structured_mesh((12, 11), boundary_tag=W.TAG_WALL), 2
+        kw = dict(pde="sw", scheme="be", dt=1e-2, Phi=1.3)
+    elif name == "sw_be_p3":
+        mesh, p = W.structured_mesh((9, 14), boundary_tag=W.TAG_WALL), 3
+        kw = dict(pde="sw", scheme="be", dt=1e-3, Phi=1.0)
+    else:
+        raise KeyError(name)
+    prob = Problem(mesh, p, **kw)
+    u0 = rng.standard_normal((prob.nel, prob.nf, prob.Np))
+    g = None
+    if prob.pde == "transport":
+        XF = face_point_coords(mesh, p, prob.ref.q)
+        g = np.cos(2.0 * XF[..., 0] + 0.3) * np.sin(3.0 * XF[..., 1] + 0.1)
+        if mesh["dim"] == 3:
+            g = g * np.cos(XF[..., 2])
+    return mesh, p, kw, prob, u0, g
+
+
+def make_solver(E, mesh, p, kw, prob, tol=1e-10, max_iter=400):
+    args = dict(kw)
+    return E.Solver(mesh, p, tol=tol, max_iter=max_iter, **args)
+
+
+CASES = ["2d_be_const", "2d_be_zero_component", "2d_cn_variable", "2d_cn_variable_p4",
+         "2d_steady_variable", "2d_graded_mesh", "2d_per_element_const_beta", "3d_be_const", "3d_be_const_p3", "sw_be",
+         "sw_be_p3"]
+
+
+@pytest.mark.parametrize("name", CASES)
+def test_coordinates_match_oracle(ehdg, name):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        assert np.abs(s.node_coords() - node_coords(mesh, p)).max() < 1e-15
+        assert np.abs(s.face_point_coords() - face_point_coords(mesh, p, prob.ref.q)).max() < 1e-15
+        assert s.info["Nqf"] == prob.Nqf
+
+
+@pytest.mark.parametrize("name", CASES)
+@pytest.mark.parametrize("n_iter", [1, 4])
+def test_fixed_iterations_match_oracle(ehdg, name, n_iter):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        if g is not None:
+            s.set_boundary(g)
+        s.set_state(u0)
+        _, uh0 = s.get_state()
+        uhn = prob.trace(u0, g)
+        assert rel(uh0, uhn) < RTOL
+        s.step_fixed(n_iter)
+        u, uh = s.get_state()
+        hist = s.residual_history()
+    ou, ouh, ohist = prob.solve_step(u0, uhn, g_new=g, fixed_iters=n_iter)
+    assert rel(u, ou) < RTOL
+    assert rel(uh, ouh) < RTOL
+    assert len(hist) == n_iter
+    assert np.allclose(hist, ohist, rtol=1e-10, atol=1e-300)
+
+
+@pytest.mark.parametrize("name", ["2d_be_const", "2d_cn_variable", "3d_be_const", "sw_be"])
+def test_steps_to_tolerance_match_oracle(ehdg, name):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    n_steps = 3
+    with make_solver(ehdg, mesh, p, kw, prob, tol=1e-10) as s:
+        if g is not None:
+            s.set_boundary(g)
+        s.set_state(u0)
+        iters = s.run(n_steps)
+        u, uh = s.get_state()
+    ou, ouh, oiters, _ = prob.run(u0, n_steps, g_of_t=(None if g is None else (lambda t: g)),
+                                  tol=1e-10)
+    assert iters == oiters
+    assert rel(u, ou) < RTOL
+    assert rel(uh, ouh) < RTOL
+
+
+def test_converged_step_equals_direct_hdg_solve(ehdg):
+    mesh, p, kw, prob, u0, g = make_case("2d_be_const")
+    with make_solver(ehdg, mesh, p, kw, prob, tol=1e-13, max_iter=2000) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        s.step()
+        u, uh = s.get_state()
+    ud, uhd = direct.solve(prob, u0, None, g=g)
+    assert rel(u, ud) < 1e-11
+    assert rel(uh, uhd) < 1e-11
+
+
+def test_not_converged_status_keeps_state(ehdg):
+    mesh, p, kw, prob, u0, g = make_case("2d_be_const")
+    with make_solver(ehdg, mesh, p, kw, prob, tol=1e-30, max_iter=3) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        it, res, st = s.step(check=False)
+        assert st == 4 and it == 3
+        u, _ = s.get_state()
+    ou, _, _ = prob.solve_step(u0, None, g_new=g, fixed_iters=3)
+    assert rel(u, ou) < RTOL
+
+
+def test_nan_input_reports_divergence(ehdg):
+    mesh, p, kw, prob, u0, g = make_case("2d_be_const")
+    bad = u0.copy()
+    bad[3, 0, 1] = np.nan
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        s.set_boundary(g)
+        s.set_state(bad)
+        it, res, st = s.step(check=False)
+        assert st == 5 and it == 1
+
+
+def test_invalid_arguments_rejected(ehdg):
+    mesh = W.structured_mesh((4, 4))
+    with pytest.raises(ehdg.EhdgError) as ei:
+        ehdg.Solver(mesh, 2, beta_const=[1.0, 0.0], dt=-1.0)
+    assert ei.value.status == 1
+    bad = dict(mesh)
+    bad["face_elem"] = mesh["face_elem"].copy()
+    bad["face_elem"][5, 0] = 10 ** 6
+    with pytest.raises(ehdg.EhdgError):
+        ehdg.Solver(bad, 2, beta_const=[1.0, 0.0], dt=0.1)
+    with pytest.raises(ehdg.EhdgError) as ei:
+        ehdg.Solver(mesh, 9, beta_const=[1.0, 0.0], dt=0.1)
+    assert ei.value.status == 7
+
+
+def test_device_pointer_io_matches_host_io(ehdg):
+    import torch
+    mesh, p, kw, prob, u0, g = make_case("2d_cn_variable")
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        s.set_boundary(torch.from_numpy(g).cuda())
+        s.set_state(torch.from_numpy(u0).cuda())
+        s.step()
+        du = torch.empty(s.state_shape, dtype=torch.float64, device="cuda")
+        duh = torch.empty(s.trace_shape, dtype=torch.float64, device="cuda")
+        s.get_state(du, duh)
+        u, uh = s.get_state()
+    assert np.array_equal(du.cpu().numpy(), u)
+    assert np.array_equal(duh.cpu().numpy(), uh)
