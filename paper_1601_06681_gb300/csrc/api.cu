@@ -184,6 +184,7 @@ ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
   if (c.have_force)
     CK(cudaMemcpyAsync(c.force_old, c.force, sizeof(double) * c.n * c.nel,
                        cudaMemcpyDeviceToDevice, c.stream));
+  CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_step_end(c); }));
   CK(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
   CK(cudaStreamSynchronize(c.stream));
   c.last_iters = std::min(c.it_host->k, c.max_iter);
@@ -195,6 +196,131 @@ ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
   if (st == EHDG_ERR_NOT_CONVERGED) return fail(st, "eHDG did not reach the tolerance in max_iter iterations");
   if (st == EHDG_ERR_DIVERGED) return fail(st, "non-finite eHDG residual");
   return st;
+}
+
+void destroy_graph(Ctx& c) {
+  if (c.gexec) cudaGraphExecDestroy(c.gexec);
+  if (c.graph) cudaGraphDestroy(c.graph);
+  c.gexec = nullptr;
+  c.graph = nullptr;
+}
+
+// Capture one implicit step: reset, step RHS, initial trace, then a WHILE node
+// whose body is {element sweep, trace update}; the trace kernel's last block
+// sets the condition (continue while r_k >= tol and k < max_iter), so the
+// iteration runs without a host round trip; then the end-of-step kernels.
+ehdg_status build_graph(Ctx& c) {
+  destroy_graph(c);
+  if (!c.cap_stream) CK(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+  if (!c.body_stream) CK(cudaStreamCreateWithFlags(&c.body_stream, cudaStreamNonBlocking));
+  cudaStream_t user = c.stream;
+  struct Restore {
+    Ctx& c;
+    cudaStream_t s;
+    ~Restore() { c.stream = s; }
+  } restore{c, user};
+  c.stream = c.cap_stream;
+  CK(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeRelaxed));
+  cudaError_t err = cudaSuccess;
+  cudaGraph_t g = nullptr;
+  auto abort_capture = [&](cudaError_t e, const char* what) {
+    cudaGraph_t junk = nullptr;
+    cudaStreamEndCapture(c.cap_stream, &junk);
+    if (junk) cudaGraphDestroy(junk);
+    cudaGetLastError();
+    return cuda_fail(e, what);
+  };
+  if ((err = launch_reset_iter(c)) != cudaSuccess) return abort_capture(err, "capture reset");
+  if ((err = launch_step(c)) != cudaSuccess) return abort_capture(err, "capture step");
+  if ((err = launch_face(c, kFaceInitial)) != cudaSuccess) return abort_capture(err, "capture face");
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  err = cudaStreamGetCaptureInfo(c.cap_stream, &cst, nullptr, &g, &deps, nullptr, &ndeps);
+  if (err != cudaSuccess) return abort_capture(err, "cudaStreamGetCaptureInfo");
+  cudaGraphConditionalHandle handle;
+  err = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
+  if (err != cudaSuccess) return abort_capture(err, "cudaGraphConditionalHandleCreate");
+  c.handle = handle;
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cond;
+  err = cudaGraphAddNode(&cond, g, deps, nullptr, ndeps, &cp);
+  if (err != cudaSuccess) return abort_capture(err, "cudaGraphAddNode(while)");
+  err = cudaStreamUpdateCaptureDependencies(c.cap_stream, &cond, nullptr, 1,
+                                            cudaStreamSetCaptureDependencies);
+  if (err != cudaSuccess) return abort_capture(err, "cudaStreamUpdateCaptureDependencies");
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  err = cudaStreamBeginCaptureToGraph(c.body_stream, body, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeRelaxed);
+  if (err != cudaSuccess) return abort_capture(err, "cudaStreamBeginCaptureToGraph");
+  c.stream = c.body_stream;
+  cudaError_t e1 = launch_elem(c);
+  cudaError_t e2 = (e1 == cudaSuccess) ? launch_face(c, kFaceIterate, 1) : e1;
+  cudaError_t e3 = cudaStreamEndCapture(c.body_stream, &body);
+  c.stream = c.cap_stream;
+  if (e2 != cudaSuccess) return abort_capture(e2, "capture loop body");
+  if (e3 != cudaSuccess) return abort_capture(e3, "end body capture");
+  if ((err = launch_final(c)) != cudaSuccess) return abort_capture(err, "capture final");
+  if (c.have_force &&
+      (err = cudaMemcpyAsync(c.force_old, c.force, sizeof(double) * c.n * c.nel,
+                             cudaMemcpyDeviceToDevice, c.stream)) != cudaSuccess)
+    return abort_capture(err, "capture forcing copy");
+  if ((err = launch_step_end(c)) != cudaSuccess) return abort_capture(err, "capture step end");
+  CK(cudaStreamEndCapture(c.cap_stream, &g));
+  c.graph = g;
+  CK(cudaGraphInstantiate(&c.gexec, g, 0));
+  c.graph_force = c.have_force;
+  return EHDG_OK;
+}
+
+ehdg_status ensure_step_arrays(Ctx& c, int n) {
+  if (n <= c.step_cap) return EHDG_OK;
+  int cap = std::max(n, 64);
+  int *a = nullptr, *b = nullptr;
+  TRY(dalloc(c, &a, cap));
+  TRY(dalloc(c, &b, cap));
+  c.step_iters = a;
+  c.step_status = b;
+  c.step_cap = cap;
+  destroy_graph(c);   // the graph holds the old pointers
+  return EHDG_OK;
+}
+
+// n_steps implicit steps as back-to-back graph launches; one sync at the end.
+ehdg_status run_graph(Ctx& c, int n_steps, int* iters_per_step, double* res) {
+  TRY(ensure_step_arrays(c, n_steps));
+  if (!c.gexec || c.graph_force != c.have_force) TRY(build_graph(c));
+  CK(cudaMemsetAsync(&c.it->step, 0, sizeof(int), c.stream));
+  for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(c.gexec, c.stream));
+  c.launches[EHDG_KERNEL_AUX] += 2 * n_steps;   // reset + step end
+  c.launches[EHDG_KERNEL_STEP] += n_steps;
+  c.launches[EHDG_KERNEL_FINAL] += 2 * n_steps;
+  c.step_iters_h.resize(n_steps);
+  c.step_status_h.resize(n_steps);
+  CK(cudaMemcpyAsync(c.step_iters_h.data(), c.step_iters, sizeof(int) * n_steps,
+                     cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(c.step_status_h.data(), c.step_status, sizeof(int) * n_steps,
+                     cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
+  CK(cudaStreamSynchronize(c.stream));
+  ehdg_status first = EHDG_OK;
+  int64_t sweeps = 0;
+  for (int s = 0; s < n_steps; ++s) {
+    sweeps += c.step_iters_h[s];
+    if (iters_per_step) iters_per_step[s] = c.step_iters_h[s];
+    if (first == EHDG_OK && c.step_status_h[s] != EHDG_OK) first = (ehdg_status)c.step_status_h[s];
+  }
+  c.launches[EHDG_KERNEL_ELEM] += sweeps;
+  c.launches[EHDG_KERNEL_FACE] += sweeps + n_steps;
+  c.last_iters = n_steps > 0 ? std::min(c.step_iters_h[n_steps - 1], c.max_iter) : 0;
+  if (res) *res = c.it_host->r_last;
+  if (first == EHDG_ERR_NOT_CONVERGED) return fail(first, "eHDG did not reach the tolerance in max_iter iterations");
+  if (first == EHDG_ERR_DIVERGED) return fail(first, "non-finite eHDG residual");
+  return first;
 }
 
 }  // namespace
@@ -336,6 +462,10 @@ void ehdg_mesh_free(ehdg_mesh_desc* m) {
 }
 
 static void release(Ctx& c) {
+  destroy_graph(c);
+  if (c.cap_stream) cudaStreamDestroy(c.cap_stream);
+  if (c.body_stream) cudaStreamDestroy(c.body_stream);
+  c.cap_stream = c.body_stream = nullptr;
   for (auto& r : c.ev_used) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -588,7 +718,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   TRYC(dalloc(c, &c.G, state));
   TRYC(dalloc(c, &c.Gy, (size_t)c.NQFS * c.nel));
   TRYC(dalloc(c, &c.Y, (size_t)c.NQFS * c.nel));
-  TRYC(dalloc(c, &c.uhat, trace));
+  TRYC(dalloc(c, &c.uhat, 2 * trace));
   TRYC(dalloc(c, &c.uhat_n, trace));
   TRYC(dalloc(c, &c.gb, trace));
   TRYC(dalloc(c, &c.gb_old, trace));
@@ -603,7 +733,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   CKC(cudaMallocHost(&c.it_host, sizeof(IterState)));
   CKC(cudaMemsetAsync(c.u, 0, sizeof(double) * state, c.stream));
   CKC(cudaMemsetAsync(c.Y, 0, sizeof(double) * c.NQFS * c.nel, c.stream));
-  CKC(cudaMemsetAsync(c.uhat, 0, sizeof(double) * trace, c.stream));
+  CKC(cudaMemsetAsync(c.uhat, 0, sizeof(double) * 2 * trace, c.stream));
   CKC(cudaMemsetAsync(c.uhat_n, 0, sizeof(double) * trace, c.stream));
   CKC(cudaMemsetAsync(c.gb, 0, sizeof(double) * trace, c.stream));
   CKC(cudaMemsetAsync(c.gb_old, 0, sizeof(double) * trace, c.stream));
@@ -728,11 +858,15 @@ ehdg_status ehdg_set_boundary(ehdg_ctx h, const double* g, int on_device) {
 
 ehdg_status ehdg_step(ehdg_ctx h, int* iters, double* final_residual) {
   if (!h) return fail(EHDG_ERR_INVALID, "NULL context");
-  return run_step(h->c, 0, iters, final_residual);
+  // with profiling on, the host-driven loop brackets every kernel with events
+  if (h->c.profiling) return run_step(h->c, 0, iters, final_residual);
+  return run_graph(h->c, 1, iters, final_residual);
 }
 
 ehdg_status ehdg_run(ehdg_ctx h, int n_steps, int* iters_per_step) {
   if (!h || n_steps < 0) return fail(EHDG_ERR_INVALID, "bad argument");
+  if (n_steps == 0) return EHDG_OK;
+  if (!h->c.profiling) return run_graph(h->c, n_steps, iters_per_step, nullptr);
   for (int s = 0; s < n_steps; ++s) {
     int it = 0;
     const ehdg_status st = run_step(h->c, 0, &it, nullptr);

@@ -55,6 +55,7 @@ struct IterState {
   int cont;                      // 1 while the loop must go on
   int status;                    // ehdg_status of the current step
   unsigned int counter;          // last-block ticket of the residual reduction
+  int step;                      // steps finished since the last reset (ehdg_run)
   double r_last;
 };
 
@@ -96,7 +97,7 @@ struct Ctx {
   double* G = nullptr;           // [n][nel]
   double* Gy = nullptr;          // [NQFS][nel]
   double* Y = nullptr;           // [NQFS][nel] element values at face points
-  double* uhat = nullptr;        // [Nqf][nface] current trace (in place)
+  double* uhat = nullptr;        // [2][Nqf][nface] trace ping-pong pair; slot 0 holds the state's trace
   double* uhat_n = nullptr;      // [Nqf][nface] trace of the previous step (CN)
   double* gb = nullptr;          // [Nqf][nface] boundary data, new level
   double* gb_old = nullptr;      // [Nqf][nface] boundary data, previous level
@@ -110,6 +111,16 @@ struct Ctx {
   double* staging = nullptr;     // [max(state,trace)] transposition buffer
   IterState* it_host = nullptr;  // pinned
   int last_iters = 0;
+  cudaGraphConditionalHandle handle = 0;
+  // one implicit step as a CUDA graph: step RHS, initial trace, WHILE{sweep, trace}, end of step
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_force = false;      // have_force value the graph was captured with
+  cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+  int* step_iters = nullptr;     // [step_cap] iterations of each step of ehdg_run
+  int* step_status = nullptr;
+  int step_cap = 0;
+  std::vector<int> step_iters_h, step_status_h;
 
   // kernel accounting (ehdg_set_profiling / ehdg_kernel_stats)
   bool profiling = false;
@@ -127,7 +138,7 @@ cudaError_t launch_assemble(Ctx& c, int n_assemble);
 cudaError_t launch_face_signs(Ctx& c);
 cudaError_t launch_step(Ctx& c);
 cudaError_t launch_elem(Ctx& c);
-cudaError_t launch_face(Ctx& c, int mode);   // 0 initial trace, 1 iteration
+cudaError_t launch_face(Ctx& c, int mode, int graph_mode = 0);   // 0 initial trace, 1 iteration
 cudaError_t launch_final(Ctx& c);
 cudaError_t launch_aos_to_soa(const double* src, double* dst, int64_t outer, int inner,
                               cudaStream_t s);   // src [outer][inner] -> dst [inner][outer]
@@ -135,6 +146,7 @@ cudaError_t launch_soa_to_aos(const double* src, double* dst, int64_t outer, int
                               cudaStream_t s);
 cudaError_t launch_reset_iter(Ctx& c);
 cudaError_t launch_extract(Ctx& c);
+cudaError_t launch_step_end(Ctx& c);
 
 enum FaceMode { kFaceInitial = 0, kFaceIterate = 1 };
 

@@ -469,7 +469,8 @@ struct ElemParams {
   int NQFS, Nqf, F, shared, n_rows;
   const int* rows;              // output rows (face points) to compute
   const int32_t* elem_face;     // [F][nel]
-  const double* uhat;           // [Nqf][nface]
+  const double* uhat;           // [2][Nqf][nface] ping-pong pair, iteration k reads slot k&1
+  const IterState* it;
   const double* Gy;             // [NQFS][nel]
   const double* Hy;             // [NQFS][NQFS][ne]
   double* Y;                    // [NQFS][nel]
@@ -486,9 +487,10 @@ __global__ void k_elem(const ElemParams p) {
   const int64_t e = blockIdx.x * (int64_t)bd + tid;
   if (e >= p.nel) return;
   const int64_t ne = p.nel;
+  const double* src = p.uhat + (int64_t)(p.it->k & 1) * p.Nqf * p.nface;
   for (int f = 0; f < p.F; ++f) {
     const int64_t face = p.elem_face[f * ne + e];
-    for (int g = 0; g < p.Nqf; ++g) uh[(f * p.Nqf + g) * bd + tid] = p.uhat[g * p.nface + face];
+    for (int g = 0; g < p.Nqf; ++g) uh[(f * p.Nqf + g) * bd + tid] = src[g * p.nface + face];
   }
   for (int rr = 0; rr < p.n_rows; ++rr) {
     const int r = p.rows[rr];
@@ -516,6 +518,7 @@ cudaError_t launch_elem(Ctx& c) {
   p.rows = c.rows;
   p.elem_face = c.geo.elem_face;
   p.uhat = c.uhat;
+  p.it = c.it;
   p.Gy = c.Gy;
   p.Hy = c.Hy;
   p.Y = c.Y;
@@ -545,10 +548,12 @@ struct FaceParams {
   const double* Y;              // [NQFS][nel]
   const double* gb;             // [Nqf][nface]
   const double* gb_old;
-  double* uhat;                 // [Nqf][nface], updated in place
+  double* uhat;                 // [2][Nqf][nface] ping-pong pair
   double* partials;
   IterState* it;
   double* hist;
+  int graph_mode;               // set the while-node condition from the last block
+  cudaGraphConditionalHandle handle;
 };
 
 constexpr int kFaceBlock = 256;
@@ -558,6 +563,10 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
   __shared__ bool last;
   const int64_t nface = p.geo.nface, nel = p.geo.nel;
   const int64_t total = (int64_t)p.Nqf * nface;
+  // every block reads the counter before the last block advances it
+  const int kk = (p.mode == kFaceIterate) ? p.it->k : 0;
+  const double* uh_old = p.uhat + (int64_t)(kk & 1) * total;
+  double* uh_new = p.uhat + (int64_t)((p.mode == kFaceIterate ? kk + 1 : 0) & 1) * total;
   double acc = 0.0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
@@ -586,10 +595,10 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
       uh = (ep >= 0) ? ym + p.Y[(int64_t)(fpl * p.Nqf + gf) * nel + ep] : 2.0 * ym;
     }
     if (p.mode == kFaceIterate) {
-      const double d = uh - p.uhat[t];
+      const double d = uh - uh_old[t];
       acc += p.geo.face_jf[face] * fweight(p.R, gf) * d * d;
     }
-    p.uhat[t] = uh;
+    uh_new[t] = uh;
   }
   if (p.mode != kFaceIterate) return;
 
@@ -634,11 +643,14 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
     it->cont = cont;
     it->status = status;
     __threadfence();
+    if (p.graph_mode) cudaGraphSetConditional(p.handle, (unsigned int)cont);
   }
 }
 
-cudaError_t launch_face(Ctx& c, int mode) {
+cudaError_t launch_face(Ctx& c, int mode, int graph_mode) {
   FaceParams p;
+  p.graph_mode = graph_mode;
+  p.handle = c.handle;
   p.R = c.ref;
   p.geo = c.geo;
   p.pde = c.pde;
@@ -667,7 +679,8 @@ struct FinalParams {
   int64_t nel, nface;
   int n, NQFS, Nqf, F, shared, cn;
   const int32_t* elem_face;
-  const double* uhat;
+  const double* uhat;           // [2][Nqf][nface]
+  const IterState* it;
   const double* G;
   const double* H;
   double* u;
@@ -684,9 +697,11 @@ __global__ void k_final(const FinalParams p) {
   const int64_t e = blockIdx.x * (int64_t)bd + tid;
   if (e >= p.nel) return;
   const int64_t ne = p.nel;
+  // Algorithm 1 returns u^{k+1}, the local solve with the trace uhat^k
+  const double* src = p.uhat + (int64_t)((p.it->k + 1) & 1) * p.Nqf * p.nface;
   for (int f = 0; f < p.F; ++f) {
     const int64_t face = p.elem_face[f * ne + e];
-    for (int g = 0; g < p.Nqf; ++g) uh[(f * p.Nqf + g) * bd + tid] = p.uhat[g * p.nface + face];
+    for (int g = 0; g < p.Nqf; ++g) uh[(f * p.Nqf + g) * bd + tid] = src[g * p.nface + face];
   }
   for (int r = 0; r < p.n; ++r) {
     double acc = p.G[r * ne + e];
@@ -701,15 +716,16 @@ __global__ void k_final(const FinalParams p) {
   }
 }
 
-__global__ void k_trace_end(int64_t total, int cn, double* uhat, double* uhat_n,
-                            const double* gb, double* gb_old) {
+// The final trace uhat^{K} (slot K&1) becomes the state's trace in slot 0
+// (Crank-Nicolson: 2 vhat - uhat^n) and the previous-level copies are updated.
+__global__ void k_trace_end(int64_t total, int cn, const IterState* it, double* uhat,
+                            double* uhat_n, const double* gb, double* gb_old) {
+  const double* fin = uhat + (int64_t)(it->k & 1) * total;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    double v = uhat[t];
-    if (cn) {
-      v = 2.0 * v - uhat_n[t];
-      uhat[t] = v;
-    }
+    double v = fin[t];
+    if (cn) v = 2.0 * v - uhat_n[t];
+    uhat[t] = v;
     uhat_n[t] = v;
     gb_old[t] = gb[t];
   }
@@ -727,6 +743,7 @@ cudaError_t launch_final(Ctx& c) {
   p.cn = (c.scheme == EHDG_CN) ? 1 : 0;
   p.elem_face = c.geo.elem_face;
   p.uhat = c.uhat;
+  p.it = c.it;
   p.G = c.G;
   p.H = c.H;
   p.u = c.u;
@@ -743,8 +760,8 @@ cudaError_t launch_final(Ctx& c) {
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const int64_t total = (int64_t)c.Nqf * c.nface;
-  k_trace_end<<<(int)((total + 255) / 256), 256, 0, c.stream>>>(total, p.cn, c.uhat, c.uhat_n,
-                                                                  c.gb, c.gb_old);
+  k_trace_end<<<(int)((total + 255) / 256), 256, 0, c.stream>>>(total, p.cn, c.it, c.uhat,
+                                                                  c.uhat_n, c.gb, c.gb_old);
   return cudaGetLastError();
 }
 
@@ -802,6 +819,22 @@ cudaError_t launch_aos_to_soa(const double* src, double* dst, int64_t outer, int
 cudaError_t launch_soa_to_aos(const double* src, double* dst, int64_t outer, int inner,
                               cudaStream_t s) {
   return transpose(src, dst, inner, outer, s);
+}
+
+// Per-step bookkeeping after the end-of-step kernels: iterations and status
+// of step it->step, then advance the step counter.
+__global__ void k_step_end(IterState* it, int* iters, int* status, int cap) {
+  const int s = it->step;
+  if (s >= 0 && s < cap) {
+    iters[s] = it->k;
+    status[s] = it->status;
+  }
+  it->step = s + 1;
+}
+
+cudaError_t launch_step_end(Ctx& c) {
+  k_step_end<<<1, 1, 0, c.stream>>>(c.it, c.step_iters, c.step_status, c.step_cap);
+  return cudaGetLastError();
 }
 
 __global__ void k_reset(IterState* it) {
