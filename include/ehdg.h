@@ -158,6 +158,18 @@ ehdg_status ehdg_get_state(ehdg_ctx ctx, double* u, double* uhat, int on_device)
 /* Residual history r_0, r_1, ... of the last step (host buffer of cap entries). */
 ehdg_status ehdg_get_residual_history(ehdg_ctx ctx, double* buf, int64_t cap, int64_t* n_out);
 
+/* FP64 residual of Algorithm 1's convergence check (Sec. 3, "check
+ * convergence"): out[0] = sqrt(sum_i w[i] (a[i] - b[i])^2) over n entries.
+ * With a, b two trace iterates uhat^{k+1}, uhat^k at the face points and w the
+ * face Gauss weights times the face Jacobian, this is
+ * ||uhat^{k+1} - uhat^k||_{L2(E_h)}. All pointers are device pointers; the
+ * work is ordered on `stream` (a cudaStream_t, NULL = legacy default). The
+ * reduction is deterministic (same inputs give the same bits). Scratch for
+ * the block partial sums is allocated on the stream and released before the
+ * call returns. n = 0 gives 0; n < 0 or a NULL pointer is EHDG_ERR_INVALID. */
+ehdg_status ehdg_trace_residual(const double* a, const double* b, const double* w, int64_t n,
+                                double* out, void* stream);
+
 /* Kernel accounting. Every launch is counted per kind; with profiling on,
  * each launch is also bracketed by CUDA events on the context's stream and
  * ehdg_kernel_stats returns the summed device time of the kind (it

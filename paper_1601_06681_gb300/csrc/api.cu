@@ -325,6 +325,10 @@ ehdg_status run_graph(Ctx& c, int n_steps, int* iters_per_step, double* res) {
 
 }  // namespace
 
+namespace ehdg {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace ehdg
+
 extern "C" {
 
 const char* ehdg_last_error(void) { return g_err.c_str(); }

@@ -150,4 +150,11 @@ cudaError_t launch_step_end(Ctx& c);
 
 enum FaceMode { kFaceInitial = 0, kFaceIterate = 1 };
 
+void set_last_error(const std::string& msg);
+// standalone weighted difference norm (residual.cu)
+cudaError_t launch_wdiff_norm(const double* a, const double* b, const double* w, int64_t n,
+                              double* partials, unsigned int* counter, double* out,
+                              cudaStream_t s);
+int wdiff_norm_blocks(int64_t n);
+
 }  // namespace ehdg

@@ -76,6 +76,8 @@ _SIGS = [
     ("ehdg_set_profiling", C.c_int, [C.c_void_p, C.c_int]),
     ("ehdg_kernel_stats", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64),
                                     C.POINTER(C.c_double)]),
+    ("ehdg_trace_residual", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                      C.c_void_p]),
     ("ehdg_last_error", C.c_char_p, []),
 ]
 
@@ -122,6 +124,21 @@ def _buf(x, shape):
     a = np.ascontiguousarray(x, dtype=np.float64)
     assert a.size == int(np.prod(shape)), (a.shape, shape)
     return a.ctypes.data_as(C.c_void_p), 0, a
+
+
+def _dev_ptr(t):
+    import torch
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    return C.c_void_p(t.data_ptr())
+
+
+def ehdg_trace_residual(a, b, w, out, stream=None):
+    """sqrt(sum w (a - b)^2) of three float64 CUDA tensors into out (1 element)."""
+    n = a.numel()
+    assert b.numel() == n and w.numel() == n and out.numel() >= 1
+    s = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(load().ehdg_trace_residual(_dev_ptr(a), _dev_ptr(b), _dev_ptr(w), n, _dev_ptr(out), s))
+    return out
 
 
 class Mesh:

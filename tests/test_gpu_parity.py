@@ -79,7 +79,7 @@ def make_case(name):
         kw = dict(scheme="be", dt=5e-3, beta_const=np.array([0.3, -1.0, 0.6]))
     elif name == "sw_be":
         mesh, p = W.structured_mesh((12, 11), boundary_tag=W.TAG_WALL), 2
-        kw = dict(pde="sw", scheme="be", dt=1e-2, Phi=1.3)
+        kw = dict(pde="sw", scheme="be", dt=2e-3, Phi=1.3)
     elif name == "sw_be_p3":
         mesh, p = W.structured_mesh((9, 14), boundary_tag=W.TAG_WALL), 3
         kw = dict(pde="sw", scheme="be", dt=1e-3, Phi=1.0)
