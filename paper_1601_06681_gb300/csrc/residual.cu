@@ -87,7 +87,7 @@ int wdiff_norm_blocks(int64_t n) { return resid_blocks(n); }
 extern "C" ehdg_status ehdg_trace_residual(const double* a, const double* b, const double* w,
                                            int64_t n, double* out, void* stream) {
   using namespace ehdg;
-  if (!a || !b || !w || !out || n < 0) {
+  if (!out || n < 0 || (n > 0 && (!a || !b || !w))) {
     set_last_error("ehdg_trace_residual: NULL pointer or negative size");
     return EHDG_ERR_INVALID;
   }
