@@ -166,7 +166,8 @@ ehdg_status ehdg_get_residual_history(ehdg_ctx ctx, double* buf, int64_t cap, in
  * work is ordered on `stream` (a cudaStream_t, NULL = legacy default). The
  * reduction is deterministic (same inputs give the same bits). Scratch for
  * the block partial sums is allocated on the stream and released before the
- * call returns. n = 0 gives 0; n < 0 or a NULL pointer is EHDG_ERR_INVALID. */
+ * call returns. n = 0 gives 0 (a, b and w may then be NULL); n < 0, a NULL
+ * out, or a NULL data pointer with n > 0 is EHDG_ERR_INVALID. */
 ehdg_status ehdg_trace_residual(const double* a, const double* b, const double* w, int64_t n,
                                 double* out, void* stream);
 
