@@ -277,17 +277,20 @@ def run_ours(args):
     e_s = time.perf_counter() - e0
     e2e_value = ws * trace_dof * it_e2e / e_s
 
-    # roofline of the dominant kernel (element sweep)
+    # roofline of the dominant kernel (element sweep): per element and sweep it
+    # reads its computed operator rows (rows x NQFS doubles), Gy (rows), the
+    # trace at its NQFS face points, its face ids and row ids, and writes rows
+    # values; flops = 2 x rows x NQFS
     n_elem_launch, elem_ms = stats["elem"]
     info = solver.info
     nq = 4 * info["Nqf"]
-    bytes_per_elem = 8 * (nq * nq + 3 * nq) + 4 * 4
-    alg_bytes = bytes_per_elem * info["n_elem"]
+    rows = info["sweep_rows"]
+    alg_bytes = 8 * (rows * (nq + 2) + nq * info["n_elem"]) + (4 * 4 + 1) * info["n_elem"] + rows
     avg_ms = elem_ms / max(n_elem_launch, 1)
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     peaks, peak_src = measured_peaks()
     peak = float(peaks.get("hbm_gbs", 6800.0))
-    flops_per_launch = 2.0 * nq * nq * info["n_elem"]
+    flops_per_launch = 2.0 * nq * rows
     launches = sum(v[0] for v in launch_counts.values())
     share = {k: round(v[1] / max(sum(x[1] for x in stats.values()), 1e-12), 4) for k, v in stats.items()}
 

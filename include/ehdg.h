@@ -106,6 +106,8 @@ typedef struct {
   int64_t trace_len;           /* n_face * Nqf */
   int shared_operator;         /* 1 if one local operator serves every element */
   int64_t device_bytes;        /* device memory held by the context */
+  int64_t sweep_rows;          /* face-point rows the element sweep computes, summed over
+                                  elements (upwind/tangential points only for transport) */
 } ehdg_info;
 
 /* Structured N0 x N1 (x N2) mesh of the box [lo, hi] with the numbering

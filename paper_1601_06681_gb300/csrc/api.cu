@@ -718,6 +718,11 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   }
   const size_t state = (size_t)c.n * c.nel, trace = (size_t)c.Nqf * c.nface;
   TRYC(dalloc(c, &c.sgn, trace));
+  if (!c.shared_op) {
+    if (c.NQFS > 255) return cleanup(fail(EHDG_ERR_UNSUPPORTED, "more than 255 face points per element"));
+    TRYC(dalloc(c, &c.rowid, (size_t)c.NQFS * c.nel));
+    TRYC(dalloc(c, &c.nrows, (size_t)c.nel));
+  }
   TRYC(dalloc(c, &c.u, state));
   TRYC(dalloc(c, &c.G, state));
   TRYC(dalloc(c, &c.Gy, (size_t)c.NQFS * c.nel));
@@ -729,8 +734,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   TRYC(dalloc(c, &c.force, state));
   TRYC(dalloc(c, &c.force_old, state));
   TRYC(dalloc(c, &c.staging, std::max(state, trace)));
-  c.n_partials = (int)std::min<int64_t>((trace + 255) / 256, 152 * 8);
-  if (c.n_partials < 1) c.n_partials = 1;
+  c.n_partials = face_grid_x(c.nface, c.Nqf) * c.Nqf;
   TRYC(dalloc(c, &c.partials, (size_t)c.n_partials));
   TRYC(dalloc(c, &c.it, 1));
   TRYC(dalloc(c, &c.hist, (size_t)c.max_iter));
@@ -747,9 +751,18 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   CKC(counted(c, EHDG_KERNEL_ASSEMBLE, 1, [&] { return launch_assemble(c, c.shared_op ? 1 : (int)c.nel); }));
   if (c.pde == EHDG_TRANSPORT)
     CKC(counted(c, EHDG_KERNEL_SIGNS, 1, [&] { return launch_face_signs(c); }));
+  if (!c.shared_op) CKC(counted(c, EHDG_KERNEL_AUX, 2, [&] { return launch_rows(c); }));
   CKC(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
   CKC(cudaStreamSynchronize(c.stream));
   if (c.it_host->status != 0) return cleanup(fail(EHDG_ERR_INVALID, "singular local operator"));
+  if (c.shared_op) {
+    c.sweep_rows = (int64_t)c.n_rows * c.nel;
+  } else {
+    std::vector<uint8_t> nr(c.nel);
+    CKC(cudaMemcpy(nr.data(), c.nrows, c.nel, cudaMemcpyDeviceToHost));
+    c.sweep_rows = 0;
+    for (uint8_t v : nr) c.sweep_rows += v;
+  }
   *out = h;
   return EHDG_OK;
 }
@@ -769,6 +782,7 @@ ehdg_status ehdg_get_info(ehdg_ctx h, ehdg_info* out) {
   out->trace_len = (int64_t)c.Nqf * c.nface;
   out->shared_operator = c.shared_op ? 1 : 0;
   out->device_bytes = c.bytes;
+  out->sweep_rows = c.sweep_rows;
   return EHDG_OK;
 }
 

@@ -91,8 +91,11 @@ struct Ctx {
   int* ey_idx = nullptr;         // [NQFS][KE]
   double* ey_val = nullptr;      // [NQFS][KE]
   int8_t* sgn = nullptr;         // [Nqf][nface] sgn(beta.n^-) (transport)
-  int* rows = nullptr;           // element output rows (face points) to compute
+  int* rows = nullptr;           // shared operator: element output rows (face points)
   int n_rows = 0;
+  uint8_t* rowid = nullptr;      // per-element operator: [NQFS][nel] row of each slot
+  uint8_t* nrows = nullptr;      // [nel] slots in use
+  int64_t sweep_rows = 0;        // rows computed per sweep, all elements
   double* u = nullptr;           // [n][nel] state u^n (SoA)
   double* G = nullptr;           // [n][nel]
   double* Gy = nullptr;          // [NQFS][nel]
@@ -147,6 +150,8 @@ cudaError_t launch_soa_to_aos(const double* src, double* dst, int64_t outer, int
 cudaError_t launch_reset_iter(Ctx& c);
 cudaError_t launch_extract(Ctx& c);
 cudaError_t launch_step_end(Ctx& c);
+cudaError_t launch_rows(Ctx& c);
+int face_grid_x(int64_t nface, int Nqf);   // blocks along faces of the trace kernel
 
 enum FaceMode { kFaceInitial = 0, kFaceIterate = 1 };
 

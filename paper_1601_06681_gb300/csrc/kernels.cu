@@ -382,8 +382,12 @@ struct StepParams {
   const double* force_old;
   const int* ey_idx;
   const double* ey_val;
+  const int* rows;              // shared operator: output rows of every element
+  int n_rows;
+  const uint8_t* rowid;         // per-element operator: [NQFS][nel] row of each slot
+  const uint8_t* nrows;         // [nel] slots in use
   double* G;
-  double* Gy;
+  double* Gy;                   // [slot][nel], slot order of the element sweep
   double* Y;
 };
 
@@ -416,16 +420,20 @@ __global__ void k_step(const StepParams s) {
     g[r * bd + tid] = acc;
     s.G[r * ne + e] = acc;
   }
+  // initial-trace input: element values at every face point
   for (int r = 0; r < s.NQFS; ++r) {
-    double gy = 0.0, y0 = 0.0;
-    for (int k = 0; k < s.KE; ++k) {
-      const double ev = s.ey_val[r * s.KE + k];
-      const int ix = s.ey_idx[r * s.KE + k];
-      gy += ev * g[ix * bd + tid];
-      y0 += ev * s.u[ix * ne + e];
-    }
-    s.Gy[r * ne + e] = gy;
+    double y0 = 0.0;
+    for (int k = 0; k < s.KE; ++k)
+      y0 += s.ey_val[r * s.KE + k] * s.u[s.ey_idx[r * s.KE + k] * ne + e];
     s.Y[r * ne + e] = y0;
+  }
+  // Gy in the sweep's slot order (only the rows the sweep computes)
+  const int nr = s.shared ? s.n_rows : s.nrows[e];
+  for (int j = 0; j < nr; ++j) {
+    const int r = s.shared ? s.rows[j] : s.rowid[j * ne + e];
+    double gy = 0.0;
+    for (int k = 0; k < s.KE; ++k) gy += s.ey_val[r * s.KE + k] * g[s.ey_idx[r * s.KE + k] * bd + tid];
+    s.Gy[j * ne + e] = gy;
   }
 }
 
@@ -445,6 +453,10 @@ cudaError_t launch_step(Ctx& c) {
   s.force_old = c.force_old;
   s.ey_idx = c.ey_idx;
   s.ey_val = c.ey_val;
+  s.rows = c.rows;
+  s.n_rows = c.n_rows;
+  s.rowid = c.rowid;
+  s.nrows = c.nrows;
   s.G = c.G;
   s.Gy = c.Gy;
   s.Y = c.Y;
@@ -463,47 +475,85 @@ cudaError_t launch_step(Ctx& c) {
 
 // ===========================================================================
 // Element sweep (eq. transportLocalk1 / localSolverDD): Y = Gy + Hy uhat
+//
+// Block = 32 consecutive elements (threadIdx.x) x kElemT row groups
+// (threadIdx.y): a warp reads one slot of 32 consecutive elements, i.e. a
+// contiguous 256-byte segment of the [slot][col][elem] operator. Only the
+// face-point rows the trace formula will read are computed: for a constant
+// velocity the upwind/tangential faces (a list shared by all elements), for a
+// per-node velocity each element's own compacted list (rowid/nrows).
 // ===========================================================================
+constexpr int kElemT = 4;
+
 struct ElemParams {
   int64_t nel, nface;
   int NQFS, Nqf, F, shared, n_rows;
-  const int* rows;              // output rows (face points) to compute
+  const int* rows;              // shared operator: output rows
+  const uint8_t* rowid;         // per-element operator: [slot][nel] row of a slot
+  const uint8_t* nrows;         // [nel]
   const int32_t* elem_face;     // [F][nel]
   const double* uhat;           // [2][Nqf][nface] ping-pong pair, iteration k reads slot k&1
   const IterState* it;
-  const double* Gy;             // [NQFS][nel]
-  const double* Hy;             // [NQFS][NQFS][ne]
+  const double* Gy;             // [slot][nel]
+  const double* Hy;             // shared: [NQFS][NQFS]; per element: [slot][NQFS][nel]
   double* Y;                    // [NQFS][nel]
 };
 
-__global__ void k_elem(const ElemParams p) {
+template <int NQ>
+__global__ void __launch_bounds__(32 * kElemT) k_elem(const ElemParams p) {
   extern __shared__ double sm[];
-  const int bd = blockDim.x, tid = threadIdx.x;
+  const int nq = NQ > 0 ? NQ : p.NQFS;
+  const int lane = threadIdx.x, t = threadIdx.y;
   double* Hsh = sm;
-  double* uh = sm + (p.shared ? p.NQFS * p.NQFS : 0);   // [NQFS][bd]
+  double* uh = sm + (p.shared ? nq * nq : 0);          // [nq][32]
   if (p.shared)
-    for (int t = tid; t < p.NQFS * p.NQFS; t += bd) Hsh[t] = p.Hy[t];
-  __syncthreads();
-  const int64_t e = blockIdx.x * (int64_t)bd + tid;
-  if (e >= p.nel) return;
+    for (int i = t * 32 + lane; i < nq * nq; i += 32 * kElemT) Hsh[i] = p.Hy[i];
   const int64_t ne = p.nel;
+  const int64_t e = blockIdx.x * 32LL + lane;
   const double* src = p.uhat + (int64_t)(p.it->k & 1) * p.Nqf * p.nface;
-  for (int f = 0; f < p.F; ++f) {
-    const int64_t face = p.elem_face[f * ne + e];
-    for (int g = 0; g < p.Nqf; ++g) uh[(f * p.Nqf + g) * bd + tid] = src[g * p.nface + face];
-  }
-  for (int rr = 0; rr < p.n_rows; ++rr) {
-    const int r = p.rows[rr];
-    double acc = p.Gy[r * ne + e];
-    if (p.shared) {
-      const double* Hr = Hsh + r * p.NQFS;
-      for (int t = 0; t < p.NQFS; ++t) acc += Hr[t] * uh[t * bd + tid];
-    } else {
-      const double* Hr = p.Hy + (int64_t)r * p.NQFS * ne + e;
-      for (int t = 0; t < p.NQFS; ++t) acc += Hr[t * ne] * uh[t * bd + tid];
+  if (e < ne) {
+    for (int i = t; i < nq; i += kElemT) {
+      const int f = i / p.Nqf, g = i - f * p.Nqf;
+      const int64_t face = p.elem_face[f * ne + e];
+      uh[i * 32 + lane] = src[g * p.nface + face];
     }
-    p.Y[r * ne + e] = acc;
   }
+  __syncthreads();
+  if (e >= ne) return;
+  const int nr = p.shared ? p.n_rows : p.nrows[e];
+  for (int j = t; j < nr; j += kElemT) {
+    double acc = p.Gy[j * ne + e];
+    int r;
+    if (p.shared) {
+      r = p.rows[j];
+      const double* Hr = Hsh + r * nq;
+      if constexpr (NQ > 0) {
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) acc += Hr[c] * uh[c * 32 + lane];
+      } else {
+        for (int c = 0; c < nq; ++c) acc += Hr[c] * uh[c * 32 + lane];
+      }
+    } else {
+      r = p.rowid[j * ne + e];
+      const double* Hr = p.Hy + (int64_t)j * nq * ne + e;
+      if constexpr (NQ > 0) {
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) acc += Hr[c * ne] * uh[c * 32 + lane];
+      } else {
+        for (int c = 0; c < nq; ++c) acc += Hr[c * ne] * uh[c * 32 + lane];
+      }
+    }
+    p.Y[(int64_t)r * ne + e] = acc;
+  }
+}
+
+template <int NQ>
+static cudaError_t launch_elem_t(const ElemParams& p, size_t smem, int grid, cudaStream_t s) {
+  cudaError_t err = cudaFuncSetAttribute(k_elem<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+  if (err != cudaSuccess) return err;
+  k_elem<NQ><<<grid, dim3(32, kElemT), smem, s>>>(p);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_elem(Ctx& c) {
@@ -516,22 +566,77 @@ cudaError_t launch_elem(Ctx& c) {
   p.shared = c.shared_op ? 1 : 0;
   p.n_rows = c.n_rows;
   p.rows = c.rows;
+  p.rowid = c.rowid;
+  p.nrows = c.nrows;
   p.elem_face = c.geo.elem_face;
   p.uhat = c.uhat;
   p.it = c.it;
   p.Gy = c.Gy;
   p.Hy = c.Hy;
   p.Y = c.Y;
-  int bd = 128;
-  size_t smem = sizeof(double) * ((p.shared ? (size_t)c.NQFS * c.NQFS : 0) + (size_t)c.NQFS * bd);
-  while (smem > 200 * 1024 && bd > 32) {
-    bd /= 2;
-    smem = sizeof(double) * ((p.shared ? (size_t)c.NQFS * c.NQFS : 0) + (size_t)c.NQFS * bd);
+  const size_t smem = sizeof(double) * ((p.shared ? (size_t)c.NQFS * c.NQFS : 0) + (size_t)c.NQFS * 32);
+  const int grid = (int)((c.nel + 31) / 32);
+  switch (c.NQFS) {
+    case 8: return launch_elem_t<8>(p, smem, grid, c.stream);
+    case 12: return launch_elem_t<12>(p, smem, grid, c.stream);
+    case 16: return launch_elem_t<16>(p, smem, grid, c.stream);
+    case 20: return launch_elem_t<20>(p, smem, grid, c.stream);
+    case 24: return launch_elem_t<24>(p, smem, grid, c.stream);
+    case 28: return launch_elem_t<28>(p, smem, grid, c.stream);
+    case 36: return launch_elem_t<36>(p, smem, grid, c.stream);
+    case 40: return launch_elem_t<40>(p, smem, grid, c.stream);
+    case 54: return launch_elem_t<54>(p, smem, grid, c.stream);
+    case 96: return launch_elem_t<96>(p, smem, grid, c.stream);
+    default: return launch_elem_t<0>(p, smem, grid, c.stream);
   }
-  cudaError_t err = cudaFuncSetAttribute(k_elem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  const int grid = (int)((c.nel + bd - 1) / bd);
-  k_elem<<<grid, bd, smem, c.stream>>>(p);
+}
+
+// Per-element operator: the rows each element's sweep must produce (the face
+// points where it is the upwind or tangential side, from the same sgn array
+// the trace kernel uses; every point for shallow water), compacted into slots.
+__global__ void k_rows(int64_t nel, int NQFS, int Nqf, int F, int transport,
+                       const int32_t* elem_face, const int32_t* face_elem, int64_t nface,
+                       const int8_t* sgn, uint8_t* rowid, uint8_t* nrows) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nel) return;
+  int j = 0;
+  for (int s = 0; s < NQFS; ++s) {
+    bool need = true;
+    if (transport) {
+      const int f = s / Nqf, g = s - f * Nqf;
+      const int64_t face = elem_face[f * nel + e];
+      const bool minus = face_elem[face] == (int32_t)e;
+      const int sg = sgn[g * nface + face];
+      need = minus ? (sg >= 0) : (sg <= 0);
+    }
+    if (need) rowid[(int64_t)(j++) * nel + e] = (uint8_t)s;
+  }
+  nrows[e] = (uint8_t)j;
+}
+
+// Move each element's needed rows of Hy to the front (slot order), in place:
+// slot j takes row rowid[j] >= j, and no later slot reads a row below it.
+__global__ void k_compact_hy(int64_t nel, int NQFS, const uint8_t* rowid, const uint8_t* nrows,
+                             double* Hy) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= nel) return;
+  const int nr = nrows[e];
+  for (int j = 0; j < nr; ++j) {
+    const int r = rowid[(int64_t)j * nel + e];
+    if (r == j) continue;
+    for (int c = 0; c < NQFS; ++c)
+      Hy[((int64_t)j * NQFS + c) * nel + e] = Hy[((int64_t)r * NQFS + c) * nel + e];
+  }
+}
+
+cudaError_t launch_rows(Ctx& c) {
+  const int grid = (int)((c.nel + 255) / 256);
+  k_rows<<<grid, 256, 0, c.stream>>>(c.nel, c.NQFS, c.Nqf, c.F, c.pde == EHDG_TRANSPORT ? 1 : 0,
+                                     c.geo.elem_face, c.geo.face_elem, c.nface, c.sgn, c.rowid,
+                                     c.nrows);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_compact_hy<<<grid, 256, 0, c.stream>>>(c.nel, c.NQFS, c.rowid, c.nrows, c.Hy);
   return cudaGetLastError();
 }
 
@@ -539,11 +644,11 @@ cudaError_t launch_elem(Ctx& c) {
 // Face trace update (eq. transportLocale; shallow-water trace) + residual
 // ===========================================================================
 struct FaceParams {
-  RefTables R;
   Geometry geo;
   int pde, mode, cn, Nqf;
   double tol, res_scale;
   int max_iter;
+  double fw[kMaxQ * kMaxQ];     // face Gauss weight of each face point (tangential product)
   const int8_t* sgn;
   const double* Y;              // [NQFS][nel]
   const double* gb;             // [Nqf][nface]
@@ -557,52 +662,62 @@ struct FaceParams {
 };
 
 constexpr int kFaceBlock = 256;
+constexpr int kFaceMaxBlocks = 2432;   // 16 per SM
 
+// Grid: x strides over faces, y = face point. Block partials are reduced in a
+// fixed order by the last block to finish (deterministic).
 __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
   __shared__ double red[kFaceBlock / 32];
   __shared__ bool last;
   const int64_t nface = p.geo.nface, nel = p.geo.nel;
   const int64_t total = (int64_t)p.Nqf * nface;
+  const int gf = blockIdx.y;
   // every block reads the counter before the last block advances it
   const int kk = (p.mode == kFaceIterate) ? p.it->k : 0;
-  const double* uh_old = p.uhat + (int64_t)(kk & 1) * total;
-  double* uh_new = p.uhat + (int64_t)((p.mode == kFaceIterate ? kk + 1 : 0) & 1) * total;
+  const double* uh_old = p.uhat + (int64_t)(kk & 1) * total + (int64_t)gf * nface;
+  double* uh_new = p.uhat + (int64_t)((p.mode == kFaceIterate ? kk + 1 : 0) & 1) * total +
+                   (int64_t)gf * nface;
+  const int8_t* sgn = p.sgn + (int64_t)gf * nface;
+  const double* gb = p.gb + (int64_t)gf * nface;
+  const double* gbo = p.gb_old + (int64_t)gf * nface;
+  const double wg = p.fw[gf];
+  const int64_t ym_off = (int64_t)gf * nel;   // + (local face * Nqf) * nel + elem
   double acc = 0.0;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int gf = (int)(t / nface);
-    const int64_t face = t - (int64_t)gf * nface;
+  for (int64_t face = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; face < nface;
+       face += (int64_t)gridDim.x * blockDim.x) {
     const int em = p.geo.face_elem[face];
     const int ep = p.geo.face_elem[nface + face];
     const int fm = p.geo.face_local[face];
     const int fpl = p.geo.face_local[nface + face];
     double uh;
     if (p.pde == EHDG_TRANSPORT) {
-      const int s = p.sgn[t];
+      const int s = sgn[face];
       double ext = 0.0;
-      if (ep < 0) ext = p.cn ? 0.5 * (p.gb[t] + p.gb_old[t]) : p.gb[t];
+      if (ep < 0) ext = p.cn ? 0.5 * (gb[face] + gbo[face]) : gb[face];
       if (s > 0) {
-        uh = p.Y[(int64_t)(fm * p.Nqf + gf) * nel + em];
+        uh = p.Y[ym_off + (int64_t)fm * p.Nqf * nel + em];
       } else if (s < 0) {
-        uh = (ep >= 0) ? p.Y[(int64_t)(fpl * p.Nqf + gf) * nel + ep] : ext;
+        uh = (ep >= 0) ? p.Y[ym_off + (int64_t)fpl * p.Nqf * nel + ep] : ext;
       } else {
-        const double ym = p.Y[(int64_t)(fm * p.Nqf + gf) * nel + em];
-        const double yp = (ep >= 0) ? p.Y[(int64_t)(fpl * p.Nqf + gf) * nel + ep] : ext;
+        const double ym = p.Y[ym_off + (int64_t)fm * p.Nqf * nel + em];
+        const double yp = (ep >= 0) ? p.Y[ym_off + (int64_t)fpl * p.Nqf * nel + ep] : ext;
         uh = 0.5 * (ym + yp);
       }
     } else {
-      const double ym = p.Y[(int64_t)(fm * p.Nqf + gf) * nel + em];
-      uh = (ep >= 0) ? ym + p.Y[(int64_t)(fpl * p.Nqf + gf) * nel + ep] : 2.0 * ym;
+      const double ym = p.Y[ym_off + (int64_t)fm * p.Nqf * nel + em];
+      uh = (ep >= 0) ? ym + p.Y[ym_off + (int64_t)fpl * p.Nqf * nel + ep] : 2.0 * ym;
     }
     if (p.mode == kFaceIterate) {
-      const double d = uh - uh_old[t];
-      acc += p.geo.face_jf[face] * fweight(p.R, gf) * d * d;
+      const double d = uh - uh_old[face];
+      acc += p.geo.face_jf[face] * wg * d * d;
     }
-    uh_new[t] = uh;
+    uh_new[face] = uh;
   }
   if (p.mode != kFaceIterate) return;
 
   // deterministic reduction: warp -> block -> partials[block] -> last block
+  const unsigned int nblocks = gridDim.x * gridDim.y;
+  const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
   acc = warp_sum(acc);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = acc;
@@ -611,17 +726,17 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
     double v = (lane < (int)(blockDim.x >> 5)) ? red[lane] : 0.0;
     v = warp_sum(v);
     if (lane == 0) {
-      p.partials[blockIdx.x] = v;
+      p.partials[bid] = v;
       __threadfence();
       const unsigned int ticket = atomicAdd(&p.it->counter, 1u);
-      last = (ticket == gridDim.x - 1);
+      last = (ticket == nblocks - 1);
     }
   }
   __syncthreads();
   if (!last) return;
   __threadfence();
   double v = 0.0;
-  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+  for (unsigned int i = threadIdx.x; i < nblocks; i += blockDim.x)
     v += reinterpret_cast<volatile double*>(p.partials)[i];
   v = warp_sum(v);
   if (lane == 0) red[wid] = v;
@@ -647,11 +762,18 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
   }
 }
 
+int face_grid_x(int64_t nface, int Nqf) {
+  int64_t gx = (nface + kFaceBlock - 1) / kFaceBlock;
+  int64_t cap = kFaceMaxBlocks / Nqf;
+  if (cap < 1) cap = 1;
+  if (gx > cap) gx = cap;
+  return gx < 1 ? 1 : (int)gx;
+}
+
 cudaError_t launch_face(Ctx& c, int mode, int graph_mode) {
   FaceParams p;
   p.graph_mode = graph_mode;
   p.handle = c.handle;
-  p.R = c.ref;
   p.geo = c.geo;
   p.pde = c.pde;
   p.mode = mode;
@@ -660,6 +782,15 @@ cudaError_t launch_face(Ctx& c, int mode, int graph_mode) {
   p.tol = c.tol;
   p.res_scale = c.res_scale;
   p.max_iter = c.max_iter;
+  for (int g = 0; g < c.Nqf; ++g) {
+    double w = 1.0;
+    int rem = g;
+    for (int t = 0; t < c.dim - 1; ++t) {
+      w *= c.r1d.om[rem % c.q];
+      rem /= c.q;
+    }
+    p.fw[g] = w;
+  }
   p.sgn = c.sgn;
   p.Y = c.Y;
   p.gb = c.gb;
@@ -668,7 +799,8 @@ cudaError_t launch_face(Ctx& c, int mode, int graph_mode) {
   p.partials = c.partials;
   p.it = c.it;
   p.hist = c.hist;
-  k_face<<<c.n_partials, kFaceBlock, 0, c.stream>>>(p);
+  const dim3 grid(face_grid_x(c.nface, c.Nqf), c.Nqf);
+  k_face<<<grid, kFaceBlock, 0, c.stream>>>(p);
   return cudaGetLastError();
 }
 

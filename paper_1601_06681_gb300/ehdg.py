@@ -48,7 +48,8 @@ class Info(C.Structure):
     _fields_ = [("dim", C.c_int), ("p", C.c_int), ("nf", C.c_int), ("Np", C.c_int),
                 ("q", C.c_int), ("Nqf", C.c_int), ("n_elem", C.c_int64), ("n_face", C.c_int64),
                 ("state_len", C.c_int64), ("trace_len", C.c_int64),
-                ("shared_operator", C.c_int), ("device_bytes", C.c_int64)]
+                ("shared_operator", C.c_int), ("device_bytes", C.c_int64),
+                ("sweep_rows", C.c_int64)]
 
 
 _lib = None
