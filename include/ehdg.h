@@ -173,6 +173,25 @@ ehdg_status ehdg_get_residual_history(ehdg_ctx ctx, double* buf, int64_t cap, in
 ehdg_status ehdg_trace_residual(const double* a, const double* b, const double* w, int64_t n,
                                 double* out, void* stream);
 
+/* Allocation-free variant of ehdg_trace_residual. The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory,
+ * such as code running under a host application's memory manager that owns
+ * every device allocation, or code in latency-critical loops where
+ * cudaMalloc/cudaFree would synchronise the device. It computes the same
+ * out[0] = sqrt(sum_i w[i] (a[i] - b[i])^2) with the same kernel, but the block
+ * partial sums live in a fixed device array inside the library (8 KB plus a
+ * ticket word, 256-byte aligned), which every GPU that loads the library holds
+ * until the process exits. It calls no cudaMalloc, cudaFree or other
+ * allocating routine. n may be at most EHDG_NOALLOC_MAX_N; larger n returns
+ * EHDG_ERR_UNSUPPORTED with a message. The first call on a device looks up the
+ * array's device address (once per device, with that device current), so make
+ * that first call before any stream capture. All calls share the one array:
+ * calls that overlap on the GPU (different streams, or concurrent host threads
+ * on one device) race and may return wrong results; order them on one stream. */
+#define EHDG_NOALLOC_MAX_N 16777216LL
+ehdg_status ehdg_trace_residual_noalloc(const double* a, const double* b, const double* w,
+                                        int64_t n, double* out, void* stream);
+
 /* Kernel accounting. Every launch is counted per kind; with profiling on,
  * each launch is also bracketed by CUDA events on the context's stream and
  * ehdg_kernel_stats returns the summed device time of the kind (it

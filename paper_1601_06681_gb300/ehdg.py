@@ -79,8 +79,12 @@ _SIGS = [
                                     C.POINTER(C.c_double)]),
     ("ehdg_trace_residual", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                       C.c_void_p]),
+    ("ehdg_trace_residual_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
+                                              C.c_void_p, C.c_void_p]),
     ("ehdg_last_error", C.c_char_p, []),
 ]
+
+EHDG_NOALLOC_MAX_N = 16777216
 
 KERNEL_KINDS = ["assemble", "signs", "step", "elem", "face", "final", "aux"]
 
@@ -139,6 +143,17 @@ def ehdg_trace_residual(a, b, w, out, stream=None):
     assert b.numel() == n and w.numel() == n and out.numel() >= 1
     s = None if stream is None else C.c_void_p(stream.cuda_stream)
     _check(load().ehdg_trace_residual(_dev_ptr(a), _dev_ptr(b), _dev_ptr(w), n, _dev_ptr(out), s))
+    return out
+
+
+def ehdg_trace_residual_noalloc(a, b, w, out, stream=None):
+    """As ehdg_trace_residual, with the scratch in the library's fixed device
+    array (no allocation; calls must not overlap on the GPU)."""
+    n = a.numel()
+    assert b.numel() == n and w.numel() == n and out.numel() >= 1
+    s = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(load().ehdg_trace_residual_noalloc(_dev_ptr(a), _dev_ptr(b), _dev_ptr(w), n,
+                                              _dev_ptr(out), s))
     return out
 
 
