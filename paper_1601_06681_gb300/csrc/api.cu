@@ -171,8 +171,14 @@ ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
   const int n_it = fixed_iters > 0 ? fixed_iters : c.max_iter;
   int done = 0;
   for (int k = 0; k < n_it; ++k) {
-    CK(counted(c, EHDG_KERNEL_ELEM, 1, [&] { return launch_elem(c); }));
-    CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceIterate); }));
+    if (c.pde == EHDG_TRANSPORT) {
+      // element solve + trace formula + residual in one kernel (+ tangential points)
+      CK(counted(c, EHDG_KERNEL_ELEM, 1, [&] { return launch_sweep_fused(c, 0); }));
+      if (c.n_tan > 0) c.launches[EHDG_KERNEL_FACE] += 1;
+    } else {
+      CK(counted(c, EHDG_KERNEL_ELEM, 1, [&] { return launch_elem(c); }));
+      CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceIterate); }));
+    }
     ++done;
     if (fixed_iters <= 0) {
       CK(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
@@ -258,8 +264,14 @@ ehdg_status build_graph(Ctx& c) {
                                       cudaStreamCaptureModeRelaxed);
   if (err != cudaSuccess) return abort_capture(err, "cudaStreamBeginCaptureToGraph");
   c.stream = c.body_stream;
-  cudaError_t e1 = launch_elem(c);
-  cudaError_t e2 = (e1 == cudaSuccess) ? launch_face(c, kFaceIterate, 1) : e1;
+  cudaError_t e1, e2;
+  if (c.pde == EHDG_TRANSPORT) {
+    e1 = cudaSuccess;
+    e2 = launch_sweep_fused(c, 1);
+  } else {
+    e1 = launch_elem(c);
+    e2 = (e1 == cudaSuccess) ? launch_face(c, kFaceIterate, 1) : e1;
+  }
   cudaError_t e3 = cudaStreamEndCapture(c.body_stream, &body);
   c.stream = c.cap_stream;
   if (e2 != cudaSuccess) return abort_capture(e2, "capture loop body");
@@ -315,7 +327,8 @@ ehdg_status run_graph(Ctx& c, int n_steps, int* iters_per_step, double* res) {
     if (first == EHDG_OK && c.step_status_h[s] != EHDG_OK) first = (ehdg_status)c.step_status_h[s];
   }
   c.launches[EHDG_KERNEL_ELEM] += sweeps;
-  c.launches[EHDG_KERNEL_FACE] += sweeps + n_steps;
+  c.launches[EHDG_KERNEL_FACE] +=
+      n_steps + ((c.pde == EHDG_TRANSPORT) ? (c.n_tan > 0 ? sweeps : 0) : sweeps);
   c.last_iters = n_steps > 0 ? std::min(c.step_iters_h[n_steps - 1], c.max_iter) : 0;
   if (res) *res = c.it_host->r_last;
   if (first == EHDG_ERR_NOT_CONVERGED) return fail(first, "eHDG did not reach the tolerance in max_iter iterations");
@@ -609,16 +622,23 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
       eyv[s * c.KE + k] = ey[s][k].second;
     }
   // rows each element must produce: for a constant velocity only the faces
-  // where it is upwind or tangential (eq. transportLocale selects those)
+  // where it is upwind (first) or tangential (eq. transportLocale reads those)
   std::vector<int> rows;
-  for (int s = 0; s < c.NQFS; ++s) {
-    const int f = s / c.Nqf, ax = f >> 1;
-    if (c.pde == EHDG_TRANSPORT && !variable) {
-      const double bn = ((f & 1) ? 1.0 : -1.0) * c.beta_const[ax];
-      if (bn < 0.0) continue;
+  int n_up = 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int s = 0; s < c.NQFS; ++s) {
+      const int f = s / c.Nqf, ax = f >> 1;
+      if (c.pde == EHDG_TRANSPORT && !variable) {
+        const double bn = ((f & 1) ? 1.0 : -1.0) * c.beta_const[ax];
+        if (pass == 0 ? !(bn > 0.0) : !(bn == 0.0)) continue;
+      } else if (pass == 1) {
+        continue;
+      }
+      rows.push_back(s);
     }
-    rows.push_back(s);
+    if (pass == 0) n_up = (int)rows.size();
   }
+  c.n_up = n_up;
   c.n_rows = (int)rows.size();
 
   // shared memory needed by the assembly kernel
@@ -722,6 +742,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
     if (c.NQFS > 255) return cleanup(fail(EHDG_ERR_UNSUPPORTED, "more than 255 face points per element"));
     TRYC(dalloc(c, &c.rowid, (size_t)c.NQFS * c.nel));
     TRYC(dalloc(c, &c.nrows, (size_t)c.nel));
+    TRYC(dalloc(c, &c.nup, (size_t)c.nel));
   }
   TRYC(dalloc(c, &c.u, state));
   TRYC(dalloc(c, &c.G, state));
@@ -734,7 +755,8 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   TRYC(dalloc(c, &c.force, state));
   TRYC(dalloc(c, &c.force_old, state));
   TRYC(dalloc(c, &c.staging, std::max(state, trace)));
-  c.n_partials = face_grid_x(c.nface, c.Nqf) * c.Nqf;
+  c.n_partials = std::max(face_grid_x(c.nface, c.Nqf) * c.Nqf,
+                          fused_grid(c.nel) + tangent_grid((int64_t)trace));
   TRYC(dalloc(c, &c.partials, (size_t)c.n_partials));
   TRYC(dalloc(c, &c.it, 1));
   TRYC(dalloc(c, &c.hist, (size_t)c.max_iter));
@@ -755,6 +777,25 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   CKC(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
   CKC(cudaStreamSynchronize(c.stream));
   if (c.it_host->status != 0) return cleanup(fail(EHDG_ERR_INVALID, "singular local operator"));
+  if (c.pde == EHDG_TRANSPORT) {
+    // face points with beta.n = 0 (average of both sides), finished after the sweep
+    std::vector<int8_t> sg((size_t)trace);
+    CKC(cudaMemcpy(sg.data(), c.sgn, trace, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> tg, tf;
+    for (int g = 0; g < c.Nqf; ++g)
+      for (int64_t f = 0; f < c.nface; ++f)
+        if (sg[(size_t)g * c.nface + f] == 0) {
+          tg.push_back(g);
+          tf.push_back((int32_t)f);
+        }
+    c.n_tan = (int64_t)tg.size();
+    if (c.n_tan > 0) {
+      TRYC(dalloc(c, &c.tan_g, tg.size()));
+      TRYC(dalloc(c, &c.tan_face, tf.size()));
+      CKC(cudaMemcpy(c.tan_g, tg.data(), sizeof(int32_t) * tg.size(), cudaMemcpyHostToDevice));
+      CKC(cudaMemcpy(c.tan_face, tf.data(), sizeof(int32_t) * tf.size(), cudaMemcpyHostToDevice));
+    }
+  }
   if (c.shared_op) {
     c.sweep_rows = (int64_t)c.n_rows * c.nel;
   } else {

@@ -95,6 +95,11 @@ struct Ctx {
   int n_rows = 0;
   uint8_t* rowid = nullptr;      // per-element operator: [NQFS][nel] row of each slot
   uint8_t* nrows = nullptr;      // [nel] slots in use
+  uint8_t* nup = nullptr;        // [nel] leading slots that are upwind points (transport)
+  int n_up = 0;                  // shared operator: leading upwind rows
+  int32_t* tan_g = nullptr;      // face points with beta.n = 0: point index
+  int32_t* tan_face = nullptr;   //   and face
+  int64_t n_tan = 0;
   int64_t sweep_rows = 0;        // rows computed per sweep, all elements
   double* u = nullptr;           // [n][nel] state u^n (SoA)
   double* G = nullptr;           // [n][nel]
@@ -152,6 +157,10 @@ cudaError_t launch_extract(Ctx& c);
 cudaError_t launch_step_end(Ctx& c);
 cudaError_t launch_rows(Ctx& c);
 int face_grid_x(int64_t nface, int Nqf);   // blocks along faces of the trace kernel
+// fused transport sweep (sweep_fused.cu)
+cudaError_t launch_sweep_fused(Ctx& c, int graph_mode);
+int fused_grid(int64_t nel);
+int tangent_grid(int64_t n_tan);
 
 enum FaceMode { kFaceInitial = 0, kFaceIterate = 1 };
 

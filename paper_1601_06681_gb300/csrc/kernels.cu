@@ -596,20 +596,25 @@ cudaError_t launch_elem(Ctx& c) {
 // the trace kernel uses; every point for shallow water), compacted into slots.
 __global__ void k_rows(int64_t nel, int NQFS, int Nqf, int F, int transport,
                        const int32_t* elem_face, const int32_t* face_elem, int64_t nface,
-                       const int8_t* sgn, uint8_t* rowid, uint8_t* nrows) {
+                       const int8_t* sgn, uint8_t* rowid, uint8_t* nrows, uint8_t* nup) {
   const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= nel) return;
   int j = 0;
-  for (int s = 0; s < NQFS; ++s) {
-    bool need = true;
-    if (transport) {
-      const int f = s / Nqf, g = s - f * Nqf;
-      const int64_t face = elem_face[f * nel + e];
-      const bool minus = face_elem[face] == (int32_t)e;
-      const int sg = sgn[g * nface + face];
-      need = minus ? (sg >= 0) : (sg <= 0);
+  // pass 0: strictly upwind points (this element owns them); pass 1: beta.n = 0
+  for (int pass = 0; pass < (transport ? 2 : 1); ++pass) {
+    for (int s = 0; s < NQFS; ++s) {
+      bool need = true;
+      if (transport) {
+        const int f = s / Nqf, g = s - f * Nqf;
+        const int64_t face = elem_face[f * nel + e];
+        const bool minus = face_elem[face] == (int32_t)e;
+        const int sg = sgn[g * nface + face];
+        const int own = minus ? sg : -sg;          // sgn(beta.n) seen from this element
+        need = (pass == 0) ? (own > 0) : (own == 0);
+      }
+      if (need) rowid[(int64_t)(j++) * nel + e] = (uint8_t)s;
     }
-    if (need) rowid[(int64_t)(j++) * nel + e] = (uint8_t)s;
+    if (pass == 0) nup[e] = (uint8_t)j;
   }
   nrows[e] = (uint8_t)j;
 }
@@ -633,7 +638,7 @@ cudaError_t launch_rows(Ctx& c) {
   const int grid = (int)((c.nel + 255) / 256);
   k_rows<<<grid, 256, 0, c.stream>>>(c.nel, c.NQFS, c.Nqf, c.F, c.pde == EHDG_TRANSPORT ? 1 : 0,
                                      c.geo.elem_face, c.geo.face_elem, c.nface, c.sgn, c.rowid,
-                                     c.nrows);
+                                     c.nrows, c.nup);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_compact_hy<<<grid, 256, 0, c.stream>>>(c.nel, c.NQFS, c.rowid, c.nrows, c.Hy);
@@ -710,6 +715,8 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
     if (p.mode == kFaceIterate) {
       const double d = uh - uh_old[face];
       acc += p.geo.face_jf[face] * wg * d * d;
+    } else {
+      uh_new[total + face] = uh;     // both slots: points no sweep rewrites keep this value
     }
     uh_new[face] = uh;
   }

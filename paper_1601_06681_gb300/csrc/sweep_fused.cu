@@ -1,0 +1,362 @@
+// Fused transport sweep: element solve + trace formula + FP64 residual in one
+// kernel (Sec. 3, eqs. transportLocalk1 and transportLocale).
+//
+// For transport the trace formula picks, at every face point, the value of
+// the upwind element (sgn(beta.n) = +-1), so the upwind element owns the
+// point and writes uhat^{k+1} there itself; every point has exactly one owner.
+// Points with beta.n = 0 (average of both sides) are finished by a small
+// kernel over a precomputed list; inflow boundary points hold g in both
+// ping-pong slots for the whole step. The owner also adds the point's share
+// of ||uhat^{k+1} - uhat^k||^2, with uhat^k taken from the values it staged
+// for its own solve.
+#include <cuda_runtime.h>
+
+#include "ehdg_internal.h"
+
+namespace ehdg {
+
+namespace {
+
+constexpr int kFT = 4;                 // row groups per 32-element tile
+constexpr int kFusedMaxBlocks = 152 * 8;
+
+__device__ __forceinline__ double fsum_warp(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct FusedParams {
+  int64_t nel, nface;
+  int NQFS, Nqf, F, shared, n_rows, n_up;
+  const int* rows;              // shared operator: rows, upwind ones first
+  const uint8_t* rowid;         // per-element operator: [slot][nel], upwind slots first
+  const uint8_t* nrows;
+  const uint8_t* nup;
+  const int32_t* elem_face;     // [F][nel]
+  const double* face_jf;        // [nface]
+  double fw[kMaxQ * kMaxQ];
+  double* uhat;                 // [2][Nqf][nface]
+  IterState* it;
+  const double* Gy;
+  const double* Hy;
+  double* Y;                    // rows of tangential points, for the finishing kernel
+  double* partials;
+  int final_here;               // 1: this kernel's last block finishes the residual
+  double tol, res_scale;
+  int max_iter;
+  double* hist;
+  int graph_mode;
+  cudaGraphConditionalHandle handle;
+};
+
+// Final reduction of nblocks partials by the last block to take a ticket;
+// records r_k and sets the loop condition (same rule as the trace kernel).
+// partials[slot] receives this block's sum; the last of the nblocks blocks of
+// this launch to take a ticket sums partials[0 .. n_total_partials).
+__device__ void finish_residual(double acc, double* partials, unsigned int slot,
+                                unsigned int nblocks, IterState* it, double* hist, int max_iter,
+                                double tol, double res_scale, int graph_mode,
+                                cudaGraphConditionalHandle handle, int n_total_partials) {
+  __shared__ double red[32];
+  __shared__ bool last;
+  acc = fsum_warp(acc);
+  const int nw = (blockDim.x * blockDim.y) >> 5;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, wid = tid >> 5;
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (wid == 0) {
+    double v = (lane < nw) ? red[lane] : 0.0;
+    v = fsum_warp(v);
+    if (lane == 0) {
+      partials[slot] = v;
+      __threadfence();
+      last = (atomicAdd(&it->counter, 1u) == nblocks - 1);
+    }
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (int i = tid; i < n_total_partials; i += blockDim.x * blockDim.y)
+    v += reinterpret_cast<volatile double*>(partials)[i];
+  v = fsum_warp(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (tid == 0) {
+    double sum = 0.0;
+    for (int w = 0; w < nw; ++w) sum += red[w];
+    const double r = res_scale * sqrt(sum);
+    const int k = it->k;
+    if (k < max_iter) hist[k] = r;
+    it->k = k + 1;
+    it->r_last = r;
+    it->counter = 0u;
+    int cont = 1, status = EHDG_OK;
+    if (!isfinite(r)) { cont = 0; status = EHDG_ERR_DIVERGED; }
+    else if (r < tol) { cont = 0; status = EHDG_OK; }
+    else if (k + 1 >= max_iter) { cont = 0; status = EHDG_ERR_NOT_CONVERGED; }
+    it->cont = cont;
+    it->status = status;
+    __threadfence();
+    if (graph_mode) cudaGraphSetConditional(handle, (unsigned int)cont);
+  }
+}
+
+template <int NQ>
+__global__ void __launch_bounds__(32 * kFT) k_sweep_fused(const FusedParams p) {
+  extern __shared__ double sm[];
+  const int nq = NQ > 0 ? NQ : p.NQFS;
+  const int lane = threadIdx.x, t = threadIdx.y;
+  double* Hsh = sm;
+  double* uh = sm + (p.shared ? nq * nq : 0);            // [nq][32]
+  int* fid = reinterpret_cast<int*>(uh + nq * 32);        // [F][32]
+  if (p.shared)
+    for (int i = t * 32 + lane; i < nq * nq; i += 32 * kFT) Hsh[i] = p.Hy[i];
+  const int64_t ne = p.nel, nface = p.nface;
+  const int kk = p.it->k;                                 // read before the last block advances it
+  const int64_t tlen = (int64_t)p.Nqf * nface;
+  const double* src = p.uhat + (int64_t)(kk & 1) * tlen;
+  double* dst = p.uhat + (int64_t)((kk + 1) & 1) * tlen;
+  const int64_t ntiles = (ne + 31) / 32;
+  double acc_res = 0.0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e = tile * 32 + lane;
+    __syncthreads();                                      // previous tile done with uh/fid
+    if (e < ne) {
+      for (int f = t; f < p.F; f += kFT) fid[f * 32 + lane] = p.elem_face[f * ne + e];
+    }
+    __syncthreads();
+    if (e < ne) {
+      for (int i = t; i < nq; i += kFT) {
+        const int f = i / p.Nqf, g = i - f * p.Nqf;
+        uh[i * 32 + lane] = src[g * nface + fid[f * 32 + lane]];
+      }
+    }
+    __syncthreads();
+    if (e < ne) {
+      const int nr = p.shared ? p.n_rows : p.nrows[e];
+      const int nu = p.shared ? p.n_up : p.nup[e];
+      for (int j = t; j < nr; j += kFT) {
+        double acc = p.Gy[j * ne + e];
+        int r;
+        if (p.shared) {
+          r = p.rows[j];
+          const double* Hr = Hsh + r * nq;
+          if constexpr (NQ > 0) {
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) acc += Hr[c] * uh[c * 32 + lane];
+          } else {
+            for (int c = 0; c < nq; ++c) acc += Hr[c] * uh[c * 32 + lane];
+          }
+        } else {
+          r = p.rowid[j * ne + e];
+          const double* Hr = p.Hy + (int64_t)j * nq * ne + e;
+          if constexpr (NQ > 0) {
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) acc += Hr[c * ne] * uh[c * 32 + lane];
+          } else {
+            for (int c = 0; c < nq; ++c) acc += Hr[c * ne] * uh[c * 32 + lane];
+          }
+        }
+        if (j < nu) {
+          const int f = r / p.Nqf, g = r - f * p.Nqf;
+          const int face = fid[f * 32 + lane];
+          dst[g * nface + face] = acc;
+          const double d = acc - uh[r * 32 + lane];
+          acc_res += p.face_jf[face] * p.fw[g] * d * d;
+        } else {
+          p.Y[(int64_t)r * ne + e] = acc;
+        }
+      }
+    }
+  }
+  if (p.final_here) {
+    finish_residual(acc_res, p.partials, blockIdx.x, gridDim.x, p.it, p.hist, p.max_iter, p.tol,
+                    p.res_scale, p.graph_mode, p.handle, gridDim.x);
+  } else {
+    // partial sums only; the finishing kernel reduces them with its own
+    acc_res = fsum_warp(acc_res);
+    __shared__ double red2[32];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if ((tid & 31) == 0) red2[tid >> 5] = acc_res;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < (int)((blockDim.x * blockDim.y) >> 5); ++w) s += red2[w];
+      p.partials[blockIdx.x] = s;
+    }
+  }
+}
+
+// Points with beta.n = 0: average of the two sides (eq. transportLocale with
+// sgn = 0), and the final residual reduction over both kernels' partials.
+struct TangentParams {
+  int64_t nel, nface, n_tan;
+  int Nqf, cn;
+  const int32_t* tan_g;
+  const int32_t* tan_face;
+  const int32_t* face_elem;     // [2][nface]
+  const int8_t* face_local;     // [2][nface]
+  const double* face_jf;
+  double fw[kMaxQ * kMaxQ];
+  const double* gb;
+  const double* gb_old;
+  const double* Y;
+  double* uhat;
+  IterState* it;
+  double* partials;             // [elem blocks + own blocks]
+  int elem_blocks;
+  double tol, res_scale;
+  int max_iter;
+  double* hist;
+  int graph_mode;
+  cudaGraphConditionalHandle handle;
+};
+
+__global__ void __launch_bounds__(256) k_tangent(const TangentParams p) {
+  const int64_t nface = p.nface, ne = p.nel;
+  const int kk = p.it->k;
+  const int64_t tlen = (int64_t)p.Nqf * nface;
+  const double* src = p.uhat + (int64_t)(kk & 1) * tlen;
+  double* dst = p.uhat + (int64_t)((kk + 1) & 1) * tlen;
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < p.n_tan;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int g = p.tan_g[i];
+    const int64_t face = p.tan_face[i];
+    const int em = p.face_elem[face], ep = p.face_elem[nface + face];
+    const int fm = p.face_local[face], fpl = p.face_local[nface + face];
+    const double ym = p.Y[(int64_t)(fm * p.Nqf + g) * ne + em];
+    double yp;
+    if (ep >= 0) {
+      yp = p.Y[(int64_t)(fpl * p.Nqf + g) * ne + ep];
+    } else {
+      const int64_t t = (int64_t)g * nface + face;
+      yp = p.cn ? 0.5 * (p.gb[t] + p.gb_old[t]) : p.gb[t];
+    }
+    const double v = 0.5 * (ym + yp);
+    const int64_t t = (int64_t)g * nface + face;
+    const double d = v - src[t];
+    dst[t] = v;
+    acc += p.face_jf[face] * p.fw[g] * d * d;
+  }
+  finish_residual(acc, p.partials, p.elem_blocks + blockIdx.x, gridDim.x, p.it, p.hist,
+                  p.max_iter, p.tol, p.res_scale, p.graph_mode, p.handle,
+                  p.elem_blocks + gridDim.x);
+}
+
+}  // namespace
+
+int tangent_grid(int64_t n_tan) {
+  int g = (int)((n_tan + 255) / 256);
+  if (g > 152 * 4) g = 152 * 4;
+  return g < 1 ? 1 : g;
+}
+
+int fused_grid(int64_t nel) {
+  int64_t g = (nel + 31) / 32;
+  if (g > kFusedMaxBlocks) g = kFusedMaxBlocks;
+  return g < 1 ? 1 : (int)g;
+}
+
+static void fill_fw(const Ctx& c, double* fw) {
+  for (int g = 0; g < c.Nqf; ++g) {
+    double w = 1.0;
+    int rem = g;
+    for (int t = 0; t < c.dim - 1; ++t) {
+      w *= c.r1d.om[rem % c.q];
+      rem /= c.q;
+    }
+    fw[g] = w;
+  }
+}
+
+template <int NQ>
+static cudaError_t launch_fused_t(const FusedParams& p, size_t smem, int grid, cudaStream_t s) {
+  cudaError_t err = cudaFuncSetAttribute(k_sweep_fused<NQ>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  k_sweep_fused<NQ><<<grid, dim3(32, kFT), smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
+  FusedParams p;
+  p.nel = c.nel;
+  p.nface = c.nface;
+  p.NQFS = c.NQFS;
+  p.Nqf = c.Nqf;
+  p.F = c.F;
+  p.shared = c.shared_op ? 1 : 0;
+  p.n_rows = c.n_rows;
+  p.n_up = c.n_up;
+  p.rows = c.rows;
+  p.rowid = c.rowid;
+  p.nrows = c.nrows;
+  p.nup = c.nup;
+  p.elem_face = c.geo.elem_face;
+  p.face_jf = c.geo.face_jf;
+  fill_fw(c, p.fw);
+  p.uhat = c.uhat;
+  p.it = c.it;
+  p.Gy = c.Gy;
+  p.Hy = c.Hy;
+  p.Y = c.Y;
+  p.partials = c.partials;
+  p.final_here = c.n_tan == 0 ? 1 : 0;
+  p.tol = c.tol;
+  p.res_scale = c.res_scale;
+  p.max_iter = c.max_iter;
+  p.hist = c.hist;
+  p.graph_mode = graph_mode;
+  p.handle = c.handle;
+  const size_t smem = sizeof(double) * ((p.shared ? (size_t)c.NQFS * c.NQFS : 0) +
+                                        (size_t)c.NQFS * 32) + sizeof(int) * c.F * 32;
+  const int grid = fused_grid(c.nel);
+  cudaError_t err;
+  switch (c.NQFS) {
+    case 8: err = launch_fused_t<8>(p, smem, grid, c.stream); break;
+    case 12: err = launch_fused_t<12>(p, smem, grid, c.stream); break;
+    case 16: err = launch_fused_t<16>(p, smem, grid, c.stream); break;
+    case 20: err = launch_fused_t<20>(p, smem, grid, c.stream); break;
+    case 24: err = launch_fused_t<24>(p, smem, grid, c.stream); break;
+    case 28: err = launch_fused_t<28>(p, smem, grid, c.stream); break;
+    case 36: err = launch_fused_t<36>(p, smem, grid, c.stream); break;
+    case 40: err = launch_fused_t<40>(p, smem, grid, c.stream); break;
+    case 54: err = launch_fused_t<54>(p, smem, grid, c.stream); break;
+    case 96: err = launch_fused_t<96>(p, smem, grid, c.stream); break;
+    default: err = launch_fused_t<0>(p, smem, grid, c.stream); break;
+  }
+  if (err != cudaSuccess || c.n_tan == 0) return err;
+  TangentParams q;
+  q.nel = c.nel;
+  q.nface = c.nface;
+  q.n_tan = c.n_tan;
+  q.Nqf = c.Nqf;
+  q.cn = (c.scheme == EHDG_CN) ? 1 : 0;
+  q.tan_g = c.tan_g;
+  q.tan_face = c.tan_face;
+  q.face_elem = c.geo.face_elem;
+  q.face_local = c.geo.face_local;
+  q.face_jf = c.geo.face_jf;
+  fill_fw(c, q.fw);
+  q.gb = c.gb;
+  q.gb_old = c.gb_old;
+  q.Y = c.Y;
+  q.uhat = c.uhat;
+  q.it = c.it;
+  q.partials = c.partials;
+  q.elem_blocks = grid;
+  q.tol = c.tol;
+  q.res_scale = c.res_scale;
+  q.max_iter = c.max_iter;
+  q.hist = c.hist;
+  q.graph_mode = graph_mode;
+  q.handle = c.handle;
+  k_tangent<<<tangent_grid(c.n_tan), 256, 0, c.stream>>>(q);
+  return cudaGetLastError();
+}
+
+}  // namespace ehdg
