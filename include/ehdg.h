@@ -65,7 +65,19 @@ typedef enum { EHDG_TRANSPORT = 0, EHDG_SW_LINEAR = 1 } ehdg_pde;
  * (eq. transport). */
 typedef enum { EHDG_BE = 0, EHDG_CN = 1, EHDG_STEADY = 2 } ehdg_scheme;
 
-typedef enum { EHDG_FP64 = 0, EHDG_MIXED_TF32 = 1, EHDG_MIXED_BF16 = 2 } ehdg_precision;
+/* Precision of the element sweeps. FP64: every sweep in float64. MIXED_*:
+ * defect correction on the trace fixed point -- each outer iteration is one
+ * FP64 sweep (FP64 residual R = F(uhat) - uhat and the FP64 convergence test),
+ * followed by `inner_sweeps` low-precision eHDG sweeps on the correction
+ * equation delta = R + S H delta and the FP64 update uhat += delta; the fixed
+ * point and the stopping rule are those of the FP64 iteration. MIXED_FP32 uses
+ * float32 operands and accumulation on the CUDA cores. */
+typedef enum {
+  EHDG_FP64 = 0,
+  EHDG_MIXED_TF32 = 1,
+  EHDG_MIXED_BF16 = 2,
+  EHDG_MIXED_FP32 = 3
+} ehdg_precision;
 
 /* Face tags. */
 enum { EHDG_FACE_INTERIOR = 0, EHDG_FACE_DIRICHLET = 1, EHDG_FACE_WALL = 2 };
@@ -92,10 +104,12 @@ typedef struct {
   double dt;                   /* time step (ignored for STEADY) */
   double tol;                  /* stop when ||uhat^{k+1}-uhat^k||_{L2(E_h)} < tol */
   int max_iter;                /* iteration cap per step, >= 1 */
-  ehdg_precision precision;    /* EHDG_FP64 in this build */
+  ehdg_precision precision;    /* EHDG_FP64 or EHDG_MIXED_FP32 in this build */
   const double* beta_const;    /* [dim] constant velocity, or NULL */
   const double* beta_nodes;    /* [n_elem][dim][Np] nodal velocity, or NULL (transport) */
   double Phi;                  /* shallow water: mean geopotential Phi > 0 */
+  int inner_sweeps;            /* mixed precision: low-precision sweeps per outer
+                                  iteration (0 = 8) */
 } ehdg_problem_desc;
 
 /* Sizes of a created context. */

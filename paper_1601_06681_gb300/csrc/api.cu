@@ -169,8 +169,13 @@ ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
   CK(counted(c, EHDG_KERNEL_STEP, 1, [&] { return launch_step(c); }));
   CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceInitial); }));
   const int n_it = fixed_iters > 0 ? fixed_iters : c.max_iter;
-  int done = 0;
   for (int k = 0; k < n_it; ++k) {
+    if (k > 0 && c.mixed) {
+      // low-precision correction of uhat before the next FP64 sweep
+      int nl = 0;
+      CK(counted(c, EHDG_KERNEL_AUX, 0, [&] { return launch_correction(c, &nl); }));
+      c.launches[EHDG_KERNEL_AUX] += nl;
+    }
     if (c.pde == EHDG_TRANSPORT) {
       // element solve + trace formula + residual in one kernel (+ tangential points)
       CK(counted(c, EHDG_KERNEL_ELEM, 1, [&] { return launch_sweep_fused(c, 0); }));
@@ -179,7 +184,6 @@ ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
       CK(counted(c, EHDG_KERNEL_ELEM, 1, [&] { return launch_elem(c); }));
       CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceIterate); }));
     }
-    ++done;
     if (fixed_iters <= 0) {
       CK(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
       CK(cudaStreamSynchronize(c.stream));
@@ -196,7 +200,6 @@ ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
   c.last_iters = std::min(c.it_host->k, c.max_iter);
   if (iters) *iters = c.it_host->k;
   if (res) *res = c.it_host->r_last;
-  (void)done;
   if (fixed_iters > 0) return EHDG_OK;
   const ehdg_status st = (ehdg_status)c.it_host->status;
   if (st == EHDG_ERR_NOT_CONVERGED) return fail(st, "eHDG did not reach the tolerance in max_iter iterations");
@@ -240,14 +243,28 @@ ehdg_status build_graph(Ctx& c) {
   if ((err = launch_step(c)) != cudaSuccess) return abort_capture(err, "capture step");
   if ((err = launch_face(c, kFaceInitial)) != cudaSuccess) return abort_capture(err, "capture face");
   cudaStreamCaptureStatus cst;
+  cudaGraphConditionalHandle handle;
+  if (c.mixed) {
+    // the first FP64 sweep runs before the loop; the loop body is
+    // {correction, FP64 sweep}; the sweep's last block sets the condition
+    err = cudaStreamGetCaptureInfo(c.cap_stream, &cst, nullptr, &g, nullptr, nullptr, nullptr);
+    if (err != cudaSuccess) return abort_capture(err, "cudaStreamGetCaptureInfo");
+    err = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
+    if (err != cudaSuccess) return abort_capture(err, "cudaGraphConditionalHandleCreate");
+    c.handle = handle;
+    err = (c.pde == EHDG_TRANSPORT) ? launch_sweep_fused(c, 1) : launch_elem(c);
+    if (err == cudaSuccess && c.pde != EHDG_TRANSPORT) err = launch_face(c, kFaceIterate, 1);
+    if (err != cudaSuccess) return abort_capture(err, "capture first FP64 sweep");
+  }
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
   err = cudaStreamGetCaptureInfo(c.cap_stream, &cst, nullptr, &g, &deps, nullptr, &ndeps);
   if (err != cudaSuccess) return abort_capture(err, "cudaStreamGetCaptureInfo");
-  cudaGraphConditionalHandle handle;
-  err = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
-  if (err != cudaSuccess) return abort_capture(err, "cudaGraphConditionalHandleCreate");
-  c.handle = handle;
+  if (!c.mixed) {
+    err = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
+    if (err != cudaSuccess) return abort_capture(err, "cudaGraphConditionalHandleCreate");
+    c.handle = handle;
+  }
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = handle;
@@ -265,6 +282,15 @@ ehdg_status build_graph(Ctx& c) {
   if (err != cudaSuccess) return abort_capture(err, "cudaStreamBeginCaptureToGraph");
   c.stream = c.body_stream;
   cudaError_t e1, e2;
+  if (c.mixed) {
+    cudaError_t ec = launch_correction(c, nullptr);
+    if (ec != cudaSuccess) {
+      cudaGraph_t junk = body;
+      cudaStreamEndCapture(c.body_stream, &junk);
+      c.stream = c.cap_stream;
+      return abort_capture(ec, "capture correction");
+    }
+  }
   if (c.pde == EHDG_TRANSPORT) {
     e1 = cudaSuccess;
     e2 = launch_sweep_fused(c, 1);
@@ -329,8 +355,17 @@ ehdg_status run_graph(Ctx& c, int n_steps, int* iters_per_step, double* res) {
   c.launches[EHDG_KERNEL_ELEM] += sweeps;
   c.launches[EHDG_KERNEL_FACE] +=
       n_steps + ((c.pde == EHDG_TRANSPORT) ? (c.n_tan > 0 ? sweeps : 0) : sweeps);
+  if (c.mixed) {
+    const int per_lp = 1 + ((c.pde == EHDG_TRANSPORT) ? (c.n_tan > 0 ? 1 : 0) : 1);
+    c.launches[EHDG_KERNEL_AUX] += (sweeps - n_steps) * (c.inner_sweeps * per_lp + 1);
+  }
   c.last_iters = n_steps > 0 ? std::min(c.step_iters_h[n_steps - 1], c.max_iter) : 0;
   if (res) *res = c.it_host->r_last;
+  if (c.tc_err) {
+    int te = 0;
+    CK(cudaMemcpy(&te, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (te) return fail(EHDG_ERR_TIMEOUT, "a tensor-core sweep's bounded wait gave up");
+  }
   if (first == EHDG_ERR_NOT_CONVERGED) return fail(first, "eHDG did not reach the tolerance in max_iter iterations");
   if (first == EHDG_ERR_DIVERGED) return fail(first, "non-finite eHDG residual");
   return first;
@@ -505,8 +540,11 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
     return fail(EHDG_ERR_INVALID, "unknown pde");
   TRY(validate_mesh(mesh, prob->pde));
   const int dim = mesh->dim, p = prob->p;
-  if (prob->precision != EHDG_FP64)
-    return fail(EHDG_ERR_UNSUPPORTED, "only EHDG_FP64 is available in this build");
+  if (prob->precision != EHDG_FP64 && prob->precision != EHDG_MIXED_FP32 &&
+      prob->precision != EHDG_MIXED_TF32 && prob->precision != EHDG_MIXED_BF16)
+    return fail(EHDG_ERR_INVALID, "unknown precision");
+  if (prob->inner_sweeps < 0 || prob->inner_sweeps > 64)
+    return fail(EHDG_ERR_INVALID, "inner_sweeps must be 0..64");
   if (prob->scheme != EHDG_BE && prob->scheme != EHDG_CN && prob->scheme != EHDG_STEADY)
     return fail(EHDG_ERR_INVALID, "unknown scheme");
   if (prob->scheme != EHDG_STEADY && !(prob->dt > 0.0 && std::isfinite(prob->dt)))
@@ -552,6 +590,9 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   c.max_iter = prob->max_iter;
   c.Phi = prob->Phi;
   c.variable_beta = variable;
+  c.mixed = prob->precision != EHDG_FP64;
+  c.precision = prob->precision;
+  c.inner_sweeps = prob->inner_sweeps > 0 ? prob->inner_sweeps : 8;
   c.stream = (cudaStream_t)stream;
   if (prob->pde == EHDG_TRANSPORT && !variable)
     for (int a = 0; a < dim; ++a) c.beta_const[a] = prob->beta_const[a];
@@ -561,6 +602,12 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
     for (int a = 0; a < dim; ++a)
       if (mesh->elem_h[e * dim + a] != mesh->elem_h[a]) uniform = false;
   c.shared_op = uniform && !variable;
+  if ((c.precision == EHDG_MIXED_TF32 || c.precision == EHDG_MIXED_BF16) && !c.shared_op) {
+    delete h;
+    return fail(EHDG_ERR_UNSUPPORTED,
+                "TF32/BF16 tensor-core sweeps need one local operator shared by all elements "
+                "(constant velocity, uniform mesh); use EHDG_MIXED_FP32");
+  }
 
   build_ref1d(p, q, &c.r1d);
   c.ref.dim = dim;
@@ -758,6 +805,18 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   c.n_partials = std::max(face_grid_x(c.nface, c.Nqf) * c.Nqf,
                           fused_grid(c.nel) + tangent_grid((int64_t)trace));
   TRYC(dalloc(c, &c.partials, (size_t)c.n_partials));
+  if (c.mixed) {
+    TRYC(dalloc(c, &c.Hy32, (size_t)c.NQFS * c.NQFS * ne));
+    TRYC(dalloc(c, &c.R32, trace));
+    TRYC(dalloc(c, &c.d32, 2 * trace));
+    TRYC(dalloc(c, &c.Y32, (size_t)c.NQFS * c.nel));
+    TRYC(dalloc(c, &c.tc_err, 1));
+    CKC(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
+    // points no sweep owns (inflow boundary) keep R = delta = 0 for good
+    CKC(cudaMemsetAsync(c.R32, 0, sizeof(float) * trace, c.stream));
+    CKC(cudaMemsetAsync(c.d32, 0, sizeof(float) * 2 * trace, c.stream));
+    CKC(cudaMemsetAsync(c.Y32, 0, sizeof(float) * c.NQFS * c.nel, c.stream));
+  }
   TRYC(dalloc(c, &c.it, 1));
   TRYC(dalloc(c, &c.hist, (size_t)c.max_iter));
   CKC(cudaMallocHost(&c.it_host, sizeof(IterState)));
@@ -774,6 +833,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   if (c.pde == EHDG_TRANSPORT)
     CKC(counted(c, EHDG_KERNEL_SIGNS, 1, [&] { return launch_face_signs(c); }));
   if (!c.shared_op) CKC(counted(c, EHDG_KERNEL_AUX, 2, [&] { return launch_rows(c); }));
+  if (c.mixed) CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_hy_to_f32(c); }));
   CKC(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
   CKC(cudaStreamSynchronize(c.stream));
   if (c.it_host->status != 0) return cleanup(fail(EHDG_ERR_INVALID, "singular local operator"));

@@ -101,6 +101,15 @@ struct Ctx {
   int32_t* tan_face = nullptr;   //   and face
   int64_t n_tan = 0;
   int64_t sweep_rows = 0;        // rows computed per sweep, all elements
+  // mixed precision (defect correction)
+  bool mixed = false;
+  ehdg_precision precision = EHDG_FP64;
+  int* tc_err = nullptr;         // set by a tensor-core sweep whose bounded wait gave up
+  int inner_sweeps = 0;
+  float* Hy32 = nullptr;         // FP32 copy of Hy in the sweep's slot layout
+  float* R32 = nullptr;          // [Nqf][nface] FP64 residual F(uhat) - uhat, rounded
+  float* d32 = nullptr;          // [2][Nqf][nface] correction iterates
+  float* Y32 = nullptr;          // [NQFS][nel] low-precision element values
   double* u = nullptr;           // [n][nel] state u^n (SoA)
   double* G = nullptr;           // [n][nel]
   double* Gy = nullptr;          // [NQFS][nel]
@@ -159,8 +168,15 @@ cudaError_t launch_rows(Ctx& c);
 int face_grid_x(int64_t nface, int Nqf);   // blocks along faces of the trace kernel
 // fused transport sweep (sweep_fused.cu)
 cudaError_t launch_sweep_fused(Ctx& c, int graph_mode);
-int fused_grid(int64_t nel);
+int fused_grid(int64_t nel);      // upper bound of the fused sweep's grid
+int device_sms();
 int tangent_grid(int64_t n_tan);
+// mixed precision (mixed.cu)
+cudaError_t launch_hy_to_f32(Ctx& c);
+cudaError_t launch_correction(Ctx& c, int* n_launched);
+// tensor-core correction sweep (tc_sweep.cu)
+bool tc_supported(const Ctx& c);
+cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out);
 
 enum FaceMode { kFaceInitial = 0, kFaceIterate = 1 };
 

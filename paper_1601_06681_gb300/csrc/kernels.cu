@@ -659,6 +659,7 @@ struct FaceParams {
   const double* gb;             // [Nqf][nface]
   const double* gb_old;
   double* uhat;                 // [2][Nqf][nface] ping-pong pair
+  float* R_out;                 // mixed precision: F(uhat) - uhat (or null)
   double* partials;
   IterState* it;
   double* hist;
@@ -715,6 +716,7 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
     if (p.mode == kFaceIterate) {
       const double d = uh - uh_old[face];
       acc += p.geo.face_jf[face] * wg * d * d;
+      if (p.R_out) p.R_out[(int64_t)gf * nface + face] = (float)d;
     } else {
       uh_new[total + face] = uh;     // both slots: points no sweep rewrites keep this value
     }
@@ -803,6 +805,7 @@ cudaError_t launch_face(Ctx& c, int mode, int graph_mode) {
   p.gb = c.gb;
   p.gb_old = c.gb_old;
   p.uhat = c.uhat;
+  p.R_out = c.mixed ? c.R32 : nullptr;
   p.partials = c.partials;
   p.it = c.it;
   p.hist = c.hist;

@@ -18,7 +18,7 @@ namespace ehdg {
 namespace {
 
 constexpr int kFT = 4;                 // row groups per 32-element tile
-constexpr int kFusedMaxBlocks = 152 * 8;
+constexpr int kFusedMaxBlocks = 4096;
 
 __device__ __forceinline__ double fsum_warp(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -40,6 +40,7 @@ struct FusedParams {
   const double* Gy;
   const double* Hy;
   double* Y;                    // rows of tangential points, for the finishing kernel
+  float* R_out;                 // mixed precision: F(uhat) - uhat at owned points (or null)
   double* partials;
   int final_here;               // 1: this kernel's last block finishes the residual
   double tol, res_scale;
@@ -105,7 +106,7 @@ __device__ void finish_residual(double acc, double* partials, unsigned int slot,
 }
 
 template <int NQ>
-__global__ void __launch_bounds__(32 * kFT) k_sweep_fused(const FusedParams p) {
+__global__ void __launch_bounds__(32 * kFT, 4) k_sweep_fused(const FusedParams p) {
   extern __shared__ double sm[];
   const int nq = NQ > 0 ? NQ : p.NQFS;
   const int lane = threadIdx.x, t = threadIdx.y;
@@ -139,33 +140,42 @@ __global__ void __launch_bounds__(32 * kFT) k_sweep_fused(const FusedParams p) {
       const int nr = p.shared ? p.n_rows : p.nrows[e];
       const int nu = p.shared ? p.n_up : p.nup[e];
       for (int j = t; j < nr; j += kFT) {
-        double acc = p.Gy[j * ne + e];
+        // two independent FMA chains (even and odd columns)
+        double a0 = p.Gy[j * ne + e], a1 = 0.0;
         int r;
         if (p.shared) {
           r = p.rows[j];
           const double* Hr = Hsh + r * nq;
           if constexpr (NQ > 0) {
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) acc += Hr[c] * uh[c * 32 + lane];
+#pragma unroll 16
+            for (int c = 0; c < NQ; c += 2) {
+              a0 = fma(Hr[c], uh[c * 32 + lane], a0);
+              if (c + 1 < NQ) a1 = fma(Hr[c + 1], uh[(c + 1) * 32 + lane], a1);
+            }
           } else {
-            for (int c = 0; c < nq; ++c) acc += Hr[c] * uh[c * 32 + lane];
+            for (int c = 0; c < nq; ++c) a0 = fma(Hr[c], uh[c * 32 + lane], a0);
           }
         } else {
           r = p.rowid[j * ne + e];
           const double* Hr = p.Hy + (int64_t)j * nq * ne + e;
           if constexpr (NQ > 0) {
-#pragma unroll
-            for (int c = 0; c < NQ; ++c) acc += Hr[c * ne] * uh[c * 32 + lane];
+#pragma unroll 16
+            for (int c = 0; c < NQ; c += 2) {
+              a0 = fma(Hr[c * ne], uh[c * 32 + lane], a0);
+              if (c + 1 < NQ) a1 = fma(Hr[(c + 1) * ne], uh[(c + 1) * 32 + lane], a1);
+            }
           } else {
-            for (int c = 0; c < nq; ++c) acc += Hr[c * ne] * uh[c * 32 + lane];
+            for (int c = 0; c < nq; ++c) a0 = fma(Hr[c * ne], uh[c * 32 + lane], a0);
           }
         }
+        const double acc = a0 + a1;
         if (j < nu) {
           const int f = r / p.Nqf, g = r - f * p.Nqf;
           const int face = fid[f * 32 + lane];
           dst[g * nface + face] = acc;
           const double d = acc - uh[r * 32 + lane];
           acc_res += p.face_jf[face] * p.fw[g] * d * d;
+          if (p.R_out) p.R_out[g * nface + face] = (float)d;
         } else {
           p.Y[(int64_t)r * ne + e] = acc;
         }
@@ -205,6 +215,7 @@ struct TangentParams {
   const double* gb_old;
   const double* Y;
   double* uhat;
+  float* R_out;
   IterState* it;
   double* partials;             // [elem blocks + own blocks]
   int elem_blocks;
@@ -241,6 +252,7 @@ __global__ void __launch_bounds__(256) k_tangent(const TangentParams p) {
     const double d = v - src[t];
     dst[t] = v;
     acc += p.face_jf[face] * p.fw[g] * d * d;
+    if (p.R_out) p.R_out[t] = (float)d;
   }
   finish_residual(acc, p.partials, p.elem_blocks + blockIdx.x, gridDim.x, p.it, p.hist,
                   p.max_iter, p.tol, p.res_scale, p.graph_mode, p.handle,
@@ -273,11 +285,41 @@ static void fill_fw(const Ctx& c, double* fw) {
   }
 }
 
+int device_sms() {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+      nsm = 152;
+  }
+  return nsm;
+}
+
+// Persistent grid: one full wave of resident blocks (no partial last wave),
+// capped by the number of 32-element tiles and by `cap`.
+template <class K>
+int one_wave_grid(K kernel, int threads, size_t smem, int64_t ntiles, int cap) {
+  int bpsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, threads, smem) != cudaSuccess ||
+      bpsm < 1) {
+    cudaGetLastError();
+    bpsm = 1;
+  }
+  int64_t g = (int64_t)bpsm * device_sms();
+  if (g > ntiles) g = ntiles;
+  if (g > cap) g = cap;
+  return g < 1 ? 1 : (int)g;
+}
+
 template <int NQ>
-static cudaError_t launch_fused_t(const FusedParams& p, size_t smem, int grid, cudaStream_t s) {
+static cudaError_t launch_fused_t(const FusedParams& p, size_t smem, int64_t ntiles,
+                                  cudaStream_t s, int* grid_out) {
   cudaError_t err = cudaFuncSetAttribute(k_sweep_fused<NQ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
+  const int grid = one_wave_grid(k_sweep_fused<NQ>, 32 * kFT, smem, ntiles, kFusedMaxBlocks);
+  *grid_out = grid;
   k_sweep_fused<NQ><<<grid, dim3(32, kFT), smem, s>>>(p);
   return cudaGetLastError();
 }
@@ -304,6 +346,7 @@ cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
   p.Gy = c.Gy;
   p.Hy = c.Hy;
   p.Y = c.Y;
+  p.R_out = c.mixed ? c.R32 : nullptr;
   p.partials = c.partials;
   p.final_here = c.n_tan == 0 ? 1 : 0;
   p.tol = c.tol;
@@ -314,20 +357,21 @@ cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
   p.handle = c.handle;
   const size_t smem = sizeof(double) * ((p.shared ? (size_t)c.NQFS * c.NQFS : 0) +
                                         (size_t)c.NQFS * 32) + sizeof(int) * c.F * 32;
-  const int grid = fused_grid(c.nel);
+  const int64_t ntiles = (c.nel + 31) / 32;
+  int grid = 1;
   cudaError_t err;
   switch (c.NQFS) {
-    case 8: err = launch_fused_t<8>(p, smem, grid, c.stream); break;
-    case 12: err = launch_fused_t<12>(p, smem, grid, c.stream); break;
-    case 16: err = launch_fused_t<16>(p, smem, grid, c.stream); break;
-    case 20: err = launch_fused_t<20>(p, smem, grid, c.stream); break;
-    case 24: err = launch_fused_t<24>(p, smem, grid, c.stream); break;
-    case 28: err = launch_fused_t<28>(p, smem, grid, c.stream); break;
-    case 36: err = launch_fused_t<36>(p, smem, grid, c.stream); break;
-    case 40: err = launch_fused_t<40>(p, smem, grid, c.stream); break;
-    case 54: err = launch_fused_t<54>(p, smem, grid, c.stream); break;
-    case 96: err = launch_fused_t<96>(p, smem, grid, c.stream); break;
-    default: err = launch_fused_t<0>(p, smem, grid, c.stream); break;
+    case 8: err = launch_fused_t<8>(p, smem, ntiles, c.stream, &grid); break;
+    case 12: err = launch_fused_t<12>(p, smem, ntiles, c.stream, &grid); break;
+    case 16: err = launch_fused_t<16>(p, smem, ntiles, c.stream, &grid); break;
+    case 20: err = launch_fused_t<20>(p, smem, ntiles, c.stream, &grid); break;
+    case 24: err = launch_fused_t<24>(p, smem, ntiles, c.stream, &grid); break;
+    case 28: err = launch_fused_t<28>(p, smem, ntiles, c.stream, &grid); break;
+    case 36: err = launch_fused_t<36>(p, smem, ntiles, c.stream, &grid); break;
+    case 40: err = launch_fused_t<40>(p, smem, ntiles, c.stream, &grid); break;
+    case 54: err = launch_fused_t<54>(p, smem, ntiles, c.stream, &grid); break;
+    case 96: err = launch_fused_t<96>(p, smem, ntiles, c.stream, &grid); break;
+    default: err = launch_fused_t<0>(p, smem, ntiles, c.stream, &grid); break;
   }
   if (err != cudaSuccess || c.n_tan == 0) return err;
   TangentParams q;
@@ -346,6 +390,7 @@ cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
   q.gb_old = c.gb_old;
   q.Y = c.Y;
   q.uhat = c.uhat;
+  q.R_out = c.mixed ? c.R32 : nullptr;
   q.it = c.it;
   q.partials = c.partials;
   q.elem_blocks = grid;

@@ -1,0 +1,266 @@
+// Low-precision correction sweep on the 5th-generation tensor cores (tcgen05),
+// for a local operator shared by every element (constant velocity on a
+// uniform mesh): Ydelta = delta_loc Hy^T is a dense GEMM with
+//   M = elements (128 per tile, one TMEM lane each), K = face points of an
+//   element (NQFS, padded), N = sweep rows (upwind first, padded to 16),
+// operands TF32 or BF16 in shared memory, FP32 accumulation in TMEM.
+//
+// Shared-memory operands use the canonical K-major layout without swizzle:
+// 8-row x 16-byte core matrices, adjacent core matrices along K 128 bytes
+// apart (LBO) and 8-row groups (K bytes / 16) * 128 bytes apart (SBO).
+// One thread issues the MMAs and commits them to an mbarrier; every wait on
+// the mbarrier is bounded and records an error instead of hanging.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "ehdg_internal.h"
+
+namespace ehdg {
+
+namespace {
+
+constexpr int kTcM = 128;
+constexpr uint32_t kWaitLimit = 1u << 24;   // mbarrier polls before giving up
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;                    // descriptor version of sm_100-family MMA
+  return d;                                  // base offset 0, no swizzle
+}
+
+// byte offset of element (row, k) in the K-major no-swizzle layout
+__device__ __forceinline__ uint32_t kmajor_off(int row, int kbyte, uint32_t sbo) {
+  return (uint32_t)(row >> 3) * sbo + (uint32_t)(kbyte >> 4) * 128u + (uint32_t)(row & 7) * 16u +
+         (uint32_t)(kbyte & 15);
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+struct TcParams {
+  int64_t nel, nface;
+  int NQFS, Nqf, F, n_rows, n_up, owner_writes;
+  int Kp, Np, ncols;            // padded K and N, TMEM columns
+  int bf16;                     // 1: kind::f16 with BF16 operands, 0: kind::tf32
+  uint32_t idesc;
+  const int* rows;
+  const int32_t* elem_face;
+  const float* Hy32;            // [NQFS][NQFS] shared operator
+  const float* R;
+  const float* in;
+  float* out;
+  float* Y32;
+  int* err;
+};
+
+__device__ __forceinline__ void store_elem(unsigned char* base, int row, int k, int esize,
+                                           uint32_t sbo, float v, int bf16) {
+  const uint32_t off = kmajor_off(row, k * esize, sbo);
+  if (bf16) {
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+  } else {
+    *reinterpret_cast<uint32_t*>(base + off) = to_tf32(v);
+  }
+}
+
+__global__ void __launch_bounds__(kTcM) k_sweep_tc(const TcParams p) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int esize = p.bf16 ? 2 : 4;
+  const uint32_t kbytes = (uint32_t)p.Kp * esize;
+  const uint32_t sbo = kbytes * 8u;             // (K bytes / 16) core matrices of 128 B
+  unsigned char* Bs = sm;                        // Np x Kp
+  unsigned char* As = sm + (size_t)p.Np * kbytes; // 128 x Kp
+  int* fid = reinterpret_cast<int*>(As + (size_t)kTcM * kbytes);   // [F][128]
+
+  // B = sweep rows of the shared operator, zero-padded
+  for (int i = tid; i < p.Np * p.Kp; i += kTcM) {
+    const int n = i / p.Kp, k = i - n * p.Kp;
+    float v = 0.f;
+    if (n < p.n_rows && k < p.NQFS) v = p.Hy32[p.rows[n] * p.NQFS + k];
+    store_elem(Bs, n, k, esize, sbo, v, p.bf16);
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_base)),
+                 "r"(p.ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tbase = tmem_base;
+
+  const int64_t ne = p.nel, nface = p.nface;
+  const int64_t ntiles = (ne + kTcM - 1) / kTcM;
+  uint32_t phase = 0;
+  bool failed = false;
+  for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    const int64_t e = tile * kTcM + tid;
+    // A = this tile's correction values at its elements' face points
+    if (e < ne)
+      for (int f = 0; f < p.F; ++f) fid[f * kTcM + tid] = p.elem_face[f * ne + e];
+    for (int k = 0; k < p.Kp; ++k) {
+      float v = 0.f;
+      if (e < ne && k < p.NQFS) {
+        const int f = k / p.Nqf, g = k - f * p.Nqf;
+        v = p.in[g * nface + fid[f * kTcM + tid]];
+      }
+      store_elem(As, tid, k, esize, sbo, v, p.bf16);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+      const int ksteps = (int)(kbytes / 32u);
+      for (int s = 0; s < ksteps; ++s) {
+        const uint64_t ad = umma_desc(a0 + 256u * s, 128u, sbo);
+        const uint64_t bd = umma_desc(b0 + 256u * s, 128u, sbo);
+        const uint32_t acc = s > 0 ? 1u : 0u;
+        if (p.bf16) {
+          asm volatile(
+              "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tbase),
+              "l"(ad), "l"(bd), "r"(p.idesc), "r"(acc));
+        } else {
+          asm volatile(
+              "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}\n" ::"r"(tbase),
+              "l"(ad), "l"(bd), "r"(p.idesc), "r"(acc));
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_addr(&mbar)));
+    }
+    // bounded wait for the MMAs
+    uint32_t ok = 0;
+    for (uint32_t it = 0; it < kWaitLimit; ++it) {
+      asm volatile(
+          "{\n .reg .pred w;\n mbarrier.try_wait.parity.shared::cta.b64 w, [%1], %2;\n"
+          " selp.u32 %0, 1, 0, w;\n}\n"
+          : "=r"(ok)
+          : "r"(smem_addr(&mbar)), "r"(phase)
+          : "memory");
+      if (ok) break;
+    }
+    // block-uniform outcome, so every thread takes the same path below
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      if (tid == 0) atomicExch(p.err, 1);
+      failed = true;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!failed) {
+      // epilogue: this warp's 32 TMEM lanes = its 32 elements, N columns
+      for (int c0 = 0; c0 < p.Np; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
+            "%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+              "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (e < ne) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int j = c0 + q;
+            if (j >= p.n_rows) break;
+            const float acc = __uint_as_float(v[q]);
+            const int r = p.rows[j];
+            if (p.owner_writes && j < p.n_up) {
+              const int f = r / p.Nqf, g = r - f * p.Nqf;
+              const int64_t pt = (int64_t)g * nface + fid[f * kTcM + tid];
+              p.out[pt] = p.R[pt] + acc;
+            } else {
+              p.Y32[(int64_t)r * ne + e] = acc;
+            }
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "r"(p.ncols));
+}
+
+}  // namespace
+
+bool tc_supported(const Ctx& c) {
+  // one shared operator, N (rows) and K (face points) small enough for one MMA tile
+  return c.shared_op && c.n_rows >= 1 && c.n_rows <= 256 && c.NQFS <= 256;
+}
+
+cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
+  TcParams p;
+  p.nel = c.nel;
+  p.nface = c.nface;
+  p.NQFS = c.NQFS;
+  p.Nqf = c.Nqf;
+  p.F = c.F;
+  p.n_rows = c.n_rows;
+  p.n_up = c.n_up;
+  p.owner_writes = (c.pde == EHDG_TRANSPORT) ? 1 : 0;
+  p.bf16 = (c.precision == EHDG_MIXED_BF16) ? 1 : 0;
+  const int kstep = p.bf16 ? 16 : 8;                // elements per 32-byte MMA K step
+  p.Kp = (c.NQFS + kstep - 1) / kstep * kstep;
+  p.Np = (c.n_rows + 15) / 16 * 16;
+  if (p.Np < 16) p.Np = 16;
+  int ncols = 32;
+  while (ncols < p.Np) ncols *= 2;
+  p.ncols = ncols;
+  // instruction descriptor: D f32, A/B format, K-major A and B, N>>3, M>>4
+  const uint32_t fmt = p.bf16 ? 1u : 2u;            // BF16 (kind::f16) or TF32
+  p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(p.Np >> 3) << 17) |
+            ((uint32_t)(kTcM >> 4) << 24);
+  p.rows = c.rows;
+  p.elem_face = c.geo.elem_face;
+  p.Hy32 = c.Hy32;
+  p.R = c.R32;
+  p.in = in;
+  p.out = out;
+  p.Y32 = c.Y32;
+  p.err = c.tc_err;
+  const int esize = p.bf16 ? 2 : 4;
+  const size_t smem = (size_t)(p.Np + kTcM) * p.Kp * esize + sizeof(int) * c.F * kTcM + 1024;
+  cudaError_t err =
+      cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int bpsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_sweep_tc, kTcM, smem) !=
+          cudaSuccess || bpsm < 1) {
+    cudaGetLastError();
+    bpsm = 1;
+  }
+  if (bpsm > 512 / ncols) bpsm = 512 / ncols;        // TMEM: 512 columns per SM
+  const int64_t ntiles = (c.nel + kTcM - 1) / kTcM;
+  int64_t grid = (int64_t)bpsm * device_sms();
+  if (grid > ntiles) grid = ntiles;
+  k_sweep_tc<<<(int)grid, kTcM, smem, c.stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace ehdg

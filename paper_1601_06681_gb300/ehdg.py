@@ -20,7 +20,7 @@ STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "DI
           6: "TIMEOUT", 7: "UNSUPPORTED"}
 PDE = {"transport": 0, "sw": 1}
 SCHEME = {"be": 0, "cn": 1, "steady": 2}
-PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2}
+PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3}
 FACE_INTERIOR, FACE_DIRICHLET, FACE_WALL = 0, 1, 2
 
 
@@ -41,7 +41,7 @@ class ProblemDesc(C.Structure):
     _fields_ = [("pde", C.c_int), ("p", C.c_int), ("scheme", C.c_int), ("dt", C.c_double),
                 ("tol", C.c_double), ("max_iter", C.c_int), ("precision", C.c_int),
                 ("beta_const", C.POINTER(C.c_double)), ("beta_nodes", C.POINTER(C.c_double)),
-                ("Phi", C.c_double)]
+                ("Phi", C.c_double), ("inner_sweeps", C.c_int)]
 
 
 class Info(C.Structure):
@@ -210,7 +210,8 @@ class Solver:
     """One eHDG problem on the GPU (wraps an ehdg_ctx)."""
 
     def __init__(self, mesh, p, pde="transport", scheme="be", dt=1.0, tol=1e-10, max_iter=1000,
-                 beta_const=None, beta_nodes=None, Phi=1.0, precision="fp64", stream=None):
+                 beta_const=None, beta_nodes=None, Phi=1.0, precision="fp64", inner_sweeps=0,
+                 stream=None):
         lib = load()
         self.mesh = mesh if isinstance(mesh, Mesh) else Mesh(mesh)
         self._beta_const = None if beta_const is None else np.ascontiguousarray(beta_const, np.float64)
@@ -219,7 +220,8 @@ class Solver:
             PDE[pde], int(p), SCHEME[scheme], float(dt), float(tol), int(max_iter),
             PRECISION[precision],
             None if self._beta_const is None else _ptr(self._beta_const, C.c_double),
-            None if self._beta_nodes is None else _ptr(self._beta_nodes, C.c_double), float(Phi))
+            None if self._beta_nodes is None else _ptr(self._beta_nodes, C.c_double), float(Phi),
+            int(inner_sweeps))
         if stream is None:
             s = None
         elif isinstance(stream, int):

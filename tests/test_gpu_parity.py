@@ -216,3 +216,74 @@ def test_device_pointer_io_matches_host_io(ehdg):
         u, uh = s.get_state()
     assert np.array_equal(du.cpu().numpy(), u)
     assert np.array_equal(duh.cpu().numpy(), uh)
+
+
+# ---------------------------------------------------------------------------
+# mixed precision: FP32 inner sweeps + FP64 defect correction
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["2d_be_const", "2d_be_zero_component", "2d_cn_variable",
+                                  "2d_cn_variable_p4", "3d_be_const", "sw_be", "2d_graded_mesh"])
+def test_mixed_precision_reaches_fp64_solution(ehdg, name):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    n_steps = 3
+    args = dict(kw)
+    with ehdg.Solver(mesh, p, tol=1e-12, max_iter=400, precision="fp32", inner_sweeps=6,
+                     **args) as s:
+        if g is not None:
+            s.set_boundary(g)
+        s.set_state(u0)
+        iters = s.run(n_steps)
+        u, uh = s.get_state()
+        hist = s.residual_history()
+    ou, ouh, oiters, _ = prob.run(u0, n_steps, g_of_t=(None if g is None else (lambda t: g)),
+                                  tol=1e-13, max_iter=2000)
+    assert hist[-1] < 1e-12
+    assert rel(u, ou) < 1e-10
+    assert rel(uh, ouh) < 1e-10
+    # the correction makes every FP64 sweep count for several
+    assert sum(iters) < sum(oiters)
+
+
+def test_mixed_fixed_iterations_are_deterministic(ehdg):
+    mesh, p, kw, prob, u0, g = make_case("2d_cn_variable")
+    outs = []
+    for _ in range(2):
+        with ehdg.Solver(mesh, p, tol=1e-10, max_iter=50, precision="fp32", **kw) as s:
+            s.set_boundary(g)
+            s.set_state(u0)
+            s.step_fixed(3)
+            outs.append(s.get_state())
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+
+
+# ---------------------------------------------------------------------------
+# tensor-core (tcgen05) correction sweeps: TF32 and BF16 operands, FP32 accumulate
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("precision", ["tf32", "bf16"])
+@pytest.mark.parametrize("name", ["2d_be_const", "2d_be_zero_component", "3d_be_const",
+                                  "3d_be_const_p3", "sw_be_p3"])
+def test_tensor_core_mixed_reaches_fp64_solution(ehdg, name, precision):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    n_steps = 2
+    with ehdg.Solver(mesh, p, tol=1e-12, max_iter=400, precision=precision, inner_sweeps=6,
+                     **kw) as s:
+        if g is not None:
+            s.set_boundary(g)
+        s.set_state(u0)
+        iters = s.run(n_steps)
+        u, uh = s.get_state()
+    ou, ouh, oiters, _ = prob.run(u0, n_steps, g_of_t=(None if g is None else (lambda t: g)),
+                                  tol=1e-13, max_iter=2000)
+    assert rel(u, ou) < 1e-10
+    assert rel(uh, ouh) < 1e-10
+    assert sum(iters) < sum(oiters)
+
+
+def test_tensor_core_precision_needs_shared_operator(ehdg):
+    mesh, p, kw, prob, u0, g = make_case("2d_cn_variable")
+    with pytest.raises(ehdg.EhdgError) as ei:
+        ehdg.Solver(mesh, p, precision="tf32", **kw)
+    assert ei.value.status == 7
