@@ -46,7 +46,13 @@ def parse():
     ap.add_argument("--time-steps", type=int, default=50)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--workload", default="transport2d_varbeta",
+                    choices=["transport2d_varbeta", "transport3d", "sw2d", "transport2d_small",
+                             "batch"],
+                    help="transport2d_varbeta is the benchmark; the others print a "
+                         "time-to-tolerance comparison of FP64 and mixed precision")
     ap.add_argument("--inner-sweeps", type=int, default=8)
+    ap.add_argument("--n-inst", type=int, default=256)
     return ap.parse_args()
 
 
@@ -378,10 +384,139 @@ def _beta_nodes(ehdg, mesh, wl):
     return wl.beta_nodes(X)
 
 
+# ---------------------------------------------------------------------------
+# other workloads: FP64 versus mixed precision, time to the same tolerance
+# ---------------------------------------------------------------------------
+def compare_workload(args):
+    import torch
+    from paper_1601_06681_gb300 import build, ehdg
+    from paper_1601_06681_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    build.build()
+    ehdg.load()
+    stream = torch.cuda.current_stream()
+    if args.workload == "transport3d":
+        wl = W.transport_3d(n=(args.n, args.n, args.n), p=3, n_steps=args.time_steps)
+        precisions = ["fp64", "tf32", "bf16", "fp32"]
+    elif args.workload == "sw2d":
+        # dt at which Theorem 2 holds on this mesh: h / (dt (p+1)(p+2)) = 3.9, C = 0.34
+        wl = W.sw_2d(n=(args.n, args.n), p=3, dt=2.5e-5, n_steps=args.time_steps)
+        precisions = ["fp64", "tf32", "bf16", "fp32"]
+    else:
+        wl = W.transport_2d_small(n=(args.n, args.n), p=2, n_steps=args.time_steps)
+        precisions = ["fp64", "tf32", "fp32"]
+    mesh = ehdg.ehdg_mesh_structured(wl.n, boundary_tag=(2 if wl.pde == "sw" else 1))
+    results = {}
+    ref = None
+    for prec in precisions:
+        kw = dict(pde=wl.pde, scheme=wl.scheme, dt=wl.dt, tol=wl.tol, max_iter=400,
+                  precision=prec, inner_sweeps=args.inner_sweeps, stream=stream)
+        if wl.pde == "sw":
+            kw["Phi"] = wl.Phi
+        else:
+            kw["beta_const"] = wl.beta_const
+        s = ehdg.Solver(mesh, wl.p, **kw)
+        X, XF = s.node_coords(), s.face_point_coords()
+        u0 = torch.from_numpy(np.ascontiguousarray(wl.initial(X))).cuda()
+        gs = [torch.from_numpy(np.ascontiguousarray(wl.boundary(XF, k * wl.dt))).cuda()
+              for k in range(wl.n_steps + 1)]
+
+        def one_run():
+            s.set_boundary(gs[0])
+            s.set_state(u0)
+            its = 0
+            for k in range(wl.n_steps):
+                if wl.pde != "sw":
+                    s.set_boundary(gs[k + 1])
+                it, _, _ = s.step()
+                its += it
+            return its
+
+        one_run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = 0
+        for _ in range(args.steps):
+            its = one_run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        u, _ = s.get_state()
+        if ref is None:
+            ref = u
+        results[prec] = {"ms_per_run": ms, "fp64_sweeps_per_run": its,
+                         "rel_l2_vs_fp64": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
+                         "speedup_vs_fp64": None}
+        s.close()
+    for prec in precisions:
+        results[prec]["speedup_vs_fp64"] = results["fp64"]["ms_per_run"] / results[prec]["ms_per_run"]
+    info = {"workload": wl.name, "n_elem": int(np.prod(wl.n)), "p": wl.p, "dt": wl.dt,
+            "time_steps": wl.n_steps, "tol": wl.tol, "inner_sweeps": args.inner_sweeps}
+    print(json.dumps({"metric": "time-to-tol per run, mixed vs FP64", "config": info,
+                      "results": results}), flush=True)
+
+
+def batch_workload(args):
+    """Config 5: independent 2D transport instances (N 8..128, p 1..5) stepped
+    together, one graph launch per time step; FP64 versus mixed precision."""
+    import torch
+    from paper_1601_06681_gb300 import build, ehdg
+    from paper_1601_06681_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    build.build()
+    ehdg.load()
+    stream = torch.cuda.current_stream()
+    wls = W.batched_mix(n_inst=args.n_inst)
+    out = {}
+    for prec in ["fp64", "tf32"]:
+        specs, inputs = [], []
+        for wl in wls:
+            mesh = ehdg.ehdg_mesh_structured(wl.n)
+            specs.append(dict(mesh=mesh, p=wl.p, scheme=wl.scheme, dt=wl.dt, tol=wl.tol,
+                              max_iter=400, beta_const=wl.beta_const, precision=prec,
+                              inner_sweeps=args.inner_sweeps))
+        t0 = time.perf_counter()
+        b = ehdg.Batch(specs, stream=stream)
+        setup = time.perf_counter() - t0
+        for wl, s in zip(wls, b.instances):
+            X, XF = s.node_coords(), s.face_point_coords()
+            s.set_boundary(wl.u0_fn(XF))
+            inputs.append(torch.from_numpy(np.ascontiguousarray(wl.initial(X))).cuda())
+
+        def one_run():
+            for s, u0 in zip(b.instances, inputs):
+                s.set_state(u0)
+            return b.run(wls[0].n_steps)
+
+        one_run()                                     # warm-up (captures the graph)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        iters, times = one_run()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        out[prec] = {"instances_per_s": len(wls) / wall, "wall_s": wall, "setup_s": setup,
+                     "p50_instance_ms": float(np.percentile(times, 50) * 1e3),
+                     "p99_instance_ms": float(np.percentile(times, 99) * 1e3),
+                     "sweeps_total": int(iters.sum())}
+        b.close()
+    out["tf32"]["speedup_vs_fp64"] = out["fp64"]["wall_s"] / out["tf32"]["wall_s"]
+    info = {"workload": f"batched_mix_{args.n_inst}", "time_steps": wls[0].n_steps,
+            "elements_total": int(sum(np.prod(w.n) for w in wls))}
+    print(json.dumps({"metric": "instances/s (one graph launch per step)", "config": info,
+                      "results": out}), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "batch":
+        batch_workload(args)
+        return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "transport2d_varbeta":
+        compare_workload(args)
     else:
         run_ours(args)
 

@@ -174,6 +174,24 @@ ehdg_status ehdg_get_state(ehdg_ctx ctx, double* u, double* uhat, int on_device)
 /* Residual history r_0, r_1, ... of the last step (host buffer of cap entries). */
 ehdg_status ehdg_get_residual_history(ehdg_ctx ctx, double* buf, int64_t cap, int64_t* n_out);
 
+/* Batched form: n independent problems (each its own mesh, degree, velocity,
+ * precision) stepped together. Every implicit step of every instance is
+ * captured as an independent branch of ONE CUDA graph (each branch with its
+ * own device-side convergence loop), so one graph launch advances all
+ * instances by one time step, running them concurrently. */
+typedef struct ehdg_batch_s* ehdg_batch;
+ehdg_status ehdg_batch_create(int n, const ehdg_mesh_desc* meshes, const ehdg_problem_desc* probs,
+                              void* cuda_stream, ehdg_batch* out);
+/* The context of instance i (owned by the batch): set its state, boundary
+ * data and forcing, read its results, with the single-problem calls. */
+ehdg_status ehdg_batch_instance(ehdg_batch b, int i, ehdg_ctx* out);
+/* n_steps steps of every instance. iters [n][n_steps] (may be NULL) receives
+ * each step's eHDG iterations; inst_time_s [n] (may be NULL) the device time
+ * of each instance's branch, summed over the steps (%globaltimer). Returns
+ * the first non-OK status of any instance. */
+ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_time_s);
+void ehdg_batch_destroy(ehdg_batch b);
+
 /* FP64 residual of Algorithm 1's convergence check (Sec. 3, "check
  * convergence"): out[0] = sqrt(sum_i w[i] (a[i] - b[i])^2) over n entries.
  * With a, b two trace iterates uhat^{k+1}, uhat^k at the face points and w the

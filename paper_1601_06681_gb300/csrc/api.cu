@@ -17,6 +17,18 @@ struct ehdg_ctx_s {
   Ctx c;
 };
 
+struct ehdg_batch_s {
+  std::vector<ehdg_ctx> inst;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> branch;
+  cudaStream_t cap = nullptr, body = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<char> graph_force;
+  unsigned long long* t_start = nullptr;
+  unsigned long long* t_acc = nullptr;
+};
+
 namespace {
 
 thread_local std::string g_err;
@@ -214,57 +226,42 @@ void destroy_graph(Ctx& c) {
   c.graph = nullptr;
 }
 
-// Capture one implicit step: reset, step RHS, initial trace, then a WHILE node
-// whose body is {element sweep, trace update}; the trace kernel's last block
-// sets the condition (continue while r_k >= tol and k < max_iter), so the
+// Append one implicit step of context c to the graph being captured on
+// stream s: reset, step RHS, initial trace, then a WHILE node whose body is
+// {element sweep, trace update} (mixed precision: an FP64 sweep before the
+// loop and {correction, FP64 sweep} as the body); the sweep's last block sets
+// the condition (continue while r_k >= tol and k < max_iter), so the
 // iteration runs without a host round trip; then the end-of-step kernels.
-ehdg_status build_graph(Ctx& c) {
-  destroy_graph(c);
-  if (!c.cap_stream) CK(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
-  if (!c.body_stream) CK(cudaStreamCreateWithFlags(&c.body_stream, cudaStreamNonBlocking));
+// body_stream is a spare stream used to capture the loop body.
+ehdg_status capture_step(Ctx& c, cudaStream_t s, cudaStream_t body_stream) {
   cudaStream_t user = c.stream;
   struct Restore {
     Ctx& c;
     cudaStream_t s;
     ~Restore() { c.stream = s; }
   } restore{c, user};
-  c.stream = c.cap_stream;
-  CK(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeRelaxed));
+  c.stream = s;
   cudaError_t err = cudaSuccess;
-  cudaGraph_t g = nullptr;
-  auto abort_capture = [&](cudaError_t e, const char* what) {
-    cudaGraph_t junk = nullptr;
-    cudaStreamEndCapture(c.cap_stream, &junk);
-    if (junk) cudaGraphDestroy(junk);
-    cudaGetLastError();
-    return cuda_fail(e, what);
-  };
-  if ((err = launch_reset_iter(c)) != cudaSuccess) return abort_capture(err, "capture reset");
-  if ((err = launch_step(c)) != cudaSuccess) return abort_capture(err, "capture step");
-  if ((err = launch_face(c, kFaceInitial)) != cudaSuccess) return abort_capture(err, "capture face");
+  if ((err = launch_reset_iter(c)) != cudaSuccess) return cuda_fail(err, "capture reset");
+  if ((err = launch_step(c)) != cudaSuccess) return cuda_fail(err, "capture step");
+  if ((err = launch_face(c, kFaceInitial)) != cudaSuccess) return cuda_fail(err, "capture face");
   cudaStreamCaptureStatus cst;
+  cudaGraph_t g = nullptr;
   cudaGraphConditionalHandle handle;
+  err = cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, nullptr, nullptr, nullptr);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaStreamGetCaptureInfo");
+  err = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGraphConditionalHandleCreate");
+  c.handle = handle;
   if (c.mixed) {
-    // the first FP64 sweep runs before the loop; the loop body is
-    // {correction, FP64 sweep}; the sweep's last block sets the condition
-    err = cudaStreamGetCaptureInfo(c.cap_stream, &cst, nullptr, &g, nullptr, nullptr, nullptr);
-    if (err != cudaSuccess) return abort_capture(err, "cudaStreamGetCaptureInfo");
-    err = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
-    if (err != cudaSuccess) return abort_capture(err, "cudaGraphConditionalHandleCreate");
-    c.handle = handle;
     err = (c.pde == EHDG_TRANSPORT) ? launch_sweep_fused(c, 1) : launch_elem(c);
     if (err == cudaSuccess && c.pde != EHDG_TRANSPORT) err = launch_face(c, kFaceIterate, 1);
-    if (err != cudaSuccess) return abort_capture(err, "capture first FP64 sweep");
+    if (err != cudaSuccess) return cuda_fail(err, "capture first FP64 sweep");
   }
   const cudaGraphNode_t* deps = nullptr;
   size_t ndeps = 0;
-  err = cudaStreamGetCaptureInfo(c.cap_stream, &cst, nullptr, &g, &deps, nullptr, &ndeps);
-  if (err != cudaSuccess) return abort_capture(err, "cudaStreamGetCaptureInfo");
-  if (!c.mixed) {
-    err = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
-    if (err != cudaSuccess) return abort_capture(err, "cudaGraphConditionalHandleCreate");
-    c.handle = handle;
-  }
+  err = cudaStreamGetCaptureInfo(s, &cst, nullptr, &g, &deps, nullptr, &ndeps);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaStreamGetCaptureInfo");
   cudaGraphNodeParams cp = {};
   cp.type = cudaGraphNodeTypeConditional;
   cp.conditional.handle = handle;
@@ -272,42 +269,57 @@ ehdg_status build_graph(Ctx& c) {
   cp.conditional.size = 1;
   cudaGraphNode_t cond;
   err = cudaGraphAddNode(&cond, g, deps, nullptr, ndeps, &cp);
-  if (err != cudaSuccess) return abort_capture(err, "cudaGraphAddNode(while)");
-  err = cudaStreamUpdateCaptureDependencies(c.cap_stream, &cond, nullptr, 1,
-                                            cudaStreamSetCaptureDependencies);
-  if (err != cudaSuccess) return abort_capture(err, "cudaStreamUpdateCaptureDependencies");
+  if (err != cudaSuccess) return cuda_fail(err, "cudaGraphAddNode(while)");
+  err = cudaStreamUpdateCaptureDependencies(s, &cond, nullptr, 1, cudaStreamSetCaptureDependencies);
+  if (err != cudaSuccess) return cuda_fail(err, "cudaStreamUpdateCaptureDependencies");
   cudaGraph_t body = cp.conditional.phGraph_out[0];
-  err = cudaStreamBeginCaptureToGraph(c.body_stream, body, nullptr, nullptr, 0,
+  err = cudaStreamBeginCaptureToGraph(body_stream, body, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeRelaxed);
-  if (err != cudaSuccess) return abort_capture(err, "cudaStreamBeginCaptureToGraph");
-  c.stream = c.body_stream;
-  cudaError_t e1, e2;
-  if (c.mixed) {
-    cudaError_t ec = launch_correction(c, nullptr);
-    if (ec != cudaSuccess) {
-      cudaGraph_t junk = body;
-      cudaStreamEndCapture(c.body_stream, &junk);
-      c.stream = c.cap_stream;
-      return abort_capture(ec, "capture correction");
+  if (err != cudaSuccess) return cuda_fail(err, "cudaStreamBeginCaptureToGraph");
+  c.stream = body_stream;
+  cudaError_t e2 = cudaSuccess;
+  if (c.mixed) e2 = launch_correction(c, nullptr);
+  if (e2 == cudaSuccess) {
+    if (c.pde == EHDG_TRANSPORT) {
+      e2 = launch_sweep_fused(c, 1);
+    } else {
+      e2 = launch_elem(c);
+      if (e2 == cudaSuccess) e2 = launch_face(c, kFaceIterate, 1);
     }
   }
-  if (c.pde == EHDG_TRANSPORT) {
-    e1 = cudaSuccess;
-    e2 = launch_sweep_fused(c, 1);
-  } else {
-    e1 = launch_elem(c);
-    e2 = (e1 == cudaSuccess) ? launch_face(c, kFaceIterate, 1) : e1;
-  }
-  cudaError_t e3 = cudaStreamEndCapture(c.body_stream, &body);
-  c.stream = c.cap_stream;
-  if (e2 != cudaSuccess) return abort_capture(e2, "capture loop body");
-  if (e3 != cudaSuccess) return abort_capture(e3, "end body capture");
-  if ((err = launch_final(c)) != cudaSuccess) return abort_capture(err, "capture final");
+  cudaError_t e3 = cudaStreamEndCapture(body_stream, &body);
+  c.stream = s;
+  if (e2 != cudaSuccess) return cuda_fail(e2, "capture loop body");
+  if (e3 != cudaSuccess) return cuda_fail(e3, "end body capture");
+  if ((err = launch_final(c)) != cudaSuccess) return cuda_fail(err, "capture final");
   if (c.have_force &&
       (err = cudaMemcpyAsync(c.force_old, c.force, sizeof(double) * c.n * c.nel,
                              cudaMemcpyDeviceToDevice, c.stream)) != cudaSuccess)
-    return abort_capture(err, "capture forcing copy");
-  if ((err = launch_step_end(c)) != cudaSuccess) return abort_capture(err, "capture step end");
+    return cuda_fail(err, "capture forcing copy");
+  if ((err = launch_step_end(c)) != cudaSuccess) return cuda_fail(err, "capture step end");
+  return EHDG_OK;
+}
+
+void abort_capture(cudaStream_t s) {
+  cudaGraph_t junk = nullptr;
+  cudaStreamEndCapture(s, &junk);
+  if (junk) cudaGraphDestroy(junk);
+  cudaGetLastError();
+}
+
+ehdg_status build_graph(Ctx& c) {
+  destroy_graph(c);
+  if (!c.cap_stream) CK(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
+  if (!c.body_stream) CK(cudaStreamCreateWithFlags(&c.body_stream, cudaStreamNonBlocking));
+  CK(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeRelaxed));
+  const ehdg_status st = capture_step(c, c.cap_stream, c.body_stream);
+  if (st != EHDG_OK) {
+    const std::string msg = g_err;
+    abort_capture(c.cap_stream);
+    g_err = msg;
+    return st;
+  }
+  cudaGraph_t g = nullptr;
   CK(cudaStreamEndCapture(c.cap_stream, &g));
   c.graph = g;
   CK(cudaGraphInstantiate(&c.gexec, g, 0));
@@ -1019,6 +1031,175 @@ ehdg_status ehdg_get_residual_history(ehdg_ctx h, double* buf, int64_t cap, int6
   }
   if (n_out) *n_out = c.last_iters;
   return EHDG_OK;
+}
+
+
+static void batch_destroy_graph(ehdg_batch b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;
+}
+
+// One graph: fork from a start event into one branch stream per instance,
+// capture each instance's step there (stamped with %globaltimer), join back.
+static ehdg_status batch_build_graph(ehdg_batch b) {
+  batch_destroy_graph(b);
+  const int n = (int)b->inst.size();
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins(n, nullptr);
+  CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+  for (int i = 0; i < n; ++i) CK(cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming));
+  auto cleanup_events = [&]() {
+    cudaEventDestroy(fork);
+    for (auto e : joins) cudaEventDestroy(e);
+  };
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cleanup_events();
+    return cuda_fail(e, "batch capture");
+  }
+  e = cudaEventRecord(fork, b->cap);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) {
+    Ctx& c = b->inst[i]->c;
+    cudaStream_t s = b->branch[i];
+    e = cudaStreamWaitEvent(s, fork, 0);
+    if (e == cudaSuccess) e = launch_stamp(s, b->t_start, b->t_acc, i, 0);
+    if (e != cudaSuccess) break;
+    const ehdg_status st = capture_step(c, s, b->body);
+    if (st != EHDG_OK) {
+      const std::string msg = g_err;
+      for (int j = 0; j <= i; ++j) {
+        cudaEventRecord(joins[j], b->branch[j]);
+        cudaStreamWaitEvent(b->cap, joins[j], 0);
+      }
+      abort_capture(b->cap);
+      cleanup_events();
+      g_err = msg;
+      return st;
+    }
+    e = launch_stamp(s, b->t_start, b->t_acc, i, 1);
+    if (e == cudaSuccess) e = cudaEventRecord(joins[i], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, joins[i], 0);
+    b->graph_force[i] = c.have_force ? 1 : 0;
+  }
+  if (e != cudaSuccess) {
+    abort_capture(b->cap);
+    cleanup_events();
+    return cuda_fail(e, "batch capture");
+  }
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->cap, &g);
+  cleanup_events();
+  if (e != cudaSuccess) return cuda_fail(e, "batch end capture");
+  b->graph = g;
+  CK(cudaGraphInstantiate(&b->exec, g, 0));
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_batch_create(int n, const ehdg_mesh_desc* meshes, const ehdg_problem_desc* probs,
+                              void* stream, ehdg_batch* out) {
+  if (!out || n < 1 || !meshes || !probs) return fail(EHDG_ERR_INVALID, "bad batch arguments");
+  *out = nullptr;
+  ehdg_batch b = new (std::nothrow) ehdg_batch_s();
+  if (!b) return fail(EHDG_ERR_OOM, "host allocation failed");
+  b->stream = (cudaStream_t)stream;
+  auto bail = [&](ehdg_status s) {
+    const std::string msg = g_err;
+    ehdg_batch_destroy(b);
+    g_err = msg;
+    return s;
+  };
+  for (int i = 0; i < n; ++i) {
+    ehdg_ctx h = nullptr;
+    const ehdg_status st = ehdg_create(&meshes[i], &probs[i], stream, &h);
+    if (st != EHDG_OK) {
+      g_err = "instance " + std::to_string(i) + ": " + g_err;
+      return bail(st);
+    }
+    b->inst.push_back(h);
+  }
+  b->branch.resize(n, nullptr);
+  for (int i = 0; i < n; ++i)
+    if (cudaStreamCreateWithFlags(&b->branch[i], cudaStreamNonBlocking) != cudaSuccess)
+      return bail(cuda_fail(cudaGetLastError(), "branch stream"));
+  if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "capture stream"));
+  if (cudaMalloc(&b->t_start, sizeof(unsigned long long) * n) != cudaSuccess ||
+      cudaMalloc(&b->t_acc, sizeof(unsigned long long) * n) != cudaSuccess)
+    return bail(fail(EHDG_ERR_OOM, "cudaMalloc failed"));
+  b->graph_force.assign(n, 0);
+  *out = b;
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_batch_instance(ehdg_batch b, int i, ehdg_ctx* out) {
+  if (!b || !out || i < 0 || i >= (int)b->inst.size()) return fail(EHDG_ERR_INVALID, "bad instance");
+  *out = b->inst[i];
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_time_s) {
+  if (!b || n_steps < 0) return fail(EHDG_ERR_INVALID, "bad argument");
+  const int n = (int)b->inst.size();
+  if (n_steps == 0) return EHDG_OK;
+  bool rebuild = !b->exec;
+  for (int i = 0; i < n; ++i) {
+    Ctx& c = b->inst[i]->c;
+    const int cap = c.step_cap;
+    TRY(ensure_step_arrays(c, n_steps));
+    if (c.step_cap != cap || (c.have_force ? 1 : 0) != b->graph_force[i]) rebuild = true;
+  }
+  if (rebuild) TRY(batch_build_graph(b));
+  // the instance contexts run on the batch's stream: order their earlier work first
+  CK(cudaStreamSynchronize(b->stream));
+  CK(cudaMemsetAsync(b->t_acc, 0, sizeof(unsigned long long) * n, b->stream));
+  for (int i = 0; i < n; ++i)
+    CK(cudaMemsetAsync(&b->inst[i]->c.it->step, 0, sizeof(int), b->stream));
+  for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(b->exec, b->stream));
+  std::vector<unsigned long long> acc(n);
+  CK(cudaMemcpyAsync(acc.data(), b->t_acc, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost,
+                     b->stream));
+  ehdg_status first = EHDG_OK;
+  for (int i = 0; i < n; ++i) {
+    Ctx& c = b->inst[i]->c;
+    c.step_iters_h.resize(n_steps);
+    c.step_status_h.resize(n_steps);
+    CK(cudaMemcpyAsync(c.step_iters_h.data(), c.step_iters, sizeof(int) * n_steps,
+                       cudaMemcpyDeviceToHost, b->stream));
+    CK(cudaMemcpyAsync(c.step_status_h.data(), c.step_status, sizeof(int) * n_steps,
+                       cudaMemcpyDeviceToHost, b->stream));
+  }
+  CK(cudaStreamSynchronize(b->stream));
+  for (int i = 0; i < n; ++i) {
+    Ctx& c = b->inst[i]->c;
+    for (int s = 0; s < n_steps; ++s) {
+      if (iters) iters[(int64_t)i * n_steps + s] = c.step_iters_h[s];
+      if (first == EHDG_OK && c.step_status_h[s] != EHDG_OK) {
+        first = (ehdg_status)c.step_status_h[s];
+        g_err = "instance " + std::to_string(i) + " step " + std::to_string(s) + ": status " +
+                std::to_string(c.step_status_h[s]);
+      }
+    }
+    c.last_iters = std::min(c.step_iters_h[n_steps - 1], c.max_iter);
+    if (inst_time_s) inst_time_s[i] = (double)acc[i] * 1e-9;
+  }
+  return first;
+}
+
+void ehdg_batch_destroy(ehdg_batch b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_destroy_graph(b);
+  for (auto s : b->branch)
+    if (s) cudaStreamDestroy(s);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  if (b->body) cudaStreamDestroy(b->body);
+  if (b->t_start) cudaFree(b->t_start);
+  if (b->t_acc) cudaFree(b->t_acc);
+  for (auto h : b->inst) ehdg_destroy(h);
+  delete b;
 }
 
 }  // extern "C"

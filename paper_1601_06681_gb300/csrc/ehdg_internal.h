@@ -164,6 +164,8 @@ cudaError_t launch_soa_to_aos(const double* src, double* dst, int64_t outer, int
 cudaError_t launch_reset_iter(Ctx& c);
 cudaError_t launch_extract(Ctx& c);
 cudaError_t launch_step_end(Ctx& c);
+cudaError_t launch_stamp(cudaStream_t s, unsigned long long* t_start, unsigned long long* t_acc,
+                         int i, int end);
 cudaError_t launch_rows(Ctx& c);
 int face_grid_x(int64_t nface, int Nqf);   // blocks along faces of the trace kernel
 // fused transport sweep (sweep_fused.cu)

@@ -979,6 +979,21 @@ cudaError_t launch_step_end(Ctx& c) {
   return cudaGetLastError();
 }
 
+// Per-instance device time of a batched step: %globaltimer at the start of
+// the instance's branch, and the elapsed time added at its end.
+__global__ void k_stamp(unsigned long long* t_start, unsigned long long* t_acc, int i, int end) {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  if (end) t_acc[i] += t - t_start[i];
+  else t_start[i] = t;
+}
+
+cudaError_t launch_stamp(cudaStream_t s, unsigned long long* t_start, unsigned long long* t_acc,
+                         int i, int end) {
+  k_stamp<<<1, 1, 0, s>>>(t_start, t_acc, i, end);
+  return cudaGetLastError();
+}
+
 __global__ void k_reset(IterState* it) {
   it->k = 0;
   it->cont = 1;

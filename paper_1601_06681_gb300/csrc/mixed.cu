@@ -56,20 +56,36 @@ __global__ void __launch_bounds__(32 * kLT) k_sweep_lp(const LpParams p) {
   const int64_t ntiles = (ne + 31) / 32;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e = tile * 32 + lane;
+    const bool live = e < ne;
+    const int nr = live ? (p.shared ? p.n_rows : p.nrows[e]) : 0;
+    const int nu = (live && p.owner_writes) ? (p.shared ? p.n_up : p.nup[e]) : 0;
+    // per-element operator: fetch the first pass's two rows now, so their
+    // latency overlaps the trace gather below (they do not depend on it)
+    float h1[NQ > 0 ? NQ : 1], h2[NQ > 0 ? NQ : 1];
+    if constexpr (NQ > 0) {
+      if (!p.shared) {
+        const int j = t, j2 = t + kLT;
+        const float* H1 = p.Hy32 + (int64_t)j * NQ * ne + e;
+        const float* H2 = p.Hy32 + (int64_t)j2 * NQ * ne + e;
+#pragma unroll
+        for (int c = 0; c < NQ; ++c) {
+          h1[c] = (j < nr) ? H1[c * ne] : 0.f;
+          h2[c] = (j2 < nr) ? H2[c * ne] : 0.f;
+        }
+      }
+    }
     __syncthreads();
-    if (e < ne)
+    if (live)
       for (int f = t; f < p.F; f += kLT) fid[f * 32 + lane] = p.elem_face[f * ne + e];
     __syncthreads();
-    if (e < ne) {
+    if (live) {
       for (int i = t; i < nq; i += kLT) {
         const int f = i / p.Nqf, g = i - f * p.Nqf;
         dl[i * 32 + lane] = p.in[g * nface + fid[f * 32 + lane]];
       }
     }
     __syncthreads();
-    if (e >= ne) continue;
-    const int nr = p.shared ? p.n_rows : p.nrows[e];
-    const int nu = p.owner_writes ? (p.shared ? p.n_up : p.nup[e]) : 0;
+    if (!live) continue;
     // two rows per pass (j and j + kLT) so twice as many loads are in flight
     for (int j = t; j < nr; j += 2 * kLT) {
       const int j2 = j + kLT;
@@ -89,16 +105,25 @@ __global__ void __launch_bounds__(32 * kLT) k_sweep_lp(const LpParams p) {
       } else {
         r = p.rowid[j * ne + e];
         r2 = two ? p.rowid[j2 * ne + e] : r;
-        const float* H1 = p.Hy32 + (int64_t)j * nq * ne + e;
-        const float* H2 = p.Hy32 + (int64_t)(two ? j2 : j) * nq * ne + e;
         if constexpr (NQ > 0) {
+          if (j != t) {                       // later passes: fetch now
+            const float* H1 = p.Hy32 + (int64_t)j * NQ * ne + e;
+            const float* H2 = p.Hy32 + (int64_t)j2 * NQ * ne + e;
+#pragma unroll
+            for (int c = 0; c < NQ; ++c) {
+              h1[c] = H1[c * ne];
+              h2[c] = two ? H2[c * ne] : 0.f;
+            }
+          }
 #pragma unroll
           for (int c = 0; c < NQ; ++c) {
             const float d = dl[c * 32 + lane];
-            a = fmaf(H1[c * ne], d, a);
-            b = fmaf(H2[c * ne], d, b);
+            a = fmaf(h1[c], d, a);
+            b = fmaf(h2[c], d, b);
           }
         } else {
+          const float* H1 = p.Hy32 + (int64_t)j * nq * ne + e;
+          const float* H2 = p.Hy32 + (int64_t)(two ? j2 : j) * nq * ne + e;
           for (int c = 0; c < nq; ++c) {
             const float d = dl[c * 32 + lane];
             a = fmaf(H1[c * ne], d, a);

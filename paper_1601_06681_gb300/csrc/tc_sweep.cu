@@ -113,16 +113,24 @@ __global__ void __launch_bounds__(kTcM) k_sweep_tc(const TcParams p) {
   bool failed = false;
   for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
     const int64_t e = tile * kTcM + tid;
-    // A = this tile's correction values at its elements' face points
+    // A = this tile's correction values at its elements' face points; loads
+    // are issued 16 at a time so they overlap instead of serialising
     if (e < ne)
       for (int f = 0; f < p.F; ++f) fid[f * kTcM + tid] = p.elem_face[f * ne + e];
-    for (int k = 0; k < p.Kp; ++k) {
-      float v = 0.f;
-      if (e < ne && k < p.NQFS) {
-        const int f = k / p.Nqf, g = k - f * p.Nqf;
-        v = p.in[g * nface + fid[f * kTcM + tid]];
+    for (int k0 = 0; k0 < p.Kp; k0 += 16) {
+      float v[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int k = k0 + q;
+        v[q] = 0.f;
+        if (e < ne && k < p.NQFS) {
+          const int f = k / p.Nqf, g = k - f * p.Nqf;
+          v[q] = p.in[g * nface + fid[f * kTcM + tid]];
+        }
       }
-      store_elem(As, tid, k, esize, sbo, v, p.bf16);
+#pragma unroll
+      for (int q = 0; q < 16; ++q)
+        if (k0 + q < p.Kp) store_elem(As, tid, k0 + q, esize, sbo, v[q], p.bf16);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
@@ -182,18 +190,30 @@ __global__ void __launch_bounds__(kTcM) k_sweep_tc(const TcParams p) {
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         if (e < ne) {
+          // residual values of the owned points first (16 loads in flight), then the writes
+          int64_t pt[16];
+          float rv[16];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int j = c0 + q;
+            pt[q] = -1;
+            rv[q] = 0.f;
+            if (j < p.n_rows && p.owner_writes && j < p.n_up) {
+              const int r = p.rows[j];
+              const int f = r / p.Nqf, g = r - f * p.Nqf;
+              pt[q] = (int64_t)g * nface + fid[f * kTcM + tid];
+              rv[q] = p.R[pt[q]];
+            }
+          }
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
             const int j = c0 + q;
             if (j >= p.n_rows) break;
             const float acc = __uint_as_float(v[q]);
-            const int r = p.rows[j];
-            if (p.owner_writes && j < p.n_up) {
-              const int f = r / p.Nqf, g = r - f * p.Nqf;
-              const int64_t pt = (int64_t)g * nface + fid[f * kTcM + tid];
-              p.out[pt] = p.R[pt] + acc;
+            if (pt[q] >= 0) {
+              p.out[pt[q]] = rv[q] + acc;
             } else {
-              p.Y32[(int64_t)r * ne + e] = acc;
+              p.Y32[(int64_t)p.rows[j] * ne + e] = acc;
             }
           }
         }
@@ -248,6 +268,9 @@ cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
   const size_t smem = (size_t)(p.Np + kTcM) * p.Kp * esize + sizeof(int) * c.F * kTcM + 1024;
   cudaError_t err =
       cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  // favour shared memory over L1 so several tiles' blocks fit per SM
+  err = cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (err != cudaSuccess) return err;
   int bpsm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_sweep_tc, kTcM, smem) !=

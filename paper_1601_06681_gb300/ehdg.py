@@ -77,6 +77,11 @@ _SIGS = [
     ("ehdg_set_profiling", C.c_int, [C.c_void_p, C.c_int]),
     ("ehdg_kernel_stats", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64),
                                     C.POINTER(C.c_double)]),
+    ("ehdg_batch_create", C.c_int, [C.c_int, C.POINTER(MeshDesc), C.POINTER(ProblemDesc),
+                                    C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("ehdg_batch_instance", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    ("ehdg_batch_run", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("ehdg_batch_destroy", None, [C.c_void_p]),
     ("ehdg_trace_residual", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                       C.c_void_p]),
     ("ehdg_trace_residual_noalloc", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64,
@@ -157,6 +162,14 @@ def ehdg_trace_residual_noalloc(a, b, w, out, stream=None):
     return out
 
 
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
 class Mesh:
     """A mesh descriptor that keeps its arrays alive (from a dict of arrays or
     from the library's structured-mesh builder)."""
@@ -211,30 +224,29 @@ class Solver:
 
     def __init__(self, mesh, p, pde="transport", scheme="be", dt=1.0, tol=1e-10, max_iter=1000,
                  beta_const=None, beta_nodes=None, Phi=1.0, precision="fp64", inner_sweeps=0,
-                 stream=None):
+                 stream=None, _handle=None):
         lib = load()
         self.mesh = mesh if isinstance(mesh, Mesh) else Mesh(mesh)
         self._beta_const = None if beta_const is None else np.ascontiguousarray(beta_const, np.float64)
         self._beta_nodes = None if beta_nodes is None else np.ascontiguousarray(beta_nodes, np.float64)
-        prob = ProblemDesc(
+        self.prob = ProblemDesc(
             PDE[pde], int(p), SCHEME[scheme], float(dt), float(tol), int(max_iter),
             PRECISION[precision],
             None if self._beta_const is None else _ptr(self._beta_const, C.c_double),
             None if self._beta_nodes is None else _ptr(self._beta_nodes, C.c_double), float(Phi),
             int(inner_sweeps))
-        if stream is None:
-            s = None
-        elif isinstance(stream, int):
-            s = C.c_void_p(stream)
-        else:
-            s = C.c_void_p(stream.cuda_stream)
-        h = C.c_void_p()
-        _check(lib.ehdg_create(C.byref(self.mesh.desc), C.byref(prob), s, C.byref(h)))
-        self._h = h
-        info = Info()
-        _check(lib.ehdg_get_info(h, C.byref(info)))
-        self.info = {k: getattr(info, k) for k, _ in Info._fields_}
         self.max_iter = int(max_iter)
+        self._owned = _handle is None
+        if _handle is not None:          # an instance of a batch (owned by the batch)
+            self._h = _handle
+        else:
+            s = _stream_ptr(stream)
+            h = C.c_void_p()
+            _check(lib.ehdg_create(C.byref(self.mesh.desc), C.byref(self.prob), s, C.byref(h)))
+            self._h = h
+        info = Info()
+        _check(lib.ehdg_get_info(self._h, C.byref(info)))
+        self.info = {k: getattr(info, k) for k, _ in Info._fields_}
 
     # sizes
     @property
@@ -321,8 +333,78 @@ class Solver:
         return out
 
     def close(self):
-        if getattr(self, "_h", None) is not None and self._h.value:
+        if getattr(self, "_owned", True) and getattr(self, "_h", None) is not None and self._h.value:
             load().ehdg_destroy(self._h)
+        self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Independent problems stepped together: one CUDA graph launch per time
+    step advances every instance (ehdg_batch_*). problems: list of dicts with
+    the Solver keyword arguments (mesh, p, pde, scheme, dt, tol, ...)."""
+
+    def __init__(self, problems, stream=None):
+        lib = load()
+        n = len(problems)
+        self._keep = []
+        meshes = (MeshDesc * n)()
+        probs = (ProblemDesc * n)()
+        self._specs = []
+        for i, kw in enumerate(problems):
+            kw = dict(kw)
+            mesh = kw.pop("mesh")
+            m = mesh if isinstance(mesh, Mesh) else Mesh(mesh)
+            bc = kw.get("beta_const")
+            bn = kw.get("beta_nodes")
+            bc = None if bc is None else np.ascontiguousarray(bc, np.float64)
+            bn = None if bn is None else np.ascontiguousarray(bn, np.float64)
+            self._keep += [m, bc, bn]
+            meshes[i] = m.desc
+            probs[i] = ProblemDesc(
+                PDE[kw.get("pde", "transport")], int(kw["p"]), SCHEME[kw.get("scheme", "be")],
+                float(kw.get("dt", 1.0)), float(kw.get("tol", 1e-10)), int(kw.get("max_iter", 1000)),
+                PRECISION[kw.get("precision", "fp64")],
+                None if bc is None else _ptr(bc, C.c_double),
+                None if bn is None else _ptr(bn, C.c_double), float(kw.get("Phi", 1.0)),
+                int(kw.get("inner_sweeps", 0)))
+            self._specs.append((m, kw))
+        h = C.c_void_p()
+        _check(lib.ehdg_batch_create(n, meshes, probs, _stream_ptr(stream), C.byref(h)))
+        self._h = h
+        self.n = n
+        self.instances = []
+        for i in range(n):
+            ih = C.c_void_p()
+            _check(lib.ehdg_batch_instance(h, i, C.byref(ih)))
+            m, kw = self._specs[i]
+            args = {k: v for k, v in kw.items() if k not in ("p",)}
+            self.instances.append(Solver(m, kw["p"], _handle=ih, **args))
+
+    def run(self, n_steps):
+        """(iters [n, n_steps], per-instance device seconds [n])."""
+        iters = np.zeros((self.n, n_steps), dtype=np.int32)
+        times = np.zeros(self.n)
+        _check(load().ehdg_batch_run(self._h, int(n_steps), iters.ctypes.data_as(C.c_void_p),
+                                     times.ctypes.data_as(C.c_void_p)))
+        return iters, times
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            for s in self.instances:
+                s._h = C.c_void_p()
+            load().ehdg_batch_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

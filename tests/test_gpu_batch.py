@@ -1,0 +1,73 @@
+"""Batched form: independent instances stepped by one CUDA graph launch per
+time step give the same results as solo runs (and as the oracle)."""
+import zlib
+
+import numpy as np
+import pytest
+
+from oracle.ehdg import Problem
+from oracle.geometry import face_point_coords, node_coords
+from paper_1601_06681_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ehdg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_06681_gb300 import build, ehdg as E
+    build.build()
+    E.load()
+    return E
+
+
+def instances(n=7, seed=77):
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nx, ny = int(rng.integers(3, 13)), int(rng.integers(3, 13))
+        p = int(rng.integers(1, 5))
+        th = rng.uniform(0, 2 * np.pi)
+        beta = rng.uniform(0.5, 1.5) * np.array([np.cos(th), np.sin(th)])
+        precision = ["fp64", "tf32", "fp32", "bf16"][i % 4]
+        mesh = W.structured_mesh((nx, ny))
+        prob = Problem(mesh, p, scheme="be", dt=0.01, beta_const=beta)
+        X = node_coords(mesh, p)
+        XF = face_point_coords(mesh, p, prob.ref.q)
+        c = rng.uniform(0.2, 0.8, 2)
+        s = rng.uniform(0.05, 0.15)
+        u0 = W.gaussian(X, c, s)[:, None, :]
+        g = W.gaussian(XF, c, s)
+        kw = dict(mesh=mesh, p=p, scheme="be", dt=0.01, tol=1e-12, max_iter=500,
+                  beta_const=beta, precision=precision, inner_sweeps=4)
+        out.append((kw, prob, u0, g))
+    return out
+
+
+def test_batch_matches_solo_runs_and_oracle(ehdg):
+    inst = instances()
+    n_steps = 3
+    with ehdg.Batch([kw for kw, _, _, _ in inst]) as b:
+        for (kw, prob, u0, g), s in zip(inst, b.instances):
+            s.set_boundary(g)
+            s.set_state(u0)
+        iters, times = b.run(n_steps)
+        batch_states = [s.get_state() for s in b.instances]
+    assert np.all(times > 0)
+    for i, (kw, prob, u0, g) in enumerate(inst):
+        args = dict(kw)
+        mesh = args.pop("mesh")
+        p = args.pop("p")
+        with ehdg.Solver(mesh, p, **args) as s:
+            s.set_boundary(g)
+            s.set_state(u0)
+            solo_iters = s.run(n_steps)
+            u, uh = s.get_state()
+        assert list(iters[i]) == solo_iters, i
+        assert np.array_equal(batch_states[i][0], u), i
+        assert np.array_equal(batch_states[i][1], uh), i
+        ou, _, _, _ = prob.run(u0, n_steps, g_of_t=lambda t: g, tol=1e-13, max_iter=2000)
+        err = np.linalg.norm(u - ou) / np.linalg.norm(ou)
+        assert err < 1e-10, (i, kw["precision"], err)

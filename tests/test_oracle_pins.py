@@ -407,3 +407,24 @@ def test_transport_element_conservation():
             uhat = uh[mesh["elem_face"][K, f]]
             flux += np.sum(w * bn * uhat)        # upwind flux beta.n uhat at convergence
         assert abs(dudt + flux) < 1e-11
+
+
+def test_shallow_water_contraction_threshold_of_theorem2():
+    """Theorem 2 needs B > 0, i.e. h / (dt (p+1)(p+2)) above (1 + sqrt(Phi))/2 = 1
+    here (Phi = 1, gamma = 0). Below that threshold the iteration grows, by the
+    factor dt (p+1)(p+2) / h per iteration; with C < 1 it converges."""
+    N, p = 4, 1
+    h = 1.0 / N
+    rng = np.random.default_rng(0)
+    mesh = W.structured_mesh((N, N), boundary_tag=W.TAG_WALL)
+    for ratio in (0.5, 0.8):
+        dt = h / (ratio * (p + 1) * (p + 2))
+        prob = Problem(mesh, p, pde="sw", scheme="be", dt=dt, Phi=1.0)
+        u0 = rng.standard_normal((prob.nel, 3, prob.Np))
+        _, _, hist = prob.solve_step(u0, tol=0.0, fixed_iters=150)
+        assert abs(hist[-1] / hist[-2] - 1.0 / ratio) < 1e-3
+    dt = h / (4.0 * (p + 1) * (p + 2))           # C = 1/3
+    prob = Problem(mesh, p, pde="sw", scheme="be", dt=dt, Phi=1.0)
+    u0 = rng.standard_normal((prob.nel, 3, prob.Np))
+    _, _, hist = prob.solve_step(u0, tol=0.0, fixed_iters=60)
+    assert hist[-1] < 1e-12 * hist[0]
