@@ -171,6 +171,22 @@ ehdg_status ehdg_run(ehdg_ctx ctx, int n_steps, int* iters_per_step);
 ehdg_status ehdg_step_fixed(ehdg_ctx ctx, int n_iter);
 
 ehdg_status ehdg_get_state(ehdg_ctx ctx, double* u, double* uhat, int on_device);
+
+/* Checkpoint and resume. ehdg_save writes everything a later step depends on:
+ * the state u^n, its trace, the previous step's trace (Crank-Nicolson), the
+ * boundary data of the new and previous levels, and the forcing. The file
+ * format is versioned: a header with the sizes and a hash of the mesh and
+ * problem, then the arrays, then a CRC-32 of the arrays. ehdg_load restores
+ * them into a context created with the same mesh and problem; a mismatch
+ * (sizes, hash, CRC) returns EHDG_ERR_INVALID and leaves the context unchanged. */
+ehdg_status ehdg_save(ehdg_ctx ctx, const char* path);
+ehdg_status ehdg_load(ehdg_ctx ctx, const char* path);
+
+/* Autotuner for the mixed-precision inner sweep count: runs one implicit step
+ * from the current state with each candidate (restoring the state after each),
+ * keeps the fastest, and reports it; the state is left as it was. */
+ehdg_status ehdg_autotune_inner_sweeps(ehdg_ctx ctx, const int* candidates, int n_candidates,
+                                       int* best, double* best_ms);
 /* Residual history r_0, r_1, ... of the last step (host buffer of cap entries). */
 ehdg_status ehdg_get_residual_history(ehdg_ctx ctx, double* buf, int64_t cap, int64_t* n_out);
 

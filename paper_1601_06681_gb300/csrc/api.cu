@@ -13,9 +13,6 @@
 
 using namespace ehdg;
 
-struct ehdg_ctx_s {
-  Ctx c;
-};
 
 struct ehdg_batch_s {
   std::vector<ehdg_ctx> inst;

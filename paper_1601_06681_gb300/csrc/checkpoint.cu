@@ -1,0 +1,237 @@
+// Checkpoint/resume of a context's stepping state, and the inner-sweep autotuner.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ehdg_internal.h"
+
+using namespace ehdg;
+
+
+namespace {
+
+constexpr uint32_t kMagic = 0x47444845u;   // "EHDG"
+constexpr uint32_t kVersion = 1;
+
+uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
+  static uint32_t table[256];
+  static bool init = false;
+  if (!init) {
+    for (uint32_t i = 0; i < 256; ++i) {
+      uint32_t c = i;
+      for (int k = 0; k < 8; ++k) c = (c & 1) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+      table[i] = c;
+    }
+    init = true;
+  }
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  crc = ~crc;
+  for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xFFu] ^ (crc >> 8);
+  return ~crc;
+}
+
+uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+  const unsigned char* p = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+struct Header {
+  uint32_t magic, version;
+  int32_t dim, p, nf, Np, q, Nqf, scheme, pde, have_force, pad;
+  int64_t nel, nface;
+  uint64_t config_hash;
+  uint64_t payload_bytes;
+};
+
+uint64_t config_hash(const Ctx& c) {
+  uint64_t h = 1469598103934665603ull;
+  h = fnv1a(h, c.elem_lo.data(), sizeof(double) * c.elem_lo.size());
+  h = fnv1a(h, c.elem_h.data(), sizeof(double) * c.elem_h.size());
+  h = fnv1a(h, c.face_elem_h.data(), sizeof(int64_t) * c.face_elem_h.size());
+  h = fnv1a(h, &c.dt, sizeof(double));
+  h = fnv1a(h, &c.Phi, sizeof(double));
+  h = fnv1a(h, c.beta_const, sizeof(double) * 3);
+  return h;
+}
+
+// the device arrays a checkpoint carries, in file order
+std::vector<std::pair<void*, size_t>> state_arrays(Ctx& c) {
+  const size_t state = sizeof(double) * (size_t)c.n * c.nel;
+  const size_t trace = sizeof(double) * (size_t)c.Nqf * c.nface;
+  return {{c.u, state},      {c.uhat, trace},       {c.uhat_n, trace}, {c.gb, trace},
+          {c.gb_old, trace}, {c.force, state},      {c.force_old, state}};
+}
+
+ehdg_status io_fail(ehdg_status s, const std::string& m) {
+  set_last_error(m);
+  return s;
+}
+
+}  // namespace
+
+extern "C" ehdg_status ehdg_save(ehdg_ctx h, const char* path) {
+  if (!h || !path) return io_fail(EHDG_ERR_INVALID, "NULL argument");
+  Ctx& c = h->c;
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess)
+    return io_fail(EHDG_ERR_CUDA, "stream synchronisation failed");
+  auto arrays = state_arrays(c);
+  Header hd{};
+  hd.magic = kMagic;
+  hd.version = kVersion;
+  hd.dim = c.dim;
+  hd.p = c.p;
+  hd.nf = c.nf;
+  hd.Np = c.Np;
+  hd.q = c.q;
+  hd.Nqf = c.Nqf;
+  hd.scheme = c.scheme;
+  hd.pde = c.pde;
+  hd.have_force = c.have_force ? 1 : 0;
+  hd.nel = c.nel;
+  hd.nface = c.nface;
+  hd.config_hash = config_hash(c);
+  for (auto& a : arrays) hd.payload_bytes += a.second;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return io_fail(EHDG_ERR_INVALID, std::string("cannot open ") + path);
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+  uint32_t crc = 0;
+  std::vector<char> buf;
+  for (auto& a : arrays) {
+    if (!ok) break;
+    buf.resize(a.second);
+    if (cudaMemcpy(buf.data(), a.first, a.second, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      std::fclose(f);
+      return io_fail(EHDG_ERR_CUDA, "device read failed");
+    }
+    crc = crc32_update(crc, buf.data(), buf.size());
+    ok = std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+  }
+  ok = ok && std::fwrite(&crc, sizeof(crc), 1, f) == 1;
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? EHDG_OK : io_fail(EHDG_ERR_INVALID, std::string("write failed: ") + path);
+}
+
+extern "C" ehdg_status ehdg_load(ehdg_ctx h, const char* path) {
+  if (!h || !path) return io_fail(EHDG_ERR_INVALID, "NULL argument");
+  Ctx& c = h->c;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return io_fail(EHDG_ERR_INVALID, std::string("cannot open ") + path);
+  Header hd{};
+  auto arrays = state_arrays(c);
+  uint64_t payload = 0;
+  for (auto& a : arrays) payload += a.second;
+  if (std::fread(&hd, sizeof(hd), 1, f) != 1 || hd.magic != kMagic || hd.version != kVersion) {
+    std::fclose(f);
+    return io_fail(EHDG_ERR_INVALID, "not an eHDG checkpoint of this version");
+  }
+  if (hd.dim != c.dim || hd.p != c.p || hd.nf != c.nf || hd.Np != c.Np || hd.q != c.q ||
+      hd.Nqf != c.Nqf || hd.scheme != (int)c.scheme || hd.pde != (int)c.pde || hd.nel != c.nel ||
+      hd.nface != c.nface || hd.payload_bytes != payload || hd.config_hash != config_hash(c)) {
+    std::fclose(f);
+    return io_fail(EHDG_ERR_INVALID, "checkpoint belongs to a different mesh or problem");
+  }
+  std::vector<std::vector<char>> bufs(arrays.size());
+  uint32_t crc = 0;
+  for (size_t i = 0; i < arrays.size(); ++i) {
+    bufs[i].resize(arrays[i].second);
+    if (std::fread(bufs[i].data(), 1, bufs[i].size(), f) != bufs[i].size()) {
+      std::fclose(f);
+      return io_fail(EHDG_ERR_INVALID, "truncated checkpoint");
+    }
+    crc = crc32_update(crc, bufs[i].data(), bufs[i].size());
+  }
+  uint32_t stored = 0;
+  const bool got = std::fread(&stored, sizeof(stored), 1, f) == 1;
+  std::fclose(f);
+  if (!got || stored != crc) return io_fail(EHDG_ERR_INVALID, "checkpoint CRC mismatch");
+  if (cudaStreamSynchronize(c.stream) != cudaSuccess)
+    return io_fail(EHDG_ERR_CUDA, "stream synchronisation failed");
+  for (size_t i = 0; i < arrays.size(); ++i)
+    if (cudaMemcpy(arrays[i].first, bufs[i].data(), bufs[i].size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess)
+      return io_fail(EHDG_ERR_CUDA, "device write failed");
+  c.have_force = hd.have_force != 0;
+  return EHDG_OK;
+}
+
+extern "C" ehdg_status ehdg_autotune_inner_sweeps(ehdg_ctx h, const int* cands, int n, int* best,
+                                                  double* best_ms) {
+  if (!h || !cands || n < 1) return io_fail(EHDG_ERR_INVALID, "bad argument");
+  Ctx& c = h->c;
+  if (!c.mixed) return io_fail(EHDG_ERR_INVALID, "the context is not mixed precision");
+  auto arrays = state_arrays(c);
+  // snapshot on the device
+  std::vector<void*> snap(arrays.size(), nullptr);
+  auto free_snap = [&]() {
+    for (void* p : snap)
+      if (p) cudaFree(p);
+  };
+  for (size_t i = 0; i < arrays.size(); ++i) {
+    if (cudaMalloc(&snap[i], arrays[i].second) != cudaSuccess ||
+        cudaMemcpyAsync(snap[i], arrays[i].first, arrays[i].second, cudaMemcpyDeviceToDevice,
+                        c.stream) != cudaSuccess) {
+      free_snap();
+      return io_fail(EHDG_ERR_OOM, "autotune snapshot failed");
+    }
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int saved = c.inner_sweeps;
+  int best_m = saved;
+  double best_t = 1e300;
+  ehdg_status st = EHDG_OK;
+  for (int k = 0; k < n && st == EHDG_OK; ++k) {
+    if (cands[k] < 1 || cands[k] > 64) continue;
+    c.inner_sweeps = cands[k];
+    if (c.gexec) {
+      cudaGraphExecDestroy(c.gexec);
+      c.gexec = nullptr;
+    }
+    if (c.graph) {
+      cudaGraphDestroy(c.graph);
+      c.graph = nullptr;
+    }
+    int iters = 0;
+    double ms_sum = 0.0;
+    for (int rep = 0; rep < 2 && st == EHDG_OK; ++rep) {   // first run also captures the graph
+      cudaEventRecord(e0, c.stream);
+      st = ehdg_step(h, &iters, nullptr);
+      cudaEventRecord(e1, c.stream);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep == 1) ms_sum = ms;
+      for (size_t i = 0; i < arrays.size(); ++i)
+        cudaMemcpyAsync(arrays[i].first, snap[i], arrays[i].second, cudaMemcpyDeviceToDevice,
+                        c.stream);
+    }
+    if (st == EHDG_OK && ms_sum < best_t) {
+      best_t = ms_sum;
+      best_m = cands[k];
+    }
+  }
+  cudaStreamSynchronize(c.stream);
+  free_snap();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c.inner_sweeps = (st == EHDG_OK) ? best_m : saved;
+  if (c.gexec) {
+    cudaGraphExecDestroy(c.gexec);
+    c.gexec = nullptr;
+  }
+  if (c.graph) {
+    cudaGraphDestroy(c.graph);
+    c.graph = nullptr;
+  }
+  if (best) *best = c.inner_sweeps;
+  if (best_ms) *best_ms = best_t;
+  return st;
+}

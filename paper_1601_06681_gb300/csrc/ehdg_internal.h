@@ -190,3 +190,7 @@ cudaError_t launch_wdiff_norm(const double* a, const double* b, const double* w,
 int wdiff_norm_blocks(int64_t n);
 
 }  // namespace ehdg
+
+struct ehdg_ctx_s {
+  ehdg::Ctx c;
+};

@@ -74,6 +74,10 @@ _SIGS = [
     ("ehdg_get_state", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
     ("ehdg_get_residual_history", C.c_int, [C.c_void_p, C.c_void_p, C.c_int64,
                                             C.POINTER(C.c_int64)]),
+    ("ehdg_save", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("ehdg_load", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("ehdg_autotune_inner_sweeps", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
+                                             C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_set_profiling", C.c_int, [C.c_void_p, C.c_int]),
     ("ehdg_kernel_stats", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64),
                                     C.POINTER(C.c_double)]),
@@ -320,6 +324,25 @@ class Solver:
                                                 buf.size, C.byref(n)))
         return buf[:min(n.value, buf.size)].copy()
 
+    def save(self, path):
+        _check(load().ehdg_save(self._h, os.fsencode(path)))
+
+    def load_checkpoint(self, path):
+        _check(load().ehdg_load(self._h, os.fsencode(path)))
+
+    def autotune_inner_sweeps(self, candidates=(2, 3, 4, 6, 8, 12)):
+        """Fastest inner sweep count for one step from the current state (which
+        is restored); the context keeps it. Returns (best, ms)."""
+        arr = (C.c_int * len(candidates))(*candidates)
+        best, ms = C.c_int(), C.c_double()
+        _check(load().ehdg_autotune_inner_sweeps(self._h, arr, len(candidates), C.byref(best),
+                                                 C.byref(ms)))
+        return best.value, ms.value
+
+    def tune_key(self):
+        i = self.info
+        return f"d{i['dim']}_p{i['p']}_nf{i['nf']}_q{i['q']}_shared{i['shared_operator']}_prec{self.prob.precision}"
+
     def set_profiling(self, on=True):
         _check(load().ehdg_set_profiling(self._h, 1 if on else 0))
 
@@ -418,3 +441,27 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+def autotune_cached(solver, cache_path, candidates=(2, 3, 4, 6, 8, 12)):
+    """Inner sweep count for this kind of problem from a JSON cache keyed by
+    dimension, degree, fields, quadrature, operator sharing and precision;
+    tuned (ehdg_autotune_inner_sweeps) and stored on a miss. Returns the count,
+    which the solver is then configured with."""
+    import json
+    cache = {}
+    if os.path.exists(cache_path):
+        with open(cache_path) as fh:
+            cache = json.load(fh)
+    key = solver.tune_key()
+    if key in cache:
+        best = int(cache[key]["inner_sweeps"])
+        solver.autotune_inner_sweeps((best,))
+        return best
+    best, ms = solver.autotune_inner_sweeps(candidates)
+    cache[key] = {"inner_sweeps": best, "ms_per_step": ms, "candidates": list(candidates)}
+    tmp = cache_path + ".tmp"
+    with open(tmp, "w") as fh:
+        json.dump(cache, fh, indent=1, sort_keys=True)
+    os.replace(tmp, cache_path)
+    return best

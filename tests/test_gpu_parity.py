@@ -287,3 +287,54 @@ def test_tensor_core_precision_needs_shared_operator(ehdg):
     with pytest.raises(ehdg.EhdgError) as ei:
         ehdg.Solver(mesh, p, precision="tf32", **kw)
     assert ei.value.status == 7
+
+
+# ---------------------------------------------------------------------------
+# checkpoint / resume and the autotuner
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["2d_cn_variable", "sw_be"])
+def test_checkpoint_resume_is_bitwise(ehdg, name, tmp_path):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        if g is not None:
+            s.set_boundary(g)
+        s.set_state(u0)
+        s.run(4)
+        u_ref, uh_ref = s.get_state()
+    path = str(tmp_path / "ck.ehdg")
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        if g is not None:
+            s.set_boundary(g)
+        s.set_state(u0)
+        s.run(2)
+        s.save(path)
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        s.load_checkpoint(path)
+        s.run(2)
+        u, uh = s.get_state()
+    assert np.array_equal(u, u_ref) and np.array_equal(uh, uh_ref)
+    # a checkpoint of another problem is rejected
+    other = W.structured_mesh((5, 5), boundary_tag=mesh["face_tag"].max())
+    kw2 = dict(kw)
+    if "beta_nodes" in kw2:
+        kw2.pop("beta_nodes")
+        kw2["beta_const"] = np.array([1.0, 0.0])
+    with ehdg.Solver(other, p, **kw2) as s:
+        with pytest.raises(ehdg.EhdgError):
+            s.load_checkpoint(path)
+
+
+def test_autotuner_keeps_state_and_results(ehdg, tmp_path):
+    mesh, p, kw, prob, u0, g = make_case("3d_be_const")
+    with ehdg.Solver(mesh, p, tol=1e-12, max_iter=400, precision="tf32", **kw) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        best = ehdg.autotune_cached(s, str(tmp_path / "tune.json"), candidates=(2, 4, 8))
+        assert best in (2, 4, 8)
+        s.run(2)
+        u, _ = s.get_state()
+        again = ehdg.autotune_cached(s, str(tmp_path / "tune.json"))
+        assert again == best
+    ou, _, _, _ = prob.run(u0, 2, g_of_t=lambda t: g, tol=1e-13, max_iter=2000)
+    assert rel(u, ou) < 1e-10
