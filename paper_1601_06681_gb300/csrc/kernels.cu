@@ -73,6 +73,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// One full wave of resident blocks, capped by the number of tiles.
+template <class K>
+int persistent_grid(K kernel, int threads, size_t smem, int64_t ntiles) {
+  int bpsm = 0;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, threads, smem) != cudaSuccess ||
+      bpsm < 1) {
+    cudaGetLastError();
+    bpsm = 1;
+  }
+  int64_t g = (int64_t)bpsm * device_sms();
+  if (g > ntiles) g = ntiles;
+  return g < 1 ? 1 : (int)g;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -391,49 +406,78 @@ struct StepParams {
   double* Y;
 };
 
-__global__ void k_step(const StepParams s) {
+// Tile of 32 consecutive elements (threadIdx.x) x kStepT row groups
+// (threadIdx.y); persistent over tiles. w and G of the tile live in shared
+// memory; a shared operator P is staged once per block.
+constexpr int kStepT = 4;
+
+__global__ void __launch_bounds__(32 * kStepT) k_step(const StepParams s) {
   extern __shared__ double sm[];
-  const int bd = blockDim.x, tid = threadIdx.x;
-  double* Psh = sm;                                   // shared operator (n*n) if shared
-  double* w = sm + (s.shared ? s.n * s.n : 0);        // [n][bd]
-  double* g = w + s.n * bd;                           // [n][bd]
+  const int lane = threadIdx.x, t = threadIdx.y, tid = t * 32 + lane;
+  const int n = s.n;
+  double* Psh = sm;                                   // n*n if shared
+  double* w = sm + (s.shared ? n * n : 0);            // [n][32]
+  double* g = w + n * 32;                             // [n][32]
   if (s.shared)
-    for (int t = tid; t < s.n * s.n; t += bd) Psh[t] = s.P[t];
-  __syncthreads();
-  const int64_t e = blockIdx.x * (int64_t)bd + tid;
-  if (e >= s.nel) return;
+    for (int i = tid; i < n * n; i += 32 * kStepT) Psh[i] = s.P[i];
   const int64_t ne = s.nel;
-  for (int c = 0; c < s.n; ++c) {
-    double v = s.u[c * ne + e] * s.ucoef;
-    if (s.have_force)
-      v += s.force_avg ? 0.5 * (s.force[c * ne + e] + s.force_old[c * ne + e]) : s.force[c * ne + e];
-    w[c * bd + tid] = v;
-  }
-  for (int r = 0; r < s.n; ++r) {
-    double acc = 0.0;
-    if (s.shared) {
-      for (int c = 0; c < s.n; ++c) acc += Psh[r * s.n + c] * w[c * bd + tid];
-    } else {
-      const double* Pr = s.P + (int64_t)r * s.n * ne + e;
-      for (int c = 0; c < s.n; ++c) acc += Pr[c * ne] * w[c * bd + tid];
+  const int64_t ntiles = (ne + 31) / 32;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e = tile * 32 + lane;
+    const bool live = e < ne;
+    __syncthreads();
+    for (int c = t; c < n; c += kStepT) {
+      double v = 0.0;
+      if (live) {
+        v = s.u[c * ne + e] * s.ucoef;
+        if (s.have_force)
+          v += s.force_avg ? 0.5 * (s.force[c * ne + e] + s.force_old[c * ne + e])
+                           : s.force[c * ne + e];
+      }
+      w[c * 32 + lane] = v;
     }
-    g[r * bd + tid] = acc;
-    s.G[r * ne + e] = acc;
-  }
-  // initial-trace input: element values at every face point
-  for (int r = 0; r < s.NQFS; ++r) {
-    double y0 = 0.0;
-    for (int k = 0; k < s.KE; ++k)
-      y0 += s.ey_val[r * s.KE + k] * s.u[s.ey_idx[r * s.KE + k] * ne + e];
-    s.Y[r * ne + e] = y0;
-  }
-  // Gy in the sweep's slot order (only the rows the sweep computes)
-  const int nr = s.shared ? s.n_rows : s.nrows[e];
-  for (int j = 0; j < nr; ++j) {
-    const int r = s.shared ? s.rows[j] : s.rowid[j * ne + e];
-    double gy = 0.0;
-    for (int k = 0; k < s.KE; ++k) gy += s.ey_val[r * s.KE + k] * g[s.ey_idx[r * s.KE + k] * bd + tid];
-    s.Gy[j * ne + e] = gy;
+    __syncthreads();
+    for (int r = t; r < n; r += kStepT) {
+      double a0 = 0.0, a1 = 0.0;
+      if (s.shared) {
+        const double* Pr = Psh + r * n;
+        int c = 0;
+        for (; c + 1 < n; c += 2) {
+          a0 = fma(Pr[c], w[c * 32 + lane], a0);
+          a1 = fma(Pr[c + 1], w[(c + 1) * 32 + lane], a1);
+        }
+        if (c < n) a0 = fma(Pr[c], w[c * 32 + lane], a0);
+      } else if (live) {
+        const double* Pr = s.P + (int64_t)r * n * ne + e;
+        int c = 0;
+        for (; c + 1 < n; c += 2) {
+          a0 = fma(Pr[c * ne], w[c * 32 + lane], a0);
+          a1 = fma(Pr[(c + 1) * ne], w[(c + 1) * 32 + lane], a1);
+        }
+        if (c < n) a0 = fma(Pr[c * ne], w[c * 32 + lane], a0);
+      }
+      const double acc = a0 + a1;
+      g[r * 32 + lane] = acc;
+      if (live) s.G[r * ne + e] = acc;
+    }
+    __syncthreads();
+    if (!live) continue;
+    // initial-trace input: element values at every face point
+    for (int r = t; r < s.NQFS; r += kStepT) {
+      double y0 = 0.0;
+      for (int k2 = 0; k2 < s.KE; ++k2)
+        y0 += s.ey_val[r * s.KE + k2] * s.u[s.ey_idx[r * s.KE + k2] * ne + e];
+      s.Y[r * ne + e] = y0;
+    }
+    // Gy in the sweep's slot order (only the rows the sweep computes)
+    const int nr = s.shared ? s.n_rows : s.nrows[e];
+    for (int j = t; j < nr; j += kStepT) {
+      const int r = s.shared ? s.rows[j] : s.rowid[j * ne + e];
+      double gy = 0.0;
+      for (int k2 = 0; k2 < s.KE; ++k2)
+        gy += s.ey_val[r * s.KE + k2] * g[s.ey_idx[r * s.KE + k2] * 32 + lane];
+      s.Gy[j * ne + e] = gy;
+    }
   }
 }
 
@@ -460,16 +504,11 @@ cudaError_t launch_step(Ctx& c) {
   s.G = c.G;
   s.Gy = c.Gy;
   s.Y = c.Y;
-  int bd = 128;
-  size_t smem = sizeof(double) * ((s.shared ? (size_t)c.n * c.n : 0) + 2 * (size_t)c.n * bd);
-  while (smem > 200 * 1024 && bd > 32) {
-    bd /= 2;
-    smem = sizeof(double) * ((s.shared ? (size_t)c.n * c.n : 0) + 2 * (size_t)c.n * bd);
-  }
+  const size_t smem = sizeof(double) * ((s.shared ? (size_t)c.n * c.n : 0) + 2 * (size_t)c.n * 32);
   cudaError_t err = cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  const int grid = (int)((c.nel + bd - 1) / bd);
-  k_step<<<grid, bd, smem, c.stream>>>(s);
+  const int grid = persistent_grid(k_step, 32 * kStepT, smem, (c.nel + 31) / 32);
+  k_step<<<grid, dim3(32, kStepT), smem, c.stream>>>(s);
   return cudaGetLastError();
 }
 
@@ -828,33 +867,53 @@ struct FinalParams {
   double* u;
 };
 
-__global__ void k_final(const FinalParams p) {
+__global__ void __launch_bounds__(32 * kStepT) k_final(const FinalParams p) {
   extern __shared__ double sm[];
-  const int bd = blockDim.x, tid = threadIdx.x;
+  const int lane = threadIdx.x, t = threadIdx.y, tid = t * 32 + lane;
   double* Hsh = sm;
-  double* uh = sm + (p.shared ? p.n * p.NQFS : 0);
+  double* uh = sm + (p.shared ? p.n * p.NQFS : 0);     // [NQFS][32]
   if (p.shared)
-    for (int t = tid; t < p.n * p.NQFS; t += bd) Hsh[t] = p.H[t];
-  __syncthreads();
-  const int64_t e = blockIdx.x * (int64_t)bd + tid;
-  if (e >= p.nel) return;
+    for (int i = tid; i < p.n * p.NQFS; i += 32 * kStepT) Hsh[i] = p.H[i];
   const int64_t ne = p.nel;
+  const int64_t ntiles = (ne + 31) / 32;
   // Algorithm 1 returns u^{k+1}, the local solve with the trace uhat^k
   const double* src = p.uhat + (int64_t)((p.it->k + 1) & 1) * p.Nqf * p.nface;
-  for (int f = 0; f < p.F; ++f) {
-    const int64_t face = p.elem_face[f * ne + e];
-    for (int g = 0; g < p.Nqf; ++g) uh[(f * p.Nqf + g) * bd + tid] = src[g * p.nface + face];
-  }
-  for (int r = 0; r < p.n; ++r) {
-    double acc = p.G[r * ne + e];
-    if (p.shared) {
-      for (int t = 0; t < p.NQFS; ++t) acc += Hsh[r * p.NQFS + t] * uh[t * bd + tid];
-    } else {
-      const double* Hr = p.H + (int64_t)r * p.NQFS * ne + e;
-      for (int t = 0; t < p.NQFS; ++t) acc += Hr[t * ne] * uh[t * bd + tid];
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t e = tile * 32 + lane;
+    const bool live = e < ne;
+    __syncthreads();
+    if (live) {
+      for (int f = 0; f < p.F; ++f) {
+        const int64_t face = p.elem_face[f * ne + e];
+        for (int g = t; g < p.Nqf; g += kStepT)
+          uh[(f * p.Nqf + g) * 32 + lane] = src[g * p.nface + face];
+      }
     }
-    if (p.cn) acc = 2.0 * acc - p.u[r * ne + e];
-    p.u[r * ne + e] = acc;
+    __syncthreads();
+    if (!live) continue;
+    for (int r = t; r < p.n; r += kStepT) {
+      double a0 = p.G[r * ne + e], a1 = 0.0;
+      if (p.shared) {
+        const double* Hr = Hsh + r * p.NQFS;
+        int c = 0;
+        for (; c + 1 < p.NQFS; c += 2) {
+          a0 = fma(Hr[c], uh[c * 32 + lane], a0);
+          a1 = fma(Hr[c + 1], uh[(c + 1) * 32 + lane], a1);
+        }
+        if (c < p.NQFS) a0 = fma(Hr[c], uh[c * 32 + lane], a0);
+      } else {
+        const double* Hr = p.H + (int64_t)r * p.NQFS * ne + e;
+        int c = 0;
+        for (; c + 1 < p.NQFS; c += 2) {
+          a0 = fma(Hr[c * ne], uh[c * 32 + lane], a0);
+          a1 = fma(Hr[(c + 1) * ne], uh[(c + 1) * 32 + lane], a1);
+        }
+        if (c < p.NQFS) a0 = fma(Hr[c * ne], uh[c * 32 + lane], a0);
+      }
+      double acc = a0 + a1;
+      if (p.cn) acc = 2.0 * acc - p.u[r * ne + e];
+      p.u[r * ne + e] = acc;
+    }
   }
 }
 
@@ -889,16 +948,11 @@ cudaError_t launch_final(Ctx& c) {
   p.G = c.G;
   p.H = c.H;
   p.u = c.u;
-  int bd = 128;
-  size_t smem = sizeof(double) * ((p.shared ? (size_t)c.n * c.NQFS : 0) + (size_t)c.NQFS * bd);
-  while (smem > 200 * 1024 && bd > 32) {
-    bd /= 2;
-    smem = sizeof(double) * ((p.shared ? (size_t)c.n * c.NQFS : 0) + (size_t)c.NQFS * bd);
-  }
+  const size_t smem = sizeof(double) * ((p.shared ? (size_t)c.n * c.NQFS : 0) + (size_t)c.NQFS * 32);
   cudaError_t err = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  const int grid = (int)((c.nel + bd - 1) / bd);
-  k_final<<<grid, bd, smem, c.stream>>>(p);
+  const int grid = persistent_grid(k_final, 32 * kStepT, smem, (c.nel + 31) / 32);
+  k_final<<<grid, dim3(32, kStepT), smem, c.stream>>>(p);
   err = cudaGetLastError();
   if (err != cudaSuccess) return err;
   const int64_t total = (int64_t)c.Nqf * c.nface;
