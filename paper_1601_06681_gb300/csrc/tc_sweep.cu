@@ -20,6 +20,7 @@ namespace ehdg {
 namespace {
 
 constexpr int kTcM = 128;
+constexpr int kTcThreads = 256;                // two threads per element (tile row)
 constexpr uint32_t kWaitLimit = 1u << 24;   // mbarrier polls before giving up
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -63,6 +64,24 @@ struct TcParams {
   int* err;
 };
 
+// one 16-byte chunk (one row of one core matrix): 4 TF32 or 8 BF16 values
+__device__ __forceinline__ void store_chunk(unsigned char* dst, const float* v, int per, int bf16) {
+  if (bf16) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v[2 * q]);
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v[2 * q + 1]);
+      w[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+    }
+    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {
+    *reinterpret_cast<uint4*>(dst) =
+        make_uint4(to_tf32(v[0]), to_tf32(v[1]), to_tf32(v[2]), to_tf32(v[3]));
+  }
+  (void)per;
+}
+
 __device__ __forceinline__ void store_elem(unsigned char* base, int row, int k, int esize,
                                            uint32_t sbo, float v, int bf16) {
   const uint32_t off = kmajor_off(row, k * esize, sbo);
@@ -73,20 +92,28 @@ __device__ __forceinline__ void store_elem(unsigned char* base, int row, int k, 
   }
 }
 
-__global__ void __launch_bounds__(kTcM) k_sweep_tc(const TcParams p) {
+__global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int row = tid & (kTcM - 1), half = tid >> 7;   // tile row (element) and K / N half
   const int esize = p.bf16 ? 2 : 4;
   const uint32_t kbytes = (uint32_t)p.Kp * esize;
   const uint32_t sbo = kbytes * 8u;             // (K bytes / 16) core matrices of 128 B
   unsigned char* Bs = sm;                        // Np x Kp
   unsigned char* As = sm + (size_t)p.Np * kbytes; // 128 x Kp
   int* fid = reinterpret_cast<int*>(As + (size_t)kTcM * kbytes);   // [F][128]
+  int* row_f = fid + p.F * kTcM;                                   // [Np] face of a row
+  int* row_g = row_f + p.Np;                                       // [Np] point of a row
+  for (int j = tid; j < p.Np; j += kTcThreads) {
+    const int r = j < p.n_rows ? p.rows[j] : 0;
+    row_f[j] = r / p.Nqf;
+    row_g[j] = r - (r / p.Nqf) * p.Nqf;
+  }
 
   // B = sweep rows of the shared operator, zero-padded
-  for (int i = tid; i < p.Np * p.Kp; i += kTcM) {
+  for (int i = tid; i < p.Np * p.Kp; i += kTcThreads) {
     const int n = i / p.Kp, k = i - n * p.Kp;
     float v = 0.f;
     if (n < p.n_rows && k < p.NQFS) v = p.Hy32[p.rows[n] * p.NQFS + k];
@@ -112,25 +139,45 @@ __global__ void __launch_bounds__(kTcM) k_sweep_tc(const TcParams p) {
   uint32_t phase = 0;
   bool failed = false;
   for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
-    const int64_t e = tile * kTcM + tid;
-    // A = this tile's correction values at its elements' face points; loads
-    // are issued 16 at a time so they overlap instead of serialising
+    const int64_t e = tile * kTcM + row;
+    // A = this tile's correction values at its elements' face points: each
+    // element's K range is split between its two threads; face/point counters
+    // advance incrementally and 16 loads are in flight per round
+    __syncthreads();
     if (e < ne)
-      for (int f = 0; f < p.F; ++f) fid[f * kTcM + tid] = p.elem_face[f * ne + e];
-    for (int k0 = 0; k0 < p.Kp; k0 += 16) {
-      float v[16];
+      for (int f = half; f < p.F; f += 2) fid[f * kTcM + row] = p.elem_face[f * ne + e];
+    __syncthreads();
+    {
+      const uint32_t rowoff = (uint32_t)(row >> 3) * sbo + (uint32_t)(row & 7) * 16u;
+      const int khalf = p.Kp / 2;                        // a multiple of the chunk size
+      const int kbeg = half * khalf, kend = kbeg + khalf;
+      int f = kbeg / p.Nqf, g = kbeg - (kbeg / p.Nqf) * p.Nqf;
+      for (int k0 = kbeg; k0 < kend; k0 += 16) {
+        float v[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        const int k = k0 + q;
-        v[q] = 0.f;
-        if (e < ne && k < p.NQFS) {
-          const int f = k / p.Nqf, g = k - f * p.Nqf;
-          v[q] = p.in[g * nface + fid[f * kTcM + tid]];
+        for (int q = 0; q < 16; ++q) {
+          float x = 0.f;
+          if (e < ne && k0 + q < p.NQFS && k0 + q < kend) {
+            x = p.in[g * nface + fid[f * kTcM + row]];
+            if (++g == p.Nqf) {
+              g = 0;
+              ++f;
+            }
+          }
+          v[q] = x;
+        }
+        if (p.bf16) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            if (k0 + 8 * h < kend)
+              store_chunk(As + rowoff + (uint32_t)((k0 + 8 * h) / 8) * 128u, v + 8 * h, 8, 1);
+        } else {
+#pragma unroll
+          for (int h = 0; h < 4; ++h)
+            if (k0 + 4 * h < kend)
+              store_chunk(As + rowoff + (uint32_t)((k0 + 4 * h) / 4) * 128u, v + 4 * h, 4, 0);
         }
       }
-#pragma unroll
-      for (int q = 0; q < 16; ++q)
-        if (k0 + q < p.Kp) store_elem(As, tid, k0 + q, esize, sbo, v[q], p.bf16);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
@@ -158,16 +205,20 @@ __global__ void __launch_bounds__(kTcM) k_sweep_tc(const TcParams p) {
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               smem_addr(&mbar)));
     }
-    // bounded wait for the MMAs
-    uint32_t ok = 0;
-    for (uint32_t it = 0; it < kWaitLimit; ++it) {
-      asm volatile(
-          "{\n .reg .pred w;\n mbarrier.try_wait.parity.shared::cta.b64 w, [%1], %2;\n"
-          " selp.u32 %0, 1, 0, w;\n}\n"
-          : "=r"(ok)
-          : "r"(smem_addr(&mbar)), "r"(phase)
-          : "memory");
-      if (ok) break;
+    // bounded wait for the MMAs: one thread polls the mbarrier, the others
+    // wait at the block barrier (no issue slots burnt while the MMA runs)
+    uint32_t ok = 1;
+    if (tid == 0) {
+      ok = 0;
+      for (uint32_t it = 0; it < kWaitLimit; ++it) {
+        asm volatile(
+            "{\n .reg .pred w;\n mbarrier.try_wait.parity.shared::cta.b64 w, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, w;\n}\n"
+            : "=r"(ok)
+            : "r"(smem_addr(&mbar)), "r"(phase)
+            : "memory");
+        if (ok) break;
+      }
     }
     // block-uniform outcome, so every thread takes the same path below
     if (__syncthreads_or(ok ? 0 : 1)) {
@@ -177,43 +228,40 @@ __global__ void __launch_bounds__(kTcM) k_sweep_tc(const TcParams p) {
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!failed) {
-      // epilogue: this warp's 32 TMEM lanes = its 32 elements, N columns
-      for (int c0 = 0; c0 < p.Np; c0 += 16) {
-        uint32_t v[16];
-        const uint32_t taddr = tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"
-            "%13,%14,%15}, [%16];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-              "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-              "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(taddr));
+      // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its elements) and
+      // the columns of its half of N, 8 at a time
+      const int nhalf = p.Np / 2;
+      const int cbeg = half * nhalf, cend = cbeg + nhalf;
+      for (int c0 = cbeg; c0 < cend; c0 += 8) {
+        uint32_t v[8];
+        const uint32_t taddr = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                       "=r"(v[6]), "=r"(v[7])
+                     : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         if (e < ne) {
-          // residual values of the owned points first (16 loads in flight), then the writes
-          int64_t pt[16];
-          float rv[16];
+          int64_t pt[8];
+          float rv[8];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
+          for (int q = 0; q < 8; ++q) {
             const int j = c0 + q;
             pt[q] = -1;
             rv[q] = 0.f;
             if (j < p.n_rows && p.owner_writes && j < p.n_up) {
-              const int r = p.rows[j];
-              const int f = r / p.Nqf, g = r - f * p.Nqf;
-              pt[q] = (int64_t)g * nface + fid[f * kTcM + tid];
+              pt[q] = (int64_t)row_g[j] * nface + fid[row_f[j] * kTcM + row];
               rv[q] = p.R[pt[q]];
             }
           }
 #pragma unroll
-          for (int q = 0; q < 16; ++q) {
+          for (int q = 0; q < 8; ++q) {
             const int j = c0 + q;
             if (j >= p.n_rows) break;
             const float acc = __uint_as_float(v[q]);
             if (pt[q] >= 0) {
               p.out[pt[q]] = rv[q] + acc;
             } else {
-              p.Y32[(int64_t)p.rows[j] * ne + e] = acc;
+              p.Y32[(int64_t)(row_f[j] * p.Nqf + row_g[j]) * ne + e] = acc;
             }
           }
         }
@@ -265,24 +313,23 @@ cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
   p.Y32 = c.Y32;
   p.err = c.tc_err;
   const int esize = p.bf16 ? 2 : 4;
-  const size_t smem = (size_t)(p.Np + kTcM) * p.Kp * esize + sizeof(int) * c.F * kTcM + 1024;
+  const size_t smem = (size_t)(p.Np + kTcM) * p.Kp * esize +
+                      sizeof(int) * ((size_t)c.F * kTcM + 2 * (size_t)p.Np) + 1024;
   cudaError_t err =
       cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   // favour shared memory over L1 so several tiles' blocks fit per SM
   err = cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (err != cudaSuccess) return err;
-  int bpsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_sweep_tc, kTcM, smem) !=
-          cudaSuccess || bpsm < 1) {
-    cudaGetLastError();
-    bpsm = 1;
-  }
-  if (bpsm > 512 / ncols) bpsm = 512 / ncols;        // TMEM: 512 columns per SM
+  // resident blocks per SM: shared memory (227 KB per SM usable) and TMEM (512 columns)
+  int bpsm = (int)((227 * 1024) / (smem + 1024));
+  if (bpsm > 512 / ncols) bpsm = 512 / ncols;
+  if (bpsm > 8) bpsm = 8;
+  if (bpsm < 1) bpsm = 1;
   const int64_t ntiles = (c.nel + kTcM - 1) / kTcM;
   int64_t grid = (int64_t)bpsm * device_sms();
   if (grid > ntiles) grid = ntiles;
-  k_sweep_tc<<<(int)grid, kTcM, smem, c.stream>>>(p);
+  k_sweep_tc<<<(int)grid, kTcThreads, smem, c.stream>>>(p);
   return cudaGetLastError();
 }
 
