@@ -373,7 +373,7 @@ ehdg_status run_graph(Ctx& c, int n_steps, int* iters_per_step, double* res) {
   if (c.tc_err) {
     int te = 0;
     CK(cudaMemcpy(&te, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (te) return fail(EHDG_ERR_TIMEOUT, "a tensor-core sweep's bounded wait gave up");
+    if (te) return fail(EHDG_ERR_TIMEOUT, "a sweep's bounded mbarrier wait gave up");
   }
   if (first == EHDG_ERR_NOT_CONVERGED) return fail(first, "eHDG did not reach the tolerance in max_iter iterations");
   if (first == EHDG_ERR_DIVERGED) return fail(first, "non-finite eHDG residual");
@@ -819,13 +819,13 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
     TRYC(dalloc(c, &c.R32, trace));
     TRYC(dalloc(c, &c.d32, 2 * trace));
     TRYC(dalloc(c, &c.Y32, (size_t)c.NQFS * c.nel));
-    TRYC(dalloc(c, &c.tc_err, 1));
-    CKC(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
     // points no sweep owns (inflow boundary) keep R = delta = 0 for good
     CKC(cudaMemsetAsync(c.R32, 0, sizeof(float) * trace, c.stream));
     CKC(cudaMemsetAsync(c.d32, 0, sizeof(float) * 2 * trace, c.stream));
     CKC(cudaMemsetAsync(c.Y32, 0, sizeof(float) * c.NQFS * c.nel, c.stream));
   }
+  TRYC(dalloc(c, &c.tc_err, 1));
+  CKC(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
   TRYC(dalloc(c, &c.it, 1));
   TRYC(dalloc(c, &c.hist, (size_t)c.max_iter));
   CKC(cudaMallocHost(&c.it_host, sizeof(IterState)));
@@ -842,6 +842,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   if (c.pde == EHDG_TRANSPORT)
     CKC(counted(c, EHDG_KERNEL_SIGNS, 1, [&] { return launch_face_signs(c); }));
   if (!c.shared_op) CKC(counted(c, EHDG_KERNEL_AUX, 2, [&] { return launch_rows(c); }));
+  if (tiled_supported(c)) CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return build_tiled_operator(c); }));
   if (c.mixed) CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_hy_to_f32(c); }));
   CKC(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
   CKC(cudaStreamSynchronize(c.stream));

@@ -101,10 +101,17 @@ struct Ctx {
   int32_t* tan_face = nullptr;   //   and face
   int64_t n_tan = 0;
   int64_t sweep_rows = 0;        // rows computed per sweep, all elements
+  // per-element transport operator, tile-major (32 elements per tile): the
+  // rows each tile needs, NQFS x 32 doubles each, streamed by the tiled sweep
+  double* Hyt = nullptr;
+  int32_t* tile_row0 = nullptr;  // [ntiles] first row of a tile in Hyt
+  uint8_t* tile_nrows = nullptr; // [ntiles] rows of a tile (max over its elements)
+  int64_t ntiles = 0;
+  int64_t tile_rows = 0;         // rows in Hyt
   // mixed precision (defect correction)
   bool mixed = false;
   ehdg_precision precision = EHDG_FP64;
-  int* tc_err = nullptr;         // set by a tensor-core sweep whose bounded wait gave up
+  int* tc_err = nullptr;         // set by a sweep whose bounded mbarrier wait gave up
   int inner_sweeps = 0;
   float* Hy32 = nullptr;         // FP32 copy of Hy in the sweep's slot layout
   float* R32 = nullptr;          // [Nqf][nface] FP64 residual F(uhat) - uhat, rounded
@@ -173,6 +180,11 @@ cudaError_t launch_sweep_fused(Ctx& c, int graph_mode);
 int fused_grid(int64_t nel);      // upper bound of the fused sweep's grid
 int device_sms();
 int tangent_grid(int64_t n_tan);
+void fill_face_weights(const Ctx& c, double* fw);   // face Gauss weight of each face point
+// tiled per-element transport sweep (sweep_tiled.cu)
+bool tiled_supported(const Ctx& c);
+cudaError_t build_tiled_operator(Ctx& c);           // after launch_rows; synchronous
+cudaError_t launch_sweep_tiled(Ctx& c, int graph_mode, int* grid_out);
 // mixed precision (mixed.cu)
 cudaError_t launch_hy_to_f32(Ctx& c);
 cudaError_t launch_correction(Ctx& c, int* n_launched);

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "ehdg_internal.h"
+#include "sweep_common.cuh"
 
 namespace ehdg {
 
@@ -19,11 +20,6 @@ namespace {
 
 constexpr int kFT = 4;                 // row groups per 32-element tile
 constexpr int kFusedMaxBlocks = 4096;
-
-__device__ __forceinline__ double fsum_warp(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 struct FusedParams {
   int64_t nel, nface;
@@ -49,61 +45,6 @@ struct FusedParams {
   int graph_mode;
   cudaGraphConditionalHandle handle;
 };
-
-// Final reduction of nblocks partials by the last block to take a ticket;
-// records r_k and sets the loop condition (same rule as the trace kernel).
-// partials[slot] receives this block's sum; the last of the nblocks blocks of
-// this launch to take a ticket sums partials[0 .. n_total_partials).
-__device__ void finish_residual(double acc, double* partials, unsigned int slot,
-                                unsigned int nblocks, IterState* it, double* hist, int max_iter,
-                                double tol, double res_scale, int graph_mode,
-                                cudaGraphConditionalHandle handle, int n_total_partials) {
-  __shared__ double red[32];
-  __shared__ bool last;
-  acc = fsum_warp(acc);
-  const int nw = (blockDim.x * blockDim.y) >> 5;
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int lane = tid & 31, wid = tid >> 5;
-  if (lane == 0) red[wid] = acc;
-  __syncthreads();
-  if (wid == 0) {
-    double v = (lane < nw) ? red[lane] : 0.0;
-    v = fsum_warp(v);
-    if (lane == 0) {
-      partials[slot] = v;
-      __threadfence();
-      last = (atomicAdd(&it->counter, 1u) == nblocks - 1);
-    }
-  }
-  __syncthreads();
-  if (!last) return;
-  __threadfence();
-  double v = 0.0;
-  for (int i = tid; i < n_total_partials; i += blockDim.x * blockDim.y)
-    v += reinterpret_cast<volatile double*>(partials)[i];
-  v = fsum_warp(v);
-  __syncthreads();
-  if (lane == 0) red[wid] = v;
-  __syncthreads();
-  if (tid == 0) {
-    double sum = 0.0;
-    for (int w = 0; w < nw; ++w) sum += red[w];
-    const double r = res_scale * sqrt(sum);
-    const int k = it->k;
-    if (k < max_iter) hist[k] = r;
-    it->k = k + 1;
-    it->r_last = r;
-    it->counter = 0u;
-    int cont = 1, status = EHDG_OK;
-    if (!isfinite(r)) { cont = 0; status = EHDG_ERR_DIVERGED; }
-    else if (r < tol) { cont = 0; status = EHDG_OK; }
-    else if (k + 1 >= max_iter) { cont = 0; status = EHDG_ERR_NOT_CONVERGED; }
-    it->cont = cont;
-    it->status = status;
-    __threadfence();
-    if (graph_mode) cudaGraphSetConditional(handle, (unsigned int)cont);
-  }
-}
 
 template <int NQ>
 __global__ void __launch_bounds__(32 * kFT, 4) k_sweep_fused(const FusedParams p) {
@@ -273,7 +214,7 @@ int fused_grid(int64_t nel) {
   return g < 1 ? 1 : (int)g;
 }
 
-static void fill_fw(const Ctx& c, double* fw) {
+void fill_face_weights(const Ctx& c, double* fw) {
   for (int g = 0; g < c.Nqf; ++g) {
     double w = 1.0;
     int rem = g;
@@ -340,7 +281,7 @@ cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
   p.nup = c.nup;
   p.elem_face = c.geo.elem_face;
   p.face_jf = c.geo.face_jf;
-  fill_fw(c, p.fw);
+  fill_face_weights(c, p.fw);
   p.uhat = c.uhat;
   p.it = c.it;
   p.Gy = c.Gy;
@@ -360,7 +301,9 @@ cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
   const int64_t ntiles = (c.nel + 31) / 32;
   int grid = 1;
   cudaError_t err;
-  switch (c.NQFS) {
+  if (c.Hyt) {
+    err = launch_sweep_tiled(c, graph_mode, &grid);
+  } else switch (c.NQFS) {
     case 8: err = launch_fused_t<8>(p, smem, ntiles, c.stream, &grid); break;
     case 12: err = launch_fused_t<12>(p, smem, ntiles, c.stream, &grid); break;
     case 16: err = launch_fused_t<16>(p, smem, ntiles, c.stream, &grid); break;
@@ -385,7 +328,7 @@ cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
   q.face_elem = c.geo.face_elem;
   q.face_local = c.geo.face_local;
   q.face_jf = c.geo.face_jf;
-  fill_fw(c, q.fw);
+  fill_face_weights(c, q.fw);
   q.gb = c.gb;
   q.gb_old = c.gb_old;
   q.Y = c.Y;
