@@ -108,6 +108,9 @@ struct Ctx {
   uint8_t* tile_nrows = nullptr; // [ntiles] rows of a tile (max over its elements)
   int64_t ntiles = 0;
   int64_t tile_rows = 0;         // rows in Hyt
+  int tiled_grid = 0;            // launch shape of the tiled sweep
+  size_t tiled_smem = 0;
+  int32_t* tiled_warp_tile = nullptr;   // [tiled_grid * warps per block] first tile of a warp
   // mixed precision (defect correction)
   bool mixed = false;
   ehdg_precision precision = EHDG_FP64;

@@ -31,13 +31,32 @@ namespace ehdg {
 
 namespace {
 
-constexpr int kTW = 2;                        // warps per block (independent)
-constexpr int kTS = 3;                        // stages per warp
+// compile-time tuning: warps per block (independent of each other), stages
+// per warp, independent FMA chains per row
+#ifndef EHDG_TILED_TW
+#define EHDG_TILED_TW 4
+#endif
+#ifndef EHDG_TILED_TS
+#define EHDG_TILED_TS 2
+#endif
+#ifndef EHDG_TILED_CH
+#define EHDG_TILED_CH 1
+#endif
+// minimum resident blocks per SM asked of the compiler (instances with up
+// to 28 face points per element)
+#ifndef EHDG_TILED_MINB
+#define EHDG_TILED_MINB 3
+#endif
+constexpr int kTW = EHDG_TILED_TW;
+constexpr int kTS = EHDG_TILED_TS;
+constexpr int kCH = EHDG_TILED_CH;
+static_assert(kCH == 1 || kCH == 2 || kCH == 4, "FMA chains per row: 1, 2 or 4");
 constexpr uint32_t kTileWaitLimit = 1u << 22; // mbarrier polls before giving up
 constexpr int kTiledMaxBlocks = 4096;         // same bound as the other transport sweep
 
 struct TiledParams {
   int64_t nel, nface, ntiles, total_rows;
+  const int32_t* warp_tile;      // [grid * kTW] tile holding each warp's first row
   const uint8_t* rowid;          // [slot][nel]
   const uint8_t* nrows;          // [nel]
   const uint8_t* nup;            // [nel]
@@ -104,23 +123,12 @@ __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
-// The tile holding global row J of the tile-major operator: the last tile
-// whose first row is <= J (tiles without rows share their successor's first
-// row, so the tile found has J among its rows).
-__device__ __forceinline__ int64_t tile_of_row(const int32_t* row0, int64_t ntiles, int64_t J) {
-  int64_t lo = 0, hi = ntiles - 1;
-  while (lo < hi) {
-    const int64_t mid = (lo + hi + 1) >> 1;
-    if ((int64_t)row0[mid] <= J) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
 // Each warp owns an equal, contiguous range of the operator's rows (so every
 // warp has the same work to within one row, whatever the tile boundaries) and
 // runs on its own: no block barrier before the final residual reduction.
 template <int F, int NQF>
-__global__ void __launch_bounds__(32 * kTW) k_sweep_tiled(const TiledParams p) {
+__global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 1)
+    k_sweep_tiled(const TiledParams p) {
   constexpr int NQ = F * NQF;
   constexpr uint32_t kRowBytes = (uint32_t)NQ * 32u * 8u;
   extern __shared__ __align__(256) unsigned char tsm[];
@@ -151,22 +159,45 @@ __global__ void __launch_bounds__(32 * kTW) k_sweep_tiled(const TiledParams p) {
                 kRowBytes);
 
   double acc_res = 0.0;
-  int64_t t = J0 < J1 ? tile_of_row(p.tile_row0, p.ntiles, J0) : 0;
+  int64_t t = J0 < J1 ? p.warp_tile[gw] : p.ntiles;
   int j = J0 < J1 ? (int)(J0 - p.tile_row0[t]) : 0;
   int nr_t = 0, nr_e = 0, nu_e = 0;
   int64_t e = 0;
   int fid[F];
   double jf[F], u[NQ];
+  // per-tile values of tile t, loaded as soon as t is known (one row before
+  // the warp enters the tile): face ids, row counts
+  int fid_n[F], nr_e_n = 0, nu_e_n = 0, nr_t_n = 0;
+  auto load_tile = [&](int64_t tt) {
+    const int64_t ee = tt * 32 + lane;
+    const bool live = tt < p.ntiles && ee < ne;
+    nr_t_n = tt < p.ntiles ? p.tile_nrows[tt] : 0;
+#pragma unroll
+    for (int f = 0; f < F; ++f) fid_n[f] = live ? p.elem_face[(int64_t)f * ne + ee] : 0;
+    nr_e_n = live ? p.nrows[ee] : 0;
+    nu_e_n = live ? p.nup[ee] : 0;
+  };
+  load_tile(t);
   bool fresh = true;                             // tile t not gathered yet
+  // the next row's Gy value and point id are loaded one row ahead (slots
+  // beyond an element's rows exist in both arrays and are never used)
+  double gy_n = 0.0;
+  int rid_n = 0;
+  if (J0 < J1 && t * 32 + lane < ne) {
+    gy_n = p.Gy[(int64_t)j * ne + t * 32 + lane];
+    rid_n = p.rowid[(int64_t)j * ne + t * 32 + lane];
+  }
   int64_t J = J0;
   for (; J < J1; ++J) {
     if (fresh) {
       // the element's faces, their Jacobians and uhat^k at its face points
       e = t * 32 + lane;
       const bool live = e < ne;
-      nr_t = p.tile_nrows[t];
+      nr_t = nr_t_n;
+      nr_e = nr_e_n;
+      nu_e = nu_e_n;
 #pragma unroll
-      for (int f = 0; f < F; ++f) fid[f] = live ? p.elem_face[(int64_t)f * ne + e] : 0;
+      for (int f = 0; f < F; ++f) fid[f] = fid_n[f];
 #pragma unroll
       for (int f = 0; f < F; ++f) {
         jf[f] = live ? p.face_jf[fid[f]] : 0.0;
@@ -174,14 +205,25 @@ __global__ void __launch_bounds__(32 * kTW) k_sweep_tiled(const TiledParams p) {
         for (int g = 0; g < NQF; ++g)
           u[f * NQF + g] = live ? src[(int64_t)g * nface + fid[f]] : 0.0;
       }
-      nr_e = live ? p.nrows[e] : 0;
-      nu_e = live ? p.nup[e] : 0;
       fresh = false;
     }
-    // issued early, used after the FMA chain
     const bool row_live = j < nr_e;
-    const double gy = row_live ? p.Gy[(int64_t)j * ne + e] : 0.0;
-    const int rid = row_live ? p.rowid[(int64_t)j * ne + e] : 0;
+    const double gy = gy_n;
+    const int rid = rid_n;
+    const int j_cur = j;
+    // advance to the next row (and tile) and start its Gy / point-id loads
+    if (++j == nr_t) {
+      j = 0;
+      do {
+        ++t;
+      } while (t < p.ntiles && p.tile_nrows[t] == 0);
+      fresh = true;
+      if (J + 1 < J1) load_tile(t);
+    }
+    if (J + 1 < J1 && t * 32 + lane < ne) {
+      gy_n = p.Gy[(int64_t)j * ne + t * 32 + lane];
+      rid_n = p.rowid[(int64_t)j * ne + t * 32 + lane];
+    }
 
     const int st = (int)((J - J0) % kTS);
     const uint32_t par = (uint32_t)(((J - J0) / kTS) & 1);
@@ -204,15 +246,15 @@ __global__ void __launch_bounds__(32 * kTW) k_sweep_tiled(const TiledParams p) {
       break;
     }
     const double* Hs = stages + (size_t)st * NQ * 32;
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    double a[kCH];
+    a[0] = row_live ? gy : 0.0;
 #pragma unroll
-    for (int c = 0; c < NQ; c += 4) {
-      a0 = fma(Hs[c * 32 + lane], u[c], a0);
-      if (c + 1 < NQ) a1 = fma(Hs[(c + 1) * 32 + lane], u[c + 1], a1);
-      if (c + 2 < NQ) a2 = fma(Hs[(c + 2) * 32 + lane], u[c + 2], a2);
-      if (c + 3 < NQ) a3 = fma(Hs[(c + 3) * 32 + lane], u[c + 3], a3);
-    }
-    const double acc = gy + ((a0 + a1) + (a2 + a3));
+    for (int q = 1; q < kCH; ++q) a[q] = 0.0;
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) a[c % kCH] = fma(Hs[c * 32 + lane], u[c], a[c % kCH]);
+    double acc = a[0];
+    if constexpr (kCH == 2) acc = a[0] + a[1];
+    if constexpr (kCH == 4) acc = (a[0] + a[1]) + (a[2] + a[3]);
     __syncwarp();                                // every lane has read the stage
     if (Jp < J1) {
       if (lane == 0)
@@ -233,22 +275,15 @@ __global__ void __launch_bounds__(32 * kTW) k_sweep_tiled(const TiledParams p) {
 #pragma unroll
       for (int c = 0; c < NQ; ++c)
         if (c == rid) uk = u[c];
-      if (j < nu_e) {
+      if (j_cur < nu_e) {
         const int64_t pt = (int64_t)g * nface + face;
         dst[pt] = acc;
         const double d = acc - uk;
-        acc_res += jfv * p.fw[g] * d * d;
+        acc_res = fma(jfv * p.fw[g] * d, d, acc_res);
         if (p.R_out) p.R_out[pt] = (float)d;
       } else {
         p.Y[(int64_t)rid * ne + e] = acc;
       }
-    }
-    if (++j == nr_t) {                           // next tile with rows
-      j = 0;
-      do {
-        ++t;
-      } while (t < p.ntiles && p.tile_nrows[t] == 0);
-      fresh = true;
     }
   }
   // copies still in flight (only after a wait gave up): wait for them, bounded
@@ -290,8 +325,10 @@ __global__ void k_tile_hy(int64_t nel, int nq, int64_t ntiles, const int32_t* ti
   }
 }
 
+// launch shape of one instance: dynamic shared memory and a one-wave grid
+// with at least four rows per warp
 template <int F, int NQF>
-cudaError_t launch_tiled_t(const TiledParams& p, int* grid_out, cudaStream_t s) {
+cudaError_t tiled_config(int64_t total_rows, int64_t ntiles, int* grid, size_t* smem_out) {
   constexpr int NQ = F * NQF;
   const size_t smem = sizeof(double) * (size_t)kTW * kTS * NQ * 32;
   auto kern = k_sweep_tiled<F, NQF>;
@@ -306,28 +343,59 @@ cudaError_t launch_tiled_t(const TiledParams& p, int* grid_out, cudaStream_t s) 
     bpsm = 1;
   }
   int64_t g = (int64_t)bpsm * device_sms();
-  const int64_t by_rows = (p.total_rows + 4 * kTW - 1) / (4 * kTW);   // >= 4 rows per warp
+  const int64_t by_rows = (total_rows + 4 * kTW - 1) / (4 * kTW);
   if (g > by_rows) g = by_rows;
-  if (g > p.ntiles) g = p.ntiles;
+  if (g > ntiles) g = ntiles;
   if (g > kTiledMaxBlocks) g = kTiledMaxBlocks;
   if (g < 1) g = 1;
-  *grid_out = (int)g;
-  kern<<<(int)g, 32 * kTW, smem, s>>>(p);
+  *grid = (int)g;
+  *smem_out = smem;
+  return cudaSuccess;
+}
+
+template <int F, int NQF>
+cudaError_t tiled_launch(const TiledParams& p, int grid, size_t smem, cudaStream_t s) {
+  k_sweep_tiled<F, NQF><<<grid, 32 * kTW, smem, s>>>(p);
   return cudaGetLastError();
+}
+
+struct TiledOps {
+  cudaError_t (*config)(int64_t, int64_t, int*, size_t*);
+  cudaError_t (*launch)(const TiledParams&, int, size_t, cudaStream_t);
+};
+
+template <int F, int NQF>
+constexpr TiledOps ops_of() {
+  return TiledOps{&tiled_config<F, NQF>, &tiled_launch<F, NQF>};
+}
+
+// (faces, points per face) pairs with a kernel instance: quadrilaterals with
+// 2..10 Gauss points per edge, hexahedra with 2x2 or 3x3 per face
+bool tiled_ops(int F, int Nqf, TiledOps* out) {
+  if (F == 4) {
+    switch (Nqf) {
+      case 2: *out = ops_of<4, 2>(); return true;
+      case 3: *out = ops_of<4, 3>(); return true;
+      case 4: *out = ops_of<4, 4>(); return true;
+      case 5: *out = ops_of<4, 5>(); return true;
+      case 6: *out = ops_of<4, 6>(); return true;
+      case 7: *out = ops_of<4, 7>(); return true;
+      case 8: *out = ops_of<4, 8>(); return true;
+      case 9: *out = ops_of<4, 9>(); return true;
+      case 10: *out = ops_of<4, 10>(); return true;
+      default: return false;
+    }
+  }
+  if (F == 6 && Nqf == 4) { *out = ops_of<6, 4>(); return true; }
+  if (F == 6 && Nqf == 9) { *out = ops_of<6, 9>(); return true; }
+  return false;
 }
 
 }  // namespace
 
-// (faces, points per face) pairs with a kernel instance: quadrilaterals with
-// 2..10 Gauss points per edge, hexahedra with 2x2 or 3x3 per face
-static bool tiled_shape(int F, int Nqf) {
-  if (F == 4) return Nqf >= 2 && Nqf <= 10;
-  if (F == 6) return Nqf == 4 || Nqf == 9;
-  return false;
-}
-
 bool tiled_supported(const Ctx& c) {
-  return c.pde == EHDG_TRANSPORT && !c.shared_op && tiled_shape(c.F, c.Nqf);
+  TiledOps ops;
+  return c.pde == EHDG_TRANSPORT && !c.shared_op && tiled_ops(c.F, c.Nqf, &ops);
 }
 
 cudaError_t build_tiled_operator(Ctx& c) {
@@ -360,6 +428,23 @@ cudaError_t build_tiled_operator(Ctx& c) {
   if ((err = cudaMemcpy(c.tile_row0, row0.data(), sizeof(int32_t) * (size_t)ntiles,
                         cudaMemcpyHostToDevice)) != cudaSuccess)
     return err;
+  // launch shape, fixed for the context, and the tile of each warp's first row
+  TiledOps ops;
+  if (!tiled_ops(c.F, c.Nqf, &ops)) return cudaErrorInvalidValue;
+  if ((err = ops.config(rows, ntiles, &c.tiled_grid, &c.tiled_smem)) != cudaSuccess) return err;
+  const int64_t nwarps = (int64_t)c.tiled_grid * kTW;
+  std::vector<int32_t> wt((size_t)nwarps, 0);
+  for (int64_t gw = 0, tt = 0; gw < nwarps; ++gw) {
+    const int64_t J0 = rows * gw / nwarps;
+    while (tt + 1 < ntiles && row0[tt + 1] <= J0) ++tt;   // last tile starting at or before J0
+    wt[gw] = (int32_t)tt;
+  }
+  if ((err = dalloc_raw(c, (void**)&c.tiled_warp_tile, sizeof(int32_t) * (size_t)nwarps)) !=
+      cudaSuccess)
+    return err;
+  if ((err = cudaMemcpy(c.tiled_warp_tile, wt.data(), sizeof(int32_t) * (size_t)nwarps,
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+    return err;
   int grid = (int)std::min<int64_t>(ntiles, 152 * 16);
   k_tile_hy<<<grid < 1 ? 1 : grid, 256, 0, c.stream>>>(c.nel, c.NQFS, ntiles, c.tile_row0,
                                                        c.tile_nrows, c.nrows, c.Hy, c.Hyt);
@@ -372,6 +457,7 @@ cudaError_t launch_sweep_tiled(Ctx& c, int graph_mode, int* grid_out) {
   p.nface = c.nface;
   p.ntiles = c.ntiles;
   p.total_rows = c.tile_rows;
+  p.warp_tile = c.tiled_warp_tile;
   p.rowid = c.rowid;
   p.nrows = c.nrows;
   p.nup = c.nup;
@@ -395,24 +481,10 @@ cudaError_t launch_sweep_tiled(Ctx& c, int graph_mode, int* grid_out) {
   p.graph_mode = graph_mode;
   p.handle = c.handle;
   p.err = c.tc_err;
-  if (c.F == 4) {
-    switch (c.Nqf) {
-      case 2: return launch_tiled_t<4, 2>(p, grid_out, c.stream);
-      case 3: return launch_tiled_t<4, 3>(p, grid_out, c.stream);
-      case 4: return launch_tiled_t<4, 4>(p, grid_out, c.stream);
-      case 5: return launch_tiled_t<4, 5>(p, grid_out, c.stream);
-      case 6: return launch_tiled_t<4, 6>(p, grid_out, c.stream);
-      case 7: return launch_tiled_t<4, 7>(p, grid_out, c.stream);
-      case 8: return launch_tiled_t<4, 8>(p, grid_out, c.stream);
-      case 9: return launch_tiled_t<4, 9>(p, grid_out, c.stream);
-      case 10: return launch_tiled_t<4, 10>(p, grid_out, c.stream);
-      default: break;
-    }
-  } else if (c.F == 6) {
-    if (c.Nqf == 4) return launch_tiled_t<6, 4>(p, grid_out, c.stream);
-    if (c.Nqf == 9) return launch_tiled_t<6, 9>(p, grid_out, c.stream);
-  }
-  return cudaErrorInvalidValue;
+  TiledOps ops;
+  if (!tiled_ops(c.F, c.Nqf, &ops)) return cudaErrorInvalidValue;
+  *grid_out = c.tiled_grid;
+  return ops.launch(p, c.tiled_grid, c.tiled_smem, c.stream);
 }
 
 }  // namespace ehdg
