@@ -948,12 +948,18 @@ cudaError_t launch_final(Ctx& c) {
   p.G = c.G;
   p.H = c.H;
   p.u = c.u;
-  const size_t smem = sizeof(double) * ((p.shared ? (size_t)c.n * c.NQFS : 0) + (size_t)c.NQFS * 32);
-  cudaError_t err = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  const int grid = persistent_grid(k_final, 32 * kStepT, smem, (c.nel + 31) / 32);
-  k_final<<<grid, dim3(32, kStepT), smem, c.stream>>>(p);
-  err = cudaGetLastError();
+  cudaError_t err;
+  if (c.Ht) {
+    err = launch_final_tiled(c);
+  } else {
+    const size_t smem =
+        sizeof(double) * ((p.shared ? (size_t)c.n * c.NQFS : 0) + (size_t)c.NQFS * 32);
+    err = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    const int grid = persistent_grid(k_final, 32 * kStepT, smem, (c.nel + 31) / 32);
+    k_final<<<grid, dim3(32, kStepT), smem, c.stream>>>(p);
+    err = cudaGetLastError();
+  }
   if (err != cudaSuccess) return err;
   const int64_t total = (int64_t)c.Nqf * c.nface;
   k_trace_end<<<(int)((total + 255) / 256), 256, 0, c.stream>>>(total, p.cn, c.it, c.uhat,

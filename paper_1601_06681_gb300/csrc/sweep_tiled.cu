@@ -123,6 +123,22 @@ __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
   return false;
 }
 
+// bounded wait polled by every lane of a warp (each lane then sees the
+// stage's data); the result is warp-uniform
+__device__ __forceinline__ bool wait_phase_warp(uint32_t mbar, uint32_t parity) {
+  for (uint32_t it = 0; it < kTileWaitLimit; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred w;\n mbarrier.try_wait.parity.shared::cta.b64 w, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, w;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(parity)
+        : "memory");
+    if (__all_sync(0xffffffffu, done)) return true;
+  }
+  return false;
+}
+
 // Each warp owns an equal, contiguous range of the operator's rows (so every
 // warp has the same work to within one row, whatever the tile boundaries) and
 // runs on its own: no block barrier before the final residual reduction.
@@ -226,22 +242,7 @@ __global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 
     }
 
     const int st = (int)((J - J0) % kTS);
-    const uint32_t par = (uint32_t)(((J - J0) / kTS) & 1);
-    bool ok = false;
-    for (uint32_t it = 0; it < kTileWaitLimit; ++it) {
-      uint32_t done;
-      asm volatile(
-          "{\n .reg .pred w;\n mbarrier.try_wait.parity.shared::cta.b64 w, [%1], %2;\n"
-          " selp.u32 %0, 1, 0, w;\n}\n"
-          : "=r"(done)
-          : "r"(saddr(&mbar[w][st])), "r"(par)
-          : "memory");
-      if (__all_sync(0xffffffffu, done)) {
-        ok = true;
-        break;
-      }
-    }
-    if (!ok) {
+    if (!wait_phase_warp(saddr(&mbar[w][st]), (uint32_t)(((J - J0) / kTS) & 1))) {
       if (lane == 0) atomicExch(p.err, 1);
       break;
     }
@@ -308,6 +309,126 @@ __global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 
   }
 }
 
+// Reconstruction after the last iteration, u = G + H uhat (Algorithm 1
+// returns the local solution for the final trace; Crank-Nicolson then takes
+// u^{n+1} = 2 v - u^n), with H kept tile-major like Hy: for each tile of 32
+// elements its n rows, NQFS columns x 32 elements each. Warps take equal
+// contiguous ranges of the tiles' rows and stream them as the sweep does.
+struct FinalTParams {
+  int64_t nel, nface, ntiles, total_rows;
+  int n, cn;
+  const int32_t* elem_face;     // [F][nel]
+  const double* Ht;             // [tile][n][NQFS][32]
+  const double* uhat;           // [2][Nqf][nface]
+  const IterState* it;
+  const double* G;              // [n][nel]
+  double* u;                    // [n][nel]
+  int* err;
+};
+
+template <int F, int NQF>
+__global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 1)
+    k_final_tiled(const FinalTParams p) {
+  constexpr int NQ = F * NQF;
+  constexpr uint32_t kRowBytes = (uint32_t)NQ * 32u * 8u;
+  extern __shared__ __align__(256) unsigned char tsm[];
+  __shared__ __align__(8) uint64_t mbar[kTW][kTS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* stages = reinterpret_cast<double*>(tsm) + (size_t)w * kTS * NQ * 32;
+  if (lane == 0) {
+    for (int s = 0; s < kTS; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[w][s])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+
+  const int64_t ne = p.nel, nface = p.nface;
+  const double* src = p.uhat + (int64_t)((p.it->k + 1) & 1) * NQF * nface;
+  const int64_t nwarps = (int64_t)gridDim.x * kTW, gw = (int64_t)blockIdx.x * kTW + w;
+  const int64_t J0 = p.total_rows * gw / nwarps, J1 = p.total_rows * (gw + 1) / nwarps;
+  int64_t Jp = J0;
+  for (int s = 0; s < kTS && Jp < J1; ++s, ++Jp)
+    if (lane == 0)
+      issue_row(saddr(&mbar[w][s]), saddr(stages + (size_t)s * NQ * 32), p.Ht + Jp * NQ * 32,
+                kRowBytes);
+
+  int64_t t = J0 / p.n;
+  int r = (int)(J0 - t * p.n);
+  int fid_n[F];
+  auto load_faces = [&](int64_t tt) {
+    const int64_t ee = tt * 32 + lane;
+#pragma unroll
+    for (int f = 0; f < F; ++f)
+      fid_n[f] = (tt < p.ntiles && ee < ne) ? p.elem_face[(int64_t)f * ne + ee] : 0;
+  };
+  if (J0 < J1) load_faces(t);
+  double u[NQ];
+  int64_t e = 0;
+  bool fresh = true;
+  int64_t J = J0;
+  for (; J < J1; ++J) {
+    if (fresh) {
+      e = t * 32 + lane;
+#pragma unroll
+      for (int f = 0; f < F; ++f)
+#pragma unroll
+        for (int g = 0; g < NQF; ++g)
+          u[f * NQF + g] = e < ne ? src[(int64_t)g * nface + fid_n[f]] : 0.0;
+      fresh = false;
+    }
+    const bool live = e < ne;
+    const int64_t at = (int64_t)r * ne + e;
+    const double g0 = live ? p.G[at] : 0.0;           // used after the FMA chain
+    const double uold = (live && p.cn) ? p.u[at] : 0.0;
+    if (++r == p.n) {
+      r = 0;
+      ++t;
+      fresh = true;
+      if (J + 1 < J1) load_faces(t);
+    }
+    const int st = (int)((J - J0) % kTS);
+    if (!wait_phase_warp(saddr(&mbar[w][st]), (uint32_t)(((J - J0) / kTS) & 1))) {
+      if (lane == 0) atomicExch(p.err, 1);
+      break;
+    }
+    const double* Hs = stages + (size_t)st * NQ * 32;
+    double acc = 0.0;
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) acc = fma(Hs[c * 32 + lane], u[c], acc);
+    __syncwarp();                                // every lane has read the stage
+    if (Jp < J1) {
+      if (lane == 0)
+        issue_row(saddr(&mbar[w][st]), saddr(stages + (size_t)st * NQ * 32),
+                  p.Ht + Jp * NQ * 32, kRowBytes);
+      ++Jp;
+    }
+    acc += g0;
+    if (live) p.u[at] = p.cn ? 2.0 * acc - uold : acc;
+  }
+  for (int64_t Jw = J; Jw < Jp; ++Jw) {
+    const int st = (int)((Jw - J0) % kTS);
+    if (lane == 0) wait_phase(saddr(&mbar[w][st]), (uint32_t)(((Jw - J0) / kTS) & 1));
+  }
+  __syncwarp();
+}
+
+// Tile-major copy of the reconstruction operator H ([n][NQFS][nel] ->
+// [tile][n][NQFS][32], zero past the last element).
+__global__ void k_tile_h(int64_t nel, int n, int nq, int64_t ntiles, const double* H, double* Ht) {
+  const int64_t total = ntiles * n * nq * 32;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int l = (int)(i & 31);
+    const int64_t rest = i >> 5;                 // (tile * n + r) * nq + c
+    const int c = (int)(rest % nq);
+    const int64_t tr = rest / nq;
+    const int r = (int)(tr % n);
+    const int64_t tile = tr / n;
+    const int64_t e = tile * 32 + l;
+    Ht[i] = e < nel ? H[((int64_t)r * nq + c) * nel + e] : 0.0;
+  }
+}
+
 // Tile-major copy of the compacted per-element rows; rows an element does not
 // use are zero, as are the lanes past the last element.
 __global__ void k_tile_hy(int64_t nel, int nq, int64_t ntiles, const int32_t* tile_row0,
@@ -325,13 +446,12 @@ __global__ void k_tile_hy(int64_t nel, int nq, int64_t ntiles, const int32_t* ti
   }
 }
 
-// launch shape of one instance: dynamic shared memory and a one-wave grid
-// with at least four rows per warp
-template <int F, int NQF>
-cudaError_t tiled_config(int64_t total_rows, int64_t ntiles, int* grid, size_t* smem_out) {
-  constexpr int NQ = F * NQF;
+// launch shape of one kernel instance: dynamic shared memory and a one-wave
+// grid with at least four rows per warp
+template <class K>
+cudaError_t tiled_shape_of(K kern, int NQ, int64_t total_rows, int64_t ntiles, int* grid,
+                           size_t* smem_out) {
   const size_t smem = sizeof(double) * (size_t)kTW * kTS * NQ * 32;
-  auto kern = k_sweep_tiled<F, NQF>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -354,6 +474,22 @@ cudaError_t tiled_config(int64_t total_rows, int64_t ntiles, int* grid, size_t* 
 }
 
 template <int F, int NQF>
+cudaError_t tiled_config(int64_t total_rows, int64_t ntiles, int* grid, size_t* smem_out) {
+  return tiled_shape_of(k_sweep_tiled<F, NQF>, F * NQF, total_rows, ntiles, grid, smem_out);
+}
+
+template <int F, int NQF>
+cudaError_t final_config(int64_t total_rows, int64_t ntiles, int* grid, size_t* smem_out) {
+  return tiled_shape_of(k_final_tiled<F, NQF>, F * NQF, total_rows, ntiles, grid, smem_out);
+}
+
+template <int F, int NQF>
+cudaError_t final_launch(const FinalTParams& p, int grid, size_t smem, cudaStream_t s) {
+  k_final_tiled<F, NQF><<<grid, 32 * kTW, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
+template <int F, int NQF>
 cudaError_t tiled_launch(const TiledParams& p, int grid, size_t smem, cudaStream_t s) {
   k_sweep_tiled<F, NQF><<<grid, 32 * kTW, smem, s>>>(p);
   return cudaGetLastError();
@@ -362,11 +498,14 @@ cudaError_t tiled_launch(const TiledParams& p, int grid, size_t smem, cudaStream
 struct TiledOps {
   cudaError_t (*config)(int64_t, int64_t, int*, size_t*);
   cudaError_t (*launch)(const TiledParams&, int, size_t, cudaStream_t);
+  cudaError_t (*final_config)(int64_t, int64_t, int*, size_t*);
+  cudaError_t (*final_launch)(const FinalTParams&, int, size_t, cudaStream_t);
 };
 
 template <int F, int NQF>
 constexpr TiledOps ops_of() {
-  return TiledOps{&tiled_config<F, NQF>, &tiled_launch<F, NQF>};
+  return TiledOps{&tiled_config<F, NQF>, &tiled_launch<F, NQF>, &final_config<F, NQF>,
+                  &final_launch<F, NQF>};
 }
 
 // (faces, points per face) pairs with a kernel instance: quadrilaterals with
@@ -448,7 +587,36 @@ cudaError_t build_tiled_operator(Ctx& c) {
   int grid = (int)std::min<int64_t>(ntiles, 152 * 16);
   k_tile_hy<<<grid < 1 ? 1 : grid, 256, 0, c.stream>>>(c.nel, c.NQFS, ntiles, c.tile_row0,
                                                        c.tile_nrows, c.nrows, c.Hy, c.Hyt);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  // reconstruction operator, all n rows of every tile
+  const int64_t hrows = ntiles * c.n;
+  if ((err = dalloc_raw(c, (void**)&c.Ht, sizeof(double) * (size_t)hrows * c.NQFS * 32)) !=
+      cudaSuccess)
+    return err;
+  if ((err = ops.final_config(hrows, ntiles, &c.ftiled_grid, &c.ftiled_smem)) != cudaSuccess)
+    return err;
+  k_tile_h<<<152 * 8, 256, 0, c.stream>>>(c.nel, c.n, c.NQFS, ntiles, c.H, c.Ht);
   return cudaGetLastError();
+}
+
+cudaError_t launch_final_tiled(Ctx& c) {
+  FinalTParams p;
+  p.nel = c.nel;
+  p.nface = c.nface;
+  p.ntiles = c.ntiles;
+  p.total_rows = c.ntiles * c.n;
+  p.n = c.n;
+  p.cn = (c.scheme == EHDG_CN) ? 1 : 0;
+  p.elem_face = c.geo.elem_face;
+  p.Ht = c.Ht;
+  p.uhat = c.uhat;
+  p.it = c.it;
+  p.G = c.G;
+  p.u = c.u;
+  p.err = c.tc_err;
+  TiledOps ops;
+  if (!tiled_ops(c.F, c.Nqf, &ops)) return cudaErrorInvalidValue;
+  return ops.final_launch(p, c.ftiled_grid, c.ftiled_smem, c.stream);
 }
 
 cudaError_t launch_sweep_tiled(Ctx& c, int graph_mode, int* grid_out) {
