@@ -130,9 +130,9 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source is unchanged since it was captured (else None)."""
+def kernel_traffic(kernel, source):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source file is unchanged since it was captured (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -142,9 +142,9 @@ def kernel_traffic(kernel):
     ent = d.get(kernel)
     if not ent:
         return None
-    src = os.path.join(ROOT, "paper_1601_06681_gb300", "csrc", "kernels.cu")
+    src = os.path.join(ROOT, "paper_1601_06681_gb300", "csrc", source)
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return ent["bytes_per_launch"] if ent.get("kernels_cu_sha") == sha else None
+    return ent["bytes_per_launch"] if ent.get("source_sha") == sha else None
 
 
 # ---------------------------------------------------------------------------
@@ -315,15 +315,17 @@ def run_ours(args):
     e_s = time.perf_counter() - e0
     e2e_value = ws * trace_dof * it_e2e / e_s
 
-    # roofline of the dominant kernel (element sweep): per element and sweep it
-    # reads its computed operator rows (rows x NQFS doubles), Gy (rows), the
-    # trace at its NQFS face points, its face ids and row ids, and writes rows
-    # values; flops = 2 x rows x NQFS
+    # roofline of the dominant kernel (the element sweep, k_sweep_tiled): per
+    # element and sweep it reads its operator rows (rows x NQFS doubles), Gy
+    # and the point id of each row, the trace at its NQFS face points, its 4
+    # face ids and face Jacobians and its two row counts, and writes one value
+    # per row; flops = 2 x rows x NQFS
     n_elem_launch, elem_ms = stats["elem"]
     info = solver.info
     nq = 4 * info["Nqf"]
     rows = info["sweep_rows"]
-    alg_bytes = 8 * (rows * (nq + 2) + nq * info["n_elem"]) + (4 * 4 + 1) * info["n_elem"] + rows
+    alg_bytes = (8 * rows * (nq + 2) + rows + 8 * nq * info["n_elem"]
+                 + (4 * 4 + 4 * 8 + 2) * info["n_elem"])
     avg_ms = elem_ms / max(n_elem_launch, 1)
     achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
     peaks, peak_src = measured_peaks()
@@ -349,13 +351,13 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(u0_h.nbytes + g_h.nbytes),
                     "d2h_bytes_per_step": int(u_out.nbytes + uh_out.nbytes)},
             "gpu_launches": int(launches),
-            "roofline": {"kernel": "k_elem", "bound": "alu",
+            "roofline": {"kernel": "k_sweep_tiled", "bound": "alu",
                          "achieved": flops_per_launch / (avg_ms * 1e-3) / 1e12,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": flops_per_launch / (avg_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                                         "(FMA-chain probe measured 1.30 TFLOP/s)",
-                         "traffic": kernel_traffic("k_elem"),
+                         "traffic": kernel_traffic("k_sweep_tiled", "sweep_tiled.cu"),
                          "alg_bytes_per_launch": alg_bytes,
                          "flops_per_launch": flops_per_launch,
                          "avg_launch_us": avg_ms * 1e3,
