@@ -112,6 +112,7 @@ struct Ctx {
   size_t tiled_smem = 0;
   int32_t* tiled_warp_tile = nullptr;   // [tiled_grid * warps per block] first tile of a warp
   double* Ht = nullptr;          // reconstruction operator H, tile-major: [tile][n][NQFS][32]
+  float* Hyt32 = nullptr;        // FP32 copy of Hyt (mixed precision)
   int ftiled_grid = 0;           // launch shape of the tiled reconstruction
   size_t ftiled_smem = 0;
   // mixed precision (defect correction)
@@ -192,6 +193,7 @@ bool tiled_supported(const Ctx& c);
 cudaError_t build_tiled_operator(Ctx& c);           // after launch_rows; synchronous
 cudaError_t launch_sweep_tiled(Ctx& c, int graph_mode, int* grid_out);
 cudaError_t launch_final_tiled(Ctx& c);              // u = G + H uhat, per-element H
+cudaError_t launch_lp_sweep_tiled(Ctx& c, const float* in, float* out);   // FP32 correction sweep
 // mixed precision (mixed.cu)
 cudaError_t launch_hy_to_f32(Ctx& c);
 cudaError_t launch_correction(Ctx& c, int* n_launched);

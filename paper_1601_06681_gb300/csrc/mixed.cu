@@ -251,6 +251,17 @@ cudaError_t launch_lp_sweep(Ctx& c, const float* in, float* out) {
     }
     return err;
   }
+  if (c.Hyt32) {
+    cudaError_t err = launch_lp_sweep_tiled(c, in, out);
+    if (err != cudaSuccess) return err;
+    if (c.n_tan > 0) {
+      k_tangent_lp<<<grid1d(c.n_tan, 256, 152 * 4), 256, 0, c.stream>>>(
+          c.n_tan, c.nel, c.nface, c.Nqf, c.tan_g, c.tan_face, c.geo.face_elem,
+          c.geo.face_local, c.Y32, c.R32, out);
+      err = cudaGetLastError();
+    }
+    return err;
+  }
   LpParams p;
   p.nel = c.nel;
   p.nface = c.nface;

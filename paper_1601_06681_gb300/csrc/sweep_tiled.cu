@@ -309,6 +309,145 @@ __global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 
   }
 }
 
+// Low-precision correction sweep of the mixed form (delta = R + S Hy delta,
+// the correction equation of the FP64 trace fixed point), FP32 on the CUDA
+// cores, with an FP32 copy of the tile-major operator. Same row ranges and
+// warp starts as the FP64 sweep; rows are half as long, so each warp keeps
+// kLS stages in the same shared memory. Owned points: out = R + row value;
+// rows of points with beta.n = 0 go to Y32 for the finishing kernel.
+constexpr int kLS = 2 * kTS;
+
+struct LpTParams {
+  int64_t nel, nface, ntiles, total_rows;
+  const int32_t* warp_tile;
+  const int32_t* tile_row0;
+  const uint8_t* tile_nrows;
+  const uint8_t* rowid;
+  const uint8_t* nrows;
+  const uint8_t* nup;
+  const int32_t* elem_face;
+  const float* Hyt32;           // tile-major rows, FP32
+  const float* R;               // [Nqf][nface]
+  const float* in;
+  float* out;
+  float* Y32;                   // [NQFS][nel]
+  int* err;
+};
+
+template <int F, int NQF>
+__global__ void __launch_bounds__(32 * kTW) k_sweep_lp_tiled(const LpTParams p) {
+  constexpr int NQ = F * NQF;
+  constexpr uint32_t kRowBytes = (uint32_t)NQ * 32u * 4u;
+  extern __shared__ __align__(256) unsigned char tsm[];
+  __shared__ __align__(8) uint64_t mbar[kTW][kLS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  float* stages = reinterpret_cast<float*>(tsm) + (size_t)w * kLS * NQ * 32;
+  if (lane == 0) {
+    for (int s = 0; s < kLS; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[w][s])));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+
+  const int64_t ne = p.nel, nface = p.nface;
+  const int64_t nwarps = (int64_t)gridDim.x * kTW, gw = (int64_t)blockIdx.x * kTW + w;
+  const int64_t J0 = p.total_rows * gw / nwarps, J1 = p.total_rows * (gw + 1) / nwarps;
+  int64_t Jp = J0;
+  for (int s = 0; s < kLS && Jp < J1; ++s, ++Jp)
+    if (lane == 0)
+      issue_row(saddr(&mbar[w][s]), saddr(stages + (size_t)s * NQ * 32),
+                reinterpret_cast<const double*>(p.Hyt32 + Jp * NQ * 32), kRowBytes);
+
+  int64_t t = J0 < J1 ? p.warp_tile[gw] : p.ntiles;
+  int j = J0 < J1 ? (int)(J0 - p.tile_row0[t]) : 0;
+  int nr_t = 0, nr_e = 0, nu_e = 0;
+  int64_t e = 0;
+  int fid[F];
+  float d[NQ];
+  int fid_n[F], nr_e_n = 0, nu_e_n = 0, nr_t_n = 0;
+  auto load_tile = [&](int64_t tt) {
+    const int64_t ee = tt * 32 + lane;
+    const bool live = tt < p.ntiles && ee < ne;
+    nr_t_n = tt < p.ntiles ? p.tile_nrows[tt] : 0;
+#pragma unroll
+    for (int f = 0; f < F; ++f) fid_n[f] = live ? p.elem_face[(int64_t)f * ne + ee] : 0;
+    nr_e_n = live ? p.nrows[ee] : 0;
+    nu_e_n = live ? p.nup[ee] : 0;
+  };
+  load_tile(t);
+  bool fresh = true;
+  int rid_n = (J0 < J1 && t * 32 + lane < ne) ? p.rowid[(int64_t)j * ne + t * 32 + lane] : 0;
+  int64_t J = J0;
+  for (; J < J1; ++J) {
+    if (fresh) {
+      e = t * 32 + lane;
+      const bool live = e < ne;
+      nr_t = nr_t_n;
+      nr_e = nr_e_n;
+      nu_e = nu_e_n;
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        fid[f] = fid_n[f];
+#pragma unroll
+        for (int g = 0; g < NQF; ++g)
+          d[f * NQF + g] = live ? p.in[(int64_t)g * nface + fid[f]] : 0.f;
+      }
+      fresh = false;
+    }
+    const bool row_live = j < nr_e;
+    const int rid = rid_n;
+    const bool owned = row_live && j < nu_e;
+    // the owned point and its R value, loaded before the FMA chain
+    const int f0 = rid / NQF, g0 = rid - f0 * NQF;
+    int face = 0;
+#pragma unroll
+    for (int q = 0; q < F; ++q)
+      if (q == f0) face = fid[q];
+    const int64_t pt = (int64_t)g0 * nface + face;
+    const float rv = owned ? p.R[pt] : 0.f;
+    if (++j == nr_t) {
+      j = 0;
+      do {
+        ++t;
+      } while (t < p.ntiles && p.tile_nrows[t] == 0);
+      fresh = true;
+      if (J + 1 < J1) load_tile(t);
+    }
+    if (J + 1 < J1 && t * 32 + lane < ne) rid_n = p.rowid[(int64_t)j * ne + t * 32 + lane];
+
+    const int st = (int)((J - J0) % kLS);
+    if (!wait_phase_warp(saddr(&mbar[w][st]), (uint32_t)(((J - J0) / kLS) & 1))) {
+      if (lane == 0) atomicExch(p.err, 1);
+      break;
+    }
+    const float* Hs = stages + (size_t)st * NQ * 32;
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int c = 0; c < NQ; c += 2) {
+      a0 = fmaf(Hs[c * 32 + lane], d[c], a0);
+      if (c + 1 < NQ) a1 = fmaf(Hs[(c + 1) * 32 + lane], d[c + 1], a1);
+    }
+    const float acc = a0 + a1;
+    __syncwarp();                                // every lane has read the stage
+    if (Jp < J1) {
+      if (lane == 0)
+        issue_row(saddr(&mbar[w][st]), saddr(stages + (size_t)st * NQ * 32),
+                  reinterpret_cast<const double*>(p.Hyt32 + Jp * NQ * 32), kRowBytes);
+      ++Jp;
+    }
+    if (owned) {
+      p.out[pt] = rv + acc;
+    } else if (row_live) {
+      p.Y32[(int64_t)rid * ne + e] = acc;
+    }
+  }
+  for (int64_t Jw = J; Jw < Jp; ++Jw) {
+    const int st = (int)((Jw - J0) % kLS);
+    if (lane == 0) wait_phase(saddr(&mbar[w][st]), (uint32_t)(((Jw - J0) / kLS) & 1));
+  }
+  __syncwarp();
+}
+
 // Reconstruction after the last iteration, u = G + H uhat (Algorithm 1
 // returns the local solution for the final trace; Crank-Nicolson then takes
 // u^{n+1} = 2 v - u^n), with H kept tile-major like Hy: for each tile of 32
@@ -412,6 +551,13 @@ __global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 
   __syncwarp();
 }
 
+// FP32 rounding of an FP64 array
+__global__ void k_round_f32(int64_t n, const double* src, float* dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
 // Tile-major copy of the reconstruction operator H ([n][NQFS][nel] ->
 // [tile][n][NQFS][32], zero past the last element).
 __global__ void k_tile_h(int64_t nel, int n, int nq, int64_t ntiles, const double* H, double* Ht) {
@@ -489,6 +635,17 @@ cudaError_t final_launch(const FinalTParams& p, int grid, size_t smem, cudaStrea
   return cudaGetLastError();
 }
 
+// the FP32 sweep runs on the FP64 sweep's grid (same warps, same row ranges)
+template <int F, int NQF>
+cudaError_t lp_launch(const LpTParams& p, int grid, cudaStream_t s) {
+  const size_t smem = sizeof(float) * (size_t)kTW * kLS * F * NQF * 32;
+  auto kern = k_sweep_lp_tiled<F, NQF>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  kern<<<grid, 32 * kTW, smem, s>>>(p);
+  return cudaGetLastError();
+}
+
 template <int F, int NQF>
 cudaError_t tiled_launch(const TiledParams& p, int grid, size_t smem, cudaStream_t s) {
   k_sweep_tiled<F, NQF><<<grid, 32 * kTW, smem, s>>>(p);
@@ -500,12 +657,13 @@ struct TiledOps {
   cudaError_t (*launch)(const TiledParams&, int, size_t, cudaStream_t);
   cudaError_t (*final_config)(int64_t, int64_t, int*, size_t*);
   cudaError_t (*final_launch)(const FinalTParams&, int, size_t, cudaStream_t);
+  cudaError_t (*lp_launch)(const LpTParams&, int, cudaStream_t);
 };
 
 template <int F, int NQF>
 constexpr TiledOps ops_of() {
   return TiledOps{&tiled_config<F, NQF>, &tiled_launch<F, NQF>, &final_config<F, NQF>,
-                  &final_launch<F, NQF>};
+                  &final_launch<F, NQF>, &lp_launch<F, NQF>};
 }
 
 // (faces, points per face) pairs with a kernel instance: quadrilaterals with
@@ -596,7 +754,41 @@ cudaError_t build_tiled_operator(Ctx& c) {
   if ((err = ops.final_config(hrows, ntiles, &c.ftiled_grid, &c.ftiled_smem)) != cudaSuccess)
     return err;
   k_tile_h<<<152 * 8, 256, 0, c.stream>>>(c.nel, c.n, c.NQFS, ntiles, c.H, c.Ht);
-  return cudaGetLastError();
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  if (c.mixed) {
+    // FP32 copy of the tile-major sweep operator for the correction sweeps
+    const int64_t n32 = rows * c.NQFS * 32;
+    if ((err = dalloc_raw(c, (void**)&c.Hyt32, sizeof(float) * (size_t)std::max<int64_t>(n32, 1))) !=
+        cudaSuccess)
+      return err;
+    k_round_f32<<<152 * 8, 256, 0, c.stream>>>(n32, c.Hyt, c.Hyt32);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_lp_sweep_tiled(Ctx& c, const float* in, float* out) {
+  LpTParams p;
+  p.nel = c.nel;
+  p.nface = c.nface;
+  p.ntiles = c.ntiles;
+  p.total_rows = c.tile_rows;
+  p.warp_tile = c.tiled_warp_tile;
+  p.tile_row0 = c.tile_row0;
+  p.tile_nrows = c.tile_nrows;
+  p.rowid = c.rowid;
+  p.nrows = c.nrows;
+  p.nup = c.nup;
+  p.elem_face = c.geo.elem_face;
+  p.Hyt32 = c.Hyt32;
+  p.R = c.R32;
+  p.in = in;
+  p.out = out;
+  p.Y32 = c.Y32;
+  p.err = c.tc_err;
+  TiledOps ops;
+  if (!tiled_ops(c.F, c.Nqf, &ops)) return cudaErrorInvalidValue;
+  return ops.lp_launch(p, c.tiled_grid, c.stream);
 }
 
 cudaError_t launch_final_tiled(Ctx& c) {
