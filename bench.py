@@ -130,10 +130,22 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def kernel_traffic(kernel, source):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's
-    source file is unchanged since it was captured (else None)."""
+def source_sha(sources):
+    """sha256[:16] of the concatenated source files (paths under csrc/)."""
     import hashlib
+    h = hashlib.sha256()
+    for s in sources:
+        with open(os.path.join(ROOT, "paper_1601_06681_gb300", "csrc", s), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+SWEEP_SOURCES = ("sweep_tiled.cu", "tiled_common.cuh", "sweep_common.cuh")
+
+
+def kernel_traffic(kernel, sources):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source files are unchanged since it was captured (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -142,9 +154,7 @@ def kernel_traffic(kernel, source):
     ent = d.get(kernel)
     if not ent:
         return None
-    src = os.path.join(ROOT, "paper_1601_06681_gb300", "csrc", source)
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return ent["bytes_per_launch"] if ent.get("source_sha") == sha else None
+    return ent["bytes_per_launch"] if ent.get("source_sha") == source_sha(sources) else None
 
 
 # ---------------------------------------------------------------------------
@@ -357,7 +367,7 @@ def run_ours(args):
                          "frac": flops_per_launch / (avg_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                                         "(FMA-chain probe measured 1.30 TFLOP/s)",
-                         "traffic": kernel_traffic("k_sweep_tiled", "sweep_tiled.cu"),
+                         "traffic": kernel_traffic("k_sweep_tiled", SWEEP_SOURCES),
                          "alg_bytes_per_launch": alg_bytes,
                          "flops_per_launch": flops_per_launch,
                          "avg_launch_us": avg_ms * 1e3,

@@ -190,6 +190,8 @@ int tangent_grid(int64_t n_tan);
 void fill_face_weights(const Ctx& c, double* fw);   // face Gauss weight of each face point
 // tiled per-element transport sweep (sweep_tiled.cu)
 bool tiled_supported(const Ctx& c);
+cudaError_t tiled_sweep_shape(const Ctx& c, int64_t rows, int64_t ntiles, int* grid,
+                              size_t* smem);             // launch shape of the tiled sweep
 cudaError_t build_tiled_operator(Ctx& c);           // after launch_rows; synchronous
 cudaError_t launch_sweep_tiled(Ctx& c, int graph_mode, int* grid_out);
 cudaError_t launch_final_tiled(Ctx& c);              // u = G + H uhat, per-element H
