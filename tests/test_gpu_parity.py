@@ -71,6 +71,18 @@ def make_case(name):
         mesh, p = W.structured_mesh((10, 13)), 2
         kw = dict(scheme="be", dt=0.03, beta_nodes=np.ascontiguousarray(
             np.broadcast_to(np.array([0.6, -0.9])[None, :, None], (mesh["n_elem"], 2, (p + 1) ** 2))))
+    elif name == "2d_per_element_tangent":
+        # per-node constant velocity with beta.n = 0 on every horizontal face:
+        # the per-element sweep plus the finishing kernel of tangential points
+        mesh, p = W.structured_mesh((11, 9)), 3
+        kw = dict(scheme="be", dt=0.04, beta_nodes=np.ascontiguousarray(
+            np.broadcast_to(np.array([-0.8, 0.0])[None, :, None], (mesh["n_elem"], 2, (p + 1) ** 2))))
+    elif name == "3d_be_variable":
+        # hexahedra with per-node velocity (per-element operators, 3x3 points per face)
+        mesh, p = W.structured_mesh((5, 4, 3)), 1
+        X = node_coords(mesh, p)
+        b = np.stack([0.6 + 0.2 * X[..., 1], -0.5 + 0.3 * X[..., 2], 0.4 + 0.2 * X[..., 0]], -1)
+        kw = dict(scheme="be", dt=0.05, beta_nodes=np.ascontiguousarray(np.transpose(b, (0, 2, 1))))
     elif name == "3d_be_const":
         mesh, p = W.structured_mesh((6, 5, 4)), 2
         kw = dict(scheme="be", dt=0.05, beta_const=np.array([1.0, 1.0, 1.0]) / np.sqrt(3.0))
@@ -102,7 +114,8 @@ def make_solver(E, mesh, p, kw, prob, tol=1e-10, max_iter=400):
 
 
 CASES = ["2d_be_const", "2d_be_zero_component", "2d_cn_variable", "2d_cn_variable_p4",
-         "2d_steady_variable", "2d_graded_mesh", "2d_per_element_const_beta", "3d_be_const", "3d_be_const_p3", "sw_be",
+         "2d_steady_variable", "2d_graded_mesh", "2d_per_element_const_beta",
+         "2d_per_element_tangent", "3d_be_const", "3d_be_const_p3", "3d_be_variable", "sw_be",
          "sw_be_p3"]
 
 
@@ -223,7 +236,8 @@ def test_device_pointer_io_matches_host_io(ehdg):
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("name", ["2d_be_const", "2d_be_zero_component", "2d_cn_variable",
-                                  "2d_cn_variable_p4", "3d_be_const", "sw_be", "2d_graded_mesh"])
+                                  "2d_cn_variable_p4", "3d_be_const", "sw_be", "2d_graded_mesh",
+                                  "2d_per_element_tangent", "3d_be_variable"])
 def test_mixed_precision_reaches_fp64_solution(ehdg, name):
     mesh, p, kw, prob, u0, g = make_case(name)
     n_steps = 3
