@@ -178,7 +178,19 @@ ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
   CK(counted(c, EHDG_KERNEL_STEP, 1, [&] { return launch_step(c); }));
   CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceInitial); }));
   const int n_it = fixed_iters > 0 ? fixed_iters : c.max_iter;
-  for (int k = 0; k < n_it; ++k) {
+  bool persist = fixed_iters <= 0 && persistent_sweep_ok(c);
+  if (persist) {   // every iteration of the step in one cooperative launch
+    if (counted(c, EHDG_KERNEL_ELEM, 1, [&] { return launch_sweep_persistent(c); }) !=
+        cudaSuccess) {
+      // not launchable here (e.g. the grid cannot be co-resident): iterate
+      // with one launch per sweep from now on
+      cudaGetLastError();
+      c.launches[EHDG_KERNEL_ELEM] -= 1;
+      c.persist_fits = false;
+      persist = false;
+    }
+  }
+  for (int k = 0; k < (persist ? 0 : n_it); ++k) {
     if (k > 0 && c.mixed) {
       // low-precision correction of uhat before the next FP64 sweep
       int nl = 0;
@@ -223,6 +235,19 @@ void destroy_graph(Ctx& c) {
   c.graph = nullptr;
 }
 
+// End-of-step kernels of a captured step: reconstruction, forcing copy,
+// bookkeeping.
+ehdg_status capture_step_end(Ctx& c) {
+  cudaError_t err;
+  if ((err = launch_final(c)) != cudaSuccess) return cuda_fail(err, "capture final");
+  if (c.have_force &&
+      (err = cudaMemcpyAsync(c.force_old, c.force, sizeof(double) * c.n * c.nel,
+                             cudaMemcpyDeviceToDevice, c.stream)) != cudaSuccess)
+    return cuda_fail(err, "capture forcing copy");
+  if ((err = launch_step_end(c)) != cudaSuccess) return cuda_fail(err, "capture step end");
+  return EHDG_OK;
+}
+
 // Append one implicit step of context c to the graph being captured on
 // stream s: reset, step RHS, initial trace, then a WHILE node whose body is
 // {element sweep, trace update} (mixed precision: an FP64 sweep before the
@@ -230,7 +255,7 @@ void destroy_graph(Ctx& c) {
 // the condition (continue while r_k >= tol and k < max_iter), so the
 // iteration runs without a host round trip; then the end-of-step kernels.
 // body_stream is a spare stream used to capture the loop body.
-ehdg_status capture_step(Ctx& c, cudaStream_t s, cudaStream_t body_stream) {
+ehdg_status capture_step(Ctx& c, cudaStream_t s, cudaStream_t body_stream, bool allow_persist) {
   cudaStream_t user = c.stream;
   struct Restore {
     Ctx& c;
@@ -242,6 +267,14 @@ ehdg_status capture_step(Ctx& c, cudaStream_t s, cudaStream_t body_stream) {
   if ((err = launch_reset_iter(c)) != cudaSuccess) return cuda_fail(err, "capture reset");
   if ((err = launch_step(c)) != cudaSuccess) return cuda_fail(err, "capture step");
   if ((err = launch_face(c, kFaceInitial)) != cudaSuccess) return cuda_fail(err, "capture face");
+  if (allow_persist && persistent_sweep_ok(c)) {
+    // every iteration in one cooperative launch: no conditional node needed
+    if ((err = launch_sweep_persistent(c)) != cudaSuccess)
+      return cuda_fail(err, "capture persistent sweep");
+    c.graph_persist = true;
+    return capture_step_end(c);
+  }
+  c.graph_persist = false;
   cudaStreamCaptureStatus cst;
   cudaGraph_t g = nullptr;
   cudaGraphConditionalHandle handle;
@@ -288,13 +321,7 @@ ehdg_status capture_step(Ctx& c, cudaStream_t s, cudaStream_t body_stream) {
   c.stream = s;
   if (e2 != cudaSuccess) return cuda_fail(e2, "capture loop body");
   if (e3 != cudaSuccess) return cuda_fail(e3, "end body capture");
-  if ((err = launch_final(c)) != cudaSuccess) return cuda_fail(err, "capture final");
-  if (c.have_force &&
-      (err = cudaMemcpyAsync(c.force_old, c.force, sizeof(double) * c.n * c.nel,
-                             cudaMemcpyDeviceToDevice, c.stream)) != cudaSuccess)
-    return cuda_fail(err, "capture forcing copy");
-  if ((err = launch_step_end(c)) != cudaSuccess) return cuda_fail(err, "capture step end");
-  return EHDG_OK;
+  return capture_step_end(c);
 }
 
 void abort_capture(cudaStream_t s) {
@@ -304,12 +331,12 @@ void abort_capture(cudaStream_t s) {
   cudaGetLastError();
 }
 
-ehdg_status build_graph(Ctx& c) {
+ehdg_status try_build_graph(Ctx& c, bool allow_persist) {
   destroy_graph(c);
   if (!c.cap_stream) CK(cudaStreamCreateWithFlags(&c.cap_stream, cudaStreamNonBlocking));
   if (!c.body_stream) CK(cudaStreamCreateWithFlags(&c.body_stream, cudaStreamNonBlocking));
   CK(cudaStreamBeginCapture(c.cap_stream, cudaStreamCaptureModeRelaxed));
-  const ehdg_status st = capture_step(c, c.cap_stream, c.body_stream);
+  const ehdg_status st = capture_step(c, c.cap_stream, c.body_stream, allow_persist);
   if (st != EHDG_OK) {
     const std::string msg = g_err;
     abort_capture(c.cap_stream);
@@ -322,6 +349,19 @@ ehdg_status build_graph(Ctx& c) {
   CK(cudaGraphInstantiate(&c.gexec, g, 0));
   c.graph_force = c.have_force;
   return EHDG_OK;
+}
+
+// The step graph; a step whose persistent sweep cannot be captured or
+// instantiated falls back to the conditional loop of per-iteration sweeps.
+ehdg_status build_graph(Ctx& c) {
+  const bool want = persistent_sweep_ok(c);
+  ehdg_status st = try_build_graph(c, want);
+  if (st != EHDG_OK && want) {
+    cudaGetLastError();
+    c.persist_fits = false;
+    st = try_build_graph(c, false);
+  }
+  return st;
 }
 
 ehdg_status ensure_step_arrays(Ctx& c, int n) {
@@ -361,7 +401,7 @@ ehdg_status run_graph(Ctx& c, int n_steps, int* iters_per_step, double* res) {
     if (iters_per_step) iters_per_step[s] = c.step_iters_h[s];
     if (first == EHDG_OK && c.step_status_h[s] != EHDG_OK) first = (ehdg_status)c.step_status_h[s];
   }
-  c.launches[EHDG_KERNEL_ELEM] += sweeps;
+  c.launches[EHDG_KERNEL_ELEM] += c.graph_persist ? n_steps : sweeps;
   c.launches[EHDG_KERNEL_FACE] +=
       n_steps + ((c.pde == EHDG_TRANSPORT) ? (c.n_tan > 0 ? sweeps : 0) : sweeps);
   if (c.mixed) {
@@ -1064,7 +1104,7 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
     e = cudaStreamWaitEvent(s, fork, 0);
     if (e == cudaSuccess) e = launch_stamp(s, b->t_start, b->t_acc, i, 0);
     if (e != cudaSuccess) break;
-    const ehdg_status st = capture_step(c, s, b->body);
+    const ehdg_status st = capture_step(c, s, b->body, false);
     if (st != EHDG_OK) {
       const std::string msg = g_err;
       for (int j = 0; j <= i; ++j) {

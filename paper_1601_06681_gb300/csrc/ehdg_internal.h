@@ -56,6 +56,8 @@ struct IterState {
   int status;                    // ehdg_status of the current step
   unsigned int counter;          // last-block ticket of the residual reduction
   int step;                      // steps finished since the last reset (ehdg_run)
+  unsigned int bar;              // grid-barrier arrivals of a persistent sweep
+  int abort;                     // a persistent sweep's bounded wait gave up
   double r_last;
 };
 
@@ -115,6 +117,8 @@ struct Ctx {
   float* Hyt32 = nullptr;        // FP32 copy of Hyt (mixed precision)
   int ftiled_grid = 0;           // launch shape of the tiled reconstruction
   size_t ftiled_smem = 0;
+  bool persist_fits = false;     // the persistent sweep's grid is co-resident
+  double* ppartials = nullptr;   // [2][tiled_grid] its residual partials
   // mixed precision (defect correction)
   bool mixed = false;
   ehdg_precision precision = EHDG_FP64;
@@ -146,6 +150,7 @@ struct Ctx {
   // one implicit step as a CUDA graph: step RHS, initial trace, WHILE{sweep, trace}, end of step
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  bool graph_persist = false;    // the captured step uses the persistent sweep
   bool graph_force = false;      // have_force value the graph was captured with
   cudaStream_t cap_stream = nullptr, body_stream = nullptr;
   int* step_iters = nullptr;     // [step_cap] iterations of each step of ehdg_run
@@ -194,6 +199,9 @@ cudaError_t tiled_sweep_shape(const Ctx& c, int64_t rows, int64_t ntiles, int* g
                               size_t* smem);             // launch shape of the tiled sweep
 cudaError_t build_tiled_operator(Ctx& c);           // after launch_rows; synchronous
 cudaError_t launch_sweep_tiled(Ctx& c, int graph_mode, int* grid_out);
+int tiled_persist_blocks_per_sm(const Ctx& c);      // co-resident blocks of the persistent sweep
+bool persistent_sweep_ok(const Ctx& c);             // whole-step sweep in one launch applies
+cudaError_t launch_sweep_persistent(Ctx& c);        // all iterations of a step, one launch
 cudaError_t launch_final_tiled(Ctx& c);              // u = G + H uhat, per-element H
 cudaError_t launch_lp_sweep_tiled(Ctx& c, const float* in, float* out);   // FP32 correction sweep
 // mixed precision (mixed.cu)

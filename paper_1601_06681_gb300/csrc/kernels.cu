@@ -1059,6 +1059,8 @@ __global__ void k_reset(IterState* it) {
   it->cont = 1;
   it->status = EHDG_OK;
   it->counter = 0u;
+  it->bar = 0u;
+  it->abort = 0;
   it->r_last = 0.0;
 }
 

@@ -57,44 +57,28 @@ struct TiledParams {
   int* err;
 };
 
-// Each warp owns an equal, contiguous range of the operator's rows (so every
-// warp has the same work to within one row, whatever the tile boundaries) and
-// runs on its own: no block barrier before the final residual reduction.
-template <int F, int NQF>
-__global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 1)
-    k_sweep_tiled(const TiledParams p) {
+// One pass of a warp over its rows J0 .. J1-1 (so every warp has the same
+// work to within one row, whatever the tile boundaries). The rows go through
+// the warp's ring of kTS stages: ring sequence number q holds row
+// J0 + (q mod L), L = J1 - J0, in stage q mod kTS, and completes mbarrier phase
+// (q / kTS) & 1 of that stage. This pass consumes q0 .. q0 + L - 1; the
+// producer cursor qp (kTS ahead of the consumer) issues up to qp_end, so a
+// persistent caller keeps streaming the next pass's rows. CG: the trace is
+// read through L2 only (it is rewritten by other SMs during a persistent
+// launch). Returns false if a bounded wait gave up.
+template <int F, int NQF, bool CG>
+__device__ __forceinline__ bool sweep_pass(const TiledParams& p, double* stages, uint32_t mbar0,
+                                           int lane, int64_t gw, int64_t J0, int64_t J1,
+                                           int64_t q0, int64_t& q_done, int64_t& qp,
+                                           int64_t qp_end, const double* src, double* dst,
+                                           double& acc_res) {
   constexpr int NQ = F * NQF;
   constexpr uint32_t kRowBytes = (uint32_t)NQ * 32u * 8u;
-  extern __shared__ __align__(256) unsigned char tsm[];
-  __shared__ __align__(8) uint64_t mbar[kTW][kTS];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double* stages = reinterpret_cast<double*>(tsm) + (size_t)w * kTS * NQ * 32;
-  if (lane == 0) {
-    for (int s = 0; s < kTS; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[w][s])));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncwarp();
-
   const int64_t ne = p.nel, nface = p.nface;
-  const int kk = p.it->k;                        // read before the last block advances it
-  const int64_t tlen = (int64_t)NQF * nface;
-  const double* src = p.uhat + (int64_t)(kk & 1) * tlen;
-  double* dst = p.uhat + (int64_t)((kk + 1) & 1) * tlen;
-
-  const int64_t nwarps = (int64_t)gridDim.x * kTW, gw = (int64_t)blockIdx.x * kTW + w;
-  const int64_t J0 = p.total_rows * gw / nwarps, J1 = p.total_rows * (gw + 1) / nwarps;
-
-  // producer: rows J0 .. J1-1 are contiguous in the operator, kTS ahead
-  int64_t Jp = J0;
-  for (int s = 0; s < kTS && Jp < J1; ++s, ++Jp)
-    if (lane == 0)
-      issue_row(saddr(&mbar[w][s]), saddr(stages + (size_t)s * NQ * 32), p.Hyt + Jp * NQ * 32,
-                kRowBytes);
-
-  double acc_res = 0.0;
-  int64_t t = J0 < J1 ? p.warp_tile[gw] : p.ntiles;
-  int j = J0 < J1 ? (int)(J0 - p.tile_row0[t]) : 0;
+  const int64_t L = J1 - J0;
+  if (L <= 0) return true;
+  int64_t t = p.warp_tile[gw];
+  int j = (int)(J0 - p.tile_row0[t]);
   int nr_t = 0, nr_e = 0, nu_e = 0;
   int64_t e = 0;
   int fid[F];
@@ -117,12 +101,11 @@ __global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 
   // beyond an element's rows exist in both arrays and are never used)
   double gy_n = 0.0;
   int rid_n = 0;
-  if (J0 < J1 && t * 32 + lane < ne) {
+  if (t * 32 + lane < ne) {
     gy_n = p.Gy[(int64_t)j * ne + t * 32 + lane];
     rid_n = p.rowid[(int64_t)j * ne + t * 32 + lane];
   }
-  int64_t J = J0;
-  for (; J < J1; ++J) {
+  for (int64_t i = 0; i < L; ++i) {
     if (fresh) {
       // the element's faces, their Jacobians and uhat^k at its face points
       e = t * 32 + lane;
@@ -136,8 +119,10 @@ __global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 
       for (int f = 0; f < F; ++f) {
         jf[f] = live ? p.face_jf[fid[f]] : 0.0;
 #pragma unroll
-        for (int g = 0; g < NQF; ++g)
-          u[f * NQF + g] = live ? src[(int64_t)g * nface + fid[f]] : 0.0;
+        for (int g = 0; g < NQF; ++g) {
+          const double* a = src + (int64_t)g * nface + fid[f];
+          u[f * NQF + g] = live ? (CG ? __ldcg(a) : *a) : 0.0;
+        }
       }
       fresh = false;
     }
@@ -152,44 +137,46 @@ __global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 
         ++t;
       } while (t < p.ntiles && p.tile_nrows[t] == 0);
       fresh = true;
-      if (J + 1 < J1) load_tile(t);
+      if (i + 1 < L) load_tile(t);
     }
-    if (J + 1 < J1 && t * 32 + lane < ne) {
+    if (i + 1 < L && t * 32 + lane < ne) {
       gy_n = p.Gy[(int64_t)j * ne + t * 32 + lane];
       rid_n = p.rowid[(int64_t)j * ne + t * 32 + lane];
     }
 
-    const int st = (int)((J - J0) % kTS);
-    if (!wait_phase_warp(saddr(&mbar[w][st]), (uint32_t)(((J - J0) / kTS) & 1))) {
+    const int64_t q = q0 + i;
+    const int st = (int)(q % kTS);
+    if (!wait_phase_warp(mbar0 + 8u * st, (uint32_t)((q / kTS) & 1))) {
       if (lane == 0) atomicExch(p.err, 1);
-      break;
+      return false;
     }
+    q_done = q + 1;
     const double* Hs = stages + (size_t)st * NQ * 32;
     double a[kCH];
     a[0] = row_live ? gy : 0.0;
 #pragma unroll
-    for (int q = 1; q < kCH; ++q) a[q] = 0.0;
+    for (int c2 = 1; c2 < kCH; ++c2) a[c2] = 0.0;
 #pragma unroll
     for (int c = 0; c < NQ; ++c) a[c % kCH] = fma(Hs[c * 32 + lane], u[c], a[c % kCH]);
     double acc = a[0];
     if constexpr (kCH == 2) acc = a[0] + a[1];
     if constexpr (kCH == 4) acc = (a[0] + a[1]) + (a[2] + a[3]);
     __syncwarp();                                // every lane has read the stage
-    if (Jp < J1) {
+    if (qp < qp_end) {
       if (lane == 0)
-        issue_row(saddr(&mbar[w][st]), saddr(stages + (size_t)st * NQ * 32),
-                  p.Hyt + Jp * NQ * 32, kRowBytes);
-      ++Jp;
+        issue_row(mbar0 + 8u * (uint32_t)(qp % kTS), saddr(stages + (size_t)(qp % kTS) * NQ * 32),
+                  p.Hyt + (J0 + qp % L) * NQ * 32, kRowBytes);
+      ++qp;
     }
     if (row_live) {
       const int f = rid / NQF, g = rid - f * NQF;
       int face = 0;
       double jfv = 0.0, uk = 0.0;
 #pragma unroll
-      for (int q = 0; q < F; ++q)
-        if (q == f) {
-          face = fid[q];
-          jfv = jf[q];
+      for (int q2 = 0; q2 < F; ++q2)
+        if (q2 == f) {
+          face = fid[q2];
+          jfv = jf[q2];
         }
 #pragma unroll
       for (int c = 0; c < NQ; ++c)
@@ -205,12 +192,61 @@ __global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 
       }
     }
   }
-  // copies still in flight (only after a wait gave up): wait for them, bounded
-  for (int64_t Jw = J; Jw < Jp; ++Jw) {
-    const int st = (int)((Jw - J0) % kTS);
-    if (lane == 0) wait_phase(saddr(&mbar[w][st]), (uint32_t)(((Jw - J0) / kTS) & 1));
+  return true;
+}
+
+// ring set-up shared by both kernels: mbarriers of this warp, the first kTS
+// copies of its sequence
+template <int NQ>
+__device__ __forceinline__ void ring_start(const TiledParams& p, double* stages, uint32_t mbar0,
+                                           int lane, int64_t J0, int64_t J1, int64_t& qp,
+                                           int64_t qp_end) {
+  constexpr uint32_t kRowBytes = (uint32_t)NQ * 32u * 8u;
+  if (lane == 0) {
+    for (int s = 0; s < kTS; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8u * s));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
+  const int64_t L = J1 - J0;
+  qp = 0;
+  for (int s = 0; s < kTS && qp < qp_end; ++s, ++qp)
+    if (lane == 0)
+      issue_row(mbar0 + 8u * s, saddr(stages + (size_t)s * NQ * 32), p.Hyt + (J0 + qp % L) * NQ * 32,
+                kRowBytes);
+}
+
+// copies still in flight after the last pass (speculative prefetch of a pass
+// that did not happen, or after a wait gave up): wait for them, bounded
+__device__ __forceinline__ void ring_drain(uint32_t mbar0, int lane, int64_t q_done, int64_t qp) {
+  for (int64_t q = q_done; q < qp; ++q)
+    if (lane == 0) wait_phase(mbar0 + 8u * (uint32_t)(q % kTS), (uint32_t)((q / kTS) & 1));
+  __syncwarp();
+}
+
+// One eHDG iteration per launch; the last block to finish reduces the
+// residual and sets the loop condition of the step's graph.
+template <int F, int NQF>
+__global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 1)
+    k_sweep_tiled(const TiledParams p) {
+  constexpr int NQ = F * NQF;
+  extern __shared__ __align__(256) unsigned char tsm[];
+  __shared__ __align__(8) uint64_t mbar[kTW][kTS];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* stages = reinterpret_cast<double*>(tsm) + (size_t)w * kTS * NQ * 32;
+  const uint32_t mbar0 = saddr(&mbar[w][0]);
+  const int kk = p.it->k;                        // read before the last block advances it
+  const int64_t tlen = (int64_t)NQF * p.nface;
+  const double* src = p.uhat + (int64_t)(kk & 1) * tlen;
+  double* dst = p.uhat + (int64_t)((kk + 1) & 1) * tlen;
+  const int64_t nwarps = (int64_t)gridDim.x * kTW, gw = (int64_t)blockIdx.x * kTW + w;
+  const int64_t J0 = p.total_rows * gw / nwarps, J1 = p.total_rows * (gw + 1) / nwarps;
+  int64_t qp = 0, q_done = 0;
+  ring_start<NQ>(p, stages, mbar0, lane, J0, J1, qp, J1 - J0);
+  double acc_res = 0.0;
+  sweep_pass<F, NQF, false>(p, stages, mbar0, lane, gw, J0, J1, 0, q_done, qp, J1 - J0, src, dst,
+                            acc_res);
+  ring_drain(mbar0, lane, q_done, qp);
   if (p.final_here) {
     finish_residual(acc_res, p.partials, blockIdx.x, gridDim.x, p.it, p.hist, p.max_iter, p.tol,
                     p.res_scale, p.graph_mode, p.handle, gridDim.x);
@@ -227,6 +263,118 @@ __global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 
   }
 }
 
+// Grid-wide barrier of a cooperative launch: generation target = number of
+// arrivals expected so far. Thread 0 of each block arrives and polls with a
+// bounded number of polls; a block that gives up, or sees another block give
+// up, raises *abort. Returns the block-uniform outcome.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int target, int* abort) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 0;
+    for (uint32_t it = 0; it < kBarrierPolls; ++it) {
+      unsigned int v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) {
+        ok = 1;
+        break;
+      }
+      if (*reinterpret_cast<volatile int*>(abort)) break;
+      __nanosleep(32);
+    }
+    // an abort raised before any block arrived is seen by every block here
+    if (ok && *reinterpret_cast<volatile int*>(abort)) ok = 0;
+    if (!ok) atomicExch(abort, 1);
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// All iterations of one implicit step in one cooperative launch (every block
+// resident): pass k reads uhat^k from slot k & 1 and writes uhat^{k+1} to the
+// other slot; after a grid barrier every block sums the blocks' residual
+// partials in the same order, so every block takes the same decision (the
+// rule of the per-iteration kernel: stop when r_k < tol, when r_k is not
+// finite, or after max_iter iterations). The warps keep streaming their rows
+// across passes, so the first rows of the next pass arrive during the
+// barrier. Block 0 records the history and the final iteration state.
+template <int F, int NQF>
+__global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 1)
+    k_sweep_persist(const TiledParams p) {
+  constexpr int NQ = F * NQF;
+  extern __shared__ __align__(256) unsigned char tsm[];
+  __shared__ __align__(8) uint64_t mbar[kTW][kTS];
+  __shared__ double red[kTW];
+  __shared__ double s_r;
+  __shared__ int s_cont, s_status;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double* stages = reinterpret_cast<double*>(tsm) + (size_t)w * kTS * NQ * 32;
+  const uint32_t mbar0 = saddr(&mbar[w][0]);
+  const int k0 = p.it->k;
+  const int64_t tlen = (int64_t)NQF * p.nface;
+  const int64_t nwarps = (int64_t)gridDim.x * kTW, gw = (int64_t)blockIdx.x * kTW + w;
+  const int64_t J0 = p.total_rows * gw / nwarps, J1 = p.total_rows * (gw + 1) / nwarps;
+  const int64_t L = J1 - J0;
+  const int passes = p.max_iter - k0 > 0 ? p.max_iter - k0 : 1;
+  int64_t qp = 0, q_done = 0;
+  ring_start<NQ>(p, stages, mbar0, lane, J0, J1, qp, L * passes);
+  int k = k0;
+  bool ok = true;
+  for (int pass = 0; pass < passes; ++pass) {
+    const double* src = p.uhat + (int64_t)(k & 1) * tlen;
+    double* dst = p.uhat + (int64_t)((k + 1) & 1) * tlen;
+    double acc_res = 0.0;
+    if (!sweep_pass<F, NQF, true>(p, stages, mbar0, lane, gw, J0, J1, (int64_t)pass * L, q_done,
+                                  qp, L * passes, src, dst, acc_res))
+      atomicExch(&p.it->abort, 1);
+    const double v = fsum_warp(acc_res);
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int i = 0; i < kTW; ++i) s += red[i];
+      p.partials[(int64_t)(pass & 1) * gridDim.x + blockIdx.x] = s;
+    }
+    if (!grid_barrier(&p.it->bar, (unsigned int)(pass + 1) * gridDim.x, &p.it->abort)) {
+      ok = false;
+      break;
+    }
+    // the residual of this pass, summed by warp 0 in a fixed order
+    if (w == 0) {
+      const double* part = p.partials + (int64_t)(pass & 1) * gridDim.x;
+      double s = 0.0;
+      for (int i = lane; i < (int)gridDim.x; i += 32) s += __ldcg(part + i);
+      s = fsum_warp(s);
+      if (lane == 0) {
+        const double r = p.res_scale * sqrt(s);
+        int cont = 1, status = EHDG_OK;
+        if (!isfinite(r)) { cont = 0; status = EHDG_ERR_DIVERGED; }
+        else if (r < p.tol) { cont = 0; status = EHDG_OK; }
+        else if (k + 1 >= p.max_iter) { cont = 0; status = EHDG_ERR_NOT_CONVERGED; }
+        s_r = r;
+        s_cont = cont;
+        s_status = status;
+        if (blockIdx.x == 0 && k < p.max_iter) p.hist[k] = r;
+      }
+    }
+    __syncthreads();
+    ++k;
+    if (!s_cont) break;
+  }
+  ring_drain(mbar0, lane, q_done, qp);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    p.it->k = k;
+    p.it->r_last = ok ? s_r : p.it->r_last;
+    p.it->cont = 0;
+    p.it->status = ok ? s_status : EHDG_ERR_TIMEOUT;
+    __threadfence();
+  }
+}
+
 template <int F, int NQF>
 cudaError_t tiled_config(int64_t total_rows, int64_t ntiles, int* grid, size_t* smem_out) {
   return tiled_shape_of(k_sweep_tiled<F, NQF>, F * NQF, total_rows, ntiles, grid, smem_out);
@@ -238,15 +386,44 @@ cudaError_t tiled_launch(const TiledParams& p, int grid, size_t smem, cudaStream
   return cudaGetLastError();
 }
 
+// blocks of the persistent kernel that fit on one SM (0 on error)
+template <int F, int NQF>
+int persist_blocks_per_sm(size_t smem) {
+  auto kern = k_sweep_persist<F, NQF>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int bpsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kern, 32 * kTW, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return bpsm;
+}
+
+template <int F, int NQF>
+cudaError_t persist_launch(const TiledParams& p, int grid, size_t smem, cudaStream_t s) {
+  void* args[] = {const_cast<TiledParams*>(&p)};
+  return cudaLaunchCooperativeKernel((const void*)k_sweep_persist<F, NQF>, dim3(grid),
+                                     dim3(32 * kTW), args, smem, s);
+}
+
 struct SweepOps {
   cudaError_t (*config)(int64_t, int64_t, int*, size_t*);
   cudaError_t (*launch)(const TiledParams&, int, size_t, cudaStream_t);
+  int (*persist_bpsm)(size_t);
+  cudaError_t (*persist)(const TiledParams&, int, size_t, cudaStream_t);
 };
 
 bool sweep_ops(int F, int Nqf, SweepOps* out) {
 #define EHDG_SWEEP_CASE(f_, q_)                                     \
   if (F == f_ && Nqf == q_) {                                       \
-    *out = SweepOps{&tiled_config<f_, q_>, &tiled_launch<f_, q_>};  \
+    *out = SweepOps{&tiled_config<f_, q_>, &tiled_launch<f_, q_>,   \
+                    &persist_blocks_per_sm<f_, q_>, &persist_launch<f_, q_>}; \
     return true;                                                    \
   }
   EHDG_TILED_SHAPES(EHDG_SWEEP_CASE)
@@ -268,8 +445,7 @@ cudaError_t tiled_sweep_shape(const Ctx& c, int64_t rows, int64_t ntiles, int* g
   return ops.config(rows, ntiles, grid, smem);
 }
 
-cudaError_t launch_sweep_tiled(Ctx& c, int graph_mode, int* grid_out) {
-  TiledParams p;
+static void fill_params(Ctx& c, TiledParams& p, int graph_mode) {
   p.nel = c.nel;
   p.nface = c.nface;
   p.ntiles = c.ntiles;
@@ -298,10 +474,34 @@ cudaError_t launch_sweep_tiled(Ctx& c, int graph_mode, int* grid_out) {
   p.graph_mode = graph_mode;
   p.handle = c.handle;
   p.err = c.tc_err;
+}
+
+cudaError_t launch_sweep_tiled(Ctx& c, int graph_mode, int* grid_out) {
+  TiledParams p;
+  fill_params(c, p, graph_mode);
   SweepOps ops;
   if (!sweep_ops(c.F, c.Nqf, &ops)) return cudaErrorInvalidValue;
   *grid_out = c.tiled_grid;
   return ops.launch(p, c.tiled_grid, c.tiled_smem, c.stream);
+}
+
+int tiled_persist_blocks_per_sm(const Ctx& c) {
+  SweepOps ops;
+  if (!sweep_ops(c.F, c.Nqf, &ops)) return 0;
+  return ops.persist_bpsm(c.tiled_smem);
+}
+
+bool persistent_sweep_ok(const Ctx& c) {
+  return c.Hyt && c.persist_fits && c.ppartials && !c.mixed && c.n_tan == 0;
+}
+
+cudaError_t launch_sweep_persistent(Ctx& c) {
+  TiledParams p;
+  fill_params(c, p, 0);
+  p.partials = c.ppartials;
+  SweepOps ops;
+  if (!sweep_ops(c.F, c.Nqf, &ops)) return cudaErrorInvalidValue;
+  return ops.persist(p, c.tiled_grid, c.tiled_smem, c.stream);
 }
 
 }  // namespace ehdg

@@ -394,6 +394,11 @@ cudaError_t build_tiled_operator(Ctx& c) {
   if ((err = dalloc_raw(c, (void**)&c.tiled_warp_tile, sizeof(int32_t) * (size_t)nwarps)) !=
       cudaSuccess)
     return err;
+  // the persistent form runs on the same grid; it needs every block resident
+  c.persist_fits = (int64_t)tiled_persist_blocks_per_sm(c) * device_sms() >= c.tiled_grid;
+  if ((err = dalloc_raw(c, (void**)&c.ppartials, sizeof(double) * 2 * (size_t)c.tiled_grid)) !=
+      cudaSuccess)
+    return err;
   if ((err = cudaMemcpy(c.tiled_warp_tile, wt.data(), sizeof(int32_t) * (size_t)nwarps,
                         cudaMemcpyHostToDevice)) != cudaSuccess)
     return err;

@@ -33,6 +33,7 @@ constexpr int kTS = EHDG_TILED_TS;
 constexpr int kCH = EHDG_TILED_CH;
 static_assert(kCH == 1 || kCH == 2 || kCH == 4, "FMA chains per row: 1, 2 or 4");
 constexpr uint32_t kTileWaitLimit = 1u << 22; // mbarrier polls before giving up
+constexpr uint32_t kBarrierPolls = 1u << 22;  // grid-barrier polls before giving up
 constexpr int kTiledMaxBlocks = 4096;         // same bound as the other transport sweep
 
 __device__ __forceinline__ uint32_t saddr(const void* p) {

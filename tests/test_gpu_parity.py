@@ -178,20 +178,45 @@ def test_converged_step_equals_direct_hdg_solve(ehdg):
     assert rel(uh, uhd) < 1e-11
 
 
-def test_not_converged_status_keeps_state(ehdg):
-    mesh, p, kw, prob, u0, g = make_case("2d_be_const")
+# "2d_cn_variable" (per-element operator, no beta.n = 0 point) runs every
+# iteration of a step in one persistent launch; "2d_be_const" launches one
+# sweep per iteration
+@pytest.mark.parametrize("name", ["2d_be_const", "2d_cn_variable"])
+def test_not_converged_status_keeps_state(ehdg, name):
+    mesh, p, kw, prob, u0, g = make_case(name)
     with make_solver(ehdg, mesh, p, kw, prob, tol=1e-30, max_iter=3) as s:
         s.set_boundary(g)
         s.set_state(u0)
         it, res, st = s.step(check=False)
         assert st == 4 and it == 3
         u, _ = s.get_state()
-    ou, _, _ = prob.solve_step(u0, None, g_new=g, fixed_iters=3)
+        hist = s.residual_history()
+    ou, _, ohist = prob.solve_step(u0, prob.trace(u0, g), g_new=g, fixed_iters=3)
     assert rel(u, ou) < RTOL
+    assert np.allclose(hist[:3], ohist, rtol=1e-9, atol=0)
 
 
-def test_nan_input_reports_divergence(ehdg):
-    mesh, p, kw, prob, u0, g = make_case("2d_be_const")
+def test_persistent_step_equals_per_iteration_sweeps(ehdg):
+    """A converged step (one launch for all iterations) and the same number
+    of iterations launched one by one give the same state, bit for bit."""
+    mesh, p, kw, prob, u0, g = make_case("2d_cn_variable")
+    with make_solver(ehdg, mesh, p, kw, prob, tol=1e-11, max_iter=400) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        it, _, _ = s.step()
+        ua, uha = s.get_state()
+        s.set_boundary(g)
+        s.set_state(u0)
+        s.step_fixed(it)
+        ub, uhb = s.get_state()
+    assert it > 3
+    assert np.array_equal(ua, ub)
+    assert np.array_equal(uha, uhb)
+
+
+@pytest.mark.parametrize("name", ["2d_be_const", "2d_cn_variable"])
+def test_nan_input_reports_divergence(ehdg, name):
+    mesh, p, kw, prob, u0, g = make_case(name)
     bad = u0.copy()
     bad[3, 0, 1] = np.nan
     with make_solver(ehdg, mesh, p, kw, prob) as s:
