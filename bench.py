@@ -144,7 +144,7 @@ SWEEP_SOURCES = ("sweep_tiled.cu", "tiled_common.cuh", "sweep_common.cuh")
 
 
 def kernel_traffic(kernel, sources):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    """DRAM bytes per sweep from the committed ncu summary, if the kernel's
     source files are unchanged since it was captured (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
@@ -154,7 +154,7 @@ def kernel_traffic(kernel, sources):
     ent = d.get(kernel)
     if not ent:
         return None
-    return ent["bytes_per_launch"] if ent.get("source_sha") == source_sha(sources) else None
+    return ent["bytes_per_sweep"] if ent.get("source_sha") == source_sha(sources) else None
 
 
 # ---------------------------------------------------------------------------
@@ -325,7 +325,9 @@ def run_ours(args):
     e_s = time.perf_counter() - e0
     e2e_value = ws * trace_dof * it_e2e / e_s
 
-    # roofline of the dominant kernel (the element sweep, k_sweep_tiled): per
+    # roofline of the dominant kernel (the element sweep: k_sweep_persist, the
+    # persistent form of k_sweep_tiled that runs a step's iterations in one
+    # launch; figures are per sweep = per iteration): per
     # element and sweep it reads its operator rows (rows x NQFS doubles), Gy
     # and the point id of each row, the trace at its NQFS face points, its 4
     # face ids and face Jacobians and its two row counts, and writes one value
@@ -364,15 +366,15 @@ def run_ours(args):
                     "h2d_bytes_per_step": int(u0_h.nbytes + g_h.nbytes),
                     "d2h_bytes_per_step": int(u_out.nbytes + uh_out.nbytes)},
             "gpu_launches": int(launches),
-            "roofline": {"kernel": "k_sweep_tiled", "bound": "alu",
+            "roofline": {"kernel": "k_sweep_persist", "bound": "alu",
                          "achieved": flops_per_launch / (avg_ms * 1e-3) / 1e12,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": flops_per_launch / (avg_ms * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz "
                                         "(FMA-chain probe measured 1.30 TFLOP/s)",
-                         "traffic": kernel_traffic("k_sweep_tiled", SWEEP_SOURCES),
-                         "alg_bytes_per_launch": alg_bytes,
-                         "flops_per_launch": flops_per_launch,
+                         "traffic": kernel_traffic("k_sweep_persist", SWEEP_SOURCES),
+                         "alg_bytes_per_sweep": alg_bytes,
+                         "flops_per_sweep": flops_per_launch,
                          "avg_sweep_us": avg_ms * 1e3,
                          "sweep_launches": int(n_elem_launch), "sweeps": int(prof_sweeps),
                          "hbm_view": {"achieved_gbs": achieved, "peak_gbs": peak,
