@@ -48,10 +48,13 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--workload", default="transport2d_varbeta",
                     choices=["transport2d_varbeta", "transport3d", "sw2d", "transport2d_small",
-                             "batch"],
+                             "batch", "residual"],
                     help="transport2d_varbeta is the benchmark; the others print a "
                          "time-to-tolerance comparison of FP64 and mixed precision")
     ap.add_argument("--inner-sweeps", type=int, default=8)
+    ap.add_argument("--host-loop", action="store_true",
+                    help="comparison workloads: host-driven steps (one launch per kernel, "
+                         "visible to ncu) instead of graph-launched steps")
     ap.add_argument("--n-inst", type=int, default=256)
     return ap.parse_args()
 
@@ -434,20 +437,25 @@ def compare_workload(args):
         else:
             kw["beta_const"] = wl.beta_const
         s = ehdg.Solver(mesh, wl.p, **kw)
+        if args.host_loop:
+            s.set_profiling(True)       # ehdg_step then drives the loop from the host
         X, XF = s.node_coords(), s.face_point_coords()
         u0 = torch.from_numpy(np.ascontiguousarray(wl.initial(X))).cuda()
         gs = [torch.from_numpy(np.ascontiguousarray(wl.boundary(XF, k * wl.dt))).cuda()
               for k in range(wl.n_steps + 1)]
 
         def one_run():
+            # graph-launched steps (the device-side loop); a transport step
+            # takes that step's inflow data first, so one graph launch per step
             s.set_boundary(gs[0])
             s.set_state(u0)
+            if wl.pde == "sw" and not args.host_loop:
+                return sum(s.run(wl.n_steps))
             its = 0
             for k in range(wl.n_steps):
                 if wl.pde != "sw":
                     s.set_boundary(gs[k + 1])
-                it, _, _ = s.step()
-                its += it
+                its += s.step()[0] if args.host_loop else s.run(1)[0]
             return its
 
         one_run()
@@ -474,6 +482,50 @@ def compare_workload(args):
             "time_steps": wl.n_steps, "tol": wl.tol, "inner_sweeps": args.inner_sweeps}
     print(json.dumps({"metric": "time-to-tol per run, mixed vs FP64", "config": info,
                       "results": results}), flush=True)
+
+
+def residual_workload(args):
+    """The standalone FP64 trace-residual reduction sqrt(sum w (a - b)^2)
+    (the convergence check of Algorithm 1) on 2^24 face points, 402.7 MB
+    read per call, larger than L2: HBM rate against the copy peak."""
+    import torch
+    from paper_1601_06681_gb300 import build, ehdg
+    torch.cuda.set_device(0)
+    build.build()
+    ehdg.load()
+    stream = torch.cuda.current_stream()
+    n = 1 << 24
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1005)
+    a = torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+    b = a + 1e-6 * torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+    w = torch.rand(n, dtype=torch.float64, device="cuda", generator=g)
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    peaks, peak_src = measured_peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    res = {}
+    for name, fn in (("ehdg_trace_residual", ehdg.ehdg_trace_residual),
+                     ("ehdg_trace_residual_noalloc", ehdg.ehdg_trace_residual_noalloc)):
+        for _ in range(max(args.warmup, 3)):
+            fn(a, b, w, out, stream)
+        torch.cuda.synchronize()
+        reps = 50
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn(a, b, w, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = 1e3 * e0.elapsed_time(e1) / reps
+        gbs = 3 * 8 * n / (us * 1e-6) / 1e9
+        ref = float(torch.sqrt(torch.sum(w * (a - b) ** 2)))
+        res[name] = {"us_per_call": us, "achieved_gbs": gbs, "frac_of_peak": gbs / peak,
+                     "rel_err_vs_torch": abs(float(out.item()) - ref) / ref}
+    print(json.dumps({"metric": "FP64 trace residual, HBM rate", "n_points": n,
+                      "bytes_per_call": 3 * 8 * n, "peak_gbs": peak, "peak_source": peak_src,
+                      "l2": "inputs larger than L2 (402.7 MB per call)", "results": res}),
+          flush=True)
 
 
 def batch_workload(args):
@@ -528,6 +580,9 @@ def batch_workload(args):
 
 def main():
     args = parse()
+    if args.workload == "residual":
+        residual_workload(args)
+        return
     if args.workload == "batch":
         batch_workload(args)
         return
