@@ -240,6 +240,17 @@ ehdg_status ehdg_trace_residual(const double* a, const double* b, const double* 
 ehdg_status ehdg_trace_residual_noalloc(const double* a, const double* b, const double* w,
                                         int64_t n, double* out, void* stream);
 
+/* Self-test of the bounded device-side waits (the paper has no
+ * counterpart). which = 0 runs the mbarrier waits of the tiled sweeps, and
+ * which = 1 runs the grid barrier of the persistent sweep. Each runs against a
+ * condition that never holds: an mbarrier that no arrival completes, or a
+ * barrier target one arrival beyond the grid. The poll limit is short, so
+ * the call takes milliseconds. Every wait must give up and report it through a
+ * flag the host reads. The expected result is EHDG_ERR_TIMEOUT; EHDG_OK means a
+ * wait did not give up, which is a defect. The device stays usable afterwards.
+ * stream: a cudaStream_t or NULL; the call synchronises it. */
+ehdg_status ehdg_selftest_wait_timeout(int which, void* stream);
+
 /* Kernel accounting. Every launch is counted per kind; with profiling on,
  * each launch is also bracketed by CUDA events on the context's stream and
  * ehdg_kernel_stats returns the summed device time of the kind (it

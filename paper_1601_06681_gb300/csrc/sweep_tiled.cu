@@ -263,37 +263,6 @@ __global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 
   }
 }
 
-// Grid-wide barrier of a cooperative launch: generation target = number of
-// arrivals expected so far. Thread 0 of each block arrives and polls with a
-// bounded number of polls; a block that gives up, or sees another block give
-// up, raises *abort. Returns the block-uniform outcome.
-__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int target, int* abort) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(bar, 1u);
-    int ok = 0;
-    for (uint32_t it = 0; it < kBarrierPolls; ++it) {
-      unsigned int v;
-      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-      if (v >= target) {
-        ok = 1;
-        break;
-      }
-      if (*reinterpret_cast<volatile int*>(abort)) break;
-      __nanosleep(32);
-    }
-    // an abort raised before any block arrived is seen by every block here
-    if (ok && *reinterpret_cast<volatile int*>(abort)) ok = 0;
-    if (!ok) atomicExch(abort, 1);
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
-
 // All iterations of one implicit step in one cooperative launch (every block
 // resident): pass k reads uhat^k from slot k & 1 and writes uhat^{k+1} to the
 // other slot; after a grid barrier every block sums the blocks' residual

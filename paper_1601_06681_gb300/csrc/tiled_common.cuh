@@ -54,8 +54,9 @@ __device__ __forceinline__ void issue_row(uint32_t mbar, uint32_t dst, const dou
 }
 
 // bounded wait for a phase of an mbarrier; true when it completed
-__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
-  for (uint32_t it = 0; it < kTileWaitLimit; ++it) {
+__device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity,
+                                           uint32_t limit = kTileWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t ok;
     asm volatile(
         "{\n .reg .pred w;\n mbarrier.try_wait.parity.shared::cta.b64 w, [%1], %2;\n"
@@ -70,8 +71,9 @@ __device__ __forceinline__ bool wait_phase(uint32_t mbar, uint32_t parity) {
 
 // bounded wait polled by every lane of a warp (each lane then sees the
 // stage's data); the result is warp-uniform
-__device__ __forceinline__ bool wait_phase_warp(uint32_t mbar, uint32_t parity) {
-  for (uint32_t it = 0; it < kTileWaitLimit; ++it) {
+__device__ __forceinline__ bool wait_phase_warp(uint32_t mbar, uint32_t parity,
+                                                uint32_t limit = kTileWaitLimit) {
+  for (uint32_t it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred w;\n mbarrier.try_wait.parity.shared::cta.b64 w, [%1], %2;\n"
@@ -82,6 +84,38 @@ __device__ __forceinline__ bool wait_phase_warp(uint32_t mbar, uint32_t parity) 
     if (__all_sync(0xffffffffu, done)) return true;
   }
   return false;
+}
+
+// Grid-wide barrier of a cooperative launch: generation target = number of
+// arrivals expected so far. Thread 0 of each block arrives and polls with a
+// bounded number of polls; a block that gives up, or sees another block give
+// up, raises *abort. Returns the block-uniform outcome.
+__device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int target, int* abort,
+                                             uint32_t polls = kBarrierPolls) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    int ok = 0;
+    for (uint32_t it = 0; it < polls; ++it) {
+      unsigned int v;
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) {
+        ok = 1;
+        break;
+      }
+      if (*reinterpret_cast<volatile int*>(abort)) break;
+      __nanosleep(32);
+    }
+    // an abort raised before any block arrived is seen by every block here
+    if (ok && *reinterpret_cast<volatile int*>(abort)) ok = 0;
+    if (!ok) atomicExch(abort, 1);
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
 }
 
 // launch shape of one kernel instance: dynamic shared memory and a one-wave

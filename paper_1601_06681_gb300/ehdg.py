@@ -79,6 +79,7 @@ _SIGS = [
     ("ehdg_autotune_inner_sweeps", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
                                              C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_set_profiling", C.c_int, [C.c_void_p, C.c_int]),
+    ("ehdg_selftest_wait_timeout", C.c_int, [C.c_int, C.c_void_p]),
     ("ehdg_kernel_stats", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64),
                                     C.POINTER(C.c_double)]),
     ("ehdg_batch_create", C.c_int, [C.c_int, C.POINTER(MeshDesc), C.POINTER(ProblemDesc),
@@ -153,6 +154,13 @@ def ehdg_trace_residual(a, b, w, out, stream=None):
     s = None if stream is None else C.c_void_p(stream.cuda_stream)
     _check(load().ehdg_trace_residual(_dev_ptr(a), _dev_ptr(b), _dev_ptr(w), n, _dev_ptr(out), s))
     return out
+
+
+def ehdg_selftest_wait_timeout(which, stream=None):
+    """Run a bounded device-side wait (0: mbarrier, 1: grid barrier) against a
+    condition that never holds; returns the status (EHDG_ERR_TIMEOUT = 6 is
+    the expected one)."""
+    return load().ehdg_selftest_wait_timeout(int(which), _stream_ptr(stream))
 
 
 def ehdg_trace_residual_noalloc(a, b, w, out, stream=None):
