@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--workload", default="transport2d_varbeta",
                     choices=["transport2d_varbeta", "transport3d", "sw2d", "transport2d_small",
-                             "batch", "residual"],
+                             "steady2d", "batch", "residual"],
                     help="transport2d_varbeta is the benchmark; the others print a "
                          "time-to-tolerance comparison of FP64 and mixed precision")
     ap.add_argument("--inner-sweeps", type=int, default=8)
@@ -423,6 +423,10 @@ def compare_workload(args):
         # dt at which Theorem 2 holds on this mesh: h / (dt (p+1)(p+2)) = 3.9, C = 0.34
         wl = W.sw_2d(n=(args.n, args.n), p=3, dt=2.5e-5, n_steps=args.time_steps)
         precisions = ["fp64", "tf32", "bf16", "fp32"]
+    elif args.workload == "steady2d":
+        # the steady solve of Sec. 4.1 (one "step", many iterations)
+        wl = W.steady_2d_smooth(n=(args.n, args.n), p=4)
+        precisions = ["fp64", "fp32"]
     else:
         wl = W.transport_2d_small(n=(args.n, args.n), p=2, n_steps=args.time_steps)
         precisions = ["fp64", "tf32", "fp32"]
@@ -430,10 +434,13 @@ def compare_workload(args):
     results = {}
     ref = None
     for prec in precisions:
-        kw = dict(pde=wl.pde, scheme=wl.scheme, dt=wl.dt, tol=wl.tol, max_iter=400,
+        kw = dict(pde=wl.pde, scheme=wl.scheme, dt=wl.dt, tol=wl.tol,
+                  max_iter=20000 if wl.scheme == "steady" else 400,
                   precision=prec, inner_sweeps=args.inner_sweeps, stream=stream)
         if wl.pde == "sw":
             kw["Phi"] = wl.Phi
+        elif wl.beta_fn is not None:
+            kw["beta_nodes"] = _beta_nodes(ehdg, mesh, wl)
         else:
             kw["beta_const"] = wl.beta_const
         s = ehdg.Solver(mesh, wl.p, **kw)
@@ -443,6 +450,9 @@ def compare_workload(args):
         u0 = torch.from_numpy(np.ascontiguousarray(wl.initial(X))).cuda()
         gs = [torch.from_numpy(np.ascontiguousarray(wl.boundary(XF, k * wl.dt))).cuda()
               for k in range(wl.n_steps + 1)]
+        f_nodes = wl.forcing(X)
+        if f_nodes is not None:
+            s.set_forcing(np.ascontiguousarray(f_nodes))
 
         def one_run():
             # graph-launched steps (the device-side loop); a transport step
@@ -475,6 +485,9 @@ def compare_workload(args):
         results[prec] = {"ms_per_run": ms, "fp64_sweeps_per_run": its,
                          "rel_l2_vs_fp64": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
                          "speedup_vs_fp64": None}
+        if "exact" in wl.meta:
+            ue = wl.meta["exact"](X)[:, None, :]
+            results[prec]["max_nodal_error_vs_exact"] = float(np.max(np.abs(u - ue)))
         s.close()
     for prec in precisions:
         results[prec]["speedup_vs_fp64"] = results["fp64"]["ms_per_run"] / results[prec]["ms_per_run"]

@@ -153,6 +153,7 @@ class Workload:
     Phi: float = 1.0
     u0_fn: object = None          # callable x -> u0 (transport) or (phi, u, v) for sw
     g_fn: object = None           # callable (x, t) -> boundary value (transport)
+    f_fn: object = None           # callable x -> forcing at volume nodes (transport), or None
     noise_amp: float = 0.0
     seed: int = 0
     meta: dict = field(default_factory=dict)
@@ -184,6 +185,12 @@ class Workload:
         """Nodal velocity [n_elem, dim, Np] (variable-beta workloads only)."""
         b = self.beta_fn(x_nodes)  # [n_elem, Np, dim]
         return np.ascontiguousarray(np.transpose(b, (0, 2, 1)))
+
+    def forcing(self, x_nodes):
+        """Forcing at the volume nodes [n_elem, 1, Np], or None."""
+        if self.f_fn is None:
+            return None
+        return self.f_fn(x_nodes)[:, None, :]
 
     def boundary(self, x_face_nodes, t):
         """Boundary data at face nodes x_face_nodes [n_face, Nfp, dim] at time t."""
@@ -239,6 +246,26 @@ def transport_2d_variable(n=(256, 256), p=4, dt=2e-3, n_steps=50, tol=1e-10, see
         p=p, scheme="cn", dt=dt, n_steps=n_steps, tol=tol,
         beta_fn=variable_beta_field(seed), u0_fn=lambda x: gaussian(x, c, s),
         g_fn=lambda x, t: gaussian(x, c, s), noise_amp=1e-3, seed=seed)
+
+
+def steady_2d_smooth(n=(256, 256), p=4, tol=1e-10):
+    """Steady 2D transport with the smooth solution of the paper's first
+    experiment (Sec. 4.1): beta = (y, x) on the unit square, u_e =
+    sin(pi x) cos(pi y) / pi, forcing f = beta . grad u_e, inflow data u_e,
+    zero initial guess. Per-node velocity, so per-element operators."""
+    def ue(x):
+        return np.sin(math.pi * x[..., 0]) * np.cos(math.pi * x[..., 1]) / math.pi
+
+    def fe(x):
+        return (x[..., 1] * np.cos(math.pi * x[..., 0]) * np.cos(math.pi * x[..., 1])
+                - x[..., 0] * np.sin(math.pi * x[..., 0]) * np.sin(math.pi * x[..., 1]))
+
+    return Workload(
+        name=f"steady2d_smooth_{n[0]}x{n[1]}_p{p}", pde="transport", dim=2, n=tuple(n), p=p,
+        scheme="steady", dt=1.0, n_steps=1, tol=tol,
+        beta_fn=lambda x: np.stack([x[..., 1], x[..., 0]], -1),
+        u0_fn=lambda x: np.zeros(x.shape[:-1]), g_fn=lambda x, t: ue(x), f_fn=fe,
+        meta={"exact": ue})
 
 
 def sw_2d(n=(512, 512), p=3, dt=1e-3, n_steps=100, tol=1e-10, seed=1003, n_bumps=16):
