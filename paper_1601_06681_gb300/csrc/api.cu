@@ -651,11 +651,16 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
     for (int a = 0; a < dim; ++a)
       if (mesh->elem_h[e * dim + a] != mesh->elem_h[a]) uniform = false;
   c.shared_op = uniform && !variable;
-  if ((c.precision == EHDG_MIXED_TF32 || c.precision == EHDG_MIXED_BF16) && !c.shared_op) {
+  if (c.precision == EHDG_MIXED_TF32 && !c.shared_op) {
     delete h;
     return fail(EHDG_ERR_UNSUPPORTED,
-                "TF32/BF16 tensor-core sweeps need one local operator shared by all elements "
-                "(constant velocity, uniform mesh); use EHDG_MIXED_FP32");
+                "TF32 tensor-core sweeps need one local operator shared by all elements "
+                "(constant velocity, uniform mesh); use EHDG_MIXED_FP32 or EHDG_MIXED_BF16");
+  }
+  if (c.precision == EHDG_MIXED_BF16 && !c.shared_op && prob->pde != EHDG_TRANSPORT) {
+    delete h;
+    return fail(EHDG_ERR_UNSUPPORTED,
+                "BF16 correction sweeps with per-element operators are built for transport");
   }
 
   build_ref1d(p, q, &c.r1d);
@@ -883,6 +888,11 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
     CKC(counted(c, EHDG_KERNEL_SIGNS, 1, [&] { return launch_face_signs(c); }));
   if (!c.shared_op) CKC(counted(c, EHDG_KERNEL_AUX, 2, [&] { return launch_rows(c); }));
   if (tiled_supported(c)) CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return build_tiled_operator(c); }));
+  if (c.precision == EHDG_MIXED_BF16 && !c.shared_op && !c.Hyt16)
+    return cleanup(fail(EHDG_ERR_UNSUPPORTED,
+                        "BF16 correction sweeps with per-element operators need a face-point "
+                        "count of the tiled sweep (quadrilaterals with 2..10 points per edge, "
+                        "hexahedra with 2x2 or 3x3 per face)"));
   if (c.mixed) CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_hy_to_f32(c); }));
   CKC(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
   CKC(cudaStreamSynchronize(c.stream));

@@ -114,7 +114,8 @@ struct Ctx {
   size_t tiled_smem = 0;
   int32_t* tiled_warp_tile = nullptr;   // [tiled_grid * warps per block] first tile of a warp
   double* Ht = nullptr;          // reconstruction operator H, tile-major: [tile][n][NQFS][32]
-  float* Hyt32 = nullptr;        // FP32 copy of Hyt (mixed precision)
+  float* Hyt32 = nullptr;        // FP32 copy of Hyt (mixed precision, FP32)
+  void* Hyt16 = nullptr;         // BF16 copy of Hyt (mixed precision, BF16)
   int ftiled_grid = 0;           // launch shape of the tiled reconstruction
   size_t ftiled_smem = 0;
   bool persist_fits = false;     // the persistent sweep's grid is co-resident

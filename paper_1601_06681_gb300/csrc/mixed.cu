@@ -233,6 +233,17 @@ cudaError_t launch_hy_to_f32(Ctx& c) {
 // run the element solve on the tensor cores (shared operator), FP32 on the
 // CUDA cores.
 cudaError_t launch_lp_sweep(Ctx& c, const float* in, float* out) {
+  if (c.Hyt32 || c.Hyt16) {
+    cudaError_t err = launch_lp_sweep_tiled(c, in, out);
+    if (err != cudaSuccess) return err;
+    if (c.n_tan > 0) {
+      k_tangent_lp<<<grid1d(c.n_tan, 256, 152 * 4), 256, 0, c.stream>>>(
+          c.n_tan, c.nel, c.nface, c.Nqf, c.tan_g, c.tan_face, c.geo.face_elem,
+          c.geo.face_local, c.Y32, c.R32, out);
+      err = cudaGetLastError();
+    }
+    return err;
+  }
   if (c.precision == EHDG_MIXED_TF32 || c.precision == EHDG_MIXED_BF16) {
     cudaError_t err = launch_lp_sweep_tc(c, in, out);
     if (err != cudaSuccess) return err;
@@ -247,17 +258,6 @@ cudaError_t launch_lp_sweep(Ctx& c, const float* in, float* out) {
       const dim3 g2(grid1d(c.nface, 256, 2432 / c.Nqf), c.Nqf);
       k_face_lp_sw<<<g2, 256, 0, c.stream>>>(c.nel, c.nface, c.Nqf, c.geo.face_elem,
                                              c.geo.face_local, c.Y32, c.R32, out);
-      err = cudaGetLastError();
-    }
-    return err;
-  }
-  if (c.Hyt32) {
-    cudaError_t err = launch_lp_sweep_tiled(c, in, out);
-    if (err != cudaSuccess) return err;
-    if (c.n_tan > 0) {
-      k_tangent_lp<<<grid1d(c.n_tan, 256, 152 * 4), 256, 0, c.stream>>>(
-          c.n_tan, c.nel, c.nface, c.Nqf, c.tan_g, c.tan_face, c.geo.face_elem,
-          c.geo.face_local, c.Y32, c.R32, out);
       err = cudaGetLastError();
     }
     return err;

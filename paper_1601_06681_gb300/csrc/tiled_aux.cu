@@ -3,6 +3,7 @@
 // sweep of the mixed form and the reconstruction u = G + H uhat, both
 // streaming their operator rows like the sweep does (cp.async.bulk into
 // per-warp mbarrier rings with bounded waits).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,12 +27,22 @@ cudaError_t dalloc_raw(Ctx& c, void** p, size_t bytes) {
 }
 
 // Low-precision correction sweep of the mixed form (delta = R + S Hy delta,
-// the correction equation of the FP64 trace fixed point), FP32 on the CUDA
-// cores, with an FP32 copy of the tile-major operator. Same row ranges and
-// warp starts as the FP64 sweep; rows are half as long, so each warp keeps
-// kLS stages in the same shared memory. Owned points: out = R + row value;
+// the correction equation of the FP64 trace fixed point), FP32 arithmetic on
+// the CUDA cores with an FP32 or BF16 copy of the tile-major operator. Same
+// row ranges and warp starts as the FP64 sweep; rows are 2x (FP32) or 4x
+// (BF16) shorter, so each warp keeps that many more stages in the same
+// shared memory. Owned points: out = R + row value;
 // rows of points with beta.n = 0 go to Y32 for the finishing kernel.
-constexpr int kLS = 2 * kTS;
+// stages per warp of the correction sweep: the FP64 sweep's shared memory
+// holds 2x as many FP32 rows and 4x as many BF16 rows
+template <class T>
+__host__ __device__ constexpr int lp_stages() {
+  return kTS * (int)(sizeof(double) / sizeof(T));
+}
+constexpr int kLSMax = 4 * kTS;
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 struct LpTParams {
   int64_t nel, nface, ntiles, total_rows;
@@ -42,7 +53,7 @@ struct LpTParams {
   const uint8_t* nrows;
   const uint8_t* nup;
   const int32_t* elem_face;
-  const float* Hyt32;           // tile-major rows, FP32
+  const void* Hyt_lp;           // tile-major rows, FP32 or BF16
   const float* R;               // [Nqf][nface]
   const float* in;
   float* out;
@@ -50,14 +61,16 @@ struct LpTParams {
   int* err;
 };
 
-template <int F, int NQF>
+template <int F, int NQF, class T>
 __global__ void __launch_bounds__(32 * kTW) k_sweep_lp_tiled(const LpTParams p) {
   constexpr int NQ = F * NQF;
-  constexpr uint32_t kRowBytes = (uint32_t)NQ * 32u * 4u;
+  constexpr int kLS = lp_stages<T>();
+  constexpr uint32_t kRowBytes = (uint32_t)NQ * 32u * (uint32_t)sizeof(T);
   extern __shared__ __align__(256) unsigned char tsm[];
-  __shared__ __align__(8) uint64_t mbar[kTW][kLS];
+  __shared__ __align__(8) uint64_t mbar[kTW][kLSMax];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  float* stages = reinterpret_cast<float*>(tsm) + (size_t)w * kLS * NQ * 32;
+  T* stages = reinterpret_cast<T*>(tsm) + (size_t)w * kLS * NQ * 32;
+  const T* hyt = static_cast<const T*>(p.Hyt_lp);
   if (lane == 0) {
     for (int s = 0; s < kLS; ++s)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[w][s])));
@@ -72,7 +85,7 @@ __global__ void __launch_bounds__(32 * kTW) k_sweep_lp_tiled(const LpTParams p) 
   for (int s = 0; s < kLS && Jp < J1; ++s, ++Jp)
     if (lane == 0)
       issue_row(saddr(&mbar[w][s]), saddr(stages + (size_t)s * NQ * 32),
-                reinterpret_cast<const double*>(p.Hyt32 + Jp * NQ * 32), kRowBytes);
+                reinterpret_cast<const double*>(hyt + Jp * NQ * 32), kRowBytes);
 
   int64_t t = J0 < J1 ? p.warp_tile[gw] : p.ntiles;
   int j = J0 < J1 ? (int)(J0 - p.tile_row0[t]) : 0;
@@ -136,19 +149,19 @@ __global__ void __launch_bounds__(32 * kTW) k_sweep_lp_tiled(const LpTParams p) 
       if (lane == 0) atomicExch(p.err, 1);
       break;
     }
-    const float* Hs = stages + (size_t)st * NQ * 32;
+    const T* Hs = stages + (size_t)st * NQ * 32;
     float a0 = 0.f, a1 = 0.f;
 #pragma unroll
     for (int c = 0; c < NQ; c += 2) {
-      a0 = fmaf(Hs[c * 32 + lane], d[c], a0);
-      if (c + 1 < NQ) a1 = fmaf(Hs[(c + 1) * 32 + lane], d[c + 1], a1);
+      a0 = fmaf(to_f32(Hs[c * 32 + lane]), d[c], a0);
+      if (c + 1 < NQ) a1 = fmaf(to_f32(Hs[(c + 1) * 32 + lane]), d[c + 1], a1);
     }
     const float acc = a0 + a1;
     __syncwarp();                                // every lane has read the stage
     if (Jp < J1) {
       if (lane == 0)
         issue_row(saddr(&mbar[w][st]), saddr(stages + (size_t)st * NQ * 32),
-                  reinterpret_cast<const double*>(p.Hyt32 + Jp * NQ * 32), kRowBytes);
+                  reinterpret_cast<const double*>(hyt + Jp * NQ * 32), kRowBytes);
       ++Jp;
     }
     if (owned) {
@@ -274,6 +287,13 @@ __global__ void k_round_f32(int64_t n, const double* src, float* dst) {
     dst[i] = (float)src[i];
 }
 
+// BF16 rounding (nearest even) of an FP64 array, through FP32
+__global__ void k_round_bf16(int64_t n, const double* src, __nv_bfloat16* dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = __float2bfloat16_rn((float)src[i]);
+}
+
 // Tile-major copy of the reconstruction operator H ([n][NQFS][nel] ->
 // [tile][n][NQFS][32], zero past the last element).
 __global__ void k_tile_h(int64_t nel, int n, int nq, int64_t ntiles, const double* H, double* Ht) {
@@ -320,10 +340,10 @@ cudaError_t final_launch(const FinalTParams& p, int grid, size_t smem, cudaStrea
 }
 
 // the FP32 sweep runs on the FP64 sweep's grid (same warps, same row ranges)
-template <int F, int NQF>
+template <int F, int NQF, class T>
 cudaError_t lp_launch(const LpTParams& p, int grid, cudaStream_t s) {
-  const size_t smem = sizeof(float) * (size_t)kTW * kLS * F * NQF * 32;
-  auto kern = k_sweep_lp_tiled<F, NQF>;
+  const size_t smem = sizeof(T) * (size_t)kTW * lp_stages<T>() * F * NQF * 32;
+  auto kern = k_sweep_lp_tiled<F, NQF, T>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   kern<<<grid, 32 * kTW, smem, s>>>(p);
@@ -334,12 +354,14 @@ struct AuxOps {
   cudaError_t (*final_config)(int64_t, int64_t, int*, size_t*);
   cudaError_t (*final_launch)(const FinalTParams&, int, size_t, cudaStream_t);
   cudaError_t (*lp_launch)(const LpTParams&, int, cudaStream_t);
+  cudaError_t (*lp16_launch)(const LpTParams&, int, cudaStream_t);
 };
 
 bool aux_ops(int F, int Nqf, AuxOps* out) {
 #define EHDG_AUX_CASE(f_, q_)                                                             \
   if (F == f_ && Nqf == q_) {                                                             \
-    *out = AuxOps{&final_config<f_, q_>, &final_launch<f_, q_>, &lp_launch<f_, q_>};      \
+    *out = AuxOps{&final_config<f_, q_>, &final_launch<f_, q_>, &lp_launch<f_, q_, float>,  \
+                  &lp_launch<f_, q_, __nv_bfloat16>};                                     \
     return true;                                                                          \
   }
   EHDG_TILED_SHAPES(EHDG_AUX_CASE)
@@ -416,12 +438,20 @@ cudaError_t build_tiled_operator(Ctx& c) {
   k_tile_h<<<152 * 8, 256, 0, c.stream>>>(c.nel, c.n, c.NQFS, ntiles, c.H, c.Ht);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (c.mixed) {
-    // FP32 copy of the tile-major sweep operator for the correction sweeps
-    const int64_t n32 = rows * c.NQFS * 32;
-    if ((err = dalloc_raw(c, (void**)&c.Hyt32, sizeof(float) * (size_t)std::max<int64_t>(n32, 1))) !=
-        cudaSuccess)
-      return err;
-    k_round_f32<<<152 * 8, 256, 0, c.stream>>>(n32, c.Hyt, c.Hyt32);
+    // low-precision copy of the tile-major sweep operator for the correction
+    // sweeps: BF16 for MIXED_BF16, FP32 otherwise
+    const int64_t nlp = std::max<int64_t>(rows * c.NQFS * 32, 1);
+    if (c.precision == EHDG_MIXED_BF16) {
+      if ((err = dalloc_raw(c, (void**)&c.Hyt16, sizeof(__nv_bfloat16) * (size_t)nlp)) !=
+          cudaSuccess)
+        return err;
+      k_round_bf16<<<152 * 8, 256, 0, c.stream>>>(rows * c.NQFS * 32, c.Hyt,
+                                                  static_cast<__nv_bfloat16*>(c.Hyt16));
+    } else {
+      if ((err = dalloc_raw(c, (void**)&c.Hyt32, sizeof(float) * (size_t)nlp)) != cudaSuccess)
+        return err;
+      k_round_f32<<<152 * 8, 256, 0, c.stream>>>(rows * c.NQFS * 32, c.Hyt, c.Hyt32);
+    }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
   }
   return cudaSuccess;
@@ -440,7 +470,7 @@ cudaError_t launch_lp_sweep_tiled(Ctx& c, const float* in, float* out) {
   p.nrows = c.nrows;
   p.nup = c.nup;
   p.elem_face = c.geo.elem_face;
-  p.Hyt32 = c.Hyt32;
+  p.Hyt_lp = c.Hyt16 ? c.Hyt16 : static_cast<const void*>(c.Hyt32);
   p.R = c.R32;
   p.in = in;
   p.out = out;
@@ -448,7 +478,8 @@ cudaError_t launch_lp_sweep_tiled(Ctx& c, const float* in, float* out) {
   p.err = c.tc_err;
   AuxOps ops;
   if (!aux_ops(c.F, c.Nqf, &ops)) return cudaErrorInvalidValue;
-  return ops.lp_launch(p, c.tiled_grid, c.stream);
+  return c.Hyt16 ? ops.lp16_launch(p, c.tiled_grid, c.stream)
+                 : ops.lp_launch(p, c.tiled_grid, c.stream);
 }
 
 cudaError_t launch_final_tiled(Ctx& c) {

@@ -321,11 +321,33 @@ def test_tensor_core_mixed_reaches_fp64_solution(ehdg, name, precision):
     assert sum(iters) < sum(oiters)
 
 
-def test_tensor_core_precision_needs_shared_operator(ehdg):
+def test_tf32_precision_needs_shared_operator(ehdg):
     mesh, p, kw, prob, u0, g = make_case("2d_cn_variable")
     with pytest.raises(ehdg.EhdgError) as ei:
         ehdg.Solver(mesh, p, precision="tf32", **kw)
     assert ei.value.status == 7
+
+
+# per-element operators: BF16 copy of the tile-major operator, FP32 arithmetic
+@pytest.mark.parametrize("name", ["2d_cn_variable", "2d_cn_variable_p4", "3d_be_variable",
+                                  "2d_per_element_tangent"])
+def test_bf16_per_element_mixed_reaches_fp64_solution(ehdg, name):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    n_steps = 3
+    with ehdg.Solver(mesh, p, tol=1e-12, max_iter=400, precision="bf16", inner_sweeps=6,
+                     **dict(kw)) as s:
+        if g is not None:
+            s.set_boundary(g)
+        s.set_state(u0)
+        iters = s.run(n_steps)
+        u, uh = s.get_state()
+        hist = s.residual_history()
+    ou, ouh, oiters, _ = prob.run(u0, n_steps, g_of_t=(None if g is None else (lambda t: g)),
+                                  tol=1e-13, max_iter=2000)
+    assert hist[-1] < 1e-12
+    assert rel(u, ou) < 1e-10
+    assert rel(uh, ouh) < 1e-10
+    assert sum(iters) < sum(oiters)
 
 
 # ---------------------------------------------------------------------------
