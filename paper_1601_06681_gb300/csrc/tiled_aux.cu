@@ -11,6 +11,7 @@
 
 #include "ehdg_internal.h"
 #include "tiled_common.cuh"
+#include "tiled_passes.cuh"
 
 namespace ehdg {
 
@@ -26,155 +27,25 @@ cudaError_t dalloc_raw(Ctx& c, void** p, size_t bytes) {
   return cudaSuccess;
 }
 
-// Low-precision correction sweep of the mixed form (delta = R + S Hy delta,
-// the correction equation of the FP64 trace fixed point), FP32 arithmetic on
-// the CUDA cores with an FP32 or BF16 copy of the tile-major operator. Same
-// row ranges and warp starts as the FP64 sweep; rows are 2x (FP32) or 4x
-// (BF16) shorter, so each warp keeps that many more stages in the same
-// shared memory. Owned points: out = R + row value;
-// rows of points with beta.n = 0 go to Y32 for the finishing kernel.
-// stages per warp of the correction sweep: the FP64 sweep's shared memory
-// holds 2x as many FP32 rows and 4x as many BF16 rows
-template <class T>
-__host__ __device__ constexpr int lp_stages() {
-  return kTS * (int)(sizeof(double) / sizeof(T));
-}
-constexpr int kLSMax = 4 * kTS;
-
-__device__ __forceinline__ float to_f32(float v) { return v; }
-__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
-
-struct LpTParams {
-  int64_t nel, nface, ntiles, total_rows;
-  const int32_t* warp_tile;
-  const int32_t* tile_row0;
-  const uint8_t* tile_nrows;
-  const uint8_t* rowid;
-  const uint8_t* nrows;
-  const uint8_t* nup;
-  const int32_t* elem_face;
-  const void* Hyt_lp;           // tile-major rows, FP32 or BF16
-  const float* R;               // [Nqf][nface]
-  const float* in;
-  float* out;
-  float* Y32;                   // [NQFS][nel]
-  int* err;
-};
-
+// One correction sweep per launch (mixed form, per-element operators).
 template <int F, int NQF, class T>
 __global__ void __launch_bounds__(32 * kTW) k_sweep_lp_tiled(const LpTParams p) {
   constexpr int NQ = F * NQF;
-  constexpr int kLS = lp_stages<T>();
-  constexpr uint32_t kRowBytes = (uint32_t)NQ * 32u * (uint32_t)sizeof(T);
+  constexpr int S = lp_stages<T>();
   extern __shared__ __align__(256) unsigned char tsm[];
   __shared__ __align__(8) uint64_t mbar[kTW][kLSMax];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  T* stages = reinterpret_cast<T*>(tsm) + (size_t)w * kLS * NQ * 32;
-  const T* hyt = static_cast<const T*>(p.Hyt_lp);
-  if (lane == 0) {
-    for (int s = 0; s < kLS; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(&mbar[w][s])));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncwarp();
-
-  const int64_t ne = p.nel, nface = p.nface;
+  T* stages = reinterpret_cast<T*>(tsm) + (size_t)w * S * NQ * 32;
+  const uint32_t mbar0 = saddr(&mbar[w][0]);
   const int64_t nwarps = (int64_t)gridDim.x * kTW, gw = (int64_t)blockIdx.x * kTW + w;
   const int64_t J0 = p.total_rows * gw / nwarps, J1 = p.total_rows * (gw + 1) / nwarps;
-  int64_t Jp = J0;
-  for (int s = 0; s < kLS && Jp < J1; ++s, ++Jp)
-    if (lane == 0)
-      issue_row(saddr(&mbar[w][s]), saddr(stages + (size_t)s * NQ * 32),
-                reinterpret_cast<const double*>(hyt + Jp * NQ * 32), kRowBytes);
-
-  int64_t t = J0 < J1 ? p.warp_tile[gw] : p.ntiles;
-  int j = J0 < J1 ? (int)(J0 - p.tile_row0[t]) : 0;
-  int nr_t = 0, nr_e = 0, nu_e = 0;
-  int64_t e = 0;
-  int fid[F];
-  float d[NQ];
-  int fid_n[F], nr_e_n = 0, nu_e_n = 0, nr_t_n = 0;
-  auto load_tile = [&](int64_t tt) {
-    const int64_t ee = tt * 32 + lane;
-    const bool live = tt < p.ntiles && ee < ne;
-    nr_t_n = tt < p.ntiles ? p.tile_nrows[tt] : 0;
-#pragma unroll
-    for (int f = 0; f < F; ++f) fid_n[f] = live ? p.elem_face[(int64_t)f * ne + ee] : 0;
-    nr_e_n = live ? p.nrows[ee] : 0;
-    nu_e_n = live ? p.nup[ee] : 0;
-  };
-  load_tile(t);
-  bool fresh = true;
-  int rid_n = (J0 < J1 && t * 32 + lane < ne) ? p.rowid[(int64_t)j * ne + t * 32 + lane] : 0;
-  int64_t J = J0;
-  for (; J < J1; ++J) {
-    if (fresh) {
-      e = t * 32 + lane;
-      const bool live = e < ne;
-      nr_t = nr_t_n;
-      nr_e = nr_e_n;
-      nu_e = nu_e_n;
-#pragma unroll
-      for (int f = 0; f < F; ++f) {
-        fid[f] = fid_n[f];
-#pragma unroll
-        for (int g = 0; g < NQF; ++g)
-          d[f * NQF + g] = live ? p.in[(int64_t)g * nface + fid[f]] : 0.f;
-      }
-      fresh = false;
-    }
-    const bool row_live = j < nr_e;
-    const int rid = rid_n;
-    const bool owned = row_live && j < nu_e;
-    // the owned point and its R value, loaded before the FMA chain
-    const int f0 = rid / NQF, g0 = rid - f0 * NQF;
-    int face = 0;
-#pragma unroll
-    for (int q = 0; q < F; ++q)
-      if (q == f0) face = fid[q];
-    const int64_t pt = (int64_t)g0 * nface + face;
-    const float rv = owned ? p.R[pt] : 0.f;
-    if (++j == nr_t) {
-      j = 0;
-      do {
-        ++t;
-      } while (t < p.ntiles && p.tile_nrows[t] == 0);
-      fresh = true;
-      if (J + 1 < J1) load_tile(t);
-    }
-    if (J + 1 < J1 && t * 32 + lane < ne) rid_n = p.rowid[(int64_t)j * ne + t * 32 + lane];
-
-    const int st = (int)((J - J0) % kLS);
-    if (!wait_phase_warp(saddr(&mbar[w][st]), (uint32_t)(((J - J0) / kLS) & 1))) {
-      if (lane == 0) atomicExch(p.err, 1);
-      break;
-    }
-    const T* Hs = stages + (size_t)st * NQ * 32;
-    float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-    for (int c = 0; c < NQ; c += 2) {
-      a0 = fmaf(to_f32(Hs[c * 32 + lane]), d[c], a0);
-      if (c + 1 < NQ) a1 = fmaf(to_f32(Hs[(c + 1) * 32 + lane]), d[c + 1], a1);
-    }
-    const float acc = a0 + a1;
-    __syncwarp();                                // every lane has read the stage
-    if (Jp < J1) {
-      if (lane == 0)
-        issue_row(saddr(&mbar[w][st]), saddr(stages + (size_t)st * NQ * 32),
-                  reinterpret_cast<const double*>(hyt + Jp * NQ * 32), kRowBytes);
-      ++Jp;
-    }
-    if (owned) {
-      p.out[pt] = rv + acc;
-    } else if (row_live) {
-      p.Y32[(int64_t)rid * ne + e] = acc;
-    }
-  }
-  for (int64_t Jw = J; Jw < Jp; ++Jw) {
-    const int st = (int)((Jw - J0) % kLS);
-    if (lane == 0) wait_phase(saddr(&mbar[w][st]), (uint32_t)(((Jw - J0) / kLS) & 1));
-  }
-  __syncwarp();
+  int64_t qp = 0, q_done = 0;
+  ring_init(mbar0, S, lane);
+  ring_fill(static_cast<const T*>(p.Hyt_lp), stages, mbar0, S, NQ, lane, J0, J1 - J0, 0, qp,
+            J1 - J0);
+  lp_pass<F, NQF, T, false>(p, stages, mbar0, lane, gw, J0, J1, 0, q_done, qp, J1 - J0, p.in,
+                            p.out);
+  ring_drain(mbar0, S, lane, q_done, qp);
 }
 
 // Reconstruction after the last iteration, u = G + H uhat (Algorithm 1

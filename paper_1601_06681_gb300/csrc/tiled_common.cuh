@@ -41,7 +41,7 @@ __device__ __forceinline__ uint32_t saddr(const void* p) {
 }
 
 // lane 0 only: start the copy of one operator row into a stage
-__device__ __forceinline__ void issue_row(uint32_t mbar, uint32_t dst, const double* src,
+__device__ __forceinline__ void issue_row(uint32_t mbar, uint32_t dst, const void* src,
                                           uint32_t bytes) {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes)
