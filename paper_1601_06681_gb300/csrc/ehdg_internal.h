@@ -116,6 +116,10 @@ struct Ctx {
   double* Ht = nullptr;          // reconstruction operator H, tile-major: [tile][n][NQFS][32]
   float* Hyt32 = nullptr;        // FP32 copy of Hyt (mixed precision, FP32)
   void* Hyt16 = nullptr;         // BF16 copy of Hyt (mixed precision, BF16)
+  int32_t* ptid = nullptr;       // [slot][nel] trace index of each row's point (mixed)
+  int lp_grid = 0;               // launch shape of the tiled correction sweep
+  size_t lp_smem = 0;
+  int32_t* lp_warp_tile = nullptr;   // [lp_grid * warps per block] first tile of a warp
   int ftiled_grid = 0;           // launch shape of the tiled reconstruction
   size_t ftiled_smem = 0;
   bool persist_fits = false;     // the persistent sweep's grid is co-resident

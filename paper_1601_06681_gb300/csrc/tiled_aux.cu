@@ -151,18 +151,43 @@ __global__ void __launch_bounds__(32 * kTW, (F * NQF <= 28) ? EHDG_TILED_MINB : 
   __syncwarp();
 }
 
-// FP32 rounding of an FP64 array
-__global__ void k_round_f32(int64_t n, const double* src, float* dst) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = (float)src[i];
+// Trace index g * nface + face of the point each (slot, element) row
+// produces; slots past an element's rows hold 0.
+__global__ void k_row_points(int64_t nel, int NQFS, int Nqf, int64_t nface,
+                             const uint8_t* rowid, const uint8_t* nrows,
+                             const int32_t* elem_face, int32_t* ptid) {
+  const int64_t total = (int64_t)NQFS * nel;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(i / nel);
+    const int64_t e = i - (int64_t)j * nel;
+    int32_t v = 0;
+    if (j < nrows[e]) {
+      const int r = rowid[i];
+      const int f = r / Nqf, g = r - f * Nqf;
+      v = (int32_t)((int64_t)g * nface + elem_face[(int64_t)f * nel + e]);
+    }
+    ptid[i] = v;
+  }
 }
 
-// BF16 rounding (nearest even) of an FP64 array, through FP32
-__global__ void k_round_bf16(int64_t n, const double* src, __nv_bfloat16* dst) {
+// Low-precision copy of the tile-major rows (nq x 32 values each) in the
+// correction sweep's pair-interleaved order: FP32, or BF16 rounded to
+// nearest even through FP32.
+__device__ __forceinline__ void put_lp(float* d, double v) { *d = (float)v; }
+__device__ __forceinline__ void put_lp(__nv_bfloat16* d, double v) {
+  *d = __float2bfloat16_rn((float)v);
+}
+
+template <class T>
+__global__ void k_round_rows(int64_t n, int nq, const double* src, T* dst) {
+  const int64_t row_len = (int64_t)nq * 32;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = __float2bfloat16_rn((float)src[i]);
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / row_len, w = i - r * row_len;
+    const int c = (int)(w >> 5), lane = (int)(w & 31);
+    put_lp(dst + r * row_len + pair_index(c, lane), src[i]);
+  }
 }
 
 // Tile-major copy of the reconstruction operator H ([n][NQFS][nel] ->
@@ -212,26 +237,31 @@ cudaError_t final_launch(const FinalTParams& p, int grid, size_t smem, cudaStrea
 
 // the FP32 sweep runs on the FP64 sweep's grid (same warps, same row ranges)
 template <int F, int NQF, class T>
-cudaError_t lp_launch(const LpTParams& p, int grid, cudaStream_t s) {
-  const size_t smem = sizeof(T) * (size_t)kTW * lp_stages<T>() * F * NQF * 32;
-  auto kern = k_sweep_lp_tiled<F, NQF, T>;
-  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  kern<<<grid, 32 * kTW, smem, s>>>(p);
+cudaError_t lp_config(int64_t total_rows, int64_t ntiles, int* grid, size_t* smem_out) {
+  return tiled_shape_of(k_sweep_lp_tiled<F, NQF, T>, F * NQF, total_rows, ntiles, grid, smem_out,
+                        sizeof(T) * lp_stages<T>());
+}
+
+template <int F, int NQF, class T>
+cudaError_t lp_launch(const LpTParams& p, int grid, size_t smem, cudaStream_t s) {
+  k_sweep_lp_tiled<F, NQF, T><<<grid, 32 * kTW, smem, s>>>(p);
   return cudaGetLastError();
 }
 
 struct AuxOps {
   cudaError_t (*final_config)(int64_t, int64_t, int*, size_t*);
   cudaError_t (*final_launch)(const FinalTParams&, int, size_t, cudaStream_t);
-  cudaError_t (*lp_launch)(const LpTParams&, int, cudaStream_t);
-  cudaError_t (*lp16_launch)(const LpTParams&, int, cudaStream_t);
+  cudaError_t (*lp_config)(int64_t, int64_t, int*, size_t*);
+  cudaError_t (*lp_launch)(const LpTParams&, int, size_t, cudaStream_t);
+  cudaError_t (*lp16_config)(int64_t, int64_t, int*, size_t*);
+  cudaError_t (*lp16_launch)(const LpTParams&, int, size_t, cudaStream_t);
 };
 
 bool aux_ops(int F, int Nqf, AuxOps* out) {
 #define EHDG_AUX_CASE(f_, q_)                                                             \
   if (F == f_ && Nqf == q_) {                                                             \
-    *out = AuxOps{&final_config<f_, q_>, &final_launch<f_, q_>, &lp_launch<f_, q_, float>,  \
+    *out = AuxOps{&final_config<f_, q_>, &final_launch<f_, q_>, &lp_config<f_, q_, float>,  \
+                  &lp_launch<f_, q_, float>, &lp_config<f_, q_, __nv_bfloat16>,            \
                   &lp_launch<f_, q_, __nv_bfloat16>};                                     \
     return true;                                                                          \
   }
@@ -309,6 +339,14 @@ cudaError_t build_tiled_operator(Ctx& c) {
   k_tile_h<<<152 * 8, 256, 0, c.stream>>>(c.nel, c.n, c.NQFS, ntiles, c.H, c.Ht);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   if (c.mixed) {
+    // the trace index of every row's point (the correction sweeps prefetch it)
+    if ((int64_t)c.Nqf * c.nface > INT32_MAX) return cudaErrorInvalidValue;
+    if ((err = dalloc_raw(c, (void**)&c.ptid, sizeof(int32_t) * (size_t)c.NQFS * c.nel)) !=
+        cudaSuccess)
+      return err;
+    k_row_points<<<152 * 8, 256, 0, c.stream>>>(c.nel, c.NQFS, c.Nqf, c.nface, c.rowid, c.nrows,
+                                                c.geo.elem_face, c.ptid);
+    if ((err = cudaGetLastError()) != cudaSuccess) return err;
     // low-precision copy of the tile-major sweep operator for the correction
     // sweeps: BF16 for MIXED_BF16, FP32 otherwise
     const int64_t nlp = std::max<int64_t>(rows * c.NQFS * 32, 1);
@@ -316,14 +354,34 @@ cudaError_t build_tiled_operator(Ctx& c) {
       if ((err = dalloc_raw(c, (void**)&c.Hyt16, sizeof(__nv_bfloat16) * (size_t)nlp)) !=
           cudaSuccess)
         return err;
-      k_round_bf16<<<152 * 8, 256, 0, c.stream>>>(rows * c.NQFS * 32, c.Hyt,
+      k_round_rows<<<152 * 8, 256, 0, c.stream>>>(rows * c.NQFS * 32, c.NQFS, c.Hyt,
                                                   static_cast<__nv_bfloat16*>(c.Hyt16));
     } else {
       if ((err = dalloc_raw(c, (void**)&c.Hyt32, sizeof(float) * (size_t)nlp)) != cudaSuccess)
         return err;
-      k_round_f32<<<152 * 8, 256, 0, c.stream>>>(rows * c.NQFS * 32, c.Hyt, c.Hyt32);
+      k_round_rows<<<152 * 8, 256, 0, c.stream>>>(rows * c.NQFS * 32, c.NQFS, c.Hyt, c.Hyt32);
     }
     if ((err = cudaGetLastError()) != cudaSuccess) return err;
+    // the correction sweep's own launch shape (its shared memory allows more
+    // warps than the FP64 sweep's) and the tile of each of its warps' first row
+    AuxOps ops2;
+    if (!aux_ops(c.F, c.Nqf, &ops2)) return cudaErrorInvalidValue;
+    if ((err = (c.Hyt16 ? ops2.lp16_config : ops2.lp_config)(rows, ntiles, &c.lp_grid,
+                                                             &c.lp_smem)) != cudaSuccess)
+      return err;
+    const int64_t lwarps = (int64_t)c.lp_grid * kTW;
+    std::vector<int32_t> lt((size_t)lwarps, 0);
+    for (int64_t gw = 0, tt = 0; gw < lwarps; ++gw) {
+      const int64_t J0 = rows * gw / lwarps;
+      while (tt + 1 < ntiles && row0[tt + 1] <= J0) ++tt;
+      lt[gw] = (int32_t)tt;
+    }
+    if ((err = dalloc_raw(c, (void**)&c.lp_warp_tile, sizeof(int32_t) * (size_t)lwarps)) !=
+        cudaSuccess)
+      return err;
+    if ((err = cudaMemcpy(c.lp_warp_tile, lt.data(), sizeof(int32_t) * (size_t)lwarps,
+                          cudaMemcpyHostToDevice)) != cudaSuccess)
+      return err;
   }
   return cudaSuccess;
 }
@@ -334,13 +392,14 @@ cudaError_t launch_lp_sweep_tiled(Ctx& c, const float* in, float* out) {
   p.nface = c.nface;
   p.ntiles = c.ntiles;
   p.total_rows = c.tile_rows;
-  p.warp_tile = c.tiled_warp_tile;
+  p.warp_tile = c.lp_warp_tile;
   p.tile_row0 = c.tile_row0;
   p.tile_nrows = c.tile_nrows;
   p.rowid = c.rowid;
   p.nrows = c.nrows;
   p.nup = c.nup;
   p.elem_face = c.geo.elem_face;
+  p.ptid = c.ptid;
   p.Hyt_lp = c.Hyt16 ? c.Hyt16 : static_cast<const void*>(c.Hyt32);
   p.R = c.R32;
   p.in = in;
@@ -349,8 +408,8 @@ cudaError_t launch_lp_sweep_tiled(Ctx& c, const float* in, float* out) {
   p.err = c.tc_err;
   AuxOps ops;
   if (!aux_ops(c.F, c.Nqf, &ops)) return cudaErrorInvalidValue;
-  return c.Hyt16 ? ops.lp16_launch(p, c.tiled_grid, c.stream)
-                 : ops.lp_launch(p, c.tiled_grid, c.stream);
+  return c.Hyt16 ? ops.lp16_launch(p, c.lp_grid, c.lp_smem, c.stream)
+                 : ops.lp_launch(p, c.lp_grid, c.lp_smem, c.stream);
 }
 
 cudaError_t launch_final_tiled(Ctx& c) {

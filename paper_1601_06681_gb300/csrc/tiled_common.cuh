@@ -122,8 +122,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned int* bar, unsigned int tar
 // grid with at least four rows per warp
 template <class K>
 cudaError_t tiled_shape_of(K kern, int NQ, int64_t total_rows, int64_t ntiles, int* grid,
-                           size_t* smem_out) {
-  const size_t smem = sizeof(double) * (size_t)kTW * kTS * NQ * 32;
+                           size_t* smem_out, size_t stage_bytes_per_value = sizeof(double) * kTS) {
+  const size_t smem = stage_bytes_per_value * (size_t)kTW * NQ * 32;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);

@@ -221,16 +221,28 @@ __device__ __forceinline__ bool sweep_pass(const TiledParams& p, double* stages,
 // (BF16) shorter, so each warp keeps that many more stages in the same
 // shared memory. Owned points: out = R + row value;
 // rows of points with beta.n = 0 go to Y32 for the finishing kernel.
-// stages per warp of the correction sweep: the FP64 sweep's shared memory
-// holds 2x as many FP32 rows and 4x as many BF16 rows
+// stages per warp of the correction sweep (rows of FP32 or BF16)
 template <class T>
 __host__ __device__ constexpr int lp_stages() {
-  return kTS * (int)(sizeof(double) / sizeof(T));
+  return 4;
 }
-constexpr int kLSMax = 4 * kTS;
+constexpr int kLSMax = 4;
 
 __device__ __forceinline__ float to_f32(float v) { return v; }
 __device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// two adjacent values of a pair-interleaved row as FP32
+__device__ __forceinline__ float2 load_pair(const float* p) {
+  return *reinterpret_cast<const float2*>(p);
+}
+__device__ __forceinline__ float2 load_pair(const __nv_bfloat16* p) {
+  return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+}
+
+// index of (column c, lane) in a pair-interleaved row of nq x 32 values
+__host__ __device__ __forceinline__ int64_t pair_index(int c, int lane) {
+  return ((int64_t)(c >> 1) * 32 + lane) * 2 + (c & 1);
+}
 
 struct LpTParams {
   int64_t nel, nface, ntiles, total_rows;
@@ -241,6 +253,7 @@ struct LpTParams {
   const uint8_t* nrows;
   const uint8_t* nup;
   const int32_t* elem_face;
+  const int32_t* ptid;          // [slot][nel] trace index g * nface + face of each row's point
   const void* Hyt_lp;           // tile-major rows, FP32 or BF16
   const float* R;               // [Nqf][nface]
   const float* in;
@@ -249,9 +262,29 @@ struct LpTParams {
   int* err;
 };
 
+// Position of a warp in its row sequence: tile t, slot j, rows of the tile.
+struct RowPos {
+  int64_t t;
+  int j, nr;
+};
+
+template <class P>
+__device__ __forceinline__ void rowpos_next(const P& p, RowPos& r) {
+  if (++r.j == r.nr) {
+    r.j = 0;
+    do {
+      ++r.t;
+    } while (r.t < p.ntiles && p.tile_nrows[r.t] == 0);
+    r.nr = r.t < p.ntiles ? p.tile_nrows[r.t] : 0;
+  }
+}
+
 // One correction pass of a warp over its rows (FP32 arithmetic): owned
 // points get out = R + row value, rows of points with beta.n = 0 go to Y32.
-// CG: the input trace is read through L2 only (persistent launches).
+// The correction has a short FMA chain, so the pass is bound by the latency
+// of its dependent loads. Each row's trace index is loaded two rows ahead and
+// its R value one row ahead. CG: the input trace is read through L2 only
+// (persistent launches).
 template <int F, int NQF, class T, bool CG>
 __device__ __forceinline__ bool lp_pass(const LpTParams& p, T* stages, uint32_t mbar0, int lane,
                                         int64_t gw, int64_t J0, int64_t J1, int64_t q0,
@@ -263,63 +296,70 @@ __device__ __forceinline__ bool lp_pass(const LpTParams& p, T* stages, uint32_t 
   const int64_t ne = p.nel, nface = p.nface;
   const int64_t L = J1 - J0;
   if (L <= 0) return true;
-  int64_t t = p.warp_tile[gw];
-  int j = (int)(J0 - p.tile_row0[t]);
-  int nr_t = 0, nr_e = 0, nu_e = 0;
-  int64_t e = 0;
-  int fid[F];
-  float d[NQ];
-  int fid_n[F], nr_e_n = 0, nu_e_n = 0, nr_t_n = 0;
-  auto load_tile = [&](int64_t tt) {
-    const int64_t ee = tt * 32 + lane;
-    const bool live = tt < p.ntiles && ee < ne;
-    nr_t_n = tt < p.ntiles ? p.tile_nrows[tt] : 0;
-#pragma unroll
-    for (int f = 0; f < F; ++f) fid_n[f] = live ? p.elem_face[(int64_t)f * ne + ee] : 0;
-    nr_e_n = live ? p.nrows[ee] : 0;
-    nu_e_n = live ? p.nup[ee] : 0;
+  auto ptid_at = [&](const RowPos& r) -> int {
+    const int64_t ee = r.t * 32 + lane;
+    return (r.t < p.ntiles && ee < ne) ? p.ptid[(int64_t)r.j * ne + ee] : 0;
   };
-  load_tile(t);
-  bool fresh = true;
-  int rid_n = (t * 32 + lane < ne) ? p.rowid[(int64_t)j * ne + t * 32 + lane] : 0;
+  RowPos cur;
+  cur.t = p.warp_tile[gw];
+  cur.j = (int)(J0 - p.tile_row0[cur.t]);
+  cur.nr = p.tile_nrows[cur.t];
+  RowPos ahead1 = cur, ahead2 = cur;
+  rowpos_next(p, ahead1);
+  ahead2 = ahead1;
+  rowpos_next(p, ahead2);
+  int pt_cur = ptid_at(cur);
+  int pt_nxt = L > 1 ? ptid_at(ahead1) : 0;
+  float rv_cur = CG ? __ldcg(p.R + pt_cur) : p.R[pt_cur];
+  int nr_e = 0, nu_e = 0;
+  int64_t e = 0, t_gathered = -1;
+  float d[NQ];
+  // face ids of the tile the next row enters, loaded a row early
+  int fid_n[F];
+  int64_t fid_tile = -1;
+  int rid_n = (cur.t * 32 + lane < ne) ? p.rowid[(int64_t)cur.j * ne + cur.t * 32 + lane] : 0;
   for (int64_t i = 0; i < L; ++i) {
-    if (fresh) {
-      e = t * 32 + lane;
+    if (cur.t != t_gathered) {
+      // the tile's correction values at each element's face points
+      e = cur.t * 32 + lane;
       const bool live = e < ne;
-      nr_t = nr_t_n;
-      nr_e = nr_e_n;
-      nu_e = nu_e_n;
+      nr_e = live ? p.nrows[e] : 0;
+      nu_e = live ? p.nup[e] : 0;
+      const bool have = fid_tile == cur.t;
 #pragma unroll
       for (int f = 0; f < F; ++f) {
-        fid[f] = fid_n[f];
+        const int fid = have ? fid_n[f] : (live ? p.elem_face[(int64_t)f * ne + e] : 0);
 #pragma unroll
         for (int g = 0; g < NQF; ++g) {
-          const float* a = in + (int64_t)g * nface + fid[f];
+          const float* a = in + (int64_t)g * nface + fid;
           d[f * NQF + g] = live ? (CG ? __ldcg(a) : *a) : 0.f;
         }
       }
-      fresh = false;
+      t_gathered = cur.t;
     }
+    const int j = cur.j;
     const bool row_live = j < nr_e;
-    const int rid = rid_n;
     const bool owned = row_live && j < nu_e;
-    // the owned point and its R value, loaded before the FMA chain
-    const int f0 = rid / NQF, g0 = rid - f0 * NQF;
-    int face = 0;
+    const int pt = pt_cur;
+    const float rv = rv_cur;
+    const int rid = rid_n;
+    // prefetch: R of the next row, the trace index of the row after it
+    float rv_nxt = 0.f;
+    if (i + 1 < L) rv_nxt = CG ? __ldcg(p.R + pt_nxt) : p.R[pt_nxt];
+    int pt_nn = 0;
+    if (i + 2 < L) pt_nn = ptid_at(ahead2);
+    // the next row's position and point id
+    cur = ahead1;
+    ahead1 = ahead2;
+    if (i + 2 < L) rowpos_next(p, ahead2);
+    if (i + 1 < L && cur.t * 32 + lane < ne) rid_n = p.rowid[(int64_t)cur.j * ne + cur.t * 32 + lane];
+    if (i + 1 < L && cur.t != t_gathered && fid_tile != cur.t) {
+      const int64_t ee = cur.t * 32 + lane;
 #pragma unroll
-    for (int q2 = 0; q2 < F; ++q2)
-      if (q2 == f0) face = fid[q2];
-    const int64_t pt = (int64_t)g0 * nface + face;
-    const float rv = owned ? (CG ? __ldcg(p.R + pt) : p.R[pt]) : 0.f;
-    if (++j == nr_t) {
-      j = 0;
-      do {
-        ++t;
-      } while (t < p.ntiles && p.tile_nrows[t] == 0);
-      fresh = true;
-      if (i + 1 < L) load_tile(t);
+      for (int f = 0; f < F; ++f)
+        fid_n[f] = (cur.t < p.ntiles && ee < ne) ? p.elem_face[(int64_t)f * ne + ee] : 0;
+      fid_tile = cur.t;
     }
-    if (i + 1 < L && t * 32 + lane < ne) rid_n = p.rowid[(int64_t)j * ne + t * 32 + lane];
 
     const int64_t q = q0 + i;
     const int st = (int)(q % S);
@@ -328,12 +368,14 @@ __device__ __forceinline__ bool lp_pass(const LpTParams& p, T* stages, uint32_t 
       return false;
     }
     q_done = q + 1;
+    // the copy is pair-interleaved: columns 2h and 2h+1 of a lane are adjacent
     const T* Hs = stages + (size_t)st * NQ * 32;
     float a0 = 0.f, a1 = 0.f;
 #pragma unroll
     for (int c = 0; c < NQ; c += 2) {
-      a0 = fmaf(to_f32(Hs[c * 32 + lane]), d[c], a0);
-      if (c + 1 < NQ) a1 = fmaf(to_f32(Hs[(c + 1) * 32 + lane]), d[c + 1], a1);
+      const float2 h = load_pair(Hs + ((c >> 1) * 32 + lane) * 2);
+      a0 = fmaf(h.x, d[c], a0);
+      a1 = fmaf(h.y, d[c + 1], a1);
     }
     const float acc = a0 + a1;
     __syncwarp();                                // every lane has read the stage
@@ -343,6 +385,9 @@ __device__ __forceinline__ bool lp_pass(const LpTParams& p, T* stages, uint32_t 
     } else if (row_live) {
       p.Y32[(int64_t)rid * ne + e] = acc;
     }
+    pt_cur = pt_nxt;
+    rv_cur = rv_nxt;
+    pt_nxt = pt_nn;
   }
   return true;
 }
