@@ -143,7 +143,7 @@ def source_sha(sources):
     return h.hexdigest()[:16]
 
 
-SWEEP_SOURCES = ("sweep_tiled.cu", "tiled_passes.cuh", "tiled_common.cuh", "sweep_common.cuh")
+SWEEP_SOURCES = ("sweep_tiled.cu", "sweep_pass.cuh", "tiled_common.cuh", "sweep_common.cuh")
 
 
 def kernel_traffic(kernel, sources):

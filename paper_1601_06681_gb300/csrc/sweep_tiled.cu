@@ -25,7 +25,7 @@
 #include "ehdg_internal.h"
 #include "sweep_common.cuh"
 #include "tiled_common.cuh"
-#include "tiled_passes.cuh"
+#include "sweep_pass.cuh"
 
 namespace ehdg {
 

@@ -11,7 +11,8 @@
 
 #include "ehdg_internal.h"
 #include "tiled_common.cuh"
-#include "tiled_passes.cuh"
+#include "lp_pass.cuh"
+#include "sweep_pass.cuh"
 
 namespace ehdg {
 
