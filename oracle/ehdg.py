@@ -48,12 +48,18 @@ class Problem:
     (elements, faces, face_elem/face_local/elem_face, face_tag)."""
 
     def __init__(self, mesh, p, pde="transport", scheme="be", dt=1.0, Phi=1.0,
-                 beta_const=None, beta_nodes=None):
+                 beta_const=None, beta_nodes=None, coriolis=(0.0, 0.0, 0.0), friction=0.0):
         self.mesh = mesh
         self.p, self.pde, self.scheme, self.dt, self.Phi = p, pde, scheme, float(dt), float(Phi)
         self.dim = dim = mesh["dim"]
         self.nel, self.nface = mesh["n_elem"], mesh["n_face"]
         variable = beta_nodes is not None
+        # shallow water: Coriolis f = f0 + beta (y - y_m) and bottom friction
+        # gamma (eq. linearizedShallow); a beta-plane makes every element's
+        # operator different
+        self.coriolis = tuple(float(v) for v in coriolis)
+        self.friction = float(friction)
+        sw_varying = pde == "sw" and self.coriolis[1] != 0.0
         self.ref = ref = local_ops.make_ref(dim, p, variable)
         self.Np, self.Nfp = ref.Np, ref.Nfp
         self.nf = 3 if pde == "sw" else 1
@@ -69,7 +75,7 @@ class Problem:
                 self.beta_nodes = np.broadcast_to(bc[None, :, None], (self.nel, dim, self.Np))
         else:
             self.beta_nodes = None
-        if (not variable) and uniform:
+        if (not variable) and (not sw_varying) and uniform:
             ops = self._element_ops(0)
             self.M, self.Asp, self.B = (np.broadcast_to(o, (self.nel,) + o.shape) for o in ops)
         else:
@@ -89,7 +95,8 @@ class Problem:
         h = self.mesh["elem_h"][e]
         if self.pde == "transport":
             return local_ops.transport_element(self.ref, h, self.beta_nodes[e])
-        return local_ops.sw_element(self.ref, h, self.Phi)
+        return local_ops.sw_element(self.ref, h, self.Phi, lo=self.mesh["elem_lo"][e],
+                                    coriolis=self.coriolis, friction=self.friction)
 
     # -- the trace formula ---------------------------------------------------
     def face_values(self, u, e, side):

@@ -64,6 +64,9 @@ class RefElement:
             mats = [D if a == ax else L for a in range(dim)]
             self.dphi.append(_tensor(mats))                # reference d/dr_ax
         self.W = _tensor([self.om[:, None]] * dim)[:, 0]   # [Q]
+        # reference coordinates of the volume points (axis 0 fastest, as in _tensor)
+        idx = np.indices((q,) * dim).reshape(dim, -1)[::-1]
+        self.X = np.stack([self.xi[idx[a]] for a in range(dim)], -1)   # [Q, dim]
         # face tables, local face f = 2*ax + side
         self.fphi, self.fpsi, self.fW = [], [], []
         for f in range(2 * dim):
@@ -118,17 +121,25 @@ def transport_element(ref, h, beta_nodes):
     return M, Asp, B
 
 
-def sw_element(ref, h, Phi):
+def sw_element(ref, h, Phi, lo=None, coriolis=(0.0, 0.0, 0.0), friction=0.0):
     """(Mblk, A_sp, B) for one 2D linearised shallow-water element.
 
     Unknown order (phi, u, v), each Np nodal values; B maps the scalar trace
-    phihat (ordered by local face, face point) to the three right-hand sides."""
+    phihat (ordered by local face, face point) to the three right-hand sides.
+    Source terms of eq. linearizedShallow, moved to the left-hand side of the
+    local equations (Sec. 3, eq. localSolverDD): bottom friction gamma adds
+    (gamma Phi u, w) to the u-row and (gamma Phi v, w) to the v-row; the
+    Coriolis parameter f = f0 + beta (y - y_m) adds -(f Phi v, w) to the
+    u-row and +(f Phi u, w) to the v-row, with f at the volume quadrature
+    points of the element whose lower corner is lo. coriolis = (f0, beta, y_m)."""
     assert ref.dim == 2
     Np = ref.Np
     J, Jf = _geometry(h)
     h = np.asarray(h, dtype=np.float64)
     W = ref.W * J
     M = ref.phi.T @ (W[:, None] * ref.phi)
+    f0, beta_c, y_m = (float(v) for v in coriolis)
+    gamma = float(friction)
     sq = np.sqrt(Phi)
     # G_ax[i, j] = (phi_j, d phi_i / dx_ax)_K
     G = [(2.0 / h[ax]) * (ref.dphi[ax].T @ (W[:, None] * ref.phi)) for ax in range(2)]
@@ -155,6 +166,16 @@ def sw_element(ref, h, Phi):
         B[0:Np, cols] = sq * Bf
         B[Np:2 * Np, cols] = -Phi * nrm[0] * Bf
         B[2 * Np:3 * Np, cols] = -Phi * nrm[1] * Bf
+    if gamma != 0.0:
+        A[Np:2 * Np, Np:2 * Np] += gamma * Phi * M
+        A[2 * Np:3 * Np, 2 * Np:3 * Np] += gamma * Phi * M
+    if f0 != 0.0 or beta_c != 0.0:
+        lo_y = 0.0 if lo is None else float(np.asarray(lo)[1])
+        y_q = lo_y + 0.5 * h[1] * (ref.X[:, 1] + 1.0)     # physical y of the quadrature points
+        fq = f0 + beta_c * (y_q - y_m)
+        Mf = ref.phi.T @ ((W * fq)[:, None] * ref.phi)
+        A[Np:2 * Np, 2 * Np:3 * Np] -= Phi * Mf
+        A[2 * Np:3 * Np, Np:2 * Np] += Phi * Mf
     Mblk = np.zeros((n, n))
     Mblk[0:Np, 0:Np] = M
     Mblk[Np:2 * Np, Np:2 * Np] = Phi * M

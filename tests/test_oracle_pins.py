@@ -428,3 +428,77 @@ def test_shallow_water_contraction_threshold_of_theorem2():
     u0 = rng.standard_normal((prob.nel, 3, prob.Np))
     _, _, hist = prob.solve_step(u0, tol=0.0, fixed_iters=60)
     assert hist[-1] < 1e-12 * hist[0]
+
+
+# ---------------------------------------------------------------------------
+# shallow water with Coriolis and bottom friction (eq. linearizedShallow)
+# ---------------------------------------------------------------------------
+
+def _sw_manufactured(Phi, f0, beta_c, y_m, gamma):
+    """A steady solution with walls (u = 0 at x = 0, 1 and v = 0 at y = 0, 1)
+    and the forcing of each unknown that makes it exact: the phi equation
+    phi_t + Phi (u_x + v_y) = F_phi, and Phi u_t + Phi phi_x = f Phi v -
+    gamma Phi u + Phi F_u (v likewise), with f = f0 + beta (y - y_m)."""
+    a, b = 0.7, -0.4
+    c, s = np.cos, np.sin
+    phi = lambda x: c(PI * x[..., 0]) * c(PI * x[..., 1])
+    u = lambda x: a * s(PI * x[..., 0]) * c(PI * x[..., 1])
+    v = lambda x: b * c(PI * x[..., 0]) * s(PI * x[..., 1])
+    cor = lambda x: f0 + beta_c * (x[..., 1] - y_m)
+    f_phi = lambda x: Phi * PI * (a + b) * c(PI * x[..., 0]) * c(PI * x[..., 1])
+    f_u = lambda x: -PI * s(PI * x[..., 0]) * c(PI * x[..., 1]) - cor(x) * v(x) + gamma * u(x)
+    f_v = lambda x: -PI * c(PI * x[..., 0]) * s(PI * x[..., 1]) + cor(x) * u(x) + gamma * v(x)
+    return (phi, u, v), (f_phi, f_u, f_v)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_sw_coriolis_friction_manufactured_order(p):
+    """Backward Euler with dt = 1 over t = 20 by the monolithic HDG solve (no
+    contraction limit on dt): the source terms act for long enough that a
+    wrong sign or coefficient leaves an O(1) error, while the discretisation
+    error of the steady solution falls at order p + 1."""
+    Phi, f0, beta_c, y_m, gamma = 1.0, 0.8, 1.5, 0.5, 0.3
+    ex, fo = _sw_manufactured(Phi, f0, beta_c, y_m, gamma)
+    errs = []
+    for N in (4, 8, 16):
+        mesh = W.structured_mesh((N, N), boundary_tag=W.TAG_WALL)
+        prob = Problem(mesh, p, pde="sw", scheme="be", dt=1.0, Phi=Phi,
+                       coriolis=(f0, beta_c, y_m), friction=gamma)
+        X = node_coords(mesh, p)
+        u = np.stack([ex[k](X) for k in range(3)], 1)
+        f = np.stack([fo[k](X) for k in range(3)], 1)
+        for _ in range(20):
+            u, _ = direct.solve(prob, u, None, f_new=f)
+        err = math.sqrt(sum(l2_volume(prob, np.roll(u, -k, axis=1), ex[k]) ** 2
+                            for k in range(3)))
+        errs.append(err)
+    assert math.log2(errs[-2] / errs[-1]) > p + 1 - 0.3, errs
+    assert errs[-1] < errs[0] / 4.0 ** (p + 1 - 0.3), errs
+
+
+@pytest.mark.parametrize("coriolis,gamma", [((0.9, 0.0, 0.0), 0.0), ((0.5, 2.0, 0.5), 0.0),
+                                            ((0.5, 2.0, 0.5), 0.7)])
+def test_sw_coriolis_energy_and_friction_dissipation(coriolis, gamma):
+    """Coriolis does no work: its two terms cancel in the energy identity,
+    so BE with upwind traces keeps the energy E = phi M phi + Phi (u M u +
+    v M v) non-increasing, and friction takes out at least 2 dt gamma Phi
+    (u M u + v M v) of the new state per step."""
+    rng = np.random.default_rng(21)
+    p, dt, Phi = 2, 5e-3, 1.0
+    mesh = W.structured_mesh((5, 4), boundary_tag=W.TAG_WALL)
+    prob = Problem(mesh, p, pde="sw", scheme="be", dt=dt, Phi=Phi, coriolis=coriolis,
+                   friction=gamma)
+    Mb = prob.M[0]
+    Np = prob.Np
+    energy = lambda v: float(np.einsum("ei,ij,ej->", v.reshape(prob.nel, -1), Mb,
+                                       v.reshape(prob.nel, -1)))
+    vel = lambda v: float(np.einsum("ei,ij,ej->", v.reshape(prob.nel, -1)[:, Np:],
+                                    Mb[Np:, Np:], v.reshape(prob.nel, -1)[:, Np:]))
+    u = rng.standard_normal((prob.nel, 3, Np))
+    e0 = energy(u)
+    for _ in range(3):
+        u, _, _ = prob.solve_step(u, tol=1e-14, max_iter=500)
+        e1 = energy(u)
+        assert e1 <= e0 * (1 + 1e-12)
+        assert e0 - e1 >= 2.0 * dt * gamma * vel(u) * (1 - 1e-9) - 1e-12 * e0
+        e0 = e1
