@@ -110,6 +110,18 @@ typedef struct {
   double Phi;                  /* shallow water: mean geopotential Phi > 0 */
   int inner_sweeps;            /* mixed precision: low-precision sweeps per outer
                                   iteration (0 = 8) */
+  /* Shallow water source terms of eq. linearizedShallow (Sec. 3): Coriolis
+   * parameter f = coriolis_f0 + coriolis_beta (y - coriolis_ym) and bottom
+   * friction gamma = friction >= 0, in the local equations (eq.
+   * localSolverDD). All zero gives the equations without them; transport
+   * requires zeros. A nonzero coriolis_beta makes every element's operator
+   * different (per-element operators). Wind stress tau / rho enters as
+   * forcing of the velocity rows: ehdg_set_forcing with (tau_x, tau_y) /
+   * (rho Phi) in the u and v fields. */
+  double coriolis_f0;
+  double coriolis_beta;
+  double coriolis_ym;
+  double friction;
 } ehdg_problem_desc;
 
 /* Sizes of a created context. */

@@ -611,6 +611,14 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
     if (!(prob->Phi > 0.0)) return fail(EHDG_ERR_INVALID, "Phi must be positive");
     if (p > 5) return fail(EHDG_ERR_UNSUPPORTED, "shallow water supports p <= 5");
   }
+  const double src_terms[4] = {prob->coriolis_f0, prob->coriolis_beta, prob->coriolis_ym,
+                               prob->friction};
+  for (double v : src_terms)
+    if (!std::isfinite(v)) return fail(EHDG_ERR_INVALID, "Coriolis and friction must be finite");
+  if (prob->friction < 0.0) return fail(EHDG_ERR_INVALID, "friction must be >= 0");
+  if (prob->pde == EHDG_TRANSPORT && (prob->coriolis_f0 != 0.0 || prob->coriolis_beta != 0.0 ||
+                                      prob->friction != 0.0))
+    return fail(EHDG_ERR_INVALID, "Coriolis and friction are shallow-water terms");
   const int q = variable ? (3 * p + 1) / 2 + 1 : p + 1;
   if (q > kMaxQ || p + 1 > kMaxP1) return fail(EHDG_ERR_UNSUPPORTED, "degree too high");
 
@@ -638,6 +646,10 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   c.tol = prob->tol;
   c.max_iter = prob->max_iter;
   c.Phi = prob->Phi;
+  c.cor_f0 = prob->coriolis_f0;
+  c.cor_beta = prob->coriolis_beta;
+  c.cor_ym = prob->coriolis_ym;
+  c.friction = prob->friction;
   c.variable_beta = variable;
   c.mixed = prob->precision != EHDG_FP64;
   c.precision = prob->precision;
@@ -650,7 +662,8 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   for (int64_t e = 1; e < c.nel && uniform; ++e)
     for (int a = 0; a < dim; ++a)
       if (mesh->elem_h[e * dim + a] != mesh->elem_h[a]) uniform = false;
-  c.shared_op = uniform && !variable;
+  // a beta-plane Coriolis parameter varies with y: one operator per element
+  c.shared_op = uniform && !variable && !(prob->pde == EHDG_SW_LINEAR && c.cor_beta != 0.0);
   if (c.precision == EHDG_MIXED_TF32 && !c.shared_op) {
     delete h;
     return fail(EHDG_ERR_UNSUPPORTED,
@@ -672,6 +685,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   c.ref.nf = c.nf;
   for (int g = 0; g < q; ++g) {
     c.ref.om[g] = c.r1d.om[g];
+    c.ref.xi[g] = c.r1d.xi[g];
     for (int a = 0; a <= p; ++a) {
       c.ref.L[g * kMaxP1 + a] = c.r1d.L[g * (p + 1) + a];
       c.ref.D[g * kMaxP1 + a] = c.r1d.D[g * (p + 1) + a];
@@ -832,6 +846,11 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   CKC(cudaMemcpy(c.ey_idx, eyi.data(), sizeof(int) * eyi.size(), cudaMemcpyHostToDevice));
   CKC(cudaMemcpy(c.ey_val, eyv.data(), sizeof(double) * eyv.size(), cudaMemcpyHostToDevice));
   CKC(cudaMemcpy(c.rows, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice));
+  if (c.pde == EHDG_SW_LINEAR && (c.cor_f0 != 0.0 || c.cor_beta != 0.0)) {
+    TRYC(dalloc(c, &c.elem_lo_d, (size_t)c.nel * dim));
+    CKC(cudaMemcpy(c.elem_lo_d, c.elem_lo.data(), sizeof(double) * c.nel * dim,
+                   cudaMemcpyHostToDevice));
+  }
   if (variable) {
     TRYC(dalloc(c, &c.beta_nodes, (size_t)c.nel * dim * c.Np));
     CKC(cudaMemcpy(c.beta_nodes, prob->beta_nodes, sizeof(double) * c.nel * dim * c.Np,

@@ -57,6 +57,8 @@ uint64_t config_hash(const Ctx& c) {
   h = fnv1a(h, c.face_elem_h.data(), sizeof(int64_t) * c.face_elem_h.size());
   h = fnv1a(h, &c.dt, sizeof(double));
   h = fnv1a(h, &c.Phi, sizeof(double));
+  const double src[4] = {c.cor_f0, c.cor_beta, c.cor_ym, c.friction};
+  h = fnv1a(h, src, sizeof(src));
   h = fnv1a(h, c.beta_const, sizeof(double) * 3);
   return h;
 }

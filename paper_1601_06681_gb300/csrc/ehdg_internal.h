@@ -37,6 +37,7 @@ struct RefTables {               // lives in kernel parameter space (small)
   double D[kMaxQ * kMaxP1];
   double Lend[2 * kMaxP1];
   double om[kMaxQ];
+  double xi[kMaxQ];               // Gauss points on [-1, 1]
 };
 
 struct Geometry {
@@ -68,6 +69,7 @@ struct Ctx {
   ehdg_pde pde = EHDG_TRANSPORT;
   ehdg_scheme scheme = EHDG_BE;
   double dt = 0, dt_eff = 0, tol = 0, Phi = 1, res_scale = 1;
+  double cor_f0 = 0, cor_beta = 0, cor_ym = 0, friction = 0;   // shallow-water source terms
   int max_iter = 0;
   bool shared_op = false;        // one operator for all elements
   bool variable_beta = false;
@@ -87,6 +89,7 @@ struct Ctx {
   int64_t bytes = 0;
   Geometry geo{};
   double* beta_nodes = nullptr;  // [nel][dim][Np] (variable velocity)
+  double* elem_lo_d = nullptr;   // [nel][dim] element lower corners (beta-plane Coriolis)
   double* P = nullptr;           // [n][n][ne]   A^{-1} Mblk
   double* H = nullptr;           // [n][NQFS][ne] A^{-1} B
   double* Hy = nullptr;          // [NQFS][NQFS][ne] face-point rows of H

@@ -99,8 +99,10 @@ struct AsmParams {
   double tcoef;                 // coefficient of the mass term in A (1/dt_eff, 0 for steady)
   double Phi;
   double beta_c[3];
+  double cor_f0, cor_beta, cor_ym, friction;   // shallow-water source terms
   int variable;
   const double* elem_h;         // [nel][dim]
+  const double* elem_lo;        // [nel][dim] (beta-plane Coriolis), or null
   const double* beta_nodes;     // [nel][dim][Np]
   const int* ey_idx;
   const double* ey_val;
@@ -200,11 +202,16 @@ __global__ void k_assemble(const AsmParams a) {
     for (int t = tid; t < n * n; t += nt) {
       const int I = t / n, Jc = t % n;
       const int fi = I / Np, i = I % Np, fj = Jc / Np, j = Jc % Np;
-      double m = 0.0, gx[3] = {0.0, 0.0, 0.0};
+      double m = 0.0, mf = 0.0, gx[3] = {0.0, 0.0, 0.0};
+      const double lo_y = a.elem_lo ? a.elem_lo[(int64_t)e * dim + 1] : 0.0;
       for (int g = 0; g < Q; ++g) {
         const double w = vweight(R, g) * J;
         const double pj = vphi(R, j, g);
-        m += w * vphi(R, i, g) * pj;
+        const double pij = vphi(R, i, g) * pj;
+        m += w * pij;
+        // Coriolis parameter f = f0 + beta (y - y_m) at the point's physical y
+        const double y = lo_y + 0.5 * hsh[1] * (R.xi[digit(g, R.q, 1)] + 1.0);
+        mf += w * (a.cor_f0 + a.cor_beta * (y - a.cor_ym)) * pij;
         for (int ax = 0; ax < dim; ++ax) gx[ax] += w * (2.0 / hsh[ax]) * vdphi(R, ax, i, g) * pj;
       }
       double ef[6];
@@ -228,8 +235,12 @@ __global__ void k_assemble(const AsmParams a) {
       } else if (fj == 0) {
         A = -Phi * gx[fi - 1];
       } else if (fi == fj) {
-        A = a.tcoef * Phi * m;
+        // velocity rows: mass term and bottom friction (gamma Phi u, w)
+        A = (a.tcoef + a.friction) * Phi * m;
         Mb = Phi * m;
+      } else {
+        // Coriolis: -(f Phi v, w) in the u-row, +(f Phi u, w) in the v-row
+        A = (fi == 1 ? -1.0 : 1.0) * Phi * mf;
       }
       aug[I * ncol + Jc] = A;
       aug[I * ncol + n + Jc] = Mb;
@@ -328,6 +339,11 @@ cudaError_t launch_assemble(Ctx& c, int n_assemble) {
   a.tcoef = (c.scheme == EHDG_STEADY) ? 0.0 : 1.0 / c.dt_eff;
   a.Phi = c.Phi;
   for (int d = 0; d < 3; ++d) a.beta_c[d] = c.beta_const[d];
+  a.cor_f0 = c.cor_f0;
+  a.cor_beta = c.cor_beta;
+  a.cor_ym = c.cor_ym;
+  a.friction = c.friction;
+  a.elem_lo = c.elem_lo_d;
   a.variable = c.variable_beta ? 1 : 0;
   a.elem_h = c.geo.elem_h;
   a.beta_nodes = c.beta_nodes;

@@ -92,6 +92,16 @@ def make_case(name):
     elif name == "sw_be":
         mesh, p = W.structured_mesh((12, 11), boundary_tag=W.TAG_WALL), 2
         kw = dict(pde="sw", scheme="be", dt=2e-3, Phi=1.3)
+    elif name == "sw_fplane":
+        # Coriolis f-plane and bottom friction: still one shared operator
+        mesh, p = W.structured_mesh((12, 11), boundary_tag=W.TAG_WALL), 2
+        kw = dict(pde="sw", scheme="be", dt=2e-3, Phi=1.3, coriolis=(0.9, 0.0, 0.0),
+                  friction=0.2)
+    elif name == "sw_betaplane":
+        # beta-plane Coriolis f = f0 + beta (y - y_m) and friction: per-element operators
+        mesh, p = W.structured_mesh((9, 10), boundary_tag=W.TAG_WALL), 3
+        kw = dict(pde="sw", scheme="be", dt=1e-3, Phi=1.0, coriolis=(0.5, 2.0, 0.4),
+                  friction=0.3)
     elif name == "sw_be_p3":
         mesh, p = W.structured_mesh((9, 14), boundary_tag=W.TAG_WALL), 3
         kw = dict(pde="sw", scheme="be", dt=1e-3, Phi=1.0)
@@ -116,7 +126,7 @@ def make_solver(E, mesh, p, kw, prob, tol=1e-10, max_iter=400):
 CASES = ["2d_be_const", "2d_be_zero_component", "2d_cn_variable", "2d_cn_variable_p4",
          "2d_steady_variable", "2d_graded_mesh", "2d_per_element_const_beta",
          "2d_per_element_tangent", "3d_be_const", "3d_be_const_p3", "3d_be_variable", "sw_be",
-         "sw_be_p3"]
+         "sw_be_p3", "sw_fplane", "sw_betaplane"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -149,7 +159,8 @@ def test_fixed_iterations_match_oracle(ehdg, name, n_iter):
     assert np.allclose(hist, ohist, rtol=1e-10, atol=1e-300)
 
 
-@pytest.mark.parametrize("name", ["2d_be_const", "2d_cn_variable", "3d_be_const", "sw_be"])
+@pytest.mark.parametrize("name", ["2d_be_const", "2d_cn_variable", "3d_be_const", "sw_be",
+                                  "sw_fplane", "sw_betaplane"])
 def test_steps_to_tolerance_match_oracle(ehdg, name):
     mesh, p, kw, prob, u0, g = make_case(name)
     n_steps = 3
@@ -262,7 +273,7 @@ def test_device_pointer_io_matches_host_io(ehdg):
 
 @pytest.mark.parametrize("name", ["2d_be_const", "2d_be_zero_component", "2d_cn_variable",
                                   "2d_cn_variable_p4", "3d_be_const", "sw_be", "2d_graded_mesh",
-                                  "2d_per_element_tangent", "3d_be_variable"])
+                                  "2d_per_element_tangent", "3d_be_variable", "sw_betaplane"])
 def test_mixed_precision_reaches_fp64_solution(ehdg, name):
     mesh, p, kw, prob, u0, g = make_case(name)
     n_steps = 3
@@ -303,7 +314,7 @@ def test_mixed_fixed_iterations_are_deterministic(ehdg):
 
 @pytest.mark.parametrize("precision", ["tf32", "bf16"])
 @pytest.mark.parametrize("name", ["2d_be_const", "2d_be_zero_component", "3d_be_const",
-                                  "3d_be_const_p3", "sw_be_p3"])
+                                  "3d_be_const_p3", "sw_be_p3", "sw_fplane"])
 def test_tensor_core_mixed_reaches_fp64_solution(ehdg, name, precision):
     mesh, p, kw, prob, u0, g = make_case(name)
     n_steps = 2
