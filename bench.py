@@ -421,7 +421,7 @@ def compare_workload(args):
     stream = torch.cuda.current_stream()
     if args.workload == "transport3d":
         wl = W.transport_3d(n=(args.n, args.n, args.n), p=3, n_steps=args.time_steps)
-        precisions = ["fp64", "tf32", "bf16", "fp32"]
+        precisions = ["fp64", "fp64_emulated", "tf32", "bf16", "fp32"]
     elif args.workload == "sw2d":
         # dt at which Theorem 2 holds on this mesh: h / (dt (p+1)(p+2)) = 3.9, C = 0.34
         wl = W.sw_2d(n=(args.n, args.n), p=3, dt=2.5e-5, n_steps=args.time_steps)
@@ -432,7 +432,7 @@ def compare_workload(args):
         precisions = ["fp64", "fp32", "bf16"]
     else:
         wl = W.transport_2d_small(n=(args.n, args.n), p=2, n_steps=args.time_steps)
-        precisions = ["fp64", "tf32", "fp32"]
+        precisions = ["fp64", "fp64_emulated", "tf32", "fp32"]
     mesh = ehdg.ehdg_mesh_structured(wl.n, boundary_tag=(2 if wl.pde == "sw" else 1))
     results = {}
     ref = None

@@ -71,12 +71,24 @@ typedef enum { EHDG_BE = 0, EHDG_CN = 1, EHDG_STEADY = 2 } ehdg_scheme;
  * followed by `inner_sweeps` low-precision eHDG sweeps on the correction
  * equation delta = R + S H delta and the FP64 update uhat += delta; the fixed
  * point and the stopping rule are those of the FP64 iteration. MIXED_FP32 uses
- * float32 operands and accumulation on the CUDA cores. */
+ * float32 operands and accumulation on the CUDA cores.
+ * FP64_EMULATED: every sweep FP64-accurate, with the element products on the
+ * BF16 tensor cores by the Ozaki splitting -- each element's traces and each
+ * operator row in 49-bit fixed point against their largest exponent, split
+ * into seven 7-bit digits whose products are summed exactly (integers below
+ * 2^24 in FP32 accumulators) and recombined in 64-bit integers; the trace
+ * formula and the residual stay FP64. Per product the error is below about
+ * 2^-49 (|uhat| max|Hy row| + |Hy| max|uhat_e|) + 2^-51 max|uhat_e| max|Hy row|.
+ * Transport with one local operator shared by all elements (constant
+ * velocity, uniform mesh), 2D p <= 6 or 3D p <= 3, at most 64 sweep rows per
+ * element; otherwise ehdg_create returns EHDG_ERR_UNSUPPORTED. The paper has
+ * no counterpart: it is a GB300 form of the plain FP64 sweep. */
 typedef enum {
   EHDG_FP64 = 0,
   EHDG_MIXED_TF32 = 1,
   EHDG_MIXED_BF16 = 2,
-  EHDG_MIXED_FP32 = 3
+  EHDG_MIXED_FP32 = 3,
+  EHDG_FP64_EMULATED = 4
 } ehdg_precision;
 
 /* Face tags. */
@@ -104,7 +116,7 @@ typedef struct {
   double dt;                   /* time step (ignored for STEADY) */
   double tol;                  /* stop when ||uhat^{k+1}-uhat^k||_{L2(E_h)} < tol */
   int max_iter;                /* iteration cap per step, >= 1 */
-  ehdg_precision precision;    /* EHDG_FP64 or EHDG_MIXED_FP32 in this build */
+  ehdg_precision precision;    /* one of ehdg_precision */
   const double* beta_const;    /* [dim] constant velocity, or NULL */
   const double* beta_nodes;    /* [n_elem][dim][Np] nodal velocity, or NULL (transport) */
   double Phi;                  /* shallow water: mean geopotential Phi > 0 */

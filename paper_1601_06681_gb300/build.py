@@ -32,7 +32,7 @@ def build(verbose=False, force=False, extra=None):
     """Compile every translation unit and link libehdg.so; returns its path."""
     os.makedirs(BUILD, exist_ok=True)
     srcs = sources()
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "ehdg.h"))
     newest_dep = max(os.path.getmtime(p) for p in srcs + headers)
     if (not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest_dep

@@ -173,6 +173,15 @@ ehdg_status download(Ctx& c, double* dst, const double* src_soa, int64_t outer, 
   return EHDG_OK;
 }
 
+// A tensor-core sweep whose bounded mbarrier wait gave up leaves a flag.
+ehdg_status check_tc_err(Ctx& c) {
+  if (!c.tc_err) return EHDG_OK;
+  int te = 0;
+  CK(cudaMemcpy(&te, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (te) return fail(EHDG_ERR_TIMEOUT, "a sweep's bounded mbarrier wait gave up");
+  return EHDG_OK;
+}
+
 ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
   CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_reset_iter(c); }));
   CK(counted(c, EHDG_KERNEL_STEP, 1, [&] { return launch_step(c); }));
@@ -221,6 +230,7 @@ ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
   c.last_iters = std::min(c.it_host->k, c.max_iter);
   if (iters) *iters = c.it_host->k;
   if (res) *res = c.it_host->r_last;
+  TRY(check_tc_err(c));
   if (fixed_iters > 0) return EHDG_OK;
   const ehdg_status st = (ehdg_status)c.it_host->status;
   if (st == EHDG_ERR_NOT_CONVERGED) return fail(st, "eHDG did not reach the tolerance in max_iter iterations");
@@ -410,11 +420,7 @@ ehdg_status run_graph(Ctx& c, int n_steps, int* iters_per_step, double* res) {
   }
   c.last_iters = n_steps > 0 ? std::min(c.step_iters_h[n_steps - 1], c.max_iter) : 0;
   if (res) *res = c.it_host->r_last;
-  if (c.tc_err) {
-    int te = 0;
-    CK(cudaMemcpy(&te, c.tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (te) return fail(EHDG_ERR_TIMEOUT, "a sweep's bounded mbarrier wait gave up");
-  }
+  TRY(check_tc_err(c));
   if (first == EHDG_ERR_NOT_CONVERGED) return fail(first, "eHDG did not reach the tolerance in max_iter iterations");
   if (first == EHDG_ERR_DIVERGED) return fail(first, "non-finite eHDG residual");
   return first;
@@ -590,7 +596,8 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   TRY(validate_mesh(mesh, prob->pde));
   const int dim = mesh->dim, p = prob->p;
   if (prob->precision != EHDG_FP64 && prob->precision != EHDG_MIXED_FP32 &&
-      prob->precision != EHDG_MIXED_TF32 && prob->precision != EHDG_MIXED_BF16)
+      prob->precision != EHDG_MIXED_TF32 && prob->precision != EHDG_MIXED_BF16 &&
+      prob->precision != EHDG_FP64_EMULATED)
     return fail(EHDG_ERR_INVALID, "unknown precision");
   if (prob->inner_sweeps < 0 || prob->inner_sweeps > 64)
     return fail(EHDG_ERR_INVALID, "inner_sweeps must be 0..64");
@@ -651,7 +658,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   c.cor_ym = prob->coriolis_ym;
   c.friction = prob->friction;
   c.variable_beta = variable;
-  c.mixed = prob->precision != EHDG_FP64;
+  c.mixed = prob->precision != EHDG_FP64 && prob->precision != EHDG_FP64_EMULATED;
   c.precision = prob->precision;
   c.inner_sweeps = prob->inner_sweeps > 0 ? prob->inner_sweeps : 8;
   c.stream = (cudaStream_t)stream;
@@ -669,6 +676,12 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
     return fail(EHDG_ERR_UNSUPPORTED,
                 "TF32 tensor-core sweeps need one local operator shared by all elements "
                 "(constant velocity, uniform mesh); use EHDG_MIXED_FP32 or EHDG_MIXED_BF16");
+  }
+  if (c.precision == EHDG_FP64_EMULATED && (prob->pde != EHDG_TRANSPORT || !c.shared_op)) {
+    delete h;
+    return fail(EHDG_ERR_UNSUPPORTED,
+                "FP64_EMULATED sweeps need transport with one local operator shared by all "
+                "elements (constant velocity, uniform mesh)");
   }
   if (c.precision == EHDG_MIXED_BF16 && !c.shared_op && prob->pde != EHDG_TRANSPORT) {
     delete h;
@@ -913,6 +926,14 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
                         "count of the tiled sweep (quadrilaterals with 2..10 points per edge, "
                         "hexahedra with 2x2 or 3x3 per face)"));
   if (c.mixed) CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_hy_to_f32(c); }));
+  if (c.precision == EHDG_FP64_EMULATED) {
+    if (!ozaki_supported(c))
+      return cleanup(fail(EHDG_ERR_UNSUPPORTED,
+                          "FP64_EMULATED sweeps support at most 64 sweep rows and 96 face "
+                          "points per element"));
+    CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return build_ozaki_operator(c); }));
+    c.use_ozaki = true;
+  }
   CKC(cudaMemcpyAsync(c.it_host, c.it, sizeof(IterState), cudaMemcpyDeviceToHost, c.stream));
   CKC(cudaStreamSynchronize(c.stream));
   if (c.it_host->status != 0) return cleanup(fail(EHDG_ERR_INVALID, "singular local operator"));

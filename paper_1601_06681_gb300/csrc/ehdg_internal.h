@@ -131,6 +131,13 @@ struct Ctx {
   bool mixed = false;
   ehdg_precision precision = EHDG_FP64;
   int* tc_err = nullptr;         // set by a sweep whose bounded mbarrier wait gave up
+  // FP64-accurate sweep on the BF16 tensor cores (Ozaki splitting, shared operator)
+  bool use_ozaki = false;
+  void* oz_img = nullptr;        // [7][Np x KP] BF16 digit slices of the sweep rows
+  int* oz_Fb = nullptr;          // [Np] largest biased exponent of each sweep row
+  int oz_Np = 0, oz_LS = 0, oz_ncols = 0;   // padded rows, TMEM columns per level, allocated
+  int oz_grid = 0;
+  size_t oz_smem = 0;
   int inner_sweeps = 0;
   float* Hy32 = nullptr;         // FP32 copy of Hy in the sweep's slot layout
   float* R32 = nullptr;          // [Nqf][nface] FP64 residual F(uhat) - uhat, rounded
@@ -215,6 +222,11 @@ cudaError_t launch_lp_sweep_tiled(Ctx& c, const float* in, float* out);   // FP3
 // mixed precision (mixed.cu)
 cudaError_t launch_hy_to_f32(Ctx& c);
 cudaError_t launch_correction(Ctx& c, int* n_launched);
+// FP64-accurate tensor-core sweep (ozaki_sweep.cu)
+bool ozaki_supported(const Ctx& c);
+cudaError_t build_ozaki_operator(Ctx& c);   // after assembly and rows
+cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out);
+cudaError_t dalloc_raw(Ctx& c, void** p, size_t bytes);   // device allocation owned by c
 // tensor-core correction sweep (tc_sweep.cu)
 bool tc_supported(const Ctx& c);
 cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out);

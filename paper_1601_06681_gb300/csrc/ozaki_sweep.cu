@@ -1,0 +1,591 @@
+// FP64-accurate transport sweep on the BF16 tensor cores (Ozaki splitting),
+// for a local operator shared by every element (constant velocity, uniform
+// mesh).
+//
+// Per eHDG iteration (Algorithm 1, Sec. 3) and element e, every sweep row n
+// (a face point r_n of e) needs y = sum_j Hy[r_n][j] uhat_e[j]: the local
+// solve (eq. transportLocalk1) evaluated at the face points, with Hy the
+// face-point rows of A^{-1} B. The owner of the point then writes
+// uhat^{k+1} = Gy + y (eq. transportLocale, upwind selection) and adds its
+// share of the FP64 residual ||uhat^{k+1} - uhat^k||_{L2(E_h)}.
+//
+// Over all elements the products are one GEMM, M = elements, N = rows,
+// K = face points. Here it runs as exact integer arithmetic:
+//  - each element's traces go to fixed point against the element's largest
+//    exponent E, X_j = round(|uhat_j| 2^(1071 - E)) < 2^49 + 1, and each
+//    operator row against its own largest exponent, Y_nj;
+//  - the signed X and Y are written in base 128 with seven digits,
+//    X = x_0 2^42 + sum_{i>=1} x_i 2^(42 - 7 i): x_0 = floor(X / 2^42) in
+//    [-128, 128] carries the sign and x_1..x_6 are in [0, 127], all exact in
+//    BF16;
+//  - tcgen05.mma (kind::f16, BF16 operands, FP32 accumulation) sums the digit
+//    products of level L = i + l into one TMEM accumulator per level,
+//    L = 0..7. Every partial sum is an integer of magnitude below 2^24
+//    (7 * K * 128 * 128 with K <= 144), so the FP32 accumulation is exact;
+//  - the epilogue recombines the levels in 64-bit integers and builds the
+//    double from its bits, then adds Gy and forms the residual in FP64.
+// Rounding X and Y costs at most 2^-49 of the element's (row's) largest
+// magnitude per operand; the dropped levels L >= 8 cost below 2^-51 of
+// max|uhat_e| max|Hy_n| per product.
+//
+// Shared-memory operands use the K-major layout without swizzle. B (the
+// seven digit slices of the sweep rows) stays resident; A (one digit slice
+// of the tile's 128 elements) is double-buffered so that the digits of slice
+// i + 1 are written while the MMAs of slice i run. One thread issues the MMAs
+// and commits each slice to an mbarrier; every wait is bounded and records an
+// error instead of hanging.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "ehdg_internal.h"
+#include "sweep_common.cuh"
+#include "umma.cuh"
+
+namespace ehdg {
+
+namespace {
+
+constexpr int kOzM = 128;                  // elements per tile (TMEM lanes)
+constexpr int kOzThreads = 256;            // two threads per element
+constexpr int kOzDigits = 7;               // 7-bit digits per operand: 49-bit fixed point
+constexpr int kOzLevels = 8;               // digit-product levels kept, L = i + l <= 7
+constexpr uint32_t kOzWait = 1u << 24;     // mbarrier polls before giving up
+
+struct OzParams {
+  int64_t nel, nface;
+  int NQFS, Nqf, F, n_rows, n_up;
+  int Np, LS, ncols;            // rows padded to 16, TMEM columns per level, allocated columns
+  uint32_t idesc;
+  const int* rows;              // sweep rows (face points), upwind first
+  const int32_t* elem_face;     // [F][nel]
+  const double* face_jf;        // [nface]
+  double fw[kMaxQ * kMaxQ];
+  const uint4* Bimg;            // [kOzDigits][Np x KP] BF16 digits, K-major image
+  const int* Fb;                // [Np] largest biased exponent of each row
+  double* uhat;                 // [2][Nqf][nface]
+  IterState* it;
+  const double* Gy;             // [row][nel]
+  double* Y;                    // [point][nel] rows of tangential points
+  double* partials;
+  int final_here;
+  double tol, res_scale;
+  int max_iter;
+  double* hist;
+  int graph_mode;
+  cudaGraphConditionalHandle handle;
+  int* err;
+};
+
+// Signed fixed point of x against biased exponent E >= that of x:
+// round(x 2^(1071 - E)), of magnitude <= 2^49. Zeros and subnormals give 0
+// (below the fixed point's resolution).
+__host__ __device__ __forceinline__ int64_t oz_fixed(uint64_t bits, int E) {
+  const int be = (int)((bits >> 52) & 0x7FF);
+  if (be == 0) return 0;
+  const int sh = E - be + 4;
+  if (sh >= 54) return 0;
+  const uint64_t mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int64_t a = (int64_t)((mant + (1ull << (sh - 1))) >> sh);
+  return (bits >> 63) ? -a : a;
+}
+
+// Base-128 digit i of a signed fixed-point value as BF16 bits (exact):
+// i = 0 is floor(X / 2^42) in [-128, 128], i >= 1 is in [0, 127].
+template <int I>
+__device__ __forceinline__ uint32_t oz_digit_bf16(int64_t X) {
+  if (I == 0) {
+    const int d = (int)(X >> 42);
+    // 1.5 * 2^23 + d as float bits, minus 1.5 * 2^23: exactly d
+    const float f = __int_as_float(0x4B400000 + d) - 12582912.0f;
+    return __float_as_uint(f) >> 16;
+  } else {
+    const uint32_t d = (uint32_t)(X >> (42 - 7 * I)) & 127u;
+    const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;
+    return __float_as_uint(f) >> 16;
+  }
+}
+
+// T * 2^(sc - 1023) as a double, from the bits (|T| < 2^62; truncated to
+// 53 bits; 0 below the normal range).
+__device__ __forceinline__ double oz_to_double(int64_t T, int sc) {
+  if (T == 0) return 0.0;
+  const uint64_t s = (uint64_t)(T >> 63);
+  const uint64_t a = ((uint64_t)T ^ s) - s;
+  const int lz = __clzll((long long)a);
+  const int be = 63 - lz + sc;
+  if (be <= 0) return 0.0;
+  if (be >= 2047) return __longlong_as_double((long long)((s << 63) | (0x7FFull << 52)));
+  const uint64_t m = (a << lz) >> 11;
+  return __longlong_as_double(
+      (long long)((s << 63) | ((uint64_t)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// 8-byte asynchronous copy global -> shared; n = 0 fills zeros without reading
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int n) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src),
+               "r"(n)
+               : "memory");
+}
+
+__device__ __forceinline__ void oz_mma(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(d),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void oz_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar)));
+}
+
+// Setup: digit slices and row exponents of the shared operator's sweep rows,
+// one warp per padded row.
+template <int I>
+__device__ __forceinline__ void oz_put_digit(unsigned short* img, int Np, int KP, int n, int j,
+                                             int64_t Yv) {
+  const size_t off = (size_t)I * Np * KP * 2 + kmajor_off(n, 2 * j, 16u * (uint32_t)KP);
+  img[off / 2] = (unsigned short)oz_digit_bf16<I>(Yv);
+}
+
+__global__ void k_oz_split_rows(const double* Hy, const int* rows, int n_rows, int NQFS, int Np,
+                                int KP, unsigned short* img, int* Fb) {
+  const int n = blockIdx.x, lane = threadIdx.x;
+  int emax = 0;
+  if (n < n_rows)
+    for (int j = lane; j < NQFS; j += 32) {
+      const uint64_t b = (uint64_t)__double_as_longlong(Hy[(int64_t)rows[n] * NQFS + j]);
+      emax = max(emax, (int)((b >> 52) & 0x7FF));
+    }
+  for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  if (lane == 0) Fb[n] = emax;
+  for (int j = lane; j < KP; j += 32) {
+    uint64_t bits = 0;
+    if (n < n_rows && j < NQFS)
+      bits = (uint64_t)__double_as_longlong(Hy[(int64_t)rows[n] * NQFS + j]);
+    const int64_t Yv = oz_fixed(bits, emax);
+    oz_put_digit<0>(img, Np, KP, n, j, Yv);
+    oz_put_digit<1>(img, Np, KP, n, j, Yv);
+    oz_put_digit<2>(img, Np, KP, n, j, Yv);
+    oz_put_digit<3>(img, Np, KP, n, j, Yv);
+    oz_put_digit<4>(img, Np, KP, n, j, Yv);
+    oz_put_digit<5>(img, Np, KP, n, j, Yv);
+    oz_put_digit<6>(img, Np, KP, n, j, Yv);
+  }
+}
+
+// Per-CTA state of the sweep kernel that the slice steps share.
+struct OzCta {
+  unsigned char* As;            // [2][128 x KP] A digit buffers
+  uint64_t* mbar;               // [3]
+  uint64_t adesc[2];            // descriptors of the two A buffers (K step 0)
+  uint64_t bdesc[kOzDigits];    // descriptors of the B digit slices (K step 0)
+  uint32_t tbase;
+  uint32_t ph0, ph1;            // phases of mbar[0] and mbar[1]
+};
+
+// Digit slice I of the tile: wait until its buffer's previous slice (I - 2)
+// is consumed, write this thread's digits, then one thread issues the MMAs of
+// every level I + l <= 7 and commits them. Returns false (block-uniform) if a
+// wait gave up.
+template <int KP, int I>
+__device__ __forceinline__ bool oz_slice(OzCta& t, const int64_t* X, uint32_t rowoff,
+                                         uint32_t kc0, int LS, uint32_t idesc, int tid) {
+  constexpr int KH = KP / 2;
+  constexpr uint32_t ABYTES = (uint32_t)kOzM * KP * 2u;
+  bool ok = true;
+  if (I >= 2) {
+    if (I & 1) {
+      ok = mbar_wait_bounded(&t.mbar[1], t.ph1, kOzWait);
+      t.ph1 ^= 1u;
+    } else {
+      ok = mbar_wait_bounded(&t.mbar[0], t.ph0, kOzWait);
+      t.ph0 ^= 1u;
+    }
+  }
+  unsigned char* Ab = t.As + (I & 1) * ABYTES;
+#pragma unroll
+  for (int c8 = 0; c8 < KH / 8; ++c8) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      w[q] = oz_digit_bf16<I>(X[c8 * 8 + 2 * q]) | (oz_digit_bf16<I>(X[c8 * 8 + 2 * q + 1]) << 16);
+    *reinterpret_cast<uint4*>(Ab + rowoff + (kc0 + (uint32_t)c8) * 128u) =
+        make_uint4(w[0], w[1], w[2], w[3]);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  if (__syncthreads_or(ok ? 0 : 1)) return false;
+  if (tid == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    constexpr int lmax = (kOzDigits - 1) < (kOzLevels - 1 - I) ? (kOzDigits - 1) : (kOzLevels - 1 - I);
+#pragma unroll
+    for (int l = 0; l <= lmax; ++l) {
+      const int L = I + l;
+      // the first slice that reaches level L starts its accumulator
+      const bool first = I == (L - (kOzDigits - 1) > 0 ? L - (kOzDigits - 1) : 0);
+      const uint32_t d = t.tbase + (uint32_t)(L * LS);
+#pragma unroll
+      for (int s = 0; s < KP / 16; ++s)
+        oz_mma(d, t.adesc[I & 1] + 16u * s, t.bdesc[l] + 16u * s, idesc,
+               (first && s == 0) ? 0u : 1u);
+    }
+    oz_commit(&t.mbar[I & 1]);
+  }
+  return true;
+}
+
+template <int KP>
+__global__ void __launch_bounds__(kOzThreads, 1) k_sweep_ozaki(const OzParams p) {
+  constexpr int KH = KP / 2;                         // face points per thread
+  constexpr uint32_t SBO = 16u * KP;                 // bytes between 8-row groups
+  constexpr uint32_t ABYTES = (uint32_t)kOzM * KP * 2u;
+  static_assert(KH % 8 == 0 && KH <= 64, "two threads per element, 16-byte chunks");
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar[3];
+  __shared__ uint32_t tmem_base;
+  __shared__ int emax_sh[kOzThreads];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (kOzM - 1), half = tid >> 7;
+  const uint32_t bbytes = (uint32_t)p.Np * KP * 2u;
+  unsigned char* Bs = sm;                                          // [7][Np x KP]
+  unsigned char* As = sm + kOzDigits * bbytes;                     // [2][128 x KP]
+  int* fidb = reinterpret_cast<int*>(As + 2 * ABYTES);             // [2][F][128] face ids
+  int* row_fg = fidb + 2 * p.F * kOzM;                             // [Np] face << 16 | point
+  int* row_pt = row_fg + p.Np;                                     // [Np] element face point
+  int* row_sc = row_pt + p.Np;                                     // [Np] Fb - 1074
+  double* row_w = reinterpret_cast<double*>(row_sc + p.Np);        // [Np] residual weight
+  double* Gsh = row_w + p.Np;                                       // [Np][128] Gy of the tile
+  double* Osh = Gsh + p.Np * kOzM;                                  // [Np][128] uhat^k, owned rows
+
+  {
+    const uint4* src = p.Bimg;
+    uint4* dstB = reinterpret_cast<uint4*>(Bs);
+    const int n16 = (int)(kOzDigits * bbytes / 16u);
+    for (int i = tid; i < n16; i += kOzThreads) dstB[i] = src[i];
+  }
+  for (int j = tid; j < p.Np; j += kOzThreads) {
+    const int r = j < p.n_rows ? p.rows[j] : 0;
+    const int f = r / p.Nqf, g = r - f * p.Nqf;
+    row_fg[j] = (f << 16) | g;
+    row_pt[j] = r;
+    row_sc[j] = p.Fb[j] - 1074;
+    // one face Jacobian per local face: the mesh is uniform
+    row_w[j] = p.face_jf[p.elem_face[(int64_t)f * p.nel]] * p.fw[g];
+  }
+  if (tid == 0) {
+    for (int b = 0; b < 3; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(p.ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  const int64_t ne = p.nel, nface = p.nface;
+  // face ids of the first tile, and of this thread's faces (f = half,
+  // half + 2, ...) of the second, kept in registers
+  int nfid[3] = {0, 0, 0};
+  {
+    const int64_t e0 = (int64_t)blockIdx.x * kOzM + row;
+    const int64_t e1 = e0 + (int64_t)gridDim.x * kOzM;
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+      if (half + 2 * m < p.F) {
+        if (e0 < ne) fidb[(half + 2 * m) * kOzM + row] = p.elem_face[(int64_t)(half + 2 * m) * ne + e0];
+        if (e1 < ne) nfid[m] = p.elem_face[(int64_t)(half + 2 * m) * ne + e1];
+      }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+
+  OzCta t;
+  t.As = As;
+  t.mbar = mbar;
+  t.tbase = tmem_base;
+  t.ph0 = t.ph1 = 0;
+  t.adesc[0] = umma_desc(smem_u32(As), 128u, SBO);
+  t.adesc[1] = umma_desc(smem_u32(As + ABYTES), 128u, SBO);
+#pragma unroll
+  for (int l = 0; l < kOzDigits; ++l) t.bdesc[l] = umma_desc(smem_u32(Bs + l * bbytes), 128u, SBO);
+
+  const int kk = p.it->k;                                 // read before the last block advances it
+  const int64_t tlen = (int64_t)p.Nqf * nface;
+  const double* src = p.uhat + (int64_t)(kk & 1) * tlen;
+  double* dst = p.uhat + (int64_t)((kk + 1) & 1) * tlen;
+  const int64_t ntiles = (ne + kOzM - 1) / kOzM;
+  const uint32_t rowoff = (uint32_t)(row >> 3) * SBO + (uint32_t)(row & 7) * 16u;
+  const uint32_t kc0 = (uint32_t)(half * KH) / 8u;        // this thread's first 16-byte chunk
+  const int nh = p.Np / 2, nb = half * nh;               // this thread's rows in the epilogue
+  const int kbeg = half * KH;
+  double acc_res = 0.0;
+  bool failed = false;
+
+  // raw bits of this thread's half of an element's traces
+  int64_t X[KH];
+  auto gather = [&](const int* fid, bool live) {
+    int f = kbeg / p.Nqf, g = kbeg - f * p.Nqf;
+#pragma unroll
+    for (int q = 0; q < KH; ++q) {
+      int64_t b = 0;
+      if (live && kbeg + q < p.NQFS) {
+        b = __double_as_longlong(src[(int64_t)g * nface + fid[f * kOzM + row]]);
+        if (++g == p.Nqf) {
+          g = 0;
+          ++f;
+        }
+      }
+      X[q] = b;
+    }
+  };
+  gather(fidb, (int64_t)blockIdx.x * kOzM + row < ne);
+
+  int buf = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+    const int64_t e = tile * kOzM + row;
+    const bool live = e < ne;
+    int* fid = fidb + buf * p.F * kOzM;
+    int* fidn = fidb + (buf ^ 1) * p.F * kOzM;
+    // largest exponent of the element's traces, then the fixed point
+    int emax = 0;
+#pragma unroll
+    for (int q = 0; q < KH; ++q) emax = max(emax, (int)(((uint64_t)X[q] >> 52) & 0x7FF));
+    emax_sh[tid] = emax;
+    __syncthreads();
+    const int E = max(emax_sh[row], emax_sh[row ^ kOzM]);
+    const bool bad = E == 0x7FF;                          // inf or nan among the traces
+#pragma unroll
+    for (int q = 0; q < KH; ++q) X[q] = oz_fixed((uint64_t)X[q], E);
+    // Gy and the current traces of the rows this thread finishes, staged in
+    // shared memory while the digits and the MMAs run
+    for (int n = nb; n < nb + nh; ++n) {
+      const bool valid = live && n < p.n_rows;
+      cp_async8(&Gsh[n * kOzM + row], valid ? p.Gy + (int64_t)n * ne + e : p.Gy, valid ? 8 : 0);
+      const bool own = valid && n < p.n_up;
+      const double* o = src;
+      if (own) {
+        const int fg = row_fg[n];
+        o = src + (int64_t)(fg & 0xFFFF) * nface + fid[(fg >> 16) * kOzM + row];
+      }
+      cp_async8(&Osh[n * kOzM + row], o, own ? 8 : 0);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+
+    // the digit slices and their MMAs
+    if (!oz_slice<KP, 0>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
+        !oz_slice<KP, 1>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
+        !oz_slice<KP, 2>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
+        !oz_slice<KP, 3>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
+        !oz_slice<KP, 4>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
+        !oz_slice<KP, 5>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
+        !oz_slice<KP, 6>(t, X, rowoff, kc0, p.LS, p.idesc, tid)) {
+      failed = true;
+      break;
+    }
+    // the next tile's face ids (its faces of this thread from registers),
+    // visible after the barrier below; prefetch the ones after
+    const int64_t en = e + (int64_t)gridDim.x * kOzM;
+    const int64_t enn = en + (int64_t)gridDim.x * kOzM;
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+      if (half + 2 * m < p.F) {
+        fidn[(half + 2 * m) * kOzM + row] = nfid[m];
+        if (enn < ne) nfid[m] = p.elem_face[(int64_t)(half + 2 * m) * ne + enn];
+      }
+    {  // slices 5 and 6: every MMA of the tile
+      bool ok = mbar_wait_bounded(&mbar[1], t.ph1, kOzWait);
+      t.ph1 ^= 1u;
+      ok = mbar_wait_bounded(&mbar[0], t.ph0, kOzWait) && ok;
+      t.ph0 ^= 1u;
+      if (__syncthreads_or(ok ? 0 : 1)) {
+        failed = true;
+        break;
+      }
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // the next tile's traces are in flight during this epilogue
+    gather(fidn, en < ne);
+    asm volatile("cp.async.wait_all;" ::: "memory");     // this thread's staged rows
+
+    // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its elements) and
+    // the rows of its half, 8 at a time, all levels
+    {
+      const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+      for (int n0 = nb; n0 < nb + nh; n0 += 8) {
+        uint32_t v[kOzLevels][8];
+#pragma unroll
+        for (int L = 0; L < kOzLevels; ++L)
+          tmem_ld8(t.tbase + lanes + (uint32_t)(L * p.LS + n0), v[L]);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!live) continue;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int n = n0 + q;
+          if (n >= p.n_rows) continue;
+          int64_t D[kOzLevels];
+#pragma unroll
+          for (int L = 0; L < kOzLevels; ++L) D[L] = __float2int_rn(__uint_as_float(v[L][q]));
+          // sum_L D_L 2^(7 (6 - L)) = 2^3 (hi 2^25 + lo 2^-10), hi and lo exact
+          const int64_t hi = D[0] * (1ll << 14) + D[1] * (1ll << 7) + D[2];
+          const int64_t lo = D[3] * (1ll << 28) + D[4] * (1ll << 21) + D[5] * (1ll << 14) +
+                             D[6] * (1ll << 7) + D[7];
+          const int64_t T = hi * (1ll << 25) + (lo >> 10);
+          double y = oz_to_double(T, E + row_sc[n]);
+          if (bad) y = __longlong_as_double(0x7FF8000000000000ll);
+          const double vnew = Gsh[n * kOzM + row] + y;
+          if (n < p.n_up) {
+            const int fg = row_fg[n];
+            const int64_t ti = (int64_t)(fg & 0xFFFF) * nface + fid[(fg >> 16) * kOzM + row];
+            const double dd = vnew - Osh[n * kOzM + row];
+            dst[ti] = vnew;
+            acc_res = fma(row_w[n] * dd, dd, acc_res);
+          } else {
+            p.Y[(int64_t)row_pt[n] * ne + e] = vnew;
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  if (failed && tid == 0) {
+    atomicExch(p.err, 1);
+    // drain: a commit tracks every MMA issued before it
+    oz_commit(&mbar[2]);
+    mbar_wait_bounded(&mbar[2], 0u, kOzWait);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t.tbase),
+                 "r"(p.ncols));
+  if (p.final_here) {
+    finish_residual(acc_res, p.partials, blockIdx.x, gridDim.x, p.it, p.hist, p.max_iter, p.tol,
+                    p.res_scale, p.graph_mode, p.handle, gridDim.x);
+  } else {
+    // partial sums only; the tangential-point kernel reduces them with its own
+    acc_res = fsum_warp(acc_res);
+    __shared__ double red2[kOzThreads / 32];
+    if ((tid & 31) == 0) red2[tid >> 5] = acc_res;
+    __syncthreads();
+    if (tid == 0) {
+      double s = 0.0;
+      for (int w = 0; w < kOzThreads / 32; ++w) s += red2[w];
+      p.partials[blockIdx.x] = s;
+    }
+  }
+}
+
+int oz_kp(const Ctx& c) { return (c.NQFS + 15) / 16 * 16; }
+
+size_t oz_smem(const Ctx& c) {
+  const int KP = oz_kp(c), Np = c.oz_Np;
+  return (size_t)kOzDigits * Np * KP * 2 + 2 * (size_t)kOzM * KP * 2 + 2 * sizeof(int) * c.F * kOzM +
+         (size_t)Np * (3 * sizeof(int) + sizeof(double)) + 2 * sizeof(double) * Np * kOzM;
+}
+
+template <int KP>
+cudaError_t oz_prepare(Ctx& c) {
+  const size_t smem = oz_smem(c);
+  cudaError_t err = cudaFuncSetAttribute(k_sweep_ozaki<KP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (err != cudaSuccess) return err;
+  int bpsm = 0;
+  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_sweep_ozaki<KP>, kOzThreads, smem);
+  if (err != cudaSuccess) return err;
+  bpsm = std::min(bpsm, 512 / c.oz_ncols);          // TMEM columns per SM
+  if (bpsm < 1) return cudaErrorInvalidConfiguration;
+  const int64_t ntiles = (c.nel + kOzM - 1) / kOzM;
+  c.oz_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bpsm * device_sms(), ntiles));
+  c.oz_smem = smem;
+  return cudaSuccess;
+}
+
+template <int KP>
+cudaError_t oz_launch(const Ctx& c, const OzParams& p) {
+  k_sweep_ozaki<KP><<<c.oz_grid, kOzThreads, c.oz_smem, c.stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool ozaki_supported(const Ctx& c) {
+  const int KP = oz_kp(c);
+  const int Np = std::max(16, (c.n_rows + 15) / 16 * 16);
+  const int LS = (Np + 31) / 32 * 32;
+  return c.pde == EHDG_TRANSPORT && c.shared_op && c.n_rows >= 1 &&
+         (KP == 16 || KP == 32 || KP == 64 || KP == 96) && kOzLevels * LS <= 512;
+}
+
+cudaError_t build_ozaki_operator(Ctx& c) {
+  if (!ozaki_supported(c)) return cudaErrorInvalidValue;
+  const int KP = oz_kp(c);
+  c.oz_Np = std::max(16, (c.n_rows + 15) / 16 * 16);
+  c.oz_LS = (c.oz_Np + 31) / 32 * 32;
+  int ncols = 32;
+  while (ncols < kOzLevels * c.oz_LS) ncols *= 2;
+  c.oz_ncols = ncols;
+  const size_t img = (size_t)kOzDigits * c.oz_Np * KP * 2;
+  cudaError_t err;
+  if ((err = dalloc_raw(c, &c.oz_img, img)) != cudaSuccess) return err;
+  if ((err = dalloc_raw(c, (void**)&c.oz_Fb, sizeof(int) * c.oz_Np)) != cudaSuccess) return err;
+  k_oz_split_rows<<<c.oz_Np, 32, 0, c.stream>>>(c.Hy, c.rows, c.n_rows, c.NQFS, c.oz_Np, KP,
+                                                 (unsigned short*)c.oz_img, c.oz_Fb);
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  switch (KP) {
+    case 16: return oz_prepare<16>(c);
+    case 32: return oz_prepare<32>(c);
+    case 64: return oz_prepare<64>(c);
+    default: return oz_prepare<96>(c);
+  }
+}
+
+cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out) {
+  OzParams p;
+  p.nel = c.nel;
+  p.nface = c.nface;
+  p.NQFS = c.NQFS;
+  p.Nqf = c.Nqf;
+  p.F = c.F;
+  p.n_rows = c.n_rows;
+  p.n_up = c.n_up;
+  p.Np = c.oz_Np;
+  p.LS = c.oz_LS;
+  p.ncols = c.oz_ncols;
+  p.idesc = umma_idesc(1u, kOzM, c.oz_Np);
+  p.rows = c.rows;
+  p.elem_face = c.geo.elem_face;
+  p.face_jf = c.geo.face_jf;
+  fill_face_weights(c, p.fw);
+  p.Bimg = reinterpret_cast<const uint4*>(c.oz_img);
+  p.Fb = c.oz_Fb;
+  p.uhat = c.uhat;
+  p.it = c.it;
+  p.Gy = c.Gy;
+  p.Y = c.Y;
+  p.partials = c.partials;
+  p.final_here = c.n_tan == 0 ? 1 : 0;
+  p.tol = c.tol;
+  p.res_scale = c.res_scale;
+  p.max_iter = c.max_iter;
+  p.hist = c.hist;
+  p.graph_mode = graph_mode;
+  p.handle = c.handle;
+  p.err = c.tc_err;
+  *grid_out = c.oz_grid;
+  switch (oz_kp(c)) {
+    case 16: return oz_launch<16>(c, p);
+    case 32: return oz_launch<32>(c, p);
+    case 64: return oz_launch<64>(c, p);
+    default: return oz_launch<96>(c, p);
+  }
+}
+
+}  // namespace ehdg

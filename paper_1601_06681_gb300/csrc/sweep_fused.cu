@@ -301,7 +301,9 @@ cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
   const int64_t ntiles = (c.nel + 31) / 32;
   int grid = 1;
   cudaError_t err;
-  if (c.Hyt) {
+  if (c.use_ozaki) {
+    err = launch_sweep_ozaki(c, graph_mode, &grid);
+  } else if (c.Hyt) {
     err = launch_sweep_tiled(c, graph_mode, &grid);
   } else switch (c.NQFS) {
     case 8: err = launch_fused_t<8>(p, smem, ntiles, c.stream, &grid); break;

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include "ehdg_internal.h"
+#include "umma.cuh"
 
 namespace ehdg {
 
@@ -22,25 +23,6 @@ namespace {
 constexpr int kTcM = 128;
 constexpr int kTcThreads = 256;                // two threads per element (tile row)
 constexpr uint32_t kWaitLimit = 1u << 24;   // mbarrier polls before giving up
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;                    // descriptor version of sm_100-family MMA
-  return d;                                  // base offset 0, no swizzle
-}
-
-// byte offset of element (row, k) in the K-major no-swizzle layout
-__device__ __forceinline__ uint32_t kmajor_off(int row, int kbyte, uint32_t sbo) {
-  return (uint32_t)(row >> 3) * sbo + (uint32_t)(kbyte >> 4) * 128u + (uint32_t)(row & 7) * 16u +
-         (uint32_t)(kbyte & 15);
-}
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
@@ -120,12 +102,12 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
     store_elem(Bs, n, k, esize, sbo, v, p.bf16);
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_addr(&tmem_base)),
+                     smem_u32(&tmem_base)),
                  "r"(p.ncols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
@@ -183,7 +165,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_addr(As), b0 = smem_addr(Bs);
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
       const int ksteps = (int)(kbytes / 32u);
       for (int s = 0; s < ksteps; ++s) {
         const uint64_t ad = umma_desc(a0 + 256u * s, 128u, sbo);
@@ -203,7 +185,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
       }
       asm volatile(
           "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_addr(&mbar)));
+              smem_u32(&mbar)));
     }
     // bounded wait for the MMAs: one thread polls the mbarrier, the others
     // wait at the block barrier (no issue slots burnt while the MMA runs)
@@ -215,7 +197,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
             "{\n .reg .pred w;\n mbarrier.try_wait.parity.shared::cta.b64 w, [%1], %2;\n"
             " selp.u32 %0, 1, 0, w;\n}\n"
             : "=r"(ok)
-            : "r"(smem_addr(&mbar)), "r"(phase)
+            : "r"(smem_u32(&mbar)), "r"(phase)
             : "memory");
         if (ok) break;
       }
@@ -300,10 +282,8 @@ cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
   int ncols = 32;
   while (ncols < p.Np) ncols *= 2;
   p.ncols = ncols;
-  // instruction descriptor: D f32, A/B format, K-major A and B, N>>3, M>>4
   const uint32_t fmt = p.bf16 ? 1u : 2u;            // BF16 (kind::f16) or TF32
-  p.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(p.Np >> 3) << 17) |
-            ((uint32_t)(kTcM >> 4) << 24);
+  p.idesc = umma_idesc(fmt, kTcM, p.Np);
   p.rows = c.rows;
   p.elem_face = c.geo.elem_face;
   p.Hy32 = c.Hy32;

@@ -16,8 +16,6 @@
 
 namespace ehdg {
 
-namespace {
-
 // device allocation recorded in the context (freed by ehdg_destroy)
 cudaError_t dalloc_raw(Ctx& c, void** p, size_t bytes) {
   *p = nullptr;
@@ -27,6 +25,8 @@ cudaError_t dalloc_raw(Ctx& c, void** p, size_t bytes) {
   c.bytes += (int64_t)bytes;
   return cudaSuccess;
 }
+
+namespace {
 
 // One correction sweep per launch (mixed form, per-element operators).
 template <int F, int NQF, class T>

@@ -20,7 +20,7 @@ STATUS = {0: "OK", 1: "INVALID", 2: "OOM", 3: "CUDA", 4: "NOT_CONVERGED", 5: "DI
           6: "TIMEOUT", 7: "UNSUPPORTED"}
 PDE = {"transport": 0, "sw": 1}
 SCHEME = {"be": 0, "cn": 1, "steady": 2}
-PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3}
+PRECISION = {"fp64": 0, "tf32": 1, "bf16": 2, "fp32": 3, "fp64_emulated": 4}
 FACE_INTERIOR, FACE_DIRICHLET, FACE_WALL = 0, 1, 2
 
 

@@ -126,3 +126,82 @@ def test_full_size_sampled_elements_match_oracle(full_run, k):
         assert err_u < 1e-12, (ci, cj, err_u)
         assert err_t < 1e-12, (ci, cj, err_t)
     assert worst < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# 3D transport at its benchmark size: 64^3 hexahedra, p = 3, one operator
+# shared by all elements, backward Euler. The native FP64 sweep and the
+# FP64-accurate tensor-core sweep (Ozaki splitting) against the oracle on
+# patches of (2k + 3)^3 elements.
+# ---------------------------------------------------------------------------
+
+N3 = 64
+P3 = 3
+SAMPLES3 = [(0, 0, 0), (N3 - 1, N3 - 1, N3 - 1), (0, N3 - 1, 31), (31, 32, 33), (N3 - 1, 0, 10),
+            (5, 60, N3 - 1), (40, 2, 17)]
+
+
+@pytest.fixture(scope="module")
+def full_run_3d(ehdg):
+    wl = W.transport_3d(n=(N3, N3, N3), p=P3)
+    mesh = W.structured_mesh((N3, N3, N3))
+    u0 = wl.initial(node_coords(mesh, P3))
+    out = {}
+    for prec in ("fp64", "fp64_emulated"):
+        with ehdg.Solver(mesh, P3, scheme="be", dt=wl.dt, tol=wl.tol, max_iter=100,
+                         beta_const=wl.beta_const, precision=prec) as s:
+            g = wl.boundary(s.face_point_coords(), wl.dt)
+            for k in (1, 2):
+                s.set_boundary(g)
+                s.set_state(u0)
+                s.step_fixed(k)
+                out[prec, k] = s.get_state()
+    return wl, mesh, u0, out
+
+
+def patch_solve_3d(wl, mesh, u0, c, k):
+    """Oracle state and traces of element c = (ci, cj, ck) of the N3^3 mesh
+    after k iterations of one backward-Euler step, from a patch of radius
+    k + 1 around it (true inflow data on the domain's faces, zero elsewhere)."""
+    r = k + 1
+    lo = [max(v - r, 0) for v in c]
+    hi = [min(v + r, N3 - 1) for v in c]
+    n = [hi[a] - lo[a] + 1 for a in range(3)]
+    h = 1.0 / N3
+    pm = W.structured_mesh(tuple(n), lo=tuple(v * h for v in lo),
+                           hi=tuple((v + 1) * h for v in hi))
+    prob = Problem(pm, P3, scheme="be", dt=wl.dt, beta_const=wl.beta_const)
+    ii, jj, kk = np.meshgrid(np.arange(lo[0], hi[0] + 1), np.arange(lo[1], hi[1] + 1),
+                             np.arange(lo[2], hi[2] + 1), indexing="ij")
+    # patch element ids run x fastest, like the full mesh's
+    full_ids = ((kk * N3 + jj) * N3 + ii).transpose(2, 1, 0).reshape(-1)
+    up = u0.reshape(N3 ** 3, 1, -1)[full_ids]
+    XFp = face_point_coords(pm, P3, prob.ref.q)
+    gp = np.zeros((pm["n_face"], prob.Nqf))
+    true_g = wl.boundary(XFp, wl.dt)
+    for f in range(pm["n_face"]):
+        if pm["face_elem"][f, 1] >= 0:
+            continue
+        x = XFp[f].mean(axis=0)
+        if min(x.min(), (1.0 - x).min()) < 0.25 * h:
+            gp[f] = true_g[f]
+    u, uh, _ = prob.solve_step(up, prob.trace(up, gp), gp, fixed_iters=k)
+    ep = ((c[2] - lo[2]) * n[1] + (c[1] - lo[1])) * n[0] + (c[0] - lo[0])
+    return u[ep], uh[pm["elem_face"][ep]]
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["fp64", "fp64_emulated"])
+@pytest.mark.parametrize("k", [1, 2])
+def test_full_size_3d_sampled_elements_match_oracle(full_run_3d, prec, k):
+    wl, mesh, u0, out = full_run_3d
+    u_gpu, uh_gpu = out[prec, k]
+    for c in SAMPLES3:
+        u_or, uh_or = patch_solve_3d(wl, mesh, u0, c, k)
+        e = (c[2] * N3 + c[1]) * N3 + c[0]
+        ug = u_gpu.reshape(N3 ** 3, 1, -1)[e]
+        uhg = uh_gpu[mesh["elem_face"][e]]
+        err_u = np.linalg.norm(ug - u_or) / max(np.linalg.norm(u_or), 1e-3)
+        err_t = np.linalg.norm(uhg - uh_or) / max(np.linalg.norm(uh_or), 1e-3)
+        assert err_u < 1e-12, (c, err_u)
+        assert err_t < 1e-12, (c, err_t)

@@ -89,6 +89,14 @@ def make_case(name):
     elif name == "3d_be_const_p3":
         mesh, p = W.structured_mesh((5, 3, 4)), 3
         kw = dict(scheme="be", dt=5e-3, beta_const=np.array([0.3, -1.0, 0.6]))
+    elif name == "3d_be_const_p3_tiles":
+        # 360 elements: two full 128-element tiles and a ragged third
+        mesh, p = W.structured_mesh((9, 8, 5)), 3
+        kw = dict(scheme="be", dt=5e-3, beta_const=np.array([1.0, 1.0, 1.0]) / np.sqrt(3.0))
+    elif name == "3d_be_tangent_p2":
+        # beta.n = 0 on the y and z faces: tangential rows beside the upwind ones
+        mesh, p = W.structured_mesh((7, 5, 4)), 2
+        kw = dict(scheme="be", dt=0.02, beta_const=np.array([0.7, 0.0, 0.0]))
     elif name == "sw_be":
         mesh, p = W.structured_mesh((12, 11), boundary_tag=W.TAG_WALL), 2
         kw = dict(pde="sw", scheme="be", dt=2e-3, Phi=1.3)
@@ -410,3 +418,81 @@ def test_autotuner_keeps_state_and_results(ehdg, tmp_path):
         assert again == best
     ou, _, _, _ = prob.run(u0, 2, g_of_t=lambda t: g, tol=1e-13, max_iter=2000)
     assert rel(u, ou) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# FP64-accurate sweeps on the BF16 tensor cores (Ozaki splitting): same
+# tolerances as the FP64 path
+# ---------------------------------------------------------------------------
+
+OZAKI_CASES = ["2d_be_const", "2d_be_zero_component", "3d_be_const", "3d_be_const_p3",
+               "3d_be_const_p3_tiles", "3d_be_tangent_p2"]
+
+
+@pytest.mark.parametrize("name", OZAKI_CASES)
+@pytest.mark.parametrize("n_iter", [1, 4])
+def test_fp64_emulated_fixed_iterations_match_oracle(ehdg, name, n_iter):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    with ehdg.Solver(mesh, p, tol=1e-10, max_iter=400, precision="fp64_emulated", **kw) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        s.step_fixed(n_iter)
+        u, uh = s.get_state()
+        hist = s.residual_history()
+    ou, ouh, ohist = prob.solve_step(u0, prob.trace(u0, g), g_new=g, fixed_iters=n_iter)
+    assert rel(u, ou) < RTOL
+    assert rel(uh, ouh) < RTOL
+    assert len(hist) == n_iter
+    assert np.allclose(hist, ohist, rtol=1e-10, atol=1e-300)
+
+
+@pytest.mark.parametrize("name", OZAKI_CASES)
+def test_fp64_emulated_steps_to_tolerance_match_oracle(ehdg, name):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    n_steps = 3
+    with ehdg.Solver(mesh, p, tol=1e-10, max_iter=400, precision="fp64_emulated", **kw) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        iters = s.run(n_steps)
+        u, uh = s.get_state()
+    ou, ouh, oiters, _ = prob.run(u0, n_steps, g_of_t=lambda t: g, tol=1e-10)
+    assert iters == oiters
+    assert rel(u, ou) < RTOL
+    assert rel(uh, ouh) < RTOL
+
+
+def test_fp64_emulated_converged_step_equals_direct_hdg_solve(ehdg):
+    mesh, p, kw, prob, u0, g = make_case("3d_be_const")
+    with ehdg.Solver(mesh, p, tol=1e-13, max_iter=2000, precision="fp64_emulated", **kw) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        s.step()
+        u, uh = s.get_state()
+    ud, uhd = direct.solve(prob, u0, None, g=g)
+    assert rel(u, ud) < 1e-11
+    assert rel(uh, uhd) < 1e-11
+
+
+def test_fp64_emulated_nan_input_reports_divergence(ehdg):
+    mesh, p, kw, prob, u0, g = make_case("3d_be_const")
+    bad = u0.copy()
+    bad[7, 0, 2] = np.nan
+    with ehdg.Solver(mesh, p, tol=1e-10, max_iter=400, precision="fp64_emulated", **kw) as s:
+        s.set_boundary(g)
+        s.set_state(bad)
+        it, res, st = s.step(check=False)
+        assert st == 5 and it == 1
+
+
+def test_fp64_emulated_rejects_unsupported_problems(ehdg):
+    # per-element operators, shallow water, and more than 64 sweep rows
+    for name in ("2d_cn_variable", "sw_be"):
+        mesh, p, kw, prob, u0, g = make_case(name)
+        with pytest.raises(ehdg.EhdgError) as ei:
+            ehdg.Solver(mesh, p, precision="fp64_emulated", **kw)
+        assert ei.value.status == 7
+    mesh = W.structured_mesh((3, 3, 3))
+    with pytest.raises(ehdg.EhdgError) as ei:
+        ehdg.Solver(mesh, 3, scheme="be", dt=0.01, beta_const=[1.0, 0.0, 0.0],
+                    precision="fp64_emulated")
+    assert ei.value.status == 7
