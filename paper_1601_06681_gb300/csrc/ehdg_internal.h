@@ -136,7 +136,7 @@ struct Ctx {
   void* oz_img = nullptr;        // [7][Np x KP] BF16 digit slices of the sweep rows
   int* oz_Fb = nullptr;          // [Np] largest biased exponent of each sweep row
   int oz_Np = 0, oz_LS = 0, oz_ncols = 0;   // padded rows, TMEM columns per level, allocated
-  int oz_grid = 0;
+  int oz_grid = 0, oz_threads = 0;
   size_t oz_smem = 0;
   int inner_sweeps = 0;
   float* Hy32 = nullptr;         // FP32 copy of Hy in the sweep's slot layout

@@ -28,12 +28,17 @@
 // magnitude per operand; the dropped levels L >= 8 cost below 2^-51 of
 // max|uhat_e| max|Hy_n| per product.
 //
-// Shared-memory operands use the K-major layout without swizzle. B (the
-// seven digit slices of the sweep rows) stays resident; A (one digit slice
-// of the tile's 128 elements) is double-buffered so that the digits of slice
-// i + 1 are written while the MMAs of slice i run. One thread issues the MMAs
-// and commits each slice to an mbarrier; every wait is bounded and records an
-// error instead of hanging.
+// Shared-memory operands use the K-major layout without swizzle. B holds the
+// seven digit slices of the sweep rows stacked along N, LS rows each (the
+// rows padded to a multiple of 32, zero beyond the sweep rows), and stays
+// resident; level L's accumulator sits at TMEM column L * LS. So one MMA of
+// A slice i against B slices l0 .. l0 + nl - 1 (N = nl * LS <= 256) feeds
+// levels i + l0 .. i + l0 + nl - 1 at once, and each A slice is read from
+// shared memory two or three times instead of seven. A (one digit slice of
+// the tile's 128 elements) is double-buffered so that the digits of slice
+// i + 1 are written while the MMAs of slice i run. One thread issues the
+// MMAs and commits each slice to an mbarrier; every wait is bounded and
+// records an error instead of hanging.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -48,7 +53,6 @@ namespace ehdg {
 namespace {
 
 constexpr int kOzM = 128;                  // elements per tile (TMEM lanes)
-constexpr int kOzThreads = 256;            // two threads per element
 constexpr int kOzDigits = 7;               // 7-bit digits per operand: 49-bit fixed point
 constexpr int kOzLevels = 8;               // digit-product levels kept, L = i + l <= 7
 constexpr uint32_t kOzWait = 1u << 24;     // mbarrier polls before giving up
@@ -57,13 +61,12 @@ struct OzParams {
   int64_t nel, nface;
   int NQFS, Nqf, F, n_rows, n_up;
   int Np, LS, ncols;            // rows padded to 16, TMEM columns per level, allocated columns
-  uint32_t idesc;
   const int* rows;              // sweep rows (face points), upwind first
   const int32_t* elem_face;     // [F][nel]
   const double* face_jf;        // [nface]
   double fw[kMaxQ * kMaxQ];
-  const uint4* Bimg;            // [kOzDigits][Np x KP] BF16 digits, K-major image
-  const int* Fb;                // [Np] largest biased exponent of each row
+  const uint4* Bimg;            // [kOzDigits * LS x KP] BF16 digits, K-major image
+  const int* Fb;                // [LS] largest biased exponent of each row
   double* uhat;                 // [2][Nqf][nface]
   IterState* it;
   const double* Gy;             // [row][nel]
@@ -122,13 +125,6 @@ __device__ __forceinline__ double oz_to_double(int64_t T, int sc) {
       (long long)((s << 63) | ((uint64_t)be << 52) | (m & 0xFFFFFFFFFFFFFull)));
 }
 
-// 8-byte asynchronous copy global -> shared; n = 0 fills zeros without reading
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, int n) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(smem_u32(dst)), "l"(src),
-               "r"(n)
-               : "memory");
-}
-
 __device__ __forceinline__ void oz_mma(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc,
                                        uint32_t acc) {
   asm volatile(
@@ -144,15 +140,16 @@ __device__ __forceinline__ void oz_commit(uint64_t* bar) {
 }
 
 // Setup: digit slices and row exponents of the shared operator's sweep rows,
-// one warp per padded row.
+// one warp per padded row n < LS; digit l of row n is row l * LS + n of the
+// stacked K-major image.
 template <int I>
-__device__ __forceinline__ void oz_put_digit(unsigned short* img, int Np, int KP, int n, int j,
+__device__ __forceinline__ void oz_put_digit(unsigned short* img, int LS, int KP, int n, int j,
                                              int64_t Yv) {
-  const size_t off = (size_t)I * Np * KP * 2 + kmajor_off(n, 2 * j, 16u * (uint32_t)KP);
+  const size_t off = kmajor_off(I * LS + n, 2 * j, 16u * (uint32_t)KP);
   img[off / 2] = (unsigned short)oz_digit_bf16<I>(Yv);
 }
 
-__global__ void k_oz_split_rows(const double* Hy, const int* rows, int n_rows, int NQFS, int Np,
+__global__ void k_oz_split_rows(const double* Hy, const int* rows, int n_rows, int NQFS, int LS,
                                 int KP, unsigned short* img, int* Fb) {
   const int n = blockIdx.x, lane = threadIdx.x;
   int emax = 0;
@@ -168,44 +165,44 @@ __global__ void k_oz_split_rows(const double* Hy, const int* rows, int n_rows, i
     if (n < n_rows && j < NQFS)
       bits = (uint64_t)__double_as_longlong(Hy[(int64_t)rows[n] * NQFS + j]);
     const int64_t Yv = oz_fixed(bits, emax);
-    oz_put_digit<0>(img, Np, KP, n, j, Yv);
-    oz_put_digit<1>(img, Np, KP, n, j, Yv);
-    oz_put_digit<2>(img, Np, KP, n, j, Yv);
-    oz_put_digit<3>(img, Np, KP, n, j, Yv);
-    oz_put_digit<4>(img, Np, KP, n, j, Yv);
-    oz_put_digit<5>(img, Np, KP, n, j, Yv);
-    oz_put_digit<6>(img, Np, KP, n, j, Yv);
+    oz_put_digit<0>(img, LS, KP, n, j, Yv);
+    oz_put_digit<1>(img, LS, KP, n, j, Yv);
+    oz_put_digit<2>(img, LS, KP, n, j, Yv);
+    oz_put_digit<3>(img, LS, KP, n, j, Yv);
+    oz_put_digit<4>(img, LS, KP, n, j, Yv);
+    oz_put_digit<5>(img, LS, KP, n, j, Yv);
+    oz_put_digit<6>(img, LS, KP, n, j, Yv);
   }
 }
 
 // Per-CTA state of the sweep kernel that the slice steps share.
 struct OzCta {
   unsigned char* As;            // [2][128 x KP] A digit buffers
-  uint64_t* mbar;               // [3]
+  uint64_t* empty;              // [2] MMAs of the buffer's slice done (tcgen05.commit)
+  uint64_t* full;               // [2] every thread's digits of the buffer's slice written
   uint64_t adesc[2];            // descriptors of the two A buffers (K step 0)
-  uint64_t bdesc[kOzDigits];    // descriptors of the B digit slices (K step 0)
+  uint64_t bdesc;               // descriptor of the stacked B slices (K step 0, slice 0)
+  uint32_t bslice;              // descriptor address units (16 B) of one B slice
   uint32_t tbase;
-  uint32_t ph0, ph1;            // phases of mbar[0] and mbar[1]
+  uint32_t idesc_n0;            // instruction descriptor without its N field
+  uint32_t ph_empty[2], ph_full[2];
+  bool ok;                      // every bounded wait of this thread succeeded
 };
 
-// Digit slice I of the tile: wait until its buffer's previous slice (I - 2)
-// is consumed, write this thread's digits, then one thread issues the MMAs of
-// every level I + l <= 7 and commits them. Returns false (block-uniform) if a
-// wait gave up.
-template <int KP, int I>
-__device__ __forceinline__ bool oz_slice(OzCta& t, const int64_t* X, uint32_t rowoff,
-                                         uint32_t kc0, int LS, uint32_t idesc, int tid) {
-  constexpr int KH = KP / 2;
+// Digit slice I of the tile. A thread waits until the buffer's previous slice
+// (I - 2) has been consumed by the tensor cores, writes its digits and
+// arrives on the buffer's "full" barrier; thread 0 then waits for every
+// thread's digits and issues the MMAs of every level I + l <= 7, committed to
+// the buffer's "empty" barrier. No block-wide barrier: writers run up to one
+// slice ahead of the tensor cores.
+template <int KP, int TPE, int I>
+__device__ __forceinline__ void oz_slice(OzCta& t, const int64_t* X, uint32_t rowoff, uint32_t kc0,
+                                         int LS, int tid) {
+  constexpr int KH = KP / TPE;
   constexpr uint32_t ABYTES = (uint32_t)kOzM * KP * 2u;
-  bool ok = true;
   if (I >= 2) {
-    if (I & 1) {
-      ok = mbar_wait_bounded(&t.mbar[1], t.ph1, kOzWait);
-      t.ph1 ^= 1u;
-    } else {
-      ok = mbar_wait_bounded(&t.mbar[0], t.ph0, kOzWait);
-      t.ph0 ^= 1u;
-    }
+    t.ok = mbar_wait_bounded(&t.empty[I & 1], t.ph_empty[I & 1], kOzWait) && t.ok;
+    t.ph_empty[I & 1] ^= 1u;
   }
   unsigned char* Ab = t.As + (I & 1) * ABYTES;
 #pragma unroll
@@ -218,56 +215,120 @@ __device__ __forceinline__ bool oz_slice(OzCta& t, const int64_t* X, uint32_t ro
         make_uint4(w[0], w[1], w[2], w[3]);
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (__syncthreads_or(ok ? 0 : 1)) return false;
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&t.full[I & 1]))
+               : "memory");
   if (tid == 0) {
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    constexpr int lmax = (kOzDigits - 1) < (kOzLevels - 1 - I) ? (kOzDigits - 1) : (kOzLevels - 1 - I);
+    const bool got = mbar_wait_bounded(&t.full[I & 1], t.ph_full[I & 1], kOzWait);
+    t.ph_full[I & 1] ^= 1u;
+    t.ok = got && t.ok;
+    if (got) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      // groups (first B slice, slices) of levels I .. 7, each N = slices * LS
+      // <= 256; a group whose levels start their accumulators here (slice 0,
+      // and level 7 at slice 1) holds no level that is already accumulating
+      constexpr int ng = I == 1 ? 3 : (I <= 3 ? 2 : 1);
+      constexpr int g0[3] = {0, 4, I == 1 ? 6 : 0};
+      constexpr int gn[3] = {I <= 3 ? 4 : (I == 4 ? 4 : (I == 5 ? 3 : 2)),
+                             I == 0 ? 3 : (I == 1 ? 2 : (I == 2 ? 2 : 1)), 1};
 #pragma unroll
-    for (int l = 0; l <= lmax; ++l) {
-      const int L = I + l;
-      // the first slice that reaches level L starts its accumulator
-      const bool first = I == (L - (kOzDigits - 1) > 0 ? L - (kOzDigits - 1) : 0);
-      const uint32_t d = t.tbase + (uint32_t)(L * LS);
+      for (int gi = 0; gi < ng; ++gi) {
+        const bool first = I == 0 || (I == 1 && gi == 2);
+        const uint32_t d = t.tbase + (uint32_t)((I + g0[gi]) * LS);
+        const uint32_t idesc = t.idesc_n0 | ((uint32_t)((gn[gi] * LS) >> 3) << 17);
+        const uint64_t b0 = t.bdesc + (uint64_t)(g0[gi] * t.bslice);
 #pragma unroll
-      for (int s = 0; s < KP / 16; ++s)
-        oz_mma(d, t.adesc[I & 1] + 16u * s, t.bdesc[l] + 16u * s, idesc,
-               (first && s == 0) ? 0u : 1u);
+        for (int s = 0; s < KP / 16; ++s)
+          oz_mma(d, t.adesc[I & 1] + 16u * s, b0 + 16u * s, idesc, (first && s == 0) ? 0u : 1u);
+      }
     }
-    oz_commit(&t.mbar[I & 1]);
+    // committed even without MMAs, so that no waiter is left hanging
+    oz_commit(&t.empty[I & 1]);
   }
-  return true;
 }
 
-template <int KP>
-__global__ void __launch_bounds__(kOzThreads, 1) k_sweep_ozaki(const OzParams p) {
-  constexpr int KH = KP / 2;                         // face points per thread
+// This thread's KH traces of element e (raw FP64 bits); part PART of the
+// element's face points when the face-point count NQF is known at compile
+// time, so that every face and point index is a constant.
+template <int KP, int NQF, int TPE, int PART>
+__device__ __forceinline__ void oz_gather_part(int64_t* X, const double* src, const int* fid,
+                                               int row, int64_t nface, int NQFS, bool live) {
+  constexpr int KH = KP / TPE;
+#pragma unroll
+  for (int q = 0; q < KH; ++q) {
+    const int k = PART * KH + q;
+    const int f = k / NQF, g = k - f * NQF;
+    X[q] = (live && k < NQFS)
+               ? __double_as_longlong(src[(int64_t)g * nface + fid[f * kOzM + row]])
+               : 0;
+  }
+}
+
+template <int KP, int NQF, int TPE>
+__device__ __forceinline__ void oz_gather(int64_t* X, const double* src, const int* fid, int row,
+                                          int part, int64_t nface, int NQFS, int Nqf, bool live) {
+  constexpr int KH = KP / TPE;
+  if constexpr (NQF > 0) {
+    if (part == 0) oz_gather_part<KP, NQF, TPE, 0>(X, src, fid, row, nface, NQFS, live);
+    if constexpr (TPE > 1)
+      if (part == 1) oz_gather_part<KP, NQF, TPE, 1>(X, src, fid, row, nface, NQFS, live);
+    if constexpr (TPE > 2) {
+      if (part == 2) oz_gather_part<KP, NQF, TPE, 2>(X, src, fid, row, nface, NQFS, live);
+      if (part == 3) oz_gather_part<KP, NQF, TPE, 3>(X, src, fid, row, nface, NQFS, live);
+    }
+  } else {
+    const int kbeg = part * KH;
+    int f = kbeg / Nqf, g = kbeg - f * Nqf;
+#pragma unroll
+    for (int q = 0; q < KH; ++q) {
+      int64_t b = 0;
+      if (live && kbeg + q < NQFS) {
+        b = __double_as_longlong(src[(int64_t)g * nface + fid[f * kOzM + row]]);
+        if (++g == Nqf) {
+          g = 0;
+          ++f;
+        }
+      }
+      X[q] = b;
+    }
+  }
+}
+
+// KP: face points padded to 16; NQF: face points per face (0 = runtime);
+// TPE: threads per element (2 or 4), each with KP / TPE face points and
+// Np / TPE rows.
+template <int KP, int NQF, int TPE>
+__global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p) {
+  constexpr int NT = kOzM * TPE;
+  constexpr int KH = KP / TPE;                       // face points per thread
+  constexpr int NFID = (6 + TPE - 1) / TPE;          // faces per thread (at most 6 faces)
   constexpr uint32_t SBO = 16u * KP;                 // bytes between 8-row groups
   constexpr uint32_t ABYTES = (uint32_t)kOzM * KP * 2u;
-  static_assert(KH % 8 == 0 && KH <= 64, "two threads per element, 16-byte chunks");
+  static_assert(KH % 8 == 0, "16-byte digit chunks per thread");
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t mbar[3];
+  __shared__ __align__(8) uint64_t bars[5];          // empty[2], full[2], drain
   __shared__ uint32_t tmem_base;
-  __shared__ int emax_sh[kOzThreads];
+  __shared__ int emax_sh[NT];
   const int tid = threadIdx.x, warp = tid >> 5;
-  const int row = tid & (kOzM - 1), half = tid >> 7;
-  const uint32_t bbytes = (uint32_t)p.Np * KP * 2u;
-  unsigned char* Bs = sm;                                          // [7][Np x KP]
+  const int row = tid & (kOzM - 1), part = tid >> 7;
+  const uint32_t bbytes = (uint32_t)p.LS * KP * 2u;                // one B slice
+  unsigned char* Bs = sm;                                          // [7 * LS x KP]
   unsigned char* As = sm + kOzDigits * bbytes;                     // [2][128 x KP]
   int* fidb = reinterpret_cast<int*>(As + 2 * ABYTES);             // [2][F][128] face ids
   int* row_fg = fidb + 2 * p.F * kOzM;                             // [Np] face << 16 | point
   int* row_pt = row_fg + p.Np;                                     // [Np] element face point
   int* row_sc = row_pt + p.Np;                                     // [Np] Fb - 1074
-  double* row_w = reinterpret_cast<double*>(row_sc + p.Np);        // [Np] residual weight
-  double* Gsh = row_w + p.Np;                                       // [Np][128] Gy of the tile
-  double* Osh = Gsh + p.Np * kOzM;                                  // [Np][128] uhat^k, owned rows
+  int* kslot = row_sc + p.Np;                                      // [KP] owned row of a point
+  double* row_w = reinterpret_cast<double*>(kslot + KP);           // [Np] residual weight
+  double* Osh = row_w + p.Np;                                       // [Np][128] uhat^k, owned rows
 
   {
     const uint4* src = p.Bimg;
     uint4* dstB = reinterpret_cast<uint4*>(Bs);
     const int n16 = (int)(kOzDigits * bbytes / 16u);
-    for (int i = tid; i < n16; i += kOzThreads) dstB[i] = src[i];
+    for (int i = tid; i < n16; i += NT) dstB[i] = src[i];
   }
-  for (int j = tid; j < p.Np; j += kOzThreads) {
+  for (int k = tid; k < KP; k += NT) kslot[k] = -1;
+  for (int j = tid; j < p.Np; j += NT) {
     const int r = j < p.n_rows ? p.rows[j] : 0;
     const int f = r / p.Nqf, g = r - f * p.Nqf;
     row_fg[j] = (f << 16) | g;
@@ -277,8 +338,10 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_sweep_ozaki(const OzParams p)
     row_w[j] = p.face_jf[p.elem_face[(int64_t)f * p.nel]] * p.fw[g];
   }
   if (tid == 0) {
-    for (int b = 0; b < 3; ++b)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[b])));
+    for (int b = 0; b < 5; ++b) {
+      const uint32_t cnt = (b == 2 || b == 3) ? (uint32_t)NT : 1u;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[b])), "r"(cnt));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   if (warp == 0) {
@@ -288,32 +351,40 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_sweep_ozaki(const OzParams p)
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   const int64_t ne = p.nel, nface = p.nface;
-  // face ids of the first tile, and of this thread's faces (f = half,
-  // half + 2, ...) of the second, kept in registers
-  int nfid[3] = {0, 0, 0};
+  // face ids of the first tile, and of this thread's faces (f = part,
+  // part + TPE, ...) of the second, kept in registers
+  int nfid[NFID];
   {
     const int64_t e0 = (int64_t)blockIdx.x * kOzM + row;
     const int64_t e1 = e0 + (int64_t)gridDim.x * kOzM;
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
-      if (half + 2 * m < p.F) {
-        if (e0 < ne) fidb[(half + 2 * m) * kOzM + row] = p.elem_face[(int64_t)(half + 2 * m) * ne + e0];
-        if (e1 < ne) nfid[m] = p.elem_face[(int64_t)(half + 2 * m) * ne + e1];
+    for (int m = 0; m < NFID; ++m) {
+      nfid[m] = 0;
+      const int f = part + TPE * m;
+      if (f < p.F) {
+        if (e0 < ne) fidb[f * kOzM + row] = p.elem_face[(int64_t)f * ne + e0];
+        if (e1 < ne) nfid[m] = p.elem_face[(int64_t)f * ne + e1];
       }
+    }
   }
+  __syncthreads();
+  for (int n = tid; n < p.n_up; n += NT) kslot[row_pt[n]] = n;
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
 
   OzCta t;
   t.As = As;
-  t.mbar = mbar;
+  t.empty = &bars[0];
+  t.full = &bars[2];
   t.tbase = tmem_base;
-  t.ph0 = t.ph1 = 0;
+  t.ph_empty[0] = t.ph_empty[1] = t.ph_full[0] = t.ph_full[1] = 0;
+  t.ok = true;
   t.adesc[0] = umma_desc(smem_u32(As), 128u, SBO);
   t.adesc[1] = umma_desc(smem_u32(As + ABYTES), 128u, SBO);
-#pragma unroll
-  for (int l = 0; l < kOzDigits; ++l) t.bdesc[l] = umma_desc(smem_u32(Bs + l * bbytes), 128u, SBO);
+  t.bdesc = umma_desc(smem_u32(Bs), 128u, SBO);
+  t.bslice = bbytes >> 4;
+  t.idesc_n0 = umma_idesc(1u, kOzM, 0);
 
   const int kk = p.it->k;                                 // read before the last block advances it
   const int64_t tlen = (int64_t)p.Nqf * nface;
@@ -321,30 +392,15 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_sweep_ozaki(const OzParams p)
   double* dst = p.uhat + (int64_t)((kk + 1) & 1) * tlen;
   const int64_t ntiles = (ne + kOzM - 1) / kOzM;
   const uint32_t rowoff = (uint32_t)(row >> 3) * SBO + (uint32_t)(row & 7) * 16u;
-  const uint32_t kc0 = (uint32_t)(half * KH) / 8u;        // this thread's first 16-byte chunk
-  const int nh = p.Np / 2, nb = half * nh;               // this thread's rows in the epilogue
-  const int kbeg = half * KH;
+  const uint32_t kc0 = (uint32_t)(part * KH) / 8u;        // this thread's first 16-byte chunk
+  const int nh = p.Np / TPE, nb = part * nh;             // this thread's rows in the epilogue
+  const int kbeg = part * KH;
   double acc_res = 0.0;
   bool failed = false;
 
-  // raw bits of this thread's half of an element's traces
-  int64_t X[KH];
-  auto gather = [&](const int* fid, bool live) {
-    int f = kbeg / p.Nqf, g = kbeg - f * p.Nqf;
-#pragma unroll
-    for (int q = 0; q < KH; ++q) {
-      int64_t b = 0;
-      if (live && kbeg + q < p.NQFS) {
-        b = __double_as_longlong(src[(int64_t)g * nface + fid[f * kOzM + row]]);
-        if (++g == p.Nqf) {
-          g = 0;
-          ++f;
-        }
-      }
-      X[q] = b;
-    }
-  };
-  gather(fidb, (int64_t)blockIdx.x * kOzM + row < ne);
+  int64_t X[KH];                                          // this thread's traces of its element
+  oz_gather<KP, NQF, TPE>(X, src, fidb, row, part, nface, p.NQFS, p.Nqf,
+                          (int64_t)blockIdx.x * kOzM + row < ne);
 
   int buf = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
@@ -352,101 +408,99 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_sweep_ozaki(const OzParams p)
     const bool live = e < ne;
     int* fid = fidb + buf * p.F * kOzM;
     int* fidn = fidb + (buf ^ 1) * p.F * kOzM;
-    // largest exponent of the element's traces, then the fixed point
+    // the current traces at the owned points, from the gathered values, and
+    // the largest exponent of the element's traces
     int emax = 0;
 #pragma unroll
-    for (int q = 0; q < KH; ++q) emax = max(emax, (int)(((uint64_t)X[q] >> 52) & 0x7FF));
+    for (int q = 0; q < KH; ++q) {
+      emax = max(emax, (int)(((uint64_t)X[q] >> 52) & 0x7FF));
+      const int slot = kslot[kbeg + q];
+      if (live && slot >= 0) Osh[slot * kOzM + row] = __longlong_as_double(X[q]);
+    }
     emax_sh[tid] = emax;
     __syncthreads();
-    const int E = max(emax_sh[row], emax_sh[row ^ kOzM]);
+    int E = emax_sh[row];
+#pragma unroll
+    for (int m = 1; m < TPE; ++m) E = max(E, emax_sh[row + m * kOzM]);
     const bool bad = E == 0x7FF;                          // inf or nan among the traces
 #pragma unroll
     for (int q = 0; q < KH; ++q) X[q] = oz_fixed((uint64_t)X[q], E);
-    // Gy and the current traces of the rows this thread finishes, staged in
-    // shared memory while the digits and the MMAs run
-    for (int n = nb; n < nb + nh; ++n) {
-      const bool valid = live && n < p.n_rows;
-      cp_async8(&Gsh[n * kOzM + row], valid ? p.Gy + (int64_t)n * ne + e : p.Gy, valid ? 8 : 0);
-      const bool own = valid && n < p.n_up;
-      const double* o = src;
-      if (own) {
-        const int fg = row_fg[n];
-        o = src + (int64_t)(fg & 0xFFFF) * nface + fid[(fg >> 16) * kOzM + row];
-      }
-      cp_async8(&Osh[n * kOzM + row], o, own ? 8 : 0);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
 
     // the digit slices and their MMAs
-    if (!oz_slice<KP, 0>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
-        !oz_slice<KP, 1>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
-        !oz_slice<KP, 2>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
-        !oz_slice<KP, 3>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
-        !oz_slice<KP, 4>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
-        !oz_slice<KP, 5>(t, X, rowoff, kc0, p.LS, p.idesc, tid) ||
-        !oz_slice<KP, 6>(t, X, rowoff, kc0, p.LS, p.idesc, tid)) {
-      failed = true;
-      break;
-    }
+    oz_slice<KP, TPE, 0>(t, X, rowoff, kc0, p.LS, tid);
+    oz_slice<KP, TPE, 1>(t, X, rowoff, kc0, p.LS, tid);
+    oz_slice<KP, TPE, 2>(t, X, rowoff, kc0, p.LS, tid);
+    oz_slice<KP, TPE, 3>(t, X, rowoff, kc0, p.LS, tid);
+    oz_slice<KP, TPE, 4>(t, X, rowoff, kc0, p.LS, tid);
+    oz_slice<KP, TPE, 5>(t, X, rowoff, kc0, p.LS, tid);
+    oz_slice<KP, TPE, 6>(t, X, rowoff, kc0, p.LS, tid);
     // the next tile's face ids (its faces of this thread from registers),
     // visible after the barrier below; prefetch the ones after
     const int64_t en = e + (int64_t)gridDim.x * kOzM;
     const int64_t enn = en + (int64_t)gridDim.x * kOzM;
 #pragma unroll
-    for (int m = 0; m < 3; ++m)
-      if (half + 2 * m < p.F) {
-        fidn[(half + 2 * m) * kOzM + row] = nfid[m];
-        if (enn < ne) nfid[m] = p.elem_face[(int64_t)(half + 2 * m) * ne + enn];
+    for (int m = 0; m < NFID; ++m) {
+      const int f = part + TPE * m;
+      if (f < p.F) {
+        fidn[f * kOzM + row] = nfid[m];
+        if (enn < ne) nfid[m] = p.elem_face[(int64_t)f * ne + enn];
       }
-    {  // slices 5 and 6: every MMA of the tile
-      bool ok = mbar_wait_bounded(&mbar[1], t.ph1, kOzWait);
-      t.ph1 ^= 1u;
-      ok = mbar_wait_bounded(&mbar[0], t.ph0, kOzWait) && ok;
-      t.ph0 ^= 1u;
-      if (__syncthreads_or(ok ? 0 : 1)) {
-        failed = true;
-        break;
-      }
+    }
+    // slices 5 and 6: every MMA of the tile
+    t.ok = mbar_wait_bounded(&t.empty[1], t.ph_empty[1], kOzWait) && t.ok;
+    t.ph_empty[1] ^= 1u;
+    t.ok = mbar_wait_bounded(&t.empty[0], t.ph_empty[0], kOzWait) && t.ok;
+    t.ph_empty[0] ^= 1u;
+    if (__syncthreads_or(t.ok ? 0 : 1)) {
+      failed = true;
+      break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
     // the next tile's traces are in flight during this epilogue
-    gather(fidn, en < ne);
-    asm volatile("cp.async.wait_all;" ::: "memory");     // this thread's staged rows
+    oz_gather<KP, NQF, TPE>(X, src, fidn, row, part, nface, p.NQFS, p.Nqf, en < ne);
 
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its elements) and
-    // the rows of its half, 8 at a time, all levels
+    // this thread's rows, 4 at a time, all levels; the 4 rows' Gy loads are
+    // in flight during the TMEM reads
     {
       const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-      for (int n0 = nb; n0 < nb + nh; n0 += 8) {
-        uint32_t v[kOzLevels][8];
+      for (int n0 = nb; n0 < nb + nh; n0 += 4) {
+        double gy[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int n = n0 + q;
+          gy[q] = (live && n < p.n_rows) ? p.Gy[(int64_t)n * ne + e] : 0.0;
+        }
+        uint32_t v[kOzLevels][4];
 #pragma unroll
         for (int L = 0; L < kOzLevels; ++L)
-          tmem_ld8(t.tbase + lanes + (uint32_t)(L * p.LS + n0), v[L]);
+          tmem_ld4(t.tbase + lanes + (uint32_t)(L * p.LS + n0), v[L]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (!live) continue;
+        if (live) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int n = n0 + q;
-          if (n >= p.n_rows) continue;
-          int64_t D[kOzLevels];
+          for (int q = 0; q < 4; ++q) {
+            const int n = n0 + q;
+            if (n >= p.n_rows) continue;
+            int64_t D[kOzLevels];
 #pragma unroll
-          for (int L = 0; L < kOzLevels; ++L) D[L] = __float2int_rn(__uint_as_float(v[L][q]));
-          // sum_L D_L 2^(7 (6 - L)) = 2^3 (hi 2^25 + lo 2^-10), hi and lo exact
-          const int64_t hi = D[0] * (1ll << 14) + D[1] * (1ll << 7) + D[2];
-          const int64_t lo = D[3] * (1ll << 28) + D[4] * (1ll << 21) + D[5] * (1ll << 14) +
-                             D[6] * (1ll << 7) + D[7];
-          const int64_t T = hi * (1ll << 25) + (lo >> 10);
-          double y = oz_to_double(T, E + row_sc[n]);
-          if (bad) y = __longlong_as_double(0x7FF8000000000000ll);
-          const double vnew = Gsh[n * kOzM + row] + y;
-          if (n < p.n_up) {
-            const int fg = row_fg[n];
-            const int64_t ti = (int64_t)(fg & 0xFFFF) * nface + fid[(fg >> 16) * kOzM + row];
-            const double dd = vnew - Osh[n * kOzM + row];
-            dst[ti] = vnew;
-            acc_res = fma(row_w[n] * dd, dd, acc_res);
-          } else {
-            p.Y[(int64_t)row_pt[n] * ne + e] = vnew;
+            for (int L = 0; L < kOzLevels; ++L) D[L] = __float2int_rn(__uint_as_float(v[L][q]));
+            // sum_L D_L 2^(7 (6 - L)) = 2^3 (hi 2^25 + lo 2^-10), hi and lo exact
+            const int64_t hi = D[0] * (1ll << 14) + D[1] * (1ll << 7) + D[2];
+            const int64_t lo = D[3] * (1ll << 28) + D[4] * (1ll << 21) + D[5] * (1ll << 14) +
+                               D[6] * (1ll << 7) + D[7];
+            const int64_t T = hi * (1ll << 25) + (lo >> 10);
+            double y = oz_to_double(T, E + row_sc[n]);
+            if (bad) y = __longlong_as_double(0x7FF8000000000000ll);
+            const double vnew = gy[q] + y;
+            if (n < p.n_up) {
+              const int fg = row_fg[n];
+              const int64_t ti = (int64_t)(fg & 0xFFFF) * nface + fid[(fg >> 16) * kOzM + row];
+              const double dd = vnew - Osh[n * kOzM + row];
+              dst[ti] = vnew;
+              acc_res = fma(row_w[n] * dd, dd, acc_res);
+            } else {
+              p.Y[(int64_t)row_pt[n] * ne + e] = vnew;
+            }
           }
         }
       }
@@ -458,8 +512,8 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_sweep_ozaki(const OzParams p)
   if (failed && tid == 0) {
     atomicExch(p.err, 1);
     // drain: a commit tracks every MMA issued before it
-    oz_commit(&mbar[2]);
-    mbar_wait_bounded(&mbar[2], 0u, kOzWait);
+    oz_commit(&bars[4]);
+    mbar_wait_bounded(&bars[4], 0u, kOzWait);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -472,12 +526,12 @@ __global__ void __launch_bounds__(kOzThreads, 1) k_sweep_ozaki(const OzParams p)
   } else {
     // partial sums only; the tangential-point kernel reduces them with its own
     acc_res = fsum_warp(acc_res);
-    __shared__ double red2[kOzThreads / 32];
+    __shared__ double red2[NT / 32];
     if ((tid & 31) == 0) red2[tid >> 5] = acc_res;
     __syncthreads();
     if (tid == 0) {
       double s = 0.0;
-      for (int w = 0; w < kOzThreads / 32; ++w) s += red2[w];
+      for (int w = 0; w < NT / 32; ++w) s += red2[w];
       p.partials[blockIdx.x] = s;
     }
   }
@@ -487,31 +541,22 @@ int oz_kp(const Ctx& c) { return (c.NQFS + 15) / 16 * 16; }
 
 size_t oz_smem(const Ctx& c) {
   const int KP = oz_kp(c), Np = c.oz_Np;
-  return (size_t)kOzDigits * Np * KP * 2 + 2 * (size_t)kOzM * KP * 2 + 2 * sizeof(int) * c.F * kOzM +
-         (size_t)Np * (3 * sizeof(int) + sizeof(double)) + 2 * sizeof(double) * Np * kOzM;
+  return (size_t)kOzDigits * c.oz_LS * KP * 2 + 2 * (size_t)kOzM * KP * 2 +
+         2 * sizeof(int) * c.F * kOzM + (size_t)Np * 3 * sizeof(int) + sizeof(int) * KP +
+         (size_t)Np * sizeof(double) + sizeof(double) * Np * kOzM;
 }
 
-template <int KP>
-cudaError_t oz_prepare(Ctx& c) {
-  const size_t smem = oz_smem(c);
-  cudaError_t err = cudaFuncSetAttribute(k_sweep_ozaki<KP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (err != cudaSuccess) return err;
-  int bpsm = 0;
-  err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_sweep_ozaki<KP>, kOzThreads, smem);
-  if (err != cudaSuccess) return err;
-  bpsm = std::min(bpsm, 512 / c.oz_ncols);          // TMEM columns per SM
-  if (bpsm < 1) return cudaErrorInvalidConfiguration;
-  const int64_t ntiles = (c.nel + kOzM - 1) / kOzM;
-  c.oz_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bpsm * device_sms(), ntiles));
-  c.oz_smem = smem;
-  return cudaSuccess;
-}
-
-template <int KP>
-cudaError_t oz_launch(const Ctx& c, const OzParams& p) {
-  k_sweep_ozaki<KP><<<c.oz_grid, kOzThreads, c.oz_smem, c.stream>>>(p);
-  return cudaGetLastError();
+// Kernel shape of a context: (KP, NQF, TPE).
+template <class Fn>
+cudaError_t oz_dispatch(const Ctx& c, Fn&& fn) {
+  switch (oz_kp(c)) {
+    case 16: return fn(k_sweep_ozaki<16, 0, 2>, 2);
+    case 32: return fn(k_sweep_ozaki<32, 0, 2>, 2);
+    case 64:
+      return c.Nqf == 9 ? fn(k_sweep_ozaki<64, 9, 4>, 4) : fn(k_sweep_ozaki<64, 0, 4>, 4);
+    default:
+      return c.Nqf == 16 ? fn(k_sweep_ozaki<96, 16, 4>, 4) : fn(k_sweep_ozaki<96, 0, 4>, 4);
+  }
 }
 
 }  // namespace
@@ -520,8 +565,10 @@ bool ozaki_supported(const Ctx& c) {
   const int KP = oz_kp(c);
   const int Np = std::max(16, (c.n_rows + 15) / 16 * 16);
   const int LS = (Np + 31) / 32 * 32;
-  return c.pde == EHDG_TRANSPORT && c.shared_op && c.n_rows >= 1 &&
-         (KP == 16 || KP == 32 || KP == 64 || KP == 96) && kOzLevels * LS <= 512;
+  const int tpe = KP >= 64 ? 4 : 2;
+  return c.pde == EHDG_TRANSPORT && c.shared_op && c.n_rows >= 1 && c.F <= 6 &&
+         (KP == 16 || KP == 32 || KP == 64 || KP == 96) && kOzLevels * LS <= 512 &&
+         (Np / tpe) % 4 == 0;
 }
 
 cudaError_t build_ozaki_operator(Ctx& c) {
@@ -532,19 +579,29 @@ cudaError_t build_ozaki_operator(Ctx& c) {
   int ncols = 32;
   while (ncols < kOzLevels * c.oz_LS) ncols *= 2;
   c.oz_ncols = ncols;
-  const size_t img = (size_t)kOzDigits * c.oz_Np * KP * 2;
+  const size_t img = (size_t)kOzDigits * c.oz_LS * KP * 2;
   cudaError_t err;
   if ((err = dalloc_raw(c, &c.oz_img, img)) != cudaSuccess) return err;
-  if ((err = dalloc_raw(c, (void**)&c.oz_Fb, sizeof(int) * c.oz_Np)) != cudaSuccess) return err;
-  k_oz_split_rows<<<c.oz_Np, 32, 0, c.stream>>>(c.Hy, c.rows, c.n_rows, c.NQFS, c.oz_Np, KP,
+  if ((err = dalloc_raw(c, (void**)&c.oz_Fb, sizeof(int) * c.oz_LS)) != cudaSuccess) return err;
+  k_oz_split_rows<<<c.oz_LS, 32, 0, c.stream>>>(c.Hy, c.rows, c.n_rows, c.NQFS, c.oz_LS, KP,
                                                  (unsigned short*)c.oz_img, c.oz_Fb);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  switch (KP) {
-    case 16: return oz_prepare<16>(c);
-    case 32: return oz_prepare<32>(c);
-    case 64: return oz_prepare<64>(c);
-    default: return oz_prepare<96>(c);
-  }
+  const size_t smem = oz_smem(c);
+  return oz_dispatch(c, [&](auto kernel, int tpe) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    int bpsm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, kOzM * tpe, smem);
+    if (e != cudaSuccess) return e;
+    bpsm = std::min(bpsm, 512 / c.oz_ncols);          // TMEM columns per SM
+    if (bpsm < 1) return cudaErrorInvalidConfiguration;
+    const int64_t ntiles = (c.nel + kOzM - 1) / kOzM;
+    c.oz_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bpsm * device_sms(), ntiles));
+    c.oz_smem = smem;
+    c.oz_threads = kOzM * tpe;
+    return cudaSuccess;
+  });
 }
 
 cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out) {
@@ -559,7 +616,6 @@ cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out) {
   p.Np = c.oz_Np;
   p.LS = c.oz_LS;
   p.ncols = c.oz_ncols;
-  p.idesc = umma_idesc(1u, kOzM, c.oz_Np);
   p.rows = c.rows;
   p.elem_face = c.geo.elem_face;
   p.face_jf = c.geo.face_jf;
@@ -580,12 +636,10 @@ cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out) {
   p.handle = c.handle;
   p.err = c.tc_err;
   *grid_out = c.oz_grid;
-  switch (oz_kp(c)) {
-    case 16: return oz_launch<16>(c, p);
-    case 32: return oz_launch<32>(c, p);
-    case 64: return oz_launch<64>(c, p);
-    default: return oz_launch<96>(c, p);
-  }
+  return oz_dispatch(c, [&](auto kernel, int) -> cudaError_t {
+    kernel<<<c.oz_grid, c.oz_threads, c.oz_smem, c.stream>>>(p);
+    return cudaGetLastError();
+  });
 }
 
 }  // namespace ehdg
