@@ -421,7 +421,7 @@ def compare_workload(args):
     stream = torch.cuda.current_stream()
     if args.workload == "transport3d":
         wl = W.transport_3d(n=(args.n, args.n, args.n), p=3, n_steps=args.time_steps)
-        precisions = ["fp64", "fp64_emulated", "tf32", "bf16", "fp32"]
+        precisions = ["fp64", "fp64_emulated", "tf32", "bf16", "fp32", "bf16+emulated_outer"]
     elif args.workload == "sw2d":
         # dt at which Theorem 2 holds on this mesh: h / (dt (p+1)(p+2)) = 3.9, C = 0.34
         wl = W.sw_2d(n=(args.n, args.n), p=3, dt=2.5e-5, n_steps=args.time_steps)
@@ -437,9 +437,13 @@ def compare_workload(args):
     results = {}
     ref = None
     for prec in precisions:
+        # "<precision>+emulated_outer": mixed precision whose outer FP64 sweeps
+        # run FP64-accurate on the tensor cores
+        base, _, opt = prec.partition("+")
         kw = dict(pde=wl.pde, scheme=wl.scheme, dt=wl.dt, tol=wl.tol,
                   max_iter=20000 if wl.scheme == "steady" else 400,
-                  precision=prec, inner_sweeps=args.inner_sweeps, stream=stream)
+                  precision=base, inner_sweeps=args.inner_sweeps, stream=stream,
+                  emulated_outer=(opt == "emulated_outer"))
         if wl.pde == "sw":
             kw["Phi"] = wl.Phi
         elif wl.beta_fn is not None:

@@ -134,6 +134,12 @@ typedef struct {
   double coriolis_beta;
   double coriolis_ym;
   double friction;
+  /* MIXED_* precisions: nonzero runs the outer FP64 sweeps (the FP64
+   * residual R and the convergence test) as FP64_EMULATED sweeps on the BF16
+   * tensor cores, under the same conditions as FP64_EMULATED (otherwise
+   * ehdg_create returns EHDG_ERR_UNSUPPORTED). Zero: DFMA sweeps. Ignored by
+   * FP64 and FP64_EMULATED. */
+  int emulated_outer;
 } ehdg_problem_desc;
 
 /* Sizes of a created context. */

@@ -677,7 +677,9 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
                 "TF32 tensor-core sweeps need one local operator shared by all elements "
                 "(constant velocity, uniform mesh); use EHDG_MIXED_FP32 or EHDG_MIXED_BF16");
   }
-  if (c.precision == EHDG_FP64_EMULATED && (prob->pde != EHDG_TRANSPORT || !c.shared_op)) {
+  const bool want_ozaki =
+      c.precision == EHDG_FP64_EMULATED || (c.mixed && prob->emulated_outer != 0);
+  if (want_ozaki && (prob->pde != EHDG_TRANSPORT || !c.shared_op)) {
     delete h;
     return fail(EHDG_ERR_UNSUPPORTED,
                 "FP64_EMULATED sweeps need transport with one local operator shared by all "
@@ -926,7 +928,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
                         "count of the tiled sweep (quadrilaterals with 2..10 points per edge, "
                         "hexahedra with 2x2 or 3x3 per face)"));
   if (c.mixed) CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_hy_to_f32(c); }));
-  if (c.precision == EHDG_FP64_EMULATED) {
+  if (want_ozaki) {
     if (!ozaki_supported(c))
       return cleanup(fail(EHDG_ERR_UNSUPPORTED,
                           "FP64_EMULATED sweeps support at most 64 sweep rows and 96 face "

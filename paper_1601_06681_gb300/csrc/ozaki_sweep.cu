@@ -71,6 +71,7 @@ struct OzParams {
   IterState* it;
   const double* Gy;             // [row][nel]
   double* Y;                    // [point][nel] rows of tangential points
+  float* R_out;                 // mixed precision: F(uhat) - uhat at owned points (or null)
   double* partials;
   int final_here;
   double tol, res_scale;
@@ -317,9 +318,7 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
   int* row_fg = fidb + 2 * p.F * kOzM;                             // [Np] face << 16 | point
   int* row_pt = row_fg + p.Np;                                     // [Np] element face point
   int* row_sc = row_pt + p.Np;                                     // [Np] Fb - 1074
-  int* kslot = row_sc + p.Np;                                      // [KP] owned row of a point
-  double* row_w = reinterpret_cast<double*>(kslot + KP);           // [Np] residual weight
-  double* Osh = row_w + p.Np;                                       // [Np][128] uhat^k, owned rows
+  double* row_w = reinterpret_cast<double*>(row_sc + p.Np + (p.Np & 1));   // [Np] residual weight
 
   {
     const uint4* src = p.Bimg;
@@ -327,7 +326,6 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
     const int n16 = (int)(kOzDigits * bbytes / 16u);
     for (int i = tid; i < n16; i += NT) dstB[i] = src[i];
   }
-  for (int k = tid; k < KP; k += NT) kslot[k] = -1;
   for (int j = tid; j < p.Np; j += NT) {
     const int r = j < p.n_rows ? p.rows[j] : 0;
     const int f = r / p.Nqf, g = r - f * p.Nqf;
@@ -367,8 +365,6 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
       }
     }
   }
-  __syncthreads();
-  for (int n = tid; n < p.n_up; n += NT) kslot[row_pt[n]] = n;
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -394,7 +390,6 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
   const uint32_t rowoff = (uint32_t)(row >> 3) * SBO + (uint32_t)(row & 7) * 16u;
   const uint32_t kc0 = (uint32_t)(part * KH) / 8u;        // this thread's first 16-byte chunk
   const int nh = p.Np / TPE, nb = part * nh;             // this thread's rows in the epilogue
-  const int kbeg = part * KH;
   double acc_res = 0.0;
   bool failed = false;
 
@@ -408,15 +403,9 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
     const bool live = e < ne;
     int* fid = fidb + buf * p.F * kOzM;
     int* fidn = fidb + (buf ^ 1) * p.F * kOzM;
-    // the current traces at the owned points, from the gathered values, and
-    // the largest exponent of the element's traces
     int emax = 0;
 #pragma unroll
-    for (int q = 0; q < KH; ++q) {
-      emax = max(emax, (int)(((uint64_t)X[q] >> 52) & 0x7FF));
-      const int slot = kslot[kbeg + q];
-      if (live && slot >= 0) Osh[slot * kOzM + row] = __longlong_as_double(X[q]);
-    }
+    for (int q = 0; q < KH; ++q) emax = max(emax, (int)(((uint64_t)X[q] >> 52) & 0x7FF));
     emax_sh[tid] = emax;
     __syncthreads();
     int E = emax_sh[row];
@@ -460,25 +449,30 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
     oz_gather<KP, NQF, TPE>(X, src, fidn, row, part, nface, p.NQFS, p.Nqf, en < ne);
 
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its elements) and
-    // this thread's rows, 4 at a time, all levels; the 4 rows' Gy loads are
-    // in flight during the TMEM reads
+    // this thread's rows, 2 at a time (few registers while the next tile's
+    // traces are in flight), all levels; the rows' Gy loads are in flight
+    // during the TMEM reads
     {
       const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
-      for (int n0 = nb; n0 < nb + nh; n0 += 4) {
-        double gy[4];
+      for (int n0 = nb; n0 < nb + nh; n0 += 2) {
+        double gy[2], od[2];
+        int64_t tix[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int q = 0; q < 2; ++q) {
           const int n = n0 + q;
           gy[q] = (live && n < p.n_rows) ? p.Gy[(int64_t)n * ne + e] : 0.0;
+          const int fg = row_fg[n];
+          tix[q] = (int64_t)(fg & 0xFFFF) * nface + fid[(fg >> 16) * kOzM + row];
+          od[q] = (live && n < p.n_up) ? src[tix[q]] : 0.0;
         }
-        uint32_t v[kOzLevels][4];
+        uint32_t v[kOzLevels][2];
 #pragma unroll
         for (int L = 0; L < kOzLevels; ++L)
-          tmem_ld4(t.tbase + lanes + (uint32_t)(L * p.LS + n0), v[L]);
+          tmem_ld2(t.tbase + lanes + (uint32_t)(L * p.LS + n0), v[L]);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         if (live) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
+          for (int q = 0; q < 2; ++q) {
             const int n = n0 + q;
             if (n >= p.n_rows) continue;
             int64_t D[kOzLevels];
@@ -493,11 +487,11 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
             if (bad) y = __longlong_as_double(0x7FF8000000000000ll);
             const double vnew = gy[q] + y;
             if (n < p.n_up) {
-              const int fg = row_fg[n];
-              const int64_t ti = (int64_t)(fg & 0xFFFF) * nface + fid[(fg >> 16) * kOzM + row];
-              const double dd = vnew - Osh[n * kOzM + row];
+              const int64_t ti = tix[q];
+              const double dd = vnew - od[q];
               dst[ti] = vnew;
               acc_res = fma(row_w[n] * dd, dd, acc_res);
+              if (p.R_out) p.R_out[ti] = (float)dd;
             } else {
               p.Y[(int64_t)row_pt[n] * ne + e] = vnew;
             }
@@ -542,8 +536,8 @@ int oz_kp(const Ctx& c) { return (c.NQFS + 15) / 16 * 16; }
 size_t oz_smem(const Ctx& c) {
   const int KP = oz_kp(c), Np = c.oz_Np;
   return (size_t)kOzDigits * c.oz_LS * KP * 2 + 2 * (size_t)kOzM * KP * 2 +
-         2 * sizeof(int) * c.F * kOzM + (size_t)Np * 3 * sizeof(int) + sizeof(int) * KP +
-         (size_t)Np * sizeof(double) + sizeof(double) * Np * kOzM;
+         2 * sizeof(int) * c.F * kOzM + (size_t)(3 * Np + (Np & 1)) * sizeof(int) +
+         (size_t)Np * sizeof(double);
 }
 
 // Kernel shape of a context: (KP, NQF, TPE).
@@ -626,6 +620,7 @@ cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out) {
   p.it = c.it;
   p.Gy = c.Gy;
   p.Y = c.Y;
+  p.R_out = c.mixed ? c.R32 : nullptr;
   p.partials = c.partials;
   p.final_here = c.n_tan == 0 ? 1 : 0;
   p.tol = c.tol;

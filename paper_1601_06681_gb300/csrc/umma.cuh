@@ -62,10 +62,10 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* v) {
                : "r"(taddr));
 }
 
-// 4 consecutive 32-bit TMEM columns of the warp's 32 lanes
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t* v) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+// 2 consecutive 32-bit TMEM columns of the warp's 32 lanes
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
+               : "=r"(v[0]), "=r"(v[1])
                : "r"(taddr));
 }
 

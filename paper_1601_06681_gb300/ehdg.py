@@ -43,7 +43,8 @@ class ProblemDesc(C.Structure):
                 ("beta_const", C.POINTER(C.c_double)), ("beta_nodes", C.POINTER(C.c_double)),
                 ("Phi", C.c_double), ("inner_sweeps", C.c_int),
                 ("coriolis_f0", C.c_double), ("coriolis_beta", C.c_double),
-                ("coriolis_ym", C.c_double), ("friction", C.c_double)]
+                ("coriolis_ym", C.c_double), ("friction", C.c_double),
+                ("emulated_outer", C.c_int)]
 
 
 class Info(C.Structure):
@@ -238,7 +239,8 @@ class Solver:
 
     def __init__(self, mesh, p, pde="transport", scheme="be", dt=1.0, tol=1e-10, max_iter=1000,
                  beta_const=None, beta_nodes=None, Phi=1.0, precision="fp64", inner_sweeps=0,
-                 coriolis=(0.0, 0.0, 0.0), friction=0.0, stream=None, _handle=None):
+                 coriolis=(0.0, 0.0, 0.0), friction=0.0, emulated_outer=False, stream=None,
+                 _handle=None):
         lib = load()
         self.mesh = mesh if isinstance(mesh, Mesh) else Mesh(mesh)
         self._beta_const = None if beta_const is None else np.ascontiguousarray(beta_const, np.float64)
@@ -249,7 +251,7 @@ class Solver:
             None if self._beta_const is None else _ptr(self._beta_const, C.c_double),
             None if self._beta_nodes is None else _ptr(self._beta_nodes, C.c_double), float(Phi),
             int(inner_sweeps), float(coriolis[0]), float(coriolis[1]), float(coriolis[2]),
-            float(friction))
+            float(friction), int(bool(emulated_outer)))
         self.max_iter = int(max_iter)
         self._owned = _handle is None
         if _handle is not None:          # an instance of a batch (owned by the batch)
@@ -413,7 +415,7 @@ class Batch:
                 None if bc is None else _ptr(bc, C.c_double),
                 None if bn is None else _ptr(bn, C.c_double), float(kw.get("Phi", 1.0)),
                 int(kw.get("inner_sweeps", 0)), *[float(v) for v in kw.get("coriolis", (0, 0, 0))],
-                float(kw.get("friction", 0.0)))
+                float(kw.get("friction", 0.0)), int(bool(kw.get("emulated_outer", False))))
             self._specs.append((m, kw))
         h = C.c_void_p()
         _check(lib.ehdg_batch_create(n, meshes, probs, _stream_ptr(stream), C.byref(h)))

@@ -496,3 +496,31 @@ def test_fp64_emulated_rejects_unsupported_problems(ehdg):
         ehdg.Solver(mesh, 3, scheme="be", dt=0.01, beta_const=[1.0, 0.0, 0.0],
                     precision="fp64_emulated")
     assert ei.value.status == 7
+
+
+# mixed precision whose outer FP64 sweeps run on the tensor cores (Ozaki)
+@pytest.mark.parametrize("precision", ["bf16", "tf32", "fp32"])
+@pytest.mark.parametrize("name", ["2d_be_const", "3d_be_const", "3d_be_const_p3_tiles",
+                                  "3d_be_tangent_p2"])
+def test_mixed_with_emulated_outer_sweeps_reaches_fp64_solution(ehdg, name, precision):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    n_steps = 2
+    with ehdg.Solver(mesh, p, tol=1e-12, max_iter=400, precision=precision, inner_sweeps=6,
+                     emulated_outer=True, **kw) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        iters = s.run(n_steps)
+        u, uh = s.get_state()
+        hist = s.residual_history()
+    ou, ouh, oiters, _ = prob.run(u0, n_steps, g_of_t=lambda t: g, tol=1e-13, max_iter=2000)
+    assert hist[-1] < 1e-12
+    assert rel(u, ou) < 1e-10
+    assert rel(uh, ouh) < 1e-10
+    assert sum(iters) < sum(oiters)
+
+
+def test_emulated_outer_sweeps_need_a_shared_operator(ehdg):
+    mesh, p, kw, prob, u0, g = make_case("2d_cn_variable")
+    with pytest.raises(ehdg.EhdgError) as ei:
+        ehdg.Solver(mesh, p, precision="bf16", emulated_outer=True, **kw)
+    assert ei.value.status == 7
