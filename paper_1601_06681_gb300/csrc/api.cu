@@ -173,6 +173,10 @@ ehdg_status download(Ctx& c, double* dst, const double* src_soa, int64_t outer, 
   return EHDG_OK;
 }
 
+// Kernels of one step right-hand side: the tensor-core G = P w, if used,
+// before the step kernel.
+int step_launches(const Ctx& c) { return (c.use_ozaki && c.oz_step.img) ? 2 : 1; }
+
 // A tensor-core sweep whose bounded mbarrier wait gave up leaves a flag.
 ehdg_status check_tc_err(Ctx& c) {
   if (!c.tc_err) return EHDG_OK;
@@ -184,7 +188,7 @@ ehdg_status check_tc_err(Ctx& c) {
 
 ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
   CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_reset_iter(c); }));
-  CK(counted(c, EHDG_KERNEL_STEP, 1, [&] { return launch_step(c); }));
+  CK(counted(c, EHDG_KERNEL_STEP, step_launches(c), [&] { return launch_step(c); }));
   CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceInitial); }));
   const int n_it = fixed_iters > 0 ? fixed_iters : c.max_iter;
   bool persist = fixed_iters <= 0 && persistent_sweep_ok(c);
@@ -394,7 +398,7 @@ ehdg_status run_graph(Ctx& c, int n_steps, int* iters_per_step, double* res) {
   CK(cudaMemsetAsync(&c.it->step, 0, sizeof(int), c.stream));
   for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(c.gexec, c.stream));
   c.launches[EHDG_KERNEL_AUX] += 2 * n_steps;   // reset + step end
-  c.launches[EHDG_KERNEL_STEP] += n_steps;
+  c.launches[EHDG_KERNEL_STEP] += (int64_t)n_steps * step_launches(c);
   c.launches[EHDG_KERNEL_FINAL] += 2 * n_steps;
   c.step_iters_h.resize(n_steps);
   c.step_status_h.resize(n_steps);

@@ -131,13 +131,16 @@ struct Ctx {
   bool mixed = false;
   ehdg_precision precision = EHDG_FP64;
   int* tc_err = nullptr;         // set by a sweep whose bounded mbarrier wait gave up
-  // FP64-accurate sweep on the BF16 tensor cores (Ozaki splitting, shared operator)
+  // FP64-accurate products on the BF16 tensor cores (Ozaki splitting, shared
+  // operator): the sweep (Hy rows), the reconstruction (H) and the step (P)
   bool use_ozaki = false;
-  void* oz_img = nullptr;        // [7][Np x KP] BF16 digit slices of the sweep rows
-  int* oz_Fb = nullptr;          // [Np] largest biased exponent of each sweep row
-  int oz_Np = 0, oz_LS = 0, oz_ncols = 0;   // padded rows, TMEM columns per level, allocated
-  int oz_grid = 0, oz_threads = 0;
-  size_t oz_smem = 0;
+  struct OzOp {
+    void* img = nullptr;         // [7 * LS x KP] BF16 digit slices of the operator rows
+    int* Fb = nullptr;           // [LS] largest biased exponent of each row
+    int rows = 0, Np = 0, LS = 0, ncols = 0, KP = 0, tpe = 0;   // rows, padded, TMEM, K
+    int grid = 0, threads = 0;
+    size_t smem = 0;
+  } oz_sweep, oz_final, oz_step;
   int inner_sweeps = 0;
   float* Hy32 = nullptr;         // FP32 copy of Hy in the sweep's slot layout
   float* R32 = nullptr;          // [Nqf][nface] FP64 residual F(uhat) - uhat, rounded
@@ -226,6 +229,8 @@ cudaError_t launch_correction(Ctx& c, int* n_launched);
 bool ozaki_supported(const Ctx& c);
 cudaError_t build_ozaki_operator(Ctx& c);   // after assembly and rows
 cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out);
+cudaError_t launch_final_ozaki(Ctx& c);     // u = G + H uhat (Crank-Nicolson: 2 v - u^n)
+cudaError_t launch_step_ozaki(Ctx& c);      // G = P w
 cudaError_t dalloc_raw(Ctx& c, void** p, size_t bytes);   // device allocation owned by c
 // tensor-core correction sweep (tc_sweep.cu)
 bool tc_supported(const Ctx& c);

@@ -417,6 +417,7 @@ struct StepParams {
   int n_rows;
   const uint8_t* rowid;         // per-element operator: [NQFS][nel] row of each slot
   const uint8_t* nrows;         // [nel] slots in use
+  int g_ready;                  // 1: G = P w already computed (tensor-core step)
   double* G;
   double* Gy;                   // [slot][nel], slot order of the element sweep
   double* Y;
@@ -442,39 +443,44 @@ __global__ void __launch_bounds__(32 * kStepT) k_step(const StepParams s) {
     const int64_t e = tile * 32 + lane;
     const bool live = e < ne;
     __syncthreads();
-    for (int c = t; c < n; c += kStepT) {
-      double v = 0.0;
-      if (live) {
-        v = s.u[c * ne + e] * s.ucoef;
-        if (s.have_force)
-          v += s.force_avg ? 0.5 * (s.force[c * ne + e] + s.force_old[c * ne + e])
-                           : s.force[c * ne + e];
-      }
-      w[c * 32 + lane] = v;
-    }
-    __syncthreads();
-    for (int r = t; r < n; r += kStepT) {
-      double a0 = 0.0, a1 = 0.0;
-      if (s.shared) {
-        const double* Pr = Psh + r * n;
-        int c = 0;
-        for (; c + 1 < n; c += 2) {
-          a0 = fma(Pr[c], w[c * 32 + lane], a0);
-          a1 = fma(Pr[c + 1], w[(c + 1) * 32 + lane], a1);
+    if (s.g_ready) {
+      // G = P w came from the FP64-accurate tensor-core product
+      for (int r = t; r < n; r += kStepT) g[r * 32 + lane] = live ? s.G[r * ne + e] : 0.0;
+    } else {
+      for (int c = t; c < n; c += kStepT) {
+        double v = 0.0;
+        if (live) {
+          v = s.u[c * ne + e] * s.ucoef;
+          if (s.have_force)
+            v += s.force_avg ? 0.5 * (s.force[c * ne + e] + s.force_old[c * ne + e])
+                             : s.force[c * ne + e];
         }
-        if (c < n) a0 = fma(Pr[c], w[c * 32 + lane], a0);
-      } else if (live) {
-        const double* Pr = s.P + (int64_t)r * n * ne + e;
-        int c = 0;
-        for (; c + 1 < n; c += 2) {
-          a0 = fma(Pr[c * ne], w[c * 32 + lane], a0);
-          a1 = fma(Pr[(c + 1) * ne], w[(c + 1) * 32 + lane], a1);
-        }
-        if (c < n) a0 = fma(Pr[c * ne], w[c * 32 + lane], a0);
+        w[c * 32 + lane] = v;
       }
-      const double acc = a0 + a1;
-      g[r * 32 + lane] = acc;
-      if (live) s.G[r * ne + e] = acc;
+      __syncthreads();
+      for (int r = t; r < n; r += kStepT) {
+        double a0 = 0.0, a1 = 0.0;
+        if (s.shared) {
+          const double* Pr = Psh + r * n;
+          int c = 0;
+          for (; c + 1 < n; c += 2) {
+            a0 = fma(Pr[c], w[c * 32 + lane], a0);
+            a1 = fma(Pr[c + 1], w[(c + 1) * 32 + lane], a1);
+          }
+          if (c < n) a0 = fma(Pr[c], w[c * 32 + lane], a0);
+        } else if (live) {
+          const double* Pr = s.P + (int64_t)r * n * ne + e;
+          int c = 0;
+          for (; c + 1 < n; c += 2) {
+            a0 = fma(Pr[c * ne], w[c * 32 + lane], a0);
+            a1 = fma(Pr[(c + 1) * ne], w[(c + 1) * 32 + lane], a1);
+          }
+          if (c < n) a0 = fma(Pr[c * ne], w[c * 32 + lane], a0);
+        }
+        const double acc = a0 + a1;
+        g[r * 32 + lane] = acc;
+        if (live) s.G[r * ne + e] = acc;
+      }
     }
     __syncthreads();
     if (!live) continue;
@@ -520,6 +526,12 @@ cudaError_t launch_step(Ctx& c) {
   s.G = c.G;
   s.Gy = c.Gy;
   s.Y = c.Y;
+  s.g_ready = 0;
+  if (c.use_ozaki && c.oz_step.img) {
+    cudaError_t e = launch_step_ozaki(c);
+    if (e != cudaSuccess) return e;
+    s.g_ready = 1;
+  }
   const size_t smem = sizeof(double) * ((s.shared ? (size_t)c.n * c.n : 0) + 2 * (size_t)c.n * 32);
   cudaError_t err = cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
@@ -965,7 +977,9 @@ cudaError_t launch_final(Ctx& c) {
   p.H = c.H;
   p.u = c.u;
   cudaError_t err;
-  if (c.Ht) {
+  if (c.use_ozaki && c.oz_final.img) {
+    err = launch_final_ozaki(c);
+  } else if (c.Ht) {
     err = launch_final_tiled(c);
   } else {
     const size_t smem =

@@ -1,6 +1,8 @@
 // FP64-accurate transport sweep on the BF16 tensor cores (Ozaki splitting),
 // for a local operator shared by every element (constant velocity, uniform
-// mesh).
+// mesh). The same kernel, in two more modes, forms the other two shared-
+// operator products of an implicit step: the reconstruction u = G + H uhat
+// and the step's right-hand side G = P w (Sec. 3, the local solve).
 //
 // Per eHDG iteration (Algorithm 1, Sec. 3) and element e, every sweep row n
 // (a face point r_n of e) needs y = sum_j Hy[r_n][j] uhat_e[j]: the local
@@ -57,9 +59,12 @@ constexpr int kOzDigits = 7;               // 7-bit digits per operand: 49-bit f
 constexpr int kOzLevels = 8;               // digit-product levels kept, L = i + l <= 7
 constexpr uint32_t kOzWait = 1u << 24;     // mbarrier polls before giving up
 
+enum OzMode { kOzSweep = 0, kOzFinal = 1, kOzStep = 2 };
+
 struct OzParams {
   int64_t nel, nface;
-  int NQFS, Nqf, F, n_rows, n_up;
+  int NQFS, Nqf, F, n_rows, n_up;   // n_rows: output rows (sweep rows, or the n element nodes)
+  int n_in;                     // step: entries of w (the n element nodes)
   int Np, LS, ncols;            // rows padded to 16, TMEM columns per level, allocated columns
   const int* rows;              // sweep rows (face points), upwind first
   const int32_t* elem_face;     // [F][nel]
@@ -72,6 +77,15 @@ struct OzParams {
   const double* Gy;             // [row][nel]
   double* Y;                    // [point][nel] rows of tangential points
   float* R_out;                 // mixed precision: F(uhat) - uhat at owned points (or null)
+  // reconstruction: u = G + H uhat (cn: 2 (G + H uhat) - u); step: G = P w,
+  // w = ucoef u + f (force_avg: (f + f_old) / 2)
+  const double* G;
+  double* u;
+  double* Gout;
+  const double* force;
+  const double* force_old;
+  double ucoef;
+  int cn, have_force, force_avg;
   double* partials;
   int final_here;
   double tol, res_scale;
@@ -150,21 +164,21 @@ __device__ __forceinline__ void oz_put_digit(unsigned short* img, int LS, int KP
   img[off / 2] = (unsigned short)oz_digit_bf16<I>(Yv);
 }
 
-__global__ void k_oz_split_rows(const double* Hy, const int* rows, int n_rows, int NQFS, int LS,
-                                int KP, unsigned short* img, int* Fb) {
+__global__ void k_oz_split_rows(const double* M, int ld, const int* rows, int n_rows, int K,
+                                int LS, int KP, unsigned short* img, int* Fb) {
   const int n = blockIdx.x, lane = threadIdx.x;
+  const double* Mr = M + (int64_t)(n < n_rows ? (rows ? rows[n] : n) : 0) * ld;
   int emax = 0;
   if (n < n_rows)
-    for (int j = lane; j < NQFS; j += 32) {
-      const uint64_t b = (uint64_t)__double_as_longlong(Hy[(int64_t)rows[n] * NQFS + j]);
+    for (int j = lane; j < K; j += 32) {
+      const uint64_t b = (uint64_t)__double_as_longlong(Mr[j]);
       emax = max(emax, (int)((b >> 52) & 0x7FF));
     }
   for (int o = 16; o > 0; o >>= 1) emax = max(emax, __shfl_xor_sync(0xffffffffu, emax, o));
   if (lane == 0) Fb[n] = emax;
   for (int j = lane; j < KP; j += 32) {
     uint64_t bits = 0;
-    if (n < n_rows && j < NQFS)
-      bits = (uint64_t)__double_as_longlong(Hy[(int64_t)rows[n] * NQFS + j]);
+    if (n < n_rows && j < K) bits = (uint64_t)__double_as_longlong(Mr[j]);
     const int64_t Yv = oz_fixed(bits, emax);
     oz_put_digit<0>(img, LS, KP, n, j, Yv);
     oz_put_digit<1>(img, LS, KP, n, j, Yv);
@@ -294,11 +308,31 @@ __device__ __forceinline__ void oz_gather(int64_t* X, const double* src, const i
   }
 }
 
-// KP: face points padded to 16; NQF: face points per face (0 = runtime);
-// TPE: threads per element (2 or 4), each with KP / TPE face points and
-// Np / TPE rows.
-template <int KP, int NQF, int TPE>
-__global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p) {
+// The step's A operand: this thread's KH entries of w = ucoef u + f at the
+// element's nodes (raw FP64 bits); the reads are coalesced across elements.
+template <int KP, int TPE>
+__device__ __forceinline__ void oz_load_w(int64_t* X, const OzParams& p, int part, int64_t e,
+                                          bool live) {
+  constexpr int KH = KP / TPE;
+#pragma unroll
+  for (int q = 0; q < KH; ++q) {
+    const int k = part * KH + q;
+    double w = 0.0;
+    if (live && k < p.n_in) {
+      const int64_t i = (int64_t)k * p.nel + e;
+      w = p.u[i] * p.ucoef;
+      if (p.have_force) w += p.force_avg ? 0.5 * (p.force[i] + p.force_old[i]) : p.force[i];
+    }
+    X[q] = __double_as_longlong(w);
+  }
+}
+
+// KP: K padded to 16; NQF: face points per face (0 = runtime); TPE: threads
+// per element (2 or 4), each with KP / TPE entries of K and Np / TPE rows.
+// MODE: kOzSweep (one eHDG iteration), kOzFinal (u = G + H uhat) or kOzStep
+// (G = P w).
+template <int KP, int NQF, int TPE, int MODE>
+__global__ void __launch_bounds__(kOzM * TPE, 1) k_ozaki(const OzParams p) {
   constexpr int NT = kOzM * TPE;
   constexpr int KH = KP / TPE;                       // face points per thread
   constexpr int NFID = (6 + TPE - 1) / TPE;          // faces per thread (at most 6 faces)
@@ -327,13 +361,15 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
     for (int i = tid; i < n16; i += NT) dstB[i] = src[i];
   }
   for (int j = tid; j < p.Np; j += NT) {
-    const int r = j < p.n_rows ? p.rows[j] : 0;
-    const int f = r / p.Nqf, g = r - f * p.Nqf;
-    row_fg[j] = (f << 16) | g;
-    row_pt[j] = r;
     row_sc[j] = p.Fb[j] - 1074;
-    // one face Jacobian per local face: the mesh is uniform
-    row_w[j] = p.face_jf[p.elem_face[(int64_t)f * p.nel]] * p.fw[g];
+    if (MODE == kOzSweep) {
+      const int r = j < p.n_rows ? p.rows[j] : 0;
+      const int f = r / p.Nqf, g = r - f * p.Nqf;
+      row_fg[j] = (f << 16) | g;
+      row_pt[j] = r;
+      // one face Jacobian per local face: the mesh is uniform
+      row_w[j] = p.face_jf[p.elem_face[(int64_t)f * p.nel]] * p.fw[g];
+    }
   }
   if (tid == 0) {
     for (int b = 0; b < 5; ++b) {
@@ -359,7 +395,7 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
     for (int m = 0; m < NFID; ++m) {
       nfid[m] = 0;
       const int f = part + TPE * m;
-      if (f < p.F) {
+      if (MODE != kOzStep && f < p.F) {
         if (e0 < ne) fidb[f * kOzM + row] = p.elem_face[(int64_t)f * ne + e0];
         if (e1 < ne) nfid[m] = p.elem_face[(int64_t)f * ne + e1];
       }
@@ -384,7 +420,9 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
 
   const int kk = p.it->k;                                 // read before the last block advances it
   const int64_t tlen = (int64_t)p.Nqf * nface;
-  const double* src = p.uhat + (int64_t)(kk & 1) * tlen;
+  // the sweep reads uhat^k and writes uhat^{k+1}; the reconstruction uses the
+  // trace of the last sweep, uhat^{k-1} after k sweeps
+  const double* src = p.uhat + (int64_t)((MODE == kOzFinal ? kk + 1 : kk) & 1) * tlen;
   double* dst = p.uhat + (int64_t)((kk + 1) & 1) * tlen;
   const int64_t ntiles = (ne + kOzM - 1) / kOzM;
   const uint32_t rowoff = (uint32_t)(row >> 3) * SBO + (uint32_t)(row & 7) * 16u;
@@ -393,9 +431,14 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
   double acc_res = 0.0;
   bool failed = false;
 
-  int64_t X[KH];                                          // this thread's traces of its element
-  oz_gather<KP, NQF, TPE>(X, src, fidb, row, part, nface, p.NQFS, p.Nqf,
-                          (int64_t)blockIdx.x * kOzM + row < ne);
+  int64_t X[KH];                                          // this thread's part of A's row
+  {
+    const int64_t e0 = (int64_t)blockIdx.x * kOzM + row;
+    if (MODE == kOzStep)
+      oz_load_w<KP, TPE>(X, p, part, e0, e0 < ne);
+    else
+      oz_gather<KP, NQF, TPE>(X, src, fidb, row, part, nface, p.NQFS, p.Nqf, e0 < ne);
+  }
 
   int buf = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, buf ^= 1) {
@@ -430,7 +473,7 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
 #pragma unroll
     for (int m = 0; m < NFID; ++m) {
       const int f = part + TPE * m;
-      if (f < p.F) {
+      if (MODE != kOzStep && f < p.F) {
         fidn[f * kOzM + row] = nfid[m];
         if (enn < ne) nfid[m] = p.elem_face[(int64_t)f * ne + enn];
       }
@@ -445,8 +488,11 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
       break;
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // the next tile's traces are in flight during this epilogue
-    oz_gather<KP, NQF, TPE>(X, src, fidn, row, part, nface, p.NQFS, p.Nqf, en < ne);
+    // the next tile's A entries are in flight during this epilogue
+    if (MODE == kOzStep)
+      oz_load_w<KP, TPE>(X, p, part, en, en < ne);
+    else
+      oz_gather<KP, NQF, TPE>(X, src, fidn, row, part, nface, p.NQFS, p.Nqf, en < ne);
 
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (its elements) and
     // this thread's rows, 2 at a time (few registers while the next tile's
@@ -460,10 +506,16 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const int n = n0 + q;
-          gy[q] = (live && n < p.n_rows) ? p.Gy[(int64_t)n * ne + e] : 0.0;
-          const int fg = row_fg[n];
-          tix[q] = (int64_t)(fg & 0xFFFF) * nface + fid[(fg >> 16) * kOzM + row];
-          od[q] = (live && n < p.n_up) ? src[tix[q]] : 0.0;
+          const bool valid = live && n < p.n_rows;
+          if (MODE == kOzSweep) {
+            gy[q] = valid ? p.Gy[(int64_t)n * ne + e] : 0.0;
+            const int fg = row_fg[n];
+            tix[q] = (int64_t)(fg & 0xFFFF) * nface + fid[(fg >> 16) * kOzM + row];
+            od[q] = (live && n < p.n_up) ? src[tix[q]] : 0.0;
+          } else if (MODE == kOzFinal) {
+            gy[q] = valid ? p.G[(int64_t)n * ne + e] : 0.0;
+            od[q] = (valid && p.cn) ? p.u[(int64_t)n * ne + e] : 0.0;
+          }
         }
         uint32_t v[kOzLevels][2];
 #pragma unroll
@@ -485,6 +537,15 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
             const int64_t T = hi * (1ll << 25) + (lo >> 10);
             double y = oz_to_double(T, E + row_sc[n]);
             if (bad) y = __longlong_as_double(0x7FF8000000000000ll);
+            if (MODE == kOzStep) {
+              p.Gout[(int64_t)n * ne + e] = y;
+              continue;
+            }
+            if (MODE == kOzFinal) {
+              const double v = gy[q] + y;
+              p.u[(int64_t)n * ne + e] = p.cn ? 2.0 * v - od[q] : v;
+              continue;
+            }
             const double vnew = gy[q] + y;
             if (n < p.n_up) {
               const int64_t ti = tix[q];
@@ -514,6 +575,7 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(t.tbase),
                  "r"(p.ncols));
+  if (MODE != kOzSweep) return;
   if (p.final_here) {
     finish_residual(acc_res, p.partials, blockIdx.x, gridDim.x, p.it, p.hist, p.max_iter, p.tol,
                     p.res_scale, p.graph_mode, p.handle, gridDim.x);
@@ -531,93 +593,147 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_sweep_ozaki(const OzParams p)
   }
 }
 
-int oz_kp(const Ctx& c) { return (c.NQFS + 15) / 16 * 16; }
+int pad16(int v) { return std::max(16, (v + 15) / 16 * 16); }
 
-size_t oz_smem(const Ctx& c) {
-  const int KP = oz_kp(c), Np = c.oz_Np;
-  return (size_t)kOzDigits * c.oz_LS * KP * 2 + 2 * (size_t)kOzM * KP * 2 +
-         2 * sizeof(int) * c.F * kOzM + (size_t)(3 * Np + (Np & 1)) * sizeof(int) +
-         (size_t)Np * sizeof(double);
+// Shape of one operator's product: `rows` output rows, K entries of A.
+Ctx::OzOp oz_shape(int rows, int K) {
+  Ctx::OzOp op;
+  op.rows = rows;
+  op.KP = pad16(K);
+  op.Np = pad16(rows);
+  op.LS = (op.Np + 31) / 32 * 32;
+  op.ncols = 32;
+  while (op.ncols < kOzLevels * op.LS) op.ncols *= 2;
+  op.tpe = op.KP >= 64 ? 4 : 2;
+  return op;
 }
 
-// Kernel shape of a context: (KP, NQF, TPE).
-template <class Fn>
-cudaError_t oz_dispatch(const Ctx& c, Fn&& fn) {
-  switch (oz_kp(c)) {
-    case 16: return fn(k_sweep_ozaki<16, 0, 2>, 2);
-    case 32: return fn(k_sweep_ozaki<32, 0, 2>, 2);
-    case 64:
-      return c.Nqf == 9 ? fn(k_sweep_ozaki<64, 9, 4>, 4) : fn(k_sweep_ozaki<64, 0, 4>, 4);
-    default:
-      return c.Nqf == 16 ? fn(k_sweep_ozaki<96, 16, 4>, 4) : fn(k_sweep_ozaki<96, 0, 4>, 4);
+bool oz_shape_ok(const Ctx::OzOp& op, int mode) {
+  const bool kp = mode == kOzStep ? (op.KP == 16 || op.KP == 32 || op.KP == 48 || op.KP == 64)
+                                  : (op.KP == 16 || op.KP == 32 || op.KP == 64 || op.KP == 96);
+  return op.rows >= 1 && kp && kOzLevels * op.LS <= 512;
+}
+
+size_t oz_smem(const Ctx& c, const Ctx::OzOp& op) {
+  return (size_t)kOzDigits * op.LS * op.KP * 2 + 2 * (size_t)kOzM * op.KP * 2 +
+         2 * sizeof(int) * c.F * kOzM + (size_t)(3 * op.Np + (op.Np & 1)) * sizeof(int) +
+         (size_t)op.Np * sizeof(double);
+}
+
+// The kernel of an operator's shape: (KP, NQF, TPE, MODE).
+template <int MODE, class Fn>
+cudaError_t oz_dispatch(const Ctx& c, const Ctx::OzOp& op, Fn&& fn) {
+  if constexpr (MODE == kOzStep) {
+    switch (op.KP) {
+      case 16: return fn(k_ozaki<16, 0, 2, MODE>);
+      case 32: return fn(k_ozaki<32, 0, 2, MODE>);
+      case 48: return fn(k_ozaki<48, 0, 2, MODE>);
+      default: return fn(k_ozaki<64, 0, 4, MODE>);
+    }
+  } else {
+    switch (op.KP) {
+      case 16: return fn(k_ozaki<16, 0, 2, MODE>);
+      case 32: return fn(k_ozaki<32, 0, 2, MODE>);
+      case 64:
+        return c.Nqf == 9 ? fn(k_ozaki<64, 9, 4, MODE>) : fn(k_ozaki<64, 0, 4, MODE>);
+      default:
+        return c.Nqf == 16 ? fn(k_ozaki<96, 16, 4, MODE>) : fn(k_ozaki<96, 0, 4, MODE>);
+    }
   }
 }
 
-}  // namespace
-
-bool ozaki_supported(const Ctx& c) {
-  const int KP = oz_kp(c);
-  const int Np = std::max(16, (c.n_rows + 15) / 16 * 16);
-  const int LS = (Np + 31) / 32 * 32;
-  const int tpe = KP >= 64 ? 4 : 2;
-  return c.pde == EHDG_TRANSPORT && c.shared_op && c.n_rows >= 1 && c.F <= 6 &&
-         (KP == 16 || KP == 32 || KP == 64 || KP == 96) && kOzLevels * LS <= 512 &&
-         (Np / tpe) % 4 == 0;
-}
-
-cudaError_t build_ozaki_operator(Ctx& c) {
-  if (!ozaki_supported(c)) return cudaErrorInvalidValue;
-  const int KP = oz_kp(c);
-  c.oz_Np = std::max(16, (c.n_rows + 15) / 16 * 16);
-  c.oz_LS = (c.oz_Np + 31) / 32 * 32;
-  int ncols = 32;
-  while (ncols < kOzLevels * c.oz_LS) ncols *= 2;
-  c.oz_ncols = ncols;
-  const size_t img = (size_t)kOzDigits * c.oz_LS * KP * 2;
+// Digit image of the operator's rows (M with leading dimension ld; rows
+// listed, or the first op.rows), and the launch shape.
+template <int MODE>
+cudaError_t oz_build(Ctx& c, Ctx::OzOp& op, const double* M, int ld, const int* rows, int K) {
   cudaError_t err;
-  if ((err = dalloc_raw(c, &c.oz_img, img)) != cudaSuccess) return err;
-  if ((err = dalloc_raw(c, (void**)&c.oz_Fb, sizeof(int) * c.oz_LS)) != cudaSuccess) return err;
-  k_oz_split_rows<<<c.oz_LS, 32, 0, c.stream>>>(c.Hy, c.rows, c.n_rows, c.NQFS, c.oz_LS, KP,
-                                                 (unsigned short*)c.oz_img, c.oz_Fb);
+  if ((err = dalloc_raw(c, &op.img, (size_t)kOzDigits * op.LS * op.KP * 2)) != cudaSuccess)
+    return err;
+  if ((err = dalloc_raw(c, (void**)&op.Fb, sizeof(int) * op.LS)) != cudaSuccess) return err;
+  k_oz_split_rows<<<op.LS, 32, 0, c.stream>>>(M, ld, rows, op.rows, K, op.LS, op.KP,
+                                               (unsigned short*)op.img, op.Fb);
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
-  const size_t smem = oz_smem(c);
-  return oz_dispatch(c, [&](auto kernel, int tpe) -> cudaError_t {
+  op.smem = oz_smem(c, op);
+  op.threads = kOzM * op.tpe;
+  return oz_dispatch<MODE>(c, op, [&](auto kernel) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+                                         (int)op.smem);
     if (e != cudaSuccess) return e;
     int bpsm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, kOzM * tpe, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, op.threads, op.smem);
     if (e != cudaSuccess) return e;
-    bpsm = std::min(bpsm, 512 / c.oz_ncols);          // TMEM columns per SM
+    bpsm = std::min(bpsm, 512 / op.ncols);            // TMEM columns per SM
     if (bpsm < 1) return cudaErrorInvalidConfiguration;
     const int64_t ntiles = (c.nel + kOzM - 1) / kOzM;
-    c.oz_grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bpsm * device_sms(), ntiles));
-    c.oz_smem = smem;
-    c.oz_threads = kOzM * tpe;
+    op.grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)bpsm * device_sms(), ntiles));
     return cudaSuccess;
   });
 }
 
-cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out) {
-  OzParams p;
+// Fields every mode reads.
+OzParams oz_params(const Ctx& c, const Ctx::OzOp& op) {
+  OzParams p = {};
   p.nel = c.nel;
   p.nface = c.nface;
   p.NQFS = c.NQFS;
   p.Nqf = c.Nqf;
   p.F = c.F;
-  p.n_rows = c.n_rows;
-  p.n_up = c.n_up;
-  p.Np = c.oz_Np;
-  p.LS = c.oz_LS;
-  p.ncols = c.oz_ncols;
-  p.rows = c.rows;
+  p.n_rows = op.rows;
+  p.Np = op.Np;
+  p.LS = op.LS;
+  p.ncols = op.ncols;
   p.elem_face = c.geo.elem_face;
-  p.face_jf = c.geo.face_jf;
-  fill_face_weights(c, p.fw);
-  p.Bimg = reinterpret_cast<const uint4*>(c.oz_img);
-  p.Fb = c.oz_Fb;
+  p.Bimg = reinterpret_cast<const uint4*>(op.img);
+  p.Fb = op.Fb;
   p.uhat = c.uhat;
   p.it = c.it;
+  p.err = c.tc_err;
+  return p;
+}
+
+template <int MODE>
+cudaError_t oz_run(const Ctx& c, const Ctx::OzOp& op, const OzParams& p) {
+  return oz_dispatch<MODE>(c, op, [&](auto kernel) -> cudaError_t {
+    kernel<<<op.grid, op.threads, op.smem, c.stream>>>(p);
+    return cudaGetLastError();
+  });
+}
+
+}  // namespace
+
+bool ozaki_supported(const Ctx& c) {
+  return c.pde == EHDG_TRANSPORT && c.shared_op && c.F <= 6 &&
+         oz_shape_ok(oz_shape(c.n_rows, c.NQFS), kOzSweep);
+}
+
+cudaError_t build_ozaki_operator(Ctx& c) {
+  if (!ozaki_supported(c)) return cudaErrorInvalidValue;
+  cudaError_t err;
+  c.oz_sweep = oz_shape(c.n_rows, c.NQFS);
+  if ((err = oz_build<kOzSweep>(c, c.oz_sweep, c.Hy, c.NQFS, c.rows, c.NQFS)) != cudaSuccess)
+    return err;
+  // the reconstruction (H: n x NQFS) and the step (P: n x n), where their
+  // shapes fit; otherwise they stay on the FP64 pipe
+  const Ctx::OzOp fin = oz_shape(c.n, c.NQFS), stp = oz_shape(c.n, c.n);
+  if (oz_shape_ok(fin, kOzFinal)) {
+    c.oz_final = fin;
+    if ((err = oz_build<kOzFinal>(c, c.oz_final, c.H, c.NQFS, nullptr, c.NQFS)) != cudaSuccess)
+      return err;
+  }
+  if (oz_shape_ok(stp, kOzStep)) {
+    c.oz_step = stp;
+    if ((err = oz_build<kOzStep>(c, c.oz_step, c.P, c.n, nullptr, c.n)) != cudaSuccess)
+      return err;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out) {
+  OzParams p = oz_params(c, c.oz_sweep);
+  p.n_up = c.n_up;
+  p.rows = c.rows;
+  p.face_jf = c.geo.face_jf;
+  fill_face_weights(c, p.fw);
   p.Gy = c.Gy;
   p.Y = c.Y;
   p.R_out = c.mixed ? c.R32 : nullptr;
@@ -629,12 +745,29 @@ cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out) {
   p.hist = c.hist;
   p.graph_mode = graph_mode;
   p.handle = c.handle;
-  p.err = c.tc_err;
-  *grid_out = c.oz_grid;
-  return oz_dispatch(c, [&](auto kernel, int) -> cudaError_t {
-    kernel<<<c.oz_grid, c.oz_threads, c.oz_smem, c.stream>>>(p);
-    return cudaGetLastError();
-  });
+  *grid_out = c.oz_sweep.grid;
+  return oz_run<kOzSweep>(c, c.oz_sweep, p);
+}
+
+cudaError_t launch_final_ozaki(Ctx& c) {
+  OzParams p = oz_params(c, c.oz_final);
+  p.G = c.G;
+  p.u = c.u;
+  p.cn = (c.scheme == EHDG_CN) ? 1 : 0;
+  return oz_run<kOzFinal>(c, c.oz_final, p);
+}
+
+cudaError_t launch_step_ozaki(Ctx& c) {
+  OzParams p = oz_params(c, c.oz_step);
+  p.n_in = c.n;
+  p.u = c.u;
+  p.Gout = c.G;
+  p.ucoef = (c.scheme == EHDG_STEADY) ? 0.0 : 1.0 / c.dt_eff;
+  p.have_force = c.have_force ? 1 : 0;
+  p.force_avg = (c.scheme == EHDG_CN) ? 1 : 0;
+  p.force = c.force;
+  p.force_old = c.force_old;
+  return oz_run<kOzStep>(c, c.oz_step, p);
 }
 
 }  // namespace ehdg

@@ -93,6 +93,10 @@ def make_case(name):
         # 360 elements: two full 128-element tiles and a ragged third
         mesh, p = W.structured_mesh((9, 8, 5)), 3
         kw = dict(scheme="be", dt=5e-3, beta_const=np.array([1.0, 1.0, 1.0]) / np.sqrt(3.0))
+    elif name == "2d_cn_const":
+        # Crank-Nicolson with one shared operator
+        mesh, p = W.structured_mesh((15, 12)), 3
+        kw = dict(scheme="cn", dt=0.01, beta_const=np.array([0.7, -0.4]))
     elif name == "3d_be_tangent_p2":
         # beta.n = 0 on the y and z faces: tangential rows beside the upwind ones
         mesh, p = W.structured_mesh((7, 5, 4)), 2
@@ -425,8 +429,8 @@ def test_autotuner_keeps_state_and_results(ehdg, tmp_path):
 # tolerances as the FP64 path
 # ---------------------------------------------------------------------------
 
-OZAKI_CASES = ["2d_be_const", "2d_be_zero_component", "3d_be_const", "3d_be_const_p3",
-               "3d_be_const_p3_tiles", "3d_be_tangent_p2"]
+OZAKI_CASES = ["2d_be_const", "2d_be_zero_component", "2d_cn_const", "3d_be_const",
+               "3d_be_const_p3", "3d_be_const_p3_tiles", "3d_be_tangent_p2"]
 
 
 @pytest.mark.parametrize("name", OZAKI_CASES)
@@ -524,3 +528,23 @@ def test_emulated_outer_sweeps_need_a_shared_operator(ehdg):
     with pytest.raises(ehdg.EhdgError) as ei:
         ehdg.Solver(mesh, p, precision="bf16", emulated_outer=True, **kw)
     assert ei.value.status == 7
+
+
+# a forcing term f in the step's right-hand side (Crank-Nicolson averages the
+# two levels), on the DFMA and on the tensor-core step
+@pytest.mark.parametrize("precision", ["fp64", "fp64_emulated"])
+@pytest.mark.parametrize("name", ["2d_cn_const", "3d_be_const"])
+def test_forcing_matches_oracle(ehdg, name, precision):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    f = np.random.default_rng(zlib.crc32(b"forcing" + name.encode())).standard_normal(
+        (prob.nel, prob.nf, prob.Np))
+    with ehdg.Solver(mesh, p, tol=1e-10, max_iter=400, precision=precision, **kw) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        s.set_forcing(f)
+        iters = s.run(3)
+        u, uh = s.get_state()
+    ou, ouh, oiters, _ = prob.run(u0, 3, g_of_t=lambda t: g, f_of_t=lambda t: f, tol=1e-10)
+    assert iters == oiters
+    assert rel(u, ou) < RTOL
+    assert rel(uh, ouh) < RTOL
