@@ -425,7 +425,7 @@ def compare_workload(args):
     elif args.workload == "sw2d":
         # dt at which Theorem 2 holds on this mesh: h / (dt (p+1)(p+2)) = 3.9, C = 0.34
         wl = W.sw_2d(n=(args.n, args.n), p=3, dt=2.5e-5, n_steps=args.time_steps)
-        precisions = ["fp64", "tf32", "bf16", "fp32"]
+        precisions = ["fp64", "fp64_emulated", "tf32", "bf16", "fp32", "bf16+emulated_outer"]
     elif args.workload == "steady2d":
         # the steady solve of Sec. 4.1 (one "step", many iterations)
         wl = W.steady_2d_smooth(n=(args.n, args.n), p=4)
@@ -560,13 +560,16 @@ def batch_workload(args):
     stream = torch.cuda.current_stream()
     wls = W.batched_mix(n_inst=args.n_inst)
     out = {}
-    for prec in ["fp64", "tf32"]:
+    variants = ["fp64", "tf32", "fp64_emulated", "tf32+emulated_outer"]
+    for prec in variants:
+        base, _, opt = prec.partition("+")
         specs, inputs = [], []
         for wl in wls:
             mesh = ehdg.ehdg_mesh_structured(wl.n)
             specs.append(dict(mesh=mesh, p=wl.p, scheme=wl.scheme, dt=wl.dt, tol=wl.tol,
-                              max_iter=400, beta_const=wl.beta_const, precision=prec,
-                              inner_sweeps=args.inner_sweeps))
+                              max_iter=400, beta_const=wl.beta_const, precision=base,
+                              inner_sweeps=args.inner_sweeps,
+                              emulated_outer=(opt == "emulated_outer")))
         t0 = time.perf_counter()
         b = ehdg.Batch(specs, stream=stream)
         setup = time.perf_counter() - t0
@@ -591,7 +594,8 @@ def batch_workload(args):
                      "p99_instance_ms": float(np.percentile(times, 99) * 1e3),
                      "sweeps_total": int(iters.sum())}
         b.close()
-    out["tf32"]["speedup_vs_fp64"] = out["fp64"]["wall_s"] / out["tf32"]["wall_s"]
+    for prec in variants[1:]:
+        out[prec]["speedup_vs_fp64"] = out["fp64"]["wall_s"] / out[prec]["wall_s"]
     info = {"workload": f"batched_mix_{args.n_inst}", "time_steps": wls[0].n_steps,
             "elements_total": int(sum(np.prod(w.n) for w in wls))}
     print(json.dumps({"metric": "instances/s (one graph launch per step)", "config": info,

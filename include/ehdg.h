@@ -79,10 +79,12 @@ typedef enum { EHDG_BE = 0, EHDG_CN = 1, EHDG_STEADY = 2 } ehdg_scheme;
  * 2^24 in FP32 accumulators) and recombined in 64-bit integers; the trace
  * formula and the residual stay FP64. Per product the error is below about
  * 2^-49 (|uhat| max|Hy row| + |Hy| max|uhat_e|) + 2^-51 max|uhat_e| max|Hy row|.
- * Transport with one local operator shared by all elements (constant
- * velocity, uniform mesh), 2D p <= 6 or 3D p <= 3, at most 64 sweep rows per
- * element; otherwise ehdg_create returns EHDG_ERR_UNSUPPORTED. The paper has
- * no counterpart: it is a GB300 form of the plain FP64 sweep. */
+ * One local operator shared by all elements (uniform mesh; transport:
+ * constant velocity, 2D p <= 6 or 3D p <= 3, at most 64 sweep rows per
+ * element; shallow water: no beta-plane, p <= 5), otherwise ehdg_create
+ * returns EHDG_ERR_UNSUPPORTED. The step's G = P w and the reconstruction
+ * u = G + H uhat run the same way where n <= 64. The paper has no
+ * counterpart: it is a GB300 form of the plain FP64 path. */
 typedef enum {
   EHDG_FP64 = 0,
   EHDG_MIXED_TF32 = 1,

@@ -683,11 +683,11 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   }
   const bool want_ozaki =
       c.precision == EHDG_FP64_EMULATED || (c.mixed && prob->emulated_outer != 0);
-  if (want_ozaki && (prob->pde != EHDG_TRANSPORT || !c.shared_op)) {
+  if (want_ozaki && !c.shared_op) {
     delete h;
     return fail(EHDG_ERR_UNSUPPORTED,
-                "FP64_EMULATED sweeps need transport with one local operator shared by all "
-                "elements (constant velocity, uniform mesh)");
+                "FP64_EMULATED sweeps need one local operator shared by all elements (uniform "
+                "mesh; transport: constant velocity; shallow water: no beta-plane)");
   }
   if (c.precision == EHDG_MIXED_BF16 && !c.shared_op && prob->pde != EHDG_TRANSPORT) {
     delete h;
@@ -936,7 +936,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
     if (!ozaki_supported(c))
       return cleanup(fail(EHDG_ERR_UNSUPPORTED,
                           "FP64_EMULATED sweeps support at most 64 sweep rows and 96 face "
-                          "points per element"));
+                          "points per element (shallow water: 24)"));
     CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return build_ozaki_operator(c); }));
     c.use_ozaki = true;
   }

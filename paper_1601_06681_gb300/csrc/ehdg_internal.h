@@ -229,6 +229,7 @@ cudaError_t launch_correction(Ctx& c, int* n_launched);
 bool ozaki_supported(const Ctx& c);
 cudaError_t build_ozaki_operator(Ctx& c);   // after assembly and rows
 cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out);
+cudaError_t launch_elem_ozaki(Ctx& c);      // shallow water: Y = Gy + Hy uhat
 cudaError_t launch_final_ozaki(Ctx& c);     // u = G + H uhat (Crank-Nicolson: 2 v - u^n)
 cudaError_t launch_step_ozaki(Ctx& c);      // G = P w
 cudaError_t dalloc_raw(Ctx& c, void** p, size_t bytes);   // device allocation owned by c

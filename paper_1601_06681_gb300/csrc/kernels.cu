@@ -624,6 +624,7 @@ static cudaError_t launch_elem_t(const ElemParams& p, size_t smem, int grid, cud
 }
 
 cudaError_t launch_elem(Ctx& c) {
+  if (c.use_ozaki) return launch_elem_ozaki(c);
   ElemParams p;
   p.nel = c.nel;
   p.nface = c.nface;

@@ -59,7 +59,11 @@ constexpr int kOzDigits = 7;               // 7-bit digits per operand: 49-bit f
 constexpr int kOzLevels = 8;               // digit-product levels kept, L = i + l <= 7
 constexpr uint32_t kOzWait = 1u << 24;     // mbarrier polls before giving up
 
-enum OzMode { kOzSweep = 0, kOzFinal = 1, kOzStep = 2 };
+// kOzSweep: one transport eHDG iteration (owner writes, residual);
+// kOzElem: Y = Gy + Hy uhat at every sweep row (the shallow-water element
+// apply; the trace kernel forms the trace and the residual); kOzFinal:
+// u = G + H uhat; kOzStep: G = P w.
+enum OzMode { kOzSweep = 0, kOzFinal = 1, kOzStep = 2, kOzElem = 3 };
 
 struct OzParams {
   int64_t nel, nface;
@@ -362,7 +366,7 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_ozaki(const OzParams p) {
   }
   for (int j = tid; j < p.Np; j += NT) {
     row_sc[j] = p.Fb[j] - 1074;
-    if (MODE == kOzSweep) {
+    if (MODE == kOzSweep || MODE == kOzElem) {
       const int r = j < p.n_rows ? p.rows[j] : 0;
       const int f = r / p.Nqf, g = r - f * p.Nqf;
       row_fg[j] = (f << 16) | g;
@@ -512,6 +516,8 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_ozaki(const OzParams p) {
             const int fg = row_fg[n];
             tix[q] = (int64_t)(fg & 0xFFFF) * nface + fid[(fg >> 16) * kOzM + row];
             od[q] = (live && n < p.n_up) ? src[tix[q]] : 0.0;
+          } else if (MODE == kOzElem) {
+            gy[q] = valid ? p.Gy[(int64_t)n * ne + e] : 0.0;
           } else if (MODE == kOzFinal) {
             gy[q] = valid ? p.G[(int64_t)n * ne + e] : 0.0;
             od[q] = (valid && p.cn) ? p.u[(int64_t)n * ne + e] : 0.0;
@@ -547,7 +553,7 @@ __global__ void __launch_bounds__(kOzM * TPE, 1) k_ozaki(const OzParams p) {
               continue;
             }
             const double vnew = gy[q] + y;
-            if (n < p.n_up) {
+            if (MODE == kOzSweep && n < p.n_up) {
               const int64_t ti = tix[q];
               const double dd = vnew - od[q];
               dst[ti] = vnew;
@@ -609,8 +615,9 @@ Ctx::OzOp oz_shape(int rows, int K) {
 }
 
 bool oz_shape_ok(const Ctx::OzOp& op, int mode) {
-  const bool kp = mode == kOzStep ? (op.KP == 16 || op.KP == 32 || op.KP == 48 || op.KP == 64)
-                                  : (op.KP == 16 || op.KP == 32 || op.KP == 64 || op.KP == 96);
+  const bool kp = mode == kOzStep   ? (op.KP == 16 || op.KP == 32 || op.KP == 48 || op.KP == 64)
+                  : mode == kOzElem ? (op.KP == 16 || op.KP == 32)
+                                    : (op.KP == 16 || op.KP == 32 || op.KP == 64 || op.KP == 96);
   return op.rows >= 1 && kp && kOzLevels * op.LS <= 512;
 }
 
@@ -623,7 +630,9 @@ size_t oz_smem(const Ctx& c, const Ctx::OzOp& op) {
 // The kernel of an operator's shape: (KP, NQF, TPE, MODE).
 template <int MODE, class Fn>
 cudaError_t oz_dispatch(const Ctx& c, const Ctx::OzOp& op, Fn&& fn) {
-  if constexpr (MODE == kOzStep) {
+  if constexpr (MODE == kOzElem) {          // shallow water: quadrilaterals, NQFS <= 24
+    return op.KP == 16 ? fn(k_ozaki<16, 0, 2, MODE>) : fn(k_ozaki<32, 0, 2, MODE>);
+  } else if constexpr (MODE == kOzStep) {
     switch (op.KP) {
       case 16: return fn(k_ozaki<16, 0, 2, MODE>);
       case 32: return fn(k_ozaki<32, 0, 2, MODE>);
@@ -655,9 +664,23 @@ cudaError_t oz_build(Ctx& c, Ctx::OzOp& op, const double* M, int ld, const int* 
   if ((err = cudaGetLastError()) != cudaSuccess) return err;
   op.smem = oz_smem(c, op);
   op.threads = kOzM * op.tpe;
+  // The attribute belongs to the kernel function, shared by every context
+  // (and batch instance) that launches it: set it to the largest dynamic size
+  // the device allows next to the kernel's static shared memory, never lower,
+  // so that no context's launch is invalidated by another's smaller setting.
+  int optin = 0;
+  int dev = 0;
+  if ((err = cudaGetDevice(&dev)) != cudaSuccess) return err;
+  if ((err = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) !=
+      cudaSuccess)
+    return err;
   return oz_dispatch<MODE>(c, op, [&](auto kernel) -> cudaError_t {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)op.smem);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const int dyn_max = optin - (int)fa.sharedSizeBytes;
+    if (op.smem > (size_t)dyn_max) return cudaErrorInvalidConfiguration;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
     if (e != cudaSuccess) return e;
     int bpsm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, op.threads, op.smem);
@@ -702,16 +725,19 @@ cudaError_t oz_run(const Ctx& c, const Ctx::OzOp& op, const OzParams& p) {
 }  // namespace
 
 bool ozaki_supported(const Ctx& c) {
-  return c.pde == EHDG_TRANSPORT && c.shared_op && c.F <= 6 &&
-         oz_shape_ok(oz_shape(c.n_rows, c.NQFS), kOzSweep);
+  if (!c.shared_op || c.F > 6) return false;
+  if (c.pde == EHDG_TRANSPORT) return oz_shape_ok(oz_shape(c.n_rows, c.NQFS), kOzSweep);
+  return c.pde == EHDG_SW_LINEAR && oz_shape_ok(oz_shape(c.n_rows, c.NQFS), kOzElem);
 }
 
 cudaError_t build_ozaki_operator(Ctx& c) {
   if (!ozaki_supported(c)) return cudaErrorInvalidValue;
   cudaError_t err;
   c.oz_sweep = oz_shape(c.n_rows, c.NQFS);
-  if ((err = oz_build<kOzSweep>(c, c.oz_sweep, c.Hy, c.NQFS, c.rows, c.NQFS)) != cudaSuccess)
-    return err;
+  err = c.pde == EHDG_TRANSPORT
+            ? oz_build<kOzSweep>(c, c.oz_sweep, c.Hy, c.NQFS, c.rows, c.NQFS)
+            : oz_build<kOzElem>(c, c.oz_sweep, c.Hy, c.NQFS, c.rows, c.NQFS);
+  if (err != cudaSuccess) return err;
   // the reconstruction (H: n x NQFS) and the step (P: n x n), where their
   // shapes fit; otherwise they stay on the FP64 pipe
   const Ctx::OzOp fin = oz_shape(c.n, c.NQFS), stp = oz_shape(c.n, c.n);
@@ -747,6 +773,15 @@ cudaError_t launch_sweep_ozaki(Ctx& c, int graph_mode, int* grid_out) {
   p.handle = c.handle;
   *grid_out = c.oz_sweep.grid;
   return oz_run<kOzSweep>(c, c.oz_sweep, p);
+}
+
+cudaError_t launch_elem_ozaki(Ctx& c) {
+  OzParams p = oz_params(c, c.oz_sweep);
+  p.rows = c.rows;
+  p.face_jf = c.geo.face_jf;
+  p.Gy = c.Gy;
+  p.Y = c.Y;
+  return oz_run<kOzElem>(c, c.oz_sweep, p);
 }
 
 cudaError_t launch_final_ozaki(Ctx& c) {

@@ -23,7 +23,7 @@ def ehdg():
     return E
 
 
-def instances(n=7, seed=77):
+def instances(n=12, seed=77):
     rng = np.random.default_rng(seed)
     out = []
     for i in range(n):
@@ -31,7 +31,10 @@ def instances(n=7, seed=77):
         p = int(rng.integers(1, 5))
         th = rng.uniform(0, 2 * np.pi)
         beta = rng.uniform(0.5, 1.5) * np.array([np.cos(th), np.sin(th)])
-        precision = ["fp64", "tf32", "fp32", "bf16"][i % 4]
+        # the FP64-accurate tensor-core path among them: instances of different
+        # shapes launch the same kernels with different shared-memory sizes
+        precision = ["fp64", "tf32", "fp32", "bf16", "fp64_emulated", "tf32+emulated_outer"][i % 6]
+        base, _, opt = precision.partition("+")
         mesh = W.structured_mesh((nx, ny))
         prob = Problem(mesh, p, scheme="be", dt=0.01, beta_const=beta)
         X = node_coords(mesh, p)
@@ -41,7 +44,8 @@ def instances(n=7, seed=77):
         u0 = W.gaussian(X, c, s)[:, None, :]
         g = W.gaussian(XF, c, s)
         kw = dict(mesh=mesh, p=p, scheme="be", dt=0.01, tol=1e-12, max_iter=500,
-                  beta_const=beta, precision=precision, inner_sweeps=4)
+                  beta_const=beta, precision=base, inner_sweeps=4,
+                  emulated_outer=(opt == "emulated_outer"))
         out.append((kw, prob, u0, g))
     return out
 

@@ -430,7 +430,8 @@ def test_autotuner_keeps_state_and_results(ehdg, tmp_path):
 # ---------------------------------------------------------------------------
 
 OZAKI_CASES = ["2d_be_const", "2d_be_zero_component", "2d_cn_const", "3d_be_const",
-               "3d_be_const_p3", "3d_be_const_p3_tiles", "3d_be_tangent_p2"]
+               "3d_be_const_p3", "3d_be_const_p3_tiles", "3d_be_tangent_p2", "sw_be", "sw_be_p3",
+               "sw_fplane"]
 
 
 @pytest.mark.parametrize("name", OZAKI_CASES)
@@ -438,7 +439,8 @@ OZAKI_CASES = ["2d_be_const", "2d_be_zero_component", "2d_cn_const", "3d_be_cons
 def test_fp64_emulated_fixed_iterations_match_oracle(ehdg, name, n_iter):
     mesh, p, kw, prob, u0, g = make_case(name)
     with ehdg.Solver(mesh, p, tol=1e-10, max_iter=400, precision="fp64_emulated", **kw) as s:
-        s.set_boundary(g)
+        if g is not None:
+            s.set_boundary(g)
         s.set_state(u0)
         s.step_fixed(n_iter)
         u, uh = s.get_state()
@@ -455,11 +457,13 @@ def test_fp64_emulated_steps_to_tolerance_match_oracle(ehdg, name):
     mesh, p, kw, prob, u0, g = make_case(name)
     n_steps = 3
     with ehdg.Solver(mesh, p, tol=1e-10, max_iter=400, precision="fp64_emulated", **kw) as s:
-        s.set_boundary(g)
+        if g is not None:
+            s.set_boundary(g)
         s.set_state(u0)
         iters = s.run(n_steps)
         u, uh = s.get_state()
-    ou, ouh, oiters, _ = prob.run(u0, n_steps, g_of_t=lambda t: g, tol=1e-10)
+    ou, ouh, oiters, _ = prob.run(u0, n_steps, g_of_t=(None if g is None else (lambda t: g)),
+                                  tol=1e-10)
     assert iters == oiters
     assert rel(u, ou) < RTOL
     assert rel(uh, ouh) < RTOL
@@ -489,8 +493,8 @@ def test_fp64_emulated_nan_input_reports_divergence(ehdg):
 
 
 def test_fp64_emulated_rejects_unsupported_problems(ehdg):
-    # per-element operators, shallow water, and more than 64 sweep rows
-    for name in ("2d_cn_variable", "sw_be"):
+    # per-element operators (variable velocity; beta-plane), and more than 64 sweep rows
+    for name in ("2d_cn_variable", "sw_betaplane"):
         mesh, p, kw, prob, u0, g = make_case(name)
         with pytest.raises(ehdg.EhdgError) as ei:
             ehdg.Solver(mesh, p, precision="fp64_emulated", **kw)
@@ -505,18 +509,20 @@ def test_fp64_emulated_rejects_unsupported_problems(ehdg):
 # mixed precision whose outer FP64 sweeps run on the tensor cores (Ozaki)
 @pytest.mark.parametrize("precision", ["bf16", "tf32", "fp32"])
 @pytest.mark.parametrize("name", ["2d_be_const", "3d_be_const", "3d_be_const_p3_tiles",
-                                  "3d_be_tangent_p2"])
+                                  "3d_be_tangent_p2", "sw_be_p3"])
 def test_mixed_with_emulated_outer_sweeps_reaches_fp64_solution(ehdg, name, precision):
     mesh, p, kw, prob, u0, g = make_case(name)
     n_steps = 2
     with ehdg.Solver(mesh, p, tol=1e-12, max_iter=400, precision=precision, inner_sweeps=6,
                      emulated_outer=True, **kw) as s:
-        s.set_boundary(g)
+        if g is not None:
+            s.set_boundary(g)
         s.set_state(u0)
         iters = s.run(n_steps)
         u, uh = s.get_state()
         hist = s.residual_history()
-    ou, ouh, oiters, _ = prob.run(u0, n_steps, g_of_t=lambda t: g, tol=1e-13, max_iter=2000)
+    ou, ouh, oiters, _ = prob.run(u0, n_steps, g_of_t=(None if g is None else (lambda t: g)),
+                                  tol=1e-13, max_iter=2000)
     assert hist[-1] < 1e-12
     assert rel(u, ou) < 1e-10
     assert rel(uh, ouh) < 1e-10
