@@ -560,7 +560,9 @@ def batch_workload(args):
     stream = torch.cuda.current_stream()
     wls = W.batched_mix(n_inst=args.n_inst)
     out = {}
-    variants = ["fp64", "tf32", "fp64_emulated", "tf32+emulated_outer"]
+    # "+tuned": every instance's FP64 path (DFMA or tensor cores) picked by
+    # ehdg_autotune_fp64_path before the first run
+    variants = ["fp64", "tf32", "fp64_emulated", "tf32+emulated_outer", "fp64_emulated+tuned"]
     for prec in variants:
         base, _, opt = prec.partition("+")
         specs, inputs = [], []
@@ -577,6 +579,12 @@ def batch_workload(args):
             X, XF = s.node_coords(), s.face_point_coords()
             s.set_boundary(wl.u0_fn(XF))
             inputs.append(torch.from_numpy(np.ascontiguousarray(wl.initial(X))).cuda())
+        n_tensor = None
+        if opt == "tuned":
+            n_tensor = 0
+            for s, u0 in zip(b.instances, inputs):
+                s.set_state(u0)
+                n_tensor += int(s.autotune_fp64_path()[0])
 
         def one_run():
             for s, u0 in zip(b.instances, inputs):
@@ -593,6 +601,8 @@ def batch_workload(args):
                      "p50_instance_ms": float(np.percentile(times, 50) * 1e3),
                      "p99_instance_ms": float(np.percentile(times, 99) * 1e3),
                      "sweeps_total": int(iters.sum())}
+        if n_tensor is not None:
+            out[prec]["instances_on_tensor_cores"] = n_tensor
         b.close()
     for prec in variants[1:]:
         out[prec]["speedup_vs_fp64"] = out["fp64"]["wall_s"] / out[prec]["wall_s"]

@@ -219,6 +219,17 @@ ehdg_status ehdg_load(ehdg_ctx ctx, const char* path);
  * keeps the fastest, and reports it; the state is left as it was. */
 ehdg_status ehdg_autotune_inner_sweeps(ehdg_ctx ctx, const int* candidates, int n_candidates,
                                        int* best, double* best_ms);
+/* Autotuner for the FP64 path of a context that has both (FP64_EMULATED, or a
+ * MIXED_* precision with emulated_outer): runs one implicit step from the
+ * current state with the DFMA kernels and one with the tensor-core kernels
+ * (restoring the state after each), keeps the faster, and reports both times;
+ * the state is left as it was. Both paths are FP64-accurate; the tensor cores
+ * pay on large shared-operator problems, the DFMA kernels on small ones (a
+ * tensor-core launch has a fixed setup). A batch recaptures its graph after
+ * an instance's path changed. EHDG_ERR_INVALID for a context without the
+ * tensor-core path. The paper has no counterpart. */
+ehdg_status ehdg_autotune_fp64_path(ehdg_ctx ctx, int* tensor_cores, double* ms_dfma,
+                                    double* ms_tensor);
 /* Residual history r_0, r_1, ... of the last step (host buffer of cap entries). */
 ehdg_status ehdg_get_residual_history(ehdg_ctx ctx, double* buf, int64_t cap, int64_t* n_out);
 

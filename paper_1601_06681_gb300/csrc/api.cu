@@ -22,6 +22,7 @@ struct ehdg_batch_s {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<char> graph_force;
+  std::vector<int> graph_gen;          // each instance's path_gen when the graph was captured
   unsigned long long* t_start = nullptr;
   unsigned long long* t_acc = nullptr;
 };
@@ -1176,6 +1177,7 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
     if (e == cudaSuccess) e = cudaEventRecord(joins[i], s);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, joins[i], 0);
     b->graph_force[i] = c.have_force ? 1 : 0;
+    b->graph_gen[i] = c.path_gen;
   }
   if (e != cudaSuccess) {
     abort_capture(b->cap);
@@ -1224,6 +1226,7 @@ ehdg_status ehdg_batch_create(int n, const ehdg_mesh_desc* meshes, const ehdg_pr
       cudaMalloc(&b->t_acc, sizeof(unsigned long long) * n) != cudaSuccess)
     return bail(fail(EHDG_ERR_OOM, "cudaMalloc failed"));
   b->graph_force.assign(n, 0);
+  b->graph_gen.assign(n, 0);
   *out = b;
   return EHDG_OK;
 }
@@ -1243,7 +1246,9 @@ ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_t
     Ctx& c = b->inst[i]->c;
     const int cap = c.step_cap;
     TRY(ensure_step_arrays(c, n_steps));
-    if (c.step_cap != cap || (c.have_force ? 1 : 0) != b->graph_force[i]) rebuild = true;
+    if (c.step_cap != cap || (c.have_force ? 1 : 0) != b->graph_force[i] ||
+        c.path_gen != b->graph_gen[i])
+      rebuild = true;
   }
   if (rebuild) TRY(batch_build_graph(b));
   // the instance contexts run on the batch's stream: order their earlier work first

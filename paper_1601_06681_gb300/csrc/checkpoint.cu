@@ -163,13 +163,16 @@ extern "C" ehdg_status ehdg_load(ehdg_ctx h, const char* path) {
   return EHDG_OK;
 }
 
-extern "C" ehdg_status ehdg_autotune_inner_sweeps(ehdg_ctx h, const int* cands, int n, int* best,
-                                                  double* best_ms) {
-  if (!h || !cands || n < 1) return io_fail(EHDG_ERR_INVALID, "bad argument");
+namespace {
+
+// Time one implicit step from the current state under each of n variants
+// (apply(k) configures variant k), restoring the state after every step;
+// ms[k] is the second of two steps (the first also captures the step graph),
+// or 1e300 when apply(k) declines the variant. The state is left as it was.
+template <class Apply>
+ehdg_status time_step_variants(ehdg_ctx h, int n, Apply apply, double* ms) {
   Ctx& c = h->c;
-  if (!c.mixed) return io_fail(EHDG_ERR_INVALID, "the context is not mixed precision");
   auto arrays = state_arrays(c);
-  // snapshot on the device
   std::vector<void*> snap(arrays.size(), nullptr);
   auto free_snap = [&]() {
     for (void* p : snap)
@@ -186,13 +189,10 @@ extern "C" ehdg_status ehdg_autotune_inner_sweeps(ehdg_ctx h, const int* cands, 
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int saved = c.inner_sweeps;
-  int best_m = saved;
-  double best_t = 1e300;
   ehdg_status st = EHDG_OK;
-  for (int k = 0; k < n && st == EHDG_OK; ++k) {
-    if (cands[k] < 1 || cands[k] > 64) continue;
-    c.inner_sweeps = cands[k];
+  for (int k = 0; k < n; ++k) {
+    ms[k] = 1e300;
+    if (st != EHDG_OK || !apply(k)) continue;
     if (c.gexec) {
       cudaGraphExecDestroy(c.gexec);
       c.gexec = nullptr;
@@ -202,29 +202,23 @@ extern "C" ehdg_status ehdg_autotune_inner_sweeps(ehdg_ctx h, const int* cands, 
       c.graph = nullptr;
     }
     int iters = 0;
-    double ms_sum = 0.0;
-    for (int rep = 0; rep < 2 && st == EHDG_OK; ++rep) {   // first run also captures the graph
+    for (int rep = 0; rep < 2 && st == EHDG_OK; ++rep) {
       cudaEventRecord(e0, c.stream);
       st = ehdg_step(h, &iters, nullptr);
       cudaEventRecord(e1, c.stream);
       cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep == 1) ms_sum = ms;
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep == 1) ms[k] = t;
       for (size_t i = 0; i < arrays.size(); ++i)
         cudaMemcpyAsync(arrays[i].first, snap[i], arrays[i].second, cudaMemcpyDeviceToDevice,
                         c.stream);
-    }
-    if (st == EHDG_OK && ms_sum < best_t) {
-      best_t = ms_sum;
-      best_m = cands[k];
     }
   }
   cudaStreamSynchronize(c.stream);
   free_snap();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c.inner_sweeps = (st == EHDG_OK) ? best_m : saved;
   if (c.gexec) {
     cudaGraphExecDestroy(c.gexec);
     c.gexec = nullptr;
@@ -233,7 +227,59 @@ extern "C" ehdg_status ehdg_autotune_inner_sweeps(ehdg_ctx h, const int* cands, 
     cudaGraphDestroy(c.graph);
     c.graph = nullptr;
   }
+  return st;
+}
+
+}  // namespace
+
+extern "C" ehdg_status ehdg_autotune_inner_sweeps(ehdg_ctx h, const int* cands, int n, int* best,
+                                                  double* best_ms) {
+  if (!h || !cands || n < 1) return io_fail(EHDG_ERR_INVALID, "bad argument");
+  Ctx& c = h->c;
+  if (!c.mixed) return io_fail(EHDG_ERR_INVALID, "the context is not mixed precision");
+  const int saved = c.inner_sweeps;
+  std::vector<double> ms((size_t)n);
+  const ehdg_status st = time_step_variants(
+      h, n,
+      [&](int k) {
+        if (cands[k] < 1 || cands[k] > 64) return false;
+        c.inner_sweeps = cands[k];
+        return true;
+      },
+      ms.data());
+  int best_m = saved;
+  double best_t = 1e300;
+  for (int k = 0; k < n; ++k)
+    if (ms[k] < best_t) {
+      best_t = ms[k];
+      best_m = cands[k];
+    }
+  c.inner_sweeps = (st == EHDG_OK) ? best_m : saved;
   if (best) *best = c.inner_sweeps;
   if (best_ms) *best_ms = best_t;
+  return st;
+}
+
+extern "C" ehdg_status ehdg_autotune_fp64_path(ehdg_ctx h, int* tensor_cores, double* ms_dfma,
+                                               double* ms_tensor) {
+  if (!h) return io_fail(EHDG_ERR_INVALID, "NULL context");
+  Ctx& c = h->c;
+  if (!c.oz_sweep.img)
+    return io_fail(EHDG_ERR_INVALID,
+                   "the context has no tensor-core FP64 path (FP64_EMULATED or emulated_outer)");
+  const bool saved = c.use_ozaki;
+  double ms[2];
+  const ehdg_status st = time_step_variants(
+      h, 2,
+      [&](int k) {
+        c.use_ozaki = k == 1;
+        return true;
+      },
+      ms);
+  c.use_ozaki = (st == EHDG_OK) ? (ms[1] < ms[0]) : saved;
+  ++c.path_gen;
+  if (tensor_cores) *tensor_cores = c.use_ozaki ? 1 : 0;
+  if (ms_dfma) *ms_dfma = ms[0];
+  if (ms_tensor) *ms_tensor = ms[1];
   return st;
 }

@@ -134,6 +134,7 @@ struct Ctx {
   // FP64-accurate products on the BF16 tensor cores (Ozaki splitting, shared
   // operator): the sweep (Hy rows), the reconstruction (H) and the step (P)
   bool use_ozaki = false;
+  int path_gen = 0;              // bumped when the FP64 path is switched (captured graphs go stale)
   struct OzOp {
     void* img = nullptr;         // [7 * LS x KP] BF16 digit slices of the operator rows
     int* Fb = nullptr;           // [LS] largest biased exponent of each row

@@ -79,6 +79,8 @@ _SIGS = [
                                             C.POINTER(C.c_int64)]),
     ("ehdg_save", C.c_int, [C.c_void_p, C.c_char_p]),
     ("ehdg_load", C.c_int, [C.c_void_p, C.c_char_p]),
+    ("ehdg_autotune_fp64_path", C.c_int, [C.c_void_p, C.POINTER(C.c_int),
+                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("ehdg_autotune_inner_sweeps", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
                                              C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_set_profiling", C.c_int, [C.c_void_p, C.c_int]),
@@ -342,6 +344,13 @@ class Solver:
 
     def load_checkpoint(self, path):
         _check(load().ehdg_load(self._h, os.fsencode(path)))
+
+    def autotune_fp64_path(self):
+        """ehdg_autotune_fp64_path: (tensor cores chosen, ms per step DFMA, ms per
+        step tensor cores)."""
+        tc, md, mt = C.c_int(), C.c_double(), C.c_double()
+        _check(load().ehdg_autotune_fp64_path(self._h, C.byref(tc), C.byref(md), C.byref(mt)))
+        return bool(tc.value), md.value, mt.value
 
     def autotune_inner_sweeps(self, candidates=(2, 3, 4, 6, 8, 12)):
         """Fastest inner sweep count for one step from the current state (which

@@ -554,3 +554,29 @@ def test_forcing_matches_oracle(ehdg, name, precision):
     assert iters == oiters
     assert rel(u, ou) < RTOL
     assert rel(uh, ouh) < RTOL
+
+
+# the FP64-path autotuner: both paths are FP64-accurate, the state is untouched
+@pytest.mark.parametrize("name", ["3d_be_const_p3_tiles", "2d_be_const", "sw_be"])
+def test_fp64_path_autotuner_keeps_state_and_results(ehdg, name):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    with ehdg.Solver(mesh, p, tol=1e-10, max_iter=400, precision="fp64_emulated", **kw) as s:
+        if g is not None:
+            s.set_boundary(g)
+        s.set_state(u0)
+        before = s.get_state()
+        tc, ms_dfma, ms_tensor = s.autotune_fp64_path()
+        assert ms_dfma > 0 and ms_tensor > 0 and tc == (ms_tensor < ms_dfma)
+        after = s.get_state()
+        assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+        iters = s.run(2)
+        u, uh = s.get_state()
+    ou, ouh, oiters, _ = prob.run(u0, 2, g_of_t=(None if g is None else (lambda t: g)),
+                                  tol=1e-10)
+    assert iters == oiters
+    assert rel(u, ou) < RTOL
+    assert rel(uh, ouh) < RTOL
+    with ehdg.Solver(mesh, p, precision="fp64", **kw) as s:
+        with pytest.raises(ehdg.EhdgError) as ei:
+            s.autotune_fp64_path()
+        assert ei.value.status == 1
