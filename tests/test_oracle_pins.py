@@ -502,3 +502,32 @@ def test_sw_coriolis_energy_and_friction_dissipation(coriolis, gamma):
         assert e1 <= e0 * (1 + 1e-12)
         assert e0 - e1 >= 2.0 * dt * gamma * vel(u) * (1 - 1e-9) - 1e-12 * e0
         e0 = e1
+
+
+# ---------------------------------------------------------------------------
+# degenerate cases
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,p", [(2, 2), (3, 1)])
+def test_zero_velocity_keeps_state_and_averages_trace(dim, p):
+    """With beta = 0 every term of the local operator but the mass term carries
+    a factor beta (convection) or |beta.n| (the upwind face terms), so both
+    vanish exactly. The step then gives u^{n+1} = u^n, and every face point has
+    sgn(beta.n) = 0, where the trace formula is the average of the two sides
+    (of the element and the boundary data on a boundary face). The first
+    iteration therefore already reproduces the initial trace."""
+    rng = np.random.default_rng(31)
+    mesh = W.structured_mesh((4, 3) if dim == 2 else (3, 2, 2))
+    prob = Problem(mesh, p, scheme="be", dt=0.02, beta_const=np.zeros(dim))
+    assert np.abs(prob.Asp).max() == 0.0 and np.abs(prob.B).max() == 0.0
+    u0 = rng.standard_normal((prob.nel, 1, prob.Np))
+    g = rng.standard_normal((prob.nface, prob.Nqf))
+    u, uh, hist = prob.solve_step(u0, g_new=g, tol=1e-12, max_iter=50)
+    assert len(hist) == 1 and hist[0] < 1e-13
+    assert rel(u, u0) < 1e-14
+    # the average, face by face from the face-point values of each side
+    fe, fl = mesh["face_elem"], mesh["face_local"]
+    for e in range(prob.nface):
+        vm = prob.ref.fphi[int(fl[e, 0])] @ u0[fe[e, 0], 0]
+        vp = prob.ref.fphi[int(fl[e, 1])] @ u0[fe[e, 1], 0] if fe[e, 1] >= 0 else g[e]
+        assert np.abs(uh[e] - 0.5 * (vm + vp)).max() < 1e-13
