@@ -27,6 +27,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# hardware work queues for concurrent graph branches (the batch workload);
+# read when the CUDA context is created, so set before anything touches CUDA
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np  # noqa: E402
 
@@ -550,7 +553,9 @@ def residual_workload(args):
 
 def batch_workload(args):
     """Config 5: independent 2D transport instances (N 8..128, p 1..5) stepped
-    together, one graph launch per time step; FP64 versus mixed precision."""
+    together, one graph launch per time step; FP64 versus mixed precision.
+    Each variant's graph branch count comes from the batch autotuner (setup,
+    outside the timed run)."""
     import torch
     from paper_1601_06681_gb300 import build, ehdg
     from paper_1601_06681_gb300 import workloads as W
@@ -585,6 +590,10 @@ def batch_workload(args):
             for s, u0 in zip(b.instances, inputs):
                 s.set_state(u0)
                 n_tensor += int(s.autotune_fp64_path()[0])
+        # the graph's branch count, picked by ehdg_batch_autotune_chains
+        for s, u0 in zip(b.instances, inputs):
+            s.set_state(u0)
+        chains, _ = b.autotune_chains()
 
         def one_run():
             for s, u0 in zip(b.instances, inputs):
@@ -600,7 +609,7 @@ def batch_workload(args):
         out[prec] = {"instances_per_s": len(wls) / wall, "wall_s": wall, "setup_s": setup,
                      "p50_instance_ms": float(np.percentile(times, 50) * 1e3),
                      "p99_instance_ms": float(np.percentile(times, 99) * 1e3),
-                     "sweeps_total": int(iters.sum())}
+                     "sweeps_total": int(iters.sum()), "chains": chains}
         if n_tensor is not None:
             out[prec]["instances_on_tensor_cores"] = n_tensor
         b.close()

@@ -235,9 +235,13 @@ ehdg_status ehdg_get_residual_history(ehdg_ctx ctx, double* buf, int64_t cap, in
 
 /* Batched form: n independent problems (each its own mesh, degree, velocity,
  * precision) stepped together. Every implicit step of every instance is
- * captured as an independent branch of ONE CUDA graph (each branch with its
- * own device-side convergence loop), so one graph launch advances all
- * instances by one time step, running them concurrently. */
+ * captured into ONE CUDA graph (each step with its own device-side
+ * convergence loop), so one graph launch advances all instances by one time
+ * step. The graph has k independent branches ("chains"); each runs its
+ * instances' steps one after the other, and the branches run concurrently.
+ * Instances go to branches longest step first, each to the least-loaded
+ * branch, by an estimate of their step's device time (iterations of their
+ * last step times the sweep's work, plus a fixed latency per iteration). */
 typedef struct ehdg_batch_s* ehdg_batch;
 ehdg_status ehdg_batch_create(int n, const ehdg_mesh_desc* meshes, const ehdg_problem_desc* probs,
                               void* cuda_stream, ehdg_batch* out);
@@ -249,6 +253,19 @@ ehdg_status ehdg_batch_instance(ehdg_batch b, int i, ehdg_ctx* out);
  * of each instance's branch, summed over the steps (%globaltimer). Returns
  * the first non-OK status of any instance. */
 ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_time_s);
+/* Branch count k of the batch's graph. k <= 0 (the default) takes the number
+ * of hardware work queues the GPU runs concurrent branches on: the value of
+ * CUDA_DEVICE_MAX_CONNECTIONS when the CUDA context was created (8 if unset,
+ * at most 32). k >= n gives every instance its own branch. The graph is
+ * recaptured at the next run. EHDG_ERR_INVALID for a NULL batch. */
+ehdg_status ehdg_batch_set_chains(ehdg_batch b, int k);
+/* Autotuner for the branch count: from the instances' current states, one
+ * batch step (graph launch) per candidate k, timed with CUDA events on the
+ * batch's stream, every instance's state restored after each; keeps the
+ * fastest candidate and reports it with its time. The states are left as
+ * they were. EHDG_ERR_INVALID for a NULL batch or no candidates. */
+ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* candidates, int n_candidates,
+                                       int* best, double* best_ms);
 void ehdg_batch_destroy(ehdg_batch b);
 
 /* FP64 residual of Algorithm 1's convergence check (Sec. 3, "check

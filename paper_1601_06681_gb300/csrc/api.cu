@@ -25,6 +25,8 @@ struct ehdg_batch_s {
   std::vector<int> graph_gen;          // each instance's path_gen when the graph was captured
   unsigned long long* t_start = nullptr;
   unsigned long long* t_acc = nullptr;
+  int chains = 0;                       // concurrent branches of the graph (<= 0: automatic)
+  bool built_on_estimate = false;       // the graph's schedule used estimated iteration counts
 };
 
 namespace {
@@ -1136,15 +1138,61 @@ static void batch_destroy_graph(ehdg_batch b) {
   b->graph = nullptr;
 }
 
-// One graph: fork from a start event into one branch stream per instance,
-// capture each instance's step there (stamped with %globaltimer), join back.
+// Hardware work queues the GPU runs concurrent branches on: the value of
+// CUDA_DEVICE_MAX_CONNECTIONS the driver read at context creation (8 if
+// unset, at most 32).
+static int hw_queues() {
+  const char* v = std::getenv("CUDA_DEVICE_MAX_CONNECTIONS");
+  const int q = v ? std::atoi(v) : 8;
+  return std::min(32, std::max(1, q > 0 ? q : 8));
+}
+
+// Estimated device seconds of one implicit step of context c: per iteration a
+// fixed latency (launches of the loop body) plus the sweep's FP64 products at
+// an effective rate; the iteration count of the last step, or a guess from
+// the mesh diameter before the first.
+static double step_cost(const Ctx& c, bool* estimated) {
+  const bool guess = c.last_iters <= 0;
+  if (guess) *estimated = true;
+  const double iters = guess ? std::pow((double)c.nel, 1.0 / c.dim) + 10.0 : (double)c.last_iters;
+  const double rows = c.sweep_rows > 0 ? (double)c.sweep_rows : (double)c.NQFS * c.nel;
+  const double m = c.mixed ? (double)c.inner_sweeps : 0.0;
+  const double per_iter = 5e-6 * (1.0 + m) + 2.0 * rows * c.NQFS * (1.0 + 0.3 * m) / 5e11;
+  return iters * per_iter;
+}
+
+// Instances of each branch: longest-processing-time-first onto k branches
+// (each next-largest step to the least-loaded branch).
+static std::vector<std::vector<int>> batch_schedule(ehdg_batch b, int k, bool* estimated) {
+  const int n = (int)b->inst.size();
+  std::vector<double> cost(n);
+  for (int i = 0; i < n; ++i) cost[i] = step_cost(b->inst[i]->c, estimated);
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<std::vector<int>> lists(k);
+  std::vector<double> load(k, 0.0);
+  for (int i : order) {
+    const int j = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    lists[j].push_back(i);
+    load[j] += cost[i];
+  }
+  return lists;
+}
+
+// One graph: fork from a start event into k branch streams, capture the
+// steps of each branch's instances there one after the other (each stamped
+// with %globaltimer), join back.
 static ehdg_status batch_build_graph(ehdg_batch b) {
   batch_destroy_graph(b);
   const int n = (int)b->inst.size();
+  const int k = std::min(n, b->chains > 0 ? b->chains : hw_queues());
+  bool estimated = false;
+  const std::vector<std::vector<int>> lists = batch_schedule(b, k, &estimated);
   cudaEvent_t fork = nullptr;
-  std::vector<cudaEvent_t> joins(n, nullptr);
+  std::vector<cudaEvent_t> joins(k, nullptr);
   CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-  for (int i = 0; i < n; ++i) CK(cudaEventCreateWithFlags(&joins[i], cudaEventDisableTiming));
+  for (int j = 0; j < k; ++j) CK(cudaEventCreateWithFlags(&joins[j], cudaEventDisableTiming));
   auto cleanup_events = [&]() {
     cudaEventDestroy(fork);
     for (auto e : joins) cudaEventDestroy(e);
@@ -1155,35 +1203,44 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
     return cuda_fail(e, "batch capture");
   }
   e = cudaEventRecord(fork, b->cap);
-  for (int i = 0; i < n && e == cudaSuccess; ++i) {
-    Ctx& c = b->inst[i]->c;
-    cudaStream_t s = b->branch[i];
+  int started = 0;                                // branches forked so far
+  for (int j = 0; j < k && e == cudaSuccess; ++j) {
+    cudaStream_t s = b->branch[j];
     e = cudaStreamWaitEvent(s, fork, 0);
-    if (e == cudaSuccess) e = launch_stamp(s, b->t_start, b->t_acc, i, 0);
     if (e != cudaSuccess) break;
-    const ehdg_status st = capture_step(c, s, b->body, false);
-    if (st != EHDG_OK) {
-      const std::string msg = g_err;
-      for (int j = 0; j <= i; ++j) {
-        cudaEventRecord(joins[j], b->branch[j]);
-        cudaStreamWaitEvent(b->cap, joins[j], 0);
+    started = j + 1;
+    for (int i : lists[j]) {
+      Ctx& c = b->inst[i]->c;
+      if ((e = launch_stamp(s, b->t_start, b->t_acc, i, 0)) != cudaSuccess) break;
+      const ehdg_status st = capture_step(c, s, b->body, false);
+      if (st != EHDG_OK) {
+        const std::string msg = g_err;
+        for (int jj = 0; jj < started; ++jj) {
+          cudaEventRecord(joins[jj], b->branch[jj]);
+          cudaStreamWaitEvent(b->cap, joins[jj], 0);
+        }
+        abort_capture(b->cap);
+        cleanup_events();
+        g_err = msg;
+        return st;
       }
-      abort_capture(b->cap);
-      cleanup_events();
-      g_err = msg;
-      return st;
+      if ((e = launch_stamp(s, b->t_start, b->t_acc, i, 1)) != cudaSuccess) break;
+      b->graph_force[i] = c.have_force ? 1 : 0;
+      b->graph_gen[i] = c.path_gen;
     }
-    e = launch_stamp(s, b->t_start, b->t_acc, i, 1);
-    if (e == cudaSuccess) e = cudaEventRecord(joins[i], s);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, joins[i], 0);
-    b->graph_force[i] = c.have_force ? 1 : 0;
-    b->graph_gen[i] = c.path_gen;
+    if (e == cudaSuccess) e = cudaEventRecord(joins[j], s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(b->cap, joins[j], 0);
   }
   if (e != cudaSuccess) {
+    for (int jj = 0; jj < started; ++jj) {
+      cudaEventRecord(joins[jj], b->branch[jj]);
+      cudaStreamWaitEvent(b->cap, joins[jj], 0);
+    }
     abort_capture(b->cap);
     cleanup_events();
     return cuda_fail(e, "batch capture");
   }
+  b->built_on_estimate = estimated;
   cudaGraph_t g = nullptr;
   e = cudaStreamEndCapture(b->cap, &g);
   cleanup_events();
@@ -1284,7 +1341,82 @@ ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_t
     c.last_iters = std::min(c.step_iters_h[n_steps - 1], c.max_iter);
     if (inst_time_s) inst_time_s[i] = (double)acc[i] * 1e-9;
   }
+  // a schedule made on guessed iteration counts is made again on the
+  // measured ones, once, before the next run
+  if (first == EHDG_OK && b->built_on_estimate) TRY(batch_build_graph(b));
   return first;
+}
+
+ehdg_status ehdg_batch_set_chains(ehdg_batch b, int k) {
+  if (!b) return fail(EHDG_ERR_INVALID, "NULL batch");
+  if (k != b->chains) {
+    b->chains = k;
+    batch_destroy_graph(b);
+  }
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* cands, int n_cands, int* best,
+                                       double* best_ms) {
+  if (!b || !cands || n_cands < 1) return fail(EHDG_ERR_INVALID, "bad argument");
+  // snapshot of every instance's stepping state
+  std::vector<std::pair<void*, size_t>> arrays;
+  for (auto h : b->inst)
+    for (auto& a : state_arrays(h->c)) arrays.push_back(a);
+  std::vector<void*> snap(arrays.size(), nullptr);
+  auto free_snap = [&]() {
+    for (void* p : snap)
+      if (p) cudaFree(p);
+  };
+  CK(cudaStreamSynchronize(b->stream));
+  for (size_t i = 0; i < arrays.size(); ++i) {
+    if (cudaMalloc(&snap[i], arrays[i].second) != cudaSuccess ||
+        cudaMemcpyAsync(snap[i], arrays[i].first, arrays[i].second, cudaMemcpyDeviceToDevice,
+                        b->stream) != cudaSuccess) {
+      free_snap();
+      return fail(EHDG_ERR_OOM, "batch autotune snapshot failed");
+    }
+  }
+  auto restore = [&]() {
+    for (size_t i = 0; i < arrays.size(); ++i)
+      cudaMemcpyAsync(arrays[i].first, snap[i], arrays[i].second, cudaMemcpyDeviceToDevice,
+                      b->stream);
+    return cudaStreamSynchronize(b->stream);
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int saved = b->chains;
+  int best_k = saved;
+  double best_t = 1e300;
+  ehdg_status st = EHDG_OK;
+  for (int q = 0; q < n_cands && st == EHDG_OK; ++q) {
+    b->chains = cands[q];
+    // the first run captures the graph (and may recapture it on measured
+    // iteration counts); the second is timed
+    for (int rep = 0; rep < 2 && st == EHDG_OK; ++rep) {
+      if (rep == 0) batch_destroy_graph(b);
+      cudaEventRecord(e0, b->stream);
+      st = ehdg_batch_run(b, 1, nullptr, nullptr);
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (restore() != cudaSuccess && st == EHDG_OK) st = cuda_fail(cudaGetLastError(), "restore");
+      if (rep == 1 && st == EHDG_OK && t < best_t) {
+        best_t = t;
+        best_k = cands[q];
+      }
+    }
+  }
+  free_snap();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  b->chains = (st == EHDG_OK) ? best_k : saved;
+  batch_destroy_graph(b);
+  if (best) *best = b->chains;
+  if (best_ms) *best_ms = best_t;
+  return st;
 }
 
 void ehdg_batch_destroy(ehdg_batch b) {

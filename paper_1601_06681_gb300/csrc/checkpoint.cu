@@ -11,6 +11,14 @@
 using namespace ehdg;
 
 
+// the device arrays a checkpoint carries, in file order
+std::vector<std::pair<void*, size_t>> ehdg::state_arrays(Ctx& c) {
+  const size_t state = sizeof(double) * (size_t)c.n * c.nel;
+  const size_t trace = sizeof(double) * (size_t)c.Nqf * c.nface;
+  return {{c.u, state},      {c.uhat, trace},       {c.uhat_n, trace}, {c.gb, trace},
+          {c.gb_old, trace}, {c.force, state},      {c.force_old, state}};
+}
+
 namespace {
 
 constexpr uint32_t kMagic = 0x47444845u;   // "EHDG"
@@ -61,14 +69,6 @@ uint64_t config_hash(const Ctx& c) {
   h = fnv1a(h, src, sizeof(src));
   h = fnv1a(h, c.beta_const, sizeof(double) * 3);
   return h;
-}
-
-// the device arrays a checkpoint carries, in file order
-std::vector<std::pair<void*, size_t>> state_arrays(Ctx& c) {
-  const size_t state = sizeof(double) * (size_t)c.n * c.nel;
-  const size_t trace = sizeof(double) * (size_t)c.Nqf * c.nface;
-  return {{c.u, state},      {c.uhat, trace},       {c.uhat_n, trace}, {c.gb, trace},
-          {c.gb_old, trace}, {c.force, state},      {c.force_old, state}};
 }
 
 ehdg_status io_fail(ehdg_status s, const std::string& m) {

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ehdg.h"
@@ -234,6 +235,8 @@ cudaError_t launch_elem_ozaki(Ctx& c);      // shallow water: Y = Gy + Hy uhat
 cudaError_t launch_final_ozaki(Ctx& c);     // u = G + H uhat (Crank-Nicolson: 2 v - u^n)
 cudaError_t launch_step_ozaki(Ctx& c);      // G = P w
 cudaError_t dalloc_raw(Ctx& c, void** p, size_t bytes);   // device allocation owned by c
+// the device arrays of a context's stepping state (checkpoints, autotuner snapshots)
+std::vector<std::pair<void*, size_t>> state_arrays(Ctx& c);
 // tensor-core correction sweep (tc_sweep.cu)
 bool tc_supported(const Ctx& c);
 cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out);

@@ -12,6 +12,13 @@ import os
 
 import numpy as np
 
+# A batch's graph runs its branches on the GPU's hardware work queues. CUDA
+# creates 8 of them unless CUDA_DEVICE_MAX_CONNECTIONS says otherwise when
+# the context is created, and a batch then runs at most 8 branches at once.
+# Ask for the maximum, 32, unless the caller chose a value (this takes effect
+# only if CUDA has not been initialised in the process yet).
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libehdg.so")
 
@@ -91,6 +98,9 @@ _SIGS = [
                                     C.c_void_p, C.POINTER(C.c_void_p)]),
     ("ehdg_batch_instance", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     ("ehdg_batch_run", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    ("ehdg_batch_set_chains", C.c_int, [C.c_void_p, C.c_int]),
+    ("ehdg_batch_autotune_chains", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
+                                             C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_batch_destroy", None, [C.c_void_p]),
     ("ehdg_trace_residual", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                       C.c_void_p]),
@@ -445,6 +455,20 @@ class Batch:
         _check(load().ehdg_batch_run(self._h, int(n_steps), iters.ctypes.data_as(C.c_void_p),
                                      times.ctypes.data_as(C.c_void_p)))
         return iters, times
+
+    def set_chains(self, k):
+        """Concurrent branches of the batch's graph (k <= 0: one per hardware
+        work queue; k >= n: one per instance)."""
+        _check(load().ehdg_batch_set_chains(self._h, int(k)))
+
+    def autotune_chains(self, candidates=(8, 16, 32, 64, 256)):
+        """Time one batch step per branch count from the current states
+        (restored after each) and keep the fastest: (k, ms)."""
+        arr = (C.c_int * len(candidates))(*[int(k) for k in candidates])
+        best, ms = C.c_int(), C.c_double()
+        _check(load().ehdg_batch_autotune_chains(self._h, arr, len(candidates), C.byref(best),
+                                                 C.byref(ms)))
+        return best.value, ms.value
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

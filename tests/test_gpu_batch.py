@@ -75,3 +75,43 @@ def test_batch_matches_solo_runs_and_oracle(ehdg):
         ou, _, _, _ = prob.run(u0, n_steps, g_of_t=lambda t: g, tol=1e-13, max_iter=2000)
         err = np.linalg.norm(u - ou) / np.linalg.norm(ou)
         assert err < 1e-10, (i, kw["precision"], err)
+
+
+def run_batch(ehdg, inst, n_steps, chains=None, tune=None):
+    with ehdg.Batch([kw for kw, _, _, _ in inst]) as b:
+        if chains is not None:
+            b.set_chains(chains)
+        for (kw, prob, u0, g), s in zip(inst, b.instances):
+            s.set_boundary(g)
+            s.set_state(u0)
+        tuned = None
+        if tune is not None:
+            before = [s.get_state() for s in b.instances]
+            tuned = b.autotune_chains(tune)
+            after = [s.get_state() for s in b.instances]
+            for (u0_, uh0_), (u1_, uh1_) in zip(before, after):
+                assert np.array_equal(u0_, u1_) and np.array_equal(uh0_, uh1_)
+        iters, _ = b.run(n_steps)
+        return iters, [s.get_state() for s in b.instances], tuned
+
+
+def test_branch_count_does_not_change_results(ehdg):
+    """The graph's branch count only changes which steps run side by side:
+    every instance's iterations and state are the same, bit for bit."""
+    inst = instances(n=7, seed=5)
+    ref_iters, ref_states, _ = run_batch(ehdg, inst, 2)
+    for k in (1, 3, 7, 64):
+        iters, states, _ = run_batch(ehdg, inst, 2, chains=k)
+        assert np.array_equal(iters, ref_iters), k
+        for (u, uh), (ru, ruh) in zip(states, ref_states):
+            assert np.array_equal(u, ru) and np.array_equal(uh, ruh), k
+
+
+def test_chain_autotuner_keeps_states_and_results(ehdg):
+    inst = instances(n=7, seed=6)
+    ref_iters, ref_states, _ = run_batch(ehdg, inst, 2)
+    iters, states, (best, ms) = run_batch(ehdg, inst, 2, tune=(1, 2, 7))
+    assert best in (1, 2, 7) and 0 < ms < 1e300
+    assert np.array_equal(iters, ref_iters)
+    for (u, uh), (ru, ruh) in zip(states, ref_states):
+        assert np.array_equal(u, ru) and np.array_equal(uh, ruh)
