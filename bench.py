@@ -424,7 +424,8 @@ def compare_workload(args):
     stream = torch.cuda.current_stream()
     if args.workload == "transport3d":
         wl = W.transport_3d(n=(args.n, args.n, args.n), p=3, n_steps=args.time_steps)
-        precisions = ["fp64", "fp64_emulated", "tf32", "bf16", "fp32", "bf16+emulated_outer"]
+        precisions = ["fp64", "fp64+tiles", "fp64_emulated", "tf32", "bf16", "fp32",
+                      "bf16+emulated_outer"]
     elif args.workload == "sw2d":
         # dt at which Theorem 2 holds on this mesh: h / (dt (p+1)(p+2)) = 3.9, C = 0.34
         wl = W.sw_2d(n=(args.n, args.n), p=3, dt=2.5e-5, n_steps=args.time_steps)
@@ -435,13 +436,14 @@ def compare_workload(args):
         precisions = ["fp64", "fp32", "bf16"]
     else:
         wl = W.transport_2d_small(n=(args.n, args.n), p=2, n_steps=args.time_steps)
-        precisions = ["fp64", "fp64_emulated", "tf32", "fp32"]
+        precisions = ["fp64", "fp64+tiles", "fp64_emulated", "tf32", "fp32"]
     mesh = ehdg.ehdg_mesh_structured(wl.n, boundary_tag=(2 if wl.pde == "sw" else 1))
     results = {}
     ref = None
     for prec in precisions:
         # "<precision>+emulated_outer": mixed precision whose outer FP64 sweeps
-        # run FP64-accurate on the tensor cores
+        # run FP64-accurate on the tensor cores; "+tiles": the fused sweep's
+        # tile shape from ehdg_autotune_sweep_tile
         base, _, opt = prec.partition("+")
         kw = dict(pde=wl.pde, scheme=wl.scheme, dt=wl.dt, tol=wl.tol,
                   max_iter=20000 if wl.scheme == "steady" else 400,
@@ -463,6 +465,11 @@ def compare_workload(args):
         f_nodes = wl.forcing(X)
         if f_nodes is not None:
             s.set_forcing(np.ascontiguousarray(f_nodes))
+        tile_ft = None
+        if opt == "tiles":
+            s.set_boundary(gs[0])
+            s.set_state(u0)
+            tile_ft = s.autotune_sweep_tile()[0]
 
         def one_run():
             # graph-launched steps (the device-side loop); a transport step
@@ -495,6 +502,8 @@ def compare_workload(args):
         results[prec] = {"ms_per_run": ms, "fp64_sweeps_per_run": its,
                          "rel_l2_vs_fp64": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
                          "speedup_vs_fp64": None}
+        if tile_ft is not None:
+            results[prec]["tile_ft"] = tile_ft
         if "exact" in wl.meta:
             ue = wl.meta["exact"](X)[:, None, :]
             results[prec]["max_nodal_error_vs_exact"] = float(np.max(np.abs(u - ue)))
@@ -567,7 +576,10 @@ def batch_workload(args):
     out = {}
     # "+tuned": every instance's FP64 path (DFMA or tensor cores) picked by
     # ehdg_autotune_fp64_path before the first run
-    variants = ["fp64", "tf32", "fp64_emulated", "tf32+emulated_outer", "fp64_emulated+tuned"]
+    # "+tiles": the fused FP64 sweep's tile (row groups FT) of all instances
+    # picked by ehdg_batch_autotune_sweep_tile before the first run
+    variants = ["fp64", "tf32", "fp64_emulated", "tf32+emulated_outer", "fp64_emulated+tuned",
+                "fp64+tiles", "tf32+tiles"]
     for prec in variants:
         base, _, opt = prec.partition("+")
         specs, inputs = [], []
@@ -590,6 +602,11 @@ def batch_workload(args):
             for s, u0 in zip(b.instances, inputs):
                 s.set_state(u0)
                 n_tensor += int(s.autotune_fp64_path()[0])
+        tile_ft = None
+        if opt == "tiles":
+            for s, u0 in zip(b.instances, inputs):
+                s.set_state(u0)
+            tile_ft, _ = b.autotune_sweep_tile()
         # the graph's branch count, picked by ehdg_batch_autotune_chains
         for s, u0 in zip(b.instances, inputs):
             s.set_state(u0)
@@ -612,6 +629,8 @@ def batch_workload(args):
                      "sweeps_total": int(iters.sum()), "chains": chains}
         if n_tensor is not None:
             out[prec]["instances_on_tensor_cores"] = n_tensor
+        if tile_ft is not None:
+            out[prec]["tile_ft"] = tile_ft
         b.close()
     for prec in variants[1:]:
         out[prec]["speedup_vs_fp64"] = out["fp64"]["wall_s"] / out[prec]["wall_s"]

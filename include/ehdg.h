@@ -230,6 +230,19 @@ ehdg_status ehdg_autotune_inner_sweeps(ehdg_ctx ctx, const int* candidates, int 
  * tensor-core path. The paper has no counterpart. */
 ehdg_status ehdg_autotune_fp64_path(ehdg_ctx ctx, int* tensor_cores, double* ms_dfma,
                                     double* ms_tensor);
+/* Autotuner for the tile shape of the fused FP64 transport sweep (shared
+ * operator, or a per-element operator without a tiled kernel; also the outer
+ * sweeps of mixed precision): each 32-element tile is worked by 32 x FT
+ * threads, FT row groups. Candidates are FT values (2, 4 or 8; others are
+ * skipped). Runs one implicit step from the current state per candidate
+ * (restoring the state after each), keeps the fastest, and reports it with
+ * its time; the state is left as it was. Every row is one thread's FMA chain
+ * for any FT, so the iterates do not change, only the summation order of the
+ * residual. A batch recaptures its graph after the choice changed.
+ * EHDG_ERR_INVALID for a context whose FP64 sweep is another kernel (shallow
+ * water, the tiled per-element sweep, the tensor-core FP64 path). */
+ehdg_status ehdg_autotune_sweep_tile(ehdg_ctx ctx, const int* candidates, int n_candidates,
+                                     int* best_ft, double* best_ms);
 /* Residual history r_0, r_1, ... of the last step (host buffer of cap entries). */
 ehdg_status ehdg_get_residual_history(ehdg_ctx ctx, double* buf, int64_t cap, int64_t* n_out);
 
@@ -266,6 +279,13 @@ ehdg_status ehdg_batch_set_chains(ehdg_batch b, int k);
  * they were. EHDG_ERR_INVALID for a NULL batch or no candidates. */
 ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* candidates, int n_candidates,
                                        int* best, double* best_ms);
+/* Autotuner for the tile shape (FT, as in ehdg_autotune_sweep_tile) of every
+ * instance's fused FP64 sweep together, timed as whole batch steps: instances
+ * that share the GPU favour other shapes than one instance alone. Same
+ * protocol as ehdg_batch_autotune_chains; instances whose sweep is another
+ * kernel are unaffected. EHDG_ERR_INVALID for a NULL batch or no candidates. */
+ehdg_status ehdg_batch_autotune_sweep_tile(ehdg_batch b, const int* candidates, int n_candidates,
+                                           int* best_ft, double* best_ms);
 void ehdg_batch_destroy(ehdg_batch b);
 
 /* FP64 residual of Algorithm 1's convergence check (Sec. 3, "check

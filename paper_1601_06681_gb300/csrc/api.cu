@@ -1356,10 +1356,14 @@ ehdg_status ehdg_batch_set_chains(ehdg_batch b, int k) {
   return EHDG_OK;
 }
 
-ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* cands, int n_cands, int* best,
-                                       double* best_ms) {
-  if (!b || !cands || n_cands < 1) return fail(EHDG_ERR_INVALID, "bad argument");
-  // snapshot of every instance's stepping state
+}  // extern "C"
+
+// One batch step (graph launch) from the instances' current states per
+// variant (apply(k) configures variant k, false skips it), every state
+// restored after each; ms[k] is the second of two steps (the first captures
+// the graph), or 1e300 for a skipped variant.
+template <class Apply>
+static ehdg_status batch_time_variants(ehdg_batch b, int n, Apply apply, double* ms) {
   std::vector<std::pair<void*, size_t>> arrays;
   for (auto h : b->inst)
     for (auto& a : state_arrays(h->c)) arrays.push_back(a);
@@ -1386,14 +1390,10 @@ ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* cands, int n_can
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int saved = b->chains;
-  int best_k = saved;
-  double best_t = 1e300;
   ehdg_status st = EHDG_OK;
-  for (int q = 0; q < n_cands && st == EHDG_OK; ++q) {
-    b->chains = cands[q];
-    // the first run captures the graph (and may recapture it on measured
-    // iteration counts); the second is timed
+  for (int q = 0; q < n; ++q) {
+    ms[q] = 1e300;
+    if (st != EHDG_OK || !apply(q)) continue;
     for (int rep = 0; rep < 2 && st == EHDG_OK; ++rep) {
       if (rep == 0) batch_destroy_graph(b);
       cudaEventRecord(e0, b->stream);
@@ -1403,19 +1403,78 @@ ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* cands, int n_can
       float t = 0.f;
       cudaEventElapsedTime(&t, e0, e1);
       if (restore() != cudaSuccess && st == EHDG_OK) st = cuda_fail(cudaGetLastError(), "restore");
-      if (rep == 1 && st == EHDG_OK && t < best_t) {
-        best_t = t;
-        best_k = cands[q];
-      }
+      if (rep == 1 && st == EHDG_OK) ms[q] = t;
     }
   }
   free_snap();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  b->chains = (st == EHDG_OK) ? best_k : saved;
   batch_destroy_graph(b);
+  return st;
+}
+
+static int fastest(const int* cands, const double* ms, int n, int fallback, double* best_ms) {
+  int best = fallback;
+  double t = 1e300;
+  for (int q = 0; q < n; ++q)
+    if (ms[q] < t) {
+      t = ms[q];
+      best = cands[q];
+    }
+  if (best_ms) *best_ms = t;
+  return best;
+}
+
+extern "C" {
+
+ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* cands, int n_cands, int* best,
+                                       double* best_ms) {
+  if (!b || !cands || n_cands < 1) return fail(EHDG_ERR_INVALID, "bad argument");
+  const int saved = b->chains;
+  std::vector<double> ms((size_t)n_cands);
+  const ehdg_status st = batch_time_variants(
+      b, n_cands,
+      [&](int q) {
+        b->chains = cands[q];
+        return true;
+      },
+      ms.data());
+  b->chains = (st == EHDG_OK) ? fastest(cands, ms.data(), n_cands, saved, best_ms) : saved;
   if (best) *best = b->chains;
-  if (best_ms) *best_ms = best_t;
+  return st;
+}
+
+ehdg_status ehdg_batch_autotune_sweep_tile(ehdg_batch b, const int* cands, int n_cands, int* best,
+                                           double* best_ms) {
+  if (!b || !cands || n_cands < 1) return fail(EHDG_ERR_INVALID, "bad argument");
+  const int n = (int)b->inst.size();
+  std::vector<int> saved(n);
+  for (int i = 0; i < n; ++i) saved[i] = b->inst[i]->c.sweep_ft;
+  auto set_all = [&](int ft) {
+    for (auto h : b->inst) {
+      if (h->c.sweep_ft != ft) ++h->c.path_gen;
+      h->c.sweep_ft = ft;
+    }
+  };
+  std::vector<double> ms((size_t)n_cands);
+  const ehdg_status st = batch_time_variants(
+      b, n_cands,
+      [&](int q) {
+        if (cands[q] != 2 && cands[q] != 4 && cands[q] != 8) return false;
+        set_all(cands[q]);
+        return true;
+      },
+      ms.data());
+  if (st == EHDG_OK) {
+    const int ft = fastest(cands, ms.data(), n_cands, saved[0], best_ms);
+    set_all(ft);
+    if (best) *best = ft;
+  } else {
+    for (int i = 0; i < n; ++i) {
+      ++b->inst[i]->c.path_gen;
+      b->inst[i]->c.sweep_ft = saved[i];
+    }
+  }
   return st;
 }
 

@@ -283,3 +283,35 @@ extern "C" ehdg_status ehdg_autotune_fp64_path(ehdg_ctx h, int* tensor_cores, do
   if (ms_tensor) *ms_tensor = ms[1];
   return st;
 }
+
+extern "C" ehdg_status ehdg_autotune_sweep_tile(ehdg_ctx h, const int* cands, int n, int* best,
+                                                double* best_ms) {
+  if (!h || !cands || n < 1) return io_fail(EHDG_ERR_INVALID, "bad argument");
+  Ctx& c = h->c;
+  if (c.pde != EHDG_TRANSPORT || c.Hyt || c.use_ozaki)
+    return io_fail(EHDG_ERR_INVALID,
+                   "the context's FP64 sweep has no tile choice (it is not the fused transport "
+                   "sweep)");
+  const int saved = c.sweep_ft;
+  std::vector<double> ms((size_t)n);
+  const ehdg_status st = time_step_variants(
+      h, n,
+      [&](int k) {
+        if (cands[k] != 2 && cands[k] != 4 && cands[k] != 8) return false;
+        c.sweep_ft = cands[k];
+        return true;
+      },
+      ms.data());
+  int best_ft = saved;
+  double best_t = 1e300;
+  for (int k = 0; k < n; ++k)
+    if (ms[k] < best_t) {
+      best_t = ms[k];
+      best_ft = cands[k];
+    }
+  c.sweep_ft = (st == EHDG_OK) ? best_ft : saved;
+  ++c.path_gen;   // a batch recaptures its graph
+  if (best) *best = c.sweep_ft;
+  if (best_ms) *best_ms = best_t;
+  return st;
+}

@@ -144,6 +144,7 @@ struct Ctx {
     size_t smem = 0;
   } oz_sweep, oz_final, oz_step;
   int inner_sweeps = 0;
+  int sweep_ft = 4;              // row groups per 32-element tile of k_sweep_fused (2, 4 or 8)
   float* Hy32 = nullptr;         // FP32 copy of Hy in the sweep's slot layout
   float* R32 = nullptr;          // [Nqf][nface] FP64 residual F(uhat) - uhat, rounded
   float* d32 = nullptr;          // [2][Nqf][nface] correction iterates

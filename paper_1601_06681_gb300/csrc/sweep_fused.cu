@@ -18,7 +18,6 @@ namespace ehdg {
 
 namespace {
 
-constexpr int kFT = 4;                 // row groups per 32-element tile
 constexpr int kFusedMaxBlocks = 4096;
 
 struct FusedParams {
@@ -46,8 +45,11 @@ struct FusedParams {
   cudaGraphConditionalHandle handle;
 };
 
-template <int NQ>
-__global__ void __launch_bounds__(32 * kFT, 4) k_sweep_fused(const FusedParams p) {
+// FT: row groups per 32-element tile (the block is 32 x FT threads); each row
+// of an element is one thread's FMA chain whatever FT is, so the sweep's
+// values do not depend on it (only the residual's summation order does).
+template <int NQ, int FT>
+__global__ void __launch_bounds__(32 * FT, 16 / FT) k_sweep_fused(const FusedParams p) {
   extern __shared__ double sm[];
   const int nq = NQ > 0 ? NQ : p.NQFS;
   const int lane = threadIdx.x, t = threadIdx.y;
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(32 * kFT, 4) k_sweep_fused(const FusedParams p
   double* uh = sm + (p.shared ? nq * nq : 0);            // [nq][32]
   int* fid = reinterpret_cast<int*>(uh + nq * 32);        // [F][32]
   if (p.shared)
-    for (int i = t * 32 + lane; i < nq * nq; i += 32 * kFT) Hsh[i] = p.Hy[i];
+    for (int i = t * 32 + lane; i < nq * nq; i += 32 * FT) Hsh[i] = p.Hy[i];
   const int64_t ne = p.nel, nface = p.nface;
   const int kk = p.it->k;                                 // read before the last block advances it
   const int64_t tlen = (int64_t)p.Nqf * nface;
@@ -67,11 +69,11 @@ __global__ void __launch_bounds__(32 * kFT, 4) k_sweep_fused(const FusedParams p
     const int64_t e = tile * 32 + lane;
     __syncthreads();                                      // previous tile done with uh/fid
     if (e < ne) {
-      for (int f = t; f < p.F; f += kFT) fid[f * 32 + lane] = p.elem_face[f * ne + e];
+      for (int f = t; f < p.F; f += FT) fid[f * 32 + lane] = p.elem_face[f * ne + e];
     }
     __syncthreads();
     if (e < ne) {
-      for (int i = t; i < nq; i += kFT) {
+      for (int i = t; i < nq; i += FT) {
         const int f = i / p.Nqf, g = i - f * p.Nqf;
         uh[i * 32 + lane] = src[g * nface + fid[f * 32 + lane]];
       }
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(32 * kFT, 4) k_sweep_fused(const FusedParams p
     if (e < ne) {
       const int nr = p.shared ? p.n_rows : p.nrows[e];
       const int nu = p.shared ? p.n_up : p.nup[e];
-      for (int j = t; j < nr; j += kFT) {
+      for (int j = t; j < nr; j += FT) {
         // two independent FMA chains (even and odd columns)
         double a0 = p.Gy[j * ne + e], a1 = 0.0;
         int r;
@@ -253,16 +255,26 @@ int one_wave_grid(K kernel, int threads, size_t smem, int64_t ntiles, int cap) {
   return g < 1 ? 1 : (int)g;
 }
 
-template <int NQ>
-static cudaError_t launch_fused_t(const FusedParams& p, size_t smem, int64_t ntiles,
-                                  cudaStream_t s, int* grid_out) {
-  cudaError_t err = cudaFuncSetAttribute(k_sweep_fused<NQ>,
+template <int NQ, int FT>
+static cudaError_t launch_fused_ft(const FusedParams& p, size_t smem, int64_t ntiles,
+                                   cudaStream_t s, int* grid_out) {
+  cudaError_t err = cudaFuncSetAttribute(k_sweep_fused<NQ, FT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
-  const int grid = one_wave_grid(k_sweep_fused<NQ>, 32 * kFT, smem, ntiles, kFusedMaxBlocks);
+  const int grid = one_wave_grid(k_sweep_fused<NQ, FT>, 32 * FT, smem, ntiles, kFusedMaxBlocks);
   *grid_out = grid;
-  k_sweep_fused<NQ><<<grid, dim3(32, kFT), smem, s>>>(p);
+  k_sweep_fused<NQ, FT><<<grid, dim3(32, FT), smem, s>>>(p);
   return cudaGetLastError();
+}
+
+template <int NQ>
+static cudaError_t launch_fused_t(const FusedParams& p, size_t smem, int64_t ntiles, int ft,
+                                  cudaStream_t s, int* grid_out) {
+  switch (ft) {
+    case 2: return launch_fused_ft<NQ, 2>(p, smem, ntiles, s, grid_out);
+    case 8: return launch_fused_ft<NQ, 8>(p, smem, ntiles, s, grid_out);
+    default: return launch_fused_ft<NQ, 4>(p, smem, ntiles, s, grid_out);
+  }
 }
 
 cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
@@ -306,17 +318,17 @@ cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
   } else if (c.Hyt) {
     err = launch_sweep_tiled(c, graph_mode, &grid);
   } else switch (c.NQFS) {
-    case 8: err = launch_fused_t<8>(p, smem, ntiles, c.stream, &grid); break;
-    case 12: err = launch_fused_t<12>(p, smem, ntiles, c.stream, &grid); break;
-    case 16: err = launch_fused_t<16>(p, smem, ntiles, c.stream, &grid); break;
-    case 20: err = launch_fused_t<20>(p, smem, ntiles, c.stream, &grid); break;
-    case 24: err = launch_fused_t<24>(p, smem, ntiles, c.stream, &grid); break;
-    case 28: err = launch_fused_t<28>(p, smem, ntiles, c.stream, &grid); break;
-    case 36: err = launch_fused_t<36>(p, smem, ntiles, c.stream, &grid); break;
-    case 40: err = launch_fused_t<40>(p, smem, ntiles, c.stream, &grid); break;
-    case 54: err = launch_fused_t<54>(p, smem, ntiles, c.stream, &grid); break;
-    case 96: err = launch_fused_t<96>(p, smem, ntiles, c.stream, &grid); break;
-    default: err = launch_fused_t<0>(p, smem, ntiles, c.stream, &grid); break;
+    case 8: err = launch_fused_t<8>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
+    case 12: err = launch_fused_t<12>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
+    case 16: err = launch_fused_t<16>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
+    case 20: err = launch_fused_t<20>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
+    case 24: err = launch_fused_t<24>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
+    case 28: err = launch_fused_t<28>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
+    case 36: err = launch_fused_t<36>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
+    case 40: err = launch_fused_t<40>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
+    case 54: err = launch_fused_t<54>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
+    case 96: err = launch_fused_t<96>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
+    default: err = launch_fused_t<0>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
   }
   if (err != cudaSuccess || c.n_tan == 0) return err;
   TangentParams q;

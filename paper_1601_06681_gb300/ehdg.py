@@ -90,6 +90,8 @@ _SIGS = [
                                           C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("ehdg_autotune_inner_sweeps", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
                                              C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    ("ehdg_autotune_sweep_tile", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
+                                           C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_set_profiling", C.c_int, [C.c_void_p, C.c_int]),
     ("ehdg_selftest_wait_timeout", C.c_int, [C.c_int, C.c_void_p]),
     ("ehdg_kernel_stats", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64),
@@ -101,6 +103,8 @@ _SIGS = [
     ("ehdg_batch_set_chains", C.c_int, [C.c_void_p, C.c_int]),
     ("ehdg_batch_autotune_chains", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
                                              C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    ("ehdg_batch_autotune_sweep_tile", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
+                                                 C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_batch_destroy", None, [C.c_void_p]),
     ("ehdg_trace_residual", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                       C.c_void_p]),
@@ -362,6 +366,15 @@ class Solver:
         _check(load().ehdg_autotune_fp64_path(self._h, C.byref(tc), C.byref(md), C.byref(mt)))
         return bool(tc.value), md.value, mt.value
 
+    def autotune_sweep_tile(self, candidates=(2, 4, 8)):
+        """Row groups per 32-element tile of the fused FP64 sweep, timed one
+        step each from the current state (restored): (best FT, ms)."""
+        arr = (C.c_int * len(candidates))(*[int(k) for k in candidates])
+        best, ms = C.c_int(), C.c_double()
+        _check(load().ehdg_autotune_sweep_tile(self._h, arr, len(candidates), C.byref(best),
+                                               C.byref(ms)))
+        return best.value, ms.value
+
     def autotune_inner_sweeps(self, candidates=(2, 3, 4, 6, 8, 12)):
         """Fastest inner sweep count for one step from the current state (which
         is restored); the context keeps it. Returns (best, ms)."""
@@ -468,6 +481,15 @@ class Batch:
         best, ms = C.c_int(), C.c_double()
         _check(load().ehdg_batch_autotune_chains(self._h, arr, len(candidates), C.byref(best),
                                                  C.byref(ms)))
+        return best.value, ms.value
+
+    def autotune_sweep_tile(self, candidates=(2, 4, 8)):
+        """One tile shape FT for every instance's fused FP64 sweep, timed as
+        whole batch steps from the current states (restored): (FT, ms)."""
+        arr = (C.c_int * len(candidates))(*[int(k) for k in candidates])
+        best, ms = C.c_int(), C.c_double()
+        _check(load().ehdg_batch_autotune_sweep_tile(self._h, arr, len(candidates),
+                                                     C.byref(best), C.byref(ms)))
         return best.value, ms.value
 
     def close(self):

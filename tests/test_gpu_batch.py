@@ -115,3 +115,23 @@ def test_chain_autotuner_keeps_states_and_results(ehdg):
     assert np.array_equal(iters, ref_iters)
     for (u, uh), (ru, ruh) in zip(states, ref_states):
         assert np.array_equal(u, ru) and np.array_equal(uh, ruh)
+
+
+def test_batch_tile_autotuner_keeps_states_and_results(ehdg):
+    inst = instances(n=7, seed=7)
+    ref_iters, ref_states, _ = run_batch(ehdg, inst, 2)
+    with ehdg.Batch([kw for kw, _, _, _ in inst]) as b:
+        for (kw, prob, u0, g), s in zip(inst, b.instances):
+            s.set_boundary(g)
+            s.set_state(u0)
+        before = [s.get_state() for s in b.instances]
+        ft, ms = b.autotune_sweep_tile((2, 8))
+        assert ft in (2, 8) and 0 < ms < 1e300
+        for (u0_, uh0_), s in zip(before, b.instances):
+            u1_, uh1_ = s.get_state()
+            assert np.array_equal(u0_, u1_) and np.array_equal(uh0_, uh1_)
+        iters, _ = b.run(2)
+        states = [s.get_state() for s in b.instances]
+    assert np.array_equal(iters, ref_iters)
+    for (u, uh), (ru, ruh) in zip(states, ref_states):
+        assert np.array_equal(u, ru) and np.array_equal(uh, ruh)

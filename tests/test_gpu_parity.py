@@ -83,6 +83,12 @@ def make_case(name):
         X = node_coords(mesh, p)
         b = np.stack([0.6 + 0.2 * X[..., 1], -0.5 + 0.3 * X[..., 2], 0.4 + 0.2 * X[..., 0]], -1)
         kw = dict(scheme="be", dt=0.05, beta_nodes=np.ascontiguousarray(np.transpose(b, (0, 2, 1))))
+    elif name == "3d_be_variable_p2":
+        # per-node velocity with 5x5 points per face: the fused per-element sweep
+        mesh, p = W.structured_mesh((4, 3, 3)), 2
+        X = node_coords(mesh, p)
+        b = np.stack([0.6 + 0.2 * X[..., 1], -0.5 + 0.3 * X[..., 2], 0.4 + 0.2 * X[..., 0]], -1)
+        kw = dict(scheme="be", dt=0.05, beta_nodes=np.ascontiguousarray(np.transpose(b, (0, 2, 1))))
     elif name == "3d_be_const":
         mesh, p = W.structured_mesh((6, 5, 4)), 2
         kw = dict(scheme="be", dt=0.05, beta_const=np.array([1.0, 1.0, 1.0]) / np.sqrt(3.0))
@@ -580,3 +586,44 @@ def test_fp64_path_autotuner_keeps_state_and_results(ehdg, name):
         with pytest.raises(ehdg.EhdgError) as ei:
             s.autotune_fp64_path()
         assert ei.value.status == 1
+
+
+# the tile-shape autotuner of the fused FP64 sweep: FT row groups per 32-element
+# tile change which thread runs which row, not the rows' arithmetic
+@pytest.mark.parametrize("name", ["2d_be_const", "3d_be_variable_p2", "2d_be_zero_component"])
+def test_sweep_tile_choice_keeps_iterates_bitwise(ehdg, name):
+    mesh, p, kw, prob, u0, g = make_case(name)
+    states = []
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        for ft in (2, 4, 8):
+            s.set_boundary(g)
+            s.set_state(u0)
+            before = s.get_state()
+            best, ms = s.autotune_sweep_tile((ft,))
+            assert best == ft and ms > 0
+            after = s.get_state()
+            assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+            s.step_fixed(5)
+            states.append(s.get_state())
+        best, _ = s.autotune_sweep_tile()
+        assert best in (2, 4, 8)
+        s.set_boundary(g)
+        s.set_state(u0)
+        iters = s.run(2)
+        u, uh = s.get_state()
+    for a, b in zip(states[1:], states[:-1]):
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    ou, ouh, oiters, _ = prob.run(u0, 2, g_of_t=lambda t: g, tol=1e-10)
+    assert iters == oiters
+    assert rel(u, ou) < RTOL
+    assert rel(uh, ouh) < RTOL
+
+
+def test_sweep_tile_autotuner_rejects_other_sweeps(ehdg):
+    # shallow water; the tiled per-element sweeps of quadrilaterals and of 2x2-point hexahedra
+    for name in ("sw_be", "2d_cn_variable", "3d_be_variable"):
+        mesh, p, kw, prob, u0, g = make_case(name)
+        with make_solver(ehdg, mesh, p, kw, prob) as s:
+            with pytest.raises(ehdg.EhdgError) as ei:
+                s.autotune_sweep_tile()
+            assert ei.value.status == 1
