@@ -484,20 +484,21 @@ __global__ void __launch_bounds__(32 * kStepT) k_step(const StepParams s) {
     }
     __syncthreads();
     if (!live) continue;
-    // initial-trace input: element values at every face point
-    for (int r = t; r < s.NQFS; r += kStepT) {
-      double y0 = 0.0;
-      for (int k2 = 0; k2 < s.KE; ++k2)
-        y0 += s.ey_val[r * s.KE + k2] * s.u[s.ey_idx[r * s.KE + k2] * ne + e];
-      s.Y[r * ne + e] = y0;
-    }
-    // Gy in the sweep's slot order (only the rows the sweep computes)
+    // the rows the sweep computes (upwind and tangential points; every point
+    // for shallow water): Gy in the sweep's slot order, and the element
+    // values Y0 = Ey u^n there, which are all the initial trace reads (it
+    // takes the upwind side, or both sides of a tangential point)
     const int nr = s.shared ? s.n_rows : s.nrows[e];
     for (int j = t; j < nr; j += kStepT) {
       const int r = s.shared ? s.rows[j] : s.rowid[j * ne + e];
-      double gy = 0.0;
-      for (int k2 = 0; k2 < s.KE; ++k2)
-        gy += s.ey_val[r * s.KE + k2] * g[s.ey_idx[r * s.KE + k2] * 32 + lane];
+      double y0 = 0.0, gy = 0.0;
+      for (int k2 = 0; k2 < s.KE; ++k2) {
+        const double w = s.ey_val[r * s.KE + k2];
+        const int i = s.ey_idx[r * s.KE + k2];
+        y0 = fma(w, s.u[i * ne + e], y0);
+        gy = fma(w, g[i * 32 + lane], gy);
+      }
+      s.Y[r * ne + e] = y0;
       s.Gy[j * ne + e] = gy;
     }
   }
@@ -736,7 +737,9 @@ struct FaceParams {
 };
 
 constexpr int kFaceBlock = 256;
-constexpr int kFaceMaxBlocks = 2432;   // 16 per SM
+// one wave: 4 resident 256-thread blocks per SM; each thread strides over
+// several faces, so the reduction's adds are spread over more points
+constexpr int kFaceMaxBlocks = 608;
 
 // Grid: x strides over faces, y = face point. Block partials are reduced in a
 // fixed order by the last block to finish (deterministic).
@@ -782,8 +785,9 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
       uh = (ep >= 0) ? ym + p.Y[ym_off + (int64_t)fpl * p.Nqf * nel + ep] : 2.0 * ym;
     }
     if (p.mode == kFaceIterate) {
+      // the point weight wg is the block's; it multiplies the sum once below
       const double d = uh - uh_old[face];
-      acc += p.geo.face_jf[face] * wg * d * d;
+      acc = fma(p.geo.face_jf[face] * d, d, acc);
       if (p.R_out) p.R_out[(int64_t)gf * nface + face] = (float)d;
     } else {
       uh_new[total + face] = uh;     // both slots: points no sweep rewrites keep this value
@@ -795,7 +799,7 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
   // deterministic reduction: warp -> block -> partials[block] -> last block
   const unsigned int nblocks = gridDim.x * gridDim.y;
   const unsigned int bid = blockIdx.y * gridDim.x + blockIdx.x;
-  acc = warp_sum(acc);
+  acc = warp_sum(acc * wg);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) red[wid] = acc;
   __syncthreads();
