@@ -74,6 +74,42 @@ __device__ __forceinline__ void store_elem(unsigned char* base, int row, int k, 
   }
 }
 
+// A's half H (K range [H Kp/2, (H+1) Kp/2)) of one element, when the faces F_
+// and face points NQF are compile-time constants: after unrolling, every face
+// and point index below is a constant, so each value costs one load from a
+// register face id plus a constant point offset.
+template <int F_, int NQF, int BF16, int H>
+__device__ __forceinline__ void tc_gather_fixed(unsigned char* As, uint32_t rowoff,
+                                                const float* in, const int* fid, int row,
+                                                int64_t nface, bool live) {
+  constexpr int NQFS = F_ * NQF;
+  constexpr int KSTEP = BF16 ? 16 : 8;                 // elements per 32-byte MMA K step
+  constexpr int KP = (NQFS + KSTEP - 1) / KSTEP * KSTEP;
+  constexpr int KHALF = KP / 2;
+  constexpr int K0 = H * KHALF;
+  constexpr int CH = BF16 ? 8 : 4;                     // values per 16-byte chunk
+  constexpr int F0 = K0 / NQF;
+  constexpr int NF = (K0 + KHALF - 1) / NQF - F0 + 1;  // faces this half touches
+  static_assert(KHALF % CH == 0, "whole chunks per half");
+  int fr[NF];
+#pragma unroll
+  for (int m = 0; m < NF; ++m) fr[m] = (live && F0 + m < F_) ? fid[(F0 + m) * kTcM + row] : 0;
+#pragma unroll
+  for (int c = 0; c < KHALF / CH; ++c) {
+    float v[CH];
+#pragma unroll
+    for (int q = 0; q < CH; ++q) {
+      const int k = K0 + c * CH + q;
+      const int f = k / NQF, g = k - (k / NQF) * NQF;
+      v[q] = (live && k < NQFS) ? in[(int64_t)g * nface + fr[f - F0]] : 0.f;
+    }
+    store_chunk(As + rowoff + (uint32_t)((K0 + c * CH) / CH) * 128u, v, CH, BF16);
+  }
+}
+
+// F_, NQF > 0: faces and face points per face known at compile time, with
+// BF16 the operand format; F_ = NQF = 0: the general form (format from p.bf16).
+template <int F_, int NQF, int BF16>
 __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar;
@@ -129,7 +165,13 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
     if (e < ne)
       for (int f = half; f < p.F; f += 2) fid[f * kTcM + row] = p.elem_face[f * ne + e];
     __syncthreads();
-    {
+    if constexpr (NQF > 0) {
+      const uint32_t rowoff = (uint32_t)(row >> 3) * sbo + (uint32_t)(row & 7) * 16u;
+      if (half == 0)
+        tc_gather_fixed<F_, NQF, BF16, 0>(As, rowoff, p.in, fid, row, nface, e < ne);
+      else
+        tc_gather_fixed<F_, NQF, BF16, 1>(As, rowoff, p.in, fid, row, nface, e < ne);
+    } else {
       const uint32_t rowoff = (uint32_t)(row >> 3) * sbo + (uint32_t)(row & 7) * 16u;
       const int khalf = p.Kp / 2;                        // a multiple of the chunk size
       const int kbeg = half * khalf, kend = kbeg + khalf;
@@ -257,6 +299,35 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
                  "r"(p.ncols));
 }
 
+// The kernel of a face shape: quadrilaterals with 2..7 points per edge and
+// hexahedra with 2x2, 3x3 or 4x4 points per face have a compile-time form.
+using TcKernel = void (*)(const TcParams);
+template <int F_, int NQF>
+TcKernel tc_pick(int bf16) {
+  return bf16 ? k_sweep_tc<F_, NQF, 1> : k_sweep_tc<F_, NQF, 0>;
+}
+TcKernel tc_kernel(int F, int Nqf, int bf16) {
+  if (F == 4) {
+    switch (Nqf) {
+      case 2: return tc_pick<4, 2>(bf16);
+      case 3: return tc_pick<4, 3>(bf16);
+      case 4: return tc_pick<4, 4>(bf16);
+      case 5: return tc_pick<4, 5>(bf16);
+      case 6: return tc_pick<4, 6>(bf16);
+      case 7: return tc_pick<4, 7>(bf16);
+      default: break;
+    }
+  } else if (F == 6) {
+    switch (Nqf) {
+      case 4: return tc_pick<6, 4>(bf16);
+      case 9: return tc_pick<6, 9>(bf16);
+      case 16: return tc_pick<6, 16>(bf16);
+      default: break;
+    }
+  }
+  return k_sweep_tc<0, 0, 0>;
+}
+
 }  // namespace
 
 bool tc_supported(const Ctx& c) {
@@ -295,11 +366,12 @@ cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
   const int esize = p.bf16 ? 2 : 4;
   const size_t smem = (size_t)(p.Np + kTcM) * p.Kp * esize +
                       sizeof(int) * ((size_t)c.F * kTcM + 2 * (size_t)p.Np) + 1024;
+  void (*kern)(const TcParams) = tc_kernel(c.F, c.Nqf, p.bf16);
   cudaError_t err =
-      cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
   // favour shared memory over L1 so several tiles' blocks fit per SM
-  err = cudaFuncSetAttribute(k_sweep_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
   if (err != cudaSuccess) return err;
   // resident blocks per SM: shared memory (227 KB per SM usable) and TMEM (512 columns)
   int bpsm = (int)((227 * 1024) / (smem + 1024));
@@ -309,7 +381,7 @@ cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
   const int64_t ntiles = (c.nel + kTcM - 1) / kTcM;
   int64_t grid = (int64_t)bpsm * device_sms();
   if (grid > ntiles) grid = ntiles;
-  k_sweep_tc<<<(int)grid, kTcThreads, smem, c.stream>>>(p);
+  kern<<<(int)grid, kTcThreads, smem, c.stream>>>(p);
   return cudaGetLastError();
 }
 
