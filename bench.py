@@ -54,7 +54,10 @@ def parse():
                              "steady2d", "batch", "residual"],
                     help="transport2d_varbeta is the benchmark; the others print a "
                          "time-to-tolerance comparison of FP64 and mixed precision")
-    ap.add_argument("--inner-sweeps", type=int, default=8)
+    ap.add_argument("--inner-sweeps", type=int, default=8,
+                    help="inner sweeps m of mixed precision (the benchmark workload tunes m "
+                         "per precision unless --no-tune-inner)")
+    ap.add_argument("--no-tune-inner", dest="tune_inner", action="store_false")
     ap.add_argument("--host-loop", action="store_true",
                     help="comparison workloads: host-driven steps (one launch per kernel, "
                          "visible to ncu) instead of graph-launched steps")
@@ -342,13 +345,18 @@ def run_ours(args):
     u_fp64, _ = solver.get_state()
     mixed = None
     if not args.no_mixed:
-        mixed = {"inner_sweeps": args.inner_sweeps, "fp64_ms_per_run": t_max / args.steps}
+        mixed = {"fp64_ms_per_run": t_max / args.steps}
         for prec in ("fp32", "bf16"):
             ms_solver = ehdg.Solver(mesh, wl.p, scheme=wl.scheme, dt=wl.dt, tol=wl.tol,
                                     max_iter=200, beta_nodes=_beta_nodes(ehdg, mesh, wl),
                                     precision=prec, inner_sweeps=args.inner_sweeps, stream=stream)
             ms_solver.set_boundary(g_d)
             ms_solver.set_state(u0_d)
+            # the inner sweep count m from ehdg_autotune_inner_sweeps (one timed
+            # step per candidate from the initial state, which is restored)
+            m_best = args.inner_sweeps
+            if args.tune_inner:
+                m_best, _ = ms_solver.autotune_inner_sweeps((4, 6, 8, 12, 16, 24))
             ms_solver.run(wl.n_steps)                      # warm-up
             torch.cuda.synchronize()
             m0 = torch.cuda.Event(enable_timing=True)
@@ -365,6 +373,7 @@ def run_ours(args):
             mixed[prec] = {
                 "precision": f"{prec} operator in the correction sweeps (FP32 arithmetic) "
                              "+ fp64 defect correction",
+                "inner_sweeps": m_best,
                 "ms_per_run": mms, "speedup_time_to_tol": (t_max / args.steps) / mms,
                 "fp64_sweeps_per_run": mit / args.steps,
                 "rel_l2_vs_fp64": float(np.linalg.norm(u_mx - u_fp64) / np.linalg.norm(u_fp64))}
