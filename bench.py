@@ -538,6 +538,12 @@ def compare_workload(args):
             s.set_boundary(gs[0])
             s.set_state(u0)
             tile_ft = s.autotune_sweep_tile()[0]
+        m_best = None
+        if base in ("tf32", "bf16", "fp32") and args.tune_inner:
+            # inner sweep count from ehdg_autotune_inner_sweeps (state restored)
+            s.set_boundary(gs[0])
+            s.set_state(u0)
+            m_best = s.autotune_inner_sweeps((4, 6, 8, 12, 16, 24))[0]
 
         def one_run():
             # graph-launched steps (the device-side loop); a transport step
@@ -572,6 +578,8 @@ def compare_workload(args):
                          "speedup_vs_fp64": None}
         if tile_ft is not None:
             results[prec]["tile_ft"] = tile_ft
+        if m_best is not None:
+            results[prec]["inner_sweeps"] = m_best
         if "exact" in wl.meta:
             ue = wl.meta["exact"](X)[:, None, :]
             results[prec]["max_nodal_error_vs_exact"] = float(np.max(np.abs(u - ue)))
@@ -579,7 +587,8 @@ def compare_workload(args):
     for prec in precisions:
         results[prec]["speedup_vs_fp64"] = results["fp64"]["ms_per_run"] / results[prec]["ms_per_run"]
     info = {"workload": wl.name, "n_elem": int(np.prod(wl.n)), "p": wl.p, "dt": wl.dt,
-            "time_steps": wl.n_steps, "tol": wl.tol, "inner_sweeps": args.inner_sweeps}
+            "time_steps": wl.n_steps, "tol": wl.tol,
+            "inner_sweeps": "tuned per precision" if args.tune_inner else args.inner_sweeps}
     print(json.dumps({"metric": "time-to-tol per run, mixed vs FP64", "config": info,
                       "results": results}), flush=True)
 
