@@ -286,6 +286,13 @@ ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* candidates, int 
  * kernel are unaffected. EHDG_ERR_INVALID for a NULL batch or no candidates. */
 ehdg_status ehdg_batch_autotune_sweep_tile(ehdg_batch b, const int* candidates, int n_candidates,
                                            int* best_ft, double* best_ms);
+/* Autotuner for the inner sweep count m (1..64; others are skipped) of every
+ * mixed-precision instance together, timed as whole batch steps; same
+ * protocol as ehdg_batch_autotune_chains. FP64 instances are unaffected.
+ * EHDG_ERR_INVALID for a NULL batch, no candidates, or a batch without a
+ * mixed-precision instance. */
+ehdg_status ehdg_batch_autotune_inner_sweeps(ehdg_batch b, const int* candidates,
+                                             int n_candidates, int* best_m, double* best_ms);
 void ehdg_batch_destroy(ehdg_batch b);
 
 /* FP64 residual of Algorithm 1's convergence check (Sec. 3, "check

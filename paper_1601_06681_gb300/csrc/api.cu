@@ -1444,6 +1444,47 @@ ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* cands, int n_can
   return st;
 }
 
+ehdg_status ehdg_batch_autotune_inner_sweeps(ehdg_batch b, const int* cands, int n_cands,
+                                             int* best, double* best_ms) {
+  if (!b || !cands || n_cands < 1) return fail(EHDG_ERR_INVALID, "bad argument");
+  const int n = (int)b->inst.size();
+  std::vector<int> saved(n);
+  int n_mixed = 0;
+  for (int i = 0; i < n; ++i) {
+    saved[i] = b->inst[i]->c.inner_sweeps;
+    n_mixed += b->inst[i]->c.mixed ? 1 : 0;
+  }
+  if (n_mixed == 0) return fail(EHDG_ERR_INVALID, "no instance is mixed precision");
+  // the inner sweep count is captured into each mixed instance's step graph
+  auto set_all = [&](int m) {
+    for (auto h : b->inst)
+      if (h->c.mixed && h->c.inner_sweeps != m) {
+        h->c.inner_sweeps = m;
+        ++h->c.path_gen;
+      }
+  };
+  std::vector<double> ms((size_t)n_cands);
+  const ehdg_status st = batch_time_variants(
+      b, n_cands,
+      [&](int q) {
+        if (cands[q] < 1 || cands[q] > 64) return false;
+        set_all(cands[q]);
+        return true;
+      },
+      ms.data());
+  if (st == EHDG_OK) {
+    const int m = fastest(cands, ms.data(), n_cands, -1, best_ms);
+    if (m > 0) set_all(m);
+    if (best) *best = m;
+  } else {
+    for (int i = 0; i < n; ++i) {
+      ++b->inst[i]->c.path_gen;
+      b->inst[i]->c.inner_sweeps = saved[i];
+    }
+  }
+  return st;
+}
+
 ehdg_status ehdg_batch_autotune_sweep_tile(ehdg_batch b, const int* cands, int n_cands, int* best,
                                            double* best_ms) {
   if (!b || !cands || n_cands < 1) return fail(EHDG_ERR_INVALID, "bad argument");

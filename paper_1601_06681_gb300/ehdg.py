@@ -105,6 +105,8 @@ _SIGS = [
                                              C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_batch_autotune_sweep_tile", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
                                                  C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    ("ehdg_batch_autotune_inner_sweeps", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
+                                                   C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_batch_destroy", None, [C.c_void_p]),
     ("ehdg_trace_residual", C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
                                       C.c_void_p]),
@@ -481,6 +483,15 @@ class Batch:
         best, ms = C.c_int(), C.c_double()
         _check(load().ehdg_batch_autotune_chains(self._h, arr, len(candidates), C.byref(best),
                                                  C.byref(ms)))
+        return best.value, ms.value
+
+    def autotune_inner_sweeps(self, candidates=(2, 4, 6, 8, 12, 16)):
+        """One inner sweep count m for every mixed-precision instance, timed
+        as whole batch steps from the current states (restored): (m, ms)."""
+        arr = (C.c_int * len(candidates))(*[int(k) for k in candidates])
+        best, ms = C.c_int(), C.c_double()
+        _check(load().ehdg_batch_autotune_inner_sweeps(self._h, arr, len(candidates),
+                                                       C.byref(best), C.byref(ms)))
         return best.value, ms.value
 
     def autotune_sweep_tile(self, candidates=(2, 4, 8)):

@@ -135,3 +135,27 @@ def test_batch_tile_autotuner_keeps_states_and_results(ehdg):
     assert np.array_equal(iters, ref_iters)
     for (u, uh), (ru, ruh) in zip(states, ref_states):
         assert np.array_equal(u, ru) and np.array_equal(uh, ruh)
+
+
+def test_batch_inner_sweep_autotuner(ehdg):
+    inst = instances(n=6, seed=8)            # two of each mixed precision among them
+    with ehdg.Batch([kw for kw, _, _, _ in inst]) as b:
+        for (kw, prob, u0, g), s in zip(inst, b.instances):
+            s.set_boundary(g)
+            s.set_state(u0)
+        before = [s.get_state() for s in b.instances]
+        m, ms = b.autotune_inner_sweeps((3, 6))
+        assert m in (3, 6) and 0 < ms < 1e300
+        for (u0_, uh0_), s in zip(before, b.instances):
+            u1_, uh1_ = s.get_state()
+            assert np.array_equal(u0_, u1_) and np.array_equal(uh0_, uh1_)
+        b.run(2)
+        states = [s.get_state() for s in b.instances]
+    for (kw, prob, u0, g), (u, uh) in zip(inst, states):
+        ou, _, _, _ = prob.run(u0, 2, g_of_t=lambda t: g, tol=1e-13, max_iter=2000)
+        assert np.linalg.norm(u - ou) / np.linalg.norm(ou) < 1e-10, kw["precision"]
+    fp64_only = [dict(kw, precision="fp64", emulated_outer=False) for kw, _, _, _ in inst[:2]]
+    with ehdg.Batch(fp64_only) as b:
+        with pytest.raises(ehdg.EhdgError) as ei:
+            b.autotune_inner_sweeps((3, 6))
+        assert ei.value.status == 1
