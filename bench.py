@@ -77,6 +77,20 @@ def dist_env():
     return ws, rank, local
 
 
+def combine_ranks(ms, units, ws, device=None):
+    """Whole-job figures of ws independent replicas: the slowest rank's timed
+    milliseconds, the units all ranks processed, and their throughput."""
+    if ws <= 1:
+        return ms, units, units / (ms * 1e-3)
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
+    t_max, u_all = float(t.item()), float(u.item())
+    return t_max, u_all, u_all / (t_max * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ---------------------------------------------------------------------------
@@ -325,13 +339,7 @@ def run_ours(args):
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     launch_counts = solver.kernel_stats()
-    t_max = ms
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    units = trace_dof * iters_total
-    value = ws * units / (t_max * 1e-3)
+    t_max, _, value = combine_ranks(ms, trace_dof * iters_total, ws, dev)
 
     # per-kernel device time: the same run with every launch bracketed by
     # CUDA events on the library's stream (host-driven loop, same kernels)
@@ -392,7 +400,7 @@ def run_ours(args):
         u_out, uh_out = solver.get_state()
     torch.cuda.synchronize()
     e_s = time.perf_counter() - e0
-    e2e_value = ws * trace_dof * it_e2e / e_s
+    _, _, e2e_value = combine_ranks(e_s * 1e3, trace_dof * it_e2e, ws, dev)
 
     # roofline of the dominant kernel (the element sweep: k_sweep_persist, the
     # persistent form of k_sweep_tiled that runs a step's iterations in one

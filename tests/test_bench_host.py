@@ -26,3 +26,37 @@ def test_oracle_pool_runs_one_sample_per_process():
     # two independent copies of the same deterministic sample
     assert units == 2 * one_u[0]
     assert sample.startswith("2 processes")
+
+
+def _rank_main(rank, ws, port, out_dir):
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=ws)
+    try:
+        bench = load_bench()
+        # rank r times (r + 1) ms and processes 100 (r + 1) units
+        t_max, units, value = bench.combine_ranks(float(rank + 1), 100 * (rank + 1), ws, "cpu")
+        with open(os.path.join(out_dir, f"rank{rank}.txt"), "w") as f:
+            f.write(f"{t_max} {units} {value}\n")
+    finally:
+        dist.destroy_process_group()
+
+
+def test_combine_ranks_over_two_gloo_ranks(tmp_path):
+    """The multi-rank reduction of the benchmark (replicas: max time over
+    ranks, units summed) on world size 2 with the gloo backend."""
+    import socket
+
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    mp.start_processes(_rank_main, args=(2, port, str(tmp_path)), nprocs=2, join=True,
+                       start_method="spawn")
+    for rank in range(2):
+        t_max, units, value = map(float, open(tmp_path / f"rank{rank}.txt").read().split())
+        assert t_max == 2.0
+        assert units == 300.0
+        assert value == 300.0 / 2e-3
+    bench = load_bench()
+    assert bench.combine_ranks(4.0, 50, 1) == (4.0, 50, 50 / 4e-3)
