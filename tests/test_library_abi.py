@@ -48,3 +48,19 @@ def test_structured_mesh_rejects_bad_sizes():
         assert e.status == 1
     else:
         raise AssertionError("expected EhdgError")
+
+
+def test_new_entry_points_reject_null_handles_without_a_gpu():
+    """The batch and tile autotuners validate their arguments before any CUDA
+    call, so these return EHDG_ERR_INVALID (1) on a machine without a GPU."""
+    import ctypes as C
+    build.build()
+    lib = ehdg.load()
+    cands = (C.c_int * 2)(2, 4)
+    best, ms = C.c_int(), C.c_double()
+    assert lib.ehdg_batch_set_chains(None, 3) == 1
+    assert lib.ehdg_batch_autotune_chains(None, cands, 2, C.byref(best), C.byref(ms)) == 1
+    assert lib.ehdg_batch_autotune_sweep_tile(None, cands, 2, C.byref(best), C.byref(ms)) == 1
+    assert lib.ehdg_batch_autotune_inner_sweeps(None, cands, 2, C.byref(best), C.byref(ms)) == 1
+    assert lib.ehdg_autotune_sweep_tile(None, cands, 2, C.byref(best), C.byref(ms)) == 1
+    assert b"NULL" in lib.ehdg_last_error() or b"bad argument" in lib.ehdg_last_error()
