@@ -336,7 +336,8 @@ class Solver:
         return list(iters)[:n_steps]
 
     def get_state(self, u_out=None, uhat_out=None):
-        """Host copies (numpy) unless CUDA tensors are given to fill."""
+        """Host copies (numpy), or fills the given buffers: CUDA tensors, or
+        host arrays / CPU tensors (pinned ones copy fastest)."""
         if u_out is None and uhat_out is None:
             u = np.empty(self.state_shape)
             uh = np.empty(self.trace_shape)
