@@ -62,6 +62,9 @@ def parse():
                     help="comparison workloads: host-driven steps (one launch per kernel, "
                          "visible to ncu) instead of graph-launched steps")
     ap.add_argument("--n-inst", type=int, default=256)
+    ap.add_argument("--batch-chains", type=int, default=0,
+                    help="batch workload: fixed graph branch count k instead of "
+                         "ehdg_batch_autotune_chains")
     return ap.parse_args()
 
 
@@ -696,10 +699,14 @@ def batch_workload(args):
             for s, u0 in zip(b.instances, inputs):
                 s.set_state(u0)
             tile_ft, _ = b.autotune_sweep_tile()
-        # the graph's branch count, picked by ehdg_batch_autotune_chains
-        for s, u0 in zip(b.instances, inputs):
-            s.set_state(u0)
-        chains, _ = b.autotune_chains()
+        # the graph's branch count, picked by ehdg_batch_autotune_chains (or fixed)
+        if args.batch_chains > 0:
+            b.set_chains(args.batch_chains)
+            chains = args.batch_chains
+        else:
+            for s, u0 in zip(b.instances, inputs):
+                s.set_state(u0)
+            chains, _ = b.autotune_chains()
 
         def one_run():
             for s, u0 in zip(b.instances, inputs):
