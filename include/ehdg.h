@@ -338,6 +338,17 @@ ehdg_status ehdg_trace_residual_noalloc(const double* a, const double* b, const 
  * stream: a cudaStream_t or NULL; the call synchronises it. */
 ehdg_status ehdg_selftest_wait_timeout(int which, void* stream);
 
+/* Measured FP64 FMA rate of the current device (a diagnostic; the paper has no
+ * counterpart). Runs a kernel in which every thread carries 8 independent
+ * fma() chains, 4 blocks of 256 threads per SM, 2^14 steps per chain, on
+ * `stream` (a cudaStream_t or NULL), once to warm up and three times timed
+ * with CUDA events; *tflops receives 2 flops x FMAs / the fastest time in
+ * TFLOP/s, *sms (may be NULL) the SM count it ran on. It is the measured
+ * denominator of the FP64 sweeps' roofline. Synchronises the stream; allocates
+ * nothing. EHDG_ERR_INVALID for a NULL tflops, EHDG_ERR_CUDA if a launch or
+ * event call fails. */
+ehdg_status ehdg_probe_fp64_rate(void* stream, int* sms, double* tflops);
+
 /* Kernel accounting. Every launch is counted per kind; with profiling on,
  * each launch is also bracketed by CUDA events on the context's stream and
  * ehdg_kernel_stats returns the summed device time of the kind (it
@@ -349,8 +360,9 @@ typedef enum {
   EHDG_KERNEL_ELEM = 3,        /* element sweep Y = Gy + Hy uhat */
   EHDG_KERNEL_FACE = 4,        /* trace formula + residual */
   EHDG_KERNEL_FINAL = 5,       /* end-of-step reconstruction */
-  EHDG_KERNEL_AUX = 6,         /* transposes, extraction, resets */
-  EHDG_KERNEL_KINDS = 7
+  EHDG_KERNEL_AUX = 6,         /* transposes, extraction, resets, the mixed FP64 update */
+  EHDG_KERNEL_CORR = 7,        /* low-precision correction sweeps of mixed precision */
+  EHDG_KERNEL_KINDS = 8
 } ehdg_kernel_kind;
 ehdg_status ehdg_set_profiling(ehdg_ctx ctx, int on);
 ehdg_status ehdg_kernel_stats(ehdg_ctx ctx, int kind, int64_t* launches, double* total_ms);

@@ -208,10 +208,16 @@ ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
   }
   for (int k = 0; k < (persist ? 0 : n_it); ++k) {
     if (k > 0 && c.mixed) {
-      // low-precision correction of uhat before the next FP64 sweep
-      int nl = 0;
-      CK(counted(c, EHDG_KERNEL_AUX, 0, [&] { return launch_correction(c, &nl); }));
-      c.launches[EHDG_KERNEL_AUX] += nl;
+      // low-precision correction of uhat before the next FP64 sweep: m inner
+      // sweeps (each timed on its own with profiling on), then the FP64 update
+      const float* in = c.R32;
+      for (int j = 0; j < c.inner_sweeps; ++j) {
+        float* out = correction_out(c, j);
+        CK(counted(c, EHDG_KERNEL_CORR, lp_sweep_launches(c),
+                   [&] { return launch_lp_sweep(c, in, out); }));
+        in = out;
+      }
+      CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_apply(c, in); }));
     }
     if (c.pde == EHDG_TRANSPORT) {
       // element solve + trace formula + residual in one kernel (+ tangential points)
@@ -325,7 +331,7 @@ ehdg_status capture_step(Ctx& c, cudaStream_t s, cudaStream_t body_stream, bool 
   if (err != cudaSuccess) return cuda_fail(err, "cudaStreamBeginCaptureToGraph");
   c.stream = body_stream;
   cudaError_t e2 = cudaSuccess;
-  if (c.mixed) e2 = launch_correction(c, nullptr);
+  if (c.mixed) e2 = launch_correction(c);
   if (e2 == cudaSuccess) {
     if (c.pde == EHDG_TRANSPORT) {
       e2 = launch_sweep_fused(c, 1);
@@ -422,8 +428,8 @@ ehdg_status run_graph(Ctx& c, int n_steps, int* iters_per_step, double* res) {
   c.launches[EHDG_KERNEL_FACE] +=
       n_steps + ((c.pde == EHDG_TRANSPORT) ? (c.n_tan > 0 ? sweeps : 0) : sweeps);
   if (c.mixed) {
-    const int per_lp = 1 + ((c.pde == EHDG_TRANSPORT) ? (c.n_tan > 0 ? 1 : 0) : 1);
-    c.launches[EHDG_KERNEL_AUX] += (sweeps - n_steps) * (c.inner_sweeps * per_lp + 1);
+    c.launches[EHDG_KERNEL_CORR] += (sweeps - n_steps) * c.inner_sweeps * lp_sweep_launches(c);
+    c.launches[EHDG_KERNEL_AUX] += sweeps - n_steps;
   }
   c.last_iters = n_steps > 0 ? std::min(c.step_iters_h[n_steps - 1], c.max_iter) : 0;
   if (res) *res = c.it_host->r_last;

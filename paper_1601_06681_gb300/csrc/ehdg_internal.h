@@ -227,7 +227,11 @@ cudaError_t launch_final_tiled(Ctx& c);              // u = G + H uhat, per-elem
 cudaError_t launch_lp_sweep_tiled(Ctx& c, const float* in, float* out);   // FP32 correction sweep
 // mixed precision (mixed.cu)
 cudaError_t launch_hy_to_f32(Ctx& c);
-cudaError_t launch_correction(Ctx& c, int* n_launched);
+cudaError_t launch_correction(Ctx& c);                    // m inner sweeps + FP64 update
+cudaError_t launch_lp_sweep(Ctx& c, const float* in, float* out);   // one inner sweep
+cudaError_t launch_apply(Ctx& c, const float* delta);       // uhat += delta in FP64
+float* correction_out(Ctx& c, int j);                       // output buffer of inner sweep j
+int lp_sweep_launches(const Ctx& c);                        // kernels of one inner sweep
 // FP64-accurate tensor-core sweep (ozaki_sweep.cu)
 bool ozaki_supported(const Ctx& c);
 cudaError_t build_ozaki_operator(Ctx& c);   // after assembly and rows

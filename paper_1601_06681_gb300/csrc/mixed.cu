@@ -322,20 +322,26 @@ cudaError_t launch_apply(Ctx& c, const float* delta) {
   return cudaGetLastError();
 }
 
-// The m inner sweeps and the FP64 update; returns the number of kernels launched.
-cudaError_t launch_correction(Ctx& c, int* n_launched) {
-  int n = 0;
+// Kernels of one low-precision sweep (the element kernel plus the trace
+// kernel of tangential points or of shallow water).
+int lp_sweep_launches(const Ctx& c) {
+  return 1 + ((c.pde == EHDG_TRANSPORT) ? (c.n_tan > 0 ? 1 : 0) : 1);
+}
+
+// Output buffer of inner sweep j (the sweeps ping-pong between two buffers;
+// sweep 0 reads R).
+float* correction_out(Ctx& c, int j) { return c.d32 + (int64_t)(j & 1) * c.Nqf * c.nface; }
+
+// The m inner sweeps and the FP64 update.
+cudaError_t launch_correction(Ctx& c) {
   const float* in = c.R32;
   for (int j = 0; j < c.inner_sweeps; ++j) {
-    float* out = c.d32 + (int64_t)(j & 1) * c.Nqf * c.nface;
+    float* out = correction_out(c, j);
     cudaError_t e = launch_lp_sweep(c, in, out);
     if (e != cudaSuccess) return e;
-    n += 1 + ((c.pde == EHDG_TRANSPORT) ? (c.n_tan > 0 ? 1 : 0) : 1);
     in = out;
   }
-  cudaError_t e = launch_apply(c, in);
-  if (n_launched) *n_launched = n + 1;
-  return e;
+  return launch_apply(c, in);
 }
 
 }  // namespace ehdg

@@ -16,6 +16,13 @@ namespace ehdg {
 namespace {
 
 constexpr uint32_t kSelftestPolls = 4096;
+constexpr int kProbeChains = 8;        // independent FMA chains per thread
+constexpr int kProbeThreads = 256;
+constexpr int kProbeBlocksPerSM = 4;
+
+// written only when a chain ends on a value it cannot reach, so the chains
+// stay live without any store in practice
+__device__ double g_probe_sink;
 
 // An mbarrier that expects one arrival; none ever comes, so phase 0 never
 // completes. Both the warp-wide and the single-thread wait must give up.
@@ -39,9 +46,66 @@ __global__ void k_wait_never_barrier(unsigned int* bar, int* abort, int* flag) {
   if (threadIdx.x == 0 && !done) atomicAdd(flag, 1);
 }
 
+// n_iter steps of kProbeChains independent FP64 FMA chains per thread: the
+// chains hide the FMA latency, so the FP64 pipe runs at its issue rate.
+__global__ void __launch_bounds__(kProbeThreads) k_dfma_chains(int n_iter, double b, double c) {
+  double a[kProbeChains];
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) a[k] = 1.0 + 1e-3 * k + 1e-9 * threadIdx.x;
+#pragma unroll 4
+  for (int i = 0; i < n_iter; ++i) {
+#pragma unroll
+    for (int k = 0; k < kProbeChains; ++k) a[k] = fma(a[k], b, c);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < kProbeChains; ++k) s += a[k];
+  if (s == -1.0) g_probe_sink = s;
+}
+
 }  // namespace
 
 }  // namespace ehdg
+
+extern "C" ehdg_status ehdg_probe_fp64_rate(void* stream, int* sms, double* tflops) {
+  using namespace ehdg;
+  if (!tflops) {
+    set_last_error("ehdg_probe_fp64_rate: tflops is NULL");
+    return EHDG_ERR_INVALID;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n_sm = device_sms();
+  const int blocks = n_sm * kProbeBlocksPerSM;
+  constexpr int kIter = 1 << 14;
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaError_t e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  float best_ms = 0.f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {   // the first run warms up
+    e = cudaEventRecord(a, s);
+    if (e == cudaSuccess) {
+      k_dfma_chains<<<blocks, kProbeThreads, 0, s>>>(kIter, 0.999999999, 1e-12);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && rep > 0 && (best_ms == 0.f || ms < best_ms)) best_ms = ms;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess || !(best_ms > 0.f)) {
+    cudaGetLastError();
+    set_last_error(std::string("ehdg_probe_fp64_rate: ") +
+                   (e != cudaSuccess ? cudaGetErrorString(e) : "no timing"));
+    return EHDG_ERR_CUDA;
+  }
+  const double flops = 2.0 * kProbeChains * (double)kIter * blocks * kProbeThreads;
+  *tflops = flops / (best_ms * 1e-3) / 1e12;
+  if (sms) *sms = n_sm;
+  return EHDG_OK;
+}
 
 extern "C" ehdg_status ehdg_selftest_wait_timeout(int which, void* stream) {
   using namespace ehdg;

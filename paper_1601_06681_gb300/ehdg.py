@@ -94,6 +94,7 @@ _SIGS = [
                                            C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_set_profiling", C.c_int, [C.c_void_p, C.c_int]),
     ("ehdg_selftest_wait_timeout", C.c_int, [C.c_int, C.c_void_p]),
+    ("ehdg_probe_fp64_rate", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_kernel_stats", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64),
                                     C.POINTER(C.c_double)]),
     ("ehdg_batch_create", C.c_int, [C.c_int, C.POINTER(MeshDesc), C.POINTER(ProblemDesc),
@@ -117,7 +118,7 @@ _SIGS = [
 
 EHDG_NOALLOC_MAX_N = 16777216
 
-KERNEL_KINDS = ["assemble", "signs", "step", "elem", "face", "final", "aux"]
+KERNEL_KINDS = ["assemble", "signs", "step", "elem", "face", "final", "aux", "corr"]
 
 
 def load(path=LIB_PATH):
@@ -182,6 +183,13 @@ def ehdg_selftest_wait_timeout(which, stream=None):
     condition that never holds; returns the status (EHDG_ERR_TIMEOUT = 6 is
     the expected one)."""
     return load().ehdg_selftest_wait_timeout(int(which), _stream_ptr(stream))
+
+
+def ehdg_probe_fp64_rate(stream=None):
+    """(SM count, measured FP64 FMA rate in TFLOP/s) of the current device."""
+    sms, tf = C.c_int(), C.c_double()
+    _check(load().ehdg_probe_fp64_rate(_stream_ptr(stream), C.byref(sms), C.byref(tf)))
+    return sms.value, tf.value
 
 
 def ehdg_trace_residual_noalloc(a, b, w, out, stream=None):

@@ -16,16 +16,18 @@ def load_bench():
 
 def test_oracle_pool_runs_one_sample_per_process():
     bench = load_bench()
-    one_t, one_u, _ = bench.oracle_sample(n_side=4, n_time=1)
+    one_3d = bench.oracle_sample_3d(n_side=2, n_time=1)[1]
+    one_2d = bench.oracle_sample_2d(n_side=4, n_time=1)[1]
     pool = bench.OraclePool(cores=2)
     try:
-        wall, units, sample = pool.run(n_side=4, n_time=1)
+        wall, units, sample = pool.run("3d", n_side=2, n_time=1)
+        wall2, units2, sample2 = pool.run("2d", n_side=4, n_time=1)
     finally:
         pool.close()
-    assert wall > 0
+    assert wall > 0 and wall2 > 0
     # two independent copies of the same deterministic sample
-    assert units == 2 * one_u[0]
-    assert sample.startswith("2 processes")
+    assert units == 2 * one_3d and units2 == 2 * one_2d
+    assert sample.startswith("2 processes") and "64^3" in sample and "256x256" in sample2
 
 
 def _rank_main(rank, ws, port, out_dir):
