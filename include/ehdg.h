@@ -317,10 +317,12 @@ ehdg_status ehdg_trace_residual(const double* a, const double* b, const double* 
  * partial sums live in a fixed device array inside the library (8 KB plus a
  * ticket word, 256-byte aligned), which every GPU that loads the library holds
  * until the process exits. It calls no cudaMalloc, cudaFree or other
- * allocating routine. n may be at most EHDG_NOALLOC_MAX_N; larger n returns
+ * allocating routine. n may be at most EHDG_NOALLOC_MAX_N, a fixed limit of this
+ * entry point (the array itself does not depend on n); larger n returns
  * EHDG_ERR_UNSUPPORTED with a message. The first call on a device looks up the
- * array's device address (once per device, with that device current), so make
- * that first call before any stream capture. All calls share the one array:
+ * array's device address (once per device, with that device current) and
+ * keeps it for the life of the process, so make that first call before any
+ * stream capture; a cudaDeviceReset between calls is not supported. All calls share the one array:
  * calls that overlap on the GPU (different streams, or concurrent host threads
  * on one device) race and may return wrong results; order them on one stream. */
 #define EHDG_NOALLOC_MAX_N 16777216LL

@@ -883,6 +883,14 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
     TRYC(dalloc(c, &c.beta_nodes, (size_t)c.nel * dim * c.Np));
     CKC(cudaMemcpy(c.beta_nodes, prob->beta_nodes, sizeof(double) * c.nel * dim * c.Np,
                    cudaMemcpyHostToDevice));
+    // checkpoints identify the velocity field by this hash (FNV-1a of the bytes)
+    uint64_t hb = 1469598103934665603ull;
+    const unsigned char* bp = reinterpret_cast<const unsigned char*>(prob->beta_nodes);
+    for (size_t i = 0; i < sizeof(double) * (size_t)c.nel * dim * c.Np; ++i) {
+      hb ^= bp[i];
+      hb *= 1099511628211ull;
+    }
+    c.beta_nodes_hash = hb;
   }
   const size_t state = (size_t)c.n * c.nel, trace = (size_t)c.Nqf * c.nface;
   TRYC(dalloc(c, &c.sgn, trace));

@@ -24,20 +24,24 @@ namespace {
 constexpr uint32_t kMagic = 0x47444845u;   // "EHDG"
 constexpr uint32_t kVersion = 1;
 
-uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
-  static uint32_t table[256];
-  static bool init = false;
-  if (!init) {
+struct Crc32Table {
+  uint32_t t[256];
+  Crc32Table() {
     for (uint32_t i = 0; i < 256; ++i) {
       uint32_t c = i;
       for (int k = 0; k < 8; ++k) c = (c & 1) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
-      table[i] = c;
+      t[i] = c;
     }
-    init = true;
   }
+};
+
+uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
+  // a function-local static is initialised exactly once, thread-safely, so
+  // checkpoints of different contexts may be written from several threads
+  static const Crc32Table table;
   const unsigned char* p = static_cast<const unsigned char*>(data);
   crc = ~crc;
-  for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xFFu] ^ (crc >> 8);
+  for (size_t i = 0; i < n; ++i) crc = table.t[(crc ^ p[i]) & 0xFFu] ^ (crc >> 8);
   return ~crc;
 }
 
@@ -68,6 +72,10 @@ uint64_t config_hash(const Ctx& c) {
   const double src[4] = {c.cor_f0, c.cor_beta, c.cor_ym, c.friction};
   h = fnv1a(h, src, sizeof(src));
   h = fnv1a(h, c.beta_const, sizeof(double) * 3);
+  // the velocity field of a per-node velocity (beta_const is zero then)
+  const int vb = c.variable_beta ? 1 : 0;
+  h = fnv1a(h, &vb, sizeof(vb));
+  h = fnv1a(h, &c.beta_nodes_hash, sizeof(c.beta_nodes_hash));
   return h;
 }
 

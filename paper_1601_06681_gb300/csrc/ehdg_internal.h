@@ -75,6 +75,7 @@ struct Ctx {
   bool shared_op = false;        // one operator for all elements
   bool variable_beta = false;
   double beta_const[3] = {0, 0, 0};
+  uint64_t beta_nodes_hash = 0;  // FNV-1a of the nodal velocity (variable case), for checkpoints
   cudaStream_t stream = nullptr;
   RefTables ref{};
   Ref1D r1d;
@@ -249,6 +250,9 @@ cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out);
 enum FaceMode { kFaceInitial = 0, kFaceIterate = 1 };
 
 void set_last_error(const std::string& msg);
+// standalone weighted difference norm (residual.cu); its grid never exceeds
+// kResidMaxBlocks blocks, one partial sum each
+constexpr int kResidMaxBlocks = 1024;
 // standalone weighted difference norm (residual.cu)
 cudaError_t launch_wdiff_norm(const double* a, const double* b, const double* w, int64_t n,
                               double* partials, unsigned int* counter, double* out,

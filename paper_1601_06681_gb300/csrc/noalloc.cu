@@ -16,6 +16,8 @@
 namespace {
 
 constexpr int kNoAllocMaxBlocks = 1024;         // block partial sums held by the array
+static_assert(kNoAllocMaxBlocks >= ehdg::kResidMaxBlocks,
+              "the array must hold a partial sum for every block the residual kernel launches");
 constexpr int kNoAllocMaxDevices = 64;
 // one partial per block plus the last-block ticket
 constexpr size_t kNoAllocScratchBytes = sizeof(double) * kNoAllocMaxBlocks + 256;
@@ -27,7 +29,9 @@ void* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
 
 // Device address of the array on the current device. In host code the
 // array's name is only a host-side stand-in, so its device address is looked
-// up once per device, with that device current.
+// up once per device, with that device current, and kept for the life of the
+// process (a cudaDeviceReset between calls would leave it stale, and is not
+// supported).
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -57,7 +61,7 @@ extern "C" ehdg_status ehdg_trace_residual_noalloc(const double* a, const double
   if (n > EHDG_NOALLOC_MAX_N) {
     set_last_error("ehdg_trace_residual_noalloc: n = " + std::to_string(n) +
                    " exceeds the maximum of " + std::to_string((long long)EHDG_NOALLOC_MAX_N) +
-                   " entries supported by its fixed device scratch");
+                   " entries this allocation-free entry point accepts");
     return EHDG_ERR_UNSUPPORTED;
   }
   if (wdiff_norm_blocks(n) > kNoAllocMaxBlocks) {

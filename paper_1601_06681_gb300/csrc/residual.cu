@@ -14,7 +14,6 @@ namespace ehdg {
 namespace {
 
 constexpr int kResidBlock = 256;
-constexpr int kResidMaxBlocks = 1024;
 
 __device__ __forceinline__ double rsum_warp(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -413,6 +413,13 @@ def test_checkpoint_resume_is_bitwise(ehdg, name, tmp_path):
     with ehdg.Solver(other, p, **kw2) as s:
         with pytest.raises(ehdg.EhdgError):
             s.load_checkpoint(path)
+    # same mesh, degree and time step, another velocity field: rejected too
+    if "beta_nodes" in kw:
+        kw3 = dict(kw)
+        kw3["beta_nodes"] = np.ascontiguousarray(kw["beta_nodes"] * 1.01)
+        with ehdg.Solver(mesh, p, **kw3) as s:
+            with pytest.raises(ehdg.EhdgError):
+                s.load_checkpoint(path)
 
 
 def test_autotuner_keeps_state_and_results(ehdg, tmp_path):

@@ -531,3 +531,172 @@ def test_zero_velocity_keeps_state_and_averages_trace(dim, p):
         vm = prob.ref.fphi[int(fl[e, 0])] @ u0[fe[e, 0], 0]
         vp = prob.ref.fphi[int(fl[e, 1])] @ u0[fe[e, 1], 0] if fe[e, 1] >= 0 else g[e]
         assert np.abs(uh[e] - 0.5 * (vm + vp)).max() < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# the skeleton and volume L2 norms against exact rational integrals
+# ---------------------------------------------------------------------------
+# The convergence check of Algorithm 1 (Sec. 3) measures the trace increment
+# in the L2 norm of the skeleton E_h, and the stopping rule of the Table 1
+# runs uses the L2 norm on Omega (Sec. 2 inner products). Both are pinned
+# here against integrals of polynomials computed exactly with fractions:
+# meshes whose elements are not squares (so a face Jacobian taken from the
+# wrong axis, or the volume Jacobian in place of the face one, changes the
+# value), and polynomials the quadrature integrates exactly.
+from fractions import Fraction as Fr  # noqa: E402
+
+
+def _poly_mul(a, b):
+    out = {}
+    for ka, ca in a.items():
+        for kb, cb in b.items():
+            k = tuple(x + y for x, y in zip(ka, kb))
+            out[k] = out.get(k, Fr(0)) + ca * cb
+    return out
+
+
+def _poly_eval(poly, x):
+    """Float values of a polynomial {exponents: coefficient} at points x[..., dim]."""
+    out = np.zeros(x.shape[:-1])
+    for k, c in poly.items():
+        term = np.full(x.shape[:-1], float(c))
+        for a, e in enumerate(k):
+            term = term * x[..., a] ** e
+        out += term
+    return out
+
+
+def _int_box(poly, lo, hi, fixed=None):
+    """Exact integral of a polynomial over the box [lo, hi] (fractions); axes
+    listed in `fixed` ({axis: value}) are held at that value instead."""
+    fixed = fixed or {}
+    total = Fr(0)
+    for k, c in poly.items():
+        term = c
+        for a, e in enumerate(k):
+            if a in fixed:
+                term *= fixed[a] ** e
+            else:
+                term *= (hi[a] ** (e + 1) - lo[a] ** (e + 1)) / (e + 1)
+        total += term
+    return total
+
+
+def _skeleton_sq_exact(n, hi, poly):
+    """Exact sum over the unique faces of a structured n-box mesh of [0, hi] of
+    the integral of poly^2 over each face."""
+    dim = len(n)
+    h = [hi[a] / n[a] for a in range(dim)]
+    sq = _poly_mul(poly, poly)
+    total = Fr(0)
+    for ax in range(dim):
+        tang = [a for a in range(dim) if a != ax]
+        for plane in range(n[ax] + 1):
+            for cell in np.ndindex(*[n[t] for t in tang]):
+                lo = [Fr(0)] * dim
+                up = [Fr(0)] * dim
+                for t, i in zip(tang, cell):
+                    lo[t], up[t] = h[t] * i, h[t] * (i + 1)
+                total += _int_box(sq, lo, up, fixed={ax: h[ax] * plane})
+    return total
+
+
+_NORM_CASES = {
+    # 3 x 4 quads on [0, 3/2] x [0, 4/5] (h = 1/2, 1/5); u of degree <= 2 per axis
+    "2d": ((3, 4), (Fr(3, 2), Fr(4, 5)), 2,
+           {(0, 0): Fr(1), (1, 0): Fr(2), (0, 1): Fr(-3), (1, 1): Fr(1), (2, 0): Fr(1, 2),
+            (0, 2): Fr(-1), (2, 1): Fr(3, 4)}),
+    # 2 x 2 x 3 hexes on [0, 1] x [0, 1/2] x [0, 3/2] (h = 1/2, 1/4, 1/2)
+    "3d": ((2, 2, 3), (Fr(1), Fr(1, 2), Fr(3, 2)), 2,
+           {(0, 0, 0): Fr(1), (1, 0, 0): Fr(1), (0, 1, 0): Fr(-2), (0, 0, 1): Fr(3),
+            (1, 1, 0): Fr(1), (0, 1, 1): Fr(-1), (0, 0, 2): Fr(1, 3), (2, 0, 1): Fr(1, 2)}),
+}
+
+
+def _norm_problem(case, variable=False):
+    n, hi, p, poly = _NORM_CASES[case]
+    mesh = W.structured_mesh(n, hi=[float(v) for v in hi])
+    dim = len(n)
+    if variable:   # a per-node velocity: the quadrature has ceil(3p/2)+1 points
+        X = node_coords(mesh, p)
+        prob = Problem(mesh, p, scheme="steady",
+                       beta_nodes=beta_from(X, [X[..., a] + 0.3 for a in range(dim)]))
+    else:
+        prob = Problem(mesh, p, scheme="steady", beta_const=np.arange(1, dim + 1) / dim)
+    return prob, mesh, n, hi, p, poly
+
+
+@pytest.mark.parametrize("case,variable", [("2d", False), ("2d", True), ("3d", False),
+                                           ("3d", True)])
+def test_trace_norm_equals_exact_skeleton_integral(case, variable):
+    """||uhat||_{L2(E_h)}^2 = sum over faces of the exact integral of uhat^2."""
+    prob, mesh, n, hi, p, poly = _norm_problem(case, variable)
+    uh = _poly_eval(poly, face_point_coords(mesh, p, prob.ref.q))
+    exact = float(_skeleton_sq_exact(n, hi, poly))
+    got = prob.trace_norm(uh) ** 2
+    assert abs(got - exact) <= 1e-13 * exact, (got, exact)
+
+
+def test_trace_norm_pin_catches_planted_mistakes():
+    """The pin above fails for the plausible slips in the face weights: the
+    volume Jacobian in place of the face Jacobian, the face Jacobian from the
+    normal axis instead of the tangential one, and a dropped Gauss weight."""
+    prob, mesh, n, hi, p, poly = _norm_problem("2d")
+    uh = _poly_eval(poly, face_point_coords(mesh, p, prob.ref.q))
+    exact = float(_skeleton_sq_exact(n, hi, poly))
+    good = prob.face_w.copy()
+    h = mesh["elem_h"][mesh["face_elem"][:, 0]]             # [n_face, 2] minus element
+    ax = mesh["face_local"][:, 0].astype(int) // 2           # normal axis of each face
+    hn = h[np.arange(len(ax)), ax]                           # normal edge length
+    ht = h[np.arange(len(ax)), 1 - ax]                       # tangential edge length
+    wrong = {
+        "volume Jacobian": good * (hn / 2.0)[:, None],
+        "normal-axis face Jacobian": good * (hn / ht)[:, None],
+        "dropped Gauss weight": good / np.asarray(prob.ref.fW)[mesh["face_local"][:, 0].astype(int)],
+    }
+    for what, w in wrong.items():
+        prob.face_w = w
+        got = prob.trace_norm(uh) ** 2
+        assert abs(got - exact) > 1e-3 * exact, what
+    prob.face_w = good
+    assert abs(prob.trace_norm(uh) ** 2 - exact) <= 1e-13 * exact
+
+
+@pytest.mark.parametrize("case", ["2d", "3d"])
+def test_l2_volume_equals_exact_volume_integral(case):
+    """||u||_{L2(Omega)}^2 for u in Q^p (its nodal interpolant is exact), and
+    ||u - w||^2 for a w of higher degree, against exact integrals."""
+    prob, mesh, n, hi, p, poly = _norm_problem(case)
+    dim = len(n)
+    X = node_coords(mesh, p)
+    u = _poly_eval(poly, X)[:, None, :]
+    lo0 = [Fr(0)] * dim
+    exact = float(_int_box(_poly_mul(poly, poly), lo0, list(hi)))
+    got = l2_volume(prob, u) ** 2
+    assert abs(got - exact) <= 1e-13 * exact, (got, exact)
+    # a w of degree p + 1 in axis 0, so u - w is not in Q^p
+    w_poly = dict(poly)
+    w_poly[(p + 1,) + (0,) * (dim - 1)] = Fr(2, 3)
+    w_poly[(0,) * dim] = w_poly[(0,) * dim] + Fr(1, 7)
+    diff = {k: poly.get(k, Fr(0)) - w_poly.get(k, Fr(0)) for k in set(poly) | set(w_poly)}
+    exact_d = float(_int_box(_poly_mul(diff, diff), lo0, list(hi)))
+    got_d = l2_volume(prob, u, exact=lambda x: _poly_eval(w_poly, x)) ** 2
+    assert abs(got_d - exact_d) <= 1e-12 * exact_d, (got_d, exact_d)
+
+
+def test_l2_volume_pin_catches_planted_mistakes(monkeypatch):
+    """The volume pin fails when the quadrature weights are dropped, or scaled
+    as if the reference box had the wrong size (a wrong Jacobian)."""
+    import oracle.basis as B
+    prob, mesh, n, hi, p, poly = _norm_problem("2d")
+    u = _poly_eval(poly, node_coords(mesh, p))[:, None, :]
+    exact = float(_int_box(_poly_mul(poly, poly), [Fr(0)] * 2, list(hi)))
+    real_gauss = B.gauss
+    for what, fn in {"dropped weight": lambda q: (real_gauss(q)[0], np.ones(q)),
+                     "Jacobian off by 2 per axis": lambda q: (real_gauss(q)[0],
+                                                               2.0 * real_gauss(q)[1])}.items():
+        monkeypatch.setattr(B, "gauss", fn)
+        got = l2_volume(prob, u) ** 2
+        assert abs(got - exact) > 1e-3 * exact, what
+    monkeypatch.setattr(B, "gauss", real_gauss)
+    assert abs(l2_volume(prob, u) ** 2 - exact) <= 1e-13 * exact
