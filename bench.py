@@ -552,10 +552,27 @@ def run_2d(args, ws, dev, stream, standalone=False):
     return out
 
 
+def fp64_sweep(info):
+    """(kernel, FP64 flops one sweep executes, flops of the dense form
+    2 rows NQFS) of a transport context's DFMA sweep. The sum-factorised
+    sweep (hexahedra, shared operator) executes per element two 1D passes per
+    face (2 NQFS q FMAs), the face scaling (NQFS) and the dense rows x NB
+    product over the NB = (p+1)^3 - (p-1)^3 boundary nodes."""
+    nel, nq, rows = info["n_elem"], 2 * info["dim"] * info["Nqf"], info["sweep_rows"]
+    dense = 2.0 * rows * nq
+    if not info.get("sum_factorised"):
+        return "k_sweep_fused", dense, dense
+    q = info["q"]
+    nb = q ** 3 - (q - 2) ** 3
+    fma = nel * (2 * nq * q + nq) + rows * nb
+    return "k_sweep_sf", 2.0 * fma, dense
+
+
 # the dominant kernel of each kind the profiling run times, per path
-def _kernel_name(kind, precision, emulated_outer):
+def _kernel_name(kind, precision, emulated_outer, info=None):
     emulated = precision == "fp64_emulated" or emulated_outer
-    return {"elem": "k_ozaki (sweep mode)" if emulated else "k_sweep_fused",
+    fp64_name = fp64_sweep(info)[0] if info else "k_sweep_fused"
+    return {"elem": "k_ozaki (sweep mode)" if emulated else fp64_name,
             "corr": "k_sweep_tc", "step": "k_step" + (" + k_ozaki (step mode)" if emulated else ""),
             "final": "k_final" + (" / k_ozaki (reconstruction mode)" if emulated else ""),
             "face": "k_face / k_tangent", "aux": "transposes, resets, FP64 update",
@@ -571,14 +588,15 @@ def dominant_roofline(stats, info, precision, emulated_outer, fp64_peak_tf, fp64
     nel, nq, rows = info["n_elem"], 2 * info["dim"] * info["Nqf"], info["sweep_rows"]
     share = kernel_shares(stats).get(kind, 0.0)
     launches, ms = stats[kind]
-    name = _kernel_name(kind, precision, emulated_outer)
+    name = _kernel_name(kind, precision, emulated_outer, info)
     out = {"kernel": name, "kind": kind, "share": share, "launches": int(launches)}
-    if kind == "elem" and name == "k_sweep_fused":
-        flops = 2.0 * rows * nq
+    if kind == "elem" and name in ("k_sweep_fused", "k_sweep_sf"):
+        _, flops, dense = fp64_sweep(info)
         t = ms / launches * 1e-3
         out.update({"bound": "alu", "achieved": flops / t / 1e12, "peak": fp64_peak_tf,
                     "unit": "TFLOP/s", "frac": flops / t / 1e12 / fp64_peak_tf,
                     "peak_source": fp64_src, "flops_per_launch": flops,
+                    "dense_form_equivalent_tflops": dense / t / 1e12,
                     "avg_launch_us": t * 1e6})
     elif kind == "elem":
         # digit products: 34 (i, l) pairs with i + l <= 7 of M = 128 elements,
@@ -694,19 +712,21 @@ def run_headline(args):
     nq, rows, nel = 2 * info["dim"] * info["Nqf"], info["sweep_rows"], info["n_elem"]
     n_sweep, sweep_ms = stats["elem"]
     avg_ms = sweep_ms / max(n_sweep, 1)
-    flops = 2.0 * rows * nq
+    sweep_kernel, flops, dense_flops = fp64_sweep(info)
     survey_bytes = SURVEY_BYTES_PER_ELEM_3D * nel
     # bytes the fused sweep must move: the trace at the element's NQFS points
     # (each shared by the two elements of its face), Gy at its rows, the new
     # trace at its owned rows, its face ids
     own_bytes = nel * (8 * nq // 2 + 8 * 2 * (rows // nel) + 4 * 2 * info["dim"])
     roofline = {
-        "kernel": "k_sweep_fused", "bound": "alu",
+        "kernel": sweep_kernel, "bound": "alu",
         "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
         "frac": flops / (avg_ms * 1e-3) / 1e12 / peak_tf, "peak_source": peak_txt,
         "fp64_probe_tflops": probe_tf, "fp64_derived_tflops": derived_tf, "sms": sms,
-        "traffic": kernel_traffic(f"k_sweep_fused@transport3d_{n}x{n}x{n}_p3_be"),
-        "flops_per_sweep": flops, "avg_sweep_us": avg_ms * 1e3, "sweeps": int(n_sweep),
+        "traffic": kernel_traffic(f"{sweep_kernel}@transport3d_{n}x{n}x{n}_p3_be"),
+        "flops_per_sweep": flops, "dense_form_flops_per_sweep": dense_flops,
+        "dense_form_equivalent_tflops": dense_flops / (avg_ms * 1e-3) / 1e12,
+        "avg_sweep_us": avg_ms * 1e3, "sweeps": int(n_sweep),
         "hbm_view": {"alg_bytes_per_sweep": survey_bytes,
                      "alg_bytes_definition": "8 (n + 2 T_own) per element, n = 64, T_own = 48",
                      "achieved_gbs": survey_bytes / (avg_ms * 1e-3) / 1e9, "peak_gbs": hbm,

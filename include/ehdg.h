@@ -154,6 +154,10 @@ typedef struct {
   int64_t device_bytes;        /* device memory held by the context */
   int64_t sweep_rows;          /* face-point rows the element sweep computes, summed over
                                   elements (upwind/tangential points only for transport) */
+  int sum_factorised;          /* 1 if the FP64 sweep and reconstruction apply the face term
+                                  by 1D passes per face (hexahedra, one shared transport
+                                  operator): per element 2 NQFS q + NQFS + rows NB FMAs per
+                                  sweep, NB = (p+1)^3 - (p-1)^3 boundary nodes */
 } ehdg_info;
 
 /* Structured N0 x N1 (x N2) mesh of the box [lo, hi] with the numbering

@@ -938,6 +938,17 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   CKC(cudaMemsetAsync(c.hist, 0, sizeof(double) * c.max_iter, c.stream));
 
   CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_reset_iter(c); }));
+  if (sf_supported(c)) {
+    // sum-factorised sweep and reconstruction: the assembly also returns the
+    // boundary-node columns of A^{-1} (if its shared memory still fits)
+    TRYC(sf_prepare(c));
+    if (asm_smem(c) <= 220 * 1024) {
+      c.use_sf = true;
+    } else {
+      c.sf_Dy = nullptr;
+      c.sf_Ab = nullptr;
+    }
+  }
   CKC(counted(c, EHDG_KERNEL_ASSEMBLE, 1, [&] { return launch_assemble(c, c.shared_op ? 1 : (int)c.nel); }));
   if (c.pde == EHDG_TRANSPORT)
     CKC(counted(c, EHDG_KERNEL_SIGNS, 1, [&] { return launch_face_signs(c); }));
@@ -1007,6 +1018,7 @@ ehdg_status ehdg_get_info(ehdg_ctx h, ehdg_info* out) {
   out->shared_operator = c.shared_op ? 1 : 0;
   out->device_bytes = c.bytes;
   out->sweep_rows = c.sweep_rows;
+  out->sum_factorised = c.use_sf ? 1 : 0;
   return EHDG_OK;
 }
 

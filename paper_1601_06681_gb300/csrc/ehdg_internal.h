@@ -144,6 +144,17 @@ struct Ctx {
     int grid = 0, threads = 0;
     size_t smem = 0;
   } oz_sweep, oz_final, oz_step;
+  // sum-factorised FP64 sweep and reconstruction (hexahedra, one shared
+  // transport operator): the element's face traces go to its boundary nodes
+  // by two 1D passes per face (Bs), then Dy = Ey A^{-1}[:, bnd] gives the
+  // face-point rows and Ab = A^{-1}[:, bnd] the volume values
+  bool use_sf = false;
+  int sf_NB = 0;                 // boundary nodes per element
+  int* sf_bnd = nullptr;         // [NB] their node indices
+  double* sf_Ab = nullptr;       // [n][NB]
+  double* sf_Dy = nullptr;       // [NQFS][NB]
+  double sf_s[6] = {0, 0, 0, 0, 0, 0};   // J_f |beta.n| of each local face
+  std::vector<int> sf_map;       // [NB][3] faces of each boundary node: f | a_t1 << 4 | a_t2 << 8
   int inner_sweeps = 0;
   int sweep_ft = 4;              // row groups per 32-element tile of k_sweep_fused (2, 4 or 8)
   float* Hy32 = nullptr;         // FP32 copy of Hy in the sweep's slot layout
@@ -209,6 +220,12 @@ cudaError_t launch_stamp(cudaStream_t s, unsigned long long* t_start, unsigned l
                          int i, int end);
 cudaError_t launch_rows(Ctx& c);
 int face_grid_x(int64_t nface, int Nqf);   // blocks along faces of the trace kernel
+size_t asm_smem(const Ctx& c);     // shared memory of the assembly kernel
+// sum-factorised transport sweep and reconstruction (sweep_sf.cu)
+bool sf_supported(const Ctx& c);
+ehdg_status sf_prepare(Ctx& c);                           // host tables, before assembly
+cudaError_t launch_sweep_sf(Ctx& c, int graph_mode, int* grid_out);
+cudaError_t launch_final_sf(Ctx& c);
 // fused transport sweep (sweep_fused.cu)
 cudaError_t launch_sweep_fused(Ctx& c, int graph_mode);
 int fused_grid(int64_t nel);      // upper bound of the fused sweep's grid

@@ -109,6 +109,13 @@ struct AsmParams {
   double* P;
   double* H;
   double* Hy;
+  // shared transport operator of hexahedra, sum-factorised sweep: the columns
+  // of A^{-1} at the element's boundary nodes, Ab = A^{-1}[:, bnd] (n x NB),
+  // and Dy = Ey A^{-1}[:, bnd] at every face point (NQFS x NB); null if unused
+  int NB;
+  const int* bnd;               // [NB] boundary node indices
+  double* Ab;
+  double* Dy;
   int64_t ne_out;               // element stride of the outputs (1 for a shared operator)
   int* err;
 };
@@ -118,7 +125,8 @@ __global__ void k_assemble(const AsmParams a) {
   const RefTables& R = a.R;
   const int e = blockIdx.x;
   const int n = a.n, NQFS = a.NQFS, Np = R.Np, dim = R.dim, Nqf = R.Nqf;
-  const int ncol = 2 * n + NQFS;
+  const int NB = a.Dy ? a.NB : 0;             // unit columns of the boundary nodes
+  const int ncol = 2 * n + NQFS + NB;
   int Q = 1;
   for (int d = 0; d < dim; ++d) Q *= R.q;
   const int F = 2 * dim;
@@ -257,6 +265,11 @@ __global__ void k_assemble(const AsmParams a) {
       aug[I * ncol + 2 * n + s] = v;
     }
   }
+  // unit columns e_bnd[b] (sum-factorised sweep): they become A^{-1}[:, bnd]
+  for (int t = tid; t < n * NB; t += nt) {
+    const int i = t / NB, b = t % NB;
+    aug[i * ncol + 2 * n + NQFS + b] = (a.bnd[b] == i) ? 1.0 : 0.0;
+  }
   __syncthreads();
 
   // ---- Gauss-Jordan elimination with partial pivoting: [A|Mblk|B] -> [I|P|H]
@@ -320,12 +333,28 @@ __global__ void k_assemble(const AsmParams a) {
     }
     a.Hy[(int64_t)t * ne + e] = v;
   }
+  if (NB > 0) {   // shared operator only (ne = 1)
+    const int c0 = 2 * n + NQFS;
+    for (int t = tid; t < n * NB; t += nt) {
+      const int i = t / NB, b = t % NB;
+      a.Ab[t] = aug[i * ncol + c0 + b];
+    }
+    for (int t = tid; t < NQFS * NB; t += nt) {
+      const int s = t / NB, b = t % NB;
+      double v = 0.0;
+      for (int k = 0; k < a.KE; ++k) {
+        const double ev = a.ey_val[s * a.KE + k];
+        if (ev != 0.0) v += ev * aug[a.ey_idx[s * a.KE + k] * ncol + c0 + b];
+      }
+      a.Dy[t] = v;
+    }
+  }
 }
 
-static size_t asm_smem(const Ctx& c) {
+size_t asm_smem(const Ctx& c) {
   int Q = 1;
   for (int d = 0; d < c.dim; ++d) Q *= c.q;
-  const int ncol = 2 * c.n + c.NQFS;
+  const int ncol = 2 * c.n + c.NQFS + (c.sf_Dy ? c.sf_NB : 0);
   return sizeof(double) * ((size_t)c.n * ncol + c.dim * c.Np + 2 * c.dim * Q + c.F * c.Nqf + c.n);
 }
 
@@ -352,6 +381,10 @@ cudaError_t launch_assemble(Ctx& c, int n_assemble) {
   a.P = c.P;
   a.H = c.H;
   a.Hy = c.Hy;
+  a.NB = c.sf_NB;
+  a.bnd = c.sf_bnd;
+  a.Ab = c.sf_Ab;
+  a.Dy = c.sf_Dy;
   a.ne_out = c.shared_op ? 1 : c.nel;
   a.err = reinterpret_cast<int*>(&c.it->status);
   const size_t smem = asm_smem(c);
@@ -986,6 +1019,8 @@ cudaError_t launch_final(Ctx& c) {
     err = launch_final_ozaki(c);
   } else if (c.Ht) {
     err = launch_final_tiled(c);
+  } else if (c.use_sf) {
+    err = launch_final_sf(c);
   } else {
     const size_t smem =
         sizeof(double) * ((p.shared ? (size_t)c.n * c.NQFS : 0) + (size_t)c.NQFS * 32);

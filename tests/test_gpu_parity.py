@@ -99,6 +99,14 @@ def make_case(name):
         # 360 elements: two full 128-element tiles and a ragged third
         mesh, p = W.structured_mesh((9, 8, 5)), 3
         kw = dict(scheme="be", dt=5e-3, beta_const=np.array([1.0, 1.0, 1.0]) / np.sqrt(3.0))
+    elif name == "3d_cn_const_p3":
+        # Crank-Nicolson with one shared hexahedral operator (the sum-factorised
+        # sweep and its reconstruction 2 v - u^n)
+        mesh, p = W.structured_mesh((5, 4, 3)), 3
+        kw = dict(scheme="cn", dt=5e-3, beta_const=np.array([0.3, -1.0, 0.6]))
+    elif name == "3d_be_const_p1":
+        mesh, p = W.structured_mesh((7, 6, 5)), 1
+        kw = dict(scheme="be", dt=0.02, beta_const=np.array([-0.5, 0.8, 0.35]))
     elif name == "2d_cn_const":
         # Crank-Nicolson with one shared operator
         mesh, p = W.structured_mesh((15, 12)), 3
@@ -144,7 +152,7 @@ def make_solver(E, mesh, p, kw, prob, tol=1e-10, max_iter=400):
 CASES = ["2d_be_const", "2d_be_zero_component", "2d_cn_variable", "2d_cn_variable_p4",
          "2d_steady_variable", "2d_graded_mesh", "2d_per_element_const_beta",
          "2d_per_element_tangent", "3d_be_const", "3d_be_const_p3", "3d_be_variable", "sw_be",
-         "sw_be_p3", "sw_fplane", "sw_betaplane"]
+         "sw_be_p3", "sw_fplane", "sw_betaplane", "3d_cn_const_p3", "3d_be_const_p1"]
 
 
 @pytest.mark.parametrize("name", CASES)
@@ -178,7 +186,7 @@ def test_fixed_iterations_match_oracle(ehdg, name, n_iter):
 
 
 @pytest.mark.parametrize("name", ["2d_be_const", "2d_cn_variable", "3d_be_const", "sw_be",
-                                  "sw_fplane", "sw_betaplane"])
+                                  "sw_fplane", "sw_betaplane", "3d_cn_const_p3", "3d_be_const_p1"])
 def test_steps_to_tolerance_match_oracle(ehdg, name):
     mesh, p, kw, prob, u0, g = make_case(name)
     n_steps = 3
