@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "ehdg_internal.h"
+#include "fused_tile.cuh"
 #include "sweep_common.cuh"
 
 namespace ehdg {
@@ -49,7 +50,8 @@ struct FusedParams {
 // of an element is one thread's FMA chain whatever FT is, so the sweep's
 // values do not depend on it (only the residual's summation order does).
 template <int NQ, int FT>
-__global__ void __launch_bounds__(32 * FT, 16 / FT) k_sweep_fused(const FusedParams p) {
+__global__ void __launch_bounds__(32 * FT, 16 / FT)
+    k_sweep_fused(const __grid_constant__ FusedParams p) {
   extern __shared__ double sm[];
   const int nq = NQ > 0 ? NQ : p.NQFS;
   const int lane = threadIdx.x, t = threadIdx.y;
@@ -65,6 +67,13 @@ __global__ void __launch_bounds__(32 * FT, 16 / FT) k_sweep_fused(const FusedPar
   double* dst = p.uhat + (int64_t)((kk + 1) & 1) * tlen;
   const int64_t ntiles = (ne + 31) / 32;
   double acc_res = 0.0;
+  if (p.shared) {
+    // the tile body the batched loop runs too (same arithmetic)
+    const FusedTileView v = {p.nel, p.nface, p.NQFS, p.Nqf, p.F, p.n_rows, p.n_up, p.rows,
+                             p.elem_face, p.face_jf, p.fw, p.Gy, p.Y, p.R_out};
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+      fused_tile_shared<NQ, FT>(v, Hsh, uh, fid, src, dst, tile, acc_res);
+  } else
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t e = tile * 32 + lane;
     __syncthreads();                                      // previous tile done with uh/fid
