@@ -276,6 +276,21 @@ ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_t
  * at most 32). k >= n gives every instance its own branch. The graph is
  * recaptured at the next run. EHDG_ERR_INVALID for a NULL batch. */
 ehdg_status ehdg_batch_set_chains(ehdg_batch b, int k);
+/* Batched iteration loop (on by default). The instances it supports -- 2D
+ * transport with one shared operator per instance (constant velocity,
+ * uniform mesh), no face point with beta.n = 0, FP64 or TF32/BF16 mixed
+ * precision, and the tile shape of the first such instance -- iterate
+ * together: the graph of a step holds their once-per-step kernels on the
+ * branches and ONE conditional loop whose every iteration is one launch of
+ * each of: the m correction sweeps, the FP64 update, and the FP64 sweep, each
+ * over the tiles of every instance that has not converged yet (instance and
+ * tile tables on the device; each instance keeps its own counter, residual
+ * history and stopping test, Algorithm 1 of Sec. 3 per instance). The other
+ * instances run their own loops on the branches, concurrently. An instance's
+ * iterates are the same, bit for bit, either way. on = 0 runs every instance
+ * on the branches. The graph is recaptured at the next run. EHDG_ERR_INVALID
+ * for a NULL batch. */
+ehdg_status ehdg_batch_set_loop(ehdg_batch b, int on);
 /* Autotuner for the branch count: from the instances' current states, one
  * batch step (graph launch) per candidate k, timed with CUDA events on the
  * batch's stream, every instance's state restored after each; keeps the

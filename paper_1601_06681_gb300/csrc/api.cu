@@ -27,6 +27,13 @@ struct ehdg_batch_s {
   unsigned long long* t_acc = nullptr;
   int chains = 0;                       // concurrent branches of the graph (<= 0: automatic)
   bool built_on_estimate = false;       // the graph's schedule used estimated iteration counts
+  // batched iteration loop (one launch per kernel and iteration over every
+  // unconverged instance) for the instances it supports
+  bool use_loop = true;
+  ehdg::BatchLoop loop;
+  std::vector<char> looped;             // instance i iterates in the batched loop
+  std::vector<cudaStream_t> lbranch;    // branches of the looped instances' step kernels
+  unsigned long long* t_conv = nullptr; // convergence time of each instance in a step
 };
 
 namespace {
@@ -345,6 +352,35 @@ ehdg_status capture_step(Ctx& c, cudaStream_t s, cudaStream_t body_stream, bool 
   if (e2 != cudaSuccess) return cuda_fail(e2, "capture loop body");
   if (e3 != cudaSuccess) return cuda_fail(e3, "end body capture");
   return capture_step_end(c);
+}
+
+// The once-per-step kernels of an instance whose iterations run in a batch's
+// loop, appended on stream s: reset, step right-hand side, initial trace, and
+// for mixed precision the first FP64 sweep (the first residual R).
+ehdg_status capture_step_pre(Ctx& c, cudaStream_t s) {
+  cudaStream_t user = c.stream;
+  struct Restore {
+    Ctx& c;
+    cudaStream_t s;
+    ~Restore() { c.stream = s; }
+  } restore{c, user};
+  c.stream = s;
+  cudaError_t err = cudaSuccess;
+  if ((err = launch_reset_iter(c)) != cudaSuccess) return cuda_fail(err, "capture reset");
+  if ((err = launch_step(c)) != cudaSuccess) return cuda_fail(err, "capture step");
+  if ((err = launch_face(c, kFaceInitial)) != cudaSuccess) return cuda_fail(err, "capture face");
+  if (c.mixed && (err = launch_sweep_fused(c, 0)) != cudaSuccess)
+    return cuda_fail(err, "capture first FP64 sweep");
+  return EHDG_OK;
+}
+
+// The end-of-step kernels of a looped instance on stream s.
+ehdg_status capture_step_post(Ctx& c, cudaStream_t s) {
+  cudaStream_t user = c.stream;
+  c.stream = s;
+  const ehdg_status st = capture_step_end(c);
+  c.stream = user;
+  return st;
 }
 
 void abort_capture(cudaStream_t s) {
@@ -1209,7 +1245,7 @@ static std::vector<std::vector<int>> batch_schedule(ehdg_batch b, int k, bool* e
 // One graph: fork from a start event into k branch streams, capture the
 // steps of each branch's instances there one after the other (each stamped
 // with %globaltimer), join back.
-static ehdg_status batch_build_graph(ehdg_batch b) {
+static ehdg_status batch_build_graph_branches(ehdg_batch b) {
   batch_destroy_graph(b);
   const int n = (int)b->inst.size();
   const int k = std::min(n, b->chains > 0 ? b->chains : hw_queues());
@@ -1276,6 +1312,187 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
   return EHDG_OK;
 }
 
+// One graph with the batched loop: the looped instances' once-per-step
+// kernels on k branches, joined; one WHILE node whose body is the batched
+// loop (corrections, update, FP64 sweep over every unconverged instance);
+// their end-of-step kernels on k branches again. Instances the loop does not
+// support run their whole steps (each with its own loop) on other branches,
+// concurrently with all of it.
+static ehdg_status batch_build_graph(ehdg_batch b) {
+  const int n = (int)b->inst.size();
+  b->looped.assign(n, 0);
+  int ft = 0, n_loop = 0;
+  for (int i = 0; i < n && b->use_loop; ++i) {
+    const Ctx& c = b->inst[i]->c;
+    if (!batch_loop_ok(c)) continue;
+    if (ft == 0) ft = c.sweep_ft;
+    if (c.sweep_ft != ft) continue;      // one tile shape per loop
+    b->looped[i] = 1;
+    ++n_loop;
+  }
+  if (n_loop == 0) {
+    b->loop.release();
+    return batch_build_graph_branches(b);
+  }
+  batch_destroy_graph(b);
+  const int k = std::min(n, b->chains > 0 ? b->chains : hw_queues());
+  bool estimated = false;
+  const std::vector<std::vector<int>> lists = batch_schedule(b, k, &estimated);
+  std::vector<Ctx*> ctxs;
+  std::vector<int> slots;
+  for (int i = 0; i < n; ++i)
+    if (b->looped[i]) {
+      ctxs.push_back(&b->inst[i]->c);
+      slots.push_back(i);
+    }
+  CK(b->loop.build(ctxs, b->t_conv, slots));
+  while ((int)b->lbranch.size() < k) {
+    cudaStream_t st = nullptr;
+    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    b->lbranch.push_back(st);
+  }
+  std::vector<cudaEvent_t> evs;
+  auto event = [&](cudaEvent_t* e) {
+    const cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+    if (r == cudaSuccess) evs.push_back(*e);
+    return r;
+  };
+  auto cleanup_events = [&]() {
+    for (auto e : evs) cudaEventDestroy(e);
+  };
+  cudaEvent_t fork = nullptr, fork2 = nullptr;
+  if (event(&fork) != cudaSuccess || event(&fork2) != cudaSuccess) {
+    cleanup_events();
+    return cuda_fail(cudaGetLastError(), "batch events");
+  }
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+  if (e != cudaSuccess) {
+    cleanup_events();
+    return cuda_fail(e, "batch capture");
+  }
+  std::vector<cudaStream_t> forked;       // streams to join back before the end
+  ehdg_status st = EHDG_OK;
+  auto join_all = [&]() {
+    for (cudaStream_t x : forked) {
+      cudaEvent_t j = nullptr;
+      if (event(&j) != cudaSuccess) continue;
+      cudaEventRecord(j, x);
+      cudaStreamWaitEvent(b->cap, j, 0);
+    }
+    forked.clear();
+  };
+  e = cudaEventRecord(fork, b->cap);
+  // instances outside the loop: their whole steps
+  for (int j = 0; j < k && e == cudaSuccess && st == EHDG_OK; ++j) {
+    bool any = false;
+    for (int i : lists[j]) any = any || !b->looped[i];
+    if (!any) continue;
+    cudaStream_t s = b->branch[j];
+    if ((e = cudaStreamWaitEvent(s, fork, 0)) != cudaSuccess) break;
+    forked.push_back(s);
+    for (int i : lists[j]) {
+      if (b->looped[i]) continue;
+      Ctx& c = b->inst[i]->c;
+      if ((e = launch_stamp(s, b->t_start, b->t_acc, i, 0)) != cudaSuccess) break;
+      if ((st = capture_step(c, s, b->body, false)) != EHDG_OK) break;
+      if ((e = launch_stamp(s, b->t_start, b->t_acc, i, 1)) != cudaSuccess) break;
+    }
+  }
+  // looped instances: step kernels before the loop, joined
+  std::vector<cudaStream_t> pre;
+  for (int j = 0; j < k && e == cudaSuccess && st == EHDG_OK; ++j) {
+    bool any = false;
+    for (int i : lists[j]) any = any || b->looped[i];
+    if (!any) continue;
+    cudaStream_t s = b->lbranch[j];
+    if ((e = cudaStreamWaitEvent(s, fork, 0)) != cudaSuccess) break;
+    pre.push_back(s);
+    forked.push_back(s);
+    for (int i : lists[j]) {
+      if (!b->looped[i]) continue;
+      if ((e = launch_stamp(s, b->t_start, b->t_acc, i, 0)) != cudaSuccess) break;
+      if ((st = capture_step_pre(b->inst[i]->c, s)) != EHDG_OK) break;
+    }
+  }
+  for (cudaStream_t s : pre) {
+    cudaEvent_t j = nullptr;
+    if (e != cudaSuccess || (e = (cudaError_t)event(&j)) != cudaSuccess) break;
+    if ((e = cudaEventRecord(j, s)) != cudaSuccess) break;
+    e = cudaStreamWaitEvent(b->cap, j, 0);
+  }
+  // the batched loop
+  if (e == cudaSuccess && st == EHDG_OK) {
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle handle;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(b->cap, &cst, nullptr, &g, nullptr, nullptr, nullptr);
+    if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess)
+      e = cudaStreamGetCaptureInfo(b->cap, &cst, nullptr, &g, &deps, nullptr, &ndeps);
+    cudaGraphNodeParams cp = {};
+    cudaGraphNode_t cond;
+    if (e == cudaSuccess) {
+      cp.type = cudaGraphNodeTypeConditional;
+      cp.conditional.handle = handle;
+      cp.conditional.type = cudaGraphCondTypeWhile;
+      cp.conditional.size = 1;
+      e = cudaGraphAddNode(&cond, g, deps, nullptr, ndeps, &cp);
+    }
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(b->cap, &cond, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess) {
+      cudaGraph_t body = cp.conditional.phGraph_out[0];
+      e = cudaStreamBeginCaptureToGraph(b->body, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeRelaxed);
+      if (e == cudaSuccess) {
+        const cudaError_t e2 = b->loop.launch_body(b->body, handle);
+        const cudaError_t e3 = cudaStreamEndCapture(b->body, &body);
+        e = e2 != cudaSuccess ? e2 : e3;
+      }
+    }
+  }
+  // looped instances: end-of-step kernels
+  if (e == cudaSuccess && st == EHDG_OK) e = cudaEventRecord(fork2, b->cap);
+  for (int j = 0; j < k && e == cudaSuccess && st == EHDG_OK; ++j) {
+    bool any = false;
+    for (int i : lists[j]) any = any || b->looped[i];
+    if (!any) continue;
+    cudaStream_t s = b->lbranch[j];
+    if ((e = cudaStreamWaitEvent(s, fork2, 0)) != cudaSuccess) break;
+    forked.push_back(s);
+    for (int i : lists[j]) {
+      if (!b->looped[i]) continue;
+      if ((st = capture_step_post(b->inst[i]->c, s)) != EHDG_OK) break;
+      if ((e = launch_stamp_conv(s, b->t_start, b->t_acc, b->t_conv, i)) != cudaSuccess) break;
+    }
+  }
+  if (e != cudaSuccess || st != EHDG_OK) {
+    const std::string msg = e != cudaSuccess ? std::string("batch capture: ") + cudaGetErrorString(e)
+                                             : g_err;
+    join_all();
+    abort_capture(b->cap);
+    cleanup_events();
+    g_err = msg;
+    return st != EHDG_OK ? st : EHDG_ERR_CUDA;
+  }
+  join_all();
+  for (int i = 0; i < n; ++i) {
+    b->graph_force[i] = b->inst[i]->c.have_force ? 1 : 0;
+    b->graph_gen[i] = b->inst[i]->c.path_gen;
+  }
+  b->built_on_estimate = estimated;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamEndCapture(b->cap, &g);
+  cleanup_events();
+  if (e != cudaSuccess) return cuda_fail(e, "batch end capture");
+  b->graph = g;
+  CK(cudaGraphInstantiate(&b->exec, g, 0));
+  return EHDG_OK;
+}
+
 ehdg_status ehdg_batch_create(int n, const ehdg_mesh_desc* meshes, const ehdg_problem_desc* probs,
                               void* stream, ehdg_batch* out) {
   if (!out || n < 1 || !meshes || !probs) return fail(EHDG_ERR_INVALID, "bad batch arguments");
@@ -1306,8 +1523,11 @@ ehdg_status ehdg_batch_create(int n, const ehdg_mesh_desc* meshes, const ehdg_pr
       cudaStreamCreateWithFlags(&b->body, cudaStreamNonBlocking) != cudaSuccess)
     return bail(cuda_fail(cudaGetLastError(), "capture stream"));
   if (cudaMalloc(&b->t_start, sizeof(unsigned long long) * n) != cudaSuccess ||
-      cudaMalloc(&b->t_acc, sizeof(unsigned long long) * n) != cudaSuccess)
+      cudaMalloc(&b->t_acc, sizeof(unsigned long long) * n) != cudaSuccess ||
+      cudaMalloc(&b->t_conv, sizeof(unsigned long long) * n) != cudaSuccess)
     return bail(fail(EHDG_ERR_OOM, "cudaMalloc failed"));
+  if (cudaMemset(b->t_conv, 0, sizeof(unsigned long long) * n) != cudaSuccess)
+    return bail(cuda_fail(cudaGetLastError(), "cudaMemset"));
   b->graph_force.assign(n, 0);
   b->graph_gen.assign(n, 0);
   *out = b;
@@ -1367,10 +1587,23 @@ ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_t
     c.last_iters = std::min(c.step_iters_h[n_steps - 1], c.max_iter);
     if (inst_time_s) inst_time_s[i] = (double)acc[i] * 1e-9;
   }
+  for (int i = 0; i < n && first == EHDG_OK; ++i) {
+    const ehdg_status te = check_tc_err(b->inst[i]->c);
+    if (te != EHDG_OK) first = te;
+  }
   // a schedule made on guessed iteration counts is made again on the
   // measured ones, once, before the next run
   if (first == EHDG_OK && b->built_on_estimate) TRY(batch_build_graph(b));
   return first;
+}
+
+ehdg_status ehdg_batch_set_loop(ehdg_batch b, int on) {
+  if (!b) return fail(EHDG_ERR_INVALID, "NULL batch");
+  if ((on != 0) != b->use_loop) {
+    b->use_loop = on != 0;
+    batch_destroy_graph(b);
+  }
+  return EHDG_OK;
 }
 
 ehdg_status ehdg_batch_set_chains(ehdg_batch b, int k) {
@@ -1555,6 +1788,10 @@ void ehdg_batch_destroy(ehdg_batch b) {
   if (b->body) cudaStreamDestroy(b->body);
   if (b->t_start) cudaFree(b->t_start);
   if (b->t_acc) cudaFree(b->t_acc);
+  if (b->t_conv) cudaFree(b->t_conv);
+  for (auto s : b->lbranch)
+    if (s) cudaStreamDestroy(s);
+  b->loop.release();
   for (auto h : b->inst) ehdg_destroy(h);
   delete b;
 }

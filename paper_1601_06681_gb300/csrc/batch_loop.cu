@@ -1,0 +1,602 @@
+// Batched eHDG iteration: the iterations of many independent problems in one
+// launch per kernel and iteration (Algorithm 1 of Sec. 3, run per instance).
+//
+// A batch's step graph runs every instance's once-per-step kernels (reset,
+// right-hand side, initial trace; end-of-step reconstruction) on concurrent
+// branches, and between them ONE conditional WHILE loop whose body is
+//   m  correction sweeps over the tiles of every unconverged mixed-precision
+//      instance (TF32/BF16 on the tensor cores, one launch each),
+//   1  FP64 update uhat += delta of those instances,
+//   1  FP64 sweep over the tiles of every unconverged instance,
+// with the instances and their tiles in tables on the device. Each instance
+// keeps its own iteration counter, residual history and stopping test: its
+// residual is reduced by the last of its work items (a ticket per instance),
+// exactly as its own sweep launch reduces it, and the last block of the
+// launch sets the loop condition to "some instance still iterates". Converged
+// instances' work items are skipped. No block waits for another.
+//
+// Every element's arithmetic is the single-problem path's: the FP64 sweep
+// runs the same tile body (fused_tile.cuh) over the same tile partition, each
+// work item playing one block of the instance's own sweep launch (the tiles
+// j, j + g, j + 2g, ... of that launch's grid g), so the residual partials and
+// their reduction order are the same; the correction sweep stages the same
+// rounded operands into the same tcgen05 MMA shapes. A batched instance's
+// iterates therefore equal a solo run's bit for bit.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ehdg_internal.h"
+#include "fused_tile.cuh"
+#include "sweep_common.cuh"
+#include "umma.cuh"
+
+namespace ehdg {
+
+namespace {
+
+constexpr int kBTcM = 128;                 // elements per correction tile (MMA M)
+constexpr int kBTcThreads = 256;           // two threads per element
+constexpr uint32_t kBWaitLimit = 1u << 24; // mbarrier polls before giving up
+constexpr int kApplyChunk = 4096;          // trace entries per update work item
+
+struct BInst {
+  // FP64 sweep (the fused tile body of the instance's own launch)
+  int64_t nel, nface;
+  int NQFS, Nqf, F, n_rows, n_up;
+  int vblocks;                  // grid of the instance's own sweep launch
+  const int* rows;
+  const int32_t* elem_face;
+  const double* face_jf;
+  double fw[kMaxQ * kMaxQ];
+  const double* Gy;
+  double* Y;
+  float* R_out;
+  const double* Hy;
+  double* uhat;
+  IterState* it;
+  double* partials;
+  double* hist;
+  double tol, res_scale;
+  int max_iter;
+  // corrections (tensor cores), mixed precision only
+  int tc, bf16, m;
+  int Np, Kp;
+  uint32_t idesc;
+  const float* Hy32;
+  const float* R32;
+  float* d32;
+  float* Y32;
+  int* err;
+  // convergence time of the instance in the current step (%globaltimer)
+  unsigned long long* t_conv;
+};
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <int NQ, int FT>
+__device__ __forceinline__ void batch_tiles(const BInst& I, int j, const double* Hsh, double* uh,
+                                            int* fid, const double* src, double* dst,
+                                            double& acc) {
+  const FusedTileView v = {I.nel, I.nface, I.NQFS, I.Nqf, I.F, I.n_rows, I.n_up, I.rows,
+                           I.elem_face, I.face_jf, I.fw, I.Gy, I.Y, I.R_out};
+  const int64_t ntiles = (I.nel + 31) / 32;
+  for (int64_t tile = j; tile < ntiles; tile += I.vblocks)
+    fused_tile_shared<NQ, FT>(v, Hsh, uh, fid, src, dst, tile, acc);
+}
+
+// One FP64 sweep of every unconverged instance; items[w] = (instance,
+// block j of its own launch).
+template <int FT>
+__global__ void __launch_bounds__(32 * FT) k_batch_sweep(const BInst* inst, const int2* items,
+                                                          int n_items, int n_inst,
+                                                          unsigned int* ticket,
+                                                          cudaGraphConditionalHandle handle) {
+  extern __shared__ double sm[];
+  __shared__ int s_live, s_kk;
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  int cur = -1;
+  double* Hsh = sm;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int2 item = items[w];
+    const BInst& I = inst[item.x];
+    __syncthreads();   // the previous item is done with the shared scratch and flags
+    // the instance's state cannot change before all its work items are done
+    if (tid == 0) {
+      s_live = reinterpret_cast<volatile IterState*>(I.it)->cont;
+      s_kk = reinterpret_cast<volatile IterState*>(I.it)->k;
+    }
+    __syncthreads();
+    if (!s_live) continue;
+    const int nq = I.NQFS;
+    double* uh = sm + nq * nq;
+    int* fid = reinterpret_cast<int*>(uh + nq * 32);
+    if (item.x != cur) {
+      for (int i = tid; i < nq * nq; i += 32 * FT) Hsh[i] = I.Hy[i];
+      cur = item.x;
+    }
+    const int kk = s_kk;
+    const int64_t tlen = (int64_t)I.Nqf * I.nface;
+    const double* src = I.uhat + (int64_t)(kk & 1) * tlen;
+    double* dst = I.uhat + (int64_t)((kk + 1) & 1) * tlen;
+    double acc = 0.0;
+    switch (nq) {
+      case 8: batch_tiles<8, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
+      case 12: batch_tiles<12, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
+      case 16: batch_tiles<16, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
+      case 20: batch_tiles<20, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
+      case 24: batch_tiles<24, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
+      default: batch_tiles<28, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
+    }
+    const bool last = finish_residual(acc, I.partials, item.y, I.vblocks, I.it, I.hist,
+                                      I.max_iter, I.tol, I.res_scale, 0, handle, I.vblocks);
+    if (last && tid == 0 && !reinterpret_cast<volatile IterState*>(I.it)->cont)
+      *I.t_conv = global_ns();
+  }
+  // the last block of the launch: is any instance still iterating?
+  __shared__ bool s_last;
+  __syncthreads();
+  if (tid == 0) {
+    __threadfence();
+    s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  int any = 0;
+  for (int i = tid; i < n_inst; i += 32 * FT)
+    any |= reinterpret_cast<volatile IterState*>(inst[i].it)->cont;
+  any = __syncthreads_or(any);
+  if (tid == 0) {
+    *ticket = 0u;
+    cudaGraphSetConditional(handle, any ? 1u : 0u);
+  }
+}
+
+__device__ __forceinline__ uint32_t b_to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+// 16 bytes of one K-major core-matrix row: 4 TF32 or 8 BF16 values
+__device__ __forceinline__ void b_store_chunk(unsigned char* dst, const float* v, int bf16) {
+  if (bf16) {
+    uint32_t w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat16 lo = __float2bfloat16_rn(v[2 * q]);
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v[2 * q + 1]);
+      w[q] = (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+    }
+    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
+  } else {
+    *reinterpret_cast<uint4*>(dst) =
+        make_uint4(b_to_tf32(v[0]), b_to_tf32(v[1]), b_to_tf32(v[2]), b_to_tf32(v[3]));
+  }
+}
+
+__device__ __forceinline__ void b_store_elem(unsigned char* base, int row, int k, int esize,
+                                             uint32_t sbo, float v, int bf16) {
+  const uint32_t off = kmajor_off(row, k * esize, sbo);
+  if (bf16) {
+    *reinterpret_cast<__nv_bfloat16*>(base + off) = __float2bfloat16_rn(v);
+  } else {
+    *reinterpret_cast<uint32_t*>(base + off) = b_to_tf32(v);
+  }
+}
+
+// Inner correction sweep j of every unconverged TF32/BF16 mixed-precision
+// instance: delta_out = R + (delta_in Hy^T at the rows), owner writes; items[w]
+// = (instance, 128-element tile). The operands, MMA shapes and epilogue are
+// those of the single-problem tensor-core correction sweep.
+__global__ void __launch_bounds__(kBTcThreads) k_batch_tc(const BInst* inst, const int2* items,
+                                                          int n_items, int j, int ncols,
+                                                          int smem_b, int smem_a) {
+  extern __shared__ __align__(1024) unsigned char smb[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  __shared__ int s_live;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (kBTcM - 1), half = tid >> 7;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tbase = tmem_base;
+  unsigned char* Bs = smb;                          // Np x Kp of the current instance
+  unsigned char* As = smb + smem_b;                 // 128 x Kp
+  int* fid = reinterpret_cast<int*>(As + smem_a);   // [F][128]
+  int* row_f = fid + 6 * kBTcM;                     // [Np] face of a row
+  int* row_g = row_f + 256;                         // [Np] point of a row
+  uint32_t phase = 0;
+  bool failed = false;
+  int cur = -1;
+  for (int w = blockIdx.x; w < n_items && !failed; w += gridDim.x) {
+    const int2 item = items[w];
+    const BInst& I = inst[item.x];
+    __syncthreads();   // the previous item is done with the shared operands and flags
+    if (tid == 0) s_live = (I.tc && I.m > j) ? reinterpret_cast<volatile IterState*>(I.it)->cont : 0;
+    __syncthreads();
+    if (!s_live) continue;
+    const int esize = I.bf16 ? 2 : 4;
+    const uint32_t kbytes = (uint32_t)I.Kp * esize;
+    const uint32_t sbo = kbytes * 8u;
+    if (item.x != cur) {
+      // the instance's operator rows (B) and row tables
+      for (int jj = tid; jj < I.Np; jj += kBTcThreads) {
+        const int r = jj < I.n_rows ? I.rows[jj] : 0;
+        row_f[jj] = r / I.Nqf;
+        row_g[jj] = r - (r / I.Nqf) * I.Nqf;
+      }
+      for (int i = tid; i < I.Np * I.Kp; i += kBTcThreads) {
+        const int n = i / I.Kp, k = i - n * I.Kp;
+        float v = 0.f;
+        if (n < I.n_rows && k < I.NQFS) v = I.Hy32[I.rows[n] * I.NQFS + k];
+        b_store_elem(Bs, n, k, esize, sbo, v, I.bf16);
+      }
+      cur = item.x;
+    }
+    const int64_t trace = (int64_t)I.Nqf * I.nface;
+    const float* in = j == 0 ? I.R32 : I.d32 + (int64_t)((j - 1) & 1) * trace;
+    float* out = I.d32 + (int64_t)(j & 1) * trace;
+    const int64_t ne = I.nel, nface = I.nface;
+    const int64_t e = (int64_t)item.y * kBTcM + row;
+    __syncthreads();
+    if (e < ne)
+      for (int f = half; f < I.F; f += 2) fid[f * kBTcM + row] = I.elem_face[f * ne + e];
+    __syncthreads();
+    {
+      // A: this tile's correction values at its elements' face points, each
+      // element's K range split between its two threads
+      const uint32_t rowoff = (uint32_t)(row >> 3) * sbo + (uint32_t)(row & 7) * 16u;
+      const int khalf = I.Kp / 2;
+      const int kbeg = half * khalf, kend = kbeg + khalf;
+      int f = kbeg / I.Nqf, g = kbeg - (kbeg / I.Nqf) * I.Nqf;
+      for (int k0 = kbeg; k0 < kend; k0 += 16) {
+        float v[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          float x = 0.f;
+          if (e < ne && k0 + q < I.NQFS && k0 + q < kend) {
+            x = in[g * nface + fid[f * kBTcM + row]];
+            if (++g == I.Nqf) {
+              g = 0;
+              ++f;
+            }
+          }
+          v[q] = x;
+        }
+        if (I.bf16) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            if (k0 + 8 * h < kend)
+              b_store_chunk(As + rowoff + (uint32_t)((k0 + 8 * h) / 8) * 128u, v + 8 * h, 1);
+        } else {
+#pragma unroll
+          for (int h = 0; h < 4; ++h)
+            if (k0 + 4 * h < kend)
+              b_store_chunk(As + rowoff + (uint32_t)((k0 + 4 * h) / 4) * 128u, v + 4 * h, 0);
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+      const int ksteps = (int)(kbytes / 32u);
+      for (int s = 0; s < ksteps; ++s) {
+        const uint64_t ad = umma_desc(a0 + 256u * s, 128u, sbo);
+        const uint64_t bd = umma_desc(b0 + 256u * s, 128u, sbo);
+        const uint32_t acc = s > 0 ? 1u : 0u;
+        if (I.bf16) {
+          asm volatile(
+              "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tbase),
+              "l"(ad), "l"(bd), "r"(I.idesc), "r"(acc));
+        } else {
+          asm volatile(
+              "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}\n" ::"r"(tbase),
+              "l"(ad), "l"(bd), "r"(I.idesc), "r"(acc));
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&mbar)));
+    }
+    uint32_t ok = 1;
+    if (tid == 0) ok = mbar_wait_bounded(&mbar, phase, kBWaitLimit) ? 1u : 0u;
+    if (__syncthreads_or(ok ? 0 : 1)) {
+      if (tid == 0) atomicExch(I.err, 1);
+      failed = true;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!failed) {
+      const int nhalf = I.Np / 2;
+      const int cbeg = half * nhalf, cend = cbeg + nhalf;
+      for (int c0 = cbeg; c0 < cend; c0 += 8) {
+        uint32_t v[8];
+        tmem_ld8(tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (e < ne) {
+          int64_t pt[8];
+          float rv[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int jr = c0 + q;
+            pt[q] = -1;
+            rv[q] = 0.f;
+            if (jr < I.n_rows && jr < I.n_up) {
+              pt[q] = (int64_t)row_g[jr] * nface + fid[row_f[jr] * kBTcM + row];
+              rv[q] = I.R32[pt[q]];
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int jr = c0 + q;
+            if (jr >= I.n_rows) break;
+            const float acc = __uint_as_float(v[q]);
+            if (pt[q] >= 0) {
+              out[pt[q]] = rv[q] + acc;
+            } else {
+              I.Y32[(int64_t)(row_f[jr] * I.Nqf + row_g[jr]) * ne + e] = acc;
+            }
+          }
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "r"(ncols));
+}
+
+// uhat <- uhat + delta in FP64 for every unconverged mixed-precision
+// instance (the single-problem update, slot k&1 = slot (k+1)&1 + delta of
+// its last inner sweep); items[w] = (instance, chunk of kApplyChunk entries).
+__global__ void __launch_bounds__(256) k_batch_apply(const BInst* inst, const int2* items,
+                                                     int n_items) {
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int2 item = items[w];
+    const BInst& I = inst[item.x];
+    if (!I.tc || !reinterpret_cast<volatile IterState*>(I.it)->cont) continue;
+    const int K = reinterpret_cast<volatile IterState*>(I.it)->k;
+    const int64_t total = (int64_t)I.Nqf * I.nface;
+    double* dst = I.uhat + (int64_t)(K & 1) * total;
+    const double* src = I.uhat + (int64_t)((K + 1) & 1) * total;
+    const float* delta = I.d32 + (int64_t)((I.m - 1) & 1) * total;
+    const int64_t t0 = (int64_t)item.y * kApplyChunk;
+    const int64_t t1 = std::min<int64_t>(t0 + kApplyChunk, total);
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) dst[t] = src[t] + (double)delta[t];
+  }
+}
+
+// per-instance step time of a looped instance: from its step's start stamp to
+// its convergence inside the loop (or to now, if it converged before it)
+__global__ void k_stamp_conv(unsigned long long* t_start, unsigned long long* t_acc,
+                             unsigned long long* t_conv, int i) {
+  const unsigned long long t = t_conv[i] ? t_conv[i] : global_ns();
+  t_acc[i] += t - t_start[i];
+  t_conv[i] = 0ull;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+
+bool batch_loop_ok(const Ctx& c) {
+  const bool nq_ok = c.NQFS == 8 || c.NQFS == 12 || c.NQFS == 16 || c.NQFS == 20 ||
+                     c.NQFS == 24 || c.NQFS == 28;
+  const bool prec_ok = c.precision == EHDG_FP64 || c.precision == EHDG_MIXED_TF32 ||
+                       c.precision == EHDG_MIXED_BF16;
+  return c.pde == EHDG_TRANSPORT && c.dim == 2 && c.shared_op && !c.variable_beta && !c.Hyt &&
+         !c.use_ozaki && !c.use_sf && c.n_tan == 0 && nq_ok && prec_ok &&
+         (!c.mixed || tc_supported(c));
+}
+
+struct BatchLoop::Impl {
+  BInst* d_inst = nullptr;
+  int2* d_sweep = nullptr;
+  int2* d_tc = nullptr;
+  int2* d_apply = nullptr;
+  unsigned int* d_ticket = nullptr;
+  int n_inst = 0, n_sweep = 0, n_tc = 0, n_apply = 0, max_m = 0, ft = 4;
+  int sweep_grid = 1, tc_grid = 1, apply_grid = 1, tc_ncols = 32, tc_smem_b = 0, tc_smem_a = 0;
+  size_t sweep_smem = 0, tc_smem = 0;
+};
+
+BatchLoop::~BatchLoop() { release(); }
+
+void BatchLoop::release() {
+  if (!impl) return;
+  cudaFree(impl->d_inst);
+  cudaFree(impl->d_sweep);
+  cudaFree(impl->d_tc);
+  cudaFree(impl->d_apply);
+  cudaFree(impl->d_ticket);
+  delete impl;
+  impl = nullptr;
+}
+
+// Device tables of the looped instances (their contexts must stay alive).
+cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* t_conv,
+                             const std::vector<int>& slot) {
+  release();
+  impl = new Impl();
+  Impl& L = *impl;
+  L.n_inst = (int)ctxs.size();
+  L.ft = ctxs.empty() ? 4 : ctxs[0]->sweep_ft;
+  std::vector<BInst> h(L.n_inst);
+  std::vector<int2> sw, tc, ap;
+  size_t smem = 0;
+  int max_kp_bytes = 0, max_np = 16;
+  for (int i = 0; i < L.n_inst; ++i) {
+    const Ctx& c = *ctxs[i];
+    BInst& I = h[i];
+    I = BInst{};
+    I.nel = c.nel;
+    I.nface = c.nface;
+    I.NQFS = c.NQFS;
+    I.Nqf = c.Nqf;
+    I.F = c.F;
+    I.n_rows = c.n_rows;
+    I.n_up = c.n_up;
+    I.vblocks = fused_sweep_grid(c);
+    I.rows = c.rows;
+    I.elem_face = c.geo.elem_face;
+    I.face_jf = c.geo.face_jf;
+    fill_face_weights(c, I.fw);
+    I.Gy = c.Gy;
+    I.Y = c.Y;
+    I.R_out = c.mixed ? c.R32 : nullptr;
+    I.Hy = c.Hy;
+    I.uhat = c.uhat;
+    I.it = c.it;
+    I.partials = c.partials;
+    I.hist = c.hist;
+    I.tol = c.tol;
+    I.res_scale = c.res_scale;
+    I.max_iter = c.max_iter;
+    I.t_conv = t_conv + slot[i];
+    I.err = c.tc_err;
+    smem = std::max(smem, fused_sweep_smem(c));
+    for (int j = 0; j < I.vblocks; ++j) sw.push_back(make_int2(i, j));
+    if (c.mixed) {
+      I.tc = 1;
+      I.bf16 = c.precision == EHDG_MIXED_BF16 ? 1 : 0;
+      I.m = c.inner_sweeps;
+      const int kstep = I.bf16 ? 16 : 8;
+      I.Kp = (c.NQFS + kstep - 1) / kstep * kstep;
+      I.Np = std::max(16, (c.n_rows + 15) / 16 * 16);
+      I.idesc = umma_idesc(I.bf16 ? 1u : 2u, kBTcM, I.Np);
+      I.Hy32 = c.Hy32;
+      I.R32 = c.R32;
+      I.d32 = c.d32;
+      I.Y32 = c.Y32;
+      L.max_m = std::max(L.max_m, I.m);
+      max_kp_bytes = std::max(max_kp_bytes, I.Kp * (I.bf16 ? 2 : 4));
+      max_np = std::max(max_np, I.Np);
+      const int64_t tiles = (c.nel + kBTcM - 1) / kBTcM;
+      for (int64_t t = 0; t < tiles; ++t) tc.push_back(make_int2(i, (int)t));
+      const int64_t total = (int64_t)c.Nqf * c.nface;
+      for (int64_t t = 0; t * kApplyChunk < total; ++t) ap.push_back(make_int2(i, (int)t));
+    }
+  }
+  L.n_sweep = (int)sw.size();
+  L.n_tc = (int)tc.size();
+  L.n_apply = (int)ap.size();
+  L.sweep_smem = smem;
+  cudaError_t e;
+  if ((e = cudaMalloc(&L.d_inst, sizeof(BInst) * std::max(1, L.n_inst))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_sweep, sizeof(int2) * std::max(1, L.n_sweep))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_tc, sizeof(int2) * std::max(1, L.n_tc))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_apply, sizeof(int2) * std::max(1, L.n_apply))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_ticket, sizeof(unsigned int))) != cudaSuccess) return e;
+  if ((e = cudaMemset(L.d_ticket, 0, sizeof(unsigned int))) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(L.d_inst, h.data(), sizeof(BInst) * L.n_inst, cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return e;
+  if (L.n_sweep && (e = cudaMemcpy(L.d_sweep, sw.data(), sizeof(int2) * L.n_sweep,
+                                   cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  if (L.n_tc && (e = cudaMemcpy(L.d_tc, tc.data(), sizeof(int2) * L.n_tc,
+                                cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  if (L.n_apply && (e = cudaMemcpy(L.d_apply, ap.data(), sizeof(int2) * L.n_apply,
+                                   cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  // launch shapes: one wave of resident blocks each
+  auto wave = [](auto kernel, int threads, size_t sm, int items) {
+    int bpsm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, threads, sm) != cudaSuccess ||
+        bpsm < 1) {
+      cudaGetLastError();
+      bpsm = 1;
+    }
+    return std::max(1, std::min(bpsm * device_sms(), items));
+  };
+  switch (L.ft) {
+    case 2: L.sweep_grid = wave(k_batch_sweep<2>, 64, smem, L.n_sweep); break;
+    case 8: L.sweep_grid = wave(k_batch_sweep<8>, 256, smem, L.n_sweep); break;
+    default: L.sweep_grid = wave(k_batch_sweep<4>, 128, smem, L.n_sweep); break;
+  }
+  if (L.n_tc) {
+    // B: the largest instance's padded rows x K; A: 128 x K
+    L.tc_smem_b = (max_np * max_kp_bytes + 1023) / 1024 * 1024;
+    L.tc_smem_a = (kBTcM * max_kp_bytes + 15) / 16 * 16;
+    L.tc_smem = (size_t)L.tc_smem_b + L.tc_smem_a + sizeof(int) * (6 * kBTcM + 512) + 1024;
+    while (L.tc_ncols < max_np) L.tc_ncols *= 2;
+    if ((e = cudaFuncSetAttribute(k_batch_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)L.tc_smem)) != cudaSuccess)
+      return e;
+    int bpsm = (int)((227 * 1024) / (L.tc_smem + 1024));
+    bpsm = std::max(1, std::min({bpsm, 512 / L.tc_ncols, 8}));
+    L.tc_grid = std::max(1, std::min(bpsm * device_sms(), L.n_tc));
+    L.apply_grid = std::max(1, std::min(device_sms() * 8, L.n_apply));
+  }
+  return cudaSuccess;
+}
+
+// The loop body (captured into the WHILE node's body graph on stream s).
+cudaError_t BatchLoop::launch_body(cudaStream_t s, cudaGraphConditionalHandle handle) {
+  Impl& L = *impl;
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < L.max_m && L.n_tc; ++j) {
+    k_batch_tc<<<L.tc_grid, kBTcThreads, L.tc_smem, s>>>(L.d_inst, L.d_tc, L.n_tc, j,
+                                                        L.tc_ncols, L.tc_smem_b, L.tc_smem_a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (L.n_apply) {
+    k_batch_apply<<<L.apply_grid, 256, 0, s>>>(L.d_inst, L.d_apply, L.n_apply);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  switch (L.ft) {
+    case 2:
+      k_batch_sweep<2><<<L.sweep_grid, dim3(32, 2), L.sweep_smem, s>>>(
+          L.d_inst, L.d_sweep, L.n_sweep, L.n_inst, L.d_ticket, handle);
+      break;
+    case 8:
+      k_batch_sweep<8><<<L.sweep_grid, dim3(32, 8), L.sweep_smem, s>>>(
+          L.d_inst, L.d_sweep, L.n_sweep, L.n_inst, L.d_ticket, handle);
+      break;
+    default:
+      k_batch_sweep<4><<<L.sweep_grid, dim3(32, 4), L.sweep_smem, s>>>(
+          L.d_inst, L.d_sweep, L.n_sweep, L.n_inst, L.d_ticket, handle);
+      break;
+  }
+  return cudaGetLastError();
+}
+
+int BatchLoop::kernels_per_iteration() const {
+  return impl ? (impl->n_tc ? impl->max_m : 0) + (impl->n_apply ? 1 : 0) + 1 : 0;
+}
+
+cudaError_t launch_stamp_conv(cudaStream_t s, unsigned long long* t_start,
+                              unsigned long long* t_acc, unsigned long long* t_conv, int i) {
+  k_stamp_conv<<<1, 1, 0, s>>>(t_start, t_acc, t_conv, i);
+  return cudaGetLastError();
+}
+
+}  // namespace ehdg

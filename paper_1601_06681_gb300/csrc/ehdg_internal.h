@@ -228,6 +228,8 @@ cudaError_t launch_sweep_sf(Ctx& c, int graph_mode, int* grid_out);
 cudaError_t launch_final_sf(Ctx& c);
 // fused transport sweep (sweep_fused.cu)
 cudaError_t launch_sweep_fused(Ctx& c, int graph_mode);
+size_t fused_sweep_smem(const Ctx& c);   // dynamic shared memory of the fused sweep
+int fused_sweep_grid(const Ctx& c);      // its grid = its residual partials
 int fused_grid(int64_t nel);      // upper bound of the fused sweep's grid
 int device_sms();
 int tangent_grid(int64_t n_tan);
@@ -263,6 +265,27 @@ std::vector<std::pair<void*, size_t>> state_arrays(Ctx& c);
 // tensor-core correction sweep (tc_sweep.cu)
 bool tc_supported(const Ctx& c);
 cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out);
+
+// Batched iteration loop of a batch's looped instances (batch_loop.cu): one
+// launch per kernel and iteration over every unconverged instance.
+bool batch_loop_ok(const Ctx& c);   // the instance can run in the batched loop
+struct BatchLoop {
+  struct Impl;
+  Impl* impl = nullptr;
+  BatchLoop() = default;
+  BatchLoop(const BatchLoop&) = delete;
+  BatchLoop& operator=(const BatchLoop&) = delete;
+  ~BatchLoop();
+  void release();
+  // device tables of the looped instances; t_conv[slot[i]] receives instance
+  // i's convergence time in a step
+  cudaError_t build(const std::vector<Ctx*>& ctxs, unsigned long long* t_conv,
+                    const std::vector<int>& slot);
+  cudaError_t launch_body(cudaStream_t s, cudaGraphConditionalHandle handle);
+  int kernels_per_iteration() const;
+};
+cudaError_t launch_stamp_conv(cudaStream_t s, unsigned long long* t_start,
+                              unsigned long long* t_acc, unsigned long long* t_conv, int i);
 
 enum FaceMode { kFaceInitial = 0, kFaceIterate = 1 };
 

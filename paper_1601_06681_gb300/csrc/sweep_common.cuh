@@ -18,7 +18,8 @@ __device__ __forceinline__ double fsum_warp(double v) {
 // records r_k and sets the loop condition (same rule as the trace kernel).
 // partials[slot] receives this block's sum; the last of the nblocks blocks of
 // this launch to take a ticket sums partials[0 .. n_total_partials).
-__device__ __forceinline__ void finish_residual(double acc, double* partials, unsigned int slot,
+// Returns true in the block that did the final reduction.
+__device__ __forceinline__ bool finish_residual(double acc, double* partials, unsigned int slot,
                                                 unsigned int nblocks, IterState* it, double* hist,
                                                 int max_iter, double tol, double res_scale,
                                                 int graph_mode, cudaGraphConditionalHandle handle,
@@ -41,7 +42,7 @@ __device__ __forceinline__ void finish_residual(double acc, double* partials, un
     }
   }
   __syncthreads();
-  if (!last) return;
+  if (!last) return false;
   __threadfence();
   double v = 0.0;
   for (int i = tid; i < n_total_partials; i += blockDim.x * blockDim.y)
@@ -68,6 +69,7 @@ __device__ __forceinline__ void finish_residual(double acc, double* partials, un
     __threadfence();
     if (graph_mode) cudaGraphSetConditional(handle, (unsigned int)cont);
   }
+  return true;
 }
 
 }  // namespace ehdg

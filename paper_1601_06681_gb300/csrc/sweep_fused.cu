@@ -276,6 +276,17 @@ static cudaError_t launch_fused_ft(const FusedParams& p, size_t smem, int64_t nt
   return cudaGetLastError();
 }
 
+// The grid a launch of the fused sweep uses (one wave of resident blocks,
+// capped by the tiles): the number of residual partials of the instance.
+template <int NQ>
+static int fused_grid_t(size_t smem, int64_t ntiles, int ft) {
+  switch (ft) {
+    case 2: return one_wave_grid(k_sweep_fused<NQ, 2>, 64, smem, ntiles, kFusedMaxBlocks);
+    case 8: return one_wave_grid(k_sweep_fused<NQ, 8>, 256, smem, ntiles, kFusedMaxBlocks);
+    default: return one_wave_grid(k_sweep_fused<NQ, 4>, 128, smem, ntiles, kFusedMaxBlocks);
+  }
+}
+
 template <int NQ>
 static cudaError_t launch_fused_t(const FusedParams& p, size_t smem, int64_t ntiles, int ft,
                                   cudaStream_t s, int* grid_out) {
@@ -283,6 +294,29 @@ static cudaError_t launch_fused_t(const FusedParams& p, size_t smem, int64_t nti
     case 2: return launch_fused_ft<NQ, 2>(p, smem, ntiles, s, grid_out);
     case 8: return launch_fused_ft<NQ, 8>(p, smem, ntiles, s, grid_out);
     default: return launch_fused_ft<NQ, 4>(p, smem, ntiles, s, grid_out);
+  }
+}
+
+size_t fused_sweep_smem(const Ctx& c) {
+  return sizeof(double) * ((c.shared_op ? (size_t)c.NQFS * c.NQFS : 0) + (size_t)c.NQFS * 32) +
+         sizeof(int) * c.F * 32;
+}
+
+int fused_sweep_grid(const Ctx& c) {
+  const size_t smem = fused_sweep_smem(c);
+  const int64_t ntiles = (c.nel + 31) / 32;
+  switch (c.NQFS) {
+    case 8: return fused_grid_t<8>(smem, ntiles, c.sweep_ft);
+    case 12: return fused_grid_t<12>(smem, ntiles, c.sweep_ft);
+    case 16: return fused_grid_t<16>(smem, ntiles, c.sweep_ft);
+    case 20: return fused_grid_t<20>(smem, ntiles, c.sweep_ft);
+    case 24: return fused_grid_t<24>(smem, ntiles, c.sweep_ft);
+    case 28: return fused_grid_t<28>(smem, ntiles, c.sweep_ft);
+    case 36: return fused_grid_t<36>(smem, ntiles, c.sweep_ft);
+    case 40: return fused_grid_t<40>(smem, ntiles, c.sweep_ft);
+    case 54: return fused_grid_t<54>(smem, ntiles, c.sweep_ft);
+    case 96: return fused_grid_t<96>(smem, ntiles, c.sweep_ft);
+    default: return fused_grid_t<0>(smem, ntiles, c.sweep_ft);
   }
 }
 
@@ -317,8 +351,7 @@ cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
   p.hist = c.hist;
   p.graph_mode = graph_mode;
   p.handle = c.handle;
-  const size_t smem = sizeof(double) * ((p.shared ? (size_t)c.NQFS * c.NQFS : 0) +
-                                        (size_t)c.NQFS * 32) + sizeof(int) * c.F * 32;
+  const size_t smem = fused_sweep_smem(c);
   const int64_t ntiles = (c.nel + 31) / 32;
   int grid = 1;
   cudaError_t err;

@@ -102,6 +102,7 @@ _SIGS = [
     ("ehdg_batch_instance", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
     ("ehdg_batch_run", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     ("ehdg_batch_set_chains", C.c_int, [C.c_void_p, C.c_int]),
+    ("ehdg_batch_set_loop", C.c_int, [C.c_void_p, C.c_int]),
     ("ehdg_batch_autotune_chains", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
                                              C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_batch_autotune_sweep_tile", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
@@ -479,6 +480,11 @@ class Batch:
         _check(load().ehdg_batch_run(self._h, int(n_steps), iters.ctypes.data_as(C.c_void_p),
                                      times.ctypes.data_as(C.c_void_p)))
         return iters, times
+
+    def set_loop(self, on=True):
+        """Batched iteration loop for the instances it supports (default on);
+        off runs every instance's own loop on the graph's branches."""
+        _check(load().ehdg_batch_set_loop(self._h, 1 if on else 0))
 
     def set_chains(self, k):
         """Concurrent branches of the batch's graph (k <= 0: one per hardware

@@ -159,3 +159,92 @@ def test_batch_inner_sweep_autotuner(ehdg):
         with pytest.raises(ehdg.EhdgError) as ei:
             b.autotune_inner_sweeps((3, 6))
         assert ei.value.status == 1
+
+
+def loop_instances(n=10, seed=31, precisions=("fp64", "tf32", "bf16")):
+    """Instances the batched loop supports (2D, constant velocity, uniform
+    mesh), of different sizes, degrees and precisions."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nx, ny = int(rng.integers(2, 17)), int(rng.integers(2, 17))
+        p = int(rng.integers(1, 6))
+        th = rng.uniform(0.05, 1.5) + (np.pi / 2) * int(rng.integers(0, 4))
+        beta = rng.uniform(0.5, 1.5) * np.array([np.cos(th), np.sin(th)])
+        mesh = W.structured_mesh((nx, ny))
+        prob = Problem(mesh, p, scheme="be", dt=0.01, beta_const=beta)
+        X = node_coords(mesh, p)
+        XF = face_point_coords(mesh, p, prob.ref.q)
+        c = rng.uniform(0.2, 0.8, 2)
+        s = rng.uniform(0.05, 0.15)
+        kw = dict(mesh=mesh, p=p, scheme="be", dt=0.01, tol=1e-12, max_iter=500,
+                  beta_const=beta, precision=precisions[i % len(precisions)], inner_sweeps=3 + i % 3)
+        out.append((kw, prob, W.gaussian(X, c, s)[:, None, :], W.gaussian(XF, c, s)))
+    return out
+
+
+def run_loop(ehdg, inst, n_steps, loop=True):
+    with ehdg.Batch([kw for kw, _, _, _ in inst]) as b:
+        b.set_loop(loop)
+        for (kw, prob, u0, g), s in zip(inst, b.instances):
+            s.set_boundary(g)
+            s.set_state(u0)
+        iters, times = b.run(n_steps)
+        return iters, times, [s.get_state() for s in b.instances]
+
+
+def test_batched_loop_matches_solo_runs_bitwise(ehdg):
+    """Every instance iterating in the batched loop (one launch per kernel and
+    iteration over all unconverged instances) gives the iterations and the
+    state of its solo run, bit for bit, and the oracle's solution."""
+    inst = loop_instances()
+    n_steps = 3
+    iters, times, states = run_loop(ehdg, inst, n_steps)
+    assert np.all(times > 0)
+    for i, (kw, prob, u0, g) in enumerate(inst):
+        args = dict(kw)
+        mesh = args.pop("mesh")
+        p = args.pop("p")
+        with ehdg.Solver(mesh, p, **args) as s:
+            s.set_boundary(g)
+            s.set_state(u0)
+            solo_iters = s.run(n_steps)
+            u, uh = s.get_state()
+        assert list(iters[i]) == solo_iters, (i, kw["precision"])
+        assert np.array_equal(states[i][0], u), (i, kw["precision"])
+        assert np.array_equal(states[i][1], uh), (i, kw["precision"])
+        ou, _, _, _ = prob.run(u0, n_steps, g_of_t=lambda t: g, tol=1e-13, max_iter=2000)
+        assert np.linalg.norm(u - ou) / np.linalg.norm(ou) < 1e-10, (i, kw["precision"])
+
+
+def test_batched_loop_equals_branch_graph(ehdg):
+    """The loop on and off (every instance's own loop on the graph's branches)
+    give the same iterations and states, bit for bit, also with instances
+    the loop does not take (FP32 corrections, the FP64-accurate tensor-core
+    path) in the same batch."""
+    inst = loop_instances(n=9, seed=32, precisions=("fp64", "tf32", "bf16", "fp32",
+                                                     "fp64_emulated"))
+    a_iters, _, a_states = run_loop(ehdg, inst, 2, loop=True)
+    b_iters, _, b_states = run_loop(ehdg, inst, 2, loop=False)
+    assert np.array_equal(a_iters, b_iters)
+    for (u, uh), (ru, ruh) in zip(a_states, b_states):
+        assert np.array_equal(u, ru) and np.array_equal(uh, ruh)
+
+
+def test_batched_loop_reports_an_instance_that_does_not_converge(ehdg):
+    """An instance that hits max_iter stops with EHDG_ERR_NOT_CONVERGED while
+    the others run on to their tolerance."""
+    inst = loop_instances(n=4, seed=33, precisions=("fp64", "tf32"))
+    kw0 = dict(inst[0][0], tol=1e-30, max_iter=3)
+    inst[0] = (kw0,) + inst[0][1:]
+    with ehdg.Batch([kw for kw, _, _, _ in inst]) as b:
+        for (kw, prob, u0, g), s in zip(inst, b.instances):
+            s.set_boundary(g)
+            s.set_state(u0)
+        with pytest.raises(ehdg.EhdgError) as ei:
+            b.run(1)
+        assert ei.value.status == 4
+        states = [s.get_state() for s in b.instances]
+    for i, (kw, prob, u0, g) in enumerate(inst[1:], start=1):
+        ou, _, _, _ = prob.run(u0, 1, g_of_t=lambda t: g, tol=1e-13, max_iter=2000)
+        assert np.linalg.norm(states[i][0] - ou) / np.linalg.norm(ou) < 1e-10, i
