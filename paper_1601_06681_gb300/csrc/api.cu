@@ -1563,6 +1563,13 @@ ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_t
   std::vector<unsigned long long> acc(n);
   CK(cudaMemcpyAsync(acc.data(), b->t_acc, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost,
                      b->stream));
+  // flags of tensor-core waits that gave up (read with the results)
+  std::vector<int> tc_err(n, 0);
+  for (int i = 0; i < n; ++i) {
+    Ctx& c = b->inst[i]->c;
+    if (c.tc_err && (c.mixed || c.use_ozaki))
+      CK(cudaMemcpyAsync(&tc_err[i], c.tc_err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  }
   ehdg_status first = EHDG_OK;
   for (int i = 0; i < n; ++i) {
     Ctx& c = b->inst[i]->c;
@@ -1587,10 +1594,9 @@ ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_t
     c.last_iters = std::min(c.step_iters_h[n_steps - 1], c.max_iter);
     if (inst_time_s) inst_time_s[i] = (double)acc[i] * 1e-9;
   }
-  for (int i = 0; i < n && first == EHDG_OK; ++i) {
-    const ehdg_status te = check_tc_err(b->inst[i]->c);
-    if (te != EHDG_OK) first = te;
-  }
+  for (int i = 0; i < n && first == EHDG_OK; ++i)
+    if (tc_err[i]) first = fail(EHDG_ERR_TIMEOUT, "instance " + std::to_string(i) +
+                                                      ": a sweep's bounded mbarrier wait gave up");
   // a schedule made on guessed iteration counts is made again on the
   // measured ones, once, before the next run
   if (first == EHDG_OK && b->built_on_estimate) TRY(batch_build_graph(b));
