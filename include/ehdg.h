@@ -291,11 +291,13 @@ ehdg_status ehdg_batch_set_chains(ehdg_batch b, int k);
  * on the branches. The graph is recaptured at the next run. EHDG_ERR_INVALID
  * for a NULL batch. */
 ehdg_status ehdg_batch_set_loop(ehdg_batch b, int on);
-/* Autotuner for the branch count: from the instances' current states, one
- * batch step (graph launch) per candidate k, timed with CUDA events on the
- * batch's stream, every instance's state restored after each; keeps the
- * fastest candidate and reports it with its time. The states are left as
- * they were. EHDG_ERR_INVALID for a NULL batch or no candidates. */
+/* Autotuner for the branch count: from the instances' current states, each
+ * candidate k runs as many batch steps as the batch's last ehdg_batch_run
+ * (one step before the first run) -- the run the choice is for -- timed with
+ * CUDA events on the batch's stream, every instance's state restored after
+ * each; keeps the fastest candidate and reports it with its time (of all
+ * those steps). The states are left as they were. EHDG_ERR_INVALID for a
+ * NULL batch or no candidates. */
 ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* candidates, int n_candidates,
                                        int* best, double* best_ms);
 /* Autotuner for the tile shape (FT, as in ehdg_autotune_sweep_tile) of every

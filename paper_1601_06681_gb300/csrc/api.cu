@@ -30,6 +30,8 @@ struct ehdg_batch_s {
   // batched iteration loop (one launch per kernel and iteration over every
   // unconverged instance) for the instances it supports
   bool use_loop = true;
+  int last_run_steps = 0;               // steps of the last run: what the autotuners time
+  bool tuning = false;                  // an autotuner is running candidate steps
   ehdg::BatchLoop loop;
   std::vector<char> looped;             // instance i iterates in the batched loop
   std::vector<cudaStream_t> lbranch;    // branches of the looped instances' step kernels
@@ -1544,6 +1546,7 @@ ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_t
   if (!b || n_steps < 0) return fail(EHDG_ERR_INVALID, "bad argument");
   const int n = (int)b->inst.size();
   if (n_steps == 0) return EHDG_OK;
+  if (!b->tuning) b->last_run_steps = n_steps;
   bool rebuild = !b->exec;
   for (int i = 0; i < n; ++i) {
     Ctx& c = b->inst[i]->c;
@@ -1656,13 +1659,17 @@ static ehdg_status batch_time_variants(ehdg_batch b, int n, Apply apply, double*
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   ehdg_status st = EHDG_OK;
+  // each candidate is timed over as many steps as the batch's last run (the
+  // run the choice is for), or one step before the first run
+  const int steps = b->last_run_steps > 0 ? b->last_run_steps : 1;
+  b->tuning = true;
   for (int q = 0; q < n; ++q) {
     ms[q] = 1e300;
     if (st != EHDG_OK || !apply(q)) continue;
     for (int rep = 0; rep < 2 && st == EHDG_OK; ++rep) {
       if (rep == 0) batch_destroy_graph(b);
       cudaEventRecord(e0, b->stream);
-      st = ehdg_batch_run(b, 1, nullptr, nullptr);
+      st = ehdg_batch_run(b, steps, nullptr, nullptr);
       cudaEventRecord(e1, b->stream);
       cudaEventSynchronize(e1);
       float t = 0.f;
@@ -1671,6 +1678,7 @@ static ehdg_status batch_time_variants(ehdg_batch b, int n, Apply apply, double*
       if (rep == 1 && st == EHDG_OK) ms[q] = t;
     }
   }
+  b->tuning = false;
   free_snap();
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
