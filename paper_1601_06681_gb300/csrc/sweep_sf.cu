@@ -70,11 +70,13 @@ struct SfParams {
   double* u;
 };
 
-// Bs uhat of the tile's elements: uh [NQ][32] (face points) -> rb [NB][32]
-// (boundary nodes), through tmp [NQ][32]; threads t = 0 .. FT-1 of each lane.
+// Bs uhat of the tile's elements: uh [NQ][32] (face points) -> [NB][32]
+// (boundary nodes) in tmp, through tmp [NQ][32] itself: the second pass keeps
+// its results in registers until every thread has read the first pass's.
+// Threads t = 0 .. FT-1 of each lane.
 template <int P1, int FT>
 __device__ __forceinline__ void sf_face_passes(const SfParams& p, const double* uh, double* tmp,
-                                               double* rb, int lane, int t) {
+                                               int lane, int t) {
   constexpr int NQF = P1 * P1, NQ = 6 * NQF;
   constexpr int NB = P1 * P1 * P1 - (P1 - 2) * (P1 - 2) * (P1 - 2);
   // pass 1: tmp[f][j2][a1] = sum_j1 TW[a1][j1] uhat_f[j1 + q j2]
@@ -90,21 +92,33 @@ __device__ __forceinline__ void sf_face_passes(const SfParams& p, const double* 
   __syncthreads();
   // pass 2: rb[b] = sum over the faces f of node b of
   //         s_f sum_j2 TW[a_t2][j2] tmp[f][j2][a_t1]
-  for (int b = t; b < NB; b += FT) {
+  constexpr int NBT = (NB + FT - 1) / FT;
+  double rv[NBT];
+#pragma unroll
+  for (int k = 0; k < NBT; ++k) {
+    const int b = t + k * FT;
     double v = 0.0;
+    if (b < NB) {
 #pragma unroll
-    for (int m = 0; m < 3; ++m) {
-      const int e = p.bmap[b * 3 + m];
-      if (e < 0) break;
-      const int f = e & 15, a1 = (e >> 4) & 15, a2 = (e >> 8) & 15;
-      const double* w = p.tw + a2 * P1;
-      const double* u = tmp + (f * NQF + a1) * 32 + lane;
-      double x = 0.0;
+      for (int m = 0; m < 3; ++m) {
+        const int e = p.bmap[b * 3 + m];
+        if (e < 0) break;
+        const int f = e & 15, a1 = (e >> 4) & 15, a2 = (e >> 8) & 15;
+        const double* w = p.tw + a2 * P1;
+        const double* u = tmp + (f * NQF + a1) * 32 + lane;
+        double x = 0.0;
 #pragma unroll
-      for (int j2 = 0; j2 < P1; ++j2) x = fma(w[j2], u[j2 * P1 * 32], x);
-      v = fma(p.s[f], x, v);
+        for (int j2 = 0; j2 < P1; ++j2) x = fma(w[j2], u[j2 * P1 * 32], x);
+        v = fma(p.s[f], x, v);
+      }
     }
-    rb[b * 32 + lane] = v;
+    rv[k] = v;
+  }
+  __syncthreads();                                    // every thread done reading pass 1
+#pragma unroll
+  for (int k = 0; k < NBT; ++k) {
+    const int b = t + k * FT;
+    if (b < NB) tmp[b * 32 + lane] = rv[k];
   }
 }
 
@@ -116,9 +130,9 @@ __global__ void __launch_bounds__(32 * FT) k_sweep_sf(const SfParams p) {
   const int lane = threadIdx.x, t = threadIdx.y;
   double* Dsh = sm;                                   // [n_rows][NB]
   double* uh = Dsh + p.n_rows * NB;                   // [NQ][32]
-  double* tmp = uh + NQ * 32;                         // [NQ][32]
-  double* rb = tmp + NQ * 32;                         // [NB][32]
-  int* fid = reinterpret_cast<int*>(rb + NB * 32);    // [6][32]
+  double* tmp = uh + NQ * 32;                         // [NQ][32], then [NB][32] boundary values
+  const double* rb = tmp;
+  int* fid = reinterpret_cast<int*>(tmp + NQ * 32);   // [6][32]
   for (int i = t * 32 + lane; i < p.n_rows * NB; i += 32 * FT) {
     const int j = i / NB, b = i - j * NB;
     Dsh[i] = p.Dy[p.rows[j] * NB + b];
@@ -142,7 +156,7 @@ __global__ void __launch_bounds__(32 * FT) k_sweep_sf(const SfParams p) {
       uh[i * 32 + lane] = live ? src[g * nface + fid[f * 32 + lane]] : 0.0;
     }
     __syncthreads();
-    sf_face_passes<P1, FT>(p, uh, tmp, rb, lane, t);
+    sf_face_passes<P1, FT>(p, uh, tmp, lane, t);
     __syncthreads();
     if (!live) continue;
     for (int j = t; j < p.n_rows; j += FT) {
@@ -196,7 +210,7 @@ __global__ void __launch_bounds__(32 * FT) k_final_sf(const SfParams p) {
   double* Ash = sm;                                   // [n][NB]
   double* uh = Ash + p.n * NB;
   double* tmp = uh + NQ * 32;
-  double* rb = tmp + NQ * 32;
+  const double* rb = tmp;
   for (int i = t * 32 + lane; i < p.n * NB; i += 32 * FT) Ash[i] = p.Ab[i];
   const int64_t ne = p.nel, nface = p.nface;
   const double* src = p.uhat + (int64_t)((p.it->k + 1) & 1) * NQF * nface;
@@ -210,7 +224,7 @@ __global__ void __launch_bounds__(32 * FT) k_final_sf(const SfParams p) {
       uh[i * 32 + lane] = live ? src[g * nface + p.elem_face[f * ne + e]] : 0.0;
     }
     __syncthreads();
-    sf_face_passes<P1, FT>(p, uh, tmp, rb, lane, t);
+    sf_face_passes<P1, FT>(p, uh, tmp, lane, t);
     __syncthreads();
     if (!live) continue;
     for (int r = t; r < p.n; r += FT) {
@@ -268,7 +282,7 @@ template <int P1, int FT>
 cudaError_t launch_sweep_sf_t(const SfParams& p, cudaStream_t s, int* grid_out) {
   constexpr int NQ = 6 * P1 * P1;
   constexpr int NB = P1 * P1 * P1 - (P1 - 2) * (P1 - 2) * (P1 - 2);
-  const size_t smem = sizeof(double) * ((size_t)p.n_rows * NB + 2 * NQ * 32 + NB * 32) +
+  const size_t smem = sizeof(double) * ((size_t)p.n_rows * NB + 2 * NQ * 32) +
                       sizeof(int) * 6 * 32;
   cudaError_t err = cudaFuncSetAttribute(k_sweep_sf<P1, FT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -293,7 +307,7 @@ cudaError_t launch_final_sf_t(const SfParams& p, cudaStream_t s) {
   constexpr int FT = 4;
   constexpr int NQ = 6 * P1 * P1;
   constexpr int NB = P1 * P1 * P1 - (P1 - 2) * (P1 - 2) * (P1 - 2);
-  const size_t smem = sizeof(double) * ((size_t)p.n * NB + 2 * NQ * 32 + NB * 32);
+  const size_t smem = sizeof(double) * ((size_t)p.n * NB + 2 * NQ * 32);
   cudaError_t err = cudaFuncSetAttribute(k_final_sf<P1, FT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (err != cudaSuccess) return err;
