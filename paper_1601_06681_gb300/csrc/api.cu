@@ -1332,8 +1332,8 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
     b->looped[i] = 1;
     ++n_loop;
   }
-  if (n_loop == 0) {
-    b->loop.release();
+  if (n_loop == 0 || n_loop > 8192) {   // the loop's list builder keeps a flag per instance
+    b->loop.release();                   // in shared memory
     return batch_build_graph_branches(b);
   }
   batch_destroy_graph(b);
@@ -1422,7 +1422,8 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
     if ((e = cudaEventRecord(j, s)) != cudaSuccess) break;
     e = cudaStreamWaitEvent(b->cap, j, 0);
   }
-  // the batched loop
+  // the batched loop (its first iteration's work lists, then the loop)
+  if (e == cudaSuccess && st == EHDG_OK) e = b->loop.launch_lists(b->cap);
   if (e == cudaSuccess && st == EHDG_OK) {
     cudaStreamCaptureStatus cst;
     cudaGraph_t g = nullptr;

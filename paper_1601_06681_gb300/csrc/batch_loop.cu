@@ -72,7 +72,83 @@ struct BInst {
   int* err;
   // convergence time of the instance in the current step (%globaltimer)
   unsigned long long* t_conv;
+  int n_tiles128, n_chunks;     // work items of its correction sweeps and of its update
 };
+
+// Work of the next loop iteration, rebuilt on the device after every FP64
+// sweep: the instances that still iterate, with the prefix sums of their
+// work items (the k-th listed instance owns items pre[k] .. pre[k+1]-1), so
+// a launch visits live work only. Layout in one int array of size
+// kListHeader + 5 n + 3:
+//   [0] instances in the sweep list, [1] in the correction list (mixed
+//   precision), then act_sw[n], pre_sw[n+1], act_mx[n], pre_tc[n+1], pre_ap[n+1].
+constexpr int kListHeader = 2;
+struct ListView {
+  int n;
+  template <class T> __device__ T* act_sw(T* L) const { return L + kListHeader; }
+  template <class T> __device__ T* pre_sw(T* L) const { return L + kListHeader + n; }
+  template <class T> __device__ T* act_mx(T* L) const { return L + kListHeader + 2 * n + 1; }
+  template <class T> __device__ T* pre_tc(T* L) const { return L + kListHeader + 3 * n + 1; }
+  template <class T> __device__ T* pre_ap(T* L) const { return L + kListHeader + 4 * n + 2; }
+};
+
+// Rebuild the lists from the instances' continue flags (one block).
+__device__ void build_lists(const BInst* inst, int n_inst, int* L) {
+  extern __shared__ double sm[];
+  __shared__ int s_any;
+  const ListView v{n_inst};
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  __syncthreads();
+  // the flags, in a scratch area of shared memory the caller no longer uses
+  int* flag = reinterpret_cast<int*>(sm);
+  for (int i = tid; i < n_inst; i += nt)
+    flag[i] = reinterpret_cast<volatile IterState*>(inst[i].it)->cont;
+  __syncthreads();
+  if (tid == 0) {
+    int ns = 0, nm = 0, ps = 0, pt = 0, pa = 0;
+    int* act_sw = v.act_sw(L);
+    int* pre_sw = v.pre_sw(L);
+    int* act_mx = v.act_mx(L);
+    int* pre_tc = v.pre_tc(L);
+    int* pre_ap = v.pre_ap(L);
+    for (int i = 0; i < n_inst; ++i) {
+      if (!flag[i]) continue;
+      act_sw[ns] = i;
+      pre_sw[ns] = ps;
+      ps += inst[i].vblocks;
+      ++ns;
+      if (inst[i].tc) {
+        act_mx[nm] = i;
+        pre_tc[nm] = pt;
+        pre_ap[nm] = pa;
+        pt += inst[i].n_tiles128;
+        pa += inst[i].n_chunks;
+        ++nm;
+      }
+    }
+    pre_sw[ns] = ps;
+    pre_tc[nm] = pt;
+    pre_ap[nm] = pa;
+    L[0] = ns;
+    L[1] = nm;
+    __threadfence();
+    s_any = ns;
+  }
+  __syncthreads();
+  (void)s_any;
+}
+
+// Which listed instance owns item w: the last k with pre[k] <= w (binary
+// search over the prefix sums, k < count).
+__device__ __forceinline__ int owner_of(const int* pre, int count, int w) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
@@ -94,26 +170,25 @@ __device__ __forceinline__ void batch_tiles(const BInst& I, int j, const double*
 // One FP64 sweep of every unconverged instance; items[w] = (instance,
 // block j of its own launch).
 template <int FT>
-__global__ void __launch_bounds__(32 * FT) k_batch_sweep(const BInst* inst, const int2* items,
-                                                          int n_items, int n_inst,
-                                                          unsigned int* ticket,
+__global__ void __launch_bounds__(32 * FT) k_batch_sweep(const BInst* inst, int* lists,
+                                                          int n_inst, unsigned int* ticket,
                                                           cudaGraphConditionalHandle handle) {
   extern __shared__ double sm[];
-  __shared__ int s_live, s_kk;
   const int tid = threadIdx.y * 32 + threadIdx.x;
+  const ListView lv{n_inst};
+  const int n_act = lists[0];
+  const int* act = lv.act_sw(lists);
+  const int* pre = lv.pre_sw(lists);
+  const int n_items = n_act > 0 ? pre[n_act] : 0;
   int cur = -1;
   double* Hsh = sm;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int2 item = items[w];
-    const BInst& I = inst[item.x];
-    __syncthreads();   // the previous item is done with the shared scratch and flags
-    // the instance's state cannot change before all its work items are done
-    if (tid == 0) {
-      s_live = reinterpret_cast<volatile IterState*>(I.it)->cont;
-      s_kk = reinterpret_cast<volatile IterState*>(I.it)->k;
-    }
-    __syncthreads();
-    if (!s_live) continue;
+    // every listed instance iterates; its state cannot change before all its
+    // work items are done
+    const int k = owner_of(pre, n_act, w);
+    const int idx = act[k];
+    const int2 item = make_int2(idx, w - pre[k]);
+    const BInst& I = inst[idx];
     const int nq = I.NQFS;
     double* uh = sm + nq * nq;
     int* fid = reinterpret_cast<int*>(uh + nq * 32);
@@ -121,7 +196,7 @@ __global__ void __launch_bounds__(32 * FT) k_batch_sweep(const BInst* inst, cons
       for (int i = tid; i < nq * nq; i += 32 * FT) Hsh[i] = I.Hy[i];
       cur = item.x;
     }
-    const int kk = s_kk;
+    const int kk = reinterpret_cast<volatile IterState*>(I.it)->k;
     const int64_t tlen = (int64_t)I.Nqf * I.nface;
     const double* src = I.uhat + (int64_t)(kk & 1) * tlen;
     double* dst = I.uhat + (int64_t)((kk + 1) & 1) * tlen;
@@ -149,14 +224,18 @@ __global__ void __launch_bounds__(32 * FT) k_batch_sweep(const BInst* inst, cons
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  int any = 0;
-  for (int i = tid; i < n_inst; i += 32 * FT)
-    any |= reinterpret_cast<volatile IterState*>(inst[i].it)->cont;
-  any = __syncthreads_or(any);
+  // the next iteration's work, and the loop condition
+  build_lists(inst, n_inst, lists);
   if (tid == 0) {
     *ticket = 0u;
-    cudaGraphSetConditional(handle, any ? 1u : 0u);
+    cudaGraphSetConditional(handle, lists[0] > 0 ? 1u : 0u);
   }
+}
+
+// The work lists at the start of a step's loop (after the instances' reset,
+// right-hand side and, for mixed precision, first FP64 sweep).
+__global__ void k_batch_lists(const BInst* inst, int n_inst, int* lists) {
+  build_lists(inst, n_inst, lists);
 }
 
 __device__ __forceinline__ uint32_t b_to_tf32(float x) {
@@ -196,13 +275,12 @@ __device__ __forceinline__ void b_store_elem(unsigned char* base, int row, int k
 // instance: delta_out = R + (delta_in Hy^T at the rows), owner writes; items[w]
 // = (instance, 128-element tile). The operands, MMA shapes and epilogue are
 // those of the single-problem tensor-core correction sweep.
-__global__ void __launch_bounds__(kBTcThreads) k_batch_tc(const BInst* inst, const int2* items,
-                                                          int n_items, int j, int ncols,
+__global__ void __launch_bounds__(kBTcThreads) k_batch_tc(const BInst* inst, const int* lists,
+                                                          int n_inst, int j, int ncols,
                                                           int smem_b, int smem_a) {
   extern __shared__ __align__(1024) unsigned char smb[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  __shared__ int s_live;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int row = tid & (kBTcM - 1), half = tid >> 7;
   if (tid == 0) {
@@ -227,13 +305,17 @@ __global__ void __launch_bounds__(kBTcThreads) k_batch_tc(const BInst* inst, con
   uint32_t phase = 0;
   bool failed = false;
   int cur = -1;
+  const ListView lv{n_inst};
+  const int n_act = lists[1];
+  const int* act = lv.act_mx(lists);
+  const int* pre = lv.pre_tc(lists);
+  const int n_items = n_act > 0 ? pre[n_act] : 0;
   for (int w = blockIdx.x; w < n_items && !failed; w += gridDim.x) {
-    const int2 item = items[w];
+    const int k = owner_of(pre, n_act, w);
+    const int2 item = make_int2(act[k], w - pre[k]);
     const BInst& I = inst[item.x];
-    __syncthreads();   // the previous item is done with the shared operands and flags
-    if (tid == 0) s_live = (I.tc && I.m > j) ? reinterpret_cast<volatile IterState*>(I.it)->cont : 0;
-    __syncthreads();
-    if (!s_live) continue;
+    if (I.m <= j) continue;                         // its inner sweeps are done
+    __syncthreads();   // the previous item is done with the shared operands
     const int esize = I.bf16 ? 2 : 4;
     const uint32_t kbytes = (uint32_t)I.Kp * esize;
     const uint32_t sbo = kbytes * 8u;
@@ -374,12 +456,17 @@ __global__ void __launch_bounds__(kBTcThreads) k_batch_tc(const BInst* inst, con
 // uhat <- uhat + delta in FP64 for every unconverged mixed-precision
 // instance (the single-problem update, slot k&1 = slot (k+1)&1 + delta of
 // its last inner sweep); items[w] = (instance, chunk of kApplyChunk entries).
-__global__ void __launch_bounds__(256) k_batch_apply(const BInst* inst, const int2* items,
-                                                     int n_items) {
+__global__ void __launch_bounds__(256) k_batch_apply(const BInst* inst, const int* lists,
+                                                     int n_inst) {
+  const ListView lv{n_inst};
+  const int n_act = lists[1];
+  const int* act = lv.act_mx(lists);
+  const int* pre = lv.pre_ap(lists);
+  const int n_items = n_act > 0 ? pre[n_act] : 0;
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-    const int2 item = items[w];
+    const int k = owner_of(pre, n_act, w);
+    const int2 item = make_int2(act[k], w - pre[k]);
     const BInst& I = inst[item.x];
-    if (!I.tc || !reinterpret_cast<volatile IterState*>(I.it)->cont) continue;
     const int K = reinterpret_cast<volatile IterState*>(I.it)->k;
     const int64_t total = (int64_t)I.Nqf * I.nface;
     double* dst = I.uhat + (int64_t)(K & 1) * total;
@@ -418,9 +505,7 @@ bool batch_loop_ok(const Ctx& c) {
 
 struct BatchLoop::Impl {
   BInst* d_inst = nullptr;
-  int2* d_sweep = nullptr;
-  int2* d_tc = nullptr;
-  int2* d_apply = nullptr;
+  int* d_lists = nullptr;
   unsigned int* d_ticket = nullptr;
   int n_inst = 0, n_sweep = 0, n_tc = 0, n_apply = 0, max_m = 0, ft = 4;
   int sweep_grid = 1, tc_grid = 1, apply_grid = 1, tc_ncols = 32, tc_smem_b = 0, tc_smem_a = 0;
@@ -432,9 +517,7 @@ BatchLoop::~BatchLoop() { release(); }
 void BatchLoop::release() {
   if (!impl) return;
   cudaFree(impl->d_inst);
-  cudaFree(impl->d_sweep);
-  cudaFree(impl->d_tc);
-  cudaFree(impl->d_apply);
+  cudaFree(impl->d_lists);
   cudaFree(impl->d_ticket);
   delete impl;
   impl = nullptr;
@@ -449,8 +532,7 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
   L.n_inst = (int)ctxs.size();
   L.ft = ctxs.empty() ? 4 : ctxs[0]->sweep_ft;
   std::vector<BInst> h(L.n_inst);
-  std::vector<int2> sw, tc, ap;
-  size_t smem = 0;
+  size_t smem = sizeof(int) * (size_t)L.n_inst;      // the list builder's flags
   int max_kp_bytes = 0, max_np = 16;
   for (int i = 0; i < L.n_inst; ++i) {
     const Ctx& c = *ctxs[i];
@@ -482,7 +564,7 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     I.t_conv = t_conv + slot[i];
     I.err = c.tc_err;
     smem = std::max(smem, fused_sweep_smem(c));
-    for (int j = 0; j < I.vblocks; ++j) sw.push_back(make_int2(i, j));
+    L.n_sweep += I.vblocks;
     if (c.mixed) {
       I.tc = 1;
       I.bf16 = c.precision == EHDG_MIXED_BF16 ? 1 : 0;
@@ -498,36 +580,26 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
       L.max_m = std::max(L.max_m, I.m);
       max_kp_bytes = std::max(max_kp_bytes, I.Kp * (I.bf16 ? 2 : 4));
       max_np = std::max(max_np, I.Np);
-      const int64_t tiles = (c.nel + kBTcM - 1) / kBTcM;
-      for (int64_t t = 0; t < tiles; ++t) tc.push_back(make_int2(i, (int)t));
+      I.n_tiles128 = (int)((c.nel + kBTcM - 1) / kBTcM);
       const int64_t total = (int64_t)c.Nqf * c.nface;
-      for (int64_t t = 0; t * kApplyChunk < total; ++t) ap.push_back(make_int2(i, (int)t));
+      I.n_chunks = (int)((total + kApplyChunk - 1) / kApplyChunk);
+      L.n_tc += I.n_tiles128;
+      L.n_apply += I.n_chunks;
     }
   }
-  L.n_sweep = (int)sw.size();
-  L.n_tc = (int)tc.size();
-  L.n_apply = (int)ap.size();
   L.sweep_smem = smem;
   cudaError_t e;
+  const size_t list_ints = kListHeader + 5 * (size_t)L.n_inst + 3;
   if ((e = cudaMalloc(&L.d_inst, sizeof(BInst) * std::max(1, L.n_inst))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&L.d_sweep, sizeof(int2) * std::max(1, L.n_sweep))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&L.d_tc, sizeof(int2) * std::max(1, L.n_tc))) != cudaSuccess) return e;
-  if ((e = cudaMalloc(&L.d_apply, sizeof(int2) * std::max(1, L.n_apply))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_lists, sizeof(int) * list_ints)) != cudaSuccess) return e;
+  if ((e = cudaMemset(L.d_lists, 0, sizeof(int) * list_ints)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&L.d_ticket, sizeof(unsigned int))) != cudaSuccess) return e;
   if ((e = cudaMemset(L.d_ticket, 0, sizeof(unsigned int))) != cudaSuccess) return e;
   if ((e = cudaMemcpy(L.d_inst, h.data(), sizeof(BInst) * L.n_inst, cudaMemcpyHostToDevice)) !=
       cudaSuccess)
     return e;
-  if (L.n_sweep && (e = cudaMemcpy(L.d_sweep, sw.data(), sizeof(int2) * L.n_sweep,
-                                   cudaMemcpyHostToDevice)) != cudaSuccess)
-    return e;
-  if (L.n_tc && (e = cudaMemcpy(L.d_tc, tc.data(), sizeof(int2) * L.n_tc,
-                                cudaMemcpyHostToDevice)) != cudaSuccess)
-    return e;
-  if (L.n_apply && (e = cudaMemcpy(L.d_apply, ap.data(), sizeof(int2) * L.n_apply,
-                                   cudaMemcpyHostToDevice)) != cudaSuccess)
-    return e;
-  // launch shapes: one wave of resident blocks each
+  // launch shapes: one wave of resident blocks each, capped by the most work
+  // an iteration can have (every instance iterating)
   auto wave = [](auto kernel, int threads, size_t sm, int items) {
     int bpsm = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, threads, sm) != cudaSuccess ||
@@ -559,31 +631,38 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
   return cudaSuccess;
 }
 
+// The work lists of the loop's first iteration (captured before the loop).
+cudaError_t BatchLoop::launch_lists(cudaStream_t s) {
+  Impl& L = *impl;
+  k_batch_lists<<<1, 256, sizeof(int) * (size_t)L.n_inst, s>>>(L.d_inst, L.n_inst, L.d_lists);
+  return cudaGetLastError();
+}
+
 // The loop body (captured into the WHILE node's body graph on stream s).
 cudaError_t BatchLoop::launch_body(cudaStream_t s, cudaGraphConditionalHandle handle) {
   Impl& L = *impl;
   cudaError_t e = cudaSuccess;
   for (int j = 0; j < L.max_m && L.n_tc; ++j) {
-    k_batch_tc<<<L.tc_grid, kBTcThreads, L.tc_smem, s>>>(L.d_inst, L.d_tc, L.n_tc, j,
+    k_batch_tc<<<L.tc_grid, kBTcThreads, L.tc_smem, s>>>(L.d_inst, L.d_lists, L.n_inst, j,
                                                         L.tc_ncols, L.tc_smem_b, L.tc_smem_a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (L.n_apply) {
-    k_batch_apply<<<L.apply_grid, 256, 0, s>>>(L.d_inst, L.d_apply, L.n_apply);
+    k_batch_apply<<<L.apply_grid, 256, 0, s>>>(L.d_inst, L.d_lists, L.n_inst);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   switch (L.ft) {
     case 2:
       k_batch_sweep<2><<<L.sweep_grid, dim3(32, 2), L.sweep_smem, s>>>(
-          L.d_inst, L.d_sweep, L.n_sweep, L.n_inst, L.d_ticket, handle);
+          L.d_inst, L.d_lists, L.n_inst, L.d_ticket, handle);
       break;
     case 8:
       k_batch_sweep<8><<<L.sweep_grid, dim3(32, 8), L.sweep_smem, s>>>(
-          L.d_inst, L.d_sweep, L.n_sweep, L.n_inst, L.d_ticket, handle);
+          L.d_inst, L.d_lists, L.n_inst, L.d_ticket, handle);
       break;
     default:
       k_batch_sweep<4><<<L.sweep_grid, dim3(32, 4), L.sweep_smem, s>>>(
-          L.d_inst, L.d_sweep, L.n_sweep, L.n_inst, L.d_ticket, handle);
+          L.d_inst, L.d_lists, L.n_inst, L.d_ticket, handle);
       break;
   }
   return cudaGetLastError();

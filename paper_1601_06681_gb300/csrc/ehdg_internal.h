@@ -281,6 +281,7 @@ struct BatchLoop {
   // i's convergence time in a step
   cudaError_t build(const std::vector<Ctx*>& ctxs, unsigned long long* t_conv,
                     const std::vector<int>& slot);
+  cudaError_t launch_lists(cudaStream_t s);   // the first iteration's work lists
   cudaError_t launch_body(cudaStream_t s, cudaGraphConditionalHandle handle);
   int kernels_per_iteration() const;
 };
