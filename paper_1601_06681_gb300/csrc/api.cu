@@ -821,6 +821,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   }
   c.n_up = n_up;
   c.n_rows = (int)rows.size();
+  c.rows_host = rows;
 
   // shared memory needed by the assembly kernel
   {

@@ -92,50 +92,79 @@ struct ListView {
   template <class T> __device__ T* pre_ap(T* L) const { return L + kListHeader + 4 * n + 2; }
 };
 
-// Rebuild the lists from the instances' continue flags (one block).
-__device__ void build_lists(const BInst* inst, int n_inst, int* L) {
+// Rebuild the lists from the instances' continue flags (one block): each
+// thread takes a contiguous run of instances, counts its run's work, the runs'
+// offsets come from a scan over the threads, and each thread writes its run.
+// counts[i] = (sweep items, 1 if mixed precision, correction tiles, update
+// chunks) of instance i.
+__device__ void build_lists(const BInst* inst, const int4* counts, int n_inst, int* L) {
   extern __shared__ double sm[];
-  __shared__ int s_any;
   const ListView v{n_inst};
   const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+  int* part = reinterpret_cast<int*>(sm);           // [5][nt]: per-thread sums, then offsets
   __syncthreads();
-  // the flags, in a scratch area of shared memory the caller no longer uses
-  int* flag = reinterpret_cast<int*>(sm);
-  for (int i = tid; i < n_inst; i += nt)
-    flag[i] = reinterpret_cast<volatile IterState*>(inst[i].it)->cont;
-  __syncthreads();
-  if (tid == 0) {
-    int ns = 0, nm = 0, ps = 0, pt = 0, pa = 0;
-    int* act_sw = v.act_sw(L);
-    int* pre_sw = v.pre_sw(L);
-    int* act_mx = v.act_mx(L);
-    int* pre_tc = v.pre_tc(L);
-    int* pre_ap = v.pre_ap(L);
-    for (int i = 0; i < n_inst; ++i) {
-      if (!flag[i]) continue;
-      act_sw[ns] = i;
-      pre_sw[ns] = ps;
-      ps += inst[i].vblocks;
-      ++ns;
-      if (inst[i].tc) {
-        act_mx[nm] = i;
-        pre_tc[nm] = pt;
-        pre_ap[nm] = pa;
-        pt += inst[i].n_tiles128;
-        pa += inst[i].n_chunks;
-        ++nm;
-      }
+  const int per = (n_inst + nt - 1) / nt;
+  const int i0 = min(n_inst, tid * per), i1 = min(n_inst, i0 + per);
+  int ns = 0, nm = 0, ps = 0, pt = 0, pa = 0;
+  for (int i = i0; i < i1; ++i) {
+    if (!reinterpret_cast<volatile IterState*>(inst[i].it)->cont) continue;
+    const int4 c = counts[i];
+    ++ns;
+    ps += c.x;
+    if (c.y) {
+      ++nm;
+      pt += c.z;
+      pa += c.w;
     }
-    pre_sw[ns] = ps;
-    pre_tc[nm] = pt;
-    pre_ap[nm] = pa;
-    L[0] = ns;
-    L[1] = nm;
-    __threadfence();
-    s_any = ns;
+  }
+  part[0 * nt + tid] = ns;
+  part[1 * nt + tid] = nm;
+  part[2 * nt + tid] = ps;
+  part[3 * nt + tid] = pt;
+  part[4 * nt + tid] = pa;
+  __syncthreads();
+  if (tid < 5) {             // exclusive scan of each quantity over the threads
+    int run = 0;
+    for (int t = 0; t < nt; ++t) {
+      const int x = part[tid * nt + t];
+      part[tid * nt + t] = run;
+      run += x;
+    }
+    if (tid == 0) L[0] = run;
+    if (tid == 1) L[1] = run;
   }
   __syncthreads();
-  (void)s_any;
+  const int ons = part[0 * nt + tid], onm = part[1 * nt + tid];
+  int ops = part[2 * nt + tid], opt = part[3 * nt + tid], opa = part[4 * nt + tid];
+  int ks = ons, km = onm;
+  int* act_sw = v.act_sw(L);
+  int* pre_sw = v.pre_sw(L);
+  int* act_mx = v.act_mx(L);
+  int* pre_tc = v.pre_tc(L);
+  int* pre_ap = v.pre_ap(L);
+  for (int i = i0; i < i1; ++i) {
+    if (!reinterpret_cast<volatile IterState*>(inst[i].it)->cont) continue;
+    const int4 c = counts[i];
+    act_sw[ks] = i;
+    pre_sw[ks] = ops;
+    ops += c.x;
+    ++ks;
+    if (c.y) {
+      act_mx[km] = i;
+      pre_tc[km] = opt;
+      pre_ap[km] = opa;
+      opt += c.z;
+      opa += c.w;
+      ++km;
+    }
+  }
+  if (tid == nt - 1) {       // the totals close the prefix arrays
+    pre_sw[ks] = ops;
+    pre_tc[km] = opt;
+    pre_ap[km] = opa;
+  }
+  __threadfence();
+  __syncthreads();
 }
 
 // Which listed instance owns item w: the last k with pre[k] <= w (binary
@@ -170,8 +199,9 @@ __device__ __forceinline__ void batch_tiles(const BInst& I, int j, const double*
 // One FP64 sweep of every unconverged instance; items[w] = (instance,
 // block j of its own launch).
 template <int FT>
-__global__ void __launch_bounds__(32 * FT) k_batch_sweep(const BInst* inst, int* lists,
-                                                          int n_inst, unsigned int* ticket,
+__global__ void __launch_bounds__(32 * FT) k_batch_sweep(const BInst* inst, const int4* counts,
+                                                          int* lists, int n_inst,
+                                                          unsigned int* ticket,
                                                           cudaGraphConditionalHandle handle) {
   extern __shared__ double sm[];
   const int tid = threadIdx.y * 32 + threadIdx.x;
@@ -225,7 +255,7 @@ __global__ void __launch_bounds__(32 * FT) k_batch_sweep(const BInst* inst, int*
   if (!s_last) return;
   __threadfence();
   // the next iteration's work, and the loop condition
-  build_lists(inst, n_inst, lists);
+  build_lists(inst, counts, n_inst, lists);
   if (tid == 0) {
     *ticket = 0u;
     cudaGraphSetConditional(handle, lists[0] > 0 ? 1u : 0u);
@@ -234,8 +264,8 @@ __global__ void __launch_bounds__(32 * FT) k_batch_sweep(const BInst* inst, int*
 
 // The work lists at the start of a step's loop (after the instances' reset,
 // right-hand side and, for mixed precision, first FP64 sweep).
-__global__ void k_batch_lists(const BInst* inst, int n_inst, int* lists) {
-  build_lists(inst, n_inst, lists);
+__global__ void k_batch_lists(const BInst* inst, const int4* counts, int n_inst, int* lists) {
+  build_lists(inst, counts, n_inst, lists);
 }
 
 __device__ __forceinline__ uint32_t b_to_tf32(float x) {
@@ -505,6 +535,7 @@ bool batch_loop_ok(const Ctx& c) {
 
 struct BatchLoop::Impl {
   BInst* d_inst = nullptr;
+  int4* d_counts = nullptr;
   int* d_lists = nullptr;
   unsigned int* d_ticket = nullptr;
   int n_inst = 0, n_sweep = 0, n_tc = 0, n_apply = 0, max_m = 0, ft = 4;
@@ -517,6 +548,7 @@ BatchLoop::~BatchLoop() { release(); }
 void BatchLoop::release() {
   if (!impl) return;
   cudaFree(impl->d_inst);
+  cudaFree(impl->d_counts);
   cudaFree(impl->d_lists);
   cudaFree(impl->d_ticket);
   delete impl;
@@ -532,7 +564,8 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
   L.n_inst = (int)ctxs.size();
   L.ft = ctxs.empty() ? 4 : ctxs[0]->sweep_ft;
   std::vector<BInst> h(L.n_inst);
-  size_t smem = sizeof(int) * (size_t)L.n_inst;      // the list builder's flags
+  std::vector<int4> cnt(L.n_inst);
+  size_t smem = sizeof(int) * 5 * 256;               // the list builder's scan
   int max_kp_bytes = 0, max_np = 16;
   for (int i = 0; i < L.n_inst; ++i) {
     const Ctx& c = *ctxs[i];
@@ -586,11 +619,16 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
       L.n_tc += I.n_tiles128;
       L.n_apply += I.n_chunks;
     }
+    cnt[i] = make_int4(I.vblocks, I.tc, I.n_tiles128, I.n_chunks);
   }
   L.sweep_smem = smem;
   cudaError_t e;
   const size_t list_ints = kListHeader + 5 * (size_t)L.n_inst + 3;
   if ((e = cudaMalloc(&L.d_inst, sizeof(BInst) * std::max(1, L.n_inst))) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_counts, sizeof(int4) * std::max(1, L.n_inst))) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(L.d_counts, cnt.data(), sizeof(int4) * L.n_inst, cudaMemcpyHostToDevice)) !=
+      cudaSuccess)
+    return e;
   if ((e = cudaMalloc(&L.d_lists, sizeof(int) * list_ints)) != cudaSuccess) return e;
   if ((e = cudaMemset(L.d_lists, 0, sizeof(int) * list_ints)) != cudaSuccess) return e;
   if ((e = cudaMalloc(&L.d_ticket, sizeof(unsigned int))) != cudaSuccess) return e;
@@ -634,7 +672,8 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
 // The work lists of the loop's first iteration (captured before the loop).
 cudaError_t BatchLoop::launch_lists(cudaStream_t s) {
   Impl& L = *impl;
-  k_batch_lists<<<1, 256, sizeof(int) * (size_t)L.n_inst, s>>>(L.d_inst, L.n_inst, L.d_lists);
+  k_batch_lists<<<1, 256, sizeof(int) * 5 * 256, s>>>(L.d_inst, L.d_counts, L.n_inst,
+                                                       L.d_lists);
   return cudaGetLastError();
 }
 
@@ -654,15 +693,15 @@ cudaError_t BatchLoop::launch_body(cudaStream_t s, cudaGraphConditionalHandle ha
   switch (L.ft) {
     case 2:
       k_batch_sweep<2><<<L.sweep_grid, dim3(32, 2), L.sweep_smem, s>>>(
-          L.d_inst, L.d_lists, L.n_inst, L.d_ticket, handle);
+          L.d_inst, L.d_counts, L.d_lists, L.n_inst, L.d_ticket, handle);
       break;
     case 8:
       k_batch_sweep<8><<<L.sweep_grid, dim3(32, 8), L.sweep_smem, s>>>(
-          L.d_inst, L.d_lists, L.n_inst, L.d_ticket, handle);
+          L.d_inst, L.d_counts, L.d_lists, L.n_inst, L.d_ticket, handle);
       break;
     default:
       k_batch_sweep<4><<<L.sweep_grid, dim3(32, 4), L.sweep_smem, s>>>(
-          L.d_inst, L.d_lists, L.n_inst, L.d_ticket, handle);
+          L.d_inst, L.d_counts, L.d_lists, L.n_inst, L.d_ticket, handle);
       break;
   }
   return cudaGetLastError();

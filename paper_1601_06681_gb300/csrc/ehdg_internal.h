@@ -100,6 +100,7 @@ struct Ctx {
   int8_t* sgn = nullptr;         // [Nqf][nface] sgn(beta.n^-) (transport)
   int* rows = nullptr;           // shared operator: element output rows (face points)
   int n_rows = 0;
+  std::vector<int> rows_host;    // host copy of rows
   uint8_t* rowid = nullptr;      // per-element operator: [NQFS][nel] row of each slot
   uint8_t* nrows = nullptr;      // [nel] slots in use
   uint8_t* nup = nullptr;        // [nel] leading slots that are upwind points (transport)
