@@ -927,7 +927,7 @@ def compare_workload(args):
         precisions = ["fp64", "fp32", "bf16"]
     else:
         wl = W.transport_2d_small(n=(n, n), p=2, n_steps=n_steps)
-        precisions = ["fp64", "fp64+tiles", "fp64_emulated", "tf32", "fp32"]
+        precisions = ["fp64", "fp64_emulated", "tf32", "fp32"]
     mesh = ehdg.ehdg_mesh_structured(wl.n, boundary_tag=(2 if wl.pde == "sw" else 1))
     results = {}
     ref = None
@@ -1085,7 +1085,7 @@ def batch_workload(args):
     # "+tiles": the fused FP64 sweep's tile (row groups FT) of all instances
     # from ehdg_batch_autotune_sweep_tile
     variants = ["fp64", "tf32", "bf16", "fp64+branches", "tf32+branches", "tf32+inner",
-                "fp64+tiles", "tf32+tiles", "fp64_emulated", "tf32+emulated_outer"]
+                "fp64_emulated", "tf32+emulated_outer"]
     for prec in variants:
         base, _, opt = prec.partition("+")
         specs, inputs = [], []

@@ -278,9 +278,8 @@ ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_t
 ehdg_status ehdg_batch_set_chains(ehdg_batch b, int k);
 /* Batched iteration loop (on by default). The instances it supports -- 2D
  * transport with one shared operator per instance (constant velocity,
- * uniform mesh), no face point with beta.n = 0, FP64 or TF32/BF16 mixed
- * precision, and the tile shape of the first such instance -- iterate
- * together: the graph of a step holds their once-per-step kernels on the
+ * uniform mesh), p <= 6, no face point with beta.n = 0, FP64 or TF32/BF16
+ * mixed precision -- iterate together: the graph of a step holds their once-per-step kernels on the
  * branches and ONE conditional loop whose every iteration is one launch of
  * each of: the m correction sweeps, the FP64 update, and the FP64 sweep, each
  * over the tiles of every instance that has not converged yet (instance and

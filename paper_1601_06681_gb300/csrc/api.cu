@@ -1029,6 +1029,18 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
       CKC(cudaMemcpy(c.tan_face, tf.data(), sizeof(int32_t) * tf.size(), cudaMemcpyHostToDevice));
     }
   }
+  if (pe_supported(c)) {
+    // one thread per element for the 2D shared-operator FP64 sweep
+    std::vector<double> fw(kMaxQ * kMaxQ, 0.0);
+    fill_face_weights(c, fw.data());
+    TRYC(dalloc(c, &c.pe_fw, (size_t)c.Nqf));
+    CKC(cudaMemcpy(c.pe_fw, fw.data(), sizeof(double) * c.Nqf, cudaMemcpyHostToDevice));
+    if (c.n_partials < (c.nel + 127) / 128) {
+      TRYC(dalloc(c, &c.partials, (size_t)((c.nel + 127) / 128)));
+      c.n_partials = (int)((c.nel + 127) / 128);
+    }
+    c.use_pe = true;
+  }
   if (c.shared_op) {
     c.sweep_rows = (int64_t)c.n_rows * c.nel;
   } else {
@@ -1324,12 +1336,9 @@ static ehdg_status batch_build_graph_branches(ehdg_batch b) {
 static ehdg_status batch_build_graph(ehdg_batch b) {
   const int n = (int)b->inst.size();
   b->looped.assign(n, 0);
-  int ft = 0, n_loop = 0;
+  int n_loop = 0;
   for (int i = 0; i < n && b->use_loop; ++i) {
-    const Ctx& c = b->inst[i]->c;
-    if (!batch_loop_ok(c)) continue;
-    if (ft == 0) ft = c.sweep_ft;
-    if (c.sweep_ft != ft) continue;      // one tile shape per loop
+    if (!batch_loop_ok(b->inst[i]->c)) continue;
     b->looped[i] = 1;
     ++n_loop;
   }

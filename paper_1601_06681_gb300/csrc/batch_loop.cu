@@ -16,12 +16,10 @@
 // instances' work items are skipped. No block waits for another.
 //
 // Every element's arithmetic is the single-problem path's: the FP64 sweep
-// runs the same tile body (fused_tile.cuh) over the same tile partition, each
-// work item playing one block of the instance's own sweep launch (the tiles
-// j, j + g, j + 2g, ... of that launch's grid g), so the residual partials and
-// their reduction order are the same; the correction sweep stages the same
-// rounded operands into the same tcgen05 MMA shapes. A batched instance's
-// iterates therefore equal a solo run's bit for bit.
+// runs the same one-thread-per-element tile body (pe_tile.cuh), whose
+// residual reduction is the same whatever the grid; the correction sweep
+// stages the same rounded operands into the same tcgen05 MMA shapes. A
+// batched instance's iterates therefore equal a solo run's bit for bit.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -29,7 +27,7 @@
 #include <vector>
 
 #include "ehdg_internal.h"
-#include "fused_tile.cuh"
+#include "pe_tile.cuh"
 #include "sweep_common.cuh"
 #include "umma.cuh"
 
@@ -43,10 +41,10 @@ constexpr uint32_t kBWaitLimit = 1u << 24; // mbarrier polls before giving up
 constexpr int kApplyChunk = 4096;          // trace entries per update work item
 
 struct BInst {
-  // FP64 sweep (the fused tile body of the instance's own launch)
+  // FP64 sweep (the per-element tile body of the single-problem sweep)
   int64_t nel, nface;
   int NQFS, Nqf, F, n_rows, n_up;
-  int vblocks;                  // grid of the instance's own sweep launch
+  int n_tiles_pe;               // 128-element tiles of the FP64 sweep
   const int* rows;
   const int32_t* elem_face;
   const double* face_jf;
@@ -185,62 +183,71 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-template <int NQ, int FT>
-__device__ __forceinline__ void batch_tiles(const BInst& I, int j, const double* Hsh, double* uh,
-                                            int* fid, const double* src, double* dst,
-                                            double& acc) {
-  const FusedTileView v = {I.nel, I.nface, I.NQFS, I.Nqf, I.F, I.n_rows, I.n_up, I.rows,
-                           I.elem_face, I.face_jf, I.fw, I.Gy, I.Y, I.R_out};
-  const int64_t ntiles = (I.nel + 31) / 32;
-  for (int64_t tile = j; tile < ntiles; tile += I.vblocks)
-    fused_tile_shared<NQ, FT>(v, Hsh, uh, fid, src, dst, tile, acc);
-}
-
-// One FP64 sweep of every unconverged instance; items[w] = (instance,
-// block j of its own launch).
-template <int FT>
-__global__ void __launch_bounds__(32 * FT) k_batch_sweep(const BInst* inst, const int4* counts,
+// One FP64 sweep of every instance that still iterates: items = (instance,
+// 128-element tile) from the lists; the instance's own single-problem tile
+// body, reduction and stopping test.
+__global__ void __launch_bounds__(kPeTile) k_batch_sweep(const BInst* inst, const int4* counts,
                                                           int* lists, int n_inst,
                                                           unsigned int* ticket,
                                                           cudaGraphConditionalHandle handle) {
   extern __shared__ double sm[];
-  const int tid = threadIdx.y * 32 + threadIdx.x;
+  const int tid = threadIdx.x;
   const ListView lv{n_inst};
   const int n_act = lists[0];
   const int* act = lv.act_sw(lists);
   const int* pre = lv.pre_sw(lists);
   const int n_items = n_act > 0 ? pre[n_act] : 0;
   int cur = -1;
-  double* Hsh = sm;
+  double* Hsh = sm;                                   // the instance's sweep rows [n_rows][NQ]
   for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
     // every listed instance iterates; its state cannot change before all its
     // work items are done
     const int k = owner_of(pre, n_act, w);
     const int idx = act[k];
-    const int2 item = make_int2(idx, w - pre[k]);
+    const int64_t tile = w - pre[k];
     const BInst& I = inst[idx];
     const int nq = I.NQFS;
-    double* uh = sm + nq * nq;
-    int* fid = reinterpret_cast<int*>(uh + nq * 32);
-    if (item.x != cur) {
-      for (int i = tid; i < nq * nq; i += 32 * FT) Hsh[i] = I.Hy[i];
-      cur = item.x;
+    if (idx != cur) {   // the previous item's threads are past its last barrier
+      for (int i = tid; i < I.n_rows * nq; i += kPeTile) {
+        const int j = i / nq, c = i - j * nq;
+        Hsh[i] = I.Hy[I.rows[j] * nq + c];
+      }
+      __syncthreads();
+      cur = idx;
     }
     const int kk = reinterpret_cast<volatile IterState*>(I.it)->k;
     const int64_t tlen = (int64_t)I.Nqf * I.nface;
+    PeView v = {};
+    v.nel = I.nel;
+    v.nface = I.nface;
+    v.n_rows = I.n_rows;
+    v.n_up = I.n_up;
+    v.rows = I.rows;
+    v.elem_face = I.elem_face;
+    v.face_jf = I.face_jf;
+    v.fw = I.fw;
+    v.Gy = I.Gy;
+    v.Y = I.Y;
+    v.R_out = I.R_out;
+    v.partials = I.partials;
+    v.it = I.it;
+    v.hist = I.hist;
+    v.max_iter = I.max_iter;
+    v.tol = I.tol;
+    v.res_scale = I.res_scale;
+    v.uhat = I.uhat;
     const double* src = I.uhat + (int64_t)(kk & 1) * tlen;
     double* dst = I.uhat + (int64_t)((kk + 1) & 1) * tlen;
-    double acc = 0.0;
+    const int64_t ntiles = I.n_tiles_pe;
+    bool last;
     switch (nq) {
-      case 8: batch_tiles<8, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
-      case 12: batch_tiles<12, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
-      case 16: batch_tiles<16, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
-      case 20: batch_tiles<20, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
-      case 24: batch_tiles<24, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
-      default: batch_tiles<28, FT>(I, item.y, Hsh, uh, fid, src, dst, acc); break;
+      case 8: last = pe_tile<8>(v, Hsh, src, dst, tile, ntiles, 0, handle); break;
+      case 12: last = pe_tile<12>(v, Hsh, src, dst, tile, ntiles, 0, handle); break;
+      case 16: last = pe_tile<16>(v, Hsh, src, dst, tile, ntiles, 0, handle); break;
+      case 20: last = pe_tile<20>(v, Hsh, src, dst, tile, ntiles, 0, handle); break;
+      case 24: last = pe_tile<24>(v, Hsh, src, dst, tile, ntiles, 0, handle); break;
+      default: last = pe_tile<28>(v, Hsh, src, dst, tile, ntiles, 0, handle); break;
     }
-    const bool last = finish_residual(acc, I.partials, item.y, I.vblocks, I.it, I.hist,
-                                      I.max_iter, I.tol, I.res_scale, 0, handle, I.vblocks);
     if (last && tid == 0 && !reinterpret_cast<volatile IterState*>(I.it)->cont)
       *I.t_conv = global_ns();
   }
@@ -528,9 +535,7 @@ bool batch_loop_ok(const Ctx& c) {
                      c.NQFS == 24 || c.NQFS == 28;
   const bool prec_ok = c.precision == EHDG_FP64 || c.precision == EHDG_MIXED_TF32 ||
                        c.precision == EHDG_MIXED_BF16;
-  return c.pde == EHDG_TRANSPORT && c.dim == 2 && c.shared_op && !c.variable_beta && !c.Hyt &&
-         !c.use_ozaki && !c.use_sf && c.n_tan == 0 && nq_ok && prec_ok &&
-         (!c.mixed || tc_supported(c));
+  return c.use_pe && !c.use_ozaki && nq_ok && prec_ok && (!c.mixed || tc_supported(c));
 }
 
 struct BatchLoop::Impl {
@@ -538,7 +543,7 @@ struct BatchLoop::Impl {
   int4* d_counts = nullptr;
   int* d_lists = nullptr;
   unsigned int* d_ticket = nullptr;
-  int n_inst = 0, n_sweep = 0, n_tc = 0, n_apply = 0, max_m = 0, ft = 4;
+  int n_inst = 0, n_sweep = 0, n_tc = 0, n_apply = 0, max_m = 0;
   int sweep_grid = 1, tc_grid = 1, apply_grid = 1, tc_ncols = 32, tc_smem_b = 0, tc_smem_a = 0;
   size_t sweep_smem = 0, tc_smem = 0;
 };
@@ -562,10 +567,9 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
   impl = new Impl();
   Impl& L = *impl;
   L.n_inst = (int)ctxs.size();
-  L.ft = ctxs.empty() ? 4 : ctxs[0]->sweep_ft;
   std::vector<BInst> h(L.n_inst);
   std::vector<int4> cnt(L.n_inst);
-  size_t smem = sizeof(int) * 5 * 256;               // the list builder's scan
+  size_t smem = sizeof(int) * 5 * kPeTile;          // the list builder's scan
   int max_kp_bytes = 0, max_np = 16;
   for (int i = 0; i < L.n_inst; ++i) {
     const Ctx& c = *ctxs[i];
@@ -578,7 +582,7 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     I.F = c.F;
     I.n_rows = c.n_rows;
     I.n_up = c.n_up;
-    I.vblocks = fused_sweep_grid(c);
+    I.n_tiles_pe = (int)((c.nel + kPeTile - 1) / kPeTile);
     I.rows = c.rows;
     I.elem_face = c.geo.elem_face;
     I.face_jf = c.geo.face_jf;
@@ -596,8 +600,8 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     I.max_iter = c.max_iter;
     I.t_conv = t_conv + slot[i];
     I.err = c.tc_err;
-    smem = std::max(smem, fused_sweep_smem(c));
-    L.n_sweep += I.vblocks;
+    smem = std::max(smem, sizeof(double) * (size_t)c.n_rows * c.NQFS);
+    L.n_sweep += I.n_tiles_pe;
     if (c.mixed) {
       I.tc = 1;
       I.bf16 = c.precision == EHDG_MIXED_BF16 ? 1 : 0;
@@ -619,7 +623,7 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
       L.n_tc += I.n_tiles128;
       L.n_apply += I.n_chunks;
     }
-    cnt[i] = make_int4(I.vblocks, I.tc, I.n_tiles128, I.n_chunks);
+    cnt[i] = make_int4(I.n_tiles_pe, I.tc, I.n_tiles128, I.n_chunks);
   }
   L.sweep_smem = smem;
   cudaError_t e;
@@ -647,11 +651,7 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     }
     return std::max(1, std::min(bpsm * device_sms(), items));
   };
-  switch (L.ft) {
-    case 2: L.sweep_grid = wave(k_batch_sweep<2>, 64, smem, L.n_sweep); break;
-    case 8: L.sweep_grid = wave(k_batch_sweep<8>, 256, smem, L.n_sweep); break;
-    default: L.sweep_grid = wave(k_batch_sweep<4>, 128, smem, L.n_sweep); break;
-  }
+  L.sweep_grid = wave(k_batch_sweep, kPeTile, smem, L.n_sweep);
   if (L.n_tc) {
     // B: the largest instance's padded rows x K; A: 128 x K
     L.tc_smem_b = (max_np * max_kp_bytes + 1023) / 1024 * 1024;
@@ -690,20 +690,8 @@ cudaError_t BatchLoop::launch_body(cudaStream_t s, cudaGraphConditionalHandle ha
     k_batch_apply<<<L.apply_grid, 256, 0, s>>>(L.d_inst, L.d_lists, L.n_inst);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  switch (L.ft) {
-    case 2:
-      k_batch_sweep<2><<<L.sweep_grid, dim3(32, 2), L.sweep_smem, s>>>(
-          L.d_inst, L.d_counts, L.d_lists, L.n_inst, L.d_ticket, handle);
-      break;
-    case 8:
-      k_batch_sweep<8><<<L.sweep_grid, dim3(32, 8), L.sweep_smem, s>>>(
-          L.d_inst, L.d_counts, L.d_lists, L.n_inst, L.d_ticket, handle);
-      break;
-    default:
-      k_batch_sweep<4><<<L.sweep_grid, dim3(32, 4), L.sweep_smem, s>>>(
-          L.d_inst, L.d_counts, L.d_lists, L.n_inst, L.d_ticket, handle);
-      break;
-  }
+  k_batch_sweep<<<L.sweep_grid, kPeTile, L.sweep_smem, s>>>(L.d_inst, L.d_counts, L.d_lists,
+                                                           L.n_inst, L.d_ticket, handle);
   return cudaGetLastError();
 }
 

@@ -296,7 +296,7 @@ extern "C" ehdg_status ehdg_autotune_sweep_tile(ehdg_ctx h, const int* cands, in
                                                 double* best_ms) {
   if (!h || !cands || n < 1) return io_fail(EHDG_ERR_INVALID, "bad argument");
   Ctx& c = h->c;
-  if (c.pde != EHDG_TRANSPORT || c.Hyt || c.use_ozaki)
+  if (c.pde != EHDG_TRANSPORT || c.Hyt || c.use_ozaki || c.use_pe)
     return io_fail(EHDG_ERR_INVALID,
                    "the context's FP64 sweep has no tile choice (it is not the fused transport "
                    "sweep)");

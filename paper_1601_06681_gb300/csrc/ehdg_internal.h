@@ -149,6 +149,8 @@ struct Ctx {
   // transport operator): the element's face traces go to its boundary nodes
   // by two 1D passes per face (Bs), then Dy = Ey A^{-1}[:, bnd] gives the
   // face-point rows and Ab = A^{-1}[:, bnd] the volume values
+  bool use_pe = false;           // 2D shared-operator FP64 sweep, one thread per element
+  double* pe_fw = nullptr;       // its face Gauss weights [Nqf]
   bool use_sf = false;
   int sf_NB = 0;                 // boundary nodes per element
   int* sf_bnd = nullptr;         // [NB] their node indices
@@ -227,6 +229,9 @@ bool sf_supported(const Ctx& c);
 ehdg_status sf_prepare(Ctx& c);                           // host tables, before assembly
 cudaError_t launch_sweep_sf(Ctx& c, int graph_mode, int* grid_out);
 cudaError_t launch_final_sf(Ctx& c);
+// one-thread-per-element 2D transport sweep (sweep_pe.cu)
+bool pe_supported(const Ctx& c);
+cudaError_t launch_sweep_pe(Ctx& c, int graph_mode, int* grid_out);
 // fused transport sweep (sweep_fused.cu)
 cudaError_t launch_sweep_fused(Ctx& c, int graph_mode);
 size_t fused_sweep_smem(const Ctx& c);   // dynamic shared memory of the fused sweep

@@ -361,6 +361,8 @@ cudaError_t launch_sweep_fused(Ctx& c, int graph_mode) {
     err = launch_sweep_tiled(c, graph_mode, &grid);
   } else if (c.use_sf) {
     err = launch_sweep_sf(c, graph_mode, &grid);
+  } else if (c.use_pe) {
+    err = launch_sweep_pe(c, graph_mode, &grid);
   } else switch (c.NQFS) {
     case 8: err = launch_fused_t<8>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;
     case 12: err = launch_fused_t<12>(p, smem, ntiles, c.sweep_ft, c.stream, &grid); break;

@@ -299,290 +299,6 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
                  "r"(p.ncols));
 }
 
-// ---------------------------------------------------------------------------
-// Pipelined form for a velocity with no zero component (every sweep row is a
-// point of an upwind face, one upwind face per axis, rows face by face in
-// point order): while the MMA and the epilogue of one tile run, the next
-// tile's correction values are already on their way into shared memory by
-// cp.async (4-byte copies, no registers held), so the gather latency hides
-// behind the current tile's work. Each thread stages, converts and feeds the
-// MMA with its own element's half of K only, so the staging needs no block
-// barrier. The epilogue's point offsets are compile-time (row j is point
-// j % NQF of upwind face j / NQF). Operands, MMA shapes and results are those
-// of k_sweep_tc.
-// ---------------------------------------------------------------------------
-struct Tc2Params {
-  TcParams p;
-  int upf[3];                   // local face of the upwind face of each axis
-};
-
-__device__ __forceinline__ void cp_async4(uint32_t saddr, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(src) : "memory");
-}
-
-// this thread's half of the gather of tile `tile` into the staging area
-// St [KP][128] (k-major, element fastest): one cp.async per face point
-template <int F_, int NQF, int BF16, int H>
-__device__ __forceinline__ void tc2_issue(const TcParams& p, float* St, int row, int64_t tile) {
-  constexpr int NQFS = F_ * NQF;
-  constexpr int KSTEP = BF16 ? 16 : 8;
-  constexpr int KP = (NQFS + KSTEP - 1) / KSTEP * KSTEP;
-  constexpr int KHALF = KP / 2;
-  constexpr int K0 = H * KHALF;
-  constexpr int F0 = K0 / NQF;
-  constexpr int NF = (K0 + KHALF - 1) / NQF - F0 + 1;
-  const int64_t e = tile * kTcM + row;
-  if (e >= p.nel) return;
-  const int64_t ne = p.nel, nface = p.nface;
-  int fr[NF];
-#pragma unroll
-  for (int m = 0; m < NF; ++m) fr[m] = (F0 + m < F_) ? p.elem_face[(F0 + m) * ne + e] : 0;
-  const uint32_t s0 = smem_u32(St) + (uint32_t)row * 4u;
-#pragma unroll
-  for (int kk = 0; kk < KHALF; ++kk) {
-    const int k = K0 + kk;
-    if (k < NQFS) {
-      const int f = k / NQF, g = k - (k / NQF) * NQF;
-      cp_async4(s0 + (uint32_t)k * (kTcM * 4u), p.in + (int64_t)g * nface + fr[f - F0]);
-    }
-  }
-}
-
-// convert this thread's staged half into the K-major A operand (zeros for a
-// missing element and for the K padding)
-template <int F_, int NQF, int BF16, int H>
-__device__ __forceinline__ void tc2_convert(const float* St, unsigned char* As, int row,
-                                            bool live) {
-  constexpr int NQFS = F_ * NQF;
-  constexpr int KSTEP = BF16 ? 16 : 8;
-  constexpr int KP = (NQFS + KSTEP - 1) / KSTEP * KSTEP;
-  constexpr int KHALF = KP / 2;
-  constexpr int K0 = H * KHALF;
-  constexpr int CH = BF16 ? 8 : 4;
-  constexpr uint32_t SBO = (uint32_t)KP * (BF16 ? 2 : 4) * 8u;
-  const uint32_t rowoff = (uint32_t)(row >> 3) * SBO + (uint32_t)(row & 7) * 16u;
-#pragma unroll
-  for (int c = 0; c < KHALF / CH; ++c) {
-    float v[CH];
-#pragma unroll
-    for (int q = 0; q < CH; ++q) {
-      const int k = K0 + c * CH + q;
-      v[q] = (live && k < NQFS) ? St[k * kTcM + row] : 0.f;
-    }
-    store_chunk(As + rowoff + (uint32_t)((K0 + c * CH) / CH) * 128u, v, CH, BF16);
-  }
-}
-
-// epilogue of this thread's half of the N = rows columns: owner writes
-// out = R + acc at the upwind faces' points (face ids in upid)
-template <int F_, int NQF, int H>
-__device__ __forceinline__ void tc2_epilogue(const TcParams& p, uint32_t tbase, int warp,
-                                             const int* upid, int64_t e) {
-  constexpr int NR = (F_ / 2) * NQF;
-  constexpr int NP = (NR + 15) / 16 * 16;
-  constexpr int NH = NP / 2;
-  constexpr int C0 = H * NH;
-  const int64_t nface = p.nface;
-  const bool live = e < p.nel;
-#pragma unroll
-  for (int c0 = C0; c0 < C0 + NH; c0 += 8) {
-    uint32_t v[8];
-    tmem_ld8(tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0, v);
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-    if (live) {
-      float rv[8];
-      int64_t pt[8];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int j = c0 + q;
-        if (j < NR) {
-          pt[q] = (int64_t)(j % NQF) * nface + upid[j / NQF - C0 / NQF];
-          rv[q] = p.R[pt[q]];
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int j = c0 + q;
-        if (j < NR) p.out[pt[q]] = rv[q] + __uint_as_float(v[q]);
-      }
-    }
-  }
-}
-
-template <int F_, int NQF, int BF16>
-__global__ void __launch_bounds__(kTcThreads) k_sweep_tc2(const __grid_constant__ Tc2Params q) {
-  constexpr int NQFS = F_ * NQF;
-  constexpr int KSTEP = BF16 ? 16 : 8;
-  constexpr int KP = (NQFS + KSTEP - 1) / KSTEP * KSTEP;
-  constexpr int ESZ = BF16 ? 2 : 4;
-  constexpr uint32_t KBYTES = (uint32_t)KP * ESZ;
-  constexpr uint32_t SBO = KBYTES * 8u;
-  constexpr int NR = (F_ / 2) * NQF;
-  constexpr int NP = (NR + 15) / 16 * 16;
-  constexpr int NH = NP / 2;
-  // upwind faces a half's columns touch (epilogue face ids)
-  constexpr int U0 = 0, U1 = NH / NQF;                 // first upwind face of each half
-  constexpr int NU = (NH + NQF - 1) / NQF + 1;         // faces a half touches, at most
-  const TcParams& p = q.p;
-  extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int row = tid & (kTcM - 1), half = tid >> 7;
-  unsigned char* Bs = sm;                               // NP x KP
-  unsigned char* As = sm + (size_t)NP * KBYTES;         // 128 x KP
-  float* St = reinterpret_cast<float*>(As + (size_t)kTcM * KBYTES);   // [KP][128]
-
-  // B = sweep rows of the shared operator, zero-padded
-  for (int i = tid; i < NP * KP; i += kTcThreads) {
-    const int n = i / KP, k = i - n * KP;
-    float v = 0.f;
-    if (n < p.n_rows && k < NQFS) v = p.Hy32[p.rows[n] * NQFS + k];
-    store_elem(Bs, n, k, ESZ, SBO, v, BF16);
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(&tmem_base)),
-                 "r"(p.ncols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tbase = tmem_base;
-
-  const int64_t ne = p.nel;
-  const int64_t ntiles = (ne + kTcM - 1) / kTcM;
-  const int ubase = half ? U1 : U0;
-  // prologue: the first tile's gather
-  int64_t tile = blockIdx.x;
-  if (tile < ntiles) {
-    if (half == 0) tc2_issue<F_, NQF, BF16, 0>(p, St, row, tile);
-    else tc2_issue<F_, NQF, BF16, 1>(p, St, row, tile);
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  uint32_t phase = 0;
-  bool failed = false;
-  for (; tile < ntiles && !failed; tile += gridDim.x) {
-    const int64_t e = tile * kTcM + row;
-    const bool live = e < ne;
-    // this tile's upwind face ids (epilogue)
-    int upid[NU];
-#pragma unroll
-    for (int u = 0; u < NU; ++u) {
-      const int uf = ubase + u;
-      upid[u] = (live && uf < F_ / 2) ? p.elem_face[q.upf[uf] * ne + e] : 0;
-    }
-    // own staged half -> A
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (half == 0) tc2_convert<F_, NQF, BF16, 0>(St, As, row, live);
-    else tc2_convert<F_, NQF, BF16, 1>(St, As, row, live);
-    asm volatile("fence.proxy.async.shared::cta;");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
-      const uint32_t idesc = p.idesc;
-#pragma unroll
-      for (int s = 0; s < (int)(KBYTES / 32u); ++s) {
-        const uint64_t ad = umma_desc(a0 + 256u * s, 128u, SBO);
-        const uint64_t bd = umma_desc(b0 + 256u * s, 128u, SBO);
-        const uint32_t acc = s > 0 ? 1u : 0u;
-        if (BF16) {
-          asm volatile(
-              "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tbase),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-        } else {
-          asm volatile(
-              "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}\n" ::"r"(tbase),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
-        }
-      }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&mbar)));
-    }
-    // the next tile's gather into the staging area (this thread's part of it
-    // was converted above) while the MMA runs
-    const int64_t next = tile + gridDim.x;
-    if (next < ntiles) {
-      if (half == 0) tc2_issue<F_, NQF, BF16, 0>(p, St, row, next);
-      else tc2_issue<F_, NQF, BF16, 1>(p, St, row, next);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-    uint32_t ok = 1;
-    if (tid == 0) ok = mbar_wait_bounded(&mbar, phase, kWaitLimit) ? 1u : 0u;
-    if (__syncthreads_or(ok ? 0 : 1)) {
-      if (tid == 0) atomicExch(p.err, 1);
-      failed = true;
-    }
-    phase ^= 1u;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!failed) {
-      if (half == 0) tc2_epilogue<F_, NQF, 0>(p, tbase, warp, upid, e);
-      else tc2_epilogue<F_, NQF, 1>(p, tbase, warp, upid, e);
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-  }
-  asm volatile("cp.async.wait_group 0;" ::: "memory");
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
-                 "r"(p.ncols));
-}
-
-using Tc2Kernel = void (*)(const Tc2Params);
-template <int F_, int NQF>
-Tc2Kernel tc2_pick(int bf16) {
-  return bf16 ? k_sweep_tc2<F_, NQF, 1> : k_sweep_tc2<F_, NQF, 0>;
-}
-Tc2Kernel tc2_kernel(int F, int Nqf, int bf16) {
-  if (F == 4) {
-    switch (Nqf) {
-      case 2: return tc2_pick<4, 2>(bf16);
-      case 3: return tc2_pick<4, 3>(bf16);
-      case 4: return tc2_pick<4, 4>(bf16);
-      case 5: return tc2_pick<4, 5>(bf16);
-      case 6: return tc2_pick<4, 6>(bf16);
-      case 7: return tc2_pick<4, 7>(bf16);
-      default: break;
-    }
-  } else if (F == 6) {
-    switch (Nqf) {
-      case 4: return tc2_pick<6, 4>(bf16);
-      case 9: return tc2_pick<6, 9>(bf16);
-      case 16: return tc2_pick<6, 16>(bf16);
-      default: break;
-    }
-  }
-  return nullptr;
-}
-
-// The pipelined form applies when the rows are every point of one upwind
-// face per axis, face by face in point order (no tangential points); upf
-// receives those faces.
-bool tc2_rows(const Ctx& c, int* upf) {
-  const int dim = c.F / 2;
-  if (c.pde != EHDG_TRANSPORT || c.n_tan != 0 || c.n_rows != c.n_up ||
-      c.n_up != dim * c.Nqf || (int)c.rows_host.size() != c.n_rows)
-    return false;
-  for (int a = 0; a < dim; ++a) {
-    const int f = c.rows_host[a * c.Nqf] / c.Nqf;
-    if ((f >> 1) != a) return false;
-    upf[a] = f;
-    for (int g = 0; g < c.Nqf; ++g)
-      if (c.rows_host[a * c.Nqf + g] != f * c.Nqf + g) return false;
-  }
-  for (int a = dim; a < 3; ++a) upf[a] = 0;
-  return true;
-}
-
 // The kernel of a face shape: quadrilaterals with 2..7 points per edge and
 // hexahedra with 2x2, 3x3 or 4x4 points per face have a compile-time form.
 using TcKernel = void (*)(const TcParams);
@@ -650,27 +366,6 @@ cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
   const int esize = p.bf16 ? 2 : 4;
   const size_t smem = (size_t)(p.Np + kTcM) * p.Kp * esize +
                       sizeof(int) * ((size_t)c.F * kTcM + 2 * (size_t)p.Np) + 1024;
-  Tc2Params q2;
-  Tc2Kernel kern2 = tc2_rows(c, q2.upf) ? tc2_kernel(c.F, c.Nqf, p.bf16) : nullptr;
-  if (kern2) {
-    // the pipelined form: B, A and the FP32 staging of A
-    q2.p = p;
-    const size_t smem2 = (size_t)(p.Np + kTcM) * p.Kp * esize + (size_t)p.Kp * kTcM * 4 + 1024;
-    cudaError_t err =
-        cudaFuncSetAttribute(kern2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-    if (err != cudaSuccess) return err;
-    err = cudaFuncSetAttribute(kern2, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (err != cudaSuccess) return err;
-    int bpsm = (int)((227 * 1024) / (smem2 + 1024));
-    if (bpsm > 512 / ncols) bpsm = 512 / ncols;
-    if (bpsm > 8) bpsm = 8;
-    if (bpsm < 1) bpsm = 1;
-    const int64_t ntiles = (c.nel + kTcM - 1) / kTcM;
-    int64_t grid = (int64_t)bpsm * device_sms();
-    if (grid > ntiles) grid = ntiles;
-    kern2<<<(int)grid, kTcThreads, smem2, c.stream>>>(q2);
-    return cudaGetLastError();
-  }
   void (*kern)(const TcParams) = tc_kernel(c.F, c.Nqf, p.bf16);
   cudaError_t err =
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

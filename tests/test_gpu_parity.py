@@ -603,9 +603,10 @@ def test_fp64_path_autotuner_keeps_state_and_results(ehdg, name):
         assert ei.value.status == 1
 
 
-# the tile-shape autotuner of the fused FP64 sweep: FT row groups per 32-element
-# tile change which thread runs which row, not the rows' arithmetic
-@pytest.mark.parametrize("name", ["2d_be_const", "3d_be_variable_p2", "2d_be_zero_component"])
+# the tile-shape autotuner of the fused and the sum-factorised FP64 sweeps: FT
+# row groups per 32-element tile change which thread runs which row, not the
+# rows' arithmetic
+@pytest.mark.parametrize("name", ["3d_be_const", "3d_be_variable_p2", "2d_be_zero_component"])
 def test_sweep_tile_choice_keeps_iterates_bitwise(ehdg, name):
     mesh, p, kw, prob, u0, g = make_case(name)
     states = []
@@ -635,8 +636,9 @@ def test_sweep_tile_choice_keeps_iterates_bitwise(ehdg, name):
 
 
 def test_sweep_tile_autotuner_rejects_other_sweeps(ehdg):
-    # shallow water; the tiled per-element sweeps of quadrilaterals and of 2x2-point hexahedra
-    for name in ("sw_be", "2d_cn_variable", "3d_be_variable"):
+    # shallow water; the tiled per-element sweeps of quadrilaterals and of 2x2-point
+    # hexahedra; the one-thread-per-element sweep of quadrilaterals with a shared operator
+    for name in ("sw_be", "2d_cn_variable", "3d_be_variable", "2d_be_const"):
         mesh, p, kw, prob, u0, g = make_case(name)
         with make_solver(ehdg, mesh, p, kw, prob) as s:
             with pytest.raises(ehdg.EhdgError) as ei:
