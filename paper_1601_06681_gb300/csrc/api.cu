@@ -34,7 +34,6 @@ struct ehdg_batch_s {
   bool tuning = false;                  // an autotuner is running candidate steps
   ehdg::BatchLoop loop;
   std::vector<char> looped;             // instance i iterates in the batched loop
-  std::vector<cudaStream_t> lbranch;    // branches of the looped instances' step kernels
   unsigned long long* t_conv = nullptr; // convergence time of each instance in a step
 };
 
@@ -354,35 +353,6 @@ ehdg_status capture_step(Ctx& c, cudaStream_t s, cudaStream_t body_stream, bool 
   if (e2 != cudaSuccess) return cuda_fail(e2, "capture loop body");
   if (e3 != cudaSuccess) return cuda_fail(e3, "end body capture");
   return capture_step_end(c);
-}
-
-// The once-per-step kernels of an instance whose iterations run in a batch's
-// loop, appended on stream s: reset, step right-hand side, initial trace, and
-// for mixed precision the first FP64 sweep (the first residual R).
-ehdg_status capture_step_pre(Ctx& c, cudaStream_t s) {
-  cudaStream_t user = c.stream;
-  struct Restore {
-    Ctx& c;
-    cudaStream_t s;
-    ~Restore() { c.stream = s; }
-  } restore{c, user};
-  c.stream = s;
-  cudaError_t err = cudaSuccess;
-  if ((err = launch_reset_iter(c)) != cudaSuccess) return cuda_fail(err, "capture reset");
-  if ((err = launch_step(c)) != cudaSuccess) return cuda_fail(err, "capture step");
-  if ((err = launch_face(c, kFaceInitial)) != cudaSuccess) return cuda_fail(err, "capture face");
-  if (c.mixed && (err = launch_sweep_fused(c, 0)) != cudaSuccess)
-    return cuda_fail(err, "capture first FP64 sweep");
-  return EHDG_OK;
-}
-
-// The end-of-step kernels of a looped instance on stream s.
-ehdg_status capture_step_post(Ctx& c, cudaStream_t s) {
-  cudaStream_t user = c.stream;
-  c.stream = s;
-  const ehdg_status st = capture_step_end(c);
-  c.stream = user;
-  return st;
 }
 
 void abort_capture(cudaStream_t s) {
@@ -1327,23 +1297,25 @@ static ehdg_status batch_build_graph_branches(ehdg_batch b) {
   return EHDG_OK;
 }
 
-// One graph with the batched loop: the looped instances' once-per-step
-// kernels on k branches, joined; one WHILE node whose body is the batched
-// loop (corrections, update, FP64 sweep over every unconverged instance);
-// their end-of-step kernels on k branches again. Instances the loop does not
-// support run their whole steps (each with its own loop) on other branches,
-// concurrently with all of it.
+// One graph with the batched loop. The looped instances' step is a handful
+// of launches for all of them together: reset, right-hand side, initial
+// trace, work lists and the first FP64 sweep; one WHILE node whose body is
+// the batched loop (corrections, update, FP64 sweep over every instance that
+// still iterates); reconstruction, trace hand-over and step record. Instances
+// the loop does not take run their whole steps (each with its own loop) on
+// the graph's branches, concurrently with all of it.
 static ehdg_status batch_build_graph(ehdg_batch b) {
   const int n = (int)b->inst.size();
   b->looped.assign(n, 0);
   int n_loop = 0;
   for (int i = 0; i < n && b->use_loop; ++i) {
-    if (!batch_loop_ok(b->inst[i]->c)) continue;
+    const Ctx& c = b->inst[i]->c;
+    if (!batch_loop_ok(c) || c.have_force) continue;
     b->looped[i] = 1;
     ++n_loop;
   }
-  if (n_loop == 0 || n_loop > 8192) {   // the loop's list builder keeps a flag per instance
-    b->loop.release();                   // in shared memory
+  if (n_loop == 0 || n_loop > 8192) {   // the loop's list builder scans the instances in
+    b->loop.release();                   // one block
     return batch_build_graph_branches(b);
   }
   batch_destroy_graph(b);
@@ -1357,12 +1329,7 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
       ctxs.push_back(&b->inst[i]->c);
       slots.push_back(i);
     }
-  CK(b->loop.build(ctxs, b->t_conv, slots));
-  while ((int)b->lbranch.size() < k) {
-    cudaStream_t st = nullptr;
-    CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    b->lbranch.push_back(st);
-  }
+  CK(b->loop.build(ctxs, b->t_start, b->t_acc, b->t_conv, slots));
   std::vector<cudaEvent_t> evs;
   auto event = [&](cudaEvent_t* e) {
     const cudaError_t r = cudaEventCreateWithFlags(e, cudaEventDisableTiming);
@@ -1372,8 +1339,8 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
   auto cleanup_events = [&]() {
     for (auto e : evs) cudaEventDestroy(e);
   };
-  cudaEvent_t fork = nullptr, fork2 = nullptr;
-  if (event(&fork) != cudaSuccess || event(&fork2) != cudaSuccess) {
+  cudaEvent_t fork = nullptr;
+  if (event(&fork) != cudaSuccess) {
     cleanup_events();
     return cuda_fail(cudaGetLastError(), "batch events");
   }
@@ -1382,7 +1349,7 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
     cleanup_events();
     return cuda_fail(e, "batch capture");
   }
-  std::vector<cudaStream_t> forked;       // streams to join back before the end
+  std::vector<cudaStream_t> forked;       // branches to join back before the end
   ehdg_status st = EHDG_OK;
   auto join_all = [&]() {
     for (cudaStream_t x : forked) {
@@ -1394,7 +1361,7 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
     forked.clear();
   };
   e = cudaEventRecord(fork, b->cap);
-  // instances outside the loop: their whole steps
+  // instances outside the loop: their whole steps on the branches
   for (int j = 0; j < k && e == cudaSuccess && st == EHDG_OK; ++j) {
     bool any = false;
     for (int i : lists[j]) any = any || !b->looped[i];
@@ -1410,30 +1377,7 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
       if ((e = launch_stamp(s, b->t_start, b->t_acc, i, 1)) != cudaSuccess) break;
     }
   }
-  // looped instances: step kernels before the loop, joined
-  std::vector<cudaStream_t> pre;
-  for (int j = 0; j < k && e == cudaSuccess && st == EHDG_OK; ++j) {
-    bool any = false;
-    for (int i : lists[j]) any = any || b->looped[i];
-    if (!any) continue;
-    cudaStream_t s = b->lbranch[j];
-    if ((e = cudaStreamWaitEvent(s, fork, 0)) != cudaSuccess) break;
-    pre.push_back(s);
-    forked.push_back(s);
-    for (int i : lists[j]) {
-      if (!b->looped[i]) continue;
-      if ((e = launch_stamp(s, b->t_start, b->t_acc, i, 0)) != cudaSuccess) break;
-      if ((st = capture_step_pre(b->inst[i]->c, s)) != EHDG_OK) break;
-    }
-  }
-  for (cudaStream_t s : pre) {
-    cudaEvent_t j = nullptr;
-    if (e != cudaSuccess || (e = (cudaError_t)event(&j)) != cudaSuccess) break;
-    if ((e = cudaEventRecord(j, s)) != cudaSuccess) break;
-    e = cudaStreamWaitEvent(b->cap, j, 0);
-  }
-  // the batched loop (its first iteration's work lists, then the loop)
-  if (e == cudaSuccess && st == EHDG_OK) e = b->loop.launch_lists(b->cap);
+  // the looped instances: before the loop, the loop, after it
   if (e == cudaSuccess && st == EHDG_OK) {
     cudaStreamCaptureStatus cst;
     cudaGraph_t g = nullptr;
@@ -1442,6 +1386,7 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
     size_t ndeps = 0;
     e = cudaStreamGetCaptureInfo(b->cap, &cst, nullptr, &g, nullptr, nullptr, nullptr);
     if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&handle, g, 1, cudaGraphCondAssignDefault);
+    if (e == cudaSuccess) e = b->loop.launch_pre(b->cap, handle);
     if (e == cudaSuccess)
       e = cudaStreamGetCaptureInfo(b->cap, &cst, nullptr, &g, &deps, nullptr, &ndeps);
     cudaGraphNodeParams cp = {};
@@ -1466,21 +1411,7 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
         e = e2 != cudaSuccess ? e2 : e3;
       }
     }
-  }
-  // looped instances: end-of-step kernels
-  if (e == cudaSuccess && st == EHDG_OK) e = cudaEventRecord(fork2, b->cap);
-  for (int j = 0; j < k && e == cudaSuccess && st == EHDG_OK; ++j) {
-    bool any = false;
-    for (int i : lists[j]) any = any || b->looped[i];
-    if (!any) continue;
-    cudaStream_t s = b->lbranch[j];
-    if ((e = cudaStreamWaitEvent(s, fork2, 0)) != cudaSuccess) break;
-    forked.push_back(s);
-    for (int i : lists[j]) {
-      if (!b->looped[i]) continue;
-      if ((st = capture_step_post(b->inst[i]->c, s)) != EHDG_OK) break;
-      if ((e = launch_stamp_conv(s, b->t_start, b->t_acc, b->t_conv, i)) != cudaSuccess) break;
-    }
+    if (e == cudaSuccess) e = b->loop.launch_post(b->cap);
   }
   if (e != cudaSuccess || st != EHDG_OK) {
     const std::string msg = e != cudaSuccess ? std::string("batch capture: ") + cudaGetErrorString(e)
@@ -1814,8 +1745,6 @@ void ehdg_batch_destroy(ehdg_batch b) {
   if (b->t_start) cudaFree(b->t_start);
   if (b->t_acc) cudaFree(b->t_acc);
   if (b->t_conv) cudaFree(b->t_conv);
-  for (auto s : b->lbranch)
-    if (s) cudaStreamDestroy(s);
   b->loop.release();
   for (auto h : b->inst) ehdg_destroy(h);
   delete b;

@@ -28,6 +28,7 @@
 
 #include "ehdg_internal.h"
 #include "pe_tile.cuh"
+#include "step_tiles.cuh"
 #include "sweep_common.cuh"
 #include "umma.cuh"
 
@@ -68,9 +69,30 @@ struct BInst {
   float* d32;
   float* Y32;
   int* err;
-  // convergence time of the instance in the current step (%globaltimer)
+  // convergence time of the instance in the current step (%globaltimer), and
+  // the step's start and the accumulated step times
   unsigned long long* t_conv;
+  unsigned long long* t_start;
+  unsigned long long* t_acc;
   int n_tiles128, n_chunks;     // work items of its correction sweeps and of its update
+  // once-per-step kernels: right-hand side, initial trace, reconstruction
+  int n, KE, cn;
+  double ucoef;
+  const double* P;
+  double* u;
+  const int* ey_idx;
+  const double* ey_val;
+  double* G;
+  const double* H;
+  double* uhat_n;
+  const double* gb;
+  double* gb_old;
+  const int8_t* sgn;
+  const int32_t* face_elem;
+  const int8_t* face_local;
+  int* step_iters;
+  int* step_status;
+  int step_cap;
 };
 
 // Work of the next loop iteration, rebuilt on the device after every FP64
@@ -515,13 +537,177 @@ __global__ void __launch_bounds__(256) k_batch_apply(const BInst* inst, const in
   }
 }
 
-// per-instance step time of a looped instance: from its step's start stamp to
-// its convergence inside the loop (or to now, if it converged before it)
-__global__ void k_stamp_conv(unsigned long long* t_start, unsigned long long* t_acc,
-                             unsigned long long* t_conv, int i) {
-  const unsigned long long t = t_conv[i] ? t_conv[i] : global_ns();
-  t_acc[i] += t - t_start[i];
-  t_conv[i] = 0ull;
+// ---------------------------------------------------------------------------
+// Once-per-step kernels of the looped instances, each one launch for all of
+// them; static work lists: pre[i] .. pre[i+1]-1 are instance i's items.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int static_owner(const int* pre, int n, int w) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= w) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// iteration state reset (the single-problem reset) and the step's start time
+__global__ void k_batch_begin(const BInst* inst, int n_inst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_inst) return;
+  const BInst& I = inst[i];
+  IterState* it = I.it;
+  it->k = 0;
+  it->cont = 1;
+  it->status = EHDG_OK;
+  it->counter = 0u;
+  it->bar = 0u;
+  it->abort = 0;
+  it->r_last = 0.0;
+  *I.t_start = global_ns();
+  *I.t_conv = 0ull;
+}
+
+__device__ StepParams step_params(const BInst& I) {
+  StepParams p = {};
+  p.nel = I.nel;
+  p.n = I.n;
+  p.NQFS = I.NQFS;
+  p.KE = I.KE;
+  p.shared = 1;
+  p.ucoef = I.ucoef;
+  p.P = I.P;
+  p.u = I.u;
+  p.ey_idx = I.ey_idx;
+  p.ey_val = I.ey_val;
+  p.rows = I.rows;
+  p.n_rows = I.n_rows;
+  p.G = I.G;
+  p.Gy = const_cast<double*>(I.Gy);
+  p.Y = I.Y;
+  return p;
+}
+
+// the step's right-hand side G = P w, Gy and Y0 (items: 32-element tiles)
+__global__ void __launch_bounds__(32 * kStepT) k_batch_step(const BInst* inst, const int* pre,
+                                                            int n_inst, int nmax) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  double* Psh = sm;                                   // [n][n]
+  double* w = Psh + nmax * nmax;                      // [n][32]
+  double* g = w + nmax * 32;                          // [n][32]
+  const int n_items = pre[n_inst];
+  int cur = -1;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int i = static_owner(pre, n_inst, it);
+    const BInst& I = inst[i];
+    if (i != cur) {   // step_tile starts and ends with barriers around its use of Psh
+      __syncthreads();
+      for (int k = tid; k < I.n * I.n; k += 32 * kStepT) Psh[k] = I.P[k];
+      cur = i;
+    }
+    step_tile(step_params(I), Psh, w, g, it - pre[i]);
+  }
+}
+
+// the initial trace (the trace formula of u^n with the new boundary data),
+// written to both trace slots (items: chunks of kApplyChunk face points)
+__global__ void __launch_bounds__(256) k_batch_trace0(const BInst* inst, const int* pre,
+                                                      int n_inst) {
+  const int n_items = pre[n_inst];
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int i = static_owner(pre, n_inst, it);
+    const BInst& I = inst[i];
+    const int64_t total = (int64_t)I.Nqf * I.nface;
+    const int64_t t0 = (int64_t)(it - pre[i]) * kApplyChunk;
+    const int64_t t1 = std::min<int64_t>(t0 + kApplyChunk, total);
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+      const int gf = (int)(t / I.nface);
+      const int64_t face = t - (int64_t)gf * I.nface;
+      const double uh = transport_trace_point(I.nel, I.nface, I.Nqf, I.cn, I.face_elem,
+                                              I.face_local, I.sgn, I.Y, I.gb, I.gb_old, gf,
+                                              face);
+      I.uhat[total + t] = uh;
+      I.uhat[t] = uh;
+    }
+  }
+}
+
+// the reconstruction u^{k+1} = G + H uhat^k (items: 32-element tiles)
+__global__ void __launch_bounds__(32 * kStepT) k_batch_final(const BInst* inst, const int* pre,
+                                                             int n_inst, int nmax, int nqmax) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.y * 32 + threadIdx.x;
+  double* Hsh = sm;                                   // [n][NQFS]
+  double* uh = Hsh + nmax * nqmax;                    // [NQFS][32]
+  const int n_items = pre[n_inst];
+  int cur = -1;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int i = static_owner(pre, n_inst, it);
+    const BInst& I = inst[i];
+    if (i != cur) {
+      __syncthreads();
+      for (int k = tid; k < I.n * I.NQFS; k += 32 * kStepT) Hsh[k] = I.H[k];
+      cur = i;
+    }
+    FinalParams p = {};
+    p.nel = I.nel;
+    p.nface = I.nface;
+    p.n = I.n;
+    p.NQFS = I.NQFS;
+    p.Nqf = I.Nqf;
+    p.F = I.F;
+    p.shared = 1;
+    p.cn = I.cn;
+    p.elem_face = I.elem_face;
+    p.uhat = I.uhat;
+    p.it = I.it;
+    p.G = I.G;
+    p.H = I.H;
+    p.u = I.u;
+    const double* src = I.uhat + (int64_t)((I.it->k + 1) & 1) * I.Nqf * I.nface;
+    final_tile(p, Hsh, uh, src, it - pre[i]);
+  }
+}
+
+// the final trace becomes the state's trace in slot 0 (Crank-Nicolson:
+// 2 vhat - uhat^n) and the previous-level copies are updated (items: chunks)
+__global__ void __launch_bounds__(256) k_batch_trace_end(const BInst* inst, const int* pre,
+                                                         int n_inst) {
+  const int n_items = pre[n_inst];
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int i = static_owner(pre, n_inst, it);
+    const BInst& I = inst[i];
+    const int64_t total = (int64_t)I.Nqf * I.nface;
+    const double* fin = I.uhat + (int64_t)(I.it->k & 1) * total;
+    const int64_t t0 = (int64_t)(it - pre[i]) * kApplyChunk;
+    const int64_t t1 = std::min<int64_t>(t0 + kApplyChunk, total);
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+      double v = fin[t];
+      if (I.cn) v = 2.0 * v - I.uhat_n[t];
+      I.uhat[t] = v;
+      I.uhat_n[t] = v;
+      I.gb_old[t] = I.gb[t];
+    }
+  }
+}
+
+// the step's record (iterations, status) and the instance's time: from the
+// step's start to its convergence
+__global__ void k_batch_end(const BInst* inst, int n_inst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_inst) return;
+  const BInst& I = inst[i];
+  IterState* it = I.it;
+  const int s = it->step;
+  if (s >= 0 && s < I.step_cap) {
+    I.step_iters[s] = it->k;
+    I.step_status[s] = it->status;
+  }
+  it->step = s + 1;
+  const unsigned long long t = *I.t_conv ? *I.t_conv : global_ns();
+  *I.t_acc += t - *I.t_start;
+  *I.t_conv = 0ull;
 }
 
 }  // namespace
@@ -542,6 +728,11 @@ struct BatchLoop::Impl {
   BInst* d_inst = nullptr;
   int4* d_counts = nullptr;
   int* d_lists = nullptr;
+  int* d_pre32 = nullptr;       // static lists: 32-element tiles, trace chunks
+  int* d_prech = nullptr;
+  int n32 = 0, nch = 0, nmax = 1, nqmax = 1;
+  int step_grid = 1, final_grid = 1, chunk_grid = 1;
+  size_t step_smem = 0, final_smem = 0;
   unsigned int* d_ticket = nullptr;
   int n_inst = 0, n_sweep = 0, n_tc = 0, n_apply = 0, max_m = 0;
   int sweep_grid = 1, tc_grid = 1, apply_grid = 1, tc_ncols = 32, tc_smem_b = 0, tc_smem_a = 0;
@@ -555,13 +746,16 @@ void BatchLoop::release() {
   cudaFree(impl->d_inst);
   cudaFree(impl->d_counts);
   cudaFree(impl->d_lists);
+  cudaFree(impl->d_pre32);
+  cudaFree(impl->d_prech);
   cudaFree(impl->d_ticket);
   delete impl;
   impl = nullptr;
 }
 
 // Device tables of the looped instances (their contexts must stay alive).
-cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* t_conv,
+cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* t_start,
+                             unsigned long long* t_acc, unsigned long long* t_conv,
                              const std::vector<int>& slot) {
   release();
   impl = new Impl();
@@ -569,6 +763,7 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
   L.n_inst = (int)ctxs.size();
   std::vector<BInst> h(L.n_inst);
   std::vector<int4> cnt(L.n_inst);
+  std::vector<int> pre32, prech;
   size_t smem = sizeof(int) * 5 * kPeTile;          // the list builder's scan
   int max_kp_bytes = 0, max_np = 16;
   for (int i = 0; i < L.n_inst; ++i) {
@@ -599,7 +794,34 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     I.res_scale = c.res_scale;
     I.max_iter = c.max_iter;
     I.t_conv = t_conv + slot[i];
+    I.t_start = t_start + slot[i];
+    I.t_acc = t_acc + slot[i];
     I.err = c.tc_err;
+    I.n = c.n;
+    I.KE = c.KE;
+    I.cn = (c.scheme == EHDG_CN) ? 1 : 0;
+    I.ucoef = (c.scheme == EHDG_STEADY) ? 0.0 : 1.0 / c.dt_eff;
+    I.P = c.P;
+    I.u = c.u;
+    I.ey_idx = c.ey_idx;
+    I.ey_val = c.ey_val;
+    I.G = c.G;
+    I.H = c.H;
+    I.uhat_n = c.uhat_n;
+    I.gb = c.gb;
+    I.gb_old = c.gb_old;
+    I.sgn = c.sgn;
+    I.face_elem = c.geo.face_elem;
+    I.face_local = c.geo.face_local;
+    I.step_iters = c.step_iters;
+    I.step_status = c.step_status;
+    I.step_cap = c.step_cap;
+    pre32.push_back(L.n32);
+    prech.push_back(L.nch);
+    L.n32 += (int)((c.nel + 31) / 32);
+    L.nch += (int)(((int64_t)c.Nqf * c.nface + kApplyChunk - 1) / kApplyChunk);
+    L.nmax = std::max(L.nmax, c.n);
+    L.nqmax = std::max(L.nqmax, c.NQFS);
     smem = std::max(smem, sizeof(double) * (size_t)c.n_rows * c.NQFS);
     L.n_sweep += I.n_tiles_pe;
     if (c.mixed) {
@@ -626,7 +848,17 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     cnt[i] = make_int4(I.n_tiles_pe, I.tc, I.n_tiles128, I.n_chunks);
   }
   L.sweep_smem = smem;
+  pre32.push_back(L.n32);
+  prech.push_back(L.nch);
   cudaError_t e;
+  if ((e = cudaMalloc(&L.d_pre32, sizeof(int) * pre32.size())) != cudaSuccess) return e;
+  if ((e = cudaMalloc(&L.d_prech, sizeof(int) * prech.size())) != cudaSuccess) return e;
+  if ((e = cudaMemcpy(L.d_pre32, pre32.data(), sizeof(int) * pre32.size(),
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemcpy(L.d_prech, prech.data(), sizeof(int) * prech.size(),
+                      cudaMemcpyHostToDevice)) != cudaSuccess)
+    return e;
   const size_t list_ints = kListHeader + 5 * (size_t)L.n_inst + 3;
   if ((e = cudaMalloc(&L.d_inst, sizeof(BInst) * std::max(1, L.n_inst))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&L.d_counts, sizeof(int4) * std::max(1, L.n_inst))) != cudaSuccess) return e;
@@ -652,6 +884,17 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     return std::max(1, std::min(bpsm * device_sms(), items));
   };
   L.sweep_grid = wave(k_batch_sweep, kPeTile, smem, L.n_sweep);
+  L.step_smem = sizeof(double) * ((size_t)L.nmax * L.nmax + 64 * (size_t)L.nmax);
+  L.final_smem = sizeof(double) * ((size_t)L.nmax * L.nqmax + 32 * (size_t)L.nqmax);
+  if ((e = cudaFuncSetAttribute(k_batch_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)L.step_smem)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(k_batch_final, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)L.final_smem)) != cudaSuccess)
+    return e;
+  L.step_grid = wave(k_batch_step, 32 * kStepT, L.step_smem, L.n32);
+  L.final_grid = wave(k_batch_final, 32 * kStepT, L.final_smem, L.n32);
+  L.chunk_grid = std::max(1, std::min(device_sms() * 8, L.nch));
   if (L.n_tc) {
     // B: the largest instance's padded rows x K; A: 128 x K
     L.tc_smem_b = (max_np * max_kp_bytes + 1023) / 1024 * 1024;
@@ -669,11 +912,38 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
   return cudaSuccess;
 }
 
-// The work lists of the loop's first iteration (captured before the loop).
-cudaError_t BatchLoop::launch_lists(cudaStream_t s) {
+// Everything of a step before the loop, each kernel one launch for all the
+// looped instances: reset and start time, right-hand side, initial trace,
+// the work lists, and the first FP64 sweep (which sets the loop condition).
+cudaError_t BatchLoop::launch_pre(cudaStream_t s, cudaGraphConditionalHandle handle) {
   Impl& L = *impl;
+  cudaError_t e;
+  k_batch_begin<<<(L.n_inst + 127) / 128, 128, 0, s>>>(L.d_inst, L.n_inst);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_batch_step<<<L.step_grid, dim3(32, kStepT), L.step_smem, s>>>(L.d_inst, L.d_pre32, L.n_inst,
+                                                                  L.nmax);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_batch_trace0<<<L.chunk_grid, 256, 0, s>>>(L.d_inst, L.d_prech, L.n_inst);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_batch_lists<<<1, 256, sizeof(int) * 5 * 256, s>>>(L.d_inst, L.d_counts, L.n_inst,
                                                        L.d_lists);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_batch_sweep<<<L.sweep_grid, kPeTile, L.sweep_smem, s>>>(L.d_inst, L.d_counts, L.d_lists,
+                                                           L.n_inst, L.d_ticket, handle);
+  return cudaGetLastError();
+}
+
+// Everything of a step after the loop: reconstruction, trace hand-over,
+// step record and instance times.
+cudaError_t BatchLoop::launch_post(cudaStream_t s) {
+  Impl& L = *impl;
+  cudaError_t e;
+  k_batch_final<<<L.final_grid, dim3(32, kStepT), L.final_smem, s>>>(L.d_inst, L.d_pre32,
+                                                                    L.n_inst, L.nmax, L.nqmax);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_batch_trace_end<<<L.chunk_grid, 256, 0, s>>>(L.d_inst, L.d_prech, L.n_inst);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_batch_end<<<(L.n_inst + 127) / 128, 128, 0, s>>>(L.d_inst, L.n_inst);
   return cudaGetLastError();
 }
 
@@ -697,12 +967,6 @@ cudaError_t BatchLoop::launch_body(cudaStream_t s, cudaGraphConditionalHandle ha
 
 int BatchLoop::kernels_per_iteration() const {
   return impl ? (impl->n_tc ? impl->max_m : 0) + (impl->n_apply ? 1 : 0) + 1 : 0;
-}
-
-cudaError_t launch_stamp_conv(cudaStream_t s, unsigned long long* t_start,
-                              unsigned long long* t_acc, unsigned long long* t_conv, int i) {
-  k_stamp_conv<<<1, 1, 0, s>>>(t_start, t_acc, t_conv, i);
-  return cudaGetLastError();
 }
 
 }  // namespace ehdg

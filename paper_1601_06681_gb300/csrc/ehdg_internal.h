@@ -283,16 +283,18 @@ struct BatchLoop {
   BatchLoop& operator=(const BatchLoop&) = delete;
   ~BatchLoop();
   void release();
-  // device tables of the looped instances; t_conv[slot[i]] receives instance
-  // i's convergence time in a step
-  cudaError_t build(const std::vector<Ctx*>& ctxs, unsigned long long* t_conv,
+  // device tables of the looped instances; t_start/t_acc/t_conv[slot[i]]:
+  // instance i's step start, accumulated step times and convergence time
+  cudaError_t build(const std::vector<Ctx*>& ctxs, unsigned long long* t_start,
+                    unsigned long long* t_acc, unsigned long long* t_conv,
                     const std::vector<int>& slot);
-  cudaError_t launch_lists(cudaStream_t s);   // the first iteration's work lists
+  // a step's kernels before the loop (they set the loop condition), the loop
+  // body, and the kernels after it
+  cudaError_t launch_pre(cudaStream_t s, cudaGraphConditionalHandle handle);
   cudaError_t launch_body(cudaStream_t s, cudaGraphConditionalHandle handle);
+  cudaError_t launch_post(cudaStream_t s);
   int kernels_per_iteration() const;
 };
-cudaError_t launch_stamp_conv(cudaStream_t s, unsigned long long* t_start,
-                              unsigned long long* t_acc, unsigned long long* t_conv, int i);
 
 enum FaceMode { kFaceInitial = 0, kFaceIterate = 1 };
 

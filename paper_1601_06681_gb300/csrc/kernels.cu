@@ -10,6 +10,7 @@
 #include <cmath>
 
 #include "ehdg_internal.h"
+#include "step_tiles.cuh"
 
 namespace ehdg {
 
@@ -435,32 +436,10 @@ cudaError_t launch_face_signs(Ctx& c) {
 // Per-step right-hand side: G = P w, Gy = Ey G, Y0 = Ey u^n
 //   w = u^n / dt_eff + f (time-dependent) or w = f (steady)
 // ===========================================================================
-struct StepParams {
-  int64_t nel;
-  int n, NQFS, KE, shared;
-  double ucoef;                 // 1/dt_eff, or 0 for steady
-  int have_force, force_avg;    // force_avg: use 0.5 (f_old + f) (Crank-Nicolson)
-  const double* P;
-  const double* u;
-  const double* force;
-  const double* force_old;
-  const int* ey_idx;
-  const double* ey_val;
-  const int* rows;              // shared operator: output rows of every element
-  int n_rows;
-  const uint8_t* rowid;         // per-element operator: [NQFS][nel] row of each slot
-  const uint8_t* nrows;         // [nel] slots in use
-  int g_ready;                  // 1: G = P w already computed (tensor-core step)
-  double* G;
-  double* Gy;                   // [slot][nel], slot order of the element sweep
-  double* Y;
-};
-
 // Tile of 32 consecutive elements (threadIdx.x) x kStepT row groups
 // (threadIdx.y); persistent over tiles. w and G of the tile live in shared
-// memory; a shared operator P is staged once per block.
-constexpr int kStepT = 4;
-
+// memory; a shared operator P is staged once per block. The tile body is in
+// step_tiles.cuh (the batched loop runs it too).
 __global__ void __launch_bounds__(32 * kStepT) k_step(const StepParams s) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x, t = threadIdx.y, tid = t * 32 + lane;
@@ -470,71 +449,9 @@ __global__ void __launch_bounds__(32 * kStepT) k_step(const StepParams s) {
   double* g = w + n * 32;                             // [n][32]
   if (s.shared)
     for (int i = tid; i < n * n; i += 32 * kStepT) Psh[i] = s.P[i];
-  const int64_t ne = s.nel;
-  const int64_t ntiles = (ne + 31) / 32;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t e = tile * 32 + lane;
-    const bool live = e < ne;
-    __syncthreads();
-    if (s.g_ready) {
-      // G = P w came from the FP64-accurate tensor-core product
-      for (int r = t; r < n; r += kStepT) g[r * 32 + lane] = live ? s.G[r * ne + e] : 0.0;
-    } else {
-      for (int c = t; c < n; c += kStepT) {
-        double v = 0.0;
-        if (live) {
-          v = s.u[c * ne + e] * s.ucoef;
-          if (s.have_force)
-            v += s.force_avg ? 0.5 * (s.force[c * ne + e] + s.force_old[c * ne + e])
-                             : s.force[c * ne + e];
-        }
-        w[c * 32 + lane] = v;
-      }
-      __syncthreads();
-      for (int r = t; r < n; r += kStepT) {
-        double a0 = 0.0, a1 = 0.0;
-        if (s.shared) {
-          const double* Pr = Psh + r * n;
-          int c = 0;
-          for (; c + 1 < n; c += 2) {
-            a0 = fma(Pr[c], w[c * 32 + lane], a0);
-            a1 = fma(Pr[c + 1], w[(c + 1) * 32 + lane], a1);
-          }
-          if (c < n) a0 = fma(Pr[c], w[c * 32 + lane], a0);
-        } else if (live) {
-          const double* Pr = s.P + (int64_t)r * n * ne + e;
-          int c = 0;
-          for (; c + 1 < n; c += 2) {
-            a0 = fma(Pr[c * ne], w[c * 32 + lane], a0);
-            a1 = fma(Pr[(c + 1) * ne], w[(c + 1) * 32 + lane], a1);
-          }
-          if (c < n) a0 = fma(Pr[c * ne], w[c * 32 + lane], a0);
-        }
-        const double acc = a0 + a1;
-        g[r * 32 + lane] = acc;
-        if (live) s.G[r * ne + e] = acc;
-      }
-    }
-    __syncthreads();
-    if (!live) continue;
-    // the rows the sweep computes (upwind and tangential points; every point
-    // for shallow water): Gy in the sweep's slot order, and the element
-    // values Y0 = Ey u^n there, which are all the initial trace reads (it
-    // takes the upwind side, or both sides of a tangential point)
-    const int nr = s.shared ? s.n_rows : s.nrows[e];
-    for (int j = t; j < nr; j += kStepT) {
-      const int r = s.shared ? s.rows[j] : s.rowid[j * ne + e];
-      double y0 = 0.0, gy = 0.0;
-      for (int k2 = 0; k2 < s.KE; ++k2) {
-        const double w = s.ey_val[r * s.KE + k2];
-        const int i = s.ey_idx[r * s.KE + k2];
-        y0 = fma(w, s.u[i * ne + e], y0);
-        gy = fma(w, g[i * 32 + lane], gy);
-      }
-      s.Y[r * ne + e] = y0;
-      s.Gy[j * ne + e] = gy;
-    }
-  }
+  const int64_t ntiles = (s.nel + 31) / 32;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    step_tile(s, Psh, w, g, tile);
 }
 
 cudaError_t launch_step(Ctx& c) {
@@ -787,9 +704,6 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
   const double* uh_old = p.uhat + (int64_t)(kk & 1) * total + (int64_t)gf * nface;
   double* uh_new = p.uhat + (int64_t)((p.mode == kFaceIterate ? kk + 1 : 0) & 1) * total +
                    (int64_t)gf * nface;
-  const int8_t* sgn = p.sgn + (int64_t)gf * nface;
-  const double* gb = p.gb + (int64_t)gf * nface;
-  const double* gbo = p.gb_old + (int64_t)gf * nface;
   const double wg = p.fw[gf];
   const int64_t ym_off = (int64_t)gf * nel;   // + (local face * Nqf) * nel + elem
   double acc = 0.0;
@@ -801,18 +715,8 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
     const int fpl = p.geo.face_local[nface + face];
     double uh;
     if (p.pde == EHDG_TRANSPORT) {
-      const int s = sgn[face];
-      double ext = 0.0;
-      if (ep < 0) ext = p.cn ? 0.5 * (gb[face] + gbo[face]) : gb[face];
-      if (s > 0) {
-        uh = p.Y[ym_off + (int64_t)fm * p.Nqf * nel + em];
-      } else if (s < 0) {
-        uh = (ep >= 0) ? p.Y[ym_off + (int64_t)fpl * p.Nqf * nel + ep] : ext;
-      } else {
-        const double ym = p.Y[ym_off + (int64_t)fm * p.Nqf * nel + em];
-        const double yp = (ep >= 0) ? p.Y[ym_off + (int64_t)fpl * p.Nqf * nel + ep] : ext;
-        uh = 0.5 * (ym + yp);
-      }
+      uh = transport_trace_point(nel, nface, p.Nqf, p.cn, p.geo.face_elem, p.geo.face_local,
+                                 p.sgn, p.Y, p.gb, p.gb_old, gf, face);
     } else {
       const double ym = p.Y[ym_off + (int64_t)fm * p.Nqf * nel + em];
       uh = (ep >= 0) ? ym + p.Y[ym_off + (int64_t)fpl * p.Nqf * nel + ep] : 2.0 * ym;
@@ -922,17 +826,6 @@ cudaError_t launch_face(Ctx& c, int mode, int graph_mode) {
 // ===========================================================================
 // End of step: u^{n+1} = G + H uhat (Crank-Nicolson: 2 v - u^n), trace update
 // ===========================================================================
-struct FinalParams {
-  int64_t nel, nface;
-  int n, NQFS, Nqf, F, shared, cn;
-  const int32_t* elem_face;
-  const double* uhat;           // [2][Nqf][nface]
-  const IterState* it;
-  const double* G;
-  const double* H;
-  double* u;
-};
-
 __global__ void __launch_bounds__(32 * kStepT) k_final(const FinalParams p) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x, t = threadIdx.y, tid = t * 32 + lane;
@@ -940,47 +833,11 @@ __global__ void __launch_bounds__(32 * kStepT) k_final(const FinalParams p) {
   double* uh = sm + (p.shared ? p.n * p.NQFS : 0);     // [NQFS][32]
   if (p.shared)
     for (int i = tid; i < p.n * p.NQFS; i += 32 * kStepT) Hsh[i] = p.H[i];
-  const int64_t ne = p.nel;
-  const int64_t ntiles = (ne + 31) / 32;
+  const int64_t ntiles = (p.nel + 31) / 32;
   // Algorithm 1 returns u^{k+1}, the local solve with the trace uhat^k
   const double* src = p.uhat + (int64_t)((p.it->k + 1) & 1) * p.Nqf * p.nface;
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t e = tile * 32 + lane;
-    const bool live = e < ne;
-    __syncthreads();
-    if (live) {
-      for (int f = 0; f < p.F; ++f) {
-        const int64_t face = p.elem_face[f * ne + e];
-        for (int g = t; g < p.Nqf; g += kStepT)
-          uh[(f * p.Nqf + g) * 32 + lane] = src[g * p.nface + face];
-      }
-    }
-    __syncthreads();
-    if (!live) continue;
-    for (int r = t; r < p.n; r += kStepT) {
-      double a0 = p.G[r * ne + e], a1 = 0.0;
-      if (p.shared) {
-        const double* Hr = Hsh + r * p.NQFS;
-        int c = 0;
-        for (; c + 1 < p.NQFS; c += 2) {
-          a0 = fma(Hr[c], uh[c * 32 + lane], a0);
-          a1 = fma(Hr[c + 1], uh[(c + 1) * 32 + lane], a1);
-        }
-        if (c < p.NQFS) a0 = fma(Hr[c], uh[c * 32 + lane], a0);
-      } else {
-        const double* Hr = p.H + (int64_t)r * p.NQFS * ne + e;
-        int c = 0;
-        for (; c + 1 < p.NQFS; c += 2) {
-          a0 = fma(Hr[c * ne], uh[c * 32 + lane], a0);
-          a1 = fma(Hr[(c + 1) * ne], uh[(c + 1) * 32 + lane], a1);
-        }
-        if (c < p.NQFS) a0 = fma(Hr[c * ne], uh[c * 32 + lane], a0);
-      }
-      double acc = a0 + a1;
-      if (p.cn) acc = 2.0 * acc - p.u[r * ne + e];
-      p.u[r * ne + e] = acc;
-    }
-  }
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
+    final_tile(p, Hsh, uh, src, tile);
 }
 
 // The final trace uhat^{K} (slot K&1) becomes the state's trace in slot 0
