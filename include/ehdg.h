@@ -20,7 +20,11 @@
  *    ehdg_destroy.
  *  - Pointers are HOST pointers unless the argument `on_device` is non-zero,
  *    in which case they are device pointers valid on the context's device.
- *    Device-pointer transfers are ordered on the context's stream.
+ *    Device-pointer transfers are ordered on the context's stream: a call
+ *    that takes device pointers may return before the stream has read them,
+ *    so they must stay valid until later work on that stream (the next step,
+ *    or a synchronisation of the stream) has run. Host pointers are copied
+ *    before the call returns.
  *  - Meshes are conforming, axis-aligned quads (dim 2) or hexes (dim 3).
  *    Local faces are numbered f = 2*axis + side (order -x,+x,-y,+y,-z,+z).
  *    On every face the minus element sees n^- = +e_axis when it lies on the

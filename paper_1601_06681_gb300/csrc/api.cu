@@ -1105,7 +1105,8 @@ ehdg_status ehdg_set_state(ehdg_ctx h, const double* u, const double* uhat, int 
     CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceInitial); }));
   }
   CK(cudaMemcpyAsync(c.uhat_n, c.uhat, sizeof(double) * trace, cudaMemcpyDeviceToDevice, c.stream));
-  CK(cudaStreamSynchronize(c.stream));
+  // device pointers are ordered on the context's stream like every later
+  // call: nothing to wait for (host pointers were copied synchronously)
   return EHDG_OK;
 }
 

@@ -320,14 +320,19 @@ class Solver:
         if uhat is not None:
             assert dev == dev2
         _check(load().ehdg_set_state(self._h, pu, ph, dev))
+        # device buffers are read on the context's stream after the call
+        # returns: keep them alive until the next upload
+        self._state_keep = (ku, kh)
 
     def set_forcing(self, f):
         pf, dev, kf = _buf(f, self.state_shape)
         _check(load().ehdg_set_forcing(self._h, pf, dev))
+        self._forcing_keep = kf
 
     def set_boundary(self, g):
         pg, dev, kg = _buf(g, self.trace_shape)
         _check(load().ehdg_set_boundary(self._h, pg, dev))
+        self._boundary_keep = kg
 
     def step(self, check=True):
         it, res = C.c_int(), C.c_double()
