@@ -1135,6 +1135,15 @@ def batch_workload(args):
                      "p50_instance_ms": float(np.percentile(times, 50) * 1e3),
                      "p99_instance_ms": float(np.percentile(times, 99) * 1e3),
                      "sweeps_total": int(iters.sum()), "chains": chains, **tuned}
+        if opt != "branches" and base in ("fp64", "tf32", "bf16"):
+            # kernel accounting of the batched loop: the same run with its
+            # steps driven from the host and every launch timed
+            b.set_profiling(True)
+            one_run()
+            st = b.kernel_stats()
+            b.set_profiling(False)
+            out[prec]["loop_kernel_ms"] = {k: round(v[1], 3) for k, v in st.items() if v[0]}
+            out[prec]["loop_kernel_launches"] = {k: v[0] for k, v in st.items() if v[0]}
         b.close()
     for prec in variants[1:]:
         out[prec]["speedup_vs_fp64"] = out["fp64"]["wall_s"] / out[prec]["wall_s"]

@@ -294,6 +294,19 @@ ehdg_status ehdg_batch_set_chains(ehdg_batch b, int k);
  * on the branches. The graph is recaptured at the next run. EHDG_ERR_INVALID
  * for a NULL batch. */
 ehdg_status ehdg_batch_set_loop(ehdg_batch b, int on);
+/* Kernel accounting of the batched loop (a diagnostic; the paper has no
+ * counterpart). With profiling on (which resets the counters),
+ * ehdg_batch_run drives the looped instances' steps from the host -- the
+ * same kernels as the graph, each launch bracketed by CUDA events on the
+ * batch's stream, the loop condition read back after every iteration -- and
+ * runs every other instance's steps by its own graph; inst_time_s is then not
+ * filled. ehdg_batch_kernel_stats returns the launches and summed device time
+ * of one ehdg_kernel_kind of the looped instances' kernels: STEP right-hand
+ * side, FACE initial trace and trace hand-over, ELEM FP64 sweeps, CORR
+ * correction sweeps, FINAL reconstruction, AUX reset, work lists, FP64
+ * update and step record. EHDG_ERR_INVALID for a NULL batch or a bad kind. */
+ehdg_status ehdg_batch_set_profiling(ehdg_batch b, int on);
+ehdg_status ehdg_batch_kernel_stats(ehdg_batch b, int kind, int64_t* launches, double* total_ms);
 /* Autotuner for the branch count: from the instances' current states, each
  * candidate k runs as many batch steps as the batch's last ehdg_batch_run
  * (one step before the first run) -- the run the choice is for -- timed with

@@ -31,6 +31,10 @@ struct ehdg_batch_s {
   // unconverged instance) for the instances it supports
   bool use_loop = true;
   int last_run_steps = 0;               // steps of the last run: what the autotuners time
+  // kernel accounting of the batched loop (ehdg_batch_set_profiling)
+  bool profiling = false;
+  double prof_ms[EHDG_KERNEL_KINDS] = {0};
+  int64_t prof_launches[EHDG_KERNEL_KINDS] = {0};
   bool tuning = false;                  // an autotuner is running candidate steps
   ehdg::BatchLoop loop;
   std::vector<char> looped;             // instance i iterates in the batched loop
@@ -1505,7 +1509,25 @@ ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_t
   CK(cudaMemsetAsync(b->t_acc, 0, sizeof(unsigned long long) * n, b->stream));
   for (int i = 0; i < n; ++i)
     CK(cudaMemsetAsync(&b->inst[i]->c.it->step, 0, sizeof(int), b->stream));
-  for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(b->exec, b->stream));
+  if (b->profiling && b->loop.impl) {
+    // kernel accounting: the looped instances' steps driven from the host with
+    // every launch timed, the other instances' steps by their own graphs
+    for (int i = 0; i < n; ++i)
+      if (!b->looped[i]) {
+        Ctx& c = b->inst[i]->c;
+        cudaStream_t own = c.stream;
+        c.stream = b->stream;
+        const ehdg_status st = run_graph(c, n_steps, nullptr, nullptr);
+        c.stream = own;
+        if (st != EHDG_OK && st != EHDG_ERR_NOT_CONVERGED && st != EHDG_ERR_DIVERGED) return st;
+      }
+    int max_iter = 1;
+    for (int i = 0; i < n; ++i) max_iter = std::max(max_iter, b->inst[i]->c.max_iter);
+    for (int s = 0; s < n_steps; ++s)
+      CK(b->loop.run_step_profiled(b->stream, max_iter, b->prof_ms, b->prof_launches));
+  } else {
+    for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(b->exec, b->stream));
+  }
   std::vector<unsigned long long> acc(n);
   CK(cudaMemcpyAsync(acc.data(), b->t_acc, sizeof(unsigned long long) * n, cudaMemcpyDeviceToHost,
                      b->stream));
@@ -1547,6 +1569,23 @@ ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_t
   // measured ones, once, before the next run
   if (first == EHDG_OK && b->built_on_estimate) TRY(batch_build_graph(b));
   return first;
+}
+
+ehdg_status ehdg_batch_set_profiling(ehdg_batch b, int on) {
+  if (!b) return fail(EHDG_ERR_INVALID, "NULL batch");
+  b->profiling = on != 0;
+  for (int k = 0; k < EHDG_KERNEL_KINDS; ++k) {
+    b->prof_ms[k] = 0.0;
+    b->prof_launches[k] = 0;
+  }
+  return EHDG_OK;
+}
+
+ehdg_status ehdg_batch_kernel_stats(ehdg_batch b, int kind, int64_t* launches, double* total_ms) {
+  if (!b || kind < 0 || kind >= EHDG_KERNEL_KINDS) return fail(EHDG_ERR_INVALID, "bad argument");
+  if (launches) *launches = b->prof_launches[kind];
+  if (total_ms) *total_ms = b->prof_ms[kind];
+  return EHDG_OK;
 }
 
 ehdg_status ehdg_batch_set_loop(ehdg_batch b, int on) {

@@ -210,7 +210,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // body, reduction and stopping test.
 __global__ void __launch_bounds__(kPeTile) k_batch_sweep(const BInst* inst, const int4* counts,
                                                           int* lists, int n_inst,
-                                                          unsigned int* ticket,
+                                                          unsigned int* ticket, int graph_mode,
                                                           cudaGraphConditionalHandle handle) {
   extern __shared__ double sm[];
   const int tid = threadIdx.x;
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(kPeTile) k_batch_sweep(const BInst* inst, cons
   build_lists(inst, counts, n_inst, lists);
   if (tid == 0) {
     *ticket = 0u;
-    cudaGraphSetConditional(handle, lists[0] > 0 ? 1u : 0u);
+    if (graph_mode) cudaGraphSetConditional(handle, lists[0] > 0 ? 1u : 0u);
   }
 }
 
@@ -929,7 +929,7 @@ cudaError_t BatchLoop::launch_pre(cudaStream_t s, cudaGraphConditionalHandle han
                                                        L.d_lists);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_batch_sweep<<<L.sweep_grid, kPeTile, L.sweep_smem, s>>>(L.d_inst, L.d_counts, L.d_lists,
-                                                           L.n_inst, L.d_ticket, handle);
+                                                           L.n_inst, L.d_ticket, 1, handle);
   return cudaGetLastError();
 }
 
@@ -961,8 +961,92 @@ cudaError_t BatchLoop::launch_body(cudaStream_t s, cudaGraphConditionalHandle ha
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   k_batch_sweep<<<L.sweep_grid, kPeTile, L.sweep_smem, s>>>(L.d_inst, L.d_counts, L.d_lists,
-                                                           L.n_inst, L.d_ticket, handle);
+                                                           L.n_inst, L.d_ticket, 1, handle);
   return cudaGetLastError();
+}
+
+// One step of the looped instances driven from the host, every launch
+// bracketed by CUDA events on stream s (kernel accounting): the same kernels
+// as the graph, the loop condition read back after every iteration.
+cudaError_t BatchLoop::run_step_profiled(cudaStream_t s, int max_iter, double* ms,
+                                         int64_t* launches) {
+  Impl& L = *impl;
+  cudaEvent_t ev[2];
+  cudaError_t e = cudaEventCreate(&ev[0]);
+  if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+  auto timed = [&](int kind, auto&& launch) -> cudaError_t {
+    cudaError_t r = cudaEventRecord(ev[0], s);
+    if (r == cudaSuccess) r = launch();
+    if (r == cudaSuccess) r = cudaEventRecord(ev[1], s);
+    if (r == cudaSuccess) r = cudaEventSynchronize(ev[1]);
+    float t = 0.f;
+    if (r == cudaSuccess) r = cudaEventElapsedTime(&t, ev[0], ev[1]);
+    ms[kind] += t;
+    launches[kind] += 1;
+    return r;
+  };
+  const cudaGraphConditionalHandle none = 0;
+  if (e == cudaSuccess) e = timed(EHDG_KERNEL_AUX, [&] {
+    k_batch_begin<<<(L.n_inst + 127) / 128, 128, 0, s>>>(L.d_inst, L.n_inst);
+    return cudaGetLastError();
+  });
+  if (e == cudaSuccess) e = timed(EHDG_KERNEL_STEP, [&] {
+    k_batch_step<<<L.step_grid, dim3(32, kStepT), L.step_smem, s>>>(L.d_inst, L.d_pre32,
+                                                                    L.n_inst, L.nmax);
+    return cudaGetLastError();
+  });
+  if (e == cudaSuccess) e = timed(EHDG_KERNEL_FACE, [&] {
+    k_batch_trace0<<<L.chunk_grid, 256, 0, s>>>(L.d_inst, L.d_prech, L.n_inst);
+    return cudaGetLastError();
+  });
+  if (e == cudaSuccess) e = timed(EHDG_KERNEL_AUX, [&] {
+    k_batch_lists<<<1, 256, sizeof(int) * 5 * 256, s>>>(L.d_inst, L.d_counts, L.n_inst,
+                                                         L.d_lists);
+    return cudaGetLastError();
+  });
+  auto sweep = [&] {
+    return timed(EHDG_KERNEL_ELEM, [&] {
+      k_batch_sweep<<<L.sweep_grid, kPeTile, L.sweep_smem, s>>>(
+          L.d_inst, L.d_counts, L.d_lists, L.n_inst, L.d_ticket, 0, none);
+      return cudaGetLastError();
+    });
+  };
+  if (e == cudaSuccess) e = sweep();
+  int n_active = 0;
+  for (int it = 0; e == cudaSuccess && it < max_iter; ++it) {
+    if ((e = cudaMemcpy(&n_active, L.d_lists, sizeof(int), cudaMemcpyDeviceToHost)) !=
+        cudaSuccess || n_active == 0)
+      break;
+    for (int j = 0; j < L.max_m && L.n_tc && e == cudaSuccess; ++j)
+      e = timed(EHDG_KERNEL_CORR, [&] {
+        k_batch_tc<<<L.tc_grid, kBTcThreads, L.tc_smem, s>>>(L.d_inst, L.d_lists, L.n_inst, j,
+                                                            L.tc_ncols, L.tc_smem_b,
+                                                            L.tc_smem_a);
+        return cudaGetLastError();
+      });
+    if (L.n_apply && e == cudaSuccess)
+      e = timed(EHDG_KERNEL_AUX, [&] {
+        k_batch_apply<<<L.apply_grid, 256, 0, s>>>(L.d_inst, L.d_lists, L.n_inst);
+        return cudaGetLastError();
+      });
+    if (e == cudaSuccess) e = sweep();
+  }
+  if (e == cudaSuccess) e = timed(EHDG_KERNEL_FINAL, [&] {
+    k_batch_final<<<L.final_grid, dim3(32, kStepT), L.final_smem, s>>>(
+        L.d_inst, L.d_pre32, L.n_inst, L.nmax, L.nqmax);
+    return cudaGetLastError();
+  });
+  if (e == cudaSuccess) e = timed(EHDG_KERNEL_FACE, [&] {
+    k_batch_trace_end<<<L.chunk_grid, 256, 0, s>>>(L.d_inst, L.d_prech, L.n_inst);
+    return cudaGetLastError();
+  });
+  if (e == cudaSuccess) e = timed(EHDG_KERNEL_AUX, [&] {
+    k_batch_end<<<(L.n_inst + 127) / 128, 128, 0, s>>>(L.d_inst, L.n_inst);
+    return cudaGetLastError();
+  });
+  cudaEventDestroy(ev[0]);
+  cudaEventDestroy(ev[1]);
+  return e;
 }
 
 int BatchLoop::kernels_per_iteration() const {

@@ -293,6 +293,9 @@ struct BatchLoop {
   cudaError_t launch_pre(cudaStream_t s, cudaGraphConditionalHandle handle);
   cudaError_t launch_body(cudaStream_t s, cudaGraphConditionalHandle handle);
   cudaError_t launch_post(cudaStream_t s);
+  // one step driven from the host, each launch timed with CUDA events:
+  // ms[kind] and launches[kind] accumulate (ehdg_kernel_kind)
+  cudaError_t run_step_profiled(cudaStream_t s, int max_iter, double* ms, int64_t* launches);
   int kernels_per_iteration() const;
 };
 

@@ -103,6 +103,9 @@ _SIGS = [
     ("ehdg_batch_run", C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
     ("ehdg_batch_set_chains", C.c_int, [C.c_void_p, C.c_int]),
     ("ehdg_batch_set_loop", C.c_int, [C.c_void_p, C.c_int]),
+    ("ehdg_batch_set_profiling", C.c_int, [C.c_void_p, C.c_int]),
+    ("ehdg_batch_kernel_stats", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_double)]),
     ("ehdg_batch_autotune_chains", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
                                              C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_batch_autotune_sweep_tile", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
@@ -490,6 +493,20 @@ class Batch:
         """Batched iteration loop for the instances it supports (default on);
         off runs every instance's own loop on the graph's branches."""
         _check(load().ehdg_batch_set_loop(self._h, 1 if on else 0))
+
+    def set_profiling(self, on=True):
+        """Kernel accounting of the batched loop (host-driven steps, every
+        launch timed); resets the counters."""
+        _check(load().ehdg_batch_set_profiling(self._h, 1 if on else 0))
+
+    def kernel_stats(self):
+        """{kind: (launches, total device ms)} of the batched loop's kernels."""
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            n, ms = C.c_int64(), C.c_double()
+            _check(load().ehdg_batch_kernel_stats(self._h, k, C.byref(n), C.byref(ms)))
+            out[name] = (n.value, ms.value)
+        return out
 
     def set_chains(self, k):
         """Concurrent branches of the batch's graph (k <= 0: one per hardware
