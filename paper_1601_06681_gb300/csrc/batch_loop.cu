@@ -69,6 +69,8 @@ struct BInst {
   float* d32;
   float* Y32;
   int* err;
+  const uint4* Bimg;            // the rounded operator rows, K-major image (Np x Kp)
+  const int* rowfg;             // [Np] face | point << 8 of each row
   // convergence time of the instance in the current step (%globaltimer), and
   // the step's start and the accumulated step times
   unsigned long long* t_conv;
@@ -369,7 +371,11 @@ __global__ void __launch_bounds__(kBTcThreads) k_batch_tc(const BInst* inst, con
   const int* act = lv.act_mx(lists);
   const int* pre = lv.pre_tc(lists);
   const int n_items = n_act > 0 ? pre[n_act] : 0;
-  for (int w = blockIdx.x; w < n_items && !failed; w += gridDim.x) {
+  // a contiguous run of items per block: consecutive tiles of one instance
+  // share its staged operator
+  const int per = (n_items + gridDim.x - 1) / gridDim.x;
+  const int w_end = min(n_items, (int)(blockIdx.x + 1) * per);
+  for (int w = blockIdx.x * per; w < w_end && !failed; ++w) {
     const int k = owner_of(pre, n_act, w);
     const int2 item = make_int2(act[k], w - pre[k]);
     const BInst& I = inst[item.x];
@@ -379,18 +385,15 @@ __global__ void __launch_bounds__(kBTcThreads) k_batch_tc(const BInst* inst, con
     const uint32_t kbytes = (uint32_t)I.Kp * esize;
     const uint32_t sbo = kbytes * 8u;
     if (item.x != cur) {
-      // the instance's operator rows (B) and row tables
+      // the instance's operator rows (B, rounded once at setup) and row tables
       for (int jj = tid; jj < I.Np; jj += kBTcThreads) {
-        const int r = jj < I.n_rows ? I.rows[jj] : 0;
-        row_f[jj] = r / I.Nqf;
-        row_g[jj] = r - (r / I.Nqf) * I.Nqf;
+        const int fg = I.rowfg[jj];
+        row_f[jj] = fg & 255;
+        row_g[jj] = fg >> 8;
       }
-      for (int i = tid; i < I.Np * I.Kp; i += kBTcThreads) {
-        const int n = i / I.Kp, k = i - n * I.Kp;
-        float v = 0.f;
-        if (n < I.n_rows && k < I.NQFS) v = I.Hy32[I.rows[n] * I.NQFS + k];
-        b_store_elem(Bs, n, k, esize, sbo, v, I.bf16);
-      }
+      const int n16 = (int)((uint32_t)I.Np * kbytes / 16u);
+      for (int i = tid; i < n16; i += kBTcThreads)
+        reinterpret_cast<uint4*>(Bs)[i] = I.Bimg[i];
       cur = item.x;
     }
     const int64_t trace = (int64_t)I.Nqf * I.nface;
@@ -510,6 +513,25 @@ __global__ void __launch_bounds__(kBTcThreads) k_batch_tc(const BInst* inst, con
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
                  "r"(ncols));
+}
+
+// Setup: instance i's operator rows rounded to TF32 / BF16 in the K-major
+// image the correction sweep stages (the single-problem sweep's rounding),
+// and its row tables.
+__global__ void k_batch_bimg(const float* Hy32, const int* rows, int n_rows, int NQFS, int Nqf,
+                             int Np, int Kp, int bf16, unsigned char* img, int* rowfg) {
+  const int esize = bf16 ? 2 : 4;
+  const uint32_t sbo = (uint32_t)Kp * esize * 8u;
+  for (int i = threadIdx.x; i < Np * Kp; i += blockDim.x) {
+    const int n = i / Kp, k = i - n * Kp;
+    float v = 0.f;
+    if (n < n_rows && k < NQFS) v = Hy32[rows[n] * NQFS + k];
+    b_store_elem(img, n, k, esize, sbo, v, bf16);
+  }
+  for (int jj = threadIdx.x; jj < Np; jj += blockDim.x) {
+    const int r = jj < n_rows ? rows[jj] : 0;
+    rowfg[jj] = (r / Nqf) | ((r - (r / Nqf) * Nqf) << 8);
+  }
 }
 
 // uhat <- uhat + delta in FP64 for every unconverged mixed-precision
@@ -728,6 +750,7 @@ struct BatchLoop::Impl {
   BInst* d_inst = nullptr;
   int4* d_counts = nullptr;
   int* d_lists = nullptr;
+  unsigned char* d_bimg = nullptr;   // operator images and row tables of the mixed instances
   int* d_pre32 = nullptr;       // static lists: 32-element tiles, trace chunks
   int* d_prech = nullptr;
   int n32 = 0, nch = 0, nmax = 1, nqmax = 1;
@@ -747,6 +770,7 @@ void BatchLoop::release() {
   cudaFree(impl->d_counts);
   cudaFree(impl->d_lists);
   cudaFree(impl->d_pre32);
+  cudaFree(impl->d_bimg);
   cudaFree(impl->d_prech);
   cudaFree(impl->d_ticket);
   delete impl;
@@ -860,6 +884,32 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
                       cudaMemcpyHostToDevice)) != cudaSuccess)
     return e;
   const size_t list_ints = kListHeader + 5 * (size_t)L.n_inst + 3;
+  // operator images and row tables of the mixed-precision instances
+  {
+    std::vector<size_t> off(L.n_inst, 0), roff(L.n_inst, 0);
+    size_t bytes = 0;
+    for (int i = 0; i < L.n_inst; ++i) {
+      if (!h[i].tc) continue;
+      off[i] = bytes;
+      bytes += ((size_t)h[i].Np * h[i].Kp * (h[i].bf16 ? 2 : 4) + 255) / 256 * 256;
+      roff[i] = bytes;
+      bytes += ((size_t)h[i].Np * sizeof(int) + 255) / 256 * 256;
+    }
+    if (bytes > 0) {
+      if ((e = cudaMalloc(&L.d_bimg, bytes)) != cudaSuccess) return e;
+      for (int i = 0; i < L.n_inst; ++i) {
+        if (!h[i].tc) continue;
+        const Ctx& c = *ctxs[i];
+        k_batch_bimg<<<1, 256>>>(c.Hy32, c.rows, c.n_rows, c.NQFS, c.Nqf, h[i].Np, h[i].Kp,
+                                 h[i].bf16, L.d_bimg + off[i],
+                                 reinterpret_cast<int*>(L.d_bimg + roff[i]));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        h[i].Bimg = reinterpret_cast<const uint4*>(L.d_bimg + off[i]);
+        h[i].rowfg = reinterpret_cast<const int*>(L.d_bimg + roff[i]);
+      }
+      if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+    }
+  }
   if ((e = cudaMalloc(&L.d_inst, sizeof(BInst) * std::max(1, L.n_inst))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&L.d_counts, sizeof(int4) * std::max(1, L.n_inst))) != cudaSuccess) return e;
   if ((e = cudaMemcpy(L.d_counts, cnt.data(), sizeof(int4) * L.n_inst, cudaMemcpyHostToDevice)) !=
