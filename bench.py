@@ -1084,8 +1084,9 @@ def batch_workload(args):
     # "+inner": the inner sweep count m from ehdg_batch_autotune_inner_sweeps
     # "+tiles": the fused FP64 sweep's tile (row groups FT) of all instances
     # from ehdg_batch_autotune_sweep_tile
-    variants = ["fp64", "tf32", "bf16", "fp64+branches", "tf32+branches", "tf32+inner",
-                "fp64_emulated", "tf32+emulated_outer"]
+    variants = ["fp64", "fp32", "tf32", "bf16", "fp64+branches", "fp32+branches",
+                "tf32+branches", "fp32+inner", "tf32+inner", "fp64_emulated",
+                "tf32+emulated_outer"]
     for prec in variants:
         base, _, opt = prec.partition("+")
         specs, inputs = [], []
@@ -1135,7 +1136,7 @@ def batch_workload(args):
                      "p50_instance_ms": float(np.percentile(times, 50) * 1e3),
                      "p99_instance_ms": float(np.percentile(times, 99) * 1e3),
                      "sweeps_total": int(iters.sum()), "chains": chains, **tuned}
-        if opt != "branches" and base in ("fp64", "tf32", "bf16"):
+        if opt != "branches" and base in ("fp64", "fp32", "tf32", "bf16"):
             # kernel accounting of the batched loop: the same run with its
             # steps driven from the host and every launch timed
             b.set_profiling(True)

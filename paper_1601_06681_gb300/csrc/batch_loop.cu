@@ -60,8 +60,9 @@ struct BInst {
   double* hist;
   double tol, res_scale;
   int max_iter;
-  // corrections (tensor cores), mixed precision only
-  int tc, bf16, m;
+  // corrections, mixed precision only: tensor cores (mma) or FP32 on the
+  // CUDA cores, one thread per element
+  int tc, mma, bf16, m;
   int Np, Kp;
   uint32_t idesc;
   const float* Hy32;
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(kBTcThreads) k_batch_tc(const BInst* inst, con
     const int k = owner_of(pre, n_act, w);
     const int2 item = make_int2(act[k], w - pre[k]);
     const BInst& I = inst[item.x];
-    if (I.m <= j) continue;                         // its inner sweeps are done
+    if (!I.mma || I.m <= j) continue;               // FP32 corrections, or its inner sweeps done
     __syncthreads();   // the previous item is done with the shared operands
     const int esize = I.bf16 ? 2 : 4;
     const uint32_t kbytes = (uint32_t)I.Kp * esize;
@@ -531,6 +532,55 @@ __global__ void k_batch_bimg(const float* Hy32, const int* rows, int n_rows, int
   for (int jj = threadIdx.x; jj < Np; jj += blockDim.x) {
     const int r = jj < n_rows ? rows[jj] : 0;
     rowfg[jj] = (r / Nqf) | ((r - (r / Nqf) * Nqf) << 8);
+  }
+}
+
+// Inner correction sweep j of every instance that still iterates with FP32
+// corrections (the single-problem one-thread-per-element tile body); items
+// from the same list as the tensor-core sweep (128-element tiles).
+__global__ void __launch_bounds__(kPeTile) k_batch_lp(const BInst* inst, const int* lists,
+                                                      int n_inst, int j) {
+  extern __shared__ float smf[];
+  const ListView lv{n_inst};
+  const int n_act = lists[1];
+  const int* act = lv.act_mx(lists);
+  const int* pre = lv.pre_tc(lists);
+  const int n_items = n_act > 0 ? pre[n_act] : 0;
+  int cur = -1;
+  for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+    const int k = owner_of(pre, n_act, w);
+    const int idx = act[k];
+    const BInst& I = inst[idx];
+    if (I.mma || I.m <= j) continue;
+    const int nq = I.NQFS;
+    if (idx != cur) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < I.n_up * nq; i += kPeTile) {
+        const int jj = i / nq, c = i - jj * nq;
+        smf[i] = I.Hy32[I.rows[jj] * nq + c];
+      }
+      __syncthreads();
+      cur = idx;
+    }
+    const int64_t trace = (int64_t)I.Nqf * I.nface;
+    LpPeView v;
+    v.nel = I.nel;
+    v.nface = I.nface;
+    v.n_up = I.n_up;
+    v.rows = I.rows;
+    v.elem_face = I.elem_face;
+    v.R = I.R32;
+    v.in = j == 0 ? I.R32 : I.d32 + (int64_t)((j - 1) & 1) * trace;
+    v.out = I.d32 + (int64_t)(j & 1) * trace;
+    const int64_t tile = w - pre[k];
+    switch (nq) {
+      case 8: lp_pe_tile<8>(v, smf, tile); break;
+      case 12: lp_pe_tile<12>(v, smf, tile); break;
+      case 16: lp_pe_tile<16>(v, smf, tile); break;
+      case 20: lp_pe_tile<20>(v, smf, tile); break;
+      case 24: lp_pe_tile<24>(v, smf, tile); break;
+      default: lp_pe_tile<28>(v, smf, tile); break;
+    }
   }
 }
 
@@ -742,8 +792,9 @@ bool batch_loop_ok(const Ctx& c) {
   const bool nq_ok = c.NQFS == 8 || c.NQFS == 12 || c.NQFS == 16 || c.NQFS == 20 ||
                      c.NQFS == 24 || c.NQFS == 28;
   const bool prec_ok = c.precision == EHDG_FP64 || c.precision == EHDG_MIXED_TF32 ||
-                       c.precision == EHDG_MIXED_BF16;
-  return c.use_pe && !c.use_ozaki && nq_ok && prec_ok && (!c.mixed || tc_supported(c));
+                       c.precision == EHDG_MIXED_BF16 || c.precision == EHDG_MIXED_FP32;
+  return c.use_pe && !c.use_ozaki && nq_ok && prec_ok &&
+         (c.precision == EHDG_FP64 || c.precision == EHDG_MIXED_FP32 || tc_supported(c));
 }
 
 struct BatchLoop::Impl {
@@ -758,7 +809,10 @@ struct BatchLoop::Impl {
   size_t step_smem = 0, final_smem = 0;
   unsigned int* d_ticket = nullptr;
   int n_inst = 0, n_sweep = 0, n_tc = 0, n_apply = 0, max_m = 0;
+  bool any_mma = false, any_fp32 = false;   // mixed instances with each kind of correction
   int sweep_grid = 1, tc_grid = 1, apply_grid = 1, tc_ncols = 32, tc_smem_b = 0, tc_smem_a = 0;
+  int lp_grid = 1;
+  size_t lp_smem = 0;
   size_t sweep_smem = 0, tc_smem = 0;
 };
 
@@ -850,19 +904,25 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     L.n_sweep += I.n_tiles_pe;
     if (c.mixed) {
       I.tc = 1;
+      I.mma = c.precision != EHDG_MIXED_FP32 ? 1 : 0;
       I.bf16 = c.precision == EHDG_MIXED_BF16 ? 1 : 0;
       I.m = c.inner_sweeps;
-      const int kstep = I.bf16 ? 16 : 8;
-      I.Kp = (c.NQFS + kstep - 1) / kstep * kstep;
-      I.Np = std::max(16, (c.n_rows + 15) / 16 * 16);
-      I.idesc = umma_idesc(I.bf16 ? 1u : 2u, kBTcM, I.Np);
       I.Hy32 = c.Hy32;
       I.R32 = c.R32;
       I.d32 = c.d32;
       I.Y32 = c.Y32;
       L.max_m = std::max(L.max_m, I.m);
-      max_kp_bytes = std::max(max_kp_bytes, I.Kp * (I.bf16 ? 2 : 4));
-      max_np = std::max(max_np, I.Np);
+      if (I.mma) {
+        const int kstep = I.bf16 ? 16 : 8;
+        I.Kp = (c.NQFS + kstep - 1) / kstep * kstep;
+        I.Np = std::max(16, (c.n_rows + 15) / 16 * 16);
+        I.idesc = umma_idesc(I.bf16 ? 1u : 2u, kBTcM, I.Np);
+        max_kp_bytes = std::max(max_kp_bytes, I.Kp * (I.bf16 ? 2 : 4));
+        max_np = std::max(max_np, I.Np);
+        L.any_mma = true;
+      } else {
+        L.any_fp32 = true;
+      }
       I.n_tiles128 = (int)((c.nel + kBTcM - 1) / kBTcM);
       const int64_t total = (int64_t)c.Nqf * c.nface;
       I.n_chunks = (int)((total + kApplyChunk - 1) / kApplyChunk);
@@ -889,7 +949,7 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     std::vector<size_t> off(L.n_inst, 0), roff(L.n_inst, 0);
     size_t bytes = 0;
     for (int i = 0; i < L.n_inst; ++i) {
-      if (!h[i].tc) continue;
+      if (!h[i].mma) continue;
       off[i] = bytes;
       bytes += ((size_t)h[i].Np * h[i].Kp * (h[i].bf16 ? 2 : 4) + 255) / 256 * 256;
       roff[i] = bytes;
@@ -898,7 +958,7 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     if (bytes > 0) {
       if ((e = cudaMalloc(&L.d_bimg, bytes)) != cudaSuccess) return e;
       for (int i = 0; i < L.n_inst; ++i) {
-        if (!h[i].tc) continue;
+        if (!h[i].mma) continue;
         const Ctx& c = *ctxs[i];
         k_batch_bimg<<<1, 256>>>(c.Hy32, c.rows, c.n_rows, c.NQFS, c.Nqf, h[i].Np, h[i].Kp,
                                  h[i].bf16, L.d_bimg + off[i],
@@ -945,7 +1005,14 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
   L.step_grid = wave(k_batch_step, 32 * kStepT, L.step_smem, L.n32);
   L.final_grid = wave(k_batch_final, 32 * kStepT, L.final_smem, L.n32);
   L.chunk_grid = std::max(1, std::min(device_sms() * 8, L.nch));
-  if (L.n_tc) {
+  if (L.any_fp32) {
+    for (int i = 0; i < L.n_inst; ++i)
+      if (h[i].tc && !h[i].mma)
+        L.lp_smem = std::max(L.lp_smem, sizeof(float) * (size_t)h[i].n_up * h[i].NQFS);
+    L.lp_grid = wave(k_batch_lp, kPeTile, L.lp_smem, L.n_tc);
+    L.apply_grid = std::max(1, std::min(device_sms() * 8, L.n_apply));
+  }
+  if (L.any_mma) {
     // B: the largest instance's padded rows x K; A: 128 x K
     L.tc_smem_b = (max_np * max_kp_bytes + 1023) / 1024 * 1024;
     L.tc_smem_a = (kBTcM * max_kp_bytes + 15) / 16 * 16;
@@ -1002,9 +1069,15 @@ cudaError_t BatchLoop::launch_body(cudaStream_t s, cudaGraphConditionalHandle ha
   Impl& L = *impl;
   cudaError_t e = cudaSuccess;
   for (int j = 0; j < L.max_m && L.n_tc; ++j) {
-    k_batch_tc<<<L.tc_grid, kBTcThreads, L.tc_smem, s>>>(L.d_inst, L.d_lists, L.n_inst, j,
-                                                        L.tc_ncols, L.tc_smem_b, L.tc_smem_a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (L.any_mma) {
+      k_batch_tc<<<L.tc_grid, kBTcThreads, L.tc_smem, s>>>(L.d_inst, L.d_lists, L.n_inst, j,
+                                                          L.tc_ncols, L.tc_smem_b, L.tc_smem_a);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (L.any_fp32) {
+      k_batch_lp<<<L.lp_grid, kPeTile, L.lp_smem, s>>>(L.d_inst, L.d_lists, L.n_inst, j);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
   }
   if (L.n_apply) {
     k_batch_apply<<<L.apply_grid, 256, 0, s>>>(L.d_inst, L.d_lists, L.n_inst);
@@ -1067,13 +1140,20 @@ cudaError_t BatchLoop::run_step_profiled(cudaStream_t s, int max_iter, double* m
     if ((e = cudaMemcpy(&n_active, L.d_lists, sizeof(int), cudaMemcpyDeviceToHost)) !=
         cudaSuccess || n_active == 0)
       break;
-    for (int j = 0; j < L.max_m && L.n_tc && e == cudaSuccess; ++j)
-      e = timed(EHDG_KERNEL_CORR, [&] {
-        k_batch_tc<<<L.tc_grid, kBTcThreads, L.tc_smem, s>>>(L.d_inst, L.d_lists, L.n_inst, j,
-                                                            L.tc_ncols, L.tc_smem_b,
-                                                            L.tc_smem_a);
-        return cudaGetLastError();
-      });
+    for (int j = 0; j < L.max_m && L.n_tc && e == cudaSuccess; ++j) {
+      if (L.any_mma)
+        e = timed(EHDG_KERNEL_CORR, [&] {
+          k_batch_tc<<<L.tc_grid, kBTcThreads, L.tc_smem, s>>>(L.d_inst, L.d_lists, L.n_inst,
+                                                              j, L.tc_ncols, L.tc_smem_b,
+                                                              L.tc_smem_a);
+          return cudaGetLastError();
+        });
+      if (L.any_fp32 && e == cudaSuccess)
+        e = timed(EHDG_KERNEL_CORR, [&] {
+          k_batch_lp<<<L.lp_grid, kPeTile, L.lp_smem, s>>>(L.d_inst, L.d_lists, L.n_inst, j);
+          return cudaGetLastError();
+        });
+    }
     if (L.n_apply && e == cudaSuccess)
       e = timed(EHDG_KERNEL_AUX, [&] {
         k_batch_apply<<<L.apply_grid, 256, 0, s>>>(L.d_inst, L.d_lists, L.n_inst);

@@ -232,6 +232,7 @@ cudaError_t launch_final_sf(Ctx& c);
 // one-thread-per-element 2D transport sweep (sweep_pe.cu)
 bool pe_supported(const Ctx& c);
 cudaError_t launch_sweep_pe(Ctx& c, int graph_mode, int* grid_out);
+cudaError_t launch_lp_sweep_pe(Ctx& c, const float* in, float* out);   // FP32 corrections
 // fused transport sweep (sweep_fused.cu)
 cudaError_t launch_sweep_fused(Ctx& c, int graph_mode);
 size_t fused_sweep_smem(const Ctx& c);   // dynamic shared memory of the fused sweep

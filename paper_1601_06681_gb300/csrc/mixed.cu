@@ -262,6 +262,7 @@ cudaError_t launch_lp_sweep(Ctx& c, const float* in, float* out) {
     }
     return err;
   }
+  if (c.use_pe) return launch_lp_sweep_pe(c, in, out);   // FP32, one thread per element
   LpParams p;
   p.nel = c.nel;
   p.nface = c.nface;

@@ -130,4 +130,45 @@ __device__ __forceinline__ bool pe_tile(const PeView& v, const double* Hsh, cons
   return true;
 }
 
+// One 128-element tile of the FP32 correction sweep of mixed precision
+// (delta_out = R + S Hy delta_in at the owned points), same shapes, one
+// thread per element: the FP32 copy of the operator rows in Hsh32
+// [n_rows][NQ], one FMA chain per row.
+struct LpPeView {
+  int64_t nel, nface;
+  int n_up;
+  const int* rows;
+  const int32_t* elem_face;     // [4][nel]
+  const float* R;               // [Nqf][nface]
+  const float* in;
+  float* out;
+};
+
+template <int NQ>
+__device__ __forceinline__ void lp_pe_tile(const LpPeView& v, const float* Hsh32, int64_t tile) {
+  constexpr int NQF = NQ / 4;
+  const int64_t ne = v.nel, nface = v.nface;
+  const int64_t e = tile * kPeTile + threadIdx.x;
+  if (e >= ne) return;
+  float d[NQ];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const int64_t face = v.elem_face[f * ne + e];
+#pragma unroll
+    for (int g = 0; g < NQF; ++g) d[f * NQF + g] = v.in[g * nface + face];
+  }
+#pragma unroll
+  for (int j = 0; j < NQ; ++j) {
+    if (j >= v.n_up) break;
+    const float* Hr = Hsh32 + j * NQ;
+    float a = 0.f;
+#pragma unroll
+    for (int c = 0; c < NQ; ++c) a = fmaf(Hr[c], d[c], a);
+    const int r = v.rows[j];
+    const int f = r / NQF, g = r - f * NQF;
+    const int64_t pt = g * nface + v.elem_face[f * ne + e];
+    v.out[pt] = v.R[pt] + a;
+  }
+}
+
 }  // namespace ehdg

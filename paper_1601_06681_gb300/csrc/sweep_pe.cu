@@ -51,7 +51,57 @@ cudaError_t launch_pe_t(const PeView& v, const double* Hy, int graph_mode,
   return cudaGetLastError();
 }
 
+template <int NQ>
+__global__ void __launch_bounds__(kPeTile) k_lp_pe(const LpPeView v, const float* Hy32) {
+  __shared__ float Hsh[NQ * NQ];
+  for (int i = threadIdx.x; i < v.n_up * NQ; i += kPeTile) {
+    const int j = i / NQ, c = i - j * NQ;
+    Hsh[i] = Hy32[v.rows[j] * NQ + c];
+  }
+  __syncthreads();
+  const int64_t ntiles = (v.nel + kPeTile - 1) / kPeTile;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) lp_pe_tile<NQ>(v, Hsh, tile);
+}
+
+template <int NQ>
+cudaError_t launch_lp_pe_t(const LpPeView& v, const float* Hy32, cudaStream_t s) {
+  int bpsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_lp_pe<NQ>, kPeTile, 0) !=
+          cudaSuccess ||
+      bpsm < 1) {
+    cudaGetLastError();
+    bpsm = 1;
+  }
+  const int64_t ntiles = (v.nel + kPeTile - 1) / kPeTile;
+  int64_t grid = (int64_t)bpsm * device_sms();
+  if (grid > ntiles) grid = ntiles;
+  k_lp_pe<NQ><<<(int)grid, kPeTile, 0, s>>>(v, Hy32);
+  return cudaGetLastError();
+}
+
 }  // namespace
+
+// FP32 correction sweep, one thread per element (quadrilaterals, shared
+// operator, no beta.n = 0 point): every sweep row is an owned point.
+cudaError_t launch_lp_sweep_pe(Ctx& c, const float* in, float* out) {
+  LpPeView v;
+  v.nel = c.nel;
+  v.nface = c.nface;
+  v.n_up = c.n_up;
+  v.rows = c.rows;
+  v.elem_face = c.geo.elem_face;
+  v.R = c.R32;
+  v.in = in;
+  v.out = out;
+  switch (c.NQFS) {
+    case 8: return launch_lp_pe_t<8>(v, c.Hy32, c.stream);
+    case 12: return launch_lp_pe_t<12>(v, c.Hy32, c.stream);
+    case 16: return launch_lp_pe_t<16>(v, c.Hy32, c.stream);
+    case 20: return launch_lp_pe_t<20>(v, c.Hy32, c.stream);
+    case 24: return launch_lp_pe_t<24>(v, c.Hy32, c.stream);
+    default: return launch_lp_pe_t<28>(v, c.Hy32, c.stream);
+  }
+}
 
 bool pe_supported(const Ctx& c) {
   return c.pde == EHDG_TRANSPORT && c.dim == 2 && c.shared_op && !c.variable_beta &&
