@@ -973,6 +973,7 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
                         "count of the tiled sweep (quadrilaterals with 2..10 points per edge, "
                         "hexahedra with 2x2 or 3x3 per face)"));
   if (c.mixed) CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_hy_to_f32(c); }));
+  if (c.mixed) CKC(counted(c, EHDG_KERNEL_AUX, 1, [&] { return build_tc_image(c); }));
   if (want_ozaki) {
     if (!ozaki_supported(c))
       return cleanup(fail(EHDG_ERR_UNSUPPORTED,

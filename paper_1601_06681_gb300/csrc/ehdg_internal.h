@@ -134,6 +134,13 @@ struct Ctx {
   bool mixed = false;
   ehdg_precision precision = EHDG_FP64;
   int* tc_err = nullptr;         // set by a sweep whose bounded mbarrier wait gave up
+  // tensor-core correction sweep (TF32/BF16, shared operator): the sweep rows
+  // rounded into the K-major shared-memory image at setup and, for the
+  // fixed-shape form (rows are whole faces), the local face of each row face
+  void* tc_img = nullptr;
+  bool tc_fx = false;
+  int tc_nrf = 0, tc_nupf = 0;   // row faces; leading ones owned (upwind)
+  int tc_rfs[6] = {0, 0, 0, 0, 0, 0};
   // FP64-accurate products on the BF16 tensor cores (Ozaki splitting, shared
   // operator): the sweep (Hy rows), the reconstruction (H) and the step (P)
   bool use_ozaki = false;
@@ -239,6 +246,13 @@ size_t fused_sweep_smem(const Ctx& c);   // dynamic shared memory of the fused s
 int fused_sweep_grid(const Ctx& c);      // its grid = its residual partials
 int fused_grid(int64_t nel);      // upper bound of the fused sweep's grid
 int device_sms();
+// cached per kernel (and device): raise the dynamic shared-memory limit, set
+// the shared-memory carveout to 100, resident blocks per SM
+cudaError_t fn_smem(const void* fn, size_t bytes);
+cudaError_t fn_carveout(const void* fn);
+int fn_blocks_per_sm(const void* fn, int threads, size_t smem);
+// resident blocks per SM from the kernel's attributes and the device limits (0 on error)
+int fn_blocks_from_attrs(const void* fn, int threads, size_t smem);
 int tangent_grid(int64_t n_tan);
 void fill_face_weights(const Ctx& c, double* fw);   // face Gauss weight of each face point
 // tiled per-element transport sweep (sweep_tiled.cu)
@@ -271,6 +285,7 @@ cudaError_t dalloc_raw(Ctx& c, void** p, size_t bytes);   // device allocation o
 std::vector<std::pair<void*, size_t>> state_arrays(Ctx& c);
 // tensor-core correction sweep (tc_sweep.cu)
 bool tc_supported(const Ctx& c);
+cudaError_t build_tc_image(Ctx& c);   // after the FP32 operator copy
 cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out);
 
 // Batched iteration loop of a batch's looped instances (batch_loop.cu): one

@@ -77,13 +77,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 // One full wave of resident blocks, capped by the number of tiles.
 template <class K>
 int persistent_grid(K kernel, int threads, size_t smem, int64_t ntiles) {
-  int bpsm = 0;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, threads, smem) != cudaSuccess ||
-      bpsm < 1) {
-    cudaGetLastError();
-    bpsm = 1;
-  }
+  fn_carveout((const void*)kernel);
+  const int bpsm = fn_blocks_per_sm((const void*)kernel, threads, smem);
   int64_t g = (int64_t)bpsm * device_sms();
   if (g > ntiles) g = ntiles;
   return g < 1 ? 1 : (int)g;
@@ -484,7 +479,7 @@ cudaError_t launch_step(Ctx& c) {
     s.g_ready = 1;
   }
   const size_t smem = sizeof(double) * ((s.shared ? (size_t)c.n * c.n : 0) + 2 * (size_t)c.n * 32);
-  cudaError_t err = cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = fn_smem((const void*)k_step, smem);
   if (err != cudaSuccess) return err;
   const int grid = persistent_grid(k_step, 32 * kStepT, smem, (c.nel + 31) / 32);
   k_step<<<grid, dim3(32, kStepT), smem, c.stream>>>(s);
@@ -567,8 +562,7 @@ __global__ void __launch_bounds__(32 * kElemT) k_elem(const ElemParams p) {
 
 template <int NQ>
 static cudaError_t launch_elem_t(const ElemParams& p, size_t smem, int grid, cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(k_elem<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  cudaError_t err = fn_smem((const void*)k_elem<NQ>, smem);
   if (err != cudaSuccess) return err;
   k_elem<NQ><<<grid, dim3(32, kElemT), smem, s>>>(p);
   return cudaGetLastError();
@@ -881,7 +875,7 @@ cudaError_t launch_final(Ctx& c) {
   } else {
     const size_t smem =
         sizeof(double) * ((p.shared ? (size_t)c.n * c.NQFS : 0) + (size_t)c.NQFS * 32);
-    err = cudaFuncSetAttribute(k_final, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = fn_smem((const void*)k_final, smem);
     if (err != cudaSuccess) return err;
     const int grid = persistent_grid(k_final, 32 * kStepT, smem, (c.nel + 31) / 32);
     k_final<<<grid, dim3(32, kStepT), smem, c.stream>>>(p);

@@ -199,15 +199,9 @@ __global__ void k_to_f32(int64_t n, const double* src, float* dst) {
 
 template <int NQ>
 cudaError_t launch_lp_t(const LpParams& p, size_t smem, int64_t ntiles, cudaStream_t s) {
-  cudaError_t err = cudaFuncSetAttribute(k_sweep_lp<NQ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+  cudaError_t err = fn_smem((const void*)k_sweep_lp<NQ>, smem);
   if (err != cudaSuccess) return err;
-  int bpsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_sweep_lp<NQ>, 32 * kLT, smem) !=
-          cudaSuccess || bpsm < 1) {
-    cudaGetLastError();
-    bpsm = 1;
-  }
+  const int bpsm = fn_blocks_per_sm((const void*)k_sweep_lp<NQ>, 32 * kLT, smem);
   int64_t grid = (int64_t)bpsm * device_sms();     // one full wave, tiles strided
   if (grid > ntiles) grid = ntiles;
   k_sweep_lp<NQ><<<(int)grid, dim3(32, kLT), smem, s>>>(p);

@@ -11,6 +11,11 @@
 // for its own solve.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "ehdg_internal.h"
 #include "fused_tile.cuh"
 #include "sweep_common.cuh"
@@ -248,16 +253,101 @@ int device_sms() {
   return nsm;
 }
 
+// Function attributes and occupancy are set or queried once per kernel and
+// size, not per launch: they cost host time on every call (which also shows
+// in the per-launch event timings of host-driven steps), the dynamic
+// shared-memory limit is only ever raised (a lower limit would invalidate
+// launches captured into graphs with a higher one), and the carveout is set
+// once.
+namespace {
+std::mutex g_fn_mu;
+std::map<std::pair<int, const void*>, size_t> g_fn_smem;
+std::map<std::pair<int, const void*>, bool> g_fn_carve;
+std::map<std::tuple<int, const void*, int, size_t>, int> g_fn_occ;
+int cur_device() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return dev;
+}
+}  // namespace
+
+cudaError_t fn_smem(const void* fn, size_t bytes) {
+  const auto key = std::make_pair(cur_device(), fn);
+  std::lock_guard<std::mutex> lk(g_fn_mu);
+  auto it = g_fn_smem.find(key);
+  if (it != g_fn_smem.end() && it->second >= bytes) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) g_fn_smem[key] = bytes;
+  return e;
+}
+
+cudaError_t fn_carveout(const void* fn) {
+  const auto key = std::make_pair(cur_device(), fn);
+  std::lock_guard<std::mutex> lk(g_fn_mu);
+  if (g_fn_carve.count(key)) return cudaSuccess;
+  const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  if (e == cudaSuccess) g_fn_carve[key] = true;
+  return e;
+}
+
+// Resident blocks per SM from the kernel's registers and shared memory and the
+// device's per-SM limits (registers allocated per warp in units of 256).
+static int blocks_from_attrs(const void* fn, int threads, size_t smem) {
+  cudaFuncAttributes fa;
+  int dev = 0, regs_sm = 0, thr_sm = 0, smem_sm = 0, smem_rsv = 0, blk_sm = 0;
+  if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&thr_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev) !=
+          cudaSuccess ||
+      cudaDeviceGetAttribute(&blk_sm, cudaDevAttrMaxBlocksPerMultiprocessor, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int warps = (threads + 31) / 32;
+  const int regs_warp = ((fa.numRegs > 0 ? fa.numRegs : 1) * 32 + 255) / 256 * 256;
+  int b = blk_sm;
+  b = std::min(b, (regs_sm / regs_warp) / warps);
+  b = std::min(b, thr_sm / (warps * 32));
+  const size_t per_block = smem + fa.sharedSizeBytes + (size_t)smem_rsv;
+  if (per_block > 0) b = std::min<int>(b, (int)((size_t)smem_sm / per_block));
+  return b;
+}
+
+int fn_blocks_from_attrs(const void* fn, int threads, size_t smem) {
+  static std::map<std::tuple<int, const void*, int, size_t>, int> cache;
+  const auto key = std::make_tuple(cur_device(), fn, threads, smem);
+  std::lock_guard<std::mutex> lk(g_fn_mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  const int b = blocks_from_attrs(fn, threads, smem);
+  if (b > 0) cache[key] = b;
+  return b;
+}
+
+int fn_blocks_per_sm(const void* fn, int threads, size_t smem) {
+  const auto key = std::make_tuple(cur_device(), fn, threads, smem);
+  std::lock_guard<std::mutex> lk(g_fn_mu);
+  auto it = g_fn_occ.find(key);
+  if (it != g_fn_occ.end()) return it->second;
+  int bpsm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, fn, threads, smem) != cudaSuccess ||
+      bpsm < 1) {
+    cudaGetLastError();
+    return 1;                    // not cached: a later call may succeed
+  }
+  g_fn_occ[key] = bpsm;
+  return bpsm;
+}
+
 // Persistent grid: one full wave of resident blocks (no partial last wave),
 // capped by the number of 32-element tiles and by `cap`.
 template <class K>
 int one_wave_grid(K kernel, int threads, size_t smem, int64_t ntiles, int cap) {
-  int bpsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, threads, smem) != cudaSuccess ||
-      bpsm < 1) {
-    cudaGetLastError();
-    bpsm = 1;
-  }
+  const int bpsm = fn_blocks_per_sm((const void*)kernel, threads, smem);
   int64_t g = (int64_t)bpsm * device_sms();
   if (g > ntiles) g = ntiles;
   if (g > cap) g = cap;
@@ -267,8 +357,7 @@ int one_wave_grid(K kernel, int threads, size_t smem, int64_t ntiles, int cap) {
 template <int NQ, int FT>
 static cudaError_t launch_fused_ft(const FusedParams& p, size_t smem, int64_t ntiles,
                                    cudaStream_t s, int* grid_out) {
-  cudaError_t err = cudaFuncSetAttribute(k_sweep_fused<NQ, FT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = fn_smem((const void*)k_sweep_fused<NQ, FT>, smem);
   if (err != cudaSuccess) return err;
   const int grid = one_wave_grid(k_sweep_fused<NQ, FT>, 32 * FT, smem, ntiles, kFusedMaxBlocks);
   *grid_out = grid;

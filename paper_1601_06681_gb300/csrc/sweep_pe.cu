@@ -36,13 +36,7 @@ __global__ void __launch_bounds__(kPeTile) k_sweep_pe(const __grid_constant__ Pe
 template <int NQ>
 cudaError_t launch_pe_t(const PeView& v, const double* Hy, int graph_mode,
                         cudaGraphConditionalHandle handle, cudaStream_t s, int* grid_out) {
-  int bpsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_sweep_pe<NQ>, kPeTile, 0) !=
-          cudaSuccess ||
-      bpsm < 1) {
-    cudaGetLastError();
-    bpsm = 1;
-  }
+  const int bpsm = fn_blocks_per_sm((const void*)k_sweep_pe<NQ>, kPeTile, 0);
   const int64_t ntiles = (v.nel + kPeTile - 1) / kPeTile;
   int64_t grid = (int64_t)bpsm * device_sms();
   if (grid > ntiles) grid = ntiles;
@@ -65,13 +59,7 @@ __global__ void __launch_bounds__(kPeTile) k_lp_pe(const LpPeView v, const float
 
 template <int NQ>
 cudaError_t launch_lp_pe_t(const LpPeView& v, const float* Hy32, cudaStream_t s) {
-  int bpsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, k_lp_pe<NQ>, kPeTile, 0) !=
-          cudaSuccess ||
-      bpsm < 1) {
-    cudaGetLastError();
-    bpsm = 1;
-  }
+  const int bpsm = fn_blocks_per_sm((const void*)k_lp_pe<NQ>, kPeTile, 0);
   const int64_t ntiles = (v.nel + kPeTile - 1) / kPeTile;
   int64_t grid = (int64_t)bpsm * device_sms();
   if (grid > ntiles) grid = ntiles;

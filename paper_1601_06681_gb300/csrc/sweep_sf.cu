@@ -266,12 +266,7 @@ SfParams sf_params(const Ctx& c) {
 
 template <class K>
 int sf_grid(K kernel, int threads, size_t smem, int64_t ntiles) {
-  int bpsm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bpsm, kernel, threads, smem) != cudaSuccess ||
-      bpsm < 1) {
-    cudaGetLastError();
-    bpsm = 1;
-  }
+  const int bpsm = fn_blocks_per_sm((const void*)kernel, threads, smem);
   int64_t g = (int64_t)bpsm * device_sms();
   if (g > ntiles) g = ntiles;
   if (g > kSfMaxBlocks) g = kSfMaxBlocks;
@@ -284,8 +279,7 @@ cudaError_t launch_sweep_sf_t(const SfParams& p, cudaStream_t s, int* grid_out) 
   constexpr int NB = P1 * P1 * P1 - (P1 - 2) * (P1 - 2) * (P1 - 2);
   const size_t smem = sizeof(double) * ((size_t)p.n_rows * NB + 2 * NQ * 32) +
                       sizeof(int) * 6 * 32;
-  cudaError_t err = cudaFuncSetAttribute(k_sweep_sf<P1, FT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = fn_smem((const void*)k_sweep_sf<P1, FT>, smem);
   if (err != cudaSuccess) return err;
   const int grid = sf_grid(k_sweep_sf<P1, FT>, 32 * FT, smem, (p.nel + 31) / 32);
   *grid_out = grid;
@@ -308,8 +302,7 @@ cudaError_t launch_final_sf_t(const SfParams& p, cudaStream_t s) {
   constexpr int NQ = 6 * P1 * P1;
   constexpr int NB = P1 * P1 * P1 - (P1 - 2) * (P1 - 2) * (P1 - 2);
   const size_t smem = sizeof(double) * ((size_t)p.n * NB + 2 * NQ * 32);
-  cudaError_t err = cudaFuncSetAttribute(k_final_sf<P1, FT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = fn_smem((const void*)k_final_sf<P1, FT>, smem);
   if (err != cudaSuccess) return err;
   const int grid = sf_grid(k_final_sf<P1, FT>, 32 * FT, smem, (p.nel + 31) / 32);
   k_final_sf<P1, FT><<<grid, dim3(32, FT), smem, s>>>(p);

@@ -10,6 +10,8 @@
 // apart (LBO) and 8-row groups (K bytes / 16) * 128 bytes apart (SBO).
 // One thread issues the MMAs and commits them to an mbarrier; every wait on
 // the mbarrier is bounded and records an error instead of hanging.
+#include <algorithm>
+
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -74,47 +76,12 @@ __device__ __forceinline__ void store_elem(unsigned char* base, int row, int k, 
   }
 }
 
-// A's half H (K range [H Kp/2, (H+1) Kp/2)) of one element, when the faces F_
-// and face points NQF are compile-time constants: after unrolling, every face
-// and point index below is a constant, so each value costs one load from a
-// register face id plus a constant point offset.
-template <int F_, int NQF, int BF16, int H>
-__device__ __forceinline__ void tc_gather_fixed(unsigned char* As, uint32_t rowoff,
-                                                const float* in, const int* fid, int row,
-                                                int64_t nface, bool live) {
-  constexpr int NQFS = F_ * NQF;
-  constexpr int KSTEP = BF16 ? 16 : 8;                 // elements per 32-byte MMA K step
-  constexpr int KP = (NQFS + KSTEP - 1) / KSTEP * KSTEP;
-  constexpr int KHALF = KP / 2;
-  constexpr int K0 = H * KHALF;
-  constexpr int CH = BF16 ? 8 : 4;                     // values per 16-byte chunk
-  constexpr int F0 = K0 / NQF;
-  constexpr int NF = (K0 + KHALF - 1) / NQF - F0 + 1;  // faces this half touches
-  static_assert(KHALF % CH == 0, "whole chunks per half");
-  int fr[NF];
-#pragma unroll
-  for (int m = 0; m < NF; ++m) fr[m] = (live && F0 + m < F_) ? fid[(F0 + m) * kTcM + row] : 0;
-#pragma unroll
-  for (int c = 0; c < KHALF / CH; ++c) {
-    float v[CH];
-#pragma unroll
-    for (int q = 0; q < CH; ++q) {
-      const int k = K0 + c * CH + q;
-      const int f = k / NQF, g = k - (k / NQF) * NQF;
-      v[q] = (live && k < NQFS) ? in[(int64_t)g * nface + fr[f - F0]] : 0.f;
-    }
-    store_chunk(As + rowoff + (uint32_t)((K0 + c * CH) / CH) * 128u, v, CH, BF16);
-  }
-}
-
-// F_, NQF > 0: faces and face points per face known at compile time, with
-// BF16 the operand format; F_ = NQF = 0: the general form (format from p.bf16).
-template <int F_, int NQF, int BF16>
+// The general form: any face shape and row set (format from p.bf16).
 __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_base;
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, warp = tid >> 5;
   const int row = tid & (kTcM - 1), half = tid >> 7;   // tile row (element) and K / N half
   const int esize = p.bf16 ? 2 : 4;
   const uint32_t kbytes = (uint32_t)p.Kp * esize;
@@ -165,13 +132,7 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
     if (e < ne)
       for (int f = half; f < p.F; f += 2) fid[f * kTcM + row] = p.elem_face[f * ne + e];
     __syncthreads();
-    if constexpr (NQF > 0) {
-      const uint32_t rowoff = (uint32_t)(row >> 3) * sbo + (uint32_t)(row & 7) * 16u;
-      if (half == 0)
-        tc_gather_fixed<F_, NQF, BF16, 0>(As, rowoff, p.in, fid, row, nface, e < ne);
-      else
-        tc_gather_fixed<F_, NQF, BF16, 1>(As, rowoff, p.in, fid, row, nface, e < ne);
-    } else {
+    {
       const uint32_t rowoff = (uint32_t)(row >> 3) * sbo + (uint32_t)(row & 7) * 16u;
       const int khalf = p.Kp / 2;                        // a multiple of the chunk size
       const int kbeg = half * khalf, kend = kbeg + khalf;
@@ -299,33 +260,352 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
                  "r"(p.ncols));
 }
 
-// The kernel of a face shape: quadrilaterals with 2..7 points per edge and
-// hexahedra with 2x2, 3x3 or 4x4 points per face have a compile-time form.
-using TcKernel = void (*)(const TcParams);
-template <int F_, int NQF>
-TcKernel tc_pick(int bf16) {
-  return bf16 ? k_sweep_tc<F_, NQF, 1> : k_sweep_tc<F_, NQF, 0>;
+// ---------------------------------------------------------------------------
+// Fixed-shape form. Faces F_ and points per face NQF are compile-time
+// constants, and the sweep rows are whole faces (a constant velocity: every
+// point of a face is upwind, or every point tangential), listed face by face.
+// Per tile, each thread loads its element's face ids (the next tile's are
+// prefetched), gathers its half of the K range with 32-bit point indices and
+// loads the residual R at its owned points before the MMA; the epilogue then
+// only reads TMEM, adds and stores. The operator rows come rounded, in the
+// shared-memory image, from setup. The MMAs (operands, K steps, descriptors)
+// are those of the general form, so both give the same values bit for bit.
+
+struct TcFxParams {
+  int64_t nel;
+  uint32_t nface;
+  int n_rf, n_up_f;             // row faces; leading ones the element owns (owner writes)
+  int rfs[6];                   // local face of each row face
+  int Np, ncols;
+  uint32_t idesc;
+  const int32_t* elem_face;     // [F][nel]
+  const uint4* img;             // Np x Kp operator image (K-major, no swizzle)
+  const float* R;
+  const float* in;
+  float* out;
+  float* Y32;
+  int* err;
+};
+
+template <int F_>
+__device__ __forceinline__ int fx_pick(const int (&fid)[F_], int s) {
+  int r = fid[0];
+#pragma unroll
+  for (int k = 1; k < F_; ++k) r = (s == k) ? fid[k] : r;
+  return r;
 }
-TcKernel tc_kernel(int F, int Nqf, int bf16) {
+
+// Compile-time shape of the fixed form: TPE threads per element (tile row),
+// thread part q gathering K range [q KP/TPE, (q+1) KP/TPE) and owning points
+// [q NQF/TPE, (q+1) NQF/TPE) of every row face in the epilogue (the last part
+// takes the remainder).
+template <int F_, int NQF, int BF16, int TPE>
+struct FxShape {
+  static constexpr int NQFS = F_ * NQF;
+  static constexpr int KSTEP = BF16 ? 16 : 8;          // elements per 32-byte MMA K step
+  static constexpr int KP = (NQFS + KSTEP - 1) / KSTEP * KSTEP;
+  static constexpr uint32_t KBYTES = KP * (BF16 ? 2 : 4);
+  static constexpr uint32_t SBO = KBYTES * 8u;
+  static constexpr int CH = BF16 ? 8 : 4;              // values per 16-byte chunk
+  static constexpr int KQ = KP / TPE;                  // K values a part gathers
+  static constexpr int GQ = NQF / TPE;                 // epilogue points of parts 0..TPE-2
+  static constexpr int GL = NQF - (TPE - 1) * GQ;      // ... and of the last part
+  static constexpr int NUP = F_ / 2;                   // at most one outflow face per axis
+  static constexpr int THREADS = 128 * TPE;
+  static_assert(KQ % CH == 0, "whole chunks per part");
+  static_assert(GQ >= 1, "every part owns points");
+};
+
+// GN consecutive accumulator columns of the warp's 32 lanes: one x8 load when
+// GN = 8 at an 8-aligned column, else one x1 load per column
+template <int GN, bool WIDE>
+__device__ __forceinline__ void fx_tmem_ld(uint32_t taddr, uint32_t (&v)[GN]) {
+  if constexpr (WIDE) {
+    static_assert(GN == 8, "x8 load");
+    tmem_ld8(taddr, v);
+  } else {
+#pragma unroll
+    for (int q = 0; q < GN; ++q)
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];"
+                   : "=r"(v[q])
+                   : "r"(taddr + (uint32_t)q));
+  }
+}
+
+// Thread part Q of element `row`: gathers its K range into registers (all
+// loads first), rounds and stores it into A; loads R at its owned points;
+// after the MMA, writes its points of every row face.
+template <int F_, int NQF, int BF16, int TPE, int Q>
+__device__ __forceinline__ void fx_tile(const TcFxParams& p, unsigned char* As, unsigned char* Bs,
+                                        uint64_t* mbar, uint32_t tbase, uint32_t& phase,
+                                        bool& failed, int64_t tile, const int (&fid)[F_]) {
+  using S = FxShape<F_, NQF, BF16, TPE>;
+  constexpr int G0 = Q * S::GQ;                        // first point of this part
+  constexpr int GN = (Q == TPE - 1) ? S::GL : S::GQ;   // points of this part
+  constexpr bool WIDE = GN == 8 && (G0 % 8) == 0;
+  constexpr int NUP = S::NUP;
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTcM - 1);
+  const int64_t ne = p.nel;
+  const int64_t e = tile * kTcM + row;
+  const bool live = e < ne;
+  const uint32_t nface = p.nface;
+  // every load of the tile first: R at the owned points, then the K range
+  float rv[NUP][GN];
+  int fo[NUP];
+#pragma unroll
+  for (int i = 0; i < NUP; ++i) {
+    fo[i] = fx_pick<F_>(fid, p.rfs[i]);
+#pragma unroll
+    for (int q = 0; q < GN; ++q)
+      rv[i][q] = i < p.n_up_f ? __ldg(p.R + ((uint32_t)(G0 + q) * nface + (uint32_t)fo[i])) : 0.f;
+  }
+  float v[S::KQ];
+#pragma unroll
+  for (int j = 0; j < S::KQ; ++j) {
+    const int k = Q * S::KQ + j;
+    const int f = k / NQF, g = k - (k / NQF) * NQF;
+    v[j] = k < S::NQFS ? __ldg(p.in + ((uint32_t)g * nface + (uint32_t)fid[f < F_ ? f : 0])) : 0.f;
+  }
+  unsigned char* Arow = As + (uint32_t)(row >> 3) * S::SBO + (uint32_t)(row & 7) * 16u;
+#pragma unroll
+  for (int c = 0; c < S::KQ / S::CH; ++c) {
+    unsigned char* dst = Arow + (uint32_t)(Q * S::KQ / S::CH + c) * 128u;
+    const float* w = v + c * S::CH;
+    if constexpr (BF16) {
+      uint32_t u[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const __nv_bfloat162 b = __floats2bfloat162_rn(w[2 * h], w[2 * h + 1]);
+        u[h] = *reinterpret_cast<const uint32_t*>(&b);
+      }
+      *reinterpret_cast<uint4*>(dst) = make_uint4(u[0], u[1], u[2], u[3]);
+    } else {
+      *reinterpret_cast<uint4*>(dst) =
+          make_uint4(to_tf32(w[0]), to_tf32(w[1]), to_tf32(w[2]), to_tf32(w[3]));
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (tid == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+    for (int s = 0; s < (int)(S::KBYTES / 32u); ++s) {
+      const uint64_t ad = umma_desc(a0 + 256u * s, 128u, S::SBO);
+      const uint64_t bd = umma_desc(b0 + 256u * s, 128u, S::SBO);
+      const uint32_t acc = s > 0 ? 1u : 0u;
+      if constexpr (BF16) {
+        asm volatile(
+            "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, q;\n}\n" ::"r"(tbase),
+            "l"(ad), "l"(bd), "r"(p.idesc), "r"(acc));
+      } else {
+        asm volatile(
+            "{\n .reg .pred q;\n setp.ne.b32 q, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, q;\n}\n" ::"r"(tbase),
+            "l"(ad), "l"(bd), "r"(p.idesc), "r"(acc));
+      }
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(mbar)));
+  }
+  uint32_t ok = 1;
+  if (tid == 0) ok = mbar_wait_bounded(mbar, phase, kWaitLimit) ? 1u : 0u;
+  if (__syncthreads_or(ok ? 0 : 1)) {
+    if (tid == 0) atomicExch(p.err, 1);
+    failed = true;
+    return;
+  }
+  phase ^= 1u;
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tl = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)G0;
+  // owned row faces: the new correction at the element's outflow points
+#pragma unroll
+  for (int i = 0; i < NUP; ++i) {
+    if (i >= p.n_up_f) break;
+    uint32_t a[GN];
+    fx_tmem_ld<GN, WIDE>(tl + (uint32_t)(i * NQF), a);
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    if (live) {
+#pragma unroll
+      for (int q = 0; q < GN; ++q)
+        p.out[(uint32_t)(G0 + q) * nface + (uint32_t)fo[i]] = rv[i][q] + __uint_as_float(a[q]);
+    }
+  }
+  // the other row faces (tangential points; every face for shallow water)
+  for (int i = p.n_up_f; i < p.n_rf; ++i) {
+    uint32_t a[GN];
+    fx_tmem_ld<GN, WIDE>(tl + (uint32_t)(i * NQF), a);
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    if (live) {
+      const int sl = p.rfs[i];
+#pragma unroll
+      for (int q = 0; q < GN; ++q)
+        p.Y32[(int64_t)(sl * NQF + G0 + q) * ne + e] = __uint_as_float(a[q]);
+    }
+  }
+}
+
+template <int F_, int NQF, int BF16, int TPE>
+__global__ void __launch_bounds__(128 * TPE)
+    k_sweep_tc_fx(const __grid_constant__ TcFxParams p) {
+  using S = FxShape<F_, NQF, BF16, TPE>;
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, row = tid & (kTcM - 1), part = tid >> 7;
+  unsigned char* Bs = sm;                                   // Np x Kp
+  unsigned char* As = sm + (size_t)p.Np * S::KBYTES;        // 128 x Kp
+  {
+    const int n16 = (int)((uint32_t)p.Np * S::KBYTES / 16u);
+    for (int i = tid; i < n16; i += S::THREADS) reinterpret_cast<uint4*>(Bs)[i] = p.img[i];
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_base)),
+                 "r"(p.ncols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tbase = tmem_base;
+  const int64_t ne = p.nel;
+  const int64_t ntiles = (ne + kTcM - 1) / kTcM;
+  uint32_t phase = 0;
+  bool failed = false;
+  // face ids of this block's first tile; each tile prefetches the next one's
+  int fn[F_];
+  {
+    const int64_t e = (int64_t)blockIdx.x * kTcM + row;
+#pragma unroll
+    for (int f = 0; f < F_; ++f) fn[f] = e < ne ? p.elem_face[f * ne + e] : 0;
+  }
+  for (int64_t tile = blockIdx.x; tile < ntiles && !failed; tile += gridDim.x) {
+    int fid[F_];
+#pragma unroll
+    for (int f = 0; f < F_; ++f) fid[f] = fn[f];
+    const int64_t e2 = (tile + gridDim.x) * kTcM + row;
+#pragma unroll
+    for (int f = 0; f < F_; ++f) fn[f] = e2 < ne ? p.elem_face[f * ne + e2] : 0;
+    // parts are warp-uniform (128 threads each)
+    if (part == 0) {
+      fx_tile<F_, NQF, BF16, TPE, 0>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
+    } else if constexpr (TPE == 2) {
+      fx_tile<F_, NQF, BF16, TPE, 1>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
+    } else {
+      if (part == 1)
+        fx_tile<F_, NQF, BF16, TPE, 1>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
+      else if (part == 2)
+        fx_tile<F_, NQF, BF16, TPE, 2>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
+      else
+        fx_tile<F_, NQF, BF16, TPE, 3>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
+    }
+    // every thread's TMEM reads of this tile precede the next tile's MMA
+    asm volatile("tcgen05.fence::before_thread_sync;");
+  }
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
+                 "r"(p.ncols));
+}
+
+struct FxKernel {
+  void (*fn)(const TcFxParams) = nullptr;
+  int threads = 0;
+};
+// TPE = WANT where each part's K range is whole 16-byte chunks, else 2
+constexpr int fx_tpe(int F_, int NQF, int BF16, int WANT) {
+  const int kstep = BF16 ? 16 : 8, ch = BF16 ? 8 : 4;
+  const int kp = (F_ * NQF + kstep - 1) / kstep * kstep;
+  return ((kp / WANT) % ch == 0 && NQF >= WANT) ? WANT : 2;
+}
+template <int F_, int NQF, int TPE>
+FxKernel fx_pick_kernel(int bf16) {
+  constexpr int T0 = fx_tpe(F_, NQF, 0, TPE), T1 = fx_tpe(F_, NQF, 1, TPE);
+  FxKernel k;
+  k.fn = bf16 ? k_sweep_tc_fx<F_, NQF, 1, T1> : k_sweep_tc_fx<F_, NQF, 0, T0>;
+  k.threads = 128 * (bf16 ? T1 : T0);
+  return k;
+}
+// quadrilaterals with 2..7 points per edge, hexahedra with 2x2, 3x3, 4x4 per
+// face; two threads per element (four measured slower at 64^3, p = 3: one
+// block of 512 threads per SM at 64 registers against three of 256)
+FxKernel fx_kernel(int F, int Nqf, int bf16) {
   if (F == 4) {
     switch (Nqf) {
-      case 2: return tc_pick<4, 2>(bf16);
-      case 3: return tc_pick<4, 3>(bf16);
-      case 4: return tc_pick<4, 4>(bf16);
-      case 5: return tc_pick<4, 5>(bf16);
-      case 6: return tc_pick<4, 6>(bf16);
-      case 7: return tc_pick<4, 7>(bf16);
+      case 2: return fx_pick_kernel<4, 2, 2>(bf16);
+      case 3: return fx_pick_kernel<4, 3, 2>(bf16);
+      case 4: return fx_pick_kernel<4, 4, 2>(bf16);
+      case 5: return fx_pick_kernel<4, 5, 2>(bf16);
+      case 6: return fx_pick_kernel<4, 6, 2>(bf16);
+      case 7: return fx_pick_kernel<4, 7, 2>(bf16);
       default: break;
     }
   } else if (F == 6) {
     switch (Nqf) {
-      case 4: return tc_pick<6, 4>(bf16);
-      case 9: return tc_pick<6, 9>(bf16);
-      case 16: return tc_pick<6, 16>(bf16);
+      case 4: return fx_pick_kernel<6, 4, 2>(bf16);
+      case 9: return fx_pick_kernel<6, 9, 2>(bf16);
+      case 16: return fx_pick_kernel<6, 16, 2>(bf16);
       default: break;
     }
   }
-  return k_sweep_tc<0, 0, 0>;
+  return FxKernel{};
+}
+
+// Setup: the sweep rows of the shared operator rounded to TF32 / BF16 in the
+// K-major image both forms stage (zero padding to Np x Kp).
+__global__ void k_tc_image(const float* Hy32, const int* rows, int n_rows, int NQFS, int Np,
+                           int Kp, int bf16, unsigned char* img) {
+  const int esize = bf16 ? 2 : 4;
+  const uint32_t sbo = (uint32_t)Kp * esize * 8u;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < Np * Kp; i += gridDim.x * blockDim.x) {
+    const int n = i / Kp, k = i - n * Kp;
+    float v = 0.f;
+    if (n < n_rows && k < NQFS) v = Hy32[rows[n] * NQFS + k];
+    store_elem(img, n, k, esize, sbo, v, bf16);
+  }
+}
+
+struct TcShape {
+  int bf16, Kp, Np, ncols;
+  uint32_t idesc;
+  size_t smem;
+};
+
+TcShape tc_shape(const Ctx& c) {
+  TcShape t;
+  t.bf16 = (c.precision == EHDG_MIXED_BF16) ? 1 : 0;
+  const int kstep = t.bf16 ? 16 : 8;                // elements per 32-byte MMA K step
+  t.Kp = (c.NQFS + kstep - 1) / kstep * kstep;
+  t.Np = (c.n_rows + 15) / 16 * 16;
+  if (t.Np < 16) t.Np = 16;
+  int ncols = 32;
+  while (ncols < t.Np) ncols *= 2;
+  t.ncols = ncols;
+  const uint32_t fmt = t.bf16 ? 1u : 2u;            // BF16 (kind::f16) or TF32
+  t.idesc = umma_idesc(fmt, kTcM, t.Np);
+  const int esize = t.bf16 ? 2 : 4;
+  t.smem = (size_t)(t.Np + kTcM) * t.Kp * esize +
+           sizeof(int) * ((size_t)c.F * kTcM + 2 * (size_t)t.Np) + 1024;
+  return t;
+}
+
+// resident blocks per SM: shared memory (227 KB per SM usable) and TMEM (512 columns)
+int64_t tc_grid(const Ctx& c, const TcShape& t, size_t smem) {
+  int bpsm = (int)((227 * 1024) / (smem + 1024));
+  if (bpsm > 512 / t.ncols) bpsm = 512 / t.ncols;
+  if (bpsm > 8) bpsm = 8;
+  if (bpsm < 1) bpsm = 1;
+  const int64_t ntiles = (c.nel + kTcM - 1) / kTcM;
+  int64_t grid = (int64_t)bpsm * device_sms();
+  return grid > ntiles ? ntiles : grid;
 }
 
 }  // namespace
@@ -335,7 +615,78 @@ bool tc_supported(const Ctx& c) {
   return c.shared_op && c.n_rows >= 1 && c.n_rows <= 256 && c.NQFS <= 256;
 }
 
+cudaError_t build_tc_image(Ctx& c) {
+  if (!tc_supported(c) ||
+      (c.precision != EHDG_MIXED_TF32 && c.precision != EHDG_MIXED_BF16))
+    return cudaSuccess;
+  const TcShape t = tc_shape(c);
+  const size_t bytes = (size_t)t.Np * t.Kp * (t.bf16 ? 2 : 4);
+  void* img = nullptr;
+  cudaError_t err = dalloc_raw(c, &img, bytes);
+  if (err != cudaSuccess) return err;
+  k_tc_image<<<(t.Np * t.Kp + 255) / 256, 256, 0, c.stream>>>(c.Hy32, c.rows, c.n_rows, c.NQFS,
+                                                              t.Np, t.Kp, t.bf16,
+                                                              static_cast<unsigned char*>(img));
+  if ((err = cudaGetLastError()) != cudaSuccess) return err;
+  c.tc_img = img;
+  // the fixed-shape form: a compile-time face shape, whole faces as rows (in
+  // face order, points ascending), 32-bit point and value indices
+  c.tc_fx = false;
+  if (!fx_kernel(c.F, c.Nqf, 0).fn || c.n_rows % c.Nqf != 0 || c.n_up % c.Nqf != 0) return cudaSuccess;
+  if ((int64_t)c.Nqf * c.nface >= (1ll << 31) || (int64_t)c.NQFS * c.nel >= (1ll << 31))
+    return cudaSuccess;
+  const int n_rf = c.n_rows / c.Nqf;
+  if (n_rf > 6 || (int)c.rows_host.size() != c.n_rows) return cudaSuccess;
+  const int n_up_f = (c.pde == EHDG_TRANSPORT) ? c.n_up / c.Nqf : 0;
+  if (n_up_f > c.F / 2) return cudaSuccess;
+  for (int i = 0; i < n_rf; ++i) {
+    const int s = c.rows_host[i * c.Nqf] / c.Nqf;
+    for (int g = 0; g < c.Nqf; ++g)
+      if (c.rows_host[i * c.Nqf + g] != s * c.Nqf + g) return cudaSuccess;
+    c.tc_rfs[i] = s;
+  }
+  c.tc_nrf = n_rf;
+  c.tc_nupf = n_up_f;
+  c.tc_fx = true;
+  return cudaSuccess;
+}
+
 cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
+  const TcShape t = tc_shape(c);
+  if (c.tc_fx && c.tc_img) {
+    TcFxParams q;
+    q.nel = c.nel;
+    q.nface = (uint32_t)c.nface;
+    q.n_rf = c.tc_nrf;
+    q.n_up_f = c.tc_nupf;
+    for (int i = 0; i < 6; ++i) q.rfs[i] = c.tc_rfs[i];
+    q.Np = t.Np;
+    q.ncols = t.ncols;
+    q.idesc = t.idesc;
+    q.elem_face = c.geo.elem_face;
+    q.img = static_cast<const uint4*>(c.tc_img);
+    q.R = c.R32;
+    q.in = in;
+    q.out = out;
+    q.Y32 = c.Y32;
+    q.err = c.tc_err;
+    const size_t smem = (size_t)(t.Np + kTcM) * t.Kp * (t.bf16 ? 2 : 4) + 1024;
+    const FxKernel kern = fx_kernel(c.F, c.Nqf, t.bf16);
+    cudaError_t err = fn_smem((const void*)kern.fn, smem);
+    if (err != cudaSuccess) return err;
+    // favour shared memory over L1 so several tiles' blocks fit per SM
+    err = fn_carveout((const void*)kern.fn);
+    if (err != cudaSuccess) return err;
+    // one wave of resident blocks (registers, shared memory; TMEM columns)
+    int bpsm = std::max(fn_blocks_per_sm((const void*)kern.fn, kern.threads, smem),
+                        fn_blocks_from_attrs((const void*)kern.fn, kern.threads, smem));
+    if (bpsm > 512 / t.ncols) bpsm = 512 / t.ncols;
+    const int64_t ntiles = (c.nel + kTcM - 1) / kTcM;
+    int64_t grid = (int64_t)bpsm * device_sms();
+    if (grid > ntiles) grid = ntiles;
+    kern.fn<<<(int)grid, kern.threads, smem, c.stream>>>(q);
+    return cudaGetLastError();
+  }
   TcParams p;
   p.nel = c.nel;
   p.nface = c.nface;
@@ -345,16 +696,11 @@ cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
   p.n_rows = c.n_rows;
   p.n_up = c.n_up;
   p.owner_writes = (c.pde == EHDG_TRANSPORT) ? 1 : 0;
-  p.bf16 = (c.precision == EHDG_MIXED_BF16) ? 1 : 0;
-  const int kstep = p.bf16 ? 16 : 8;                // elements per 32-byte MMA K step
-  p.Kp = (c.NQFS + kstep - 1) / kstep * kstep;
-  p.Np = (c.n_rows + 15) / 16 * 16;
-  if (p.Np < 16) p.Np = 16;
-  int ncols = 32;
-  while (ncols < p.Np) ncols *= 2;
-  p.ncols = ncols;
-  const uint32_t fmt = p.bf16 ? 1u : 2u;            // BF16 (kind::f16) or TF32
-  p.idesc = umma_idesc(fmt, kTcM, p.Np);
+  p.bf16 = t.bf16;
+  p.Kp = t.Kp;
+  p.Np = t.Np;
+  p.ncols = t.ncols;
+  p.idesc = t.idesc;
   p.rows = c.rows;
   p.elem_face = c.geo.elem_face;
   p.Hy32 = c.Hy32;
@@ -363,25 +709,11 @@ cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
   p.out = out;
   p.Y32 = c.Y32;
   p.err = c.tc_err;
-  const int esize = p.bf16 ? 2 : 4;
-  const size_t smem = (size_t)(p.Np + kTcM) * p.Kp * esize +
-                      sizeof(int) * ((size_t)c.F * kTcM + 2 * (size_t)p.Np) + 1024;
-  void (*kern)(const TcParams) = tc_kernel(c.F, c.Nqf, p.bf16);
-  cudaError_t err =
-      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t err = fn_smem((const void*)k_sweep_tc, t.smem);
   if (err != cudaSuccess) return err;
-  // favour shared memory over L1 so several tiles' blocks fit per SM
-  err = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  err = fn_carveout((const void*)k_sweep_tc);
   if (err != cudaSuccess) return err;
-  // resident blocks per SM: shared memory (227 KB per SM usable) and TMEM (512 columns)
-  int bpsm = (int)((227 * 1024) / (smem + 1024));
-  if (bpsm > 512 / ncols) bpsm = 512 / ncols;
-  if (bpsm > 8) bpsm = 8;
-  if (bpsm < 1) bpsm = 1;
-  const int64_t ntiles = (c.nel + kTcM - 1) / kTcM;
-  int64_t grid = (int64_t)bpsm * device_sms();
-  if (grid > ntiles) grid = ntiles;
-  kern<<<(int)grid, kTcThreads, smem, c.stream>>>(p);
+  k_sweep_tc<<<(int)tc_grid(c, t, t.smem), kTcThreads, t.smem, c.stream>>>(p);
   return cudaGetLastError();
 }
 
