@@ -678,7 +678,7 @@ __global__ void __launch_bounds__(32 * kStepT) k_batch_step(const BInst* inst, c
       for (int k = tid; k < I.n * I.n; k += 32 * kStepT) Psh[k] = I.P[k];
       cur = i;
     }
-    step_tile(step_params(I), Psh, w, g, it - pre[i]);
+    step_tile(step_params(I), Psh, w, g, nullptr, it - pre[i]);
   }
 }
 

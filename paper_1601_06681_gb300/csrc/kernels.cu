@@ -435,18 +435,51 @@ cudaError_t launch_face_signs(Ctx& c) {
 // (threadIdx.y); persistent over tiles. w and G of the tile live in shared
 // memory; a shared operator P is staged once per block. The tile body is in
 // step_tiles.cuh (the batched loop runs it too).
-__global__ void __launch_bounds__(32 * kStepT) k_step(const StepParams s) {
+__global__ void __launch_bounds__(32 * kStepT) k_step(const __grid_constant__ StepParams s) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x, t = threadIdx.y, tid = t * 32 + lane;
   const int n = s.n;
   double* Psh = sm;                                   // n*n if shared
   double* w = sm + (s.shared ? n * n : 0);            // [n][32]
   double* g = w + n * 32;                             // [n][32]
+  double* sfw = g + n * 32;                           // face passes (sf_ey)
   if (s.shared)
     for (int i = tid; i < n * n; i += 32 * kStepT) Psh[i] = s.P[i];
   const int64_t ntiles = (s.nel + 31) / 32;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x)
-    step_tile(s, Psh, w, g, tile);
+    step_tile(s, Psh, w, g, sfw, tile);
+}
+
+// The sum-factorised face-point pass of the step (hexahedra, one shared
+// transport operator, sweep rows that are whole faces in face order, q = p+1):
+// the row faces and their node grids. Returns false where it does not apply.
+static bool step_sf_plan(const Ctx& c, StepParams& s) {
+  s.sf_ey = 0;
+  if (c.dim != 3 || !c.shared_op || c.pde != EHDG_TRANSPORT || c.q != c.p + 1 || c.p + 1 > 4)
+    return false;
+  if (c.n_rows % c.Nqf != 0 || (int)c.rows_host.size() != c.n_rows) return false;
+  const int nf = c.n_rows / c.Nqf;
+  if (nf < 1 || nf > 3) return false;
+  const int p1 = c.p + 1;
+  const int stride[3] = {1, p1, p1 * p1};
+  for (int rf = 0; rf < nf; ++rf) {
+    const int f = c.rows_host[rf * c.Nqf] / c.Nqf;
+    for (int gf = 0; gf < c.Nqf; ++gf)
+      if (c.rows_host[rf * c.Nqf + gf] != f * c.Nqf + gf) return false;
+    const int ax = f >> 1, side = f & 1;
+    const int ta = ax == 0 ? 1 : 0, tb = ax == 2 ? 1 : 2;   // tangential axes, a < b
+    s.sf_face[rf] = f;
+    s.sf_base[rf] = (side ? c.p : 0) * stride[ax];
+    s.sf_sa[rf] = stride[ta];
+    s.sf_sb[rf] = stride[tb];
+  }
+  for (int g = 0; g < c.q; ++g)
+    for (int i = 0; i < p1; ++i) s.sfL[g * p1 + i] = c.r1d.L[g * p1 + i];
+  s.sf_nf = nf;
+  s.sf_p1 = p1;
+  s.Nqf = c.Nqf;
+  s.sf_ey = 1;
+  return true;
 }
 
 cudaError_t launch_step(Ctx& c) {
@@ -473,12 +506,16 @@ cudaError_t launch_step(Ctx& c) {
   s.Gy = c.Gy;
   s.Y = c.Y;
   s.g_ready = 0;
+  s.sf_ey = 0;
   if (c.use_ozaki && c.oz_step.img) {
     cudaError_t e = launch_step_ozaki(c);
     if (e != cudaSuccess) return e;
     s.g_ready = 1;
   }
-  const size_t smem = sizeof(double) * ((s.shared ? (size_t)c.n * c.n : 0) + 2 * (size_t)c.n * 32);
+  step_sf_plan(c, s);
+  const size_t smem =
+      sizeof(double) * ((s.shared ? (size_t)c.n * c.n : 0) + 2 * (size_t)c.n * 32 +
+                        (s.sf_ey ? (size_t)s.sf_nf * s.sf_p1 * s.sf_p1 * 2 * 32 : 0));
   cudaError_t err = fn_smem((const void*)k_step, smem);
   if (err != cudaSuccess) return err;
   const int grid = persistent_grid(k_step, 32 * kStepT, smem, (c.nel + 31) / 32);

@@ -30,14 +30,22 @@ struct StepParams {
   const uint8_t* rowid;         // per-element operator: [NQFS][nel] row of each slot
   const uint8_t* nrows;         // [nel] slots in use
   int g_ready;                  // 1: G = P w already computed (tensor-core step)
+  // hexahedra whose sweep rows are whole faces (one shared transport
+  // operator, q = p + 1): Y0 and Gy by two 1D passes per row face instead of
+  // the dense (p+1)^2-term rows of Ey
+  int sf_ey, sf_nf, sf_p1, Nqf;
+  int sf_face[3];               // local face of each row face
+  int sf_base[3], sf_sa[3], sf_sb[3];   // its node index: base + ia sa + ib sb
+  double sfL[16];               // [g][i] Lagrange basis i at Gauss point g
   double* G;
   double* Gy;                   // [slot][nel], slot order of the element sweep
   double* Y;
 };
 
-// Psh: a shared operator P [n][n]; w, g: [n][32] scratch.
+// Psh: a shared operator P [n][n]; w, g: [n][32] scratch; sfw: the face
+// passes' scratch [sf_nf q][p+1][2][32] (sf_ey only).
 __device__ __forceinline__ void step_tile(const StepParams& s, const double* Psh, double* w,
-                                          double* g, int64_t tile) {
+                                          double* g, double* sfw, int64_t tile) {
   const int lane = threadIdx.x, t = threadIdx.y;
   const int n = s.n;
   const int64_t ne = s.nel;
@@ -84,6 +92,47 @@ __device__ __forceinline__ void step_tile(const StepParams& s, const double* Psh
     }
   }
   __syncthreads();
+  if (s.sf_ey) {
+    // Y0 = Ey u^n and Gy = Ey G on each row face: the face's nodes are a
+    // (p+1) x (p+1) grid (tangential axes a < b), and Ey there is L x L, so
+    // pass 1 contracts axis a for each Gauss index g0 along a, pass 2 axis b
+    const int p1 = s.sf_p1, q = s.sf_p1, nit = s.sf_nf * q;
+    for (int it = t; it < nit; it += kStepT) {
+      const int rf = it / q, g0 = it - rf * q;
+      const double* La = s.sfL + g0 * p1;
+      for (int ib = 0; ib < p1; ++ib) {
+        double y = 0.0, gg = 0.0;
+        if (live) {
+          const int i0 = s.sf_base[rf] + ib * s.sf_sb[rf];
+          for (int ia = 0; ia < p1; ++ia) {
+            const int i = i0 + ia * s.sf_sa[rf];
+            y = fma(La[ia], s.u[i * ne + e], y);
+            gg = fma(La[ia], g[i * 32 + lane], gg);
+          }
+        }
+        sfw[((it * p1 + ib) * 2) * 32 + lane] = y;
+        sfw[((it * p1 + ib) * 2 + 1) * 32 + lane] = gg;
+      }
+    }
+    __syncthreads();
+    if (!live) return;
+    for (int it = t; it < nit; it += kStepT) {
+      const int rf = it / q, g1 = it - rf * q;
+      const double* Lb = s.sfL + g1 * p1;
+      for (int g0 = 0; g0 < q; ++g0) {
+        const double* src = sfw + ((rf * q + g0) * p1) * 2 * 32 + lane;
+        double y = 0.0, gg = 0.0;
+        for (int ib = 0; ib < p1; ++ib) {
+          y = fma(Lb[ib], src[(ib * 2) * 32], y);
+          gg = fma(Lb[ib], src[(ib * 2 + 1) * 32], gg);
+        }
+        const int gf = g0 + q * g1;
+        s.Y[(int64_t)(s.sf_face[rf] * s.Nqf + gf) * ne + e] = y;
+        s.Gy[(int64_t)(rf * s.Nqf + gf) * ne + e] = gg;
+      }
+    }
+    return;
+  }
   if (!live) return;
   // the rows the sweep computes (upwind and tangential points; every point
   // for shallow water): Gy in the sweep's slot order, and the element
