@@ -196,7 +196,11 @@ ehdg_status ehdg_set_forcing(ehdg_ctx ctx, const double* f, int on_device);
 /* Boundary data g at the face points [n_face][Nqf] for the new time level
  * (entries of interior faces are ignored). Transport: the exterior value in
  * the trace formula, so uhat = g where beta.n^- < 0. Kept until replaced;
- * Crank-Nicolson also keeps the previous level's data. */
+ * Crank-Nicolson also keeps the previous level's data. Only the rows of
+ * boundary faces are read: from device memory (on_device) in stream order;
+ * from pinned host memory through its device mapping, and from other host
+ * memory by a copy of the whole array, before the call returns (the host
+ * buffer may then be reused). */
 ehdg_status ehdg_set_boundary(ehdg_ctx ctx, const double* g, int on_device);
 
 /* One implicit step (Algorithm 1 from the warm start u^n). Writes the number of

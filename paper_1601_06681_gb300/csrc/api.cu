@@ -876,6 +876,17 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   c.geo.face_local = d_fl;
   c.geo.face_tag = d_tag;
   c.geo.face_jf = d_jf;
+  {
+    // boundary faces: the only ones whose boundary data the steps read
+    std::vector<int32_t> bf;
+    for (int64_t f = 0; f < c.nface; ++f)
+      if (c.face_elem_h[2 * f + 1] < 0) bf.push_back((int32_t)f);
+    c.n_bface = (int64_t)bf.size();
+    if (!bf.empty()) {
+      TRYC(dalloc(c, &c.bface, bf.size()));
+      CKC(cudaMemcpy(c.bface, bf.data(), sizeof(int32_t) * bf.size(), cudaMemcpyHostToDevice));
+    }
+  }
 
   const int64_t ne = c.shared_op ? 1 : c.nel;
   TRYC(dalloc(c, &c.P, (size_t)c.n * c.n * ne));
@@ -1134,7 +1145,22 @@ ehdg_status ehdg_set_forcing(ehdg_ctx h, const double* f, int on_device) {
 ehdg_status ehdg_set_boundary(ehdg_ctx h, const double* g, int on_device) {
   if (!h || !g) return fail(EHDG_ERR_INVALID, "NULL argument");
   Ctx& c = h->c;
-  return upload(c, c.gb, g, c.nface, c.Nqf, on_device);
+  // only boundary faces' values are read: from device memory directly, from
+  // pinned host memory through its device mapping (then the host buffer is
+  // free again when the call returns); other host memory is copied whole
+  const double* src = on_device ? g : nullptr;
+  if (!on_device) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, g) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+        a.devicePointer != nullptr)
+      src = static_cast<const double*>(a.devicePointer);
+    else
+      cudaGetLastError();
+  }
+  if (!src) return upload(c, c.gb, g, c.nface, c.Nqf, on_device);
+  CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_gather_boundary(c, src, c.gb); }));
+  if (!on_device) CK(cudaStreamSynchronize(c.stream));
+  return EHDG_OK;
 }
 
 ehdg_status ehdg_step(ehdg_ctx h, int* iters, double* final_residual) {

@@ -139,6 +139,8 @@ struct Ctx {
   // fixed-shape form (rows are whole faces), the local face of each row face
   void* tc_img = nullptr;
   bool tc_fx = false;
+  int32_t* bface = nullptr;      // [n_bface] boundary faces (ascending)
+  int64_t n_bface = 0;
   int tc_nrf = 0, tc_nupf = 0;   // row faces; leading ones owned (upwind)
   int tc_rfs[6] = {0, 0, 0, 0, 0, 0};
   // FP64-accurate products on the BF16 tensor cores (Ozaki splitting, shared
@@ -285,6 +287,7 @@ cudaError_t dalloc_raw(Ctx& c, void** p, size_t bytes);   // device allocation o
 std::vector<std::pair<void*, size_t>> state_arrays(Ctx& c);
 // tensor-core correction sweep (tc_sweep.cu)
 bool tc_supported(const Ctx& c);
+cudaError_t launch_gather_boundary(const Ctx& c, const double* src, double* dst);
 cudaError_t build_tc_image(Ctx& c);   // after the FP32 operator copy
 cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out);
 

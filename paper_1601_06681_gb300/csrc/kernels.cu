@@ -981,6 +981,32 @@ cudaError_t launch_soa_to_aos(const double* src, double* dst, int64_t outer, int
   return transpose(src, dst, inner, outer, s);
 }
 
+// Boundary data of the boundary faces only: src [n_face][Nqf] (device memory,
+// or pinned host memory through its device mapping), dst [Nqf][n_face]. A
+// warp reads consecutive points of one face row, so each face's Nqf values
+// come as one contiguous read.
+__global__ void k_gather_boundary(const double* __restrict__ src, const int32_t* bface,
+                                  int64_t n_b, int Nqf, int64_t nface, double* dst) {
+  const int64_t total = n_b * Nqf;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / Nqf;
+    const int g = (int)(t - b * Nqf);
+    const int64_t f = bface[b];
+    dst[(int64_t)g * nface + f] = src[f * Nqf + g];
+  }
+}
+
+cudaError_t launch_gather_boundary(const Ctx& c, const double* src, double* dst) {
+  const int64_t total = c.n_bface * c.Nqf;
+  if (total == 0) return cudaSuccess;
+  int64_t grid = (total + 255) / 256;
+  if (grid > 152 * 16) grid = 152 * 16;
+  k_gather_boundary<<<(unsigned)grid, 256, 0, c.stream>>>(src, c.bface, c.n_bface, c.Nqf,
+                                                          c.nface, dst);
+  return cudaGetLastError();
+}
+
 // Per-step bookkeeping after the end-of-step kernels: iterations and status
 // of step it->step, then advance the step counter.
 __global__ void k_step_end(IterState* it, int* iters, int* status, int cap) {
