@@ -25,6 +25,10 @@ time_to_tol: every path (FP64 on the DFMA pipe, FP64-accurate on the BF16
              and the roofline of its dominant kernel.
 secondary:   the 2D variable-velocity workload (256^2 quads, p = 4,
              per-element operators, Crank-Nicolson dt = 2e-3 x 50 steps).
+batch:       the batched mix of 256 independent 2D transport instances
+             (N 8..128, p 1..5, BE dt = 0.01 x 10 steps), instances/s with
+             p50/p99 per-instance times and each variant's distance to the
+             instances' FP64 fixed points, at a matched-accuracy tolerance.
 --impl reference: the CPU oracle on a bounded sample of the same workload.
 """
 from __future__ import annotations
@@ -73,6 +77,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="headline: leave out the batched-mix key")
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "transport2d_varbeta", "transport3d", "sw2d",
                              "transport2d_small", "steady2d", "batch", "residual"],
@@ -92,6 +98,12 @@ def parse():
     ap.add_argument("--batch-chains", type=int, default=0,
                     help="batch workload: fixed graph branch count k instead of "
                          "ehdg_batch_autotune_chains")
+    ap.add_argument("--batch-variants", default="",
+                    help="batch workload: comma-separated subset of its variants "
+                         "(default: all)")
+    ap.add_argument("--batch-tol", type=float, default=0.0,
+                    help="batch workload: stopping tolerance of every instance "
+                         "(default: the matched-accuracy 3e-12)")
     return ap.parse_args()
 
 
@@ -814,6 +826,15 @@ def run_headline(args):
         a2.n, a2.time_steps = 0, 0
         secondary = run_2d(a2, ws, dev, stream)
 
+    batch = None
+    if not args.no_batch:
+        # the batched mix (256 instances), at its matched-accuracy tolerance:
+        # the batched loop and the autotuned schedule, FP64 and mixed
+        bout, binfo = batch_variants(args, ["fp64", "fp32", "tf32", "fp64+tuned", "fp32+tuned",
+                                            "tf32+tuned"], TOL_MATCHED_BATCH)
+        batch = {"metric": "instances/s (one graph launch per step)", "config": binfo,
+                 "results": bout}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -843,6 +864,7 @@ def run_headline(args):
             "kernel_time_share": kernel_shares(stats),
             "time_to_tol": ttt,
             "secondary": secondary,
+            "batch": batch,
             "clocks": clocks,
         }
         if not args.no_cpu_baseline:
@@ -1070,49 +1092,69 @@ def residual_workload(args):
           flush=True)
 
 
-def batch_workload(args):
+# stopping tolerance of the batched mix (config 5) at matched accuracy: the
+# largest of 1e-11, 3e-12, 1e-12 at which every instance's FP64 state lies
+# within 1e-10 relative L2 of its fixed point (at 1e-11: 21 of 256 above)
+TOL_MATCHED_BATCH = 3e-12
+
+
+def batch_variants(args, variants, tol, profile_loop=True):
     """Config 5: independent 2D transport instances (N 8..128, p 1..5) stepped
-    together, one graph launch per time step; FP64 versus mixed precision.
-    By default the instances iterate in the batched loop (one launch per
-    kernel and iteration over every unconverged instance); "+branches" runs
-    every instance's own loop on the graph's branches instead. The branch
-    count (and, where named, the tile shape or the inner sweep count) comes
-    from the batch autotuners, timed over the same 10-step run after one
-    warm-up run (setup, outside the timed run)."""
+    together, one graph launch per time step, every instance to `tol`.
+    Variant "prec" iterates in the batched loop (one launch per kernel and
+    iteration over every unconverged instance); "prec+branches" runs every
+    instance's own loop on the graph's branches; "prec+tuned" takes the
+    schedule from ehdg_batch_autotune_schedule (loop, or branches with
+    16/32/64 of them); "+inner" tunes the inner sweep count m; "+tiles" the
+    fused FP64 sweep's tile. Branch counts come from the batch autotuners,
+    timed over the same run after a warm-up run (setup, outside the timed
+    run). Every variant's final states are compared with the instances' FP64
+    fixed points (every step converged to 1e-13)."""
     import torch
-    from paper_1601_06681_gb300 import build, ehdg
+    from paper_1601_06681_gb300 import ehdg
     from paper_1601_06681_gb300 import workloads as W
-    torch.cuda.set_device(0)
-    build.build()
-    ehdg.load()
     stream = torch.cuda.current_stream()
     wls = W.batched_mix(n_inst=args.n_inst)
-    out = {}
-    # "+branches": each instance's own loop on the graph's branches
-    # "+inner": the inner sweep count m from ehdg_batch_autotune_inner_sweeps
-    # "+tiles": the fused FP64 sweep's tile (row groups FT) of all instances
-    # from ehdg_batch_autotune_sweep_tile
-    variants = ["fp64", "fp32", "tf32", "bf16", "fp64+branches", "fp32+branches",
-                "tf32+branches", "fp32+inner", "tf32+inner", "fp64_emulated",
-                "tf32+emulated_outer"]
-    for prec in variants:
-        base, _, opt = prec.partition("+")
-        specs, inputs = [], []
+
+    def make_specs(base, opt, tol_i, max_iter=400):
+        specs = []
         for wl in wls:
             mesh = ehdg.ehdg_mesh_structured(wl.n)
-            specs.append(dict(mesh=mesh, p=wl.p, scheme=wl.scheme, dt=wl.dt, tol=wl.tol,
-                              max_iter=400, beta_const=wl.beta_const, precision=base,
+            specs.append(dict(mesh=mesh, p=wl.p, scheme=wl.scheme, dt=wl.dt, tol=tol_i,
+                              max_iter=max_iter, beta_const=wl.beta_const, precision=base,
                               inner_sweeps=args.inner_sweeps,
                               emulated_outer=(opt == "emulated_outer")))
-        t0 = time.perf_counter()
-        b = ehdg.Batch(specs, stream=stream)
-        if opt == "branches":
-            b.set_loop(False)
-        setup = time.perf_counter() - t0
+        return specs
+
+    def start(b):
+        ins = []
         for wl, s in zip(wls, b.instances):
             X, XF = s.node_coords(), s.face_point_coords()
             s.set_boundary(wl.u0_fn(XF))
-            inputs.append(torch.from_numpy(np.ascontiguousarray(wl.initial(X))).cuda())
+            ins.append(torch.from_numpy(np.ascontiguousarray(wl.initial(X))).cuda())
+        return ins
+
+    bfix = ehdg.Batch(make_specs("fp64", "", 1e-13, max_iter=4000), stream=stream)
+    for s, u0 in zip(bfix.instances, start(bfix)):
+        s.set_state(u0)
+    bfix.run(wls[0].n_steps)
+    u_fix = [s.get_state()[0] for s in bfix.instances]
+    bfix.close()
+
+    def accuracy(b):
+        errs = np.array([rel_l2(s.get_state()[0], uf) for s, uf in zip(b.instances, u_fix)])
+        return {"max": float(errs.max()), "median": float(np.median(errs)),
+                "instances_above_target": int((errs > ACCURACY_TARGET).sum())}
+
+    out = {}
+    for prec in variants:
+        base, _, opt = prec.partition("+")
+        t0 = time.perf_counter()
+        b = ehdg.Batch(make_specs(base, opt, tol), stream=stream)
+        if opt == "branches":
+            b.set_loop(False)
+        setup = time.perf_counter() - t0
+        inputs = start(b)
 
         def reset():
             for s, u0 in zip(b.instances, inputs):
@@ -1134,6 +1176,9 @@ def batch_workload(args):
             chains = args.batch_chains
         else:
             chains, _ = b.autotune_chains()
+        if opt == "tuned":
+            loop_on, chains, _ = b.autotune_schedule((16, 32, 64))
+            tuned["schedule"] = "loop" if loop_on else "branches"
         one_run()                                     # recapture with the tuned settings
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -1143,8 +1188,10 @@ def batch_workload(args):
         out[prec] = {"instances_per_s": len(wls) / wall, "wall_s": wall, "setup_s": setup,
                      "p50_instance_ms": float(np.percentile(times, 50) * 1e3),
                      "p99_instance_ms": float(np.percentile(times, 99) * 1e3),
-                     "sweeps_total": int(iters.sum()), "chains": chains, **tuned}
-        if opt != "branches" and base in ("fp64", "fp32", "tf32", "bf16"):
+                     "sweeps_total": int(iters.sum()), "chains": chains,
+                     "rel_l2_vs_fp64_fixed_point": accuracy(b), **tuned}
+        if (profile_loop and opt not in ("branches", "tuned")
+                and base in ("fp64", "fp32", "tf32", "bf16")):
             # kernel accounting of the batched loop: the same run with its
             # steps driven from the host and every launch timed
             b.set_profiling(True)
@@ -1154,13 +1201,41 @@ def batch_workload(args):
             out[prec]["loop_kernel_ms"] = {k: round(v[1], 3) for k, v in st.items() if v[0]}
             out[prec]["loop_kernel_launches"] = {k: v[0] for k, v in st.items() if v[0]}
         b.close()
-    for prec in variants[1:]:
-        out[prec]["speedup_vs_fp64"] = out["fp64"]["wall_s"] / out[prec]["wall_s"]
+    ref = out.get("fp64+tuned", out.get("fp64"))
+    if ref:
+        for prec in variants:
+            out[prec]["speedup_vs_fp64"] = ref["wall_s"] / out[prec]["wall_s"]
     info = {"workload": f"batched_mix_{args.n_inst}", "time_steps": wls[0].n_steps,
+            "dt": wls[0].dt, "tol": tol,
+            "tol_reading": "the largest of 1e-11, 3e-12, 1e-12 at which every instance's FP64 "
+                           "state lies within 1e-10 of its fixed point (the mix's own 1e-10 "
+                           "leaves FP64 up to 2.4e-9 away)" if tol == TOL_MATCHED_BATCH else
+                           "given on the command line",
+            "accuracy": "relative L2 of each instance's final volume state from its FP64 "
+                        "fixed point (every step converged to 1e-13): max and median over "
+                        f"instances, and how many exceed {ACCURACY_TARGET:g}",
             "elements_total": int(sum(np.prod(w.n) for w in wls)),
             "per_instance_time": "device time from the instance's step start to its "
                                  "convergence (batched loop) or to its last kernel "
-                                 "(branches), summed over the steps"}
+                                 "(branches), summed over the steps",
+            "speedup_reference": "fp64+tuned" if "fp64+tuned" in out else "fp64"}
+    return out, info
+
+
+def batch_workload(args):
+    """The batch workload alone: every variant, one JSON line."""
+    import torch
+    from paper_1601_06681_gb300 import build, ehdg
+    torch.cuda.set_device(0)
+    build.build()
+    ehdg.load()
+    variants = ["fp64", "fp32", "tf32", "bf16", "fp64+branches", "fp32+branches",
+                "tf32+branches", "fp64+tuned", "fp32+tuned", "tf32+tuned", "fp32+inner",
+                "tf32+inner", "fp64_emulated", "tf32+emulated_outer"]
+    if args.batch_variants:
+        variants = [v for v in args.batch_variants.split(",") if v]
+    tol = args.batch_tol if args.batch_tol > 0 else TOL_MATCHED_BATCH
+    out, info = batch_variants(args, variants, tol)
     print(json.dumps({"metric": "instances/s (one graph launch per step)", "config": info,
                       "results": out}), flush=True)
 

@@ -320,6 +320,18 @@ ehdg_status ehdg_batch_kernel_stats(ehdg_batch b, int kind, int64_t* launches, d
  * NULL batch or no candidates. */
 ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* candidates, int n_candidates,
                                        int* best, double* best_ms);
+/* Autotuner for the schedule of a batch step (the paper has no counterpart):
+ * times the batched loop (every instance it supports iterates in one loop of
+ * launches over the unconverged instances) against every instance's own
+ * loop on k graph branches, k from chain_candidates (entries < 1 skipped),
+ * and keeps the fastest. Same protocol as ehdg_batch_autotune_chains (each
+ * candidate timed over the batch's last run, states restored). *loop_on (may
+ * be NULL) receives 1 for the loop, *chains the branch count kept, *best_ms
+ * the time of the kept schedule. Both schedules give the same iterates bit
+ * for bit. EHDG_ERR_INVALID for a NULL batch or no candidates. */
+ehdg_status ehdg_batch_autotune_schedule(ehdg_batch b, const int* chain_candidates,
+                                         int n_candidates, int* loop_on, int* chains,
+                                         double* best_ms);
 /* Autotuner for the tile shape (FT, as in ehdg_autotune_sweep_tile) of every
  * instance's fused FP64 sweep together, timed as whole batch steps: instances
  * that share the GPU favour other shapes than one instance alone. Same

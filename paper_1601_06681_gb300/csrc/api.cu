@@ -1726,6 +1726,45 @@ ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* cands, int n_can
   return st;
 }
 
+ehdg_status ehdg_batch_autotune_schedule(ehdg_batch b, const int* chain_cands, int n_cands,
+                                         int* loop_on, int* chains, double* best_ms) {
+  if (!b || !chain_cands || n_cands < 1) return fail(EHDG_ERR_INVALID, "bad argument");
+  const bool saved_loop = b->use_loop;
+  const int saved_chains = b->chains;
+  // variant 0: the batched loop (branches keep the current count); variant
+  // q >= 1: every instance on the branches, chain_cands[q - 1] of them
+  std::vector<double> ms((size_t)n_cands + 1);
+  const ehdg_status st = batch_time_variants(
+      b, n_cands + 1,
+      [&](int q) {
+        if (q > 0 && chain_cands[q - 1] < 1) return false;
+        b->use_loop = (q == 0);
+        if (q > 0) b->chains = chain_cands[q - 1];
+        return true;
+      },
+      ms.data());
+  int best = -1;
+  double t = 1e300;
+  if (st == EHDG_OK)
+    for (int q = 0; q <= n_cands; ++q)
+      if (ms[q] < t) {
+        t = ms[q];
+        best = q;
+      }
+  if (best < 0) {
+    b->use_loop = saved_loop;
+    b->chains = saved_chains;
+  } else {
+    b->use_loop = (best == 0);
+    b->chains = best == 0 ? saved_chains : chain_cands[best - 1];
+  }
+  batch_destroy_graph(b);
+  if (loop_on) *loop_on = b->use_loop ? 1 : 0;
+  if (chains) *chains = b->chains;
+  if (best_ms) *best_ms = t;
+  return st;
+}
+
 ehdg_status ehdg_batch_autotune_inner_sweeps(ehdg_batch b, const int* cands, int n_cands,
                                              int* best, double* best_ms) {
   if (!b || !cands || n_cands < 1) return fail(EHDG_ERR_INVALID, "bad argument");

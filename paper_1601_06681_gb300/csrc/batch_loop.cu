@@ -30,6 +30,7 @@
 #include "pe_tile.cuh"
 #include "step_tiles.cuh"
 #include "sweep_common.cuh"
+#include "tc_fx_tile.cuh"
 #include "umma.cuh"
 
 namespace ehdg {
@@ -72,6 +73,10 @@ struct BInst {
   int* err;
   const uint4* Bimg;            // the rounded operator rows, K-major image (Np x Kp)
   const int* rowfg;             // [Np] face | point << 8 of each row
+  // fixed-shape tile body (quadrilaterals, whole faces as rows): row faces,
+  // the leading ones owned, and the local face of each
+  int fx, nrf, nupf;
+  int rfs[6];
   // convergence time of the instance in the current step (%globaltimer), and
   // the step's start and the accumulated step times
   unsigned long long* t_conv;
@@ -333,6 +338,49 @@ __device__ __forceinline__ void b_store_elem(unsigned char* base, int row, int k
   }
 }
 
+// One 128-element tile of instance I's correction sweep j in the fixed-shape
+// tile body of the single-problem sweep (quadrilaterals, NQF points per face,
+// two threads per element; part Q = the thread's half of the tile).
+template <int NQF, int BF16, int Q>
+__device__ __forceinline__ void btc_fx_part(const BInst& I, int j, unsigned char* As,
+                                            unsigned char* Bs, uint64_t* mbar, uint32_t tbase,
+                                            uint32_t& phase, bool& failed, int64_t tile) {
+  TcFxParams q;
+  q.nel = I.nel;
+  q.nface = (uint32_t)I.nface;
+  q.n_rf = I.nrf;
+  q.n_up_f = I.nupf;
+#pragma unroll
+  for (int i = 0; i < 6; ++i) q.rfs[i] = I.rfs[i];
+  q.Np = I.Np;
+  q.ncols = 0;
+  q.idesc = I.idesc;
+  q.elem_face = I.elem_face;
+  q.img = I.Bimg;
+  const int64_t trace = (int64_t)I.Nqf * I.nface;
+  q.R = I.R32;
+  q.in = j == 0 ? I.R32 : I.d32 + (int64_t)((j - 1) & 1) * trace;
+  q.out = I.d32 + (int64_t)(j & 1) * trace;
+  q.Y32 = I.Y32;
+  q.err = I.err;
+  const int64_t e = tile * kFxM + (threadIdx.x & (kFxM - 1));
+  int fid[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) fid[f] = e < I.nel ? I.elem_face[f * I.nel + e] : 0;
+  fx_tile<4, NQF, BF16, 2, Q>(q, As, Bs, mbar, tbase, phase, failed, tile, fid);
+}
+
+template <int NQF, int BF16>
+__device__ __forceinline__ void btc_fx(const BInst& I, int j, unsigned char* As,
+                                       unsigned char* Bs, uint64_t* mbar, uint32_t tbase,
+                                       uint32_t& phase, bool& failed, int64_t tile) {
+  // the halves are warp-uniform (128 threads each)
+  if ((threadIdx.x >> 7) == 0)
+    btc_fx_part<NQF, BF16, 0>(I, j, As, Bs, mbar, tbase, phase, failed, tile);
+  else
+    btc_fx_part<NQF, BF16, 1>(I, j, As, Bs, mbar, tbase, phase, failed, tile);
+}
+
 // Inner correction sweep j of every unconverged TF32/BF16 mixed-precision
 // instance: delta_out = R + (delta_in Hy^T at the rows), owner writes; items[w]
 // = (instance, 128-element tile). The operands, MMA shapes and epilogue are
@@ -396,6 +444,28 @@ __global__ void __launch_bounds__(kBTcThreads) k_batch_tc(const BInst* inst, con
       for (int i = tid; i < n16; i += kBTcThreads)
         reinterpret_cast<uint4*>(Bs)[i] = I.Bimg[i];
       cur = item.x;
+    }
+    if (I.fx) {
+      // the fixed-shape tile body (the single-problem sweep's, bit for bit)
+#define EHDG_BTC_FX(N)                                                                   \
+  case N:                                                                                \
+    if (I.bf16)                                                                          \
+      btc_fx<N, 1>(I, j, As, Bs, &mbar, tbase, phase, failed, item.y);                   \
+    else                                                                                 \
+      btc_fx<N, 0>(I, j, As, Bs, &mbar, tbase, phase, failed, item.y);                   \
+    break;
+      switch (I.Nqf) {
+        EHDG_BTC_FX(2)
+        EHDG_BTC_FX(3)
+        EHDG_BTC_FX(4)
+        EHDG_BTC_FX(5)
+        EHDG_BTC_FX(6)
+        EHDG_BTC_FX(7)
+        default: break;
+      }
+#undef EHDG_BTC_FX
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      continue;
     }
     const int64_t trace = (int64_t)I.Nqf * I.nface;
     const float* in = j == 0 ? I.R32 : I.d32 + (int64_t)((j - 1) & 1) * trace;
@@ -917,6 +987,11 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
         I.Kp = (c.NQFS + kstep - 1) / kstep * kstep;
         I.Np = std::max(16, (c.n_rows + 15) / 16 * 16);
         I.idesc = umma_idesc(I.bf16 ? 1u : 2u, kBTcM, I.Np);
+        // the fixed-shape body where the single-problem sweep runs it
+        I.fx = (c.tc_fx && c.F == 4 && c.Nqf >= 2 && c.Nqf <= 7) ? 1 : 0;
+        I.nrf = c.tc_nrf;
+        I.nupf = c.tc_nupf;
+        for (int r = 0; r < 6; ++r) I.rfs[r] = c.tc_rfs[r];
         max_kp_bytes = std::max(max_kp_bytes, I.Kp * (I.bf16 ? 2 : 4));
         max_np = std::max(max_np, I.Np);
         L.any_mma = true;

@@ -110,6 +110,9 @@ _SIGS = [
                                              C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_batch_autotune_sweep_tile", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
                                                  C.POINTER(C.c_int), C.POINTER(C.c_double)]),
+    ("ehdg_batch_autotune_schedule", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
+                                               C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                               C.POINTER(C.c_double)]),
     ("ehdg_batch_autotune_inner_sweeps", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.c_int,
                                                    C.POINTER(C.c_int), C.POINTER(C.c_double)]),
     ("ehdg_batch_destroy", None, [C.c_void_p]),
@@ -521,6 +524,16 @@ class Batch:
         _check(load().ehdg_batch_autotune_chains(self._h, arr, len(candidates), C.byref(best),
                                                  C.byref(ms)))
         return best.value, ms.value
+
+    def autotune_schedule(self, chain_candidates=(16, 32, 64)):
+        """Time the batched loop against the branch form with each branch
+        count, from the current states (restored after each), and keep the
+        fastest: (loop_on, k, ms)."""
+        arr = (C.c_int * len(chain_candidates))(*[int(k) for k in chain_candidates])
+        loop_on, k, ms = C.c_int(), C.c_int(), C.c_double()
+        _check(load().ehdg_batch_autotune_schedule(self._h, arr, len(chain_candidates),
+                                                   C.byref(loop_on), C.byref(k), C.byref(ms)))
+        return bool(loop_on.value), k.value, ms.value
 
     def autotune_inner_sweeps(self, candidates=(2, 4, 6, 8, 12, 16)):
         """One inner sweep count m for every mixed-precision instance, timed

@@ -231,6 +231,57 @@ def test_batched_loop_equals_branch_graph(ehdg):
         assert np.array_equal(u, ru) and np.array_equal(uh, ruh)
 
 
+def test_batched_loop_with_several_tiles_per_block_equals_branch_graph(ehdg):
+    """Enough tensor-core correction tiles that each block of the batched
+    correction sweep takes a run of several, across instances of different
+    degrees (its staged operator changes inside the run): the loop and the
+    branch graph (single-problem kernels) still agree bit for bit."""
+    rng = np.random.default_rng(35)
+    inst = []
+    for i in range(28):
+        n = int(rng.integers(96, 129))
+        p = 1 + i % 5
+        th = rng.uniform(0.05, 1.5) + (np.pi / 2) * (i % 4)
+        beta = rng.uniform(0.5, 1.5) * np.array([np.cos(th), np.sin(th)])
+        mesh = W.structured_mesh((n, n))
+        X = node_coords(mesh, p)
+        XF = face_point_coords(mesh, p, p + 1)     # Gauss points: q = p + 1 (constant velocity)
+        kw = dict(mesh=mesh, p=p, scheme="be", dt=0.01, tol=1e-10, max_iter=500,
+                  beta_const=beta, precision=("tf32", "bf16")[i % 2], inner_sweeps=4)
+        inst.append((kw, None, W.gaussian(X, (0.4, 0.6), 0.1)[:, None, :],
+                     W.gaussian(XF, (0.4, 0.6), 0.1)))
+    a_iters, _, a_states = run_loop(ehdg, inst, 1, loop=True)
+    b_iters, _, b_states = run_loop(ehdg, inst, 1, loop=False)
+    assert np.array_equal(a_iters, b_iters)
+    for (u, uh), (ru, ruh) in zip(a_states, b_states):
+        assert np.array_equal(u, ru) and np.array_equal(uh, ruh)
+
+
+def test_schedule_autotuner_keeps_states_and_results(ehdg):
+    """The loop-or-branches autotuner restores every state and picks a
+    schedule whose results equal the untuned run's bit for bit."""
+    inst = loop_instances(n=8, seed=36, precisions=("fp64", "tf32", "fp32"))
+    ref_iters, _, ref_states = run_loop(ehdg, inst, 2)
+    with ehdg.Batch([kw for kw, _, _, _ in inst]) as b:
+        for (kw, prob, u0, g), s in zip(inst, b.instances):
+            s.set_boundary(g)
+            s.set_state(u0)
+        b.run(2)                                   # the run the tuner times
+        for (kw, prob, u0, g), s in zip(inst, b.instances):
+            s.set_state(u0)
+        before = [s.get_state() for s in b.instances]
+        loop_on, k, ms = b.autotune_schedule((2, 4))
+        assert 0 < ms < 1e300 and (loop_on or k in (2, 4))
+        for (u, uh), s in zip(before, b.instances):
+            su, suh = s.get_state()
+            assert np.array_equal(u, su) and np.array_equal(uh, suh)
+        iters, _ = b.run(2)
+        states = [s.get_state() for s in b.instances]
+    assert np.array_equal(iters, ref_iters)
+    for (u, uh), (ru, ruh) in zip(states, ref_states):
+        assert np.array_equal(u, ru) and np.array_equal(uh, ruh)
+
+
 def test_batched_loop_reports_an_instance_that_does_not_converge(ehdg):
     """An instance that hits max_iter stops with EHDG_ERR_NOT_CONVERGED while
     the others run on to their tolerance."""
