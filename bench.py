@@ -25,6 +25,8 @@ time_to_tol: every path (FP64 on the DFMA pipe, FP64-accurate on the BF16
              and the roofline of its dominant kernel.
 secondary:   the 2D variable-velocity workload (256^2 quads, p = 4,
              per-element operators, Crank-Nicolson dt = 2e-3 x 50 steps).
+shallow_water: linearised shallow water on 512^2 quads, p = 3 (one shared
+             48 x 48 operator), time to a matched tolerance of every path.
 batch:       the batched mix of 256 independent 2D transport instances
              (N 8..128, p 1..5, BE dt = 0.01 x 10 steps), instances/s with
              p50/p99 per-instance times and each variant's distance to the
@@ -79,6 +81,8 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-batch", action="store_true",
                     help="headline: leave out the batched-mix key")
+    ap.add_argument("--no-sw", action="store_true",
+                    help="headline: leave out the shallow-water key")
     ap.add_argument("--workload", default="headline",
                     choices=["headline", "transport2d_varbeta", "transport3d", "sw2d",
                              "transport2d_small", "steady2d", "batch", "residual"],
@@ -826,6 +830,10 @@ def run_headline(args):
         a2.n, a2.time_steps = 0, 0
         secondary = run_2d(a2, ws, dev, stream)
 
+    sw = None
+    if not args.no_sw:
+        sw = sw_variants(args)
+
     batch = None
     if not args.no_batch:
         # the batched mix (256 instances), at its matched-accuracy tolerance:
@@ -864,6 +872,7 @@ def run_headline(args):
             "kernel_time_share": kernel_shares(stats),
             "time_to_tol": ttt,
             "secondary": secondary,
+            "shallow_water": sw,
             "batch": batch,
             "clocks": clocks,
         }
@@ -945,11 +954,8 @@ def compare_workload(args):
     elif args.workload == "sw2d":
         # dt at which Theorem 2 holds on this mesh: h / (dt (p+1)(p+2)) = 3.9, C = 0.34
         wl = W.sw_2d(n=(n, n), p=3, dt=2.5e-5, n_steps=n_steps)
-        dt_note = ("changed workload: dt = 2.5e-5 (not 1e-3) and the step count given here, "
-                   "because at dt = 1e-3 on this mesh h / (dt (p+1)(p+2)) = 0.098 < 1, "
-                   "Theorem 2's contraction condition fails and the eHDG iteration grows by "
-                   "dt (p+1)(p+2) / h per iteration (pinned on the oracle); at 2.5e-5 the "
-                   "ratio is 3.9 and C = 0.34")
+        dt_note = SW_DT_NOTE.replace("and 20 steps (not 100)",
+                                     f"and {n_steps} steps (not 100)")
         precisions = ["fp64", "fp64_emulated", "tf32", "bf16", "fp32", "bf16+emulated_outer"]
     elif args.workload == "steady2d":
         # the steady solve of Sec. 4.1 (one "step", many iterations)
@@ -1090,6 +1096,94 @@ def residual_workload(args):
                       "bytes_per_call": 3 * 8 * n, "peak_gbs": peak, "peak_source": peak_src,
                       "l2": "inputs larger than L2 (402.7 MB per call)", "results": res}),
           flush=True)
+
+
+SW_DT_NOTE = ("changed workload: dt = 2.5e-5 (not 1e-3) and 20 steps (not 100), because at "
+              "dt = 1e-3 on this mesh h / (dt (p+1)(p+2)) = 0.098 < 1, Theorem 2's "
+              "contraction condition fails and the eHDG iteration grows by dt (p+1)(p+2) / h "
+              "per iteration (pinned on the oracle); at 2.5e-5 the ratio is 3.9 and C = 0.34")
+
+
+def sw_variants(args):
+    """Config 3: linearised shallow water (Phi = 1, walls) on 512^2 quads, p = 3,
+    one shared 48 x 48 local operator, backward Euler dt = 2.5e-5 x 20 steps.
+    The FP64 fixed point is the FP64 run with every step converged to 1e-13;
+    the stopping tolerance is the largest of 1e-10, 1e-11, 3e-12, 1e-12 at which
+    the FP64 run lands within 1e-10 relative L2 of it (chosen in the run), and
+    every path (FP64 on the DFMA pipe, FP64-accurate on the BF16 tensor cores,
+    TF32/BF16 tensor-core corrections with FP64 defect correction, with DFMA or
+    tensor-core outer sweeps) stops at that tolerance."""
+    import torch
+    from paper_1601_06681_gb300 import ehdg
+    from paper_1601_06681_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    wl = W.sw_2d(n=(512, 512), p=3, dt=2.5e-5, n_steps=20)
+    mesh = ehdg.ehdg_mesh_structured(wl.n, boundary_tag=2)
+
+    def make(prec, tol, max_iter=400):
+        base, _, opt = prec.partition("+")
+        return ehdg.Solver(mesh, wl.p, pde="sw", scheme=wl.scheme, dt=wl.dt, tol=tol,
+                           max_iter=max_iter, precision=base, inner_sweeps=args.inner_sweeps,
+                           stream=stream, emulated_outer=(opt == "emulated_outer"), Phi=wl.Phi)
+
+    s = make("fp64", 1e-13, 4000)
+    X, XF = s.node_coords(), s.face_point_coords()
+    u0 = torch.from_numpy(np.ascontiguousarray(wl.initial(X))).cuda()
+    g0 = torch.from_numpy(np.ascontiguousarray(wl.boundary(XF, 0.0))).cuda()
+
+    def run(sol):
+        sol.set_boundary(g0)
+        sol.set_state(u0)
+        return sum(sol.run(wl.n_steps))
+
+    run(s)
+    u_fix = s.get_state()[0]
+    s.close()
+    tol, tol_errs = 1e-12, {}
+    for t in (1e-10, 1e-11, 3e-12, 1e-12):
+        s = make("fp64", t)
+        run(s)
+        tol_errs[f"{t:g}"] = rel_l2(s.get_state()[0], u_fix)
+        s.close()
+        if tol_errs[f"{t:g}"] <= ACCURACY_TARGET:
+            tol = t
+            break
+    reps = max(1, min(args.steps, 5))
+    out = {}
+    for prec in ["fp64", "fp64_emulated", "tf32", "bf16", "tf32+emulated_outer",
+                 "bf16+emulated_outer"]:
+        base = prec.partition("+")[0]
+        s = make(prec, tol)
+        m = None
+        if base in ("tf32", "bf16") and args.tune_inner:
+            s.set_boundary(g0)
+            s.set_state(u0)
+            m = s.autotune_inner_sweeps((4, 6, 8, 12, 16))[0]
+        run(s)                                        # warm-up (captures the graphs)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = 0
+        for _ in range(reps):
+            its = run(s)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ent = {"ms_per_run": e0.elapsed_time(e1) / reps, "fp64_sweeps_per_run": int(its),
+               "rel_l2_vs_fp64_fixed_point": rel_l2(s.get_state()[0], u_fix)}
+        if base in ("tf32", "bf16"):
+            ent["inner_sweeps"] = m if m is not None else args.inner_sweeps
+        out[prec] = ent
+        s.close()
+    for prec in out:
+        out[prec]["speedup_vs_fp64"] = out["fp64"]["ms_per_run"] / out[prec]["ms_per_run"]
+    info = {"workload": wl.name, "n_elem": int(np.prod(wl.n)), "p": wl.p, "fields": 3,
+            "local_operator": "one shared 48 x 48", "dt": wl.dt, "time_steps": wl.n_steps,
+            "dt_note": SW_DT_NOTE, "tol": tol,
+            "tol_rule": "the largest of 1e-10, 1e-11, 3e-12, 1e-12 at which FP64 lands within "
+                        "1e-10 relative L2 of its fixed point (every step to 1e-13)",
+            "fp64_rel_l2_vs_fixed_point_by_tol": tol_errs, "runs_timed": reps}
+    return {"metric": "time-to-tol per run, mixed vs FP64", "config": info, "results": out}
 
 
 # stopping tolerance of the batched mix (config 5) at matched accuracy: the
