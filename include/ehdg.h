@@ -162,6 +162,13 @@ typedef struct {
                                   by 1D passes per face (hexahedra, one shared transport
                                   operator): per element 2 NQFS q + NQFS + rows NB FMAs per
                                   sweep, NB = (p+1)^3 - (p-1)^3 boundary nodes */
+  int warm_start;              /* 1 if, after a step with at least one sweep, the next step
+                                  starts from that step's final trace instead of forming the
+                                  trace formula of u^n (Algorithm 1's initial trace): the last
+                                  sweep wrote Ey u^n at every owned point, so only the inflow
+                                  boundary points are recomputed from the new boundary data
+                                  (backward Euler or steady transport on hexahedra with no
+                                  beta.n = 0 point). ehdg_set_state starts cold again. */
 } ehdg_info;
 
 /* Structured N0 x N1 (x N2) mesh of the box [lo, hi] with the numbering

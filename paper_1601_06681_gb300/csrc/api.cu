@@ -951,6 +951,8 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
   TRYC(dalloc(c, &c.tc_err, 1));
   CKC(cudaMemsetAsync(c.tc_err, 0, sizeof(int), c.stream));
   TRYC(dalloc(c, &c.it, 1));
+  TRYC(dalloc(c, &c.warm, 1));
+  CKC(cudaMemsetAsync(c.warm, 0, sizeof(int), c.stream));
   TRYC(dalloc(c, &c.hist, (size_t)c.max_iter));
   CKC(cudaMallocHost(&c.it_host, sizeof(IterState)));
   CKC(cudaMemsetAsync(c.u, 0, sizeof(double) * state, c.stream));
@@ -1008,6 +1010,9 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
           tf.push_back((int32_t)f);
         }
     c.n_tan = (int64_t)tg.size();
+    // 2D contexts keep the cold start, so that the batched loop's once-per-step
+    // kernels (2D only) and solo runs stay equal bit for bit
+    c.warm_ok = c.dim == 3 && c.scheme != EHDG_CN && c.n_tan == 0;
     if (c.n_tan > 0) {
       TRYC(dalloc(c, &c.tan_g, tg.size()));
       TRYC(dalloc(c, &c.tan_face, tf.size()));
@@ -1056,6 +1061,7 @@ ehdg_status ehdg_get_info(ehdg_ctx h, ehdg_info* out) {
   out->device_bytes = c.bytes;
   out->sweep_rows = c.sweep_rows;
   out->sum_factorised = c.use_sf ? 1 : 0;
+  out->warm_start = c.warm_ok ? 1 : 0;
   return EHDG_OK;
 }
 
@@ -1112,6 +1118,8 @@ ehdg_status ehdg_set_state(ehdg_ctx h, const double* u, const double* uhat, int 
   Ctx& c = h->c;
   const size_t trace = (size_t)c.Nqf * c.nface;
   TRY(upload(c, c.u, u, c.nel, c.n, on_device));
+  // a new state: the next step forms its initial trace from u (cold start)
+  CK(cudaMemsetAsync(c.warm, 0, sizeof(int), c.stream));
   // the state's own level: boundary data of this level on both sides of CN's average
   CK(cudaMemcpyAsync(c.gb_old, c.gb, sizeof(double) * trace, cudaMemcpyDeviceToDevice, c.stream));
   if (uhat) {

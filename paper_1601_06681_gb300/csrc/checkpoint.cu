@@ -16,13 +16,14 @@ std::vector<std::pair<void*, size_t>> ehdg::state_arrays(Ctx& c) {
   const size_t state = sizeof(double) * (size_t)c.n * c.nel;
   const size_t trace = sizeof(double) * (size_t)c.Nqf * c.nface;
   return {{c.u, state},      {c.uhat, trace},       {c.uhat_n, trace}, {c.gb, trace},
-          {c.gb_old, trace}, {c.force, state},      {c.force_old, state}};
+          {c.gb_old, trace}, {c.force, state},      {c.force_old, state},
+          {c.warm, sizeof(int)}};
 }
 
 namespace {
 
 constexpr uint32_t kMagic = 0x47444845u;   // "EHDG"
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;   // 2: the warm-start flag joins the state
 
 struct Crc32Table {
   uint32_t t[256];

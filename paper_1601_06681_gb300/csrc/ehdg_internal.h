@@ -187,6 +187,15 @@ struct Ctx {
   double* partials = nullptr;    // residual block partials
   int n_partials = 0;
   IterState* it = nullptr;
+  // Warm start of the initial trace (backward Euler / steady transport on
+  // hexahedra without beta.n = 0 points): *warm = 1 on the device while slot 0
+  // of uhat holds the previous step's final trace uhat^K and u the
+  // reconstruction from uhat^{K-1}. The last sweep wrote uhat^K = Ey u at every
+  // owned point, which is the trace formula of u^n there, so the next step
+  // starts from slot 0 and recomputes only the inflow boundary points from the
+  // new boundary data, and the step kernel skips Y0 = Ey u^n.
+  int* warm = nullptr;           // [1] device flag (part of the saved state)
+  bool warm_ok = false;          // this context qualifies
   double* hist = nullptr;        // [max_iter]
   double* staging = nullptr;     // [max(state,trace)] transposition buffer
   IterState* it_host = nullptr;  // pinned

@@ -505,6 +505,7 @@ cudaError_t launch_step(Ctx& c) {
   s.G = c.G;
   s.Gy = c.Gy;
   s.Y = c.Y;
+  s.warm = c.warm_ok ? c.warm : nullptr;
   s.g_ready = 0;
   s.sf_ey = 0;
   if (c.use_ozaki && c.oz_step.img) {
@@ -715,6 +716,7 @@ struct FaceParams {
   double* hist;
   int graph_mode;               // set the while-node condition from the last block
   cudaGraphConditionalHandle handle;
+  const int* warm;              // initial mode: warm start flag (or null)
 };
 
 constexpr int kFaceBlock = 256;
@@ -737,6 +739,9 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
                    (int64_t)gf * nface;
   const double wg = p.fw[gf];
   const int64_t ym_off = (int64_t)gf * nel;   // + (local face * Nqf) * nel + elem
+  // warm start: slot 0 holds the previous step's final trace, the trace
+  // formula of u^n at every point but the inflow boundary ones
+  const bool warm = p.mode != kFaceIterate && p.warm && *p.warm;
   double acc = 0.0;
   for (int64_t face = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; face < nface;
        face += (int64_t)gridDim.x * blockDim.x) {
@@ -745,7 +750,11 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
     const int fm = p.geo.face_local[face];
     const int fpl = p.geo.face_local[nface + face];
     double uh;
-    if (p.pde == EHDG_TRANSPORT) {
+    if (warm) {
+      // no point has beta.n = 0 here; inflow boundary points take the new data
+      const int64_t pt = (int64_t)gf * nface + face;
+      uh = (ep < 0 && p.sgn[pt] < 0) ? p.gb[pt] : uh_new[face];
+    } else if (p.pde == EHDG_TRANSPORT) {
       uh = transport_trace_point(nel, nface, p.Nqf, p.cn, p.geo.face_elem, p.geo.face_local,
                                  p.sgn, p.Y, p.gb, p.gb_old, gf, face);
     } else {
@@ -826,6 +835,7 @@ cudaError_t launch_face(Ctx& c, int mode, int graph_mode) {
   p.geo = c.geo;
   p.pde = c.pde;
   p.mode = mode;
+  p.warm = c.warm_ok ? c.warm : nullptr;
   p.cn = (c.scheme == EHDG_CN) ? 1 : 0;
   p.Nqf = c.Nqf;
   p.tol = c.tol;
@@ -874,8 +884,10 @@ __global__ void __launch_bounds__(32 * kStepT) k_final(const FinalParams p) {
 // The final trace uhat^{K} (slot K&1) becomes the state's trace in slot 0
 // (Crank-Nicolson: 2 vhat - uhat^n) and the previous-level copies are updated.
 __global__ void k_trace_end(int64_t total, int cn, const IterState* it, double* uhat,
-                            double* uhat_n, const double* gb, double* gb_old) {
+                            double* uhat_n, const double* gb, double* gb_old, int* warm) {
   const double* fin = uhat + (int64_t)(it->k & 1) * total;
+  // at least one sweep ran: its owned outputs are Ey of the reconstruction
+  if (warm && blockIdx.x == 0 && threadIdx.x == 0) *warm = it->k >= 1 ? 1 : 0;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
     double v = fin[t];
@@ -920,8 +932,8 @@ cudaError_t launch_final(Ctx& c) {
   }
   if (err != cudaSuccess) return err;
   const int64_t total = (int64_t)c.Nqf * c.nface;
-  k_trace_end<<<(int)((total + 255) / 256), 256, 0, c.stream>>>(total, p.cn, c.it, c.uhat,
-                                                                  c.uhat_n, c.gb, c.gb_old);
+  k_trace_end<<<(int)((total + 255) / 256), 256, 0, c.stream>>>(
+      total, p.cn, c.it, c.uhat, c.uhat_n, c.gb, c.gb_old, c.warm_ok ? c.warm : nullptr);
   return cudaGetLastError();
 }
 

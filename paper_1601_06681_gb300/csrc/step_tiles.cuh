@@ -40,6 +40,9 @@ struct StepParams {
   double* G;
   double* Gy;                   // [slot][nel], slot order of the element sweep
   double* Y;
+  // warm start (or null): while *warm is 1 the next initial trace comes from
+  // the previous step's final trace, so Y0 = Ey u^n is not formed
+  const int* warm;
 };
 
 // Psh: a shared operator P [n][n]; w, g: [n][32] scratch; sfw: the face
@@ -92,6 +95,7 @@ __device__ __forceinline__ void step_tile(const StepParams& s, const double* Psh
     }
   }
   __syncthreads();
+  const bool want_y0 = !(s.warm && *s.warm);
   if (s.sf_ey) {
     // Y0 = Ey u^n and Gy = Ey G on each row face: the face's nodes are a
     // (p+1) x (p+1) grid (tangential axes a < b), and Ey there is L x L, so
@@ -104,10 +108,14 @@ __device__ __forceinline__ void step_tile(const StepParams& s, const double* Psh
         double y = 0.0, gg = 0.0;
         if (live) {
           const int i0 = s.sf_base[rf] + ib * s.sf_sb[rf];
-          for (int ia = 0; ia < p1; ++ia) {
-            const int i = i0 + ia * s.sf_sa[rf];
-            y = fma(La[ia], s.u[i * ne + e], y);
-            gg = fma(La[ia], g[i * 32 + lane], gg);
+          if (want_y0) {
+            for (int ia = 0; ia < p1; ++ia) {
+              const int i = i0 + ia * s.sf_sa[rf];
+              y = fma(La[ia], s.u[i * ne + e], y);
+              gg = fma(La[ia], g[i * 32 + lane], gg);
+            }
+          } else {
+            for (int ia = 0; ia < p1; ++ia) gg = fma(La[ia], g[(i0 + ia * s.sf_sa[rf]) * 32 + lane], gg);
           }
         }
         sfw[((it * p1 + ib) * 2) * 32 + lane] = y;
@@ -122,12 +130,16 @@ __device__ __forceinline__ void step_tile(const StepParams& s, const double* Psh
       for (int g0 = 0; g0 < q; ++g0) {
         const double* src = sfw + ((rf * q + g0) * p1) * 2 * 32 + lane;
         double y = 0.0, gg = 0.0;
-        for (int ib = 0; ib < p1; ++ib) {
-          y = fma(Lb[ib], src[(ib * 2) * 32], y);
-          gg = fma(Lb[ib], src[(ib * 2 + 1) * 32], gg);
-        }
         const int gf = g0 + q * g1;
-        s.Y[(int64_t)(s.sf_face[rf] * s.Nqf + gf) * ne + e] = y;
+        if (want_y0) {
+          for (int ib = 0; ib < p1; ++ib) {
+            y = fma(Lb[ib], src[(ib * 2) * 32], y);
+            gg = fma(Lb[ib], src[(ib * 2 + 1) * 32], gg);
+          }
+          s.Y[(int64_t)(s.sf_face[rf] * s.Nqf + gf) * ne + e] = y;
+        } else {
+          for (int ib = 0; ib < p1; ++ib) gg = fma(Lb[ib], src[(ib * 2 + 1) * 32], gg);
+        }
         s.Gy[(int64_t)(rf * s.Nqf + gf) * ne + e] = gg;
       }
     }
@@ -142,13 +154,18 @@ __device__ __forceinline__ void step_tile(const StepParams& s, const double* Psh
   for (int j = t; j < nr; j += kStepT) {
     const int r = s.shared ? s.rows[j] : s.rowid[j * ne + e];
     double y0 = 0.0, gy = 0.0;
-    for (int k2 = 0; k2 < s.KE; ++k2) {
-      const double wv = s.ey_val[r * s.KE + k2];
-      const int i = s.ey_idx[r * s.KE + k2];
-      y0 = fma(wv, s.u[i * ne + e], y0);
-      gy = fma(wv, g[i * 32 + lane], gy);
+    if (want_y0) {
+      for (int k2 = 0; k2 < s.KE; ++k2) {
+        const double wv = s.ey_val[r * s.KE + k2];
+        const int i = s.ey_idx[r * s.KE + k2];
+        y0 = fma(wv, s.u[i * ne + e], y0);
+        gy = fma(wv, g[i * 32 + lane], gy);
+      }
+      s.Y[r * ne + e] = y0;
+    } else {
+      for (int k2 = 0; k2 < s.KE; ++k2)
+        gy = fma(s.ey_val[r * s.KE + k2], g[s.ey_idx[r * s.KE + k2] * 32 + lane], gy);
     }
-    s.Y[r * ne + e] = y0;
     s.Gy[j * ne + e] = gy;
   }
 }

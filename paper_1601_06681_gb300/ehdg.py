@@ -59,7 +59,8 @@ class Info(C.Structure):
                 ("q", C.c_int), ("Nqf", C.c_int), ("n_elem", C.c_int64), ("n_face", C.c_int64),
                 ("state_len", C.c_int64), ("trace_len", C.c_int64),
                 ("shared_operator", C.c_int), ("device_bytes", C.c_int64),
-                ("sweep_rows", C.c_int64), ("sum_factorised", C.c_int)]
+                ("sweep_rows", C.c_int64), ("sum_factorised", C.c_int),
+                ("warm_start", C.c_int)]
 
 
 _lib = None

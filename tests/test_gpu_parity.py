@@ -203,6 +203,46 @@ def test_steps_to_tolerance_match_oracle(ehdg, name):
     assert rel(uh, ouh) < RTOL
 
 
+@pytest.mark.parametrize("name, precision", [("3d_be_const_p3", "fp64"),
+                                             ("3d_be_const_p3", "fp64_emulated"),
+                                             ("3d_be_const_p3", "bf16"),
+                                             ("3d_be_variable", "fp64"),
+                                             ("3d_be_const_p1", "fp64")])
+def test_warm_start_of_the_initial_trace_equals_a_cold_start(ehdg, name, precision):
+    """3D backward Euler: from the second step on, the initial trace is the
+    previous step's final trace (the last sweep wrote Ey u^n at every owned
+    point) with the inflow boundary points recomputed. Starting every step
+    cold (set_state, which forms the trace formula of u^n) gives the same
+    iteration counts and the same state up to rounding."""
+    mesh, p, kw, prob, u0, g = make_case(name)
+    kw = dict(kw, precision=precision)
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        assert s.info["warm_start"] == 1
+        s.set_boundary(g)
+        s.set_state(u0)
+        it_warm = s.run(3)
+        uw, uhw = s.get_state()
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        it_cold = []
+        for _ in range(3):
+            it_cold += s.run(1)
+            u, _ = s.get_state()
+            s.set_state(u)
+        uc, uhc = s.get_state()
+    assert it_warm == it_cold
+    assert rel(uw, uc) < 1e-13 and rel(uhw, uhc) < 1e-13
+
+
+def test_warm_start_is_off_where_the_trace_formula_needs_both_sides(ehdg):
+    """Crank-Nicolson, points with beta.n = 0, and 2D keep the cold start."""
+    for name in ("3d_cn_const_p3", "3d_be_tangent_p2", "2d_be_const"):
+        mesh, p, kw, prob, u0, g = make_case(name)
+        with make_solver(ehdg, mesh, p, kw, prob) as s:
+            assert s.info["warm_start"] == 0, name
+
+
 def test_converged_step_equals_direct_hdg_solve(ehdg):
     mesh, p, kw, prob, u0, g = make_case("2d_be_const")
     with make_solver(ehdg, mesh, p, kw, prob, tol=1e-13, max_iter=2000) as s:
