@@ -223,13 +223,15 @@ ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
       // low-precision correction of uhat before the next FP64 sweep: m inner
       // sweeps (each timed on its own with profiling on), then the FP64 update
       const float* in = c.R32;
+      const bool fuse = tc_apply_fusable(c);   // the last inner sweep makes the FP64 update
       for (int j = 0; j < c.inner_sweeps; ++j) {
         float* out = correction_out(c, j);
+        const bool last = fuse && j == c.inner_sweeps - 1;
         CK(counted(c, EHDG_KERNEL_CORR, lp_sweep_launches(c),
-                   [&] { return launch_lp_sweep(c, in, out); }));
+                   [&] { return launch_lp_sweep(c, in, out, last); }));
         in = out;
       }
-      CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_apply(c, in); }));
+      if (!fuse) CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_apply(c, in); }));
     }
     if (c.pde == EHDG_TRANSPORT) {
       // element solve + trace formula + residual in one kernel (+ tangential points)

@@ -363,6 +363,9 @@ __device__ __forceinline__ void btc_fx_part(const BInst& I, int j, unsigned char
   q.out = I.d32 + (int64_t)(j & 1) * trace;
   q.Y32 = I.Y32;
   q.err = I.err;
+  q.apply_uhat = nullptr;     // the batched loop's FP64 update is its own launch
+  q.apply_k = nullptr;
+  q.apply_total = 0;
   const int64_t e = tile * kFxM + (threadIdx.x & (kFxM - 1));
   int fid[4];
 #pragma unroll
@@ -813,7 +816,9 @@ __global__ void __launch_bounds__(32 * kStepT) k_batch_final(const BInst* inst, 
 }
 
 // the final trace becomes the state's trace in slot 0 (Crank-Nicolson:
-// 2 vhat - uhat^n) and the previous-level copies are updated (items: chunks)
+// 2 vhat - uhat^n, and the previous-level copies are updated; backward Euler
+// reads neither copy, and with K even the final trace is in slot 0 already)
+// (items: chunks)
 __global__ void __launch_bounds__(256) k_batch_trace_end(const BInst* inst, const int* pre,
                                                          int n_inst) {
   const int n_items = pre[n_inst];
@@ -821,12 +826,17 @@ __global__ void __launch_bounds__(256) k_batch_trace_end(const BInst* inst, cons
     const int i = static_owner(pre, n_inst, it);
     const BInst& I = inst[i];
     const int64_t total = (int64_t)I.Nqf * I.nface;
-    const double* fin = I.uhat + (int64_t)(I.it->k & 1) * total;
+    const int K = I.it->k;
+    if (!I.cn && !(K & 1)) continue;
+    const double* fin = I.uhat + (int64_t)(K & 1) * total;
     const int64_t t0 = (int64_t)(it - pre[i]) * kApplyChunk;
     const int64_t t1 = std::min<int64_t>(t0 + kApplyChunk, total);
     for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-      double v = fin[t];
-      if (I.cn) v = 2.0 * v - I.uhat_n[t];
+      if (!I.cn) {
+        I.uhat[t] = fin[t];
+        continue;
+      }
+      const double v = 2.0 * fin[t] - I.uhat_n[t];
       I.uhat[t] = v;
       I.uhat_n[t] = v;
       I.gb_old[t] = I.gb[t];

@@ -280,7 +280,9 @@ cudaError_t launch_lp_sweep_tiled(Ctx& c, const float* in, float* out);   // FP3
 // mixed precision (mixed.cu)
 cudaError_t launch_hy_to_f32(Ctx& c);
 cudaError_t launch_correction(Ctx& c);                    // m inner sweeps + FP64 update
-cudaError_t launch_lp_sweep(Ctx& c, const float* in, float* out);   // one inner sweep
+// one inner sweep; fuse_apply: the last one also makes the FP64 update (only
+// where tc_apply_fusable; the caller then launches no separate update)
+cudaError_t launch_lp_sweep(Ctx& c, const float* in, float* out, bool fuse_apply = false);
 cudaError_t launch_apply(Ctx& c, const float* delta);       // uhat += delta in FP64
 float* correction_out(Ctx& c, int j);                       // output buffer of inner sweep j
 int lp_sweep_launches(const Ctx& c);                        // kernels of one inner sweep
@@ -298,7 +300,10 @@ std::vector<std::pair<void*, size_t>> state_arrays(Ctx& c);
 bool tc_supported(const Ctx& c);
 cudaError_t launch_gather_boundary(const Ctx& c, const double* src, double* dst);
 cudaError_t build_tc_image(Ctx& c);   // after the FP32 operator copy
-cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out);
+// fuse_apply (only where tc_apply_fusable): the last inner sweep applies the
+// correction to uhat in FP64 at the owned points instead of storing it
+cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out, bool fuse_apply = false);
+bool tc_apply_fusable(const Ctx& c);
 
 // Batched iteration loop of a batch's looped instances (batch_loop.cu): one
 // launch per kernel and iteration over every unconverged instance.

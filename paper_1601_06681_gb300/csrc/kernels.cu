@@ -882,16 +882,22 @@ __global__ void __launch_bounds__(32 * kStepT) k_final(const FinalParams p) {
 }
 
 // The final trace uhat^{K} (slot K&1) becomes the state's trace in slot 0
-// (Crank-Nicolson: 2 vhat - uhat^n) and the previous-level copies are updated.
+// (Crank-Nicolson: 2 vhat - uhat^n, and the previous-level copies uhat^n and
+// g_old are updated; backward Euler and steady solves read neither, and
+// with K even the final trace is in slot 0 already).
 __global__ void k_trace_end(int64_t total, int cn, const IterState* it, double* uhat,
                             double* uhat_n, const double* gb, double* gb_old, int* warm) {
   const double* fin = uhat + (int64_t)(it->k & 1) * total;
   // at least one sweep ran: its owned outputs are Ey of the reconstruction
   if (warm && blockIdx.x == 0 && threadIdx.x == 0) *warm = it->k >= 1 ? 1 : 0;
+  if (!cn && !(it->k & 1)) return;
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    double v = fin[t];
-    if (cn) v = 2.0 * v - uhat_n[t];
+    if (!cn) {
+      uhat[t] = fin[t];
+      continue;
+    }
+    const double v = 2.0 * fin[t] - uhat_n[t];
     uhat[t] = v;
     uhat_n[t] = v;
     gb_old[t] = gb[t];

@@ -226,7 +226,7 @@ cudaError_t launch_hy_to_f32(Ctx& c) {
 // One low-precision sweep of the correction equation: in -> out. TF32/BF16
 // run the element solve on the tensor cores (shared operator), FP32 on the
 // CUDA cores.
-cudaError_t launch_lp_sweep(Ctx& c, const float* in, float* out) {
+cudaError_t launch_lp_sweep(Ctx& c, const float* in, float* out, bool fuse_apply) {
   if (c.Hyt32 || c.Hyt16) {
     cudaError_t err = launch_lp_sweep_tiled(c, in, out);
     if (err != cudaSuccess) return err;
@@ -239,7 +239,7 @@ cudaError_t launch_lp_sweep(Ctx& c, const float* in, float* out) {
     return err;
   }
   if (c.precision == EHDG_MIXED_TF32 || c.precision == EHDG_MIXED_BF16) {
-    cudaError_t err = launch_lp_sweep_tc(c, in, out);
+    cudaError_t err = launch_lp_sweep_tc(c, in, out, fuse_apply);
     if (err != cudaSuccess) return err;
     if (c.pde == EHDG_TRANSPORT) {
       if (c.n_tan > 0) {
@@ -327,16 +327,18 @@ int lp_sweep_launches(const Ctx& c) {
 // sweep 0 reads R).
 float* correction_out(Ctx& c, int j) { return c.d32 + (int64_t)(j & 1) * c.Nqf * c.nface; }
 
-// The m inner sweeps and the FP64 update.
+// The m inner sweeps and the FP64 update (made by the last inner sweep where
+// tc_apply_fusable).
 cudaError_t launch_correction(Ctx& c) {
   const float* in = c.R32;
+  const bool fuse = tc_apply_fusable(c);
   for (int j = 0; j < c.inner_sweeps; ++j) {
     float* out = correction_out(c, j);
-    cudaError_t e = launch_lp_sweep(c, in, out);
+    cudaError_t e = launch_lp_sweep(c, in, out, fuse && j == c.inner_sweeps - 1);
     if (e != cudaSuccess) return e;
     in = out;
   }
-  return launch_apply(c, in);
+  return fuse ? cudaSuccess : launch_apply(c, in);
 }
 
 }  // namespace ehdg

@@ -41,6 +41,13 @@ struct TcFxParams {
   float* out;
   float* Y32;
   int* err;
+  // the APPLY form (the last inner sweep of a transport step without
+  // beta.n = 0 points): instead of storing the correction, apply it in FP64
+  // at the owned points, uhat slot K&1 = slot (K+1)&1 + delta with
+  // K = *apply_k (the FP64 update; points no element owns keep equal slots)
+  double* apply_uhat;           // [2][apply_total] trace ping-pong pair
+  const int* apply_k;
+  int64_t apply_total;
 };
 
 template <int F_>
@@ -91,7 +98,7 @@ __device__ __forceinline__ void fx_tmem_ld(uint32_t taddr, uint32_t (&v)[GN]) {
 // Thread part Q of element `row`: gathers its K range into registers (all
 // loads first), rounds and stores it into A; loads R at its owned points;
 // after the MMA, writes its points of every row face.
-template <int F_, int NQF, int BF16, int TPE, int Q>
+template <int F_, int NQF, int BF16, int TPE, int Q, bool APPLY = false>
 __device__ __forceinline__ void fx_tile(const TcFxParams& p, unsigned char* As, unsigned char* Bs,
                                         uint64_t* mbar, uint32_t tbase, uint32_t& phase,
                                         bool& failed, int64_t tile, const int (&fid)[F_]) {
@@ -177,17 +184,35 @@ __device__ __forceinline__ void fx_tile(const TcFxParams& p, unsigned char* As, 
   phase ^= 1u;
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tl = tbase + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)G0;
+  const double* asrc = nullptr;
+  double* adst = nullptr;
+  if constexpr (APPLY) {
+    const int K = *p.apply_k;
+    adst = p.apply_uhat + (int64_t)(K & 1) * p.apply_total;
+    asrc = p.apply_uhat + (int64_t)((K + 1) & 1) * p.apply_total;
+  }
   // owned row faces: the new correction at the element's outflow points
 #pragma unroll
   for (int i = 0; i < NUP; ++i) {
     if (i >= p.n_up_f) break;
+    double sv[GN];   // APPLY: the update's FP64 trace values, loaded before the TMEM read
+    if (APPLY && live) {
+#pragma unroll
+      for (int q = 0; q < GN; ++q) sv[q] = asrc[(uint32_t)(G0 + q) * nface + (uint32_t)fo[i]];
+    }
     uint32_t a[GN];
     fx_tmem_ld<GN, WIDE>(tl + (uint32_t)(i * NQF), a);
     asm volatile("tcgen05.wait::ld.sync.aligned;");
     if (live) {
 #pragma unroll
-      for (int q = 0; q < GN; ++q)
-        p.out[(uint32_t)(G0 + q) * nface + (uint32_t)fo[i]] = rv[i][q] + __uint_as_float(a[q]);
+      for (int q = 0; q < GN; ++q) {
+        const uint32_t pt = (uint32_t)(G0 + q) * nface + (uint32_t)fo[i];
+        const float d = rv[i][q] + __uint_as_float(a[q]);
+        if constexpr (APPLY)
+          adst[pt] = sv[q] + (double)d;
+        else
+          p.out[pt] = d;
+      }
     }
   }
   // the other row faces (tangential points; every face for shallow water)

@@ -272,9 +272,8 @@ __global__ void __launch_bounds__(kTcThreads) k_sweep_tc(const TcParams p) {
 // shared-memory image, from setup. The MMAs (operands, K steps, descriptors)
 // are those of the general form, so both give the same values bit for bit.
 
-template <int F_, int NQF, int BF16, int TPE>
-__global__ void __launch_bounds__(128 * TPE)
-    k_sweep_tc_fx(const __grid_constant__ TcFxParams p) {
+template <int F_, int NQF, int BF16, int TPE, bool APPLY>
+__device__ __forceinline__ void fx_sweep(const TcFxParams& p) {
   using S = FxShape<F_, NQF, BF16, TPE>;
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar;
@@ -320,16 +319,16 @@ __global__ void __launch_bounds__(128 * TPE)
     for (int f = 0; f < F_; ++f) fn[f] = e2 < ne ? p.elem_face[f * ne + e2] : 0;
     // parts are warp-uniform (128 threads each)
     if (part == 0) {
-      fx_tile<F_, NQF, BF16, TPE, 0>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
+      fx_tile<F_, NQF, BF16, TPE, 0, APPLY>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
     } else if constexpr (TPE == 2) {
-      fx_tile<F_, NQF, BF16, TPE, 1>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
+      fx_tile<F_, NQF, BF16, TPE, 1, APPLY>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
     } else {
       if (part == 1)
-        fx_tile<F_, NQF, BF16, TPE, 1>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
+        fx_tile<F_, NQF, BF16, TPE, 1, APPLY>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
       else if (part == 2)
-        fx_tile<F_, NQF, BF16, TPE, 2>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
+        fx_tile<F_, NQF, BF16, TPE, 2, APPLY>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
       else
-        fx_tile<F_, NQF, BF16, TPE, 3>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
+        fx_tile<F_, NQF, BF16, TPE, 3, APPLY>(p, As, Bs, &mbar, tbase, phase, failed, tile, fid);
     }
     // every thread's TMEM reads of this tile precede the next tile's MMA
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -338,6 +337,21 @@ __global__ void __launch_bounds__(128 * TPE)
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase),
                  "r"(p.ncols));
+}
+
+template <int F_, int NQF, int BF16, int TPE>
+__global__ void __launch_bounds__(128 * TPE)
+    k_sweep_tc_fx(const __grid_constant__ TcFxParams p) {
+  fx_sweep<F_, NQF, BF16, TPE, false>(p);
+}
+
+// the last inner sweep, which also makes the FP64 update (its own kernel:
+// the update's loads raise its registers, not the plain form's; held to
+// three blocks per SM it spilled and ran slower, measured at 64^3)
+template <int F_, int NQF, int BF16, int TPE>
+__global__ void __launch_bounds__(128 * TPE)
+    k_sweep_tc_fx_apply(const __grid_constant__ TcFxParams p) {
+  fx_sweep<F_, NQF, BF16, TPE, true>(p);
 }
 
 struct FxKernel {
@@ -351,32 +365,35 @@ constexpr int fx_tpe(int F_, int NQF, int BF16, int WANT) {
   return ((kp / WANT) % ch == 0 && NQF >= WANT) ? WANT : 2;
 }
 template <int F_, int NQF, int TPE>
-FxKernel fx_pick_kernel(int bf16) {
+FxKernel fx_pick_kernel(int bf16, bool apply) {
   constexpr int T0 = fx_tpe(F_, NQF, 0, TPE), T1 = fx_tpe(F_, NQF, 1, TPE);
   FxKernel k;
-  k.fn = bf16 ? k_sweep_tc_fx<F_, NQF, 1, T1> : k_sweep_tc_fx<F_, NQF, 0, T0>;
+  if (apply)
+    k.fn = bf16 ? k_sweep_tc_fx_apply<F_, NQF, 1, T1> : k_sweep_tc_fx_apply<F_, NQF, 0, T0>;
+  else
+    k.fn = bf16 ? k_sweep_tc_fx<F_, NQF, 1, T1> : k_sweep_tc_fx<F_, NQF, 0, T0>;
   k.threads = 128 * (bf16 ? T1 : T0);
   return k;
 }
 // quadrilaterals with 2..7 points per edge, hexahedra with 2x2, 3x3, 4x4 per
 // face; two threads per element (four measured slower at 64^3, p = 3: one
 // block of 512 threads per SM at 64 registers against three of 256)
-FxKernel fx_kernel(int F, int Nqf, int bf16) {
+FxKernel fx_kernel(int F, int Nqf, int bf16, bool apply = false) {
   if (F == 4) {
     switch (Nqf) {
-      case 2: return fx_pick_kernel<4, 2, 2>(bf16);
-      case 3: return fx_pick_kernel<4, 3, 2>(bf16);
-      case 4: return fx_pick_kernel<4, 4, 2>(bf16);
-      case 5: return fx_pick_kernel<4, 5, 2>(bf16);
-      case 6: return fx_pick_kernel<4, 6, 2>(bf16);
-      case 7: return fx_pick_kernel<4, 7, 2>(bf16);
+      case 2: return fx_pick_kernel<4, 2, 2>(bf16, apply);
+      case 3: return fx_pick_kernel<4, 3, 2>(bf16, apply);
+      case 4: return fx_pick_kernel<4, 4, 2>(bf16, apply);
+      case 5: return fx_pick_kernel<4, 5, 2>(bf16, apply);
+      case 6: return fx_pick_kernel<4, 6, 2>(bf16, apply);
+      case 7: return fx_pick_kernel<4, 7, 2>(bf16, apply);
       default: break;
     }
   } else if (F == 6) {
     switch (Nqf) {
-      case 4: return fx_pick_kernel<6, 4, 2>(bf16);
-      case 9: return fx_pick_kernel<6, 9, 2>(bf16);
-      case 16: return fx_pick_kernel<6, 16, 2>(bf16);
+      case 4: return fx_pick_kernel<6, 4, 2>(bf16, apply);
+      case 9: return fx_pick_kernel<6, 9, 2>(bf16, apply);
+      case 16: return fx_pick_kernel<6, 16, 2>(bf16, apply);
       default: break;
     }
   }
@@ -475,7 +492,12 @@ cudaError_t build_tc_image(Ctx& c) {
   return cudaSuccess;
 }
 
-cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
+bool tc_apply_fusable(const Ctx& c) {
+  return c.tc_fx && c.tc_img && c.pde == EHDG_TRANSPORT && c.n_tan == 0 &&
+         (c.precision == EHDG_MIXED_TF32 || c.precision == EHDG_MIXED_BF16);
+}
+
+cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out, bool fuse_apply) {
   const TcShape t = tc_shape(c);
   if (c.tc_fx && c.tc_img) {
     TcFxParams q;
@@ -494,8 +516,11 @@ cudaError_t launch_lp_sweep_tc(Ctx& c, const float* in, float* out) {
     q.out = out;
     q.Y32 = c.Y32;
     q.err = c.tc_err;
+    q.apply_uhat = fuse_apply ? c.uhat : nullptr;
+    q.apply_k = fuse_apply ? &c.it->k : nullptr;
+    q.apply_total = (int64_t)c.Nqf * c.nface;
     const size_t smem = (size_t)(t.Np + kTcM) * t.Kp * (t.bf16 ? 2 : 4) + 1024;
-    const FxKernel kern = fx_kernel(c.F, c.Nqf, t.bf16);
+    const FxKernel kern = fx_kernel(c.F, c.Nqf, t.bf16, fuse_apply);
     cudaError_t err = fn_smem((const void*)kern.fn, smem);
     if (err != cudaSuccess) return err;
     // favour shared memory over L1 so several tiles' blocks fit per SM
