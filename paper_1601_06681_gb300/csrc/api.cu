@@ -204,7 +204,8 @@ ehdg_status check_tc_err(Ctx& c) {
 ehdg_status run_step(Ctx& c, int fixed_iters, int* iters, double* res) {
   CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_reset_iter(c); }));
   CK(counted(c, EHDG_KERNEL_STEP, step_launches(c), [&] { return launch_step(c); }));
-  CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceInitial); }));
+  CK(counted(c, EHDG_KERNEL_FACE, face_launches(c, kFaceInitial),
+             [&] { return launch_face(c, kFaceInitial); }));
   const int n_it = fixed_iters > 0 ? fixed_iters : c.max_iter;
   bool persist = fixed_iters <= 0 && persistent_sweep_ok(c);
   if (persist) {   // every iteration of the step in one cooperative launch
@@ -439,11 +440,12 @@ ehdg_status run_graph(Ctx& c, int n_steps, int* iters_per_step, double* res) {
     if (first == EHDG_OK && c.step_status_h[s] != EHDG_OK) first = (ehdg_status)c.step_status_h[s];
   }
   c.launches[EHDG_KERNEL_ELEM] += c.graph_persist ? n_steps : sweeps;
-  c.launches[EHDG_KERNEL_FACE] +=
-      n_steps + ((c.pde == EHDG_TRANSPORT) ? (c.n_tan > 0 ? sweeps : 0) : sweeps);
+  c.launches[EHDG_KERNEL_FACE] += (int64_t)n_steps * face_launches(c, kFaceInitial) +
+                                   ((c.pde == EHDG_TRANSPORT) ? (c.n_tan > 0 ? sweeps : 0) : sweeps);
   if (c.mixed) {
     c.launches[EHDG_KERNEL_CORR] += (sweeps - n_steps) * c.inner_sweeps * lp_sweep_launches(c);
-    c.launches[EHDG_KERNEL_AUX] += sweeps - n_steps;
+    // the FP64 update: its own launch unless the last inner sweep makes it
+    if (!tc_apply_fusable(c)) c.launches[EHDG_KERNEL_AUX] += sweeps - n_steps;
   }
   c.last_iters = n_steps > 0 ? std::min(c.step_iters_h[n_steps - 1], c.max_iter) : 0;
   if (res) *res = c.it_host->r_last;
@@ -1128,7 +1130,8 @@ ehdg_status ehdg_set_state(ehdg_ctx h, const double* u, const double* uhat, int 
     TRY(upload(c, c.uhat, uhat, c.nface, c.Nqf, on_device));
   } else {
     CK(counted(c, EHDG_KERNEL_AUX, 1, [&] { return launch_extract(c); }));
-    CK(counted(c, EHDG_KERNEL_FACE, 1, [&] { return launch_face(c, kFaceInitial); }));
+    CK(counted(c, EHDG_KERNEL_FACE, face_launches(c, kFaceInitial),
+               [&] { return launch_face(c, kFaceInitial); }));
   }
   CK(cudaMemcpyAsync(c.uhat_n, c.uhat, sizeof(double) * trace, cudaMemcpyDeviceToDevice, c.stream));
   // device pointers are ordered on the context's stream like every later

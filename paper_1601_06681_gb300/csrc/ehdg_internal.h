@@ -333,6 +333,7 @@ struct BatchLoop {
 };
 
 enum FaceMode { kFaceInitial = 0, kFaceIterate = 1 };
+int face_launches(const Ctx& c, int mode);   // kernels one launch_face(c, mode) makes
 
 void set_last_error(const std::string& msg);
 // standalone weighted difference norm (residual.cu); its grid never exceeds

@@ -740,8 +740,10 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
   const double wg = p.fw[gf];
   const int64_t ym_off = (int64_t)gf * nel;   // + (local face * Nqf) * nel + elem
   // warm start: slot 0 holds the previous step's final trace, the trace
-  // formula of u^n at every point but the inflow boundary ones
-  const bool warm = p.mode != kFaceIterate && p.warm && *p.warm;
+  // formula of u^n at every point but the inflow boundary ones, which
+  // k_trace0_warm sets (every other point of slot 1 is written by the first
+  // sweep before any sweep reads it)
+  if (p.mode != kFaceIterate && p.warm && *p.warm) return;
   double acc = 0.0;
   for (int64_t face = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; face < nface;
        face += (int64_t)gridDim.x * blockDim.x) {
@@ -750,11 +752,7 @@ __global__ void __launch_bounds__(kFaceBlock) k_face(const FaceParams p) {
     const int fm = p.geo.face_local[face];
     const int fpl = p.geo.face_local[nface + face];
     double uh;
-    if (warm) {
-      // no point has beta.n = 0 here; inflow boundary points take the new data
-      const int64_t pt = (int64_t)gf * nface + face;
-      uh = (ep < 0 && p.sgn[pt] < 0) ? p.gb[pt] : uh_new[face];
-    } else if (p.pde == EHDG_TRANSPORT) {
+    if (p.pde == EHDG_TRANSPORT) {
       uh = transport_trace_point(nel, nface, p.Nqf, p.cn, p.geo.face_elem, p.geo.face_local,
                                  p.sgn, p.Y, p.gb, p.gb_old, gf, face);
     } else {
@@ -828,6 +826,29 @@ int face_grid_x(int64_t nface, int Nqf) {
   return gx < 1 ? 1 : (int)gx;
 }
 
+// Warm-start initial trace: the inflow boundary points (beta.n < 0 seen from
+// the inside; no point has beta.n = 0 where the warm start is on) take the
+// new step's boundary data in both slots. Nothing to do on a cold start.
+__global__ void k_trace0_warm(const int* warm, const int32_t* bface, int64_t n_bface, int Nqf,
+                              int64_t nface, const int8_t* sgn, const double* gb, double* uhat) {
+  if (!*warm) return;
+  const int64_t total = (int64_t)Nqf * nface;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n_bface * Nqf;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = t / Nqf;
+    const int g = (int)(t - b * Nqf);
+    const int64_t pt = (int64_t)g * nface + bface[b];
+    if (sgn[pt] < 0) {
+      uhat[pt] = gb[pt];
+      uhat[total + pt] = gb[pt];
+    }
+  }
+}
+
+int face_launches(const Ctx& c, int mode) {
+  return (mode == kFaceInitial && c.warm_ok && c.n_bface > 0) ? 2 : 1;
+}
+
 cudaError_t launch_face(Ctx& c, int mode, int graph_mode) {
   FaceParams p;
   p.graph_mode = graph_mode;
@@ -861,6 +882,12 @@ cudaError_t launch_face(Ctx& c, int mode, int graph_mode) {
   p.hist = c.hist;
   const dim3 grid(face_grid_x(c.nface, c.Nqf), c.Nqf);
   k_face<<<grid, kFaceBlock, 0, c.stream>>>(p);
+  cudaError_t err = cudaGetLastError();
+  if (err != cudaSuccess || face_launches(c, mode) < 2) return err;
+  const int64_t nb = c.n_bface * c.Nqf;
+  const int g2 = (int)std::min<int64_t>((nb + 255) / 256, 152 * 8);
+  k_trace0_warm<<<g2, 256, 0, c.stream>>>(c.warm, c.bface, c.n_bface, c.Nqf, c.nface, c.sgn,
+                                           c.gb, c.uhat);
   return cudaGetLastError();
 }
 
