@@ -838,7 +838,8 @@ def run_headline(args):
     if not args.no_batch:
         # the batched mix (256 instances), at its matched-accuracy tolerance:
         # the batched loop and the autotuned schedule, FP64 and mixed
-        bout, binfo = batch_variants(args, ["fp64", "fp32", "tf32", "fp64+tuned", "fp32+tuned",
+        bout, binfo = batch_variants(args, ["fp64", "fp32", "tf32", "fp64+persistent",
+                                            "fp32+persistent", "fp64+tuned", "fp32+tuned",
                                             "tf32+tuned"], TOL_MATCHED_BATCH)
         batch = {"metric": "instances/s (one graph launch per step)", "config": binfo,
                  "results": bout}
@@ -1197,9 +1198,11 @@ def batch_variants(args, variants, tol, profile_loop=True):
     together, one graph launch per time step, every instance to `tol`.
     Variant "prec" iterates in the batched loop (one launch per kernel and
     iteration over every unconverged instance); "prec+branches" runs every
-    instance's own loop on the graph's branches; "prec+tuned" takes the
-    schedule from ehdg_batch_autotune_schedule (loop, or branches with
-    16/32/64 of them); "+inner" tunes the inner sweep count m; "+tiles" the
+    instance's own loop on the graph's branches; "prec+persistent" the
+    loop's persistent form (every iteration of a step in one launch, FP64 and
+    FP32 corrections); "prec+tuned" takes the schedule from
+    ehdg_batch_autotune_schedule (loop, persistent, or branches with 16/32/64
+    of them); "+inner" tunes the inner sweep count m; "+tiles" the
     fused FP64 sweep's tile. Branch counts come from the batch autotuners,
     timed over the same run after a warm-up run (setup, outside the timed
     run). Every variant's final states are compared with the instances' FP64
@@ -1247,6 +1250,8 @@ def batch_variants(args, variants, tol, profile_loop=True):
         b = ehdg.Batch(make_specs(base, opt, tol), stream=stream)
         if opt == "branches":
             b.set_loop(False)
+        elif opt == "persistent":
+            b.set_loop("persistent")
         setup = time.perf_counter() - t0
         inputs = start(b)
 
@@ -1271,8 +1276,8 @@ def batch_variants(args, variants, tol, profile_loop=True):
         else:
             chains, _ = b.autotune_chains()
         if opt == "tuned":
-            loop_on, chains, _ = b.autotune_schedule((16, 32, 64))
-            tuned["schedule"] = "loop" if loop_on else "branches"
+            mode, chains, _ = b.autotune_schedule((16, 32, 64))
+            tuned["schedule"] = ("branches", "loop", "persistent")[mode]
         one_run()                                     # recapture with the tuned settings
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -1284,7 +1289,7 @@ def batch_variants(args, variants, tol, profile_loop=True):
                      "p99_instance_ms": float(np.percentile(times, 99) * 1e3),
                      "sweeps_total": int(iters.sum()), "chains": chains,
                      "rel_l2_vs_fp64_fixed_point": accuracy(b), **tuned}
-        if (profile_loop and opt not in ("branches", "tuned")
+        if (profile_loop and opt not in ("branches", "tuned", "emulated_outer")
                 and base in ("fp64", "fp32", "tf32", "bf16")):
             # kernel accounting of the batched loop: the same run with its
             # steps driven from the host and every launch timed
@@ -1323,9 +1328,10 @@ def batch_workload(args):
     torch.cuda.set_device(0)
     build.build()
     ehdg.load()
-    variants = ["fp64", "fp32", "tf32", "bf16", "fp64+branches", "fp32+branches",
-                "tf32+branches", "fp64+tuned", "fp32+tuned", "tf32+tuned", "fp32+inner",
-                "tf32+inner", "fp64_emulated", "tf32+emulated_outer"]
+    variants = ["fp64", "fp32", "tf32", "bf16", "fp64+persistent", "fp32+persistent",
+                "fp64+branches", "fp32+branches", "tf32+branches", "fp64+tuned", "fp32+tuned",
+                "tf32+tuned", "fp32+inner", "tf32+inner", "fp64_emulated",
+                "tf32+emulated_outer"]
     if args.batch_variants:
         variants = [v for v in args.batch_variants.split(",") if v]
     tol = args.batch_tol if args.batch_tol > 0 else TOL_MATCHED_BATCH

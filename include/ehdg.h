@@ -302,8 +302,15 @@ ehdg_status ehdg_batch_set_chains(ehdg_batch b, int k);
  * history and stopping test, Algorithm 1 of Sec. 3 per instance). The other
  * instances run their own loops on the branches, concurrently. An instance's
  * iterates are the same, bit for bit, either way. on = 0 runs every instance
- * on the branches. The graph is recaptured at the next run. EHDG_ERR_INVALID
- * for a NULL batch. */
+ * on the branches. on = 2 is the loop's persistent form where every looped
+ * instance is FP64 or has FP32 corrections (else on = 1): all iterations of a
+ * step in ONE launch, each instance at its own pace -- the block that
+ * completes a stage of an instance (its FP64 sweep, a correction sweep, the
+ * FP64 update) publishes the next stage's work items to a ring in device
+ * memory, and every block takes the next item of the ring; waits on the ring
+ * are bounded (a wait that gives up makes the step EHDG_ERR_TIMEOUT). The
+ * graph is recaptured at the next run. EHDG_ERR_INVALID for a NULL batch or
+ * a mode outside 0..2. */
 ehdg_status ehdg_batch_set_loop(ehdg_batch b, int on);
 /* Kernel accounting of the batched loop (a diagnostic; the paper has no
  * counterpart). With profiling on (which resets the counters),
@@ -329,13 +336,15 @@ ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* candidates, int 
                                        int* best, double* best_ms);
 /* Autotuner for the schedule of a batch step (the paper has no counterpart):
  * times the batched loop (every instance it supports iterates in one loop of
- * launches over the unconverged instances) against every instance's own
- * loop on k graph branches, k from chain_candidates (entries < 1 skipped),
- * and keeps the fastest. Same protocol as ehdg_batch_autotune_chains (each
- * candidate timed over the batch's last run, states restored). *loop_on (may
- * be NULL) receives 1 for the loop, *chains the branch count kept, *best_ms
- * the time of the kept schedule. Both schedules give the same iterates bit
- * for bit. EHDG_ERR_INVALID for a NULL batch or no candidates. */
+ * launches over the unconverged instances), its persistent form
+ * (ehdg_batch_set_loop mode 2) and every instance's own loop on k graph
+ * branches, k from chain_candidates (entries < 1 skipped), and keeps the
+ * fastest. Same protocol as ehdg_batch_autotune_chains (each candidate timed
+ * over the batch's last run, states restored). *loop_on (may be NULL)
+ * receives the kept ehdg_batch_set_loop mode (0 branches, 1 loop, 2
+ * persistent), *chains the branch count kept, *best_ms the time of the kept
+ * schedule. Every schedule gives the same iterates bit for bit.
+ * EHDG_ERR_INVALID for a NULL batch or no candidates. */
 ehdg_status ehdg_batch_autotune_schedule(ehdg_batch b, const int* chain_candidates,
                                          int n_candidates, int* loop_on, int* chains,
                                          double* best_ms);

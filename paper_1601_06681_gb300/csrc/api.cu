@@ -30,6 +30,9 @@ struct ehdg_batch_s {
   // batched iteration loop (one launch per kernel and iteration over every
   // unconverged instance) for the instances it supports
   bool use_loop = true;
+  // its persistent form (every iteration of a step in one launch), where the
+  // looped instances allow it (FP64 or FP32 corrections)
+  bool use_persist = false;
   int last_run_steps = 0;               // steps of the last run: what the autotuners time
   // kernel accounting of the batched loop (ehdg_batch_set_profiling)
   bool profiling = false;
@@ -1422,8 +1425,16 @@ static ehdg_status batch_build_graph(ehdg_batch b) {
       if ((e = launch_stamp(s, b->t_start, b->t_acc, i, 1)) != cudaSuccess) break;
     }
   }
+  // the looped instances in the persistent form: before the loop, one launch
+  // for every iteration, after it
+  const bool persist = b->use_persist && b->loop.persist_ok();
+  if (e == cudaSuccess && st == EHDG_OK && persist) {
+    e = b->loop.launch_pre(b->cap, 0, 0);
+    if (e == cudaSuccess) e = b->loop.launch_persist(b->cap);
+    if (e == cudaSuccess) e = b->loop.launch_post(b->cap);
+  }
   // the looped instances: before the loop, the loop, after it
-  if (e == cudaSuccess && st == EHDG_OK) {
+  if (e == cudaSuccess && st == EHDG_OK && !persist) {
     cudaStreamCaptureStatus cst;
     cudaGraph_t g = nullptr;
     cudaGraphConditionalHandle handle;
@@ -1564,7 +1575,8 @@ ehdg_status ehdg_batch_run(ehdg_batch b, int n_steps, int* iters, double* inst_t
     int max_iter = 1;
     for (int i = 0; i < n; ++i) max_iter = std::max(max_iter, b->inst[i]->c.max_iter);
     for (int s = 0; s < n_steps; ++s)
-      CK(b->loop.run_step_profiled(b->stream, max_iter, b->prof_ms, b->prof_launches));
+      CK(b->loop.run_step_profiled(b->stream, max_iter, b->prof_ms, b->prof_launches,
+                                   b->use_persist));
   } else {
     for (int s = 0; s < n_steps; ++s) CK(cudaGraphLaunch(b->exec, b->stream));
   }
@@ -1629,9 +1641,10 @@ ehdg_status ehdg_batch_kernel_stats(ehdg_batch b, int kind, int64_t* launches, d
 }
 
 ehdg_status ehdg_batch_set_loop(ehdg_batch b, int on) {
-  if (!b) return fail(EHDG_ERR_INVALID, "NULL batch");
-  if ((on != 0) != b->use_loop) {
+  if (!b || on < 0 || on > 2) return fail(EHDG_ERR_INVALID, "NULL batch or bad mode");
+  if ((on != 0) != b->use_loop || (on == 2) != b->use_persist) {
     b->use_loop = on != 0;
+    b->use_persist = on == 2;
     batch_destroy_graph(b);
   }
   return EHDG_OK;
@@ -1742,37 +1755,41 @@ ehdg_status ehdg_batch_autotune_chains(ehdg_batch b, const int* cands, int n_can
 ehdg_status ehdg_batch_autotune_schedule(ehdg_batch b, const int* chain_cands, int n_cands,
                                          int* loop_on, int* chains, double* best_ms) {
   if (!b || !chain_cands || n_cands < 1) return fail(EHDG_ERR_INVALID, "bad argument");
-  const bool saved_loop = b->use_loop;
+  const bool saved_loop = b->use_loop, saved_persist = b->use_persist;
   const int saved_chains = b->chains;
-  // variant 0: the batched loop (branches keep the current count); variant
-  // q >= 1: every instance on the branches, chain_cands[q - 1] of them
-  std::vector<double> ms((size_t)n_cands + 1);
+  // variant 0: the batched loop, 1: its persistent form (branches keep the
+  // current count); variant q >= 2: every instance on the branches,
+  // chain_cands[q - 2] of them
+  std::vector<double> ms((size_t)n_cands + 2);
   const ehdg_status st = batch_time_variants(
-      b, n_cands + 1,
+      b, n_cands + 2,
       [&](int q) {
-        if (q > 0 && chain_cands[q - 1] < 1) return false;
-        b->use_loop = (q == 0);
-        if (q > 0) b->chains = chain_cands[q - 1];
+        if (q >= 2 && chain_cands[q - 2] < 1) return false;
+        b->use_loop = q < 2;
+        b->use_persist = q == 1;
+        if (q >= 2) b->chains = chain_cands[q - 2];
         return true;
       },
       ms.data());
   int best = -1;
   double t = 1e300;
   if (st == EHDG_OK)
-    for (int q = 0; q <= n_cands; ++q)
+    for (int q = 0; q < n_cands + 2; ++q)
       if (ms[q] < t) {
         t = ms[q];
         best = q;
       }
   if (best < 0) {
     b->use_loop = saved_loop;
+    b->use_persist = saved_persist;
     b->chains = saved_chains;
   } else {
-    b->use_loop = (best == 0);
-    b->chains = best == 0 ? saved_chains : chain_cands[best - 1];
+    b->use_loop = best < 2;
+    b->use_persist = best == 1;
+    b->chains = best < 2 ? saved_chains : chain_cands[best - 2];
   }
   batch_destroy_graph(b);
-  if (loop_on) *loop_on = b->use_loop ? 1 : 0;
+  if (loop_on) *loop_on = b->use_loop ? (b->use_persist ? 2 : 1) : 0;
   if (chains) *chains = b->chains;
   if (best_ms) *best_ms = t;
   return st;

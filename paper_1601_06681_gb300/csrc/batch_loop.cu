@@ -683,6 +683,265 @@ __global__ void __launch_bounds__(256) k_batch_apply(const BInst* inst, const in
 }
 
 // ---------------------------------------------------------------------------
+// Persistent form (FP64 and FP32-correction instances): every iteration of a
+// step in ONE launch. Each instance moves through its own stages -- the FP64
+// sweep, then for mixed precision its m correction sweeps and the FP64 update,
+// then the next FP64 sweep -- at its own pace: the block that completes an
+// instance's stage publishes the next stage's work items into a ring in device
+// memory, and every block takes the next item of the ring, whatever its
+// instance. A stage's items are published only after every item of the
+// instance's previous stage is done, and they run the same tile bodies as the
+// loop, so every instance computes its solo run's iterates bit for bit. No
+// block waits for another block's progress except through the ring, whose
+// polls are bounded: a wait that gives up sets an error flag and its block
+// leaves (the step then reports EHDG_ERR_TIMEOUT).
+// ---------------------------------------------------------------------------
+constexpr int kQCap = 1 << 16;                  // ring slots (a power of two)
+constexpr unsigned int kQWaitLimit = 1u << 24;  // polls of one slot before giving up
+// stage codes (an item packs stage << 24 | index, positive): 0 the FP64 sweep,
+// 1..m correction sweep s - 1 (m <= 64), 127 the FP64 update
+constexpr int kStSweep = 0, kStApply = 127;
+
+struct BQueue {
+  unsigned long long head;      // items claimed (monotonic over the batch's life)
+  unsigned long long tail;      // items published
+  int live;                     // instances still iterating in the current step
+  int err;                      // a poll gave up
+};
+
+__device__ __forceinline__ long long q_ld_acquire(const long long* p) {
+  long long v;
+  asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void q_st_release(long long* p, long long v) {
+  asm volatile("st.release.gpu.global.s64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Publish n items (inst, stage, 0..n-1): ring positions from one reservation
+// on the tail, each slot's payload before its sequence number (release).
+// Every thread of the block calls this.
+__device__ void q_publish(BQueue* q, long long* seq, int2* items, int inst, int stage, int n) {
+  __shared__ unsigned long long s_start;
+  if (threadIdx.x == 0) s_start = atomicAdd(&q->tail, (unsigned long long)n);
+  __syncthreads();
+  const unsigned long long st = s_start;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const unsigned long long w = st + (unsigned long long)k;
+    const int slot = (int)(w & (unsigned long long)(kQCap - 1));
+    items[slot] = make_int2(inst, (stage << 24) | k);
+    q_st_release(seq + slot, (long long)w);
+  }
+  __syncthreads();
+}
+
+// the first stage of an instance that still iterates after the pre-loop sweep
+__device__ __forceinline__ int2 first_stage(const BInst& I) {
+  return (I.tc && !I.mma && I.m > 0) ? make_int2(1, I.n_tiles128) : make_int2(kStSweep, I.n_tiles_pe);
+}
+
+// Start of a step's persistent loop (one block): claims restart at the
+// published end, and every instance the pre-loop sweep left iterating gets
+// its first stage.
+__global__ void k_batch_qinit(const BInst* inst, int n_inst, BQueue* q, long long* seq,
+                              int2* items, int* stage_cnt) {
+  if (threadIdx.x == 0) {
+    q->head = q->tail;
+    q->live = 0;
+    q->err = 0;
+  }
+  for (int i = threadIdx.x; i < n_inst; i += blockDim.x) stage_cnt[i] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_inst; i += blockDim.x) {
+    const BInst& I = inst[i];
+    if (!reinterpret_cast<volatile IterState*>(I.it)->cont) continue;
+    atomicAdd(&q->live, 1);
+    const int2 st = first_stage(I);
+    const unsigned long long s0 = atomicAdd(&q->tail, (unsigned long long)st.y);
+    for (int k = 0; k < st.y; ++k) {
+      const unsigned long long w = s0 + (unsigned long long)k;
+      const int slot = (int)(w & (unsigned long long)(kQCap - 1));
+      items[slot] = make_int2(i, (st.x << 24) | k);
+      q_st_release(seq + slot, (long long)w);
+    }
+  }
+}
+
+template <int NQ>
+__device__ __forceinline__ bool q_sweep_item(const BInst& I, const double* Hsh, int64_t tile) {
+  PeView v = {};
+  v.nel = I.nel;
+  v.nface = I.nface;
+  v.n_rows = I.n_rows;
+  v.n_up = I.n_up;
+  v.rows = I.rows;
+  v.elem_face = I.elem_face;
+  v.face_jf = I.face_jf;
+  v.fw = I.fw;
+  v.Gy = I.Gy;
+  v.Y = I.Y;
+  v.R_out = I.R_out;
+  v.partials = I.partials;
+  v.it = I.it;
+  v.hist = I.hist;
+  v.max_iter = I.max_iter;
+  v.tol = I.tol;
+  v.res_scale = I.res_scale;
+  v.uhat = I.uhat;
+  const int kk = reinterpret_cast<volatile IterState*>(I.it)->k;
+  const int64_t tlen = (int64_t)I.Nqf * I.nface;
+  const double* src = I.uhat + (int64_t)(kk & 1) * tlen;
+  double* dst = I.uhat + (int64_t)((kk + 1) & 1) * tlen;
+  return pe_tile<NQ, true>(v, Hsh, src, dst, tile, I.n_tiles_pe, 0, 0);
+}
+
+template <int NQ>
+__device__ __forceinline__ void q_corr_item(const BInst& I, const float* Hsh32, int j,
+                                            int64_t tile) {
+  const int64_t trace = (int64_t)I.Nqf * I.nface;
+  LpPeView v;
+  v.nel = I.nel;
+  v.nface = I.nface;
+  v.n_up = I.n_up;
+  v.rows = I.rows;
+  v.elem_face = I.elem_face;
+  v.R = I.R32;
+  v.in = j == 0 ? I.R32 : I.d32 + (int64_t)((j - 1) & 1) * trace;
+  v.out = I.d32 + (int64_t)(j & 1) * trace;
+  lp_pe_tile<NQ, true>(v, Hsh32, tile);
+}
+
+__global__ void __launch_bounds__(kPeTile) k_batch_persist(const BInst* inst, BQueue* q,
+                                                           long long* seq, int2* items,
+                                                           int* stage_cnt) {
+  extern __shared__ double sm[];
+  __shared__ int2 s_item;
+  __shared__ int s_flag;
+  const int tid = threadIdx.x;
+  int cur = -1, cur_kind = -1;             // the operator rows in shared memory
+  for (;;) {
+    if (tid == 0) {
+      const unsigned long long w = atomicAdd(&q->head, 1ull);
+      const int slot = (int)(w & (unsigned long long)(kQCap - 1));
+      int go = 0;
+      for (unsigned int n = 0;; ++n) {
+        if (q_ld_acquire(seq + slot) == (long long)w) {
+          s_item = __ldcg(items + slot);   // ordered after the acquire
+          go = 1;
+          break;
+        }
+        if (*reinterpret_cast<volatile int*>(&q->live) == 0 ||
+            *reinterpret_cast<volatile int*>(&q->err) != 0)
+          break;
+        if (n >= kQWaitLimit) {
+          atomicExch(&q->err, 1);
+          break;
+        }
+        if (n >= 32) __nanosleep(128);
+      }
+      s_flag = go;
+    }
+    __syncthreads();
+    if (!s_flag) break;
+    const int2 item = s_item;
+    const int i = item.x, stage = (int)((unsigned int)item.y >> 24), idx = item.y & 0xFFFFFF;
+    const BInst& I = inst[i];
+    const int nq = I.NQFS;
+    const int kind = stage == kStSweep ? 0 : (stage == kStApply ? 2 : 1);
+    if (kind != 2 && (i != cur || kind != cur_kind)) {
+      // every thread is past the previous item's reads of the rows
+      if (kind == 0) {
+        for (int t = tid; t < I.n_rows * nq; t += kPeTile) {
+          const int jj = t / nq, c = t - jj * nq;
+          sm[t] = I.Hy[I.rows[jj] * nq + c];
+        }
+      } else {
+        float* smf = reinterpret_cast<float*>(sm);
+        for (int t = tid; t < I.n_up * nq; t += kPeTile) {
+          const int jj = t / nq, c = t - jj * nq;
+          smf[t] = I.Hy32[I.rows[jj] * nq + c];
+        }
+      }
+      __syncthreads();
+      cur = i;
+      cur_kind = kind;
+    }
+    bool done;
+    if (kind == 0) {
+      switch (nq) {
+        case 8: done = q_sweep_item<8>(I, sm, idx); break;
+        case 12: done = q_sweep_item<12>(I, sm, idx); break;
+        case 16: done = q_sweep_item<16>(I, sm, idx); break;
+        case 20: done = q_sweep_item<20>(I, sm, idx); break;
+        case 24: done = q_sweep_item<24>(I, sm, idx); break;
+        default: done = q_sweep_item<28>(I, sm, idx); break;
+      }
+    } else {
+      if (kind == 1) {
+        const float* smf = reinterpret_cast<const float*>(sm);
+        const int j = stage - 1;
+        switch (nq) {
+          case 8: q_corr_item<8>(I, smf, j, idx); break;
+          case 12: q_corr_item<12>(I, smf, j, idx); break;
+          case 16: q_corr_item<16>(I, smf, j, idx); break;
+          case 20: q_corr_item<20>(I, smf, j, idx); break;
+          case 24: q_corr_item<24>(I, smf, j, idx); break;
+          default: q_corr_item<28>(I, smf, j, idx); break;
+        }
+      } else {
+        // the FP64 update (the loop's k_batch_apply on one chunk)
+        const int K = reinterpret_cast<volatile IterState*>(I.it)->k;
+        const int64_t total = (int64_t)I.Nqf * I.nface;
+        double* dst = I.uhat + (int64_t)(K & 1) * total;
+        const double* src = I.uhat + (int64_t)((K + 1) & 1) * total;
+        const float* delta = I.d32 + (int64_t)((I.m - 1) & 1) * total;
+        const int64_t t0 = (int64_t)idx * kApplyChunk;
+        const int64_t t1 = std::min<int64_t>(t0 + kApplyChunk, total);
+        for (int64_t t = t0 + tid; t < t1; t += kPeTile)
+          dst[t] = __ldcg(src + t) + (double)__ldcg(delta + t);
+      }
+      // the stage is done when its last item is
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        const int n = kind == 2 ? I.n_chunks : I.n_tiles128;
+        const int last = atomicAdd(&stage_cnt[i], 1) == n - 1;
+        if (last) {
+          stage_cnt[i] = 0;
+          __threadfence();
+        }
+        s_flag = last;
+      }
+      __syncthreads();
+      done = s_flag != 0;
+    }
+    if (!done) continue;
+    // the instance's next stage, or its end in this step
+    if (tid == 0) {
+      int2 nx = make_int2(-1, 0);
+      if (kind == 0) {
+        if (reinterpret_cast<volatile IterState*>(I.it)->cont) {
+          nx = first_stage(I);
+        } else {
+          *I.t_conv = global_ns();
+          __threadfence();
+          atomicSub(&q->live, 1);
+        }
+      } else if (kind == 1) {
+        nx = (stage < I.m) ? make_int2(stage + 1, I.n_tiles128) : make_int2(kStApply, I.n_chunks);
+      } else {
+        nx = make_int2(kStSweep, I.n_tiles_pe);
+      }
+      s_item = nx;
+    }
+    __syncthreads();
+    const int2 nx = s_item;
+    __syncthreads();
+    if (nx.x >= 0) q_publish(q, seq, items, i, nx.x, nx.y);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Once-per-step kernels of the looped instances, each one launch for all of
 // them; static work lists: pre[i] .. pre[i+1]-1 are instance i's items.
 // ---------------------------------------------------------------------------
@@ -846,11 +1105,13 @@ __global__ void __launch_bounds__(256) k_batch_trace_end(const BInst* inst, cons
 
 // the step's record (iterations, status) and the instance's time: from the
 // step's start to its convergence
-__global__ void k_batch_end(const BInst* inst, int n_inst) {
+__global__ void k_batch_end(const BInst* inst, int n_inst, const int* qerr) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n_inst) return;
   const BInst& I = inst[i];
   IterState* it = I.it;
+  // the persistent loop gave up a bounded wait: the step did not complete
+  if (qerr && *qerr && it->cont) it->status = EHDG_ERR_TIMEOUT;
   const int s = it->step;
   if (s >= 0 && s < I.step_cap) {
     I.step_iters[s] = it->k;
@@ -894,6 +1155,13 @@ struct BatchLoop::Impl {
   int lp_grid = 1;
   size_t lp_smem = 0;
   size_t sweep_smem = 0, tc_smem = 0;
+  // persistent form: the work ring and the per-instance stage counters
+  BQueue* d_q = nullptr;
+  long long* d_seq = nullptr;
+  int2* d_items = nullptr;
+  int* d_stage_cnt = nullptr;
+  int persist_grid = 1;
+  size_t persist_smem = 0;
 };
 
 BatchLoop::~BatchLoop() { release(); }
@@ -907,6 +1175,10 @@ void BatchLoop::release() {
   cudaFree(impl->d_bimg);
   cudaFree(impl->d_prech);
   cudaFree(impl->d_ticket);
+  cudaFree(impl->d_q);
+  cudaFree(impl->d_seq);
+  cudaFree(impl->d_items);
+  cudaFree(impl->d_stage_cnt);
   delete impl;
   impl = nullptr;
 }
@@ -1111,13 +1383,41 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     L.tc_grid = std::max(1, std::min(bpsm * device_sms(), L.n_tc));
     L.apply_grid = std::max(1, std::min(device_sms() * 8, L.n_apply));
   }
+  if (!L.any_mma) {
+    // the persistent form: one wave of resident blocks
+    if ((e = cudaMalloc(&L.d_q, sizeof(BQueue))) != cudaSuccess) return e;
+    if ((e = cudaMemset(L.d_q, 0, sizeof(BQueue))) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.d_seq, sizeof(long long) * kQCap)) != cudaSuccess) return e;
+    if ((e = cudaMemset(L.d_seq, 0xFF, sizeof(long long) * kQCap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.d_items, sizeof(int2) * kQCap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&L.d_stage_cnt, sizeof(int) * std::max(1, L.n_inst))) != cudaSuccess)
+      return e;
+    // a few KB (operator rows of one instance): no attribute needed
+    L.persist_smem = std::max(L.sweep_smem, L.lp_smem);
+    L.persist_grid = wave(k_batch_persist, kPeTile, L.persist_smem, 1 << 30);
+  }
   return cudaSuccess;
+}
+
+bool BatchLoop::persist_ok() const { return impl && impl->d_q; }
+
+// The persistent loop of a step (after launch_pre with graph_mode 0): the
+// ring's start, then one launch that runs every remaining iteration.
+cudaError_t BatchLoop::launch_persist(cudaStream_t s) {
+  Impl& L = *impl;
+  k_batch_qinit<<<1, 256, 0, s>>>(L.d_inst, L.n_inst, L.d_q, L.d_seq, L.d_items, L.d_stage_cnt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_batch_persist<<<L.persist_grid, kPeTile, L.persist_smem, s>>>(L.d_inst, L.d_q, L.d_seq,
+                                                                  L.d_items, L.d_stage_cnt);
+  return cudaGetLastError();
 }
 
 // Everything of a step before the loop, each kernel one launch for all the
 // looped instances: reset and start time, right-hand side, initial trace,
 // the work lists, and the first FP64 sweep (which sets the loop condition).
-cudaError_t BatchLoop::launch_pre(cudaStream_t s, cudaGraphConditionalHandle handle) {
+cudaError_t BatchLoop::launch_pre(cudaStream_t s, cudaGraphConditionalHandle handle,
+                                  int graph_mode) {
   Impl& L = *impl;
   cudaError_t e;
   k_batch_begin<<<(L.n_inst + 127) / 128, 128, 0, s>>>(L.d_inst, L.n_inst);
@@ -1131,7 +1431,8 @@ cudaError_t BatchLoop::launch_pre(cudaStream_t s, cudaGraphConditionalHandle han
                                                        L.d_lists);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_batch_sweep<<<L.sweep_grid, kPeTile, L.sweep_smem, s>>>(L.d_inst, L.d_counts, L.d_lists,
-                                                           L.n_inst, L.d_ticket, 1, handle);
+                                                           L.n_inst, L.d_ticket, graph_mode,
+                                                           handle);
   return cudaGetLastError();
 }
 
@@ -1145,7 +1446,8 @@ cudaError_t BatchLoop::launch_post(cudaStream_t s) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   k_batch_trace_end<<<L.chunk_grid, 256, 0, s>>>(L.d_inst, L.d_prech, L.n_inst);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  k_batch_end<<<(L.n_inst + 127) / 128, 128, 0, s>>>(L.d_inst, L.n_inst);
+  k_batch_end<<<(L.n_inst + 127) / 128, 128, 0, s>>>(L.d_inst, L.n_inst,
+                                                     L.d_q ? &L.d_q->err : nullptr);
   return cudaGetLastError();
 }
 
@@ -1177,7 +1479,7 @@ cudaError_t BatchLoop::launch_body(cudaStream_t s, cudaGraphConditionalHandle ha
 // bracketed by CUDA events on stream s (kernel accounting): the same kernels
 // as the graph, the loop condition read back after every iteration.
 cudaError_t BatchLoop::run_step_profiled(cudaStream_t s, int max_iter, double* ms,
-                                         int64_t* launches) {
+                                         int64_t* launches, bool persist) {
   Impl& L = *impl;
   cudaEvent_t ev[2];
   cudaError_t e = cudaEventCreate(&ev[0]);
@@ -1220,6 +1522,11 @@ cudaError_t BatchLoop::run_step_profiled(cudaStream_t s, int max_iter, double* m
     });
   };
   if (e == cudaSuccess) e = sweep();
+  if (persist && persist_ok()) {
+    // every remaining iteration in the persistent launch (timed as ELEM)
+    if (e == cudaSuccess) e = timed(EHDG_KERNEL_ELEM, [&] { return launch_persist(s); });
+    max_iter = 0;
+  }
   int n_active = 0;
   for (int it = 0; e == cudaSuccess && it < max_iter; ++it) {
     if ((e = cudaMemcpy(&n_active, L.d_lists, sizeof(int), cudaMemcpyDeviceToHost)) !=
@@ -1256,7 +1563,8 @@ cudaError_t BatchLoop::run_step_profiled(cudaStream_t s, int max_iter, double* m
     return cudaGetLastError();
   });
   if (e == cudaSuccess) e = timed(EHDG_KERNEL_AUX, [&] {
-    k_batch_end<<<(L.n_inst + 127) / 128, 128, 0, s>>>(L.d_inst, L.n_inst);
+    k_batch_end<<<(L.n_inst + 127) / 128, 128, 0, s>>>(L.d_inst, L.n_inst,
+                                                       L.d_q ? &L.d_q->err : nullptr);
     return cudaGetLastError();
   });
   cudaEventDestroy(ev[0]);

@@ -323,12 +323,19 @@ struct BatchLoop {
                     const std::vector<int>& slot);
   // a step's kernels before the loop (they set the loop condition), the loop
   // body, and the kernels after it
-  cudaError_t launch_pre(cudaStream_t s, cudaGraphConditionalHandle handle);
+  // (graph_mode 0: the pre-loop sweep sets no conditional handle)
+  cudaError_t launch_pre(cudaStream_t s, cudaGraphConditionalHandle handle, int graph_mode = 1);
   cudaError_t launch_body(cudaStream_t s, cudaGraphConditionalHandle handle);
   cudaError_t launch_post(cudaStream_t s);
+  // the persistent form of the loop (every remaining iteration of a step in
+  // one launch, instances at their own pace), where every looped instance is
+  // FP64 or has FP32 corrections
+  bool persist_ok() const;
+  cudaError_t launch_persist(cudaStream_t s);
   // one step driven from the host, each launch timed with CUDA events:
   // ms[kind] and launches[kind] accumulate (ehdg_kernel_kind)
-  cudaError_t run_step_profiled(cudaStream_t s, int max_iter, double* ms, int64_t* launches);
+  cudaError_t run_step_profiled(cudaStream_t s, int max_iter, double* ms, int64_t* launches,
+                                bool persist = false);
   int kernels_per_iteration() const;
 };
 

@@ -24,6 +24,15 @@ namespace ehdg {
 
 constexpr int kPeTile = 128;   // elements per tile = threads per block
 
+// Loads of data that other blocks of the same launch write (traces,
+// corrections, residuals): CG = true reads through L2 only (a persistent
+// launch, where an SM's L1 may hold lines other SMs have rewritten since).
+template <bool CG, class T>
+__device__ __forceinline__ T pe_ld(const T* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return *p;
+}
+
 struct PeView {
   int64_t nel, nface;
   int n_rows, n_up;
@@ -45,7 +54,7 @@ struct PeView {
 
 // Hsh: the sweep rows of the operator in row order, [n_rows][NQ]. Returns true
 // in the block that did the final reduction.
-template <int NQ>
+template <int NQ, bool CG = false>
 __device__ __forceinline__ bool pe_tile(const PeView& v, const double* Hsh, const double* src,
                                         double* dst, int64_t tile, int64_t ntiles, int graph_mode,
                                         cudaGraphConditionalHandle handle) {
@@ -62,7 +71,7 @@ __device__ __forceinline__ bool pe_tile(const PeView& v, const double* Hsh, cons
     for (int f = 0; f < 4; ++f) {
       const int64_t face = v.elem_face[f * ne + e];
 #pragma unroll
-      for (int g = 0; g < NQF; ++g) u[f * NQF + g] = src[g * nface + face];
+      for (int g = 0; g < NQF; ++g) u[f * NQF + g] = pe_ld<CG>(src + g * nface + face);
     }
 #pragma unroll
     for (int j = 0; j < NQ; ++j) {
@@ -81,7 +90,7 @@ __device__ __forceinline__ bool pe_tile(const PeView& v, const double* Hsh, cons
         const int64_t face = v.elem_face[f * ne + e];
         const int64_t pt = g * nface + face;
         dst[pt] = acc;
-        const double d = acc - src[pt];
+        const double d = acc - pe_ld<CG>(src + pt);
         res += v.face_jf[face] * v.fw[g] * d * d;
         if (v.R_out) v.R_out[pt] = (float)d;
       } else {
@@ -144,7 +153,7 @@ struct LpPeView {
   float* out;
 };
 
-template <int NQ>
+template <int NQ, bool CG = false>
 __device__ __forceinline__ void lp_pe_tile(const LpPeView& v, const float* Hsh32, int64_t tile) {
   constexpr int NQF = NQ / 4;
   const int64_t ne = v.nel, nface = v.nface;
@@ -155,7 +164,7 @@ __device__ __forceinline__ void lp_pe_tile(const LpPeView& v, const float* Hsh32
   for (int f = 0; f < 4; ++f) {
     const int64_t face = v.elem_face[f * ne + e];
 #pragma unroll
-    for (int g = 0; g < NQF; ++g) d[f * NQF + g] = v.in[g * nface + face];
+    for (int g = 0; g < NQF; ++g) d[f * NQF + g] = pe_ld<CG>(v.in + g * nface + face);
   }
 #pragma unroll
   for (int j = 0; j < NQ; ++j) {
@@ -167,7 +176,7 @@ __device__ __forceinline__ void lp_pe_tile(const LpPeView& v, const float* Hsh32
     const int r = v.rows[j];
     const int f = r / NQF, g = r - f * NQF;
     const int64_t pt = g * nface + v.elem_face[f * ne + e];
-    v.out[pt] = v.R[pt] + a;
+    v.out[pt] = pe_ld<CG>(v.R + pt) + a;
   }
 }
 

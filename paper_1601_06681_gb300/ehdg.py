@@ -495,8 +495,10 @@ class Batch:
 
     def set_loop(self, on=True):
         """Batched iteration loop for the instances it supports (default on);
-        off runs every instance's own loop on the graph's branches."""
-        _check(load().ehdg_batch_set_loop(self._h, 1 if on else 0))
+        off runs every instance's own loop on the graph's branches;
+        "persistent" the loop's one-launch form (ehdg_batch_set_loop mode 2)."""
+        mode = 2 if on == "persistent" else (1 if on else 0)
+        _check(load().ehdg_batch_set_loop(self._h, mode))
 
     def set_profiling(self, on=True):
         """Kernel accounting of the batched loop (host-driven steps, every
@@ -527,14 +529,15 @@ class Batch:
         return best.value, ms.value
 
     def autotune_schedule(self, chain_candidates=(16, 32, 64)):
-        """Time the batched loop against the branch form with each branch
-        count, from the current states (restored after each), and keep the
-        fastest: (loop_on, k, ms)."""
+        """Time the batched loop, its persistent form and the branch form
+        with each branch count, from the current states (restored after
+        each), and keep the fastest: (mode, k, ms), mode 0 branches, 1 loop,
+        2 persistent."""
         arr = (C.c_int * len(chain_candidates))(*[int(k) for k in chain_candidates])
         loop_on, k, ms = C.c_int(), C.c_int(), C.c_double()
         _check(load().ehdg_batch_autotune_schedule(self._h, arr, len(chain_candidates),
                                                    C.byref(loop_on), C.byref(k), C.byref(ms)))
-        return bool(loop_on.value), k.value, ms.value
+        return loop_on.value, k.value, ms.value
 
     def autotune_inner_sweeps(self, candidates=(2, 4, 6, 8, 12, 16)):
         """One inner sweep count m for every mixed-precision instance, timed

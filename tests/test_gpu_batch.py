@@ -270,8 +270,8 @@ def test_schedule_autotuner_keeps_states_and_results(ehdg):
         for (kw, prob, u0, g), s in zip(inst, b.instances):
             s.set_state(u0)
         before = [s.get_state() for s in b.instances]
-        loop_on, k, ms = b.autotune_schedule((2, 4))
-        assert 0 < ms < 1e300 and (loop_on or k in (2, 4))
+        mode, k, ms = b.autotune_schedule((2, 4))
+        assert 0 < ms < 1e300 and mode in (0, 1, 2) and (mode or k in (2, 4))
         for (u, uh), s in zip(before, b.instances):
             su, suh = s.get_state()
             assert np.array_equal(u, su) and np.array_equal(uh, suh)
@@ -280,6 +280,75 @@ def test_schedule_autotuner_keeps_states_and_results(ehdg):
     assert np.array_equal(iters, ref_iters)
     for (u, uh), (ru, ruh) in zip(states, ref_states):
         assert np.array_equal(u, ru) and np.array_equal(uh, ruh)
+
+
+@pytest.mark.parametrize("precisions", [("fp64",), ("fp64", "fp32"), ("fp32", "fp64", "tf32")])
+def test_persistent_loop_matches_solo_runs_bitwise(ehdg, precisions):
+    """The loop's persistent form (every iteration of a step in one launch,
+    each instance through its own stages at its own pace) gives every
+    instance's solo iterations and state bit for bit; with a TF32 instance in
+    the batch it falls back to the loop of launches, with the same result."""
+    inst = loop_instances(n=12, seed=41, precisions=precisions)
+    n_steps = 3
+    iters, times, states = run_loop(ehdg, inst, n_steps, loop="persistent")
+    assert np.all(times > 0)
+    for i, (kw, prob, u0, g) in enumerate(inst):
+        args = dict(kw)
+        mesh = args.pop("mesh")
+        p = args.pop("p")
+        with ehdg.Solver(mesh, p, **args) as s:
+            s.set_boundary(g)
+            s.set_state(u0)
+            solo_iters = s.run(n_steps)
+            u, uh = s.get_state()
+        assert list(iters[i]) == solo_iters, (i, kw["precision"])
+        assert np.array_equal(states[i][0], u), (i, kw["precision"])
+        assert np.array_equal(states[i][1], uh), (i, kw["precision"])
+
+
+def test_persistent_loop_with_many_tiles_equals_the_loop(ehdg):
+    """Instances of up to 128 tiles each, FP64 and FP32 corrections: the
+    persistent form and the loop of launches agree bit for bit over two
+    steps (the ring is reused across steps)."""
+    rng = np.random.default_rng(42)
+    inst = []
+    for i in range(20):
+        n = int(rng.integers(24, 129))
+        p = 1 + i % 5
+        th = rng.uniform(0.05, 1.5) + (np.pi / 2) * (i % 4)
+        beta = rng.uniform(0.5, 1.5) * np.array([np.cos(th), np.sin(th)])
+        mesh = W.structured_mesh((n, n))
+        X = node_coords(mesh, p)
+        XF = face_point_coords(mesh, p, p + 1)
+        kw = dict(mesh=mesh, p=p, scheme="be", dt=0.01, tol=1e-11, max_iter=500,
+                  beta_const=beta, precision=("fp64", "fp32")[i % 2], inner_sweeps=3 + i % 4)
+        inst.append((kw, None, W.gaussian(X, (0.4, 0.6), 0.1)[:, None, :],
+                     W.gaussian(XF, (0.4, 0.6), 0.1)))
+    a_iters, _, a_states = run_loop(ehdg, inst, 2, loop="persistent")
+    b_iters, _, b_states = run_loop(ehdg, inst, 2, loop=True)
+    assert np.array_equal(a_iters, b_iters)
+    for (u, uh), (ru, ruh) in zip(a_states, b_states):
+        assert np.array_equal(u, ru) and np.array_equal(uh, ruh)
+
+
+def test_persistent_loop_reports_an_instance_that_does_not_converge(ehdg):
+    """An instance that hits max_iter in the persistent form stops with
+    EHDG_ERR_NOT_CONVERGED while the others run on to their tolerance."""
+    inst = loop_instances(n=5, seed=43, precisions=("fp64", "fp32"))
+    kw0 = dict(inst[0][0], tol=1e-30, max_iter=3)
+    inst[0] = (kw0,) + inst[0][1:]
+    with ehdg.Batch([kw for kw, _, _, _ in inst]) as b:
+        b.set_loop("persistent")
+        for (kw, prob, u0, g), s in zip(inst, b.instances):
+            s.set_boundary(g)
+            s.set_state(u0)
+        with pytest.raises(ehdg.EhdgError) as ei:
+            b.run(1)
+        assert ei.value.status == 4
+        states = [s.get_state() for s in b.instances]
+    for i, (kw, prob, u0, g) in enumerate(inst[1:], start=1):
+        ou, _, _, _ = prob.run(u0, 1, g_of_t=lambda t: g, tol=1e-13, max_iter=2000)
+        assert np.linalg.norm(states[i][0] - ou) / np.linalg.norm(ou) < 1e-10, i
 
 
 def test_batched_loop_reports_an_instance_that_does_not_converge(ehdg):
