@@ -735,9 +735,18 @@ __device__ void q_publish(BQueue* q, long long* seq, int2* items, int inst, int 
   __syncthreads();
 }
 
+// A correction item covers up to kQCorrTiles consecutive 128-element tiles
+// (its block runs them one after the other): the FP32 tile is short, and one
+// item per tile would spend more on taking and completing items than on the
+// tile.
+constexpr int kQCorrTiles = 4;
+__device__ __forceinline__ int corr_items(const BInst& I) {
+  return (I.n_tiles128 + kQCorrTiles - 1) / kQCorrTiles;
+}
+
 // the first stage of an instance that still iterates after the pre-loop sweep
 __device__ __forceinline__ int2 first_stage(const BInst& I) {
-  return (I.tc && !I.mma && I.m > 0) ? make_int2(1, I.n_tiles128) : make_int2(kStSweep, I.n_tiles_pe);
+  return (I.tc && !I.mma && I.m > 0) ? make_int2(1, corr_items(I)) : make_int2(kStSweep, I.n_tiles_pe);
 }
 
 // Start of a step's persistent loop (one block): claims restart at the
@@ -880,13 +889,16 @@ __global__ void __launch_bounds__(kPeTile) k_batch_persist(const BInst* inst, BQ
       if (kind == 1) {
         const float* smf = reinterpret_cast<const float*>(sm);
         const int j = stage - 1;
-        switch (nq) {
-          case 8: q_corr_item<8>(I, smf, j, idx); break;
-          case 12: q_corr_item<12>(I, smf, j, idx); break;
-          case 16: q_corr_item<16>(I, smf, j, idx); break;
-          case 20: q_corr_item<20>(I, smf, j, idx); break;
-          case 24: q_corr_item<24>(I, smf, j, idx); break;
-          default: q_corr_item<28>(I, smf, j, idx); break;
+        const int t1 = min((idx + 1) * kQCorrTiles, I.n_tiles128);
+        for (int tile = idx * kQCorrTiles; tile < t1; ++tile) {
+          switch (nq) {
+            case 8: q_corr_item<8>(I, smf, j, tile); break;
+            case 12: q_corr_item<12>(I, smf, j, tile); break;
+            case 16: q_corr_item<16>(I, smf, j, tile); break;
+            case 20: q_corr_item<20>(I, smf, j, tile); break;
+            case 24: q_corr_item<24>(I, smf, j, tile); break;
+            default: q_corr_item<28>(I, smf, j, tile); break;
+          }
         }
       } else {
         // the FP64 update (the loop's k_batch_apply on one chunk)
@@ -904,7 +916,7 @@ __global__ void __launch_bounds__(kPeTile) k_batch_persist(const BInst* inst, BQ
       __syncthreads();
       if (tid == 0) {
         __threadfence();
-        const int n = kind == 2 ? I.n_chunks : I.n_tiles128;
+        const int n = kind == 2 ? I.n_chunks : corr_items(I);
         const int last = atomicAdd(&stage_cnt[i], 1) == n - 1;
         if (last) {
           stage_cnt[i] = 0;
@@ -928,7 +940,7 @@ __global__ void __launch_bounds__(kPeTile) k_batch_persist(const BInst* inst, BQ
           atomicSub(&q->live, 1);
         }
       } else if (kind == 1) {
-        nx = (stage < I.m) ? make_int2(stage + 1, I.n_tiles128) : make_int2(kStApply, I.n_chunks);
+        nx = (stage < I.m) ? make_int2(stage + 1, corr_items(I)) : make_int2(kStApply, I.n_chunks);
       } else {
         nx = make_int2(kStSweep, I.n_tiles_pe);
       }
