@@ -399,10 +399,12 @@ ehdg_status ehdg_trace_residual_noalloc(const double* a, const double* b, const 
                                         int64_t n, double* out, void* stream);
 
 /* Self-test of the bounded device-side waits (the paper has no
- * counterpart). which = 0 runs the mbarrier waits of the tiled sweeps, and
- * which = 1 runs the grid barrier of the persistent sweep. Each runs against a
- * condition that never holds: an mbarrier that no arrival completes, or a
- * barrier target one arrival beyond the grid. The poll limit is short, so
+ * counterpart). which = 0 runs the mbarrier waits of the tiled sweeps,
+ * which = 1 the grid barrier of the persistent sweep, which = 2 the work-ring
+ * wait of the persistent batched loop. Each runs against a condition that
+ * never holds: an mbarrier that no arrival completes, a barrier target one
+ * arrival beyond the grid, or a ring with a live instance where nothing is
+ * ever published. The poll limit is short, so
  * the call takes milliseconds. Every wait must give up and report it through a
  * flag the host reads. The expected result is EHDG_ERR_TIMEOUT; EHDG_OK means a
  * wait did not give up, which is a defect. The device stays usable afterwards.

@@ -822,7 +822,7 @@ __device__ __forceinline__ void q_corr_item(const BInst& I, const float* Hsh32, 
 
 __global__ void __launch_bounds__(kPeTile) k_batch_persist(const BInst* inst, BQueue* q,
                                                            long long* seq, int2* items,
-                                                           int* stage_cnt) {
+                                                           int* stage_cnt, unsigned int limit) {
   extern __shared__ double sm[];
   __shared__ int2 s_item;
   __shared__ int s_flag;
@@ -842,7 +842,7 @@ __global__ void __launch_bounds__(kPeTile) k_batch_persist(const BInst* inst, BQ
         if (*reinterpret_cast<volatile int*>(&q->live) == 0 ||
             *reinterpret_cast<volatile int*>(&q->err) != 0)
           break;
-        if (n >= kQWaitLimit) {
+        if (n >= limit) {
           atomicExch(&q->err, 1);
           break;
         }
@@ -1420,9 +1420,39 @@ cudaError_t BatchLoop::launch_persist(cudaStream_t s) {
   k_batch_qinit<<<1, 256, 0, s>>>(L.d_inst, L.n_inst, L.d_q, L.d_seq, L.d_items, L.d_stage_cnt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_batch_persist<<<L.persist_grid, kPeTile, L.persist_smem, s>>>(L.d_inst, L.d_q, L.d_seq,
-                                                                  L.d_items, L.d_stage_cnt);
+  k_batch_persist<<<L.persist_grid, kPeTile, L.persist_smem, s>>>(
+      L.d_inst, L.d_q, L.d_seq, L.d_items, L.d_stage_cnt, kQWaitLimit);
   return cudaGetLastError();
+}
+
+// Self-test of the ring's bounded wait: one live instance and nothing ever
+// published, so every block polls an empty slot, gives up after `limit` polls
+// and leaves; *gave_up receives the ring's error flag (1 as designed).
+cudaError_t batch_ring_selftest(cudaStream_t s, unsigned int limit, int* gave_up) {
+  BQueue* q = nullptr;
+  long long* seq = nullptr;
+  int2* items = nullptr;
+  int* cnt = nullptr;
+  cudaError_t e = cudaMalloc(&q, sizeof(BQueue));
+  if (e == cudaSuccess) e = cudaMalloc(&seq, sizeof(long long) * kQCap);
+  if (e == cudaSuccess) e = cudaMalloc(&items, sizeof(int2) * kQCap);
+  if (e == cudaSuccess) e = cudaMalloc(&cnt, sizeof(int));
+  BQueue h{};
+  h.live = 1;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(q, &h, sizeof(BQueue), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(seq, 0xFF, sizeof(long long) * kQCap, s);
+  if (e == cudaSuccess) {
+    k_batch_persist<<<2, kPeTile, 0, s>>>(nullptr, q, seq, items, cnt, limit);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, q, sizeof(BQueue), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) *gave_up = h.err;
+  cudaFree(q);
+  cudaFree(seq);
+  cudaFree(items);
+  cudaFree(cnt);
+  return e;
 }
 
 // Everything of a step before the loop, each kernel one launch for all the

@@ -341,6 +341,9 @@ struct BatchLoop {
 
 enum FaceMode { kFaceInitial = 0, kFaceIterate = 1 };
 int face_launches(const Ctx& c, int mode);   // kernels one launch_face(c, mode) makes
+// the persistent batched loop's ring wait against a ring where nothing is ever
+// published (ehdg_selftest_wait_timeout, which = 2)
+cudaError_t batch_ring_selftest(cudaStream_t s, unsigned int limit, int* gave_up);
 
 void set_last_error(const std::string& msg);
 // standalone weighted difference norm (residual.cu); its grid never exceeds

@@ -109,11 +109,27 @@ extern "C" ehdg_status ehdg_probe_fp64_rate(void* stream, int* sms, double* tflo
 
 extern "C" ehdg_status ehdg_selftest_wait_timeout(int which, void* stream) {
   using namespace ehdg;
-  if (which != 0 && which != 1) {
-    set_last_error("ehdg_selftest_wait_timeout: which must be 0 (mbarrier) or 1 (grid barrier)");
+  if (which < 0 || which > 2) {
+    set_last_error("ehdg_selftest_wait_timeout: which must be 0 (mbarrier), 1 (grid barrier) or "
+                   "2 (work ring)");
     return EHDG_ERR_INVALID;
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (which == 2) {
+    int gave_up = 0;
+    const cudaError_t er = batch_ring_selftest(s, 1u << 12, &gave_up);
+    if (er != cudaSuccess) {
+      cudaGetLastError();
+      set_last_error(std::string("ehdg_selftest_wait_timeout: ") + cudaGetErrorString(er));
+      return EHDG_ERR_CUDA;
+    }
+    if (!gave_up) {
+      set_last_error("ehdg_selftest_wait_timeout: the work ring's wait did not give up");
+      return EHDG_OK;
+    }
+    set_last_error("ehdg_selftest_wait_timeout: every bounded wait gave up, as designed");
+    return EHDG_ERR_TIMEOUT;
+  }
   constexpr int kBlocks = 4;
   int* buf = nullptr;              // [0] barrier count, [1] abort, [2] gave-up count
   cudaError_t e = cudaMallocAsync((void**)&buf, 4 * sizeof(int), s);

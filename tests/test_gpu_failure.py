@@ -21,7 +21,8 @@ def ehdg():
     return E
 
 
-@pytest.mark.parametrize("which", [0, 1])   # 0: mbarrier waits, 1: grid barrier
+# 0: mbarrier waits, 1: grid barrier, 2: the persistent batched loop's work ring
+@pytest.mark.parametrize("which", [0, 1, 2])
 def test_bounded_wait_gives_up_and_device_stays_usable(ehdg, which):
     import torch
     assert ehdg.ehdg_selftest_wait_timeout(which) == 6
