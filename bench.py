@@ -408,6 +408,23 @@ def events_ms(stream, fn, reps):
     return e0.elapsed_time(e1) / reps, out
 
 
+def events_ms_each(stream, fn, reps):
+    """Device time of each of reps calls of fn (CUDA events on `stream`, ms)
+    and the value of the last call."""
+    import torch
+    out, times = None, []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    return times, out
+
+
 def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
@@ -784,7 +801,7 @@ def run_headline(args):
     # time to the matched tolerance, every path
     ttt = None
     if not args.no_mixed:
-        reps = max(1, min(args.steps, 2))
+        reps = max(1, min(args.steps, 3))
         ttt = {"rule": (f"every path stops when the FP64 trace residual "
                         f"||uhat^(k+1) - uhat^k||_L2(E_h) < {TOL_MATCHED_3D:g} (mixed precision: "
                         "the residual of its outer FP64 sweeps), the largest tolerance of "
@@ -792,6 +809,7 @@ def run_headline(args):
                         f"{ACCURACY_TARGET:g} relative L2 of its fixed point; the fixed point "
                         "is the FP64 path with every step converged to 1e-13"),
                "tol": TOL_MATCHED_3D, "accuracy_target": ACCURACY_TARGET,
+               "timing": f"median of {reps} runs, each timed with CUDA events (runs_ms)",
                "fp64_at_config_tol": {"tol": wl.tol, "ms_per_run": t_max / args.steps,
                                       "rel_l2_vs_fp64_fixed_point": rel_l2(u_head, u_fix)}}
         entries = [("fp64", "fp64", False), ("fp64_emulated", "fp64_emulated", False),
@@ -801,13 +819,15 @@ def run_headline(args):
             s = make(prec, TOL_MATCHED_3D, eo)
             run_s = runner(s)
             run_s()                                         # warm-up (captures the graph)
-            ems, its = events_ms(stream, run_s, reps)
+            runs_ms, its = events_ms_each(stream, run_s, reps)
+            ems = statistics.median(runs_ms)      # one slow run (host jitter) does not move it
             u, uh = s.get_state()
             s.set_profiling(True)
             run_s()
             st = s.kernel_stats()
             s.set_profiling(False)
-            ent = {"ms_per_run": ems, "fp64_sweeps_per_run": its,
+            ent = {"ms_per_run": ems, "runs_ms": [round(t, 2) for t in runs_ms],
+                   "fp64_sweeps_per_run": its,
                    "rel_l2_vs_fp64_fixed_point": rel_l2(u, u_fix),
                    "rel_l2_trace_vs_fp64_fixed_point": rel_l2(uh, uh_fix),
                    "kernel_time_share": kernel_shares(st),
