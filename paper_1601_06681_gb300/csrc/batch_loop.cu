@@ -72,6 +72,11 @@ struct BInst {
   float* Y32;
   int* err;
   const uint4* Bimg;            // the rounded operator rows, K-major image (Np x Kp)
+  // the sweep rows of the operator in row order, for the persistent form
+  // (read through L1 instead of staged per item): [n_rows][NQFS] FP64 and,
+  // with FP32 corrections, [n_up][NQFS] FP32
+  const double* Hyc;
+  const float* Hy32c;
   const int* rowfg;             // [Np] face | point << 8 of each row
   // fixed-shape tile body (quadrilaterals, whole faces as rows): row faces,
   // the leading ones owned, and the local face of each
@@ -589,6 +594,16 @@ __global__ void __launch_bounds__(kBTcThreads) k_batch_tc(const BInst* inst, con
                  "r"(ncols));
 }
 
+// Setup of the persistent form: instance i's sweep rows in row order
+__global__ void k_batch_rows(const double* Hy, const float* Hy32, const int* rows, int n_rows,
+                             int n_up, int NQFS, double* Hyc, float* Hy32c) {
+  for (int t = threadIdx.x; t < n_rows * NQFS; t += blockDim.x) {
+    const int j = t / NQFS, c = t - j * NQFS;
+    Hyc[t] = Hy[rows[j] * NQFS + c];
+    if (Hy32c && j < n_up) Hy32c[t] = Hy32[rows[j] * NQFS + c];
+  }
+}
+
 // Setup: instance i's operator rows rounded to TF32 / BF16 in the K-major
 // image the correction sweep stages (the single-problem sweep's rounding),
 // and its row tables.
@@ -823,11 +838,9 @@ __device__ __forceinline__ void q_corr_item(const BInst& I, const float* Hsh32, 
 __global__ void __launch_bounds__(kPeTile) k_batch_persist(const BInst* inst, BQueue* q,
                                                            long long* seq, int2* items,
                                                            int* stage_cnt, unsigned int limit) {
-  extern __shared__ double sm[];
   __shared__ int2 s_item;
   __shared__ int s_flag;
   const int tid = threadIdx.x;
-  int cur = -1, cur_kind = -1;             // the operator rows in shared memory
   for (;;) {
     if (tid == 0) {
       const unsigned long long w = atomicAdd(&q->head, 1ull);
@@ -857,37 +870,23 @@ __global__ void __launch_bounds__(kPeTile) k_batch_persist(const BInst* inst, BQ
     const BInst& I = inst[i];
     const int nq = I.NQFS;
     const int kind = stage == kStSweep ? 0 : (stage == kStApply ? 2 : 1);
-    if (kind != 2 && (i != cur || kind != cur_kind)) {
-      // every thread is past the previous item's reads of the rows
-      if (kind == 0) {
-        for (int t = tid; t < I.n_rows * nq; t += kPeTile) {
-          const int jj = t / nq, c = t - jj * nq;
-          sm[t] = I.Hy[I.rows[jj] * nq + c];
-        }
-      } else {
-        float* smf = reinterpret_cast<float*>(sm);
-        for (int t = tid; t < I.n_up * nq; t += kPeTile) {
-          const int jj = t / nq, c = t - jj * nq;
-          smf[t] = I.Hy32[I.rows[jj] * nq + c];
-        }
-      }
-      __syncthreads();
-      cur = i;
-      cur_kind = kind;
-    }
+    // the operator rows come through L1 (every thread of a row reads the same
+    // entry), not staged per item: consecutive items are mostly of other
+    // instances
     bool done;
     if (kind == 0) {
+      const double* hr = I.Hyc;
       switch (nq) {
-        case 8: done = q_sweep_item<8>(I, sm, idx); break;
-        case 12: done = q_sweep_item<12>(I, sm, idx); break;
-        case 16: done = q_sweep_item<16>(I, sm, idx); break;
-        case 20: done = q_sweep_item<20>(I, sm, idx); break;
-        case 24: done = q_sweep_item<24>(I, sm, idx); break;
-        default: done = q_sweep_item<28>(I, sm, idx); break;
+        case 8: done = q_sweep_item<8>(I, hr, idx); break;
+        case 12: done = q_sweep_item<12>(I, hr, idx); break;
+        case 16: done = q_sweep_item<16>(I, hr, idx); break;
+        case 20: done = q_sweep_item<20>(I, hr, idx); break;
+        case 24: done = q_sweep_item<24>(I, hr, idx); break;
+        default: done = q_sweep_item<28>(I, hr, idx); break;
       }
     } else {
       if (kind == 1) {
-        const float* smf = reinterpret_cast<const float*>(sm);
+        const float* smf = I.Hy32c;
         const int j = stage - 1;
         const int t1 = min((idx + 1) * kQCorrTiles, I.n_tiles128);
         for (int tile = idx * kQCorrTiles; tile < t1; ++tile) {
@@ -1169,6 +1168,7 @@ struct BatchLoop::Impl {
   size_t sweep_smem = 0, tc_smem = 0;
   // persistent form: the work ring and the per-instance stage counters
   BQueue* d_q = nullptr;
+  unsigned char* d_rows = nullptr;   // sweep rows in row order of every instance
   long long* d_seq = nullptr;
   int2* d_items = nullptr;
   int* d_stage_cnt = nullptr;
@@ -1188,6 +1188,7 @@ void BatchLoop::release() {
   cudaFree(impl->d_prech);
   cudaFree(impl->d_ticket);
   cudaFree(impl->d_q);
+  cudaFree(impl->d_rows);
   cudaFree(impl->d_seq);
   cudaFree(impl->d_items);
   cudaFree(impl->d_stage_cnt);
@@ -1339,6 +1340,29 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
       if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
     }
   }
+  if (!L.any_mma) {
+    // the persistent form reads every instance's sweep rows in row order
+    std::vector<size_t> off(L.n_inst, 0), off32(L.n_inst, 0);
+    size_t bytes = 0;
+    for (int i = 0; i < L.n_inst; ++i) {
+      off[i] = bytes;
+      bytes += (sizeof(double) * h[i].n_rows * h[i].NQFS + 255) / 256 * 256;
+      off32[i] = bytes;
+      if (h[i].tc) bytes += (sizeof(float) * h[i].n_rows * h[i].NQFS + 255) / 256 * 256;
+    }
+    if ((e = cudaMalloc(&L.d_rows, std::max<size_t>(bytes, 256))) != cudaSuccess) return e;
+    for (int i = 0; i < L.n_inst; ++i) {
+      const Ctx& c = *ctxs[i];
+      double* hyc = reinterpret_cast<double*>(L.d_rows + off[i]);
+      float* hy32c = h[i].tc ? reinterpret_cast<float*>(L.d_rows + off32[i]) : nullptr;
+      k_batch_rows<<<1, 256>>>(c.Hy, h[i].tc ? c.Hy32 : nullptr, c.rows, c.n_rows, h[i].n_up,
+                               c.NQFS, hyc, hy32c);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      h[i].Hyc = hyc;
+      h[i].Hy32c = hy32c;
+    }
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
+  }
   if ((e = cudaMalloc(&L.d_inst, sizeof(BInst) * std::max(1, L.n_inst))) != cudaSuccess) return e;
   if ((e = cudaMalloc(&L.d_counts, sizeof(int4) * std::max(1, L.n_inst))) != cudaSuccess) return e;
   if ((e = cudaMemcpy(L.d_counts, cnt.data(), sizeof(int4) * L.n_inst, cudaMemcpyHostToDevice)) !=
@@ -1404,8 +1428,8 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     if ((e = cudaMalloc(&L.d_items, sizeof(int2) * kQCap)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&L.d_stage_cnt, sizeof(int) * std::max(1, L.n_inst))) != cudaSuccess)
       return e;
-    // a few KB (operator rows of one instance): no attribute needed
-    L.persist_smem = std::max(L.sweep_smem, L.lp_smem);
+    // the operator rows come from global memory: no dynamic shared memory
+    L.persist_smem = 0;
     L.persist_grid = wave(k_batch_persist, kPeTile, L.persist_smem, 1 << 30);
   }
   return cudaSuccess;

@@ -243,6 +243,30 @@ def test_warm_start_is_off_where_the_trace_formula_needs_both_sides(ehdg):
             assert s.info["warm_start"] == 0, name
 
 
+def test_autotuner_restores_the_warm_start(ehdg):
+    """The inner-sweep autotuner restores the warm-start flag with the rest of
+    the state, from a cold state (just after set_state) and from a warm one
+    (after a step): runs with autotuner calls in between equal a plain run bit
+    for bit (a flag left wrong would change the initial trace's rounding)."""
+    mesh, p, kw, prob, u0, g = make_case("3d_be_const_p3")
+    kw = dict(kw, precision="bf16", inner_sweeps=4)
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        ref_iters = s.run(3)
+        ref = s.get_state()
+    with make_solver(ehdg, mesh, p, kw, prob) as s:
+        s.set_boundary(g)
+        s.set_state(u0)
+        assert s.autotune_inner_sweeps((4,))[0] == 4      # from a cold state
+        iters = s.run(1)
+        assert s.autotune_inner_sweeps((4,))[0] == 4      # from a warm state
+        iters += s.run(2)
+        got = s.get_state()
+    assert iters == ref_iters
+    assert np.array_equal(got[0], ref[0]) and np.array_equal(got[1], ref[1])
+
+
 def test_converged_step_equals_direct_hdg_solve(ehdg):
     mesh, p, kw, prob, u0, g = make_case("2d_be_const")
     with make_solver(ehdg, mesh, p, kw, prob, tol=1e-13, max_iter=2000) as s:
@@ -431,7 +455,8 @@ def test_bf16_per_element_mixed_reaches_fp64_solution(ehdg, name):
 # checkpoint / resume and the autotuner
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("name", ["2d_cn_variable", "sw_be"])
+# "3d_be_const_p3" starts its steps warm (the checkpoint carries that flag)
+@pytest.mark.parametrize("name", ["2d_cn_variable", "sw_be", "3d_be_const_p3"])
 def test_checkpoint_resume_is_bitwise(ehdg, name, tmp_path):
     mesh, p, kw, prob, u0, g = make_case(name)
     with make_solver(ehdg, mesh, p, kw, prob) as s:
