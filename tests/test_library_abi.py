@@ -62,6 +62,7 @@ def test_new_entry_points_reject_null_handles_without_a_gpu():
     assert lib.ehdg_batch_autotune_chains(None, cands, 2, C.byref(best), C.byref(ms)) == 1
     assert lib.ehdg_batch_autotune_sweep_tile(None, cands, 2, C.byref(best), C.byref(ms)) == 1
     assert lib.ehdg_batch_autotune_inner_sweeps(None, cands, 2, C.byref(best), C.byref(ms)) == 1
+    assert lib.ehdg_batch_set_loop(None, 2) == 1      # NULL batch (mode 2: persistent)
     loop_on = C.c_int()
     assert lib.ehdg_batch_autotune_schedule(None, cands, 2, C.byref(loop_on), C.byref(best),
                                             C.byref(ms)) == 1
