@@ -835,7 +835,10 @@ __device__ __forceinline__ void q_corr_item(const BInst& I, const float* Hsh32, 
   lp_pe_tile<NQ, true>(v, Hsh32, tile);
 }
 
-__global__ void __launch_bounds__(kPeTile) k_batch_persist(const BInst* inst, BQueue* q,
+// five resident blocks per SM (96 registers; four at the unconstrained 128):
+// the blocks spend much of an item at barriers while one thread takes the
+// next item or counts the stage, so more blocks keep the pipes busier
+__global__ void __launch_bounds__(kPeTile, 5) k_batch_persist(const BInst* inst, BQueue* q,
                                                            long long* seq, int2* items,
                                                            int* stage_cnt, unsigned int limit) {
   __shared__ int2 s_item;
