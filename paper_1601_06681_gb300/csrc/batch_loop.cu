@@ -844,9 +844,14 @@ __global__ void __launch_bounds__(kPeTile, 5) k_batch_persist(const BInst* inst,
   __shared__ int2 s_item;
   __shared__ int s_flag;
   const int tid = threadIdx.x;
+  // thread 0's claim of the next ring position; a correction or update item
+  // takes it together with its stage count (two atomics in flight at once)
+  unsigned long long w = 0ull;
+  bool claimed = false;
   for (;;) {
     if (tid == 0) {
-      const unsigned long long w = atomicAdd(&q->head, 1ull);
+      if (!claimed) w = atomicAdd(&q->head, 1ull);
+      claimed = false;
       const int slot = (int)(w & (unsigned long long)(kQCap - 1));
       int go = 0;
       for (unsigned int n = 0;; ++n) {
@@ -919,7 +924,10 @@ __global__ void __launch_bounds__(kPeTile, 5) k_batch_persist(const BInst* inst,
       if (tid == 0) {
         __threadfence();
         const int n = kind == 2 ? I.n_chunks : corr_items(I);
-        const int last = atomicAdd(&stage_cnt[i], 1) == n - 1;
+        const int c = atomicAdd(&stage_cnt[i], 1);
+        w = atomicAdd(&q->head, 1ull);   // polled after any publish below
+        claimed = true;
+        const int last = c == n - 1;
         if (last) {
           stage_cnt[i] = 0;
           __threadfence();
