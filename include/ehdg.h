@@ -168,7 +168,9 @@ typedef struct {
                                   sweep wrote Ey u^n at every owned point, so only the inflow
                                   boundary points are recomputed from the new boundary data
                                   (backward Euler or steady transport on hexahedra with no
-                                  beta.n = 0 point). ehdg_set_state starts cold again. */
+                                  beta.n = 0 point; backward-Euler shallow water, whose wall
+                                  trace reads no boundary data). ehdg_set_state starts cold
+                                  again. */
 } ehdg_info;
 
 /* Structured N0 x N1 (x N2) mesh of the box [lo, hi] with the numbering

@@ -1027,6 +1027,12 @@ ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* pro
       CKC(cudaMemcpy(c.tan_face, tf.data(), sizeof(int32_t) * tf.size(), cudaMemcpyHostToDevice));
     }
   }
+  if (c.pde == EHDG_SW_LINEAR) {
+    // shallow water: the trace formula reads no boundary data (walls), so a
+    // warm step starts from the previous step's final trace unchanged (no
+    // shallow-water instance iterates in the batched loop)
+    c.warm_ok = c.scheme != EHDG_CN;
+  }
   if (pe_supported(c)) {
     // one thread per element for the 2D shared-operator FP64 sweep
     std::vector<double> fw(kMaxQ * kMaxQ, 0.0);

@@ -846,7 +846,8 @@ __global__ void k_trace0_warm(const int* warm, const int32_t* bface, int64_t n_b
 }
 
 int face_launches(const Ctx& c, int mode) {
-  return (mode == kFaceInitial && c.warm_ok && c.n_bface > 0) ? 2 : 1;
+  // transport: the warm start's inflow boundary points (shallow water has none)
+  return (mode == kFaceInitial && c.warm_ok && c.pde == EHDG_TRANSPORT && c.n_bface > 0) ? 2 : 1;
 }
 
 cudaError_t launch_face(Ctx& c, int mode, int graph_mode) {
