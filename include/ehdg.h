@@ -305,7 +305,9 @@ ehdg_status ehdg_batch_set_chains(ehdg_batch b, int k);
  * instances run their own loops on the branches, concurrently. An instance's
  * iterates are the same, bit for bit, either way. on = 0 runs every instance
  * on the branches. on = 2 is the loop's persistent form where every looped
- * instance is FP64 or has FP32 corrections (else on = 1): all iterations of a
+ * instance is FP64 or has FP32 corrections and their largest stages fit the
+ * ring of 65,536 work items together (about 8 million elements; else on = 1):
+ * all iterations of a
  * step in ONE launch, each instance at its own pace -- the block that
  * completes a stage of an instance (its FP64 sweep, a correction sweep, the
  * FP64 update) publishes the next stage's work items to a ring in device

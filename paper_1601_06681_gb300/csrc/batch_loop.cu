@@ -1351,7 +1351,19 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
       if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
     }
   }
-  if (!L.any_mma) {
+  // the persistent form: every instance holds at most one stage's items in
+  // the ring at a time, so the ring must hold the largest stage of every
+  // instance at once (plus a claim per block); larger batches keep the loop
+  // of launches
+  int64_t ring_need = 0;
+  for (int i = 0; i < L.n_inst; ++i) {
+    const int corr = (h[i].n_tiles128 + kQCorrTiles - 1) / kQCorrTiles;
+    ring_need += std::max({(int64_t)h[i].n_tiles_pe, (int64_t)corr, (int64_t)h[i].n_chunks});
+  }
+  // a block holds at most two positions (its item and the next claim), at
+  // most 8 blocks per SM
+  const bool persist_fits = ring_need + 16 * (int64_t)device_sms() <= kQCap;
+  if (!L.any_mma && persist_fits) {
     // the persistent form reads every instance's sweep rows in row order
     std::vector<size_t> off(L.n_inst, 0), off32(L.n_inst, 0);
     size_t bytes = 0;
@@ -1430,7 +1442,7 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
     L.tc_grid = std::max(1, std::min(bpsm * device_sms(), L.n_tc));
     L.apply_grid = std::max(1, std::min(device_sms() * 8, L.n_apply));
   }
-  if (!L.any_mma) {
+  if (!L.any_mma && persist_fits) {
     // the persistent form: one wave of resident blocks
     if ((e = cudaMalloc(&L.d_q, sizeof(BQueue))) != cudaSuccess) return e;
     if ((e = cudaMemset(L.d_q, 0, sizeof(BQueue))) != cudaSuccess) return e;
