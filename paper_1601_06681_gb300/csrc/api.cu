@@ -1763,6 +1763,13 @@ ehdg_status ehdg_batch_autotune_schedule(ehdg_batch b, const int* chain_cands, i
   if (!b || !chain_cands || n_cands < 1) return fail(EHDG_ERR_INVALID, "bad argument");
   const bool saved_loop = b->use_loop, saved_persist = b->use_persist;
   const int saved_chains = b->chains;
+  // the persistent form is a candidate only where it applies (the instances
+  // the loop takes, FP64 or FP32 corrections, fitting its ring)
+  std::vector<const Ctx*> looped;
+  for (auto h : b->inst)
+    if (batch_loop_ok(h->c) && !h->c.have_force) looped.push_back(&h->c);
+  const bool persist_applies =
+      !looped.empty() && looped.size() <= 8192 && batch_persist_fits(looped);
   // variant 0: the batched loop, 1: its persistent form (branches keep the
   // current count); variant q >= 2: every instance on the branches,
   // chain_cands[q - 2] of them
@@ -1771,6 +1778,7 @@ ehdg_status ehdg_batch_autotune_schedule(ehdg_batch b, const int* chain_cands, i
       b, n_cands + 2,
       [&](int q) {
         if (q >= 2 && chain_cands[q - 2] < 1) return false;
+        if (q == 1 && !persist_applies) return false;
         b->use_loop = q < 2;
         b->use_persist = q == 1;
         if (q >= 2) b->chains = chain_cands[q - 2];

@@ -1160,6 +1160,24 @@ bool batch_loop_ok(const Ctx& c) {
          (c.precision == EHDG_FP64 || c.precision == EHDG_MIXED_FP32 || tc_supported(c));
 }
 
+// The persistent form applies to these looped instances: every one is FP64 or
+// has FP32 corrections, and their largest stages fit the ring together (an
+// instance holds at most one stage's items in it at a time) with two
+// positions per block (its item and its next claim), at most 8 blocks per SM.
+bool batch_persist_fits(const std::vector<const Ctx*>& looped) {
+  int64_t need = 0;
+  for (const Ctx* c : looped) {
+    const bool mma = c->mixed && c->precision != EHDG_MIXED_FP32;
+    if (mma) return false;
+    const int64_t tiles = (c->nel + kPeTile - 1) / kPeTile;
+    const int64_t corr = c->mixed ? (tiles + kQCorrTiles - 1) / kQCorrTiles : 0;
+    const int64_t chunks =
+        c->mixed ? ((int64_t)c->Nqf * c->nface + kApplyChunk - 1) / kApplyChunk : 0;
+    need += std::max({tiles, corr, chunks});
+  }
+  return need + 16 * (int64_t)device_sms() <= kQCap;
+}
+
 struct BatchLoop::Impl {
   BInst* d_inst = nullptr;
   int4* d_counts = nullptr;
@@ -1351,18 +1369,8 @@ cudaError_t BatchLoop::build(const std::vector<Ctx*>& ctxs, unsigned long long* 
       if ((e = cudaDeviceSynchronize()) != cudaSuccess) return e;
     }
   }
-  // the persistent form: every instance holds at most one stage's items in
-  // the ring at a time, so the ring must hold the largest stage of every
-  // instance at once (plus a claim per block); larger batches keep the loop
-  // of launches
-  int64_t ring_need = 0;
-  for (int i = 0; i < L.n_inst; ++i) {
-    const int corr = (h[i].n_tiles128 + kQCorrTiles - 1) / kQCorrTiles;
-    ring_need += std::max({(int64_t)h[i].n_tiles_pe, (int64_t)corr, (int64_t)h[i].n_chunks});
-  }
-  // a block holds at most two positions (its item and the next claim), at
-  // most 8 blocks per SM
-  const bool persist_fits = ring_need + 16 * (int64_t)device_sms() <= kQCap;
+  const bool persist_fits =
+      batch_persist_fits(std::vector<const Ctx*>(ctxs.begin(), ctxs.end()));
   if (!L.any_mma && persist_fits) {
     // the persistent form reads every instance's sweep rows in row order
     std::vector<size_t> off(L.n_inst, 0), off32(L.n_inst, 0);

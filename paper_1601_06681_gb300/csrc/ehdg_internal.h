@@ -308,6 +308,8 @@ bool tc_apply_fusable(const Ctx& c);
 // Batched iteration loop of a batch's looped instances (batch_loop.cu): one
 // launch per kernel and iteration over every unconverged instance.
 bool batch_loop_ok(const Ctx& c);   // the instance can run in the batched loop
+// the batched loop's persistent form applies to these looped instances
+bool batch_persist_fits(const std::vector<const Ctx*>& looped);
 struct BatchLoop {
   struct Impl;
   Impl* impl = nullptr;
