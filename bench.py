@@ -425,16 +425,20 @@ def events_ms_each(stream, fn, reps):
     return times, out
 
 
-def fastest_m(cands, build, stream):
+def fastest_m(cands, build, stream, timer=None):
     """Inner sweep count of mixed precision whose whole run is fastest:
     build(m) -> (context, one_run); each candidate is timed over one run after
-    a warm-up run. Returns (context, one_run, m, {m: ms}) with the kept
-    context open and the others closed."""
+    a warm-up run (timer(run) -> ms; CUDA events on `stream` by default).
+    Returns (context, one_run, m, {m: ms}) with the kept context open and the
+    others closed."""
+    if timer is None:
+        def timer(run):
+            return events_ms_each(stream, run, 1)[0][0]
     best, tried = None, {}
     for m in cands:
         ctx, run = build(m)
         run()                                               # warm-up (captures the graph)
-        t = events_ms_each(stream, run, 1)[0][0]
+        t = timer(run)
         tried[str(m)] = round(t, 2)
         if best is None or t < best[3]:
             if best is not None:

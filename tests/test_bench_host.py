@@ -62,3 +62,36 @@ def test_combine_ranks_over_two_gloo_ranks(tmp_path):
         assert value == 300.0 / 2e-3
     bench = load_bench()
     assert bench.combine_ranks(4.0, 50, 1) == (4.0, 50, 50 / 4e-3)
+
+
+def test_inner_sweep_tuner_keeps_the_fastest_run_and_closes_the_rest():
+    """fastest_m: every candidate is built, warmed up once and timed once; the
+    fastest one's context stays open, every other is closed, and the timings
+    are reported per candidate."""
+    bench = load_bench()
+    cost = {4: 9.0, 8: 5.0, 12: 3.0, 16: 7.0}
+
+    class Ctx:
+        def __init__(self, m):
+            self.m, self.closed, self.runs = m, False, 0
+
+        def close(self):
+            self.closed = True
+
+    built = []
+
+    def build(m):
+        c = Ctx(m)
+        built.append(c)
+
+        def run():
+            c.runs += 1
+            return m
+        return c, run
+
+    ctx, run, m, tried = bench.fastest_m((4, 8, 12, 16), build, None,
+                                         timer=lambda r: cost[r()])
+    assert m == 12 and ctx.m == 12 and not ctx.closed and run() == 12
+    assert tried == {"4": 9.0, "8": 5.0, "12": 3.0, "16": 7.0}
+    assert [c.closed for c in built] == [True, True, False, True]
+    assert all(c.runs >= 2 for c in built)      # a warm-up run, then the timed run
