@@ -95,3 +95,24 @@ def test_inner_sweep_tuner_keeps_the_fastest_run_and_closes_the_rest():
     assert tried == {"4": 9.0, "8": 5.0, "12": 3.0, "16": 7.0}
     assert [c.closed for c in built] == [True, True, False, True]
     assert all(c.runs >= 2 for c in built)      # a warm-up run, then the timed run
+
+
+def test_inner_sweep_tuner_default_timer_uses_the_event_timer(monkeypatch):
+    """Without a timer, fastest_m times each candidate with events_ms_each on
+    the given stream (one run)."""
+    bench = load_bench()
+    calls = []
+
+    def fake_events(stream, fn, reps):
+        calls.append((stream, reps))
+        return [float(fn())], None
+
+    monkeypatch.setattr(bench, "events_ms_each", fake_events)
+
+    class Ctx:
+        def close(self):
+            pass
+
+    ctx, run, m, tried = bench.fastest_m((6, 3), lambda m: (Ctx(), lambda: m), "s0")
+    assert m == 3 and tried == {"6": 6.0, "3": 3.0}
+    assert calls == [("s0", 1), ("s0", 1)]
