@@ -700,3 +700,35 @@ def test_l2_volume_pin_catches_planted_mistakes(monkeypatch):
         assert abs(got - exact) > 1e-3 * exact, what
     monkeypatch.setattr(B, "gauss", real_gauss)
     assert abs(l2_volume(prob, u) ** 2 - exact) <= 1e-13 * exact
+
+
+def test_trace_formula_reads_boundary_data_only_at_inflow_and_tangential_boundary_points():
+    """Where the trace formula reads boundary data (the reading of the
+    boundary trace, eq. transportLocale with exterior value g): changing g
+    changes uhat only at boundary points with beta.n^- <= 0 (inflow, or the
+    average at tangential points); every other point depends on the element
+    values alone. Shallow water with walls reads no boundary data at all.
+    This is what lets a time step start from the previous step's final trace
+    with only the inflow boundary points recomputed."""
+    rng = np.random.default_rng(7)
+    for mesh, p, beta in ((W.structured_mesh((4, 3)), 2, np.array([0.8, -0.5])),
+                          (W.structured_mesh((3, 2, 2)), 1, np.array([0.6, 0.4, -0.7])),
+                          (W.structured_mesh((4, 3)), 2, np.array([0.9, 0.0]))):
+        prob = Problem(mesh, p, scheme="be", dt=0.05, beta_const=beta)
+        u = rng.standard_normal((prob.nel, 1, prob.Np))
+        g1 = rng.standard_normal((prob.nface, prob.ref.Nqf))
+        g2 = rng.standard_normal((prob.nface, prob.ref.Nqf))
+        # the oracle forms the upwind value arithmetically, so g cancels at
+        # outflow points only up to rounding
+        changed = np.abs(prob.trace(u, g1) - prob.trace(u, g2)) > 1e-13
+        boundary = mesh["face_elem"][:, 1] < 0
+        bn = np.array([prob.beta_normal(e) for e in range(prob.nface)])
+        bn = np.broadcast_to(bn.reshape(prob.nface, -1), changed.shape)
+        may = boundary[:, None] & (bn <= 0)
+        assert not np.any(changed & ~may)
+        assert np.all(changed[boundary[:, None] & (bn < 0)])   # inflow points take g
+    mesh = W.structured_mesh((4, 3), boundary_tag=W.TAG_WALL)
+    sw = Problem(mesh, 2, pde="sw", scheme="be", dt=2e-3, Phi=1.3)
+    u = rng.standard_normal((sw.nel, 3, sw.Np))
+    assert np.array_equal(sw.trace(u, rng.standard_normal((sw.nface, sw.ref.Nqf))),
+                          sw.trace(u, None))
