@@ -51,3 +51,32 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(E):
         E.ehdg_trace_residual_noalloc(z, z, z, out)
     assert ei.value.status == 7
     assert "exceeds the maximum" in str(ei.value)
+
+
+def test_noalloc_call_captures_into_a_cuda_graph_and_replays(E):
+    """After a first call outside capture (which looks up the fixed array's
+    address), a later call is captured: the capture allocates nothing and
+    launches nothing, and each replay reads the inputs' current contents."""
+    import torch
+    n = 100_003
+    a, b, w = _inputs(n, 11)
+    ref = torch.zeros(1, dtype=torch.float64, device="cuda")
+    out = torch.full((1,), -1.0, dtype=torch.float64, device="cuda")
+    E.ehdg_trace_residual_noalloc(a, b, w, out)          # first call, outside capture
+    torch.cuda.synchronize()
+    out.fill_(-1.0)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        E.ehdg_trace_residual_noalloc(a, b, w, out, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert out.item() == -1.0                              # captured, not run
+    rng = np.random.default_rng(12)
+    for rep in range(3):
+        if rep:                                            # new values in the same buffers
+            b.copy_(a + torch.from_numpy(1e-3 * rng.standard_normal(n)).cuda())
+        E.ehdg_trace_residual(a, b, w, ref)
+        out.fill_(-1.0)
+        g.replay()
+        torch.cuda.synchronize()
+        assert abs(out.item() - ref.item()) <= 1e-13 * abs(ref.item())
