@@ -1240,7 +1240,7 @@ static void batch_destroy_graph(ehdg_batch b) {
 }
 
 // Hardware work queues the GPU runs concurrent branches on: the value of
-// CUDA_DEVICE_MAX_CONNECTIONS the driver read at context creation (8 if
+// CUDA_DEVICE_MAX_CONNECTIONS the CUDA driver read at context creation (8 if
 // unset, at most 32).
 static int hw_queues() {
   const char* v = std::getenv("CUDA_DEVICE_MAX_CONNECTIONS");
