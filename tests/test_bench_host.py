@@ -116,3 +116,58 @@ def test_inner_sweep_tuner_default_timer_uses_the_event_timer(monkeypatch):
     ctx, run, m, tried = bench.fastest_m((6, 3), lambda m: (Ctx(), lambda: m), "s0")
     assert m == 3 and tried == {"6": 6.0, "3": 3.0}
     assert calls == [("s0", 1), ("s0", 1)]
+
+
+def _tuner_fixture():
+    class Ctx:
+        def __init__(self, m):
+            self.m, self.closed = m, False
+
+        def close(self):
+            self.closed = True
+
+    built = {}
+
+    def build(m):
+        c = Ctx(m)
+        built[m] = c
+        return c, (lambda: m)
+    return build, built
+
+
+def test_inner_sweep_tuner_refines_between_grid_points():
+    """With refine, the search steps by one from the fastest grid point in the
+    direction that is faster and stops where the next step is slower: run time
+    falls from 16 to 14 and rises at 13 (the step shape of an integer outer
+    iteration count)."""
+    bench = load_bench()
+    cost = {8: 94.0, 12: 94.5, 13: 83.0, 14: 82.2, 15: 86.0, 16: 87.3, 17: 88.0,
+            20: 97.3, 24: 107.0}
+    build, built = _tuner_fixture()
+    ctx, run, m, tried = bench.fastest_m((8, 12, 16, 20, 24), build, None,
+                                         timer=lambda r: cost[r()], refine=4)
+    assert m == 14 and ctx.m == 14 and not ctx.closed and run() == 14
+    assert list(tried) == ["8", "12", "16", "20", "24", "15", "14", "13"]
+    assert [k for k, c in built.items() if not c.closed] == [14]
+
+
+def test_inner_sweep_tuner_refine_is_bounded_and_stays_in_range():
+    """The refine steps build at most `refine` more contexts, never leave the
+    library's range 1..64 and never rebuild a tried count; refine = 0 (the
+    default) tries the grid alone."""
+    bench = load_bench()
+    build, built = _tuner_fixture()
+    ctx, _, m, tried = bench.fastest_m((4, 8), build, None, timer=lambda r: float(r()),
+                                       refine=2)
+    assert (m, list(tried)) == (2, ["4", "8", "3", "2"])       # downhill, 2 steps only
+    build, built = _tuner_fixture()
+    ctx, _, m, tried = bench.fastest_m((2, 1), build, None, timer=lambda r: float(r()),
+                                       refine=4)
+    assert (m, list(tried)) == (1, ["2", "1"])                 # m = 0 is out of range
+    build, built = _tuner_fixture()
+    ctx, _, m, tried = bench.fastest_m((64, 60), build, None, timer=lambda r: -float(r()),
+                                       refine=4)
+    assert (m, list(tried)) == (64, ["64", "60", "63"])        # 65 is out of range
+    build, built = _tuner_fixture()
+    ctx, _, m, tried = bench.fastest_m((4, 8), build, None, timer=lambda r: float(r()))
+    assert (m, list(tried)) == (4, ["4", "8"])
