@@ -171,3 +171,38 @@ def test_inner_sweep_tuner_refine_is_bounded_and_stays_in_range():
     build, built = _tuner_fixture()
     ctx, _, m, tried = bench.fastest_m((4, 8), build, None, timer=lambda r: float(r()))
     assert (m, list(tried)) == (4, ["4", "8"])
+
+
+def _bench_cmd(args, env_extra):
+    import json
+    import subprocess
+    env = dict(os.environ, **env_extra)
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT,
+                       env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    return [json.loads(ln) for ln in lines]
+
+
+def test_reference_arm_prints_one_line_on_the_gpu_arms_workload_and_metric():
+    """bench.py --impl reference (the oracle on the host cores, no GPU): one
+    JSON line with the GPU arm's metric, unit, direction and workload name, a
+    cpu_baseline describing the run and an e2e with no host-device bytes."""
+    bench = load_bench()
+    out = _bench_cmd(["--impl", "reference", "--steps", "1", "--warmup", "0"],
+                     {"WORLD_SIZE": "1", "RANK": "0"})
+    assert len(out) == 1
+    d = out[0]
+    assert d["impl"] == "reference"
+    assert (d["metric"], d["unit"], d["higher_is_better"]) == (bench.METRIC, bench.UNIT, True)
+    assert d["config"]["workload"] == "transport3d_64x64x64_p3_be"
+    assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_other_ranks_exit_without_work():
+    """Under torchrun only rank 0 runs and prints the reference line."""
+    assert _bench_cmd(["--impl", "reference", "--steps", "1", "--warmup", "0"],
+                      {"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"}) == []
