@@ -186,7 +186,12 @@ void ehdg_mesh_free(ehdg_mesh_desc* mesh);
  * stream) on which all later work of the context is ordered. */
 ehdg_status ehdg_create(const ehdg_mesh_desc* mesh, const ehdg_problem_desc* prob,
                         void* cuda_stream, ehdg_ctx* out);
+/* Sizes of the context's arrays and the kernels it chose (ehdg_info above).
+ * EHDG_ERR_INVALID for a NULL argument. */
 ehdg_status ehdg_get_info(ehdg_ctx ctx, ehdg_info* out);
+/* Waits for the context's stream, then frees every device and host array the
+ * context owns. NULL is a no-op. The contexts of a batch belong to it and are
+ * freed by ehdg_batch_destroy, not here. */
 void ehdg_destroy(ehdg_ctx ctx);
 
 /* Physical coordinates of the volume nodes [n_elem][Np][dim] and of the face
@@ -223,6 +228,12 @@ ehdg_status ehdg_run(ehdg_ctx ctx, int n_steps, int* iters_per_step);
  * without the convergence test (the step is then completed as by ehdg_step). */
 ehdg_status ehdg_step_fixed(ehdg_ctx ctx, int n_iter);
 
+/* Copy the current state u^n [n_elem][nf][Np] and its trace uhat
+ * [n_face][Nqf] (either pointer may be NULL to skip it) out of the context's
+ * internal layout, into device memory (on_device) or host memory (through
+ * the context's staging array). Ordered after the context's earlier work;
+ * returns once the copies are complete. EHDG_ERR_INVALID for a NULL context,
+ * EHDG_ERR_CUDA if a copy fails. */
 ehdg_status ehdg_get_state(ehdg_ctx ctx, double* u, double* uhat, int on_device);
 
 /* Checkpoint and resume. ehdg_save writes everything a later step depends on:
@@ -429,7 +440,10 @@ ehdg_status ehdg_probe_fp64_rate(void* stream, int* sms, double* tflops);
 /* Kernel accounting. Every launch is counted per kind; with profiling on,
  * each launch is also bracketed by CUDA events on the context's stream and
  * ehdg_kernel_stats returns the summed device time of the kind (it
- * synchronises the stream). Turning profiling on resets the counters. */
+ * synchronises the stream). With profiling on, ehdg_step and ehdg_run drive
+ * the iteration from the host (one launch per kernel, the same kernels and
+ * iterates as the graph) so that every launch can be timed. ehdg_set_profiling
+ * (either value) synchronises the stream and resets the counters. */
 typedef enum {
   EHDG_KERNEL_ASSEMBLE = 0,    /* local operator assembly + factorisation (setup) */
   EHDG_KERNEL_SIGNS = 1,       /* sgn(beta.n) at face points (setup) */
@@ -444,6 +458,9 @@ typedef enum {
 ehdg_status ehdg_set_profiling(ehdg_ctx ctx, int on);
 ehdg_status ehdg_kernel_stats(ehdg_ctx ctx, int kind, int64_t* launches, double* total_ms);
 
+/* Message of the last failed call on the calling thread (the message is
+ * kept per thread; a later failure replaces it). The pointer stays valid until
+ * the thread's next failing call. */
 const char* ehdg_last_error(void);
 
 #ifdef __cplusplus
