@@ -206,3 +206,38 @@ def test_reference_arm_other_ranks_exit_without_work():
     """Under torchrun only rank 0 runs and prints the reference line."""
     assert _bench_cmd(["--impl", "reference", "--steps", "1", "--warmup", "0"],
                       {"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"}) == []
+
+
+def test_traffic_record_is_dropped_once_the_kernel_source_changes(tmp_path, monkeypatch):
+    """kernel_traffic returns the recorded DRAM bytes only while the kernel's
+    source files hash to the value stored with the capture; an edit to any of
+    them makes the bench report no traffic (null) instead of a stale figure."""
+    import json
+    bench = load_bench()
+    csrc = tmp_path / "paper_1601_06681_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "a.cu").write_text("kernel a\n")
+    (csrc / "b.cuh").write_text("helper b\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    rec = {"k_a@w": {"bytes_per_sweep": 1234, "sources": ["a.cu", "b.cuh"],
+                     "source_sha": bench.source_sha(["a.cu", "b.cuh"])}}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
+    assert bench.kernel_traffic("k_a@w") == 1234
+    assert bench.kernel_traffic("k_other@w") is None
+    (csrc / "b.cuh").write_text("helper b, changed\n")
+    assert bench.kernel_traffic("k_a@w") is None
+
+
+def test_committed_traffic_records_name_existing_sources():
+    """Every committed traffic record names source files that exist, with the
+    ncu command that measured it."""
+    import json
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        recs = json.load(fh)
+    assert recs
+    for key, ent in recs.items():
+        assert "@" in key and ent["bytes_per_sweep"] > 0
+        assert "--clock-control none" in ent["command"]
+        for s in ent["sources"]:
+            assert os.path.exists(os.path.join(ROOT, "paper_1601_06681_gb300", "csrc", s)), s
