@@ -241,3 +241,39 @@ def test_committed_traffic_records_name_existing_sources():
         assert "--clock-control none" in ent["command"]
         for s in ent["sources"]:
             assert os.path.exists(os.path.join(ROOT, "paper_1601_06681_gb300", "csrc", s)), s
+
+
+def test_clock_summary_reports_median_clock_and_every_active_throttle_reason():
+    """ClockSampler.summary over nvidia-smi's CSV (no units, no header): the
+    median SM clock, the maximum clock and each throttle reason seen Active in
+    any sample; lines it cannot parse are skipped; no sample at all is
+    reported as unsampled rather than as a clean run."""
+    bench = load_bench()
+    cs = bench.ClockSampler(0)
+    cs.out = "\n".join([
+        "0, 2070, 2070, 900.1, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.5, 0x0000000000000008, Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2070, 1000.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage",
+    ])
+    s = cs.summary()
+    assert s == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0,
+                 "reasons": ["hw_slowdown", "sw_power_cap"], "samples": 3}
+    cs.out = ""
+    assert cs.summary()["reasons"] == ["unsampled"]
+
+
+def test_measured_peaks_are_read_from_the_committed_file():
+    """The roofline denominators come from MEASURED_PEAKS.json when it exists
+    (labelled measured), else the stated fallback figures."""
+    import json
+    bench = load_bench()
+    peaks, src = bench.measured_peaks()
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            assert (peaks, src) == (json.load(fh), "measured")
+        assert peaks["hbm_gbs"] > 0
+    else:
+        assert src == "fallback" and peaks["hbm_gbs"] == 6800.0
