@@ -277,3 +277,20 @@ def test_measured_peaks_are_read_from_the_committed_file():
         assert peaks["hbm_gbs"] > 0
     else:
         assert src == "fallback" and peaks["hbm_gbs"] == 6800.0
+
+
+def test_fp64_sweep_flops_match_the_per_element_counts():
+    """The roofline's FP64 work per sweep of the 64^3, p = 3 headline: the
+    sum-factorised sweep executes 2 x 96 x 4 (two 1D passes over the 96 face
+    points) + 96 (face scaling) + 48 x 56 (owned rows x boundary nodes) =
+    3,552 FMAs per element; the dense form it replaces 48 x 96 = 4,608."""
+    bench = load_bench()
+    nel = 64 ** 3
+    info = {"n_elem": nel, "dim": 3, "Nqf": 16, "q": 4, "sweep_rows": 48 * nel,
+            "sum_factorised": 1}
+    name, flops, dense = bench.fp64_sweep(info)
+    assert name == "k_sweep_sf"
+    assert flops == 2.0 * 3552 * nel == 1862270976.0
+    assert dense == 2.0 * 4608 * nel
+    name, flops, dense = bench.fp64_sweep(dict(info, sum_factorised=0))
+    assert name == "k_sweep_fused" and flops == dense == 2.0 * 4608 * nel
