@@ -732,3 +732,78 @@ def test_trace_formula_reads_boundary_data_only_at_inflow_and_tangential_boundar
     u = rng.standard_normal((sw.nel, 3, sw.Np))
     assert np.array_equal(sw.trace(u, rng.standard_normal((sw.nface, sw.ref.Nqf))),
                           sw.trace(u, None))
+
+
+def _planted_transport_trace(kind):
+    """The transport trace formula of eq. transportLocale with one plausible
+    slip planted (kind "none" is the formula itself, written out again here so
+    that the harness is checked too)."""
+    def trace(self, u, g=None):
+        uh = np.empty((self.nface, self.ref.Nqf))
+        for e in range(self.nface):
+            vm, _ = self.face_values(u, e, 0)
+            interior = self.mesh["face_elem"][e, 1] >= 0
+            s_m = np.sign(self.beta_normal(e))
+            if kind == "downwind":
+                s_m = -s_m
+            s_p = s_m if kind == "plus-side normal not flipped" else -s_m
+            u_m = vm[0]
+            if interior:
+                u_p = self.face_values(u, e, 1)[0][0]
+            else:
+                u_p = u_m if kind == "boundary data ignored" else g[e]
+            half = 1.0 if kind == "average not halved" else 0.5
+            uh[e] = 0.5 * (u_m * s_m + u_p * s_p) + half * (u_m + u_p)
+        return uh
+    return trace
+
+
+def _steady_reproduction_error():
+    """Max nodal error of the steady eHDG fixed point for a Q^1 solution on a
+    3 x 4 mesh, p = 2 (the exact-reproduction pin above, bounded to 300
+    iterations)."""
+    p, beta = 2, np.array([1.0, 0.5])
+    mesh = W.structured_mesh((3, 4))
+    prob = Problem(mesh, p, scheme="steady", beta_const=beta)
+    ue = lambda x: 1 + x[..., 0] - 2 * x[..., 1] + x[..., 0] * x[..., 1]
+    grad = lambda x: np.stack([1 + x[..., 1], -2 + x[..., 0]], -1)
+    X, XF = node_coords(mesh, p), face_point_coords(mesh, p, prob.ref.q)
+    with np.errstate(all="ignore"):
+        u, _, _ = prob.solve_step(np.zeros((prob.nel, 1, prob.Np)), g_new=ue(XF),
+                                  f_new=(grad(X) @ beta)[:, None, :], tol=1e-14, max_iter=300)
+        err = np.abs(u[:, 0, :] - ue(X)).max()
+    return float(err) if np.isfinite(err) else math.inf
+
+
+def _boundary_data_read_only_at_inflow():
+    """The boundary-data pin above on one mesh: True when g changes uhat at
+    every inflow boundary point and nowhere with beta.n^- > 0."""
+    rng = np.random.default_rng(3)
+    mesh = W.structured_mesh((4, 3))
+    prob = Problem(mesh, 2, scheme="be", dt=0.05, beta_const=np.array([0.8, -0.5]))
+    u = rng.standard_normal((prob.nel, 1, prob.Np))
+    g1 = rng.standard_normal((prob.nface, prob.ref.Nqf))
+    g2 = rng.standard_normal((prob.nface, prob.ref.Nqf))
+    changed = np.abs(prob.trace(u, g1) - prob.trace(u, g2)) > 1e-13
+    boundary = mesh["face_elem"][:, 1] < 0
+    bn = np.array([prob.beta_normal(e) for e in range(prob.nface)]).reshape(changed.shape)
+    return (not np.any(changed & ~(boundary[:, None] & (bn <= 0)))
+            and bool(np.all(changed[boundary[:, None] & (bn < 0)])))
+
+
+@pytest.mark.parametrize("kind", ["downwind", "plus-side normal not flipped",
+                                  "boundary data ignored", "average not halved"])
+def test_trace_formula_pins_catch_planted_mistakes(kind, monkeypatch):
+    """Each plausible slip in the transport trace formula fails both the
+    exact reproduction pin and the boundary-data pin: taking the downwind
+    value (the polynomial solution is still a fixed point of it, but the
+    iteration diverges, and g is read at outflow points), not flipping the
+    normal on the plus side, using the interior value instead of g at the
+    boundary, or dropping the 1/2 of the average. The formula written out
+    again without a slip passes both."""
+    monkeypatch.setattr(Problem, "trace", _planted_transport_trace("none"))
+    assert _steady_reproduction_error() < 1e-12
+    assert _boundary_data_read_only_at_inflow()
+    monkeypatch.setattr(Problem, "trace", _planted_transport_trace(kind))
+    assert _steady_reproduction_error() > 1e-6, kind
+    assert not _boundary_data_read_only_at_inflow(), kind
