@@ -63,6 +63,27 @@ def test_steady_reproduces_linear_variable_beta():
     assert np.abs(u[:, 0, :] - ue(X)).max() < 1e-12
 
 
+def test_steady_reproduces_linear_divergent_variable_beta():
+    """A per-node velocity with nonzero divergence, beta = (1.5 - x, 1.2 - y)
+    (div beta = -2, the sign of Theorem 1's assumption): the advective form
+    beta.grad u = f still has every linear u as its exact discrete solution.
+    The field above is divergence-free; this one also exercises the
+    (div beta) v part of the volume term -(u, div(beta v))."""
+    p = 2
+    mesh = W.structured_mesh((4, 3))
+    X = node_coords(mesh, p)
+    prob = Problem(mesh, p, scheme="steady",
+                   beta_nodes=beta_from(X, [1.5 - X[..., 0], 1.2 - X[..., 1]]))
+    ue = lambda x: 1 + x[..., 0] - 2 * x[..., 1]
+    f = ((1.5 - X[..., 0]) * 1 + (1.2 - X[..., 1]) * (-2))[:, None, :]
+    XF = face_point_coords(mesh, p, prob.ref.q)
+    u, uh, hist = prob.solve_step(np.zeros((prob.nel, 1, prob.Np)), g_new=ue(XF), f_new=f,
+                                  tol=1e-14, max_iter=2000)
+    assert hist[-1] < 1e-14
+    assert np.abs(u[:, 0, :] - ue(X)).max() < 1e-12
+    assert np.abs(uh - ue(XF)).max() < 1e-12
+
+
 def test_steady_reproduces_polynomial_3d():
     p = 2
     mesh = W.structured_mesh((2, 3, 2))
@@ -807,3 +828,107 @@ def test_trace_formula_pins_catch_planted_mistakes(kind, monkeypatch):
     monkeypatch.setattr(Problem, "trace", _planted_transport_trace(kind))
     assert _steady_reproduction_error() > 1e-6, kind
     assert not _boundary_data_read_only_at_inflow(), kind
+
+
+def _planted_transport_element(kind):
+    """local_ops.transport_element with one plausible slip planted in its
+    output (kind "none" returns it unchanged): the volume term transposed,
+    the upwind face term with beta.n - |beta.n| in place of beta.n + |beta.n|,
+    B with beta.n in place of |beta.n|, the mass matrix without the volume
+    Jacobian, or the derivative of a variable velocity dropped."""
+    from oracle import local_ops
+    real = local_ops.transport_element
+
+    def element(ref, h, beta_nodes):
+        M, Asp, B = real(ref, h, beta_nodes)
+        if kind == "none":
+            return M, Asp, B
+        h = np.asarray(h, dtype=np.float64)
+        J = np.prod(h / 2.0)
+        face_up, face_down, B_signed = np.zeros_like(Asp), np.zeros_like(Asp), np.zeros_like(B)
+        Nqf = ref.Nqf
+        for f in range(2 * ref.dim):
+            ax, side = divmod(f, 2)
+            Phi_f = ref.fphi[f]
+            bn = (1.0 if side else -1.0) * (Phi_f @ beta_nodes[ax])
+            wf = ref.fW[f] * J * 2.0 / h[ax]
+            face_up += Phi_f.T @ ((wf * (bn + np.abs(bn)))[:, None] * Phi_f)
+            face_down += Phi_f.T @ ((wf * (bn - np.abs(bn)))[:, None] * Phi_f)
+            B_signed[:, f * Nqf:(f + 1) * Nqf] = Phi_f.T * (wf * bn)[None, :]
+        vol = Asp - face_up
+        if kind == "volume term transposed":
+            return M, vol.T + face_up, B
+        if kind == "downwind face term":
+            return M, vol + face_down, B
+        if kind == "B with signed beta.n":
+            return M, Asp, B_signed
+        if kind == "mass without Jacobian":
+            return M / J, Asp, B
+        if kind == "velocity derivative dropped":
+            W = ref.W * J
+            dterm = np.zeros_like(ref.phi)
+            for a in range(ref.dim):
+                dterm += (2.0 / h[a]) * ((ref.dphi[a] @ beta_nodes[a])[:, None] * ref.phi)
+            return M, Asp + dterm.T @ (W[:, None] * ref.phi), B
+        raise ValueError(kind)
+    return element
+
+
+def _be_linear_in_time_error():
+    """Max nodal error after 4 BE steps of a solution linear in t (the exact
+    BE pin above, bounded to 300 iterations per step)."""
+    p, beta, dt = 2, np.array([0.7, 1.1]), 0.05
+    mesh = W.structured_mesh((3, 3))
+    prob = Problem(mesh, p, scheme="be", dt=dt, beta_const=beta)
+    a = lambda x: 1 + x[..., 0] - 2 * x[..., 1] + x[..., 0] * x[..., 1]
+    ga = lambda x: np.stack([1 + x[..., 1], -2 + x[..., 0]], -1)
+    X, XF = node_coords(mesh, p), face_point_coords(mesh, p, prob.ref.q)
+    ue = lambda x, t: a(x) * (1 + 2 * t)
+    f_of_t = lambda t: (a(X) * 2.0 + (1 + 2 * t) * (ga(X) @ beta))[:, None, :]
+    with np.errstate(all="ignore"):
+        u, _, _, _ = prob.run(ue(X, 0.0)[:, None, :], 4, g_of_t=lambda t: ue(XF, t),
+                              f_of_t=f_of_t, tol=1e-14, max_iter=300)
+        err = np.abs(u[:, 0, :] - ue(X, 4 * dt)).max()
+    return float(err) if np.isfinite(err) else math.inf
+
+
+def _variable_beta_reproduction_error(divergent=False):
+    """Max nodal error of the steady fixed point for a linear solution under a
+    per-node velocity (the two variable-velocity pins above: divergence-free,
+    or div beta = -2; bounded to 600 iterations)."""
+    p = 2
+    mesh = W.structured_mesh((4, 3))
+    X = node_coords(mesh, p)
+    bx, by = ((1.5 - X[..., 0], 1.2 - X[..., 1]) if divergent
+              else (X[..., 1] + 0.5, X[..., 0] + 0.2))
+    prob = Problem(mesh, p, scheme="steady", beta_nodes=beta_from(X, [bx, by]))
+    ue = lambda x: 1 + x[..., 0] - 2 * x[..., 1]
+    f = (bx * 1 + by * (-2))[:, None, :]
+    XF = face_point_coords(mesh, p, prob.ref.q)
+    with np.errstate(all="ignore"):
+        u, _, _ = prob.solve_step(np.zeros((prob.nel, 1, prob.Np)), g_new=ue(XF), f_new=f,
+                                  tol=1e-14, max_iter=600)
+        err = np.abs(u[:, 0, :] - ue(X)).max()
+    return float(err) if np.isfinite(err) else math.inf
+
+
+@pytest.mark.parametrize("kind", ["volume term transposed", "downwind face term",
+                                  "B with signed beta.n", "mass without Jacobian",
+                                  "velocity derivative dropped"])
+def test_element_operator_pins_catch_planted_mistakes(kind, monkeypatch):
+    """Each plausible slip in the transport element operators (eq.
+    transportLocal with the backward-Euler mass term) fails at least one of
+    the exact-reproduction pins: steady Q^p with constant velocity, steady
+    linear with a divergence-free and with a divergent per-node velocity,
+    backward Euler linear in time. The unchanged operators pass all four.
+    (The divergence-free field alone does not see a dropped velocity
+    derivative, which is why the divergent one is pinned too.)"""
+    from oracle import local_ops
+    checks = (_steady_reproduction_error, _variable_beta_reproduction_error,
+              lambda: _variable_beta_reproduction_error(divergent=True),
+              _be_linear_in_time_error)
+    monkeypatch.setattr(local_ops, "transport_element", _planted_transport_element("none"))
+    assert all(c() < 1e-11 for c in checks)
+    monkeypatch.setattr(local_ops, "transport_element", _planted_transport_element(kind))
+    errs = [c() for c in checks]
+    assert max(errs) > 1e-6, (kind, errs)
