@@ -932,3 +932,77 @@ def test_element_operator_pins_catch_planted_mistakes(kind, monkeypatch):
     monkeypatch.setattr(local_ops, "transport_element", _planted_transport_element(kind))
     errs = [c() for c in checks]
     assert max(errs) > 1e-6, (kind, errs)
+
+
+def _planted_sw_element(kind):
+    """local_ops.sw_element with one plausible slip planted in its source
+    terms (kind "none" returns it unchanged): the Coriolis terms with the
+    wrong sign or without the factor Phi, the beta-plane's f without the
+    shift y_m, the friction with the wrong sign or without Phi."""
+    from oracle import local_ops
+    real = local_ops.sw_element
+
+    def element(ref, h, Phi, lo=None, coriolis=(0.0, 0.0, 0.0), friction=0.0):
+        Mblk, A, B = real(ref, h, Phi, lo=lo, coriolis=coriolis, friction=friction)
+        if kind == "none":
+            return Mblk, A, B
+        Np = ref.Np
+        h = np.asarray(h, dtype=np.float64)
+        Wq = ref.W * np.prod(h / 2.0)
+        mass = lambda w: ref.phi.T @ ((Wq * w)[:, None] * ref.phi)
+        f0, beta_c, y_m = coriolis
+        y = (0.0 if lo is None else float(np.asarray(lo)[1])) + 0.5 * h[1] * (ref.X[:, 1] + 1.0)
+        U, V = slice(Np, 2 * Np), slice(2 * Np, 3 * Np)
+        A = A.copy()
+        if kind == "Coriolis sign":
+            d = 2.0 * Phi * mass(f0 + beta_c * (y - y_m))
+        elif kind == "Coriolis without Phi":
+            d = (Phi - 1.0) * mass(f0 + beta_c * (y - y_m))
+        elif kind == "beta-plane without y_m":
+            d = -Phi * mass(beta_c * y_m * np.ones_like(y))
+        else:
+            d = None
+        if d is not None:                 # the u-row holds -Phi f M, the v-row +Phi f M
+            A[U, V] += d
+            A[V, U] -= d
+        if kind == "friction sign":
+            A[U, U] -= 2.0 * friction * Phi * mass(np.ones_like(y))
+            A[V, V] -= 2.0 * friction * Phi * mass(np.ones_like(y))
+        if kind == "friction without Phi":
+            A[U, U] += friction * (1.0 - Phi) * mass(np.ones_like(y))
+            A[V, V] += friction * (1.0 - Phi) * mass(np.ones_like(y))
+        return Mblk, A, B
+    return element
+
+
+def _sw_manufactured_error(N=8, p=2):
+    """L2 error of the manufactured steady shallow-water solution (the order
+    pin above, one mesh) at Phi = 1.7, so that a missing factor Phi shows."""
+    Phi, f0, beta_c, y_m, gamma = 1.7, 0.8, 1.5, 0.5, 0.3
+    ex, fo = _sw_manufactured(Phi, f0, beta_c, y_m, gamma)
+    mesh = W.structured_mesh((N, N), boundary_tag=W.TAG_WALL)
+    prob = Problem(mesh, p, pde="sw", scheme="be", dt=1.0, Phi=Phi,
+                   coriolis=(f0, beta_c, y_m), friction=gamma)
+    X = node_coords(mesh, p)
+    u = np.stack([ex[k](X) for k in range(3)], 1)
+    f = np.stack([fo[k](X) for k in range(3)], 1)
+    for _ in range(20):
+        u, _ = direct.solve(prob, u, None, f_new=f)
+    return math.sqrt(sum(l2_volume(prob, np.roll(u, -k, axis=1), ex[k]) ** 2 for k in range(3)))
+
+
+@pytest.mark.parametrize("kind", ["Coriolis sign", "Coriolis without Phi",
+                                  "beta-plane without y_m", "friction sign",
+                                  "friction without Phi"])
+def test_sw_source_term_pin_catches_planted_mistakes(kind, monkeypatch):
+    """Each plausible slip in the shallow-water source terms (eq.
+    linearizedShallow) leaves an error at least 10 times the manufactured
+    solution's discretisation error on the same mesh (8 x 8, p = 2: 2.3e-3;
+    the slips give 0.09 to 650)."""
+    from oracle import local_ops
+    monkeypatch.setattr(local_ops, "sw_element", _planted_sw_element("none"))
+    ok = _sw_manufactured_error()
+    assert ok < 5e-3, ok
+    monkeypatch.setattr(local_ops, "sw_element", _planted_sw_element(kind))
+    bad = _sw_manufactured_error()
+    assert bad > 10.0 * ok, (kind, ok, bad)
