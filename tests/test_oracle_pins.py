@@ -1006,3 +1006,56 @@ def test_sw_source_term_pin_catches_planted_mistakes(kind, monkeypatch):
     monkeypatch.setattr(local_ops, "sw_element", _planted_sw_element(kind))
     bad = _sw_manufactured_error()
     assert bad > 10.0 * ok, (kind, ok, bad)
+
+
+def _planted_sw_trace(kind):
+    """The shallow-water trace of Sec. 3 (wall boundaries) with one plausible
+    slip planted: sqrt(Phi) dropped, the wall's mirror state with the normal
+    velocity reversed, the normal velocities differenced instead of averaged,
+    or the phi average not halved ("none" writes it out again unchanged)."""
+    def trace(self, u, g=None):
+        uh = np.empty((self.nface, self.ref.Nqf))
+        sq = 1.0 if kind == "sqrt(Phi) dropped" else np.sqrt(self.Phi)
+        for e in range(self.nface):
+            vm, fm = self.face_values(u, e, 0)
+            ax, side = divmod(fm, 2)
+            nsgn = 1.0 if side else -1.0
+            phi_m, un_m = vm[0], nsgn * vm[1 + ax]
+            if self.mesh["face_elem"][e, 1] >= 0:
+                vp, _ = self.face_values(u, e, 1)
+                phi_p, un_p = vp[0], -nsgn * vp[1 + ax]
+            else:
+                phi_p = phi_m
+                un_p = -un_m if kind == "wall normal velocity reversed" else un_m
+            jump = (un_m - un_p) if kind == "normal velocities differenced" else (un_m + un_p)
+            half = 1.0 if kind == "phi average not halved" else 0.5
+            uh[e] = half * (phi_m + phi_p) + sq * 0.5 * jump
+        return uh
+    return trace
+
+
+def _sw_fixed_point_vs_direct():
+    """Relative distance of the eHDG fixed point from the monolithic solve
+    (the shallow-water case of the fixed-point pin above, Phi = 1.5)."""
+    rng = np.random.default_rng(11)
+    mesh = W.structured_mesh((4, 3), boundary_tag=W.TAG_WALL)
+    prob = Problem(mesh, 2, pde="sw", scheme="be", dt=0.01, Phi=1.5)
+    u0 = rng.standard_normal((prob.nel, prob.nf, prob.Np))
+    with np.errstate(all="ignore"):
+        u, _, _ = prob.solve_step(u0, None, tol=1e-14, max_iter=400)
+        ud, _ = direct.solve(prob, u0, None)
+        r = rel(u, ud)
+    return float(r) if np.isfinite(r) else math.inf
+
+
+@pytest.mark.parametrize("kind", ["sqrt(Phi) dropped", "wall normal velocity reversed",
+                                  "normal velocities differenced", "phi average not halved"])
+def test_sw_trace_pin_catches_planted_mistakes(kind, monkeypatch):
+    """Each plausible slip in the shallow-water trace moves the eHDG fixed
+    point away from the monolithic HDG solve (which forms its own flux
+    conditions and never calls the trace formula); the formula written out
+    again without a slip agrees to 1e-12."""
+    monkeypatch.setattr(Problem, "trace", _planted_sw_trace("none"))
+    assert _sw_fixed_point_vs_direct() < 1e-12
+    monkeypatch.setattr(Problem, "trace", _planted_sw_trace(kind))
+    assert _sw_fixed_point_vs_direct() > 1e-6, kind
