@@ -53,8 +53,8 @@ typedef struct ehdg_ctx_s* ehdg_ctx;
 typedef enum {
   EHDG_OK = 0,
   EHDG_ERR_INVALID = 1,        /* bad argument or inconsistent mesh */
-  EHDG_ERR_OOM = 2,            /* device allocation failed */
-  EHDG_ERR_CUDA = 3,           /* a CUDA call failed */
+  EHDG_ERR_OOM = 2,            /* device or host memory exhausted */
+  EHDG_ERR_CUDA = 3,           /* a CUDA call failed (also: no usable device or driver) */
   EHDG_ERR_NOT_CONVERGED = 4,  /* max_iter reached; state and history stay readable */
   EHDG_ERR_DIVERGED = 5,       /* non-finite residual */
   EHDG_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */

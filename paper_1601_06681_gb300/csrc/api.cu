@@ -72,7 +72,10 @@ ehdg_status dalloc(Ctx& c, T** p, size_t count) {
   cudaError_t e = cudaMalloc(&q, count * sizeof(T));
   if (e != cudaSuccess) {
     cudaGetLastError();
-    return fail(EHDG_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    // out of memory is EHDG_ERR_OOM; any other failure (no device, no
+    // driver, a sticky error) is a CUDA error
+    return fail(e == cudaErrorMemoryAllocation ? EHDG_ERR_OOM : EHDG_ERR_CUDA,
+                std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
   }
   c.allocs.push_back(q);
   c.bytes += (int64_t)(count * sizeof(T));

@@ -68,3 +68,19 @@ def test_new_entry_points_reject_null_handles_without_a_gpu():
                                             C.byref(ms)) == 1
     assert lib.ehdg_autotune_sweep_tile(None, cands, 2, C.byref(best), C.byref(ms)) == 1
     assert b"NULL" in lib.ehdg_last_error() or b"bad argument" in lib.ehdg_last_error()
+
+
+def test_without_a_usable_gpu_the_solver_fails_loudly():
+    """On a machine without a usable GPU, creating a context raises EhdgError
+    with EHDG_ERR_CUDA (3) and the CUDA runtime's message: there is no CPU
+    fallback anywhere in the library or the binding."""
+    import pytest
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    build.build()
+    mesh = ehdg.ehdg_mesh_structured((4, 4))
+    with pytest.raises(ehdg.EhdgError) as ei:
+        ehdg.Solver(mesh, 2, scheme="be", dt=0.01, beta_const=[1.0, 0.5])
+    assert ei.value.status == 3
+    assert "cudaMalloc failed" in str(ei.value)
