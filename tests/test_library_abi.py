@@ -84,3 +84,94 @@ def test_without_a_usable_gpu_the_solver_fails_loudly():
         ehdg.Solver(mesh, 2, scheme="be", dt=0.01, beta_const=[1.0, 0.5])
     assert ei.value.status == 3
     assert "cudaMalloc failed" in str(ei.value)
+
+
+def _header_signatures():
+    """{name: (return type, [parameter declarations])} of every function the
+    header declares."""
+    src = open(os.path.join(ROOT, "include", "ehdg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#[^\n]*", "", src)
+    out = {}
+    for ret, name, params in re.findall(
+            r"((?:const\s+)?[A-Za-z_][\w]*\s*\**)\s*\b(ehdg_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", src):
+        ps = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        out[name] = (ret.replace(" ", ""), ps)
+    return out
+
+
+def _c_class(decl):
+    """'ptr', 'i32', 'i64' or 'f64' for one C parameter declaration."""
+    if "*" in decl or "[" in decl or re.match(r"(const\s+)?ehdg_(ctx|batch)\b", decl):
+        return "ptr"
+    t = decl.split()[0]
+    return {"int": "i32", "int32_t": "i32", "int64_t": "i64", "double": "f64"}[t]
+
+
+def _ctypes_class(t):
+    import ctypes as C
+    if t in (C.c_void_p, C.c_char_p) or hasattr(t, "_type_") and t.__name__.startswith("LP_"):
+        return "ptr"
+    return {C.c_int: "i32", C.c_int32: "i32", C.c_int64: "i64", C.c_double: "f64"}[t]
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes signature of the binding has the header's parameter count,
+    and each parameter the same class (pointer, 32- or 64-bit integer,
+    double) and, where the binding names the pointee, the same pointee type;
+    the return types agree (status int, void, or a C string)."""
+    import ctypes as C
+    hdr = _header_signatures()
+    sigs = {n: (r, a) for n, r, a in ehdg._SIGS}
+    assert sorted(hdr) == sorted(sigs)
+    pointee = {"int": C.c_int, "int64_t": C.c_int64, "double": C.c_double}
+    for name, (ret, params) in hdr.items():
+        res, args = sigs[name]
+        assert len(args) == len(params), name
+        for decl, t in zip(params, args):
+            assert _c_class(decl) == _ctypes_class(t), (name, decl, t)
+            m = re.match(r"(?:const\s+)?(int|int64_t|double)\s*\*", decl)
+            if m and t not in (C.c_void_p, C.c_char_p):
+                assert t._type_ is pointee[m.group(1)], (name, decl, t)
+        want_res = {"ehdg_status": C.c_int, "void": None, "constchar*": C.c_char_p}[ret]
+        assert res is want_res, (name, ret, res)
+
+
+def test_binding_structs_have_the_c_layout():
+    """The ctypes structures of the binding (mesh, problem and info
+    descriptors) have the layout the C compiler gives the header's structs:
+    every field's offset and size, and the total size. A field added to one
+    side only, or reordered, would otherwise corrupt every call silently."""
+    import ctypes as C
+    import shutil
+    import subprocess
+    import pytest
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    structs = {"ehdg_mesh_desc": ehdg.MeshDesc, "ehdg_problem_desc": ehdg.ProblemDesc,
+               "ehdg_info": ehdg.Info}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ehdg.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in cls._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu %zu\\n", offsetof({cname}, {fname}), '
+                         f'sizeof((({cname}*)0)->{fname}));')
+    lines += ["  return 0;", "}"]
+    out_dir = os.path.join(ROOT, "paper_1601_06681_gb300", "_build", "abi_layout")
+    os.makedirs(out_dir, exist_ok=True)
+    src, exe = os.path.join(out_dir, "layout.c"), os.path.join(out_dir, "layout")
+    with open(src, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), src, "-o", exe],
+                   check=True, capture_output=True)
+    got = subprocess.run([exe], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {}
+    for ln in filter(None, got):
+        parts = ln.split()
+        c_layout[tuple(parts[:-2]) if parts[1] != "size" else (parts[0],)] = (
+            tuple(int(v) for v in parts[-2:]) if parts[1] != "size" else int(parts[2]))
+    for cname, cls in structs.items():
+        assert c_layout[(cname,)] == C.sizeof(cls), cname
+        for fname, ftype in cls._fields_:
+            assert c_layout[(cname, fname)] == (getattr(cls, fname).offset, C.sizeof(ftype)), \
+                (cname, fname)
