@@ -120,7 +120,8 @@ typedef struct {
   int p;                       /* polynomial degree, 1..6 (dim 2), 1..3 (dim 3) */
   ehdg_scheme scheme;
   double dt;                   /* time step (ignored for STEADY) */
-  double tol;                  /* stop when ||uhat^{k+1}-uhat^k||_{L2(E_h)} < tol */
+  double tol;                  /* stop when ||uhat^{k+1}-uhat^k||_{L2(E_h)} < tol; >= 0 (0 runs
+                                  max_iter iterations, reported as not converged) */
   int max_iter;                /* iteration cap per step, >= 1 */
   ehdg_precision precision;    /* one of ehdg_precision */
   const double* beta_const;    /* [dim] constant velocity, or NULL */

@@ -175,3 +175,29 @@ def test_binding_structs_have_the_c_layout():
         for fname, ftype in cls._fields_:
             assert c_layout[(cname, fname)] == (getattr(cls, fname).offset, C.sizeof(ftype)), \
                 (cname, fname)
+
+
+def test_create_validates_the_problem_before_any_cuda_call():
+    """Invalid problems are rejected with EHDG_ERR_INVALID (1) or
+    EHDG_ERR_UNSUPPORTED (7) and a message, before the library touches the
+    GPU, so the checks hold on a machine without one."""
+    import pytest
+    build.build()
+    mesh = ehdg.ehdg_mesh_structured((4, 4))
+    base = dict(scheme="be", dt=0.01, beta_const=[1.0, 0.5])
+    cases = [
+        (dict(p=0), 7, "p must be"), (dict(p=7), 7, "p must be"),
+        (dict(dt=0.0), 1, "dt must be positive"), (dict(dt=float("nan")), 1, "dt must be positive"),
+        (dict(tol=-1e-10), 1, "bad tol"), (dict(tol=float("nan")), 1, "bad tol"),
+        (dict(max_iter=0), 1, "max_iter"),
+        (dict(precision="fp32", inner_sweeps=65), 1, "inner_sweeps must be 0..64"),
+        (dict(beta_const=None), 1, "exactly one of beta_const and beta_nodes"),
+        (dict(pde="sw", beta_const=None), 1, "tagged WALL"),
+    ]
+    for kw, status, msg in cases:
+        args = dict(base, **kw)
+        p = args.pop("p", 2)
+        with pytest.raises(ehdg.EhdgError) as ei:
+            ehdg.Solver(mesh, p, **args)
+        assert ei.value.status == status, (kw, ei.value)
+        assert msg in str(ei.value), (kw, str(ei.value))
