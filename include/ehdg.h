@@ -181,7 +181,12 @@ ehdg_status ehdg_mesh_structured(int dim, const int64_t n[3], const double lo[3]
                                  const double hi[3], int32_t boundary_tag, ehdg_mesh_desc* out);
 void ehdg_mesh_free(ehdg_mesh_desc* mesh);
 
-/* Validate the mesh, upload it, assemble every local operator of Sec. 3
+/* Validate the mesh (indices in range, elem_face and face_elem consistent,
+ * every local face on exactly one face, interior faces with the minus element
+ * on the low side, boundary tags matching the PDE, positive finite sizes, and
+ * conforming geometry: the two elements of an interior face meet on it, to
+ * 1e-9 of the coordinates' magnitude; otherwise EHDG_ERR_INVALID before any
+ * CUDA call), upload it, assemble every local operator of Sec. 3
  * (eq. transportLocal or localSolverDD plus the time term) on the GPU and
  * factor it. `cuda_stream` is a cudaStream_t (NULL: the legacy default
  * stream) on which all later work of the context is ordered. */

@@ -125,6 +125,23 @@ ehdg_status validate_mesh(const ehdg_mesh_desc* m, ehdg_pde pde) {
                                           ": interior faces need the minus element on the low side");
       if (tag != EHDG_FACE_INTERIOR)
         return fail(EHDG_ERR_INVALID, "interior face with a boundary tag");
+      // conforming geometry: along the face's normal axis the plus element
+      // starts where the minus element ends, and along every other axis the
+      // two span the same interval (to rounding, relative to the coordinates)
+      const int ax = lm >> 1;
+      const double* lo_m = m->elem_lo + em * dim;
+      const double* h_m = m->elem_h + em * dim;
+      const double* lo_p = m->elem_lo + ep * dim;
+      const double* h_p = m->elem_h + ep * dim;
+      for (int a = 0; a < dim; ++a) {
+        const double scale = std::max(std::fabs(lo_m[a]) + h_m[a], std::fabs(lo_p[a]) + h_p[a]);
+        const double off = (a == ax) ? lo_m[a] + h_m[a] - lo_p[a] : lo_m[a] - lo_p[a];
+        const double dh = (a == ax) ? 0.0 : h_m[a] - h_p[a];
+        if (std::fabs(off) > 1e-9 * scale || std::fabs(dh) > 1e-9 * scale)
+          return fail(EHDG_ERR_INVALID, "face " + std::to_string(f) +
+                                            ": the elements on its two sides do not meet on it "
+                                            "(non-conforming mesh)");
+      }
       seen[ep * F + lp]++;
     } else {
       if (lp != -1) return fail(EHDG_ERR_INVALID, "boundary face with a plus local face");
