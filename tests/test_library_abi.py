@@ -40,6 +40,21 @@ def test_structured_mesh_matches_input_generator():
         assert got["n_face"] == want["n_face"]
 
 
+def test_structured_mesh_with_bounds_and_tag_matches_input_generator():
+    """The library's mesh of a box [lo, hi] other than the unit box, with
+    wall tags: the same connectivity and tags as the generator, and the same
+    geometry to rounding (the two compute the corners in their own order)."""
+    build.build()
+    for n, lo, hi in [((5, 4), (-1.0, 2.0), (3.0, 2.5)),
+                      ((3, 2, 4), (0.25, -0.5, 10.0), (1.0, 0.5, 10.2))]:
+        got = ehdg.ehdg_mesh_structured(n, lo=lo, hi=hi, boundary_tag=W.TAG_WALL)
+        want = W.structured_mesh(n, lo=lo, hi=hi, boundary_tag=W.TAG_WALL)
+        for k in ("elem_face", "face_elem", "face_local", "face_tag"):
+            assert np.array_equal(got[k], want[k]), (n, k)
+        for k in ("elem_lo", "elem_h"):
+            assert np.allclose(got[k], want[k], rtol=0, atol=1e-14 * max(map(abs, hi))), (n, k)
+
+
 def test_structured_mesh_rejects_bad_sizes():
     build.build()
     try:
