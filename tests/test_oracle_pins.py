@@ -1059,3 +1059,61 @@ def test_sw_trace_pin_catches_planted_mistakes(kind, monkeypatch):
     assert _sw_fixed_point_vs_direct() < 1e-12
     monkeypatch.setattr(Problem, "trace", _planted_sw_trace(kind))
     assert _sw_fixed_point_vs_direct() > 1e-6, kind
+
+
+def _time_exact_bounded(scheme, tfun, dtfun, max_iter=300):
+    """_time_exact (the BE / CN exactness pins above) with the iteration
+    count per step bounded, for planted-mistake runs that may diverge."""
+    p, beta, dt, n_steps = 2, np.array([0.7, 1.1]), 0.05, 4
+    mesh = W.structured_mesh((3, 3))
+    prob = Problem(mesh, p, scheme=scheme, dt=dt, beta_const=beta)
+    a = lambda x: 1 + x[..., 0] - 2 * x[..., 1] + x[..., 0] * x[..., 1]
+    ga = lambda x: np.stack([1 + x[..., 1], -2 + x[..., 0]], -1)
+    X, XF = node_coords(mesh, p), face_point_coords(mesh, p, prob.ref.q)
+    ue = lambda x, t: a(x) * tfun(t)
+    f_of_t = lambda t: (a(X) * dtfun(t) + tfun(t) * (ga(X) @ beta))[:, None, :]
+    with np.errstate(all="ignore"):
+        u, _, _, _ = prob.run(ue(X, 0.0)[:, None, :], n_steps, g_of_t=lambda t: ue(XF, t),
+                              f_of_t=f_of_t, tol=1e-14, max_iter=max_iter)
+        err = np.abs(u[:, 0, :] - ue(X, n_steps * dt)).max()
+    return float(err) if np.isfinite(err) else math.inf
+
+
+def _planted_step_system(kind):
+    """Problem.step_system with one plausible slip in the time discretisation
+    planted ("none" leaves it unchanged)."""
+    real = Problem.step_system
+    mv = lambda A, x: np.einsum("eij,ej->ei", A, x)
+
+    def step_system(self, u_n, uh_n, f_new=None, f_old=None):
+        A, r0, cB = real(self, u_n, uh_n, f_new, f_old)
+        M = self._mass()
+        un = u_n.reshape(self.nel, self.n)
+        if kind == "BE old state without 1/dt":
+            r0 = r0 - mv(M, un) / self.dt + mv(M, un)
+        elif kind == "BE forcing at the old time" and f_new is not None and f_old is not None:
+            r0 = r0 + mv(M, (f_old - f_new).reshape(self.nel, self.n))
+        elif kind == "CN old trace term dropped":
+            r0 = r0 - 0.5 * mv(self.B, self.gather(uh_n))
+        elif kind == "CN forcing at the new time only" and f_old is not None:
+            r0 = r0 + 0.5 * mv(M, (f_new - f_old).reshape(self.nel, self.n))
+        elif kind == "CN trace weight 1":
+            cB = 1.0
+        return A, r0, cB
+    return step_system
+
+
+@pytest.mark.parametrize("kind", ["BE old state without 1/dt", "BE forcing at the old time",
+                                  "CN old trace term dropped", "CN forcing at the new time only",
+                                  "CN trace weight 1"])
+def test_time_discretisation_pins_catch_planted_mistakes(kind, monkeypatch):
+    """Each plausible slip in a step's local system (backward Euler or
+    Crank-Nicolson) fails the exactness pin of its scheme: BE exact for
+    solutions linear in t, CN exact for quadratic ones."""
+    lin = (lambda t: 1 + 2 * t, lambda t: 2.0 + 0 * t)
+    quad = (lambda t: 1 + t + 3 * t * t, lambda t: 1 + 6 * t)
+    scheme, fns = ("be", lin) if kind.startswith("BE") else ("cn", quad)
+    monkeypatch.setattr(Problem, "step_system", _planted_step_system("none"))
+    assert _time_exact_bounded(scheme, *fns) < 1e-11
+    monkeypatch.setattr(Problem, "step_system", _planted_step_system(kind))
+    assert _time_exact_bounded(scheme, *fns) > 1e-6, kind
