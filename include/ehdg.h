@@ -383,6 +383,9 @@ ehdg_status ehdg_batch_autotune_sweep_tile(ehdg_batch b, const int* candidates, 
  * mixed-precision instance. */
 ehdg_status ehdg_batch_autotune_inner_sweeps(ehdg_batch b, const int* candidates,
                                              int n_candidates, int* best_m, double* best_ms);
+/* Waits for the batch's stream, then destroys its graph, its streams, its
+ * device arrays and every instance's context (the handles ehdg_batch_instance
+ * returned become invalid). NULL is a no-op. */
 void ehdg_batch_destroy(ehdg_batch b);
 
 /* FP64 residual of Algorithm 1's convergence check (Sec. 3, "check
