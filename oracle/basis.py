@@ -36,6 +36,15 @@ def gll(p):
     return x, w
 
 
+def nodes_1d(p):
+    """Nodes and weights of the 1D nodal basis of degree p: the GLL points for
+    p >= 1; for p = 0 (the piecewise-constant space of Sec. 2 with p = 0) the
+    single node at the centre of [-1, 1], weight 2."""
+    if p == 0:
+        return np.zeros(1), np.full(1, 2.0)
+    return gll(p)
+
+
 def gauss(q):
     """Gauss-Legendre rule with q points on [-1, 1] (numpy's leggauss)."""
     return npleg.leggauss(q)

@@ -11,7 +11,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .basis import gll
+from .basis import nodes_1d
 
 
 def node_multi_index(dim, p):
@@ -47,7 +47,7 @@ def face_volume_nodes(dim, p, f):
 def node_coords(mesh, p):
     """Physical coordinates of every volume node, [n_elem, Np, dim]."""
     dim = mesh["dim"]
-    r, _ = gll(p)
+    r, _ = nodes_1d(p)
     mi = node_multi_index(dim, p)
     ref = r[mi]  # [Np, dim]
     lo = mesh["elem_lo"][:, None, :]

@@ -30,7 +30,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .basis import gauss, gll, lagrange, lagrange_deriv, quad_points
+from .basis import gauss, lagrange, lagrange_deriv, nodes_1d, quad_points
 
 
 def _tensor(mats):
@@ -50,7 +50,7 @@ class RefElement:
 
     def __init__(self, dim, p, q):
         self.dim, self.p, self.q = dim, p, q
-        self.r, self.wgll = gll(p)
+        self.r, self.wgll = nodes_1d(p)
         self.xi, self.om = gauss(q)
         L = lagrange(self.r, self.xi)
         D = lagrange_deriv(self.r, self.xi)

@@ -1117,3 +1117,50 @@ def test_time_discretisation_pins_catch_planted_mistakes(kind, monkeypatch):
     assert _time_exact_bounded(scheme, *fns) < 1e-11
     monkeypatch.setattr(Problem, "step_system", _planted_step_system(kind))
     assert _time_exact_bounded(scheme, *fns) > 1e-6, kind
+
+
+@pytest.mark.parametrize("n,beta", [((5, 4), (0.9, -0.6)), ((3, 4, 2), (-0.4, 0.7, 0.5))])
+def test_p0_is_implicit_upwind_finite_volumes(n, beta):
+    """With p = 0 (one constant per element) the upwind trace takes the
+    upwind element's value, and the local equation with the test function 1
+    is the cell balance |K| (u_K - u_K^n) / dt + sum over faces |F| (beta.n)
+    u_upwind = 0: backward-Euler first-order upwind finite volumes. The
+    finite-volume system is assembled here from the mesh alone and solved
+    directly; the eHDG fixed point and its traces must equal it."""
+    dim = len(n)
+    hi = [1.0, 0.8, 0.6][:dim]
+    mesh = W.structured_mesh(n, hi=hi)
+    beta, dt = np.array(beta), 0.05
+    prob = Problem(mesh, 0, scheme="be", dt=dt, beta_const=beta)
+    rng = np.random.default_rng(17)
+    u0 = rng.standard_normal((prob.nel, 1, 1))
+    g = rng.standard_normal((prob.nface, 1))
+    u, uh, hist = prob.solve_step(u0, g_new=g, tol=1e-15, max_iter=3000)
+    assert hist[-1] < 1e-14
+    vol = np.prod(mesh["elem_h"], axis=1)
+    A = np.diag(vol / dt)
+    b = vol / dt * u0[:, 0, 0]
+    up = np.empty(prob.nface, dtype=np.int64)
+    for f in range(prob.nface):
+        em, ep = mesh["face_elem"][f]
+        lm = int(mesh["face_local"][f, 0])
+        ax = lm // 2
+        bn = (1.0 if lm % 2 else -1.0) * beta[ax]          # beta.n of the minus element
+        area = np.prod(np.delete(mesh["elem_h"][em], ax))
+        if bn > 0:                                          # em is upwind
+            A[em, em] += area * bn
+            if ep >= 0:
+                A[ep, em] -= area * bn
+            up[f] = em
+        else:                                               # ep (or g) is upwind
+            if ep >= 0:
+                A[em, ep] += area * bn
+                A[ep, ep] -= area * bn
+                up[f] = ep
+            else:
+                b[em] -= area * bn * g[f, 0]
+                up[f] = -1
+    u_fv = np.linalg.solve(A, b)
+    assert rel(u[:, 0, 0], u_fv) < 1e-12
+    want_trace = np.where(up >= 0, u_fv[np.maximum(up, 0)], g[:, 0])
+    assert np.abs(uh[:, 0] - want_trace).max() < 1e-12
