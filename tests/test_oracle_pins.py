@@ -1164,3 +1164,88 @@ def test_p0_is_implicit_upwind_finite_volumes(n, beta):
     assert rel(u[:, 0, 0], u_fv) < 1e-12
     want_trace = np.where(up >= 0, u_fv[np.maximum(up, 0)], g[:, 0])
     assert np.abs(uh[:, 0] - want_trace).max() < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Table 2: iterations per time step (warm start from the previous step)
+# ---------------------------------------------------------------------------
+
+def _table2():
+    rows = []
+    with open(os.path.join(GOLDEN, "table2_iterations.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                rows.append([int(v) for v in line.split()])
+    return rows
+
+
+def _sw_standing_wave_iterations(N, p, dt, n_steps=3):
+    """Iterations of each of n_steps backward-Euler steps of the Sec. 4.4
+    standing wave, each step from the previous step's solution, stopped by
+    the rule of Sec. 4.1 (change of the L2 error against the exact solution
+    at the new time below 1e-10)."""
+    s2 = math.sqrt(2.0)
+    ex = lambda t: [lambda x: np.cos(PI * x[..., 0]) * np.cos(PI * x[..., 1]) * math.cos(s2 * PI * t),
+                    lambda x: np.sin(PI * x[..., 0]) * np.cos(PI * x[..., 1]) * math.sin(s2 * PI * t) / s2,
+                    lambda x: np.cos(PI * x[..., 0]) * np.sin(PI * x[..., 1]) * math.sin(s2 * PI * t) / s2]
+    mesh = W.structured_mesh((N, N), boundary_tag=W.TAG_WALL)
+    prob = Problem(mesh, p, pde="sw", scheme="be", dt=dt, Phi=1.0)
+    X = node_coords(mesh, p)
+    u = np.stack([f(X) for f in ex(0.0)], 1)
+    uh = prob.trace(u)
+    its = []
+    for n in range(n_steps):
+        e_t = ex((n + 1) * dt)
+        err = lambda v: math.sqrt(sum(l2_volume(prob, np.roll(v, -k, axis=1), e_t[k]) ** 2
+                                      for k in range(3)))
+        state = {"prev": None}
+
+        def stop(unew, uold):
+            e = err(unew)
+            pe = state["prev"] if state["prev"] is not None else err(uold)
+            state["prev"] = e
+            return abs(e - pe) < 1e-10
+        u, uh, hist = prob.solve_step(u, uh, max_iter=200, stop=stop)
+        its.append(len(hist))
+    return its
+
+
+def _advection_3d_iterations(N, p, dt, n_steps=3):
+    """The same for the Sec. 4.5 moving Gaussian (beta = (0.2, 0.2, 0.2),
+    exact inflow data) on N^3 hexahedra."""
+    mesh = W.structured_mesh((N, N, N))
+    prob = Problem(mesh, p, scheme="be", dt=dt, beta_const=np.array([0.2, 0.2, 0.2]))
+    X, XF = node_coords(mesh, p), face_point_coords(mesh, p, prob.ref.q)
+    ue = lambda x, t: np.exp(-5 * ((x[..., 0] - 0.2 * t) ** 2 + (x[..., 1] - 0.2 * t) ** 2
+                                   + (x[..., 2] - 0.2 * t) ** 2))
+    u = ue(X, 0.0)[:, None, :]
+    uh = prob.trace(u, ue(XF, 0.0))
+    its = []
+    for n in range(n_steps):
+        t = (n + 1) * dt
+        u, uh, hist = prob.solve_step(u, uh, g_new=ue(XF, t), max_iter=200,
+                                      stop=_paper_stop_error_change(prob, lambda x: ue(x, t)))
+        its.append(len(hist))
+    return its
+
+
+@pytest.mark.parametrize("nel2d", [16, 64])
+def test_table2_iterations_per_time_step(nel2d):
+    """Table 2 on its two smallest meshes, p = 1..4: with each step started
+    from the previous solution, every step's count lies within 2 of the
+    printed one (the oracle counts local solves, one more than the printed
+    count in most rows); the smaller time step never needs more iterations;
+    and the 3D advection count is the same in every step, as the paper
+    states for transport."""
+    N2 = int(round(math.sqrt(nel2d)))
+    N3 = int(round(nel2d ** (1.0 / 3.0))) if nel2d == 64 else 2
+    for row in _table2():
+        if row[0] != nel2d:
+            continue
+        p = row[2]
+        sw3, sw4 = (_sw_standing_wave_iterations(N2, p, dt) for dt in (1e-3, 1e-4))
+        ad3, ad4 = (_advection_3d_iterations(N3, p, dt) for dt in (1e-3, 1e-4))
+        for its, paper in ((sw3, row[3]), (sw4, row[4]), (ad3, row[5]), (ad4, row[6])):
+            assert all(abs(k - paper) <= 2 for k in its), (nel2d, p, its, paper)
+        assert max(sw4) <= min(sw3) and max(ad4) <= min(ad3), (nel2d, p, sw3, sw4, ad3, ad4)
+        assert len(set(ad3)) == 1 and len(set(ad4)) == 1, (nel2d, p, ad3, ad4)
