@@ -1249,3 +1249,15 @@ def test_table2_iterations_per_time_step(nel2d):
             assert all(abs(k - paper) <= 2 for k in its), (nel2d, p, its, paper)
         assert max(sw4) <= min(sw3) and max(ad4) <= min(ad3), (nel2d, p, sw3, sw4, ad3, ad4)
         assert len(set(ad3)) == 1 and len(set(ad4)) == 1, (nel2d, p, ad3, ad4)
+
+
+def test_standing_wave_takes_two_iterations_per_step_at_tiny_dt():
+    """Sec. 4.4 with dt = 1e-6: the paper reports 2 iterations per step for
+    every mesh and order (the previous step's solution is almost the new
+    one); the oracle takes 2, or 1 on the coarsest p = 1 mesh."""
+    for N in (4, 8):
+        for p in (1, 2, 3, 4):
+            its = _sw_standing_wave_iterations(N, p, 1e-6, n_steps=2)
+            assert all(k in (1, 2) for k in its), (N, p, its)
+            if N == 8 or p > 1:
+                assert its == [2, 2], (N, p, its)
