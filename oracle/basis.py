@@ -4,7 +4,7 @@ The paper fixes neither basis nor quadrature (Sec. 2 only asks for degree-p
 polynomials per element and per face). Readings used throughout the oracle:
   * tensor-product Lagrange basis on the p+1 Gauss-Lobatto-Legendre (GLL)
     points of [-1, 1] per axis (the Q^p space, since every mesh in Sec. 4 is
-    made of quads/hexes);
+    made of quads/hexes); for p = 0 the one node is the centre (nodes_1d);
   * Gauss-Legendre quadrature with enough points to integrate every product
     exactly (q = p+1 for constant coefficients, ceil(3p/2)+1 when the velocity
     is a degree-p interpolant).
