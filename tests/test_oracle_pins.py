@@ -1261,3 +1261,51 @@ def test_standing_wave_takes_two_iterations_per_step_at_tiny_dt():
             assert all(k in (1, 2) for k in its), (N, p, its)
             if N == 8 or p > 1:
                 assert its == [2, 2], (N, p, its)
+
+
+def test_p0_shallow_water_is_godunov_finite_volumes():
+    """With p = 0 the upwind HDG trace of the linear shallow-water system is
+    the exact Riemann (Godunov) state of the wave system phi_t + Phi div u = 0,
+    u_t + grad phi = 0: phi* = {phi} + sqrt(Phi)/2 (u_n^- - u_n^+), u_n* =
+    {u_n} + (phi^- - phi^+) / (2 sqrt(Phi)), with a wall as the reflected
+    state (u_n* = 0). Each cell then satisfies |K| (phi - phi^n)/dt + sum_F
+    |F| Phi u_n* = 0 and |K| (u - u^n)/dt + sum_F |F| phi* n = 0. That
+    backward-Euler finite-volume system, assembled here from the mesh alone,
+    and the eHDG fixed point must agree."""
+    Phi, dt = 1.7, 0.02
+    sq = math.sqrt(Phi)
+    mesh = W.structured_mesh((5, 4), hi=(1.0, 0.8), boundary_tag=W.TAG_WALL)
+    prob = Problem(mesh, 0, pde="sw", scheme="be", dt=dt, Phi=Phi)
+    rng = np.random.default_rng(23)
+    u0 = rng.standard_normal((prob.nel, 3, 1))
+    u, _, hist = prob.solve_step(u0, tol=1e-15, max_iter=3000)
+    assert hist[-1] < 1e-14
+    nel = prob.nel
+    vol = np.prod(mesh["elem_h"], axis=1)
+
+    def residual(U):                                   # U [nel, 3] = (phi, u, v)
+        R = (vol / dt)[:, None] * (U - u0[:, :, 0])
+        for f in range(prob.nface):
+            em, ep = mesh["face_elem"][f]
+            lm = int(mesh["face_local"][f, 0])
+            ax = lm // 2
+            s = 1.0 if lm % 2 else -1.0                # n^- = s e_ax
+            area = np.prod(np.delete(mesh["elem_h"][em], ax))
+            pm, unm = U[em, 0], s * U[em, 1 + ax]
+            if ep >= 0:
+                pp, unp = U[ep, 0], s * U[ep, 1 + ax]  # plus state in the n^- frame
+                phis = 0.5 * (pm + pp) + 0.5 * sq * (unm - unp)
+                uns = 0.5 * (unm + unp) + (pm - pp) / (2.0 * sq)
+            else:                                      # wall: reflected state
+                phis, uns = pm + sq * unm, 0.0
+            R[em, 0] += area * Phi * uns
+            R[em, 1 + ax] += area * phis * s
+            if ep >= 0:
+                R[ep, 0] -= area * Phi * uns
+                R[ep, 1 + ax] -= area * phis * s
+        return R.ravel()
+
+    r0 = residual(np.zeros((nel, 3)))
+    A = np.stack([residual(np.eye(3 * nel)[k].reshape(nel, 3)) - r0 for k in range(3 * nel)], 1)
+    u_fv = np.linalg.solve(A, -r0).reshape(nel, 3)
+    assert rel(u[:, :, 0], u_fv) < 1e-12
